@@ -1,0 +1,481 @@
+#!/usr/bin/env python3
+"""Benchmark: gate-applications/s of a 30-qubit random brickwork circuit (depth 40, complex64) on one GB300.
+
+One step = one full simulation of the circuit through libqsim: |0...0>, every pass of the planned circuit
+(fused dense blocks on tensor cores or CUDA cores, diagonal passes), then the readouts the paper's
+benchmarks use -- <Z_i>, <Z_i Z_{i+1}> and 1000 measurement samples (Sec. 2.2: 1000 shots per circuit).
+value = unfused input gates x steps x ranks / max-over-ranks device time of the steps.
+
+Also reported: the plain per-gate path and every fused variant (ms/step, passes, infidelity against the
+FP64 oracle on the 20-qubit instance of the same generator), the live per-pass roofline of the dominant
+kernel, an end-to-end number through the public API with host buffers, SM clocks during the timed
+region, and the FP64 oracle timed on the host cores on a bounded sample (cpu_baseline).
+
+--impl reference times the oracle itself (the reference arm: there is no upstream code for this paper).
+Multi-GPU (--gpus N under torchrun): every rank simulates its own seeded instance (independent problems,
+no data-path collective) -> weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+UNIT = "gate-applications/s"
+METRIC = "gate-applications/s, 30-qubit random brickwork depth 40 (Haar U(2) + CZ), complex64, 1000 shots"
+SEED = 3
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=30)
+    p.add_argument("--depth", type=int, default=40)
+    p.add_argument("--shots", type=int, default=1000)
+    p.add_argument("--path", default="auto", help="auto | plain | simt4 | simt5 | tf32x3 | bf16x3 | bf16x6")
+    p.add_argument("--no-variants", action="store_true", help="skip the secondary path measurements")
+    p.add_argument("--no-accuracy", action="store_true", help="skip the 20-qubit infidelity check")
+    p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ---- distributed plumbing (independent replicas; the only collectives are a barrier and a max) ---------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend="gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def allmax(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region --------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks.", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- roofline inputs -----------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+KERNEL_SOURCES = {"dense_small": "k_gates.cu", "diag": "k_gates.cu", "dense_tile": "k_gates.cu", "tc": "k_tc.cu"}
+
+
+def source_sha(kind):
+    p = os.path.join(ROOT, "paper_2511_14664_gb300", "csrc", KERNEL_SOURCES[kind])
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
+
+
+def profiled_traffic(kind, n):
+    """DRAM bytes per launch from a committed ncu summary (profiles/*.txt lines 'bench-traffic: {...}'),
+    used only while the kernel source is unchanged since the capture; scaled by 2^(n - n_captured)."""
+    sha = source_sha(kind)
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".txt", ".md")):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            m = re.match(r"\s*bench-traffic:\s*(\{.*\})\s*$", line)
+            if not m:
+                continue
+            try:
+                d = json.loads(m.group(1))
+            except ValueError:
+                continue
+            if d.get("kind") == kind and d.get("source_sha") == sha:
+                return float(d["bytes_per_launch"]) * 2.0 ** (n - int(d["n"]))
+    return None
+
+
+# ---- the simulation step -------------------------------------------------------------------------------------
+PATHS = {
+    # name: (mode, max_fused, precision, tc_min_k)
+    "plain": (0, 1, 0, 5),
+    "simt4": (1, 4, 0, 5),
+    "simt5": (1, 5, 0, 5),
+    "tf32x3": (1, 6, 1, 5),
+    "bf16x3": (1, 6, 2, 5),
+    "bf16x6": (1, 6, 3, 5),
+}
+
+
+def make_plan(qsim, circuit, path, use_graph=False):
+    mode, k, prec, tcmin = PATHS[path]
+    return qsim.Plan(circuit, qsim.C64, mode=mode, max_fused=k, precision=prec, tc_min_k=tcmin, use_graph=use_graph)
+
+
+def count_readout_launches(n):
+    zl = 2 + (1 if n > 12 else 0) if n >= 12 else 1
+    return zl + 5  # expect_z kernels + (uniforms, segment sums, chunk sums, scan, sample)
+
+
+def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
+    """Run `steps` steps; returns (total_ms, per-pass ms list summed over steps)."""
+    stream = torch.cuda.current_stream()
+    npass = len(plan.pass_list)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    pass_ms = [0.0] * npass
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] if per_pass else None
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(steps):
+        st.set_basis(0)
+        if per_pass:
+            evs[0].record(stream)
+            for i in range(npass):
+                plan.execute_range(st, i, 1)
+                evs[i + 1].record(stream)
+        else:
+            plan.execute(st)
+        st.expect_z()
+        st.sample(1000 + s, shots)
+        if per_pass:
+            torch.cuda.synchronize()
+            for i in range(npass):
+                pass_ms[i] += evs[i].elapsed_time(evs[i + 1])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), pass_ms
+
+
+def infidelity_at(qsim, oracle_mod, W, n_small, depth, path, ref_cache):
+    import numpy as np
+    c = W.brickwork(n_small, depth, seed=SEED)
+    if "ref" not in ref_cache:
+        ref_cache["ref"] = oracle_mod.run(c)
+    ref = ref_cache["ref"]
+    plan = make_plan(qsim, c, path)
+    st = qsim.State(n_small, qsim.C64)
+    st.set_basis(0)
+    plan.execute(st)
+    psi = st.get_state().astype(np.complex128)
+    err = float(np.max(np.abs(psi - ref)))
+    inf = oracle_mod.infidelity(psi, ref, n_small)
+    return {"n": n_small, "infidelity": inf, "max_amp_err": err,
+            "norm_dev": abs(oracle_mod.norm2(psi, n_small) - 1.0)}
+
+
+def cpu_baseline(oracle_mod, W, n_full, depth, seconds):
+    """The FP64 oracle on the host cores: the first gates of the 24-qubit instance of the same generator,
+    run until `seconds` elapse; gate-applications/s scaled by 2^(24 - n_full) (work per gate ~ 2^n)."""
+    n_s = min(24, n_full)
+    c = W.brickwork(n_s, depth, seed=SEED)
+    psi = oracle_mod.basis(n_s, 0)
+    t = time.perf_counter()
+    g = 0
+    for gate in c.gates:
+        oracle_mod.apply_gate(psi, n_s, gate.targets, gate.controls, gate.matrix)
+        g += 1
+        if time.perf_counter() - t > seconds:
+            break
+    dt = time.perf_counter() - t
+    rate = g / dt * 2.0 ** (n_s - n_full)
+    return {"value": rate, "unit": UNIT, "cores": oracle_mod.num_threads(), "kind": "oracle",
+            "sample": f"first {g} gates of the {n_s}-qubit instance of the generator in {dt:.1f} s, "
+                      f"rate scaled by 2^({n_s}-{n_full}) (work per gate ~ 2^n)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as oracle_mod
+    import workloads as W
+    n_s = min(24, args.n)
+    c = W.brickwork(n_s, args.depth, seed=SEED)
+    per_step_gates = 24
+    psi = oracle_mod.basis(n_s, 0)
+    gi = 0
+
+    def step():
+        nonlocal gi
+        for _ in range(per_step_gates):
+            g = c.gates[gi % len(c.gates)]
+            oracle_mod.apply_gate(psi, n_s, g.targets, g.controls, g.matrix)
+            gi += 1
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    rate = per_step_gates * args.steps / dt * 2.0 ** (n_s - args.n)
+    sample = (f"each step: {per_step_gates} gates of the {n_s}-qubit instance of the generator on the FP64 "
+              f"oracle, rate scaled by 2^({n_s}-{args.n})")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"random brickwork n={args.n} depth={args.depth} seed={SEED}",
+                       "global_batch": 1, "seq_len": None, "parallelism": "replicas"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": oracle_mod.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    dist = dist_init(ws)
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+
+    torch.cuda.set_device(local)
+    qsim.lib()
+    dev = torch.cuda.current_device()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    n, depth, shots = args.n, args.depth, args.shots
+    circuit = W.brickwork(n, depth, seed=SEED + rank)
+    G = len(circuit)
+    st = qsim.State(n, qsim.C64)
+
+    # candidate paths (tensor-core variants only where the library supports them)
+    cands = ["tf32x3", "bf16x3", "bf16x6", "simt4", "simt5"]
+    plans = {}
+    for name in cands + ["plain"]:
+        try:
+            plans[name] = make_plan(qsim, circuit, name)
+            plans[name].pass_list = plans[name].passes()
+        except qsim.QsimError:
+            pass
+    # accuracy of each path on the 20-qubit instance (equal-accuracy comparison)
+    acc = {}
+    if rank == 0 and not args.no_accuracy:
+        import oracle as oracle_mod
+        cache = {}
+        for name in plans:
+            acc[name] = infidelity_at(qsim, oracle_mod, W, min(20, n), depth, name, cache)
+
+    def quick(name, steps=1, warm=1):
+        p = plans[name]
+        timed_steps(qsim, torch, st, p, warm, shots, per_pass=False)
+        ms, _ = timed_steps(qsim, torch, st, p, steps, shots, per_pass=False)
+        return ms / steps
+
+    variants = {}
+    if not args.no_variants:
+        for name in plans:
+            if name == "plain":
+                continue
+            variants[name] = {"ms_per_step": quick(name), "passes": len(plans[name].pass_list)}
+    if args.path == "auto":
+        ok = [k for k in variants if (not acc or acc[k]["infidelity"] <= 1e-9)]
+        main = min(ok, key=lambda k: variants[k]["ms_per_step"]) if ok else ("tf32x3" if "tf32x3" in plans else "simt4")
+    else:
+        main = args.path
+    plan = plans[main]
+
+    # ---- the timed region -------------------------------------------------------------------------------
+    timed_steps(qsim, torch, st, plan, args.warmup, shots, per_pass=True)
+    clocks = Clocks(uuid)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, pass_ms = timed_steps(qsim, torch, st, plan, args.steps, shots, per_pass=True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist)
+    t_max = allmax(dist, total_ms)
+    value = G * args.steps * ws / (t_max / 1000.0)
+
+    # ---- roofline of the dominant pass kind ------------------------------------------------------------------
+    peaks, peak_src = measured_peaks()
+    by_kind = {}
+    for info, ms in zip(plan.pass_list, pass_ms):
+        d = by_kind.setdefault(info["kind"], {"ms": 0.0, "bytes": 0.0, "launches": 0, "flops": 0.0})
+        d["ms"] += ms
+        d["bytes"] += info["algorithmic_bytes"] * args.steps
+        d["launches"] += args.steps
+        if info["kind"] == "tc":
+            mult = {1: 3, 2: 3, 3: 6}[info["precision"]]
+            # real GEMM per amplitude: 2 * (2 * 2^k) MACs per complex output -> 8 * 2^k flops x split products
+            d["flops"] += (2.0 ** n) * 8 * (2 ** info["k"]) * mult * args.steps
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    dk = by_kind[dom]
+    avg_s = dk["ms"] / dk["launches"] / 1000.0
+    bytes_per_launch = dk["bytes"] / dk["launches"]
+    gbs = bytes_per_launch / avg_s / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+            "traffic": profiled_traffic(dom, n), "kernel": dom, "launches_per_step": dk["launches"] // args.steps,
+            "avg_launch_ms": avg_s * 1000.0, "share_of_step": dk["ms"] / total_ms, "peak_source": peak_src}
+    if dom == "tc" and dk["flops"] > 0:
+        tflops = dk["flops"] / dk["launches"] / avg_s / 1e12
+        prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == "tc"][0]]["precision"]
+        # tf32 rate = measured bf16 rate x nominal tf32/bf16 ratio (1.1 / 2.25)
+        tpeak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25 if prec == 1 else 1.0)
+        roof["tensor"] = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak}
+        if tflops / tpeak > hbm_frac:
+            roof = {**roof, "bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": tflops / tpeak}
+
+    # ---- plain per-gate path (the baseline the fused forms must beat) -------------------------------------------
+    plain = None
+    if not args.no_variants and "plain" in plans:
+        pp = plans["plain"]
+        timed_steps(qsim, torch, st, pp, 1, shots, per_pass=False)
+        ms, pms = timed_steps(qsim, torch, st, pp, 1, shots, per_pass=True)
+        dense = [(i, m) for i, (i2, m) in enumerate(zip(pp.pass_list, pms)) if pp.pass_list[i]["kind"] == "dense_small"]
+        dense_bytes = sum(pp.pass_list[i]["algorithmic_bytes"] for i, _ in dense)
+        dense_ms = sum(m for _, m in dense)
+        plain = {"gates_per_s": G / (ms / 1000.0), "ms_per_step": ms, "passes": len(pp.pass_list),
+                 "per_gate_pass_gbs": dense_bytes / (dense_ms / 1000.0) / 1e9 if dense_ms > 0 else None}
+
+    # ---- end to end through the public API with host buffers -----------------------------------------------------
+    import ctypes
+    h2d = sum(16 * (1 << (2 * len(g.targets))) + ctypes.sizeof(qsim.Gate) for g in circuit.gates)
+    d2h = 8 * (2 * n - 1) + 8 * shots
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for s in range(e2e_steps):
+        p = make_plan(qsim, circuit, main)   # host gate list -> device (planning, upload, FP64 composition)
+        st.set_basis(0)
+        p.execute(st)
+        zi, zz = st.expect_z()
+        smp = st.sample(5000 + s, shots)     # device -> host
+        p.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    e2e_val = allmax(dist, e2e_s)
+    e2e = {"value": G * ws / e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if main in ("plain", "simt4", "simt5") else {"tf32x3": "tf32x3", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[main],
+        "data": "synthetic",
+        "config": {"workload": f"random brickwork n={n} depth={depth} seed={SEED}(+rank), {G} gates, complex64",
+                   "path": main, "passes": len(plan.pass_list), "global_batch": ws, "seq_len": None,
+                   "parallelism": f"replicas x{ws}", "shots": shots,
+                   "l2": f"state {2 ** n * 8 / 2 ** 30:.0f} GiB > L2 129 MB: inputs larger than L2, no flush"},
+        "gpu_launches": args.steps * (1 + len(plan.pass_list) + count_readout_launches(n)),
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": e2e,
+        "plain": plain,
+        "variants": variants,
+        "accuracy": acc,
+        "plan_ms": plan.info["host_plan_ms"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle as oracle_mod
+        line["cpu_baseline"] = cpu_baseline(oracle_mod, W, n, depth, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,256 @@
+/*
+ * qsim.h -- C ABI of libqsim, a single-GPU (GB300, sm_103a) state-vector simulator.
+ *
+ * The simulated object is the state vector of the paper (arXiv 2511.14664, Sec. 2.1 "State-Vector
+ * Simulation"): 2^n complex amplitudes, one per computational basis state, on which each gate acts as
+ * a tensor-product operator. Its hot path -- applying gates to all 2^n amplitudes -- runs in the
+ * library's own CUDA kernels; PyTorch (or any other caller) only provides device memory and a stream.
+ *
+ * Conventions used by every entry point:
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - for a gate on targets (t_0, ..., t_{k-1}) the matrix row/column index is m = sum_j bit_{t_j} 2^j;
+ *   - gate matrices are 2^k x 2^k complex128, row-major, interleaved (re, im), in HOST memory; the
+ *     library copies them before the call returns, so the caller may free them at once;
+ *   - controls fire on |1>;
+ *   - amplitudes are stored interleaved (re, im): complex64 = 2 x float32 (8 B), complex128 =
+ *     2 x float64 (16 B), amplitude x at byte offset x * sizeof(amplitude).
+ *
+ * Return codes: QSIM_OK (0) on success, otherwise one of the QSIM_E* codes below; a thread-local
+ * message describing the failure is available from qsim_last_error(). No C++ exception crosses the ABI.
+ * Argument errors (QSIM_EINVAL) are detected before any work is enqueued, so the state is unchanged.
+ * After QSIM_ECUDA or QSIM_ETIMEOUT the state contents are undefined.
+ *
+ * Threading and streams: a handle is bound to one CUDA stream and is not thread-safe. Gate and run
+ * calls are asynchronous on that stream. Calls that write host outputs (norm, probabilities,
+ * expectations, samples, get_state to host) synchronise the stream before returning.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QSIM_ABI_VERSION 1
+
+/* Status codes. */
+#define QSIM_OK 0
+#define QSIM_EINVAL 1       /* bad qubit index, duplicate qubit, control that is also a target, NULL, size */
+#define QSIM_ENOMEM 2       /* device or host allocation failed, or the caller's buffer is too small */
+#define QSIM_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define QSIM_ETIMEOUT 4     /* a bounded device-side wait expired; the kernel stopped and reported it */
+#define QSIM_EUNSUPPORTED 5 /* valid request that this build does not implement (e.g. k too large) */
+
+/* Amplitude types. */
+#define QSIM_C64 0  /* complex64: float32 real and imaginary parts */
+#define QSIM_C128 1 /* complex128: float64 real and imaginary parts */
+
+/* Arithmetic used for fused dense blocks (Sec. 2.1: fusion trades flops for arithmetic intensity). */
+#define QSIM_PREC_SIMT 0   /* CUDA-core FMA in the state's own precision */
+#define QSIM_PREC_TF32X3 1 /* tensor cores: 3 TF32 products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+#define QSIM_PREC_BF16X3 2 /* tensor cores: 2-way BF16 split, 3 products, FP32 accumulation */
+#define QSIM_PREC_BF16X6 3 /* tensor cores: 3-way BF16 split, 6 products, FP32 accumulation */
+
+/* Run modes. */
+#define QSIM_RUN_PLAIN 0 /* one device pass per gate (diagonal gates touch only their non-unit entries) */
+#define QSIM_RUN_FUSED 1 /* gates merged into dense or diagonal blocks of at most max_fused qubits */
+
+#define QSIM_MAX_TARGETS 8
+#define QSIM_MAX_CONTROLS 8
+#define QSIM_MAX_QUBITS 36
+
+typedef struct qsim_state* qsim_h;
+typedef struct qsim_plan* qsim_plan_h;
+
+/* One gate: U (2^k x 2^k, FP64 complex, host) on `targets`, applied where all `controls` are 1. */
+typedef struct {
+    int32_t k;                            /* number of targets, 1..QSIM_MAX_TARGETS */
+    int32_t nc;                           /* number of controls, 0..QSIM_MAX_CONTROLS */
+    int32_t targets[QSIM_MAX_TARGETS];    /* target j <-> bit j of the matrix index */
+    int32_t controls[QSIM_MAX_CONTROLS];
+    const double* matrix;                 /* interleaved complex128, row-major, host */
+} qsim_gate;
+
+/* A circuit: gates applied in array order. */
+typedef struct {
+    int32_t n;                /* number of qubits */
+    int32_t num_gates;
+    const qsim_gate* gates;   /* host array of num_gates gates */
+} qsim_circuit;
+
+/* Options for planning a circuit. Zero-initialise, then set fields. */
+typedef struct {
+    int32_t mode;       /* QSIM_RUN_PLAIN or QSIM_RUN_FUSED */
+    int32_t max_fused;  /* fusion width k for QSIM_RUN_FUSED: 1..6 (0 = 5) */
+    int32_t precision;  /* QSIM_PREC_* for dense blocks of >= tc_min_k qubits (complex64 states only) */
+    int32_t tc_min_k;   /* smallest dense block sent to the tensor-core kernel (0 = 5) */
+    int32_t use_graph;  /* 1: replay the plan's launches from a CUDA graph captured on first execution */
+    int32_t reserved[3];
+} qsim_run_opts;
+
+/* What a plan does per execution (filled by qsim_plan_create). */
+typedef struct {
+    int64_t input_gates;     /* unfused gates in the circuit */
+    int64_t passes;          /* device passes over the state (kernel launches on the state) */
+    int64_t dense_blocks;    /* passes applying a dense matrix on CUDA cores */
+    int64_t tc_blocks;       /* passes applying a dense matrix on tensor cores */
+    int64_t diag_blocks;     /* passes applying a diagonal */
+    int64_t reorders;        /* qubit-reorder passes */
+    double algorithmic_bytes;/* HBM bytes the passes must move at minimum (read + write) */
+    double host_plan_ms;     /* host time spent planning */
+} qsim_plan_info;
+
+/* ---- version and errors ------------------------------------------------------------------------------ */
+
+int qsim_abi_version(void);
+
+/* Message of the last failed call on this thread ("" if none). Valid until the next call. */
+const char* qsim_last_error(void);
+
+/* Bytes of a 2^n state of `dtype` (8 or 16 bytes per amplitude; Sec. 1: 2^(n-27) GiB at FP32). */
+int qsim_state_bytes(int n, int dtype, size_t* out);
+
+/* ---- state lifetime ---------------------------------------------------------------------------------- */
+
+/*
+ * Create a handle for an n-qubit state (1 <= n <= QSIM_MAX_QUBITS) of `dtype`.
+ * dev_buf: device buffer of at least qsim_state_bytes(n, dtype) bytes, 256-byte aligned, owned by the
+ *          caller, who keeps it alive until qsim_destroy; or NULL, in which case the library allocates
+ *          (and later frees) the state with cudaMalloc.
+ * stream:  the cudaStream_t every call on this handle is enqueued on (NULL = legacy default stream).
+ * The state is NOT initialised; call qsim_set_basis or qsim_set_state. The library also allocates a
+ * small device workspace for reductions (about 2^(n-9) bytes + 4 MiB).
+ */
+int qsim_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, qsim_h* out);
+int qsim_destroy(qsim_h h);
+int qsim_set_stream(qsim_h h, void* stream);
+int qsim_num_qubits(qsim_h h, int* n);
+int qsim_device_ptr(qsim_h h, void** out);
+
+/* |x>: amplitude x = 1, all others 0 (Sec. 2.1: a basis state). x < 2^n. */
+int qsim_set_basis(qsim_h h, uint64_t x);
+/* Copy a whole state in (src) or out (dst); *_on_device = 1 for device pointers, 0 for host. */
+int qsim_set_state(qsim_h h, const void* src, int src_on_device);
+int qsim_get_state(qsim_h h, void* dst, int dst_on_device);
+/* Wait for all work enqueued on h's stream and report any device-side error (QSIM_ETIMEOUT when a
+   bounded wait expired, QSIM_ECUDA for a CUDA error). */
+int qsim_synchronize(qsim_h h);
+
+/* ---- gate application (the hot path; Sec. 2.1, cost O(g 2^n)) --------------------------------------- */
+
+/*
+ * Apply U on `targets` (k of them, 1 <= k <= 6; 7..8 with QSIM_EUNSUPPORTED) controlled on `controls`
+ * (nc of them, may be NULL when nc = 0). All qubits distinct and < n. Asynchronous.
+ * Diagonal matrices (every off-diagonal entry exactly 0) touch only the amplitudes whose factor is not
+ * exactly 1; single-qubit gates use vectorised streaming or warp-shuffle butterflies; k <= 4 gathers
+ * 2^k amplitudes per thread; k = 5, 6 use a shared-memory tile kernel in the state's precision.
+ */
+int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, int nc, const double* matrix);
+
+/*
+ * Apply a dense 2^k x 2^k block (1 <= k <= 6) on `targets` with the given QSIM_PREC_* arithmetic.
+ * Tensor-core precisions need a complex64 state and k in 4..6; QSIM_PREC_SIMT works for both types.
+ * This is the single-block form of what QSIM_RUN_FUSED plans produce.
+ */
+int qsim_apply_fused(qsim_h h, const int* targets, int k, const double* matrix, int precision);
+
+/*
+ * Qubit reorder (the on-device analogue of the paper's global/local index-bit exchange, Sec. 2.1 and
+ * Sec. 2.5): exchange qubit a[i] with qubit b[i] for i < p, i.e. amplitude x moves to the index with
+ * bits a[i] and b[i] swapped. All 2p qubits distinct, p <= 8. In place, one pass over the state.
+ */
+int qsim_swap_qubits(qsim_h h, const int* a, const int* b, int p);
+
+/* ---- circuits and plans ---------------------------------------------------------------------------- */
+
+/*
+ * Plan a circuit for states of c->n qubits and `dtype`: fusion into blocks (QSIM_RUN_FUSED), choice of
+ * kernel per block, and FP64 composition of each fused block on the device (enqueued on `stream`).
+ * The plan owns its device buffers; it can be executed on any handle with matching n and dtype.
+ * info may be NULL.
+ */
+int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts, void* stream,
+                     qsim_plan_h* out, qsim_plan_info* info);
+/* Enqueue every pass of the plan on h's stream. Asynchronous. */
+int qsim_plan_execute(qsim_h h, qsim_plan_h plan);
+int qsim_plan_destroy(qsim_plan_h plan);
+
+/* One pass of a plan, for per-kernel timing and roofline accounting. */
+#define QSIM_PASS_DENSE_SMALL 0 /* dense k <= 4 on CUDA cores (register gather or warp-shuffle butterfly) */
+#define QSIM_PASS_DIAG 1        /* diagonal factors, non-unit entries only */
+#define QSIM_PASS_DENSE_TILE 2  /* dense k = 5, 6 on CUDA cores through shared memory */
+#define QSIM_PASS_TC 3          /* dense block on tensor cores (complex64) */
+typedef struct {
+    int32_t kind;             /* QSIM_PASS_* */
+    int32_t k;                /* qubits the pass's matrix acts on */
+    int32_t nc;               /* control qubits (not part of the matrix) */
+    int32_t precision;        /* QSIM_PREC_* used by the pass */
+    int64_t gates;            /* input gates merged into this pass */
+    double algorithmic_bytes; /* HBM bytes the pass must read + write */
+} qsim_pass_info;
+int qsim_plan_num_passes(qsim_plan_h plan, int64_t* out);
+int qsim_plan_pass_info(qsim_plan_h plan, int64_t i, qsim_pass_info* out);
+/* Enqueue passes [first, first + count) of the plan on h's stream (no graph). */
+int qsim_plan_execute_range(qsim_h h, qsim_plan_h plan, int64_t first, int64_t count);
+/* Plan, execute and destroy in one call (the plan's device buffers are released after the stream
+   completes the run). */
+int qsim_run(qsim_h h, const qsim_circuit* c, const qsim_run_opts* opts, qsim_plan_info* info);
+
+/* ---- readout (Sec. 2.1 "Measurement and Sampling"; Sec. 2.5 expectation values) --------------------- */
+
+/* sum_x |a_x|^2, accumulated with compensated (float-float, then FP64 TwoSum) sums. Synchronises. */
+int qsim_norm(qsim_h h, double* out);
+
+/*
+ * Marginal probabilities over `qubits` (1 <= nq <= 12): out[m] = sum of |a_x|^2 over the x whose bit
+ * qubits[j] equals bit j of m. out has 2^nq doubles (host). Compensated sums. Synchronises.
+ */
+int qsim_probs(qsim_h h, const int* qubits, int nq, double* out);
+
+/*
+ * <psi|P|psi> for the Pauli string `paulis` (n characters from "IXYZ"; character q acts on qubit q).
+ * out[0] = real part, out[1] = imaginary part (0 up to rounding). Compensated sums. Synchronises.
+ */
+int qsim_expect_pauli(qsim_h h, const char* paulis, double* out);
+
+/*
+ * All single-qubit and nearest-neighbour Z correlators in one pass: zi[i] = <Z_i> (n values) and
+ * zz[i] = <Z_i Z_{i+1}> (n - 1 values), host arrays. Compensated sums. Synchronises.
+ */
+int qsim_expect_z(qsim_h h, double* zi, double* zz);
+
+/*
+ * Draw `shots` samples x ~ |a_x|^2 / sum |a|^2 (inverse CDF: the smallest x whose inclusive prefix
+ * sum exceeds u * total). Uniform u_i is the i-th SplitMix64 output for `seed` (top 53 bits); the CDF
+ * is never materialised: block sums of 4096 amplitudes, their FP64 prefix sums, then a search inside
+ * one block per sample. out: `shots` uint64 indices, host, in the order of the uniforms. Synchronises.
+ */
+int qsim_sample(qsim_h h, uint64_t seed, int64_t shots, uint64_t* out);
+/* Same with caller-supplied uniforms u[0..shots) in [0, 1) (host). */
+int qsim_sample_uniforms(qsim_h h, const double* u, int64_t shots, uint64_t* out);
+
+/* <a|b> for two handles of equal n and dtype on the same device. out[0..1] = (re, im). Synchronises. */
+int qsim_inner(qsim_h a, qsim_h b, double* out);
+
+/* ---- batches of independent circuits (one persistent launch) ---------------------------------------- */
+
+/*
+ * Simulate `count` independent circuits (widths may differ; each n in 1..26, complex64) from |0...0>
+ * and return, for circuit i, <Z_q> at zi[zi_off[i] + q] (q < n_i) and <Z_q Z_{q+1}> at
+ * zz[zz_off[i] + q] (q < n_i - 1), where zi_off / zz_off are the running sums of n_i and n_i - 1.
+ * Each circuit is fused with its own width k (0 in opts->max_fused = chosen per circuit by the
+ * built-in tuner). States live in `dev_ws` (device, at least qsim_batch_workspace_bytes bytes). All
+ * circuits run in one persistent kernel launch whose work queue is consumed with bounded waits.
+ */
+int qsim_batch_workspace_bytes(const qsim_circuit* cs, int count, size_t* out);
+int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws,
+                   size_t ws_bytes, void* stream, double* zi, double* zz, qsim_plan_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,44 @@
+// capi_state.h -- the handle behind qsim_h and helpers shared by capi.cu and plan.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace qsim {
+
+constexpr size_t kDevMatBytes = 1 << 20;  // per-handle device scratch for one gate / block operand
+
+}  // namespace qsim
+
+struct qsim_state {
+    int n = 0;
+    int dtype = QSIM_C64;
+    void* psi = nullptr;
+    size_t bytes = 0;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    qsim::DevInfo dev;
+    qsim::ReduceScratch red;
+    void* dmat = nullptr;       // kDevMatBytes: a gate matrix in state precision or a tensor-core operand
+    double* dmat64 = nullptr;   // 64 KiB FP64 staging for a block matrix
+    unsigned* derr = nullptr;   // device error word (DEVERR_* bits)
+    uint64_t* dsamples = nullptr;
+    double* du = nullptr;
+    size_t samples_cap = 0;
+};
+
+namespace qsim {
+
+bool is_diagonal(const double* m, int k);
+bool is_unitary(const double* m, int k, double tol);
+int validate_qubits(int n, const int* targets, int k, const int* controls, int nc, int kmax);
+std::vector<int> nonunit_patterns(const double* diag, int k);
+int check_device_error(qsim_state* h);
+int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* controls, int nc, const double* m);
+
+}  // namespace qsim
+
+extern "C" int qsim_synchronize(qsim_h h);

@@ -1,0 +1,99 @@
+// internal.h -- host-side declarations shared by the libqsim translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+constexpr int kMaxFixed = QSIM_MAX_TARGETS + QSIM_MAX_CONTROLS;
+
+struct DevInfo {
+    int device = 0;
+    int num_sms = 1;
+    size_t smem_optin = 0;
+};
+
+// Per-call error message (thread-local) used by qsim_last_error().
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// ---- gate kernels (k_gates.cu) ------------------------------------------------------------------------------
+// Dense U on k <= 4 targets with controls; `mat` is 2^k x 2^k interleaved complex128 (host), converted to
+// the state precision and passed by value.
+cudaError_t launch_dense_small(int dtype, void* psi, int n, int k, const int* targets, int nc,
+                               const int* controls, const double* mat, cudaStream_t s, const DevInfo& d);
+// Diagonal gate: diag (host, 2^k complex128) on targets; only patterns listed in `touch` are updated.
+cudaError_t launch_diag(int dtype, void* psi, int n, int k, const int* targets, int nc, const int* controls,
+                        const double* diag, const std::vector<int>& touch, cudaStream_t s, const DevInfo& d);
+// Dense U on k = 5, 6 targets with controls; `dmat` is a DEVICE buffer of 2^k x 2^k complex in the state
+// precision (interleaved, row-major).
+cudaError_t launch_dense_tile(int dtype, void* psi, int n, int k, const int* targets, int nc,
+                              const int* controls, const void* dmat, cudaStream_t s, const DevInfo& d);
+// Exchange qubits a[i] <-> b[i] (i < p) in place; splits into several passes when one tile cannot hold
+// all swapped bits. Returns the number of passes through *passes when non-NULL.
+cudaError_t launch_swap(int dtype, void* psi, int n, const int* a, const int* b, int p, cudaStream_t s,
+                        const DevInfo& d, int* passes);
+cudaError_t launch_set_basis(int dtype, void* psi, int n, uint64_t x, cudaStream_t s, const DevInfo& d);
+// Convert a device FP64 matrix (2^k x 2^k complex) into the state precision (device -> device).
+cudaError_t launch_convert_matrix(int dtype, const double* src, void* dst, int64_t count, cudaStream_t s);
+
+// ---- tensor-core fused block (k_tc.cu) ----------------------------------------------------------------------
+// Bytes of the prepared B operand for a k-qubit block at `precision`.
+size_t tc_operand_bytes(int k, int precision);
+// Build the B operand (tensor-core layout) from a device FP64 matrix U (2^k x 2^k complex).
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s);
+// Apply the prepared block to a complex64 state. dev_err receives DEVERR_* bits on a bounded-wait expiry.
+cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
+                            unsigned* dev_err, cudaStream_t s, const DevInfo& d);
+bool tc_supported(int k, int precision);
+
+// ---- fused-block composition (k_compose.cu) -------------------------------------------------------------------
+struct ComposeGate {
+    int k, nc;
+    int targets[QSIM_MAX_TARGETS];   // local indices within the block's qubit list
+    int controls[QSIM_MAX_CONTROLS]; // local indices
+    int64_t mat_off;                 // offset (in complex entries) into the gate-matrix pool
+};
+struct ComposeBlock {
+    int kb;         // block width (local qubits 0..kb-1)
+    int first_gate; // index into the ComposeGate array
+    int num_gates;
+    int64_t out_off; // offset (in complex entries) of the 2^kb x 2^kb output
+};
+// For every block: U_block = G_last ... G_first on kb local qubits, in FP64, on the device.
+cudaError_t launch_compose(const ComposeBlock* dblocks, int nblocks, const ComposeGate* dgates,
+                           const double* dpool, double* dout, int max_kb, cudaStream_t s);
+
+// ---- reductions and sampling (k_reduce.cu) ------------------------------------------------------------------------
+struct ReduceScratch {
+    double* partials = nullptr;  // kPartialDoubles doubles
+    double* seg = nullptr;       // 2 * max(1, 2^(n-12)) doubles: segment sums W and helper column
+    double* scan = nullptr;      // max(1, 2^(n-12)) + 4096 doubles
+    double* result = nullptr;    // 256 doubles (device)
+    double* hresult = nullptr;   // 256 doubles (pinned host)
+};
+constexpr int64_t kPartialDoubles = 1 << 18;
+constexpr int kSegBits = 12;
+
+cudaError_t run_norm(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
+                     double* out);
+cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
+                      cudaStream_t s, const DevInfo& d, double* out);
+cudaError_t run_pauli(int dtype, const void* psi, int n, const char* paulis, ReduceScratch& r, cudaStream_t s,
+                      const DevInfo& d, double* out);
+cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
+                       double* zi, double* zz);
+cudaError_t run_inner(int dtype, const void* a, const void* b, int n, ReduceScratch& r, cudaStream_t s,
+                      const DevInfo& d, double* out);
+// Samples: u_dev (device, shots doubles) -> out_dev (device, shots uint64).
+cudaError_t run_sample(int dtype, const void* psi, int n, const double* u_dev, int64_t shots, uint64_t* out_dev,
+                       ReduceScratch& r, cudaStream_t s, const DevInfo& d);
+cudaError_t launch_uniforms(uint64_t seed, int64_t count, double* out_dev, cudaStream_t s);
+
+}  // namespace qsim

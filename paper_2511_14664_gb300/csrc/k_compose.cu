@@ -1,0 +1,71 @@
+// k_compose.cu -- FP64 composition of fused gate blocks (paper Sec. 2.1: gate fusion groups several gate
+// applications into one larger matrix).
+//
+// For a block on kb local qubits with gates G_1..G_g (each on a subset of those qubits, with controls),
+// U = G_g ... G_1 is built column by column: start from the identity and apply every gate to all 2^kb
+// columns at once, exactly like applying it to 2^kb small state vectors. One CTA per block; the matrix
+// ping-pongs between two shared-memory buffers (2 x 64 KiB for kb = 6).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace qsim {
+
+__global__ void __launch_bounds__(256) k_compose(const ComposeBlock* __restrict__ blocks,
+                                                 const ComposeGate* __restrict__ gates,
+                                                 const double* __restrict__ pool, double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ComposeBlock b = blocks[blockIdx.x];
+    const int D = 1 << b.kb, E = D * D;
+    double2* A = reinterpret_cast<double2*>(smem_raw);
+    double2* B = A + E;
+    for (int i = threadIdx.x; i < E; i += blockDim.x) A[i] = make_double2((i / D) == (i % D) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    for (int gi = 0; gi < b.num_gates; ++gi) {
+        const ComposeGate g = gates[b.first_gate + gi];
+        const double* G = pool + 2 * g.mat_off;
+        const int dg = 1 << g.k;
+        int tmask = 0, cmask = 0;
+        for (int j = 0; j < g.k; ++j) tmask |= 1 << g.targets[j];
+        for (int j = 0; j < g.nc; ++j) cmask |= 1 << g.controls[j];
+        for (int i = threadIdx.x; i < E; i += blockDim.x) {
+            const int r = i / D, c = i % D;
+            if ((r & cmask) != cmask) {
+                B[i] = A[i];
+                continue;
+            }
+            int mr = 0;
+            for (int j = 0; j < g.k; ++j) mr |= ((r >> g.targets[j]) & 1) << j;
+            const int base = r & ~tmask;
+            double re = 0.0, im = 0.0;
+            for (int m = 0; m < dg; ++m) {
+                int src = base;
+                for (int j = 0; j < g.k; ++j) src |= ((m >> j) & 1) << g.targets[j];
+                const double gr = G[2 * (mr * dg + m)], gim = G[2 * (mr * dg + m) + 1];
+                const double2 a = A[src * D + c];
+                re = __fma_rn(gr, a.x, re);
+                re = __fma_rn(-gim, a.y, re);
+                im = __fma_rn(gr, a.y, im);
+                im = __fma_rn(gim, a.x, im);
+            }
+            B[i] = make_double2(re, im);
+        }
+        __syncthreads();
+        double2* t = A; A = B; B = t;
+    }
+    double2* o = reinterpret_cast<double2*>(out) + b.out_off;
+    for (int i = threadIdx.x; i < E; i += blockDim.x) o[i] = A[i];
+}
+
+cudaError_t launch_compose(const ComposeBlock* dblocks, int nblocks, const ComposeGate* dgates,
+                           const double* dpool, double* dout, int max_kb, cudaStream_t s) {
+    if (nblocks == 0) return cudaSuccess;
+    const size_t smem = 2 * sizeof(double2) * ((size_t)1 << (2 * max_kb));
+    cudaError_t e = cudaFuncSetAttribute(k_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_compose<<<nblocks, 256, smem, s>>>(dblocks, dgates, dpool, dout);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

@@ -1,0 +1,759 @@
+// k_reduce.cu -- readout of the state (paper Sec. 2.1 "Measurement and Sampling"; Sec. 2.5: sampling and
+// expectation values): norm, marginal probabilities, Pauli-string expectations, the Z / ZZ correlators of
+// a chain in one pass, overlaps, and inverse-CDF sampling without materialising the 2^n CDF.
+//
+// Precision: each thread accumulates exact |a|^2 (or exact products) in float-float (~48 bits, FP32 ops);
+// warps reduce in float-float; per-block partials are combined in double-double (FP64 TwoSum). GB300's FP64
+// rate is far below its FP32 rate, so FP64 is kept off the per-amplitude path. complex128 states use
+// double-double throughout.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace qsim {
+
+// ---- accumulator traits -----------------------------------------------------------------------------------
+template <typename R> struct Acc;
+template <> struct Acc<float> {
+    using A = ff;
+    __device__ static A zero() { return {0.f, 0.f}; }
+    __device__ static A abs2(float re, float im) { return ff_abs2(re, im); }
+    __device__ static A prod(float x, float y) { return two_prod(x, y); }
+    __device__ static A add(A a, A b) { return ff_add(a, b); }
+    __device__ static A neg(A a) { return ff_neg(a); }
+    __device__ static A warp_sum(A a) { return warp_sum_ff(a); }
+    __device__ static dd to_dd(A a) { return {(double)a.hi + (double)a.lo, 0.0}; }
+};
+__device__ __forceinline__ dd two_prod_d(double x, double y) {
+    double p = __dmul_rn(x, y);
+    return {p, __fma_rn(x, y, -p)};
+}
+template <> struct Acc<double> {
+    using A = dd;
+    __device__ static A zero() { return {0.0, 0.0}; }
+    __device__ static A abs2(double re, double im) { return dd_add(two_prod_d(re, re), two_prod_d(im, im)); }
+    __device__ static A prod(double x, double y) { return two_prod_d(x, y); }
+    __device__ static A add(A a, A b) { return dd_add(a, b); }
+    __device__ static A neg(A a) { return {-a.hi, -a.lo}; }
+    __device__ static A warp_sum(A a) { return warp_sum_dd(a); }
+    __device__ static dd to_dd(A a) { return a; }
+};
+
+// Sum of one dd value per thread over the block; result valid in thread 0. `sm` holds >= 32 dd.
+__device__ dd block_sum_dd(dd v, dd* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum_dd(v);
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    dd r = {0.0, 0.0};
+    if (warp == 0) {
+        r = lane < nw ? sm[lane] : dd{0.0, 0.0};
+        r = warp_sum_dd(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+template <typename R>
+__device__ dd block_sum_acc(typename Acc<R>::A v, dd* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = Acc<R>::warp_sum(v);
+    if (lane == 0) sm[warp] = Acc<R>::to_dd(v);
+    __syncthreads();
+    dd r = {0.0, 0.0};
+    if (warp == 0) {
+        r = lane < nw ? sm[lane] : dd{0.0, 0.0};
+        r = warp_sum_dd(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// partials layout: quantity q, block b -> partials[2 * (q * nblocks + b)] (hi, lo).
+__global__ void __launch_bounds__(256) k_final_dd(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    __shared__ dd sm[32];
+    const int q = blockIdx.x;
+    dd acc = {0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double* p = partials + 2 * ((int64_t)q * nblocks + b);
+        acc = dd_add(acc, dd{p[0], p[1]});
+    }
+    acc = block_sum_dd(acc, sm);
+    if (threadIdx.x == 0) {
+        out[2 * q] = acc.hi;
+        out[2 * q + 1] = acc.lo;
+    }
+}
+
+// ============================================================================================================
+// Norm and overlap
+// ============================================================================================================
+template <typename R>
+__global__ void __launch_bounds__(256) k_norm_partial(const typename Amp<R>::T* __restrict__ psi, uint64_t N, double* partials) {
+    __shared__ dd sm[32];
+    using A = typename Acc<R>::A;
+    A acc = Acc<R>::zero();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const auto a = psi[i];
+        acc = Acc<R>::add(acc, Acc<R>::abs2(a.x, a.y));
+    }
+    const dd r = block_sum_acc<R>(acc, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = r.hi;
+        partials[2 * blockIdx.x + 1] = r.lo;
+    }
+}
+
+// <a|b> = sum conj(a_x) b_x: quantity 0 = real part, 1 = imaginary part.
+template <typename R>
+__global__ void __launch_bounds__(256) k_inner_partial(const typename Amp<R>::T* __restrict__ a,
+                                                       const typename Amp<R>::T* __restrict__ b, uint64_t N,
+                                                       double* partials) {
+    __shared__ dd sm[32];
+    using A = typename Acc<R>::A;
+    A re = Acc<R>::zero(), im = Acc<R>::zero();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const auto x = a[i];
+        const auto y = b[i];
+        re = Acc<R>::add(re, Acc<R>::add(Acc<R>::prod(x.x, y.x), Acc<R>::prod(x.y, y.y)));
+        im = Acc<R>::add(im, Acc<R>::add(Acc<R>::prod(x.x, y.y), Acc<R>::neg(Acc<R>::prod(x.y, y.x))));
+    }
+    const dd r0 = block_sum_acc<R>(re, sm);
+    const dd r1 = block_sum_acc<R>(im, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = r0.hi;
+        partials[2 * blockIdx.x + 1] = r0.lo;
+        partials[2 * (gridDim.x + blockIdx.x)] = r1.hi;
+        partials[2 * (gridDim.x + blockIdx.x) + 1] = r1.lo;
+    }
+}
+
+// ============================================================================================================
+// Pauli strings: <P> = i^{nY} sum_x s(x) conj(psi_{x^f}) psi_x, s(x) = (-1)^{popcount(x & (Y|Z mask))}.
+// With f != 0, x and x^f are visited together (x has the top flip bit h clear), so every amplitude is read
+// once: their two terms are s(x) w + s(x^f) conj(w), w = conj(psi_{x^f}) psi_x.
+// ============================================================================================================
+template <typename R>
+__global__ void __launch_bounds__(256) k_pauli_partial(const typename Amp<R>::T* __restrict__ psi, int n, uint64_t fmask,
+                                                       uint64_t smask, int h, double* partials) {
+    __shared__ dd sm[32];
+    using A = typename Acc<R>::A;
+    A sre = Acc<R>::zero(), sim = Acc<R>::zero();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (fmask == 0) {
+        const uint64_t N = 1ull << n;
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += stride) {
+            const auto a = psi[x];
+            A p = Acc<R>::abs2(a.x, a.y);
+            if (__popcll(x & smask) & 1) p = Acc<R>::neg(p);
+            sre = Acc<R>::add(sre, p);
+        }
+    } else {
+        const uint64_t G = 1ull << (n - 1);
+        for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride) {
+            const uint64_t x = insert_zero(g, h), y = x ^ fmask;
+            const auto a = psi[x];
+            const auto b = psi[y];
+            // w = conj(b) a
+            A wr = Acc<R>::add(Acc<R>::prod(b.x, a.x), Acc<R>::prod(b.y, a.y));
+            A wi = Acc<R>::add(Acc<R>::prod(b.x, a.y), Acc<R>::neg(Acc<R>::prod(b.y, a.x)));
+            const bool sx = __popcll(x & smask) & 1, sy = __popcll(y & smask) & 1;
+            // s(x) w + s(y) conj(w): real = (s(x)+s(y)) wr, imag = (s(x)-s(y)) wi
+            if (sx == sy) {
+                A t = Acc<R>::add(wr, wr);
+                sre = Acc<R>::add(sre, sx ? Acc<R>::neg(t) : t);
+            } else {
+                A t = Acc<R>::add(wi, wi);
+                sim = Acc<R>::add(sim, sx ? Acc<R>::neg(t) : t);
+            }
+        }
+    }
+    const dd r0 = block_sum_acc<R>(sre, sm);
+    const dd r1 = block_sum_acc<R>(sim, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = r0.hi;
+        partials[2 * blockIdx.x + 1] = r0.lo;
+        partials[2 * (gridDim.x + blockIdx.x)] = r1.hi;
+        partials[2 * (gridDim.x + blockIdx.x) + 1] = r1.lo;
+    }
+}
+
+// ============================================================================================================
+// Marginal probabilities, n >= 12: segments of 4096 amplitudes. Inside a segment the non-marginal low bits
+// are folded out pairwise (bit 11 first, down to bit 0), leaving 2^|Qlow| sums that go to the bins selected
+// by the segment's high marginal bits. Bins live in shared memory per CTA (float-float) and are written as
+// per-CTA partials.
+// ============================================================================================================
+struct ProbsArgs {
+    int nq;
+    int nlow;             // marginal qubits below 12
+    int fold[12];         // non-marginal bits below 12, descending
+    int nfold;
+    int lowj[12];         // user index j of the r-th smallest low marginal qubit
+    int nhigh;
+    int highpos[12];      // marginal qubits >= 12 (index positions)
+    int highj[12];        // their user index j
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_probs_seg(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
+                                                   const __grid_constant__ ProbsArgs a, double* partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ff* buf0 = reinterpret_cast<ff*>(smem_raw);
+    ff* buf1 = buf0 + 4096;
+    ff* bins = buf1 + 4096;
+    const int NB = 1 << a.nq;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) bins[i] = {0.f, 0.f};
+    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const uint64_t base = s << 12;
+        for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+            const auto v = psi[base + i];
+            if constexpr (sizeof(R) == 4) {
+                buf0[i] = ff_abs2(v.x, v.y);
+            } else {
+                const dd p = Acc<double>::abs2(v.x, v.y);
+                const float hi = (float)p.hi;
+                buf0[i] = {hi, (float)(p.hi - (double)hi + p.lo)};
+            }
+        }
+        __syncthreads();
+        ff* src = buf0;
+        ff* dst = buf1;
+        int len = 4096;
+        for (int f = 0; f < a.nfold; ++f) {
+            const int c = a.fold[f];
+            len >>= 1;
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                const int j = (int)insert_zero((uint64_t)i, c);
+                dst[i] = ff_add(src[j], src[j | (1 << c)]);
+            }
+            __syncthreads();
+            ff* t = src; src = dst; dst = t;
+        }
+        int mhigh = 0;
+        for (int j = 0; j < a.nhigh; ++j) mhigh |= (int)((base >> a.highpos[j]) & 1) << a.highj[j];
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            int m = mhigh;
+            for (int r = 0; r < a.nlow; ++r) m |= ((i >> r) & 1) << a.lowj[r];
+            bins[m] = ff_add(bins[m], src[i]);
+        }
+        __syncthreads();
+    }
+    for (int m = threadIdx.x; m < NB; m += blockDim.x) {
+        double* p = partials + 2 * ((int64_t)m * gridDim.x + blockIdx.x);
+        p[0] = (double)bins[m].hi + (double)bins[m].lo;
+        p[1] = 0.0;
+    }
+}
+
+// Small states (n < 12): one CTA; out[m] directly (dd), each bin summing its 2^(n-nq) amplitudes.
+template <typename R>
+__global__ void __launch_bounds__(256) k_probs_small(const typename Amp<R>::T* __restrict__ psi, int n,
+                                                     const __grid_constant__ ProbsArgs a, const int* __restrict__ qpos,
+                                                     double* out) {
+    // qpos: the nq marginal positions (user order) followed by the n-nq other positions, ascending.
+    const int nq = a.nq;
+    const int NB = 1 << nq, nr = n - nq;
+    for (int m = threadIdx.x; m < NB; m += blockDim.x) {
+        uint64_t fixedbits = 0;
+        for (int j = 0; j < nq; ++j) fixedbits |= (uint64_t)((m >> j) & 1) << qpos[j];
+        dd acc = {0.0, 0.0};
+        for (uint64_t r = 0; r < (1ull << nr); ++r) {
+            const uint64_t x = fixedbits | deposit(r, qpos + nq, nr);
+            const auto v = psi[x];
+            acc = dd_add(acc, Acc<double>::abs2((double)v.x, (double)v.y));
+        }
+        out[2 * m] = acc.hi;
+        out[2 * m + 1] = acc.lo;
+    }
+}
+
+// ============================================================================================================
+// <Z_i> and <Z_i Z_{i+1}> in one pass. With p_x = |a_x|^2, T = sum p, S_i = sum p x_i and
+// X_i = sum p (x_i xor x_{i+1}): <Z_i> = T - 2 S_i, <Z_i Z_{i+1}> = T - 2 X_i.
+// Segment s (4096 amplitudes) is processed by one CTA; thread t reads amplitudes 2t + e + 512 j (e < 2,
+// j < 8), so index bits 1..8 come from t, bit 0 from e and bits 9..11 from j. Per segment the 24
+// quantities of bits 0..11 are block-reduced and accumulated per CTA; the segment total W[s] and its
+// S_11 part go to global memory, from which k_zstats_high forms the quantities of bits >= 12.
+// ============================================================================================================
+constexpr int kZQ = 24;
+
+template <typename R>
+__device__ __forceinline__ ff load_p(const typename Amp<R>::T* psi, uint64_t i) {
+    const auto v = psi[i];
+    if constexpr (sizeof(R) == 4) {
+        return ff_abs2(v.x, v.y);
+    } else {
+        const dd p = Acc<double>::abs2(v.x, v.y);
+        const float hi = (float)p.hi;
+        return {hi, (float)(p.hi - (double)hi + p.lo)};
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_zstats_seg(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
+                                                    double* __restrict__ W, double* __restrict__ W11,
+                                                    double* __restrict__ partials) {
+    __shared__ ff sm[8][kZQ];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    dd cta = {0.0, 0.0};  // thread q < kZQ accumulates quantity q over this CTA's segments
+    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const uint64_t base = (s << 12) + 2 * t;
+        ff P[8], Q[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const ff p0 = load_p<R>(psi, base + 512 * j);
+            const ff p1 = load_p<R>(psi, base + 512 * j + 1);
+            Q[j] = p1;
+            P[j] = ff_add(p0, p1);
+        }
+        ff T = P[0], S0 = Q[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) { T = ff_add(T, P[j]); S0 = ff_add(S0, Q[j]); }
+        const ff S9 = ff_add(ff_add(P[1], P[3]), ff_add(P[5], P[7]));
+        const ff S10 = ff_add(ff_add(P[2], P[3]), ff_add(P[6], P[7]));
+        const ff S11 = ff_add(ff_add(P[4], P[5]), ff_add(P[6], P[7]));
+        const ff X9 = ff_add(ff_add(P[1], P[2]), ff_add(P[5], P[6]));
+        const ff X10 = ff_add(ff_add(P[2], P[3]), ff_add(P[4], P[5]));
+        const ff Z = {0.f, 0.f};
+        ff c[kZQ];
+        c[0] = T;
+        c[1] = S0;
+#pragma unroll
+        for (int i = 1; i <= 8; ++i) c[1 + i] = ((t >> (i - 1)) & 1) ? T : Z;
+        c[10] = S9; c[11] = S10; c[12] = S11;
+        c[13] = (t & 1) ? ff_add(T, ff_neg(S0)) : S0;
+#pragma unroll
+        for (int i = 1; i <= 7; ++i) c[13 + i] = (((t >> (i - 1)) ^ (t >> i)) & 1) ? T : Z;
+        c[21] = ((t >> 7) & 1) ? ff_add(T, ff_neg(S9)) : S9;
+        c[22] = X9;
+        c[23] = X10;
+#pragma unroll
+        for (int q = 0; q < kZQ; ++q) {
+            const ff v = warp_sum_ff(c[q]);
+            if (lane == 0) sm[warp][q] = v;
+        }
+        __syncthreads();
+        if (t < kZQ) {
+            ff v = sm[0][t];
+#pragma unroll
+            for (int w = 1; w < 8; ++w) v = ff_add(v, sm[w][t]);
+            const double vd = (double)v.hi + (double)v.lo;
+            cta = dd_add(cta, dd{vd, 0.0});
+            if (t == 0) W[s] = vd;
+            if (t == 12) W11[s] = vd;
+        }
+        __syncthreads();
+    }
+    if (t < kZQ) {
+        double* p = partials + 2 * ((int64_t)t * gridDim.x + blockIdx.x);
+        p[0] = cta.hi;
+        p[1] = cta.lo;
+    }
+}
+
+__device__ __forceinline__ ff d2ff(double w) {
+    const float hi = (float)w;
+    return {hi, (float)(w - (double)hi)};
+}
+
+// Quantities of bits >= 12 from the segment totals W (one CTA per quantity; nh = n - 12):
+//   q < nh:            S_{12+q}      = sum_s W[s] bit_q(s)
+//   q == nh:           X_11          = sum_s (bit_0(s) ? W[s] - W11[s] : W11[s])
+//   nh < q < 2 nh:     X_{12+r}, r = q - nh - 1: sum_s W[s] (bit_r(s) xor bit_{r+1}(s))
+__global__ void __launch_bounds__(256) k_zstats_high(const double* __restrict__ W, const double* __restrict__ W11,
+                                                     uint64_t nseg, int nh, double* __restrict__ out) {
+    __shared__ dd sm[32];
+    const int q = blockIdx.x;
+    ff acc = {0.f, 0.f};
+    for (uint64_t s = threadIdx.x; s < nseg; s += blockDim.x) {
+        if (q < nh) {
+            if ((s >> q) & 1) acc = ff_add(acc, d2ff(W[s]));
+        } else if (q == nh) {
+            acc = ff_add(acc, (s & 1) ? ff_add(d2ff(W[s]), ff_neg(d2ff(W11[s]))) : d2ff(W11[s]));
+        } else {
+            const int r = q - nh - 1;
+            if (((s >> r) ^ (s >> (r + 1))) & 1) acc = ff_add(acc, d2ff(W[s]));
+        }
+    }
+    const dd v = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
+    if (threadIdx.x == 0) {
+        out[2 * q] = v.hi;
+        out[2 * q + 1] = v.lo;
+    }
+}
+
+// n < 12: one CTA; quantity q: 0 -> T, 1..n -> S_{q-1}, n+1..2n-1 -> X_{q-n-1}.
+template <typename R>
+__global__ void __launch_bounds__(256) k_zstats_small(const typename Amp<R>::T* __restrict__ psi, int n, double* out) {
+    __shared__ double p[4096];
+    const int N = 1 << n;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        const ff v = load_p<R>(psi, x);
+        p[x] = (double)v.hi + (double)v.lo;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * n; q += blockDim.x) {
+        dd acc = {0.0, 0.0};
+        for (int x = 0; x < N; ++x) {
+            bool use;
+            if (q == 0) use = true;
+            else if (q <= n) use = (x >> (q - 1)) & 1;
+            else { const int i = q - n - 1; use = ((x >> i) ^ (x >> (i + 1))) & 1; }
+            if (use) acc = dd_add(acc, dd{p[x], 0.0});
+        }
+        out[2 * q] = acc.hi;
+        out[2 * q + 1] = acc.lo;
+    }
+}
+
+// ============================================================================================================
+// Sampling: W[s] segment sums (2^SB amplitudes each), chunk sums of 1024 segments, inclusive scan of the
+// chunk sums; then one warp per uniform walks chunk -> segment -> amplitude.
+// ============================================================================================================
+template <typename R>
+__global__ void __launch_bounds__(256) k_segsum(const typename Amp<R>::T* __restrict__ psi, int SB, uint64_t nseg,
+                                                double* __restrict__ W) {
+    __shared__ dd sm[32];
+    const int S = 1 << SB;
+    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        ff acc = {0.f, 0.f};
+        for (int i = threadIdx.x; i < S; i += blockDim.x) acc = ff_add(acc, load_p<R>(psi, (s << SB) + i));
+        const dd r = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
+        if (threadIdx.x == 0) W[s] = r.hi + r.lo;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_chunksum(const double* __restrict__ W, uint64_t nseg, double* __restrict__ C) {
+    __shared__ dd sm[32];
+    const uint64_t c = blockIdx.x;
+    dd acc = {0.0, 0.0};
+    for (uint64_t i = c * 1024 + threadIdx.x; i < min(nseg, (c + 1) * 1024); i += blockDim.x)
+        acc = dd_add(acc, dd{W[i], 0.0});
+    acc = block_sum_dd(acc, sm);
+    if (threadIdx.x == 0) C[c] = acc.hi + acc.lo;
+}
+
+// Inclusive scan of C[0..m) in place, m <= 4096, one CTA of 1024 threads (double-double).
+__global__ void __launch_bounds__(1024) k_scan_small(double* __restrict__ C, int m) {
+    __shared__ dd sh[1024];
+    const int t = threadIdx.x;
+    dd loc[4];
+    dd run = {0.0, 0.0};
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * t + j;
+        run = dd_add(run, dd{i < m ? C[i] : 0.0, 0.0});
+        loc[j] = run;
+    }
+    sh[t] = run;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const dd v = t >= off ? sh[t - off] : dd{0.0, 0.0};
+        __syncthreads();
+        sh[t] = dd_add(sh[t], v);
+        __syncthreads();
+    }
+    const dd before = t > 0 ? sh[t - 1] : dd{0.0, 0.0};
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * t + j;
+        if (i < m) {
+            const dd v = dd_add(before, loc[j]);
+            C[i] = v.hi + v.lo;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_incl_scan_d(double v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+__device__ __forceinline__ ff warp_incl_scan_ff(ff v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const ff u = {__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+        if (lane >= o) v = ff_add(v, u);
+    }
+    return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sample(const typename Amp<R>::T* __restrict__ psi, int SB, uint64_t nseg,
+                                                const double* __restrict__ W, const double* __restrict__ C,
+                                                int nchunk, const double* __restrict__ u, int64_t shots,
+                                                uint64_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double total = C[nchunk - 1];
+    for (int64_t i = warp0; i < shots; i += nwarps) {
+        const double target = u[i] * total;
+        // chunk: first c with C[c] > target
+        int lo = 0, hi = nchunk;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (C[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        int c = lo < nchunk ? lo : nchunk - 1;
+        double r = target - (c > 0 ? C[c - 1] : 0.0);
+        // segment inside the chunk
+        const uint64_t s0 = (uint64_t)c * 1024, s1 = min(nseg, s0 + 1024);
+        double run = 0.0;
+        uint64_t seg = ~0ull, last_nz = s0;
+        for (uint64_t sb = s0; sb < s1 && seg == ~0ull; sb += 32) {
+            const uint64_t s = sb + lane;
+            const double w = s < s1 ? W[s] : 0.0;
+            const double pre = warp_incl_scan_d(w);
+            const unsigned hit = __ballot_sync(0xffffffffu, s < s1 && run + pre > r);
+            const unsigned nz = __ballot_sync(0xffffffffu, w > 0.0);
+            if (nz) last_nz = sb + 31 - __clz(nz);
+            if (hit) {
+                const int l = __ffs(hit) - 1;
+                seg = sb + l;
+                const double before = __shfl_sync(0xffffffffu, pre - w, l);
+                r -= run + before;
+            } else {
+                run += __shfl_sync(0xffffffffu, pre, 31);
+            }
+        }
+        if (seg == ~0ull) { seg = last_nz; r = W[seg]; }
+        // amplitude inside the segment
+        const uint64_t a0 = seg << SB, a1 = a0 + (1ull << SB);
+        ff frun = {0.f, 0.f};
+        uint64_t x = ~0ull, lastx = a0;
+        for (uint64_t xb = a0; xb < a1 && x == ~0ull; xb += 32) {
+            const uint64_t xi = xb + lane;
+            const ff p = xi < a1 ? load_p<R>(psi, xi) : ff{0.f, 0.f};
+            const ff pre = warp_incl_scan_ff(p);
+            const ff tot = ff_add(frun, pre);
+            const unsigned hit = __ballot_sync(0xffffffffu, xi < a1 && ((double)tot.hi + (double)tot.lo) > r);
+            const unsigned nz = __ballot_sync(0xffffffffu, p.hi > 0.f);
+            if (nz) lastx = xb + 31 - __clz(nz);
+            if (hit) x = xb + (__ffs(hit) - 1);
+            else frun = ff_add(frun, ff{__shfl_sync(0xffffffffu, pre.hi, 31), __shfl_sync(0xffffffffu, pre.lo, 31)});
+        }
+        if (x == ~0ull) x = lastx;
+        if (lane == 0) out[i] = x;
+    }
+}
+
+__global__ void k_uniforms(uint64_t seed, int64_t count, double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        // SplitMix64 (Steele, Lea, Flood 2014): the (i+1)-th state of the golden-ratio Weyl sequence, finalised.
+        uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[i] = (double)(z >> 11) * 0x1.0p-53;
+    }
+}
+
+// ============================================================================================================
+// Host drivers
+// ============================================================================================================
+static cudaError_t fetch(ReduceScratch& r, int nvals, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(r.hresult, r.result, sizeof(double) * nvals, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+static int reduce_blocks(const DevInfo& d, uint64_t N, int nq) {
+    int64_t b = std::min<int64_t>((int64_t)d.num_sms * 4, (int64_t)((N + 255) / 256));
+    b = std::min<int64_t>(b, kPartialDoubles / (2 * std::max(1, nq)));
+    return (int)std::max<int64_t>(1, b);
+}
+
+cudaError_t run_norm(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d, double* out) {
+    const uint64_t N = 1ull << n;
+    const int nb = reduce_blocks(d, N, 1);
+    if (dtype == QSIM_C64) k_norm_partial<float><<<nb, 256, 0, s>>>((const float2*)psi, N, r.partials);
+    else k_norm_partial<double><<<nb, 256, 0, s>>>((const double2*)psi, N, r.partials);
+    k_final_dd<<<1, 256, 0, s>>>(r.partials, nb, r.result);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = fetch(r, 2, s)) != cudaSuccess) return e;
+    *out = r.hresult[0] + r.hresult[1];
+    return cudaSuccess;
+}
+
+cudaError_t run_inner(int dtype, const void* a, const void* b, int n, ReduceScratch& r, cudaStream_t s,
+                      const DevInfo& d, double* out) {
+    const uint64_t N = 1ull << n;
+    const int nb = reduce_blocks(d, N, 2);
+    if (dtype == QSIM_C64) k_inner_partial<float><<<nb, 256, 0, s>>>((const float2*)a, (const float2*)b, N, r.partials);
+    else k_inner_partial<double><<<nb, 256, 0, s>>>((const double2*)a, (const double2*)b, N, r.partials);
+    k_final_dd<<<2, 256, 0, s>>>(r.partials, nb, r.result);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = fetch(r, 4, s)) != cudaSuccess) return e;
+    out[0] = r.hresult[0] + r.hresult[1];
+    out[1] = r.hresult[2] + r.hresult[3];
+    return cudaSuccess;
+}
+
+cudaError_t run_pauli(int dtype, const void* psi, int n, const char* paulis, ReduceScratch& r, cudaStream_t s,
+                      const DevInfo& d, double* out) {
+    uint64_t f = 0, sm = 0;
+    int ny = 0;
+    for (int q = 0; q < n; ++q) {
+        const char c = paulis[q];
+        if (c == 'X' || c == 'Y') f |= 1ull << q;
+        if (c == 'Y' || c == 'Z') sm |= 1ull << q;
+        if (c == 'Y') ++ny;
+    }
+    const int h = f ? 63 - __builtin_clzll(f) : 0;
+    const uint64_t work = f ? (1ull << (n - 1)) : (1ull << n);
+    const int nb = reduce_blocks(d, work, 2);
+    if (dtype == QSIM_C64) k_pauli_partial<float><<<nb, 256, 0, s>>>((const float2*)psi, n, f, sm, h, r.partials);
+    else k_pauli_partial<double><<<nb, 256, 0, s>>>((const double2*)psi, n, f, sm, h, r.partials);
+    k_final_dd<<<2, 256, 0, s>>>(r.partials, nb, r.result);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = fetch(r, 4, s)) != cudaSuccess) return e;
+    const double sr = r.hresult[0] + r.hresult[1], si = r.hresult[2] + r.hresult[3];
+    // multiply by i^{ny}
+    switch (ny & 3) {
+        case 0: out[0] = sr; out[1] = si; break;
+        case 1: out[0] = -si; out[1] = sr; break;
+        case 2: out[0] = -sr; out[1] = -si; break;
+        default: out[0] = si; out[1] = -sr; break;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
+                      cudaStream_t s, const DevInfo& d, double* out) {
+    ProbsArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nq = nq;
+    const int NB = 1 << nq;
+    cudaError_t e;
+    if (n < kSegBits) {
+        // positions: marginal qubits in user order, then the others ascending
+        std::vector<int> qpos(qubits, qubits + nq);
+        for (int q = 0; q < n; ++q)
+            if (std::find(qubits, qubits + nq, q) == qubits + nq) qpos.push_back(q);
+        int* dq = reinterpret_cast<int*>(r.partials + kPartialDoubles - 64);
+        if ((e = cudaMemcpyAsync(dq, qpos.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+        if (dtype == QSIM_C64) k_probs_small<float><<<1, 256, 0, s>>>((const float2*)psi, n, a, dq, r.partials);
+        else k_probs_small<double><<<1, 256, 0, s>>>((const double2*)psi, n, a, dq, r.partials);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(r.hresult, r.partials, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        for (int m = 0; m < NB; ++m) out[m] = r.hresult[2 * m] + r.hresult[2 * m + 1];
+        return cudaSuccess;
+    }
+    std::vector<std::pair<int, int>> low;  // (position, user index)
+    for (int j = 0; j < nq; ++j) {
+        if (qubits[j] < kSegBits) low.push_back({qubits[j], j});
+        else { a.highpos[a.nhigh] = qubits[j]; a.highj[a.nhigh] = j; ++a.nhigh; }
+    }
+    std::sort(low.begin(), low.end());
+    a.nlow = (int)low.size();
+    for (int r2 = 0; r2 < a.nlow; ++r2) a.lowj[r2] = low[r2].second;
+    for (int b = kSegBits - 1; b >= 0; --b) {
+        bool marg = false;
+        for (auto& pr : low) marg |= pr.first == b;
+        if (!marg) a.fold[a.nfold++] = b;
+    }
+    const uint64_t nseg = 1ull << (n - kSegBits);
+    int nb = (int)std::min<int64_t>((int64_t)d.num_sms * 2, (int64_t)nseg);
+    nb = (int)std::min<int64_t>(nb, kPartialDoubles / (2 * NB));
+    nb = std::max(1, nb);
+    const size_t smem = 2 * 4096 * sizeof(ff) + (size_t)NB * sizeof(ff);
+    if (dtype == QSIM_C64) {
+        if ((e = cudaFuncSetAttribute(k_probs_seg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k_probs_seg<float><<<nb, 256, smem, s>>>((const float2*)psi, nseg, a, r.partials);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_probs_seg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k_probs_seg<double><<<nb, 256, smem, s>>>((const double2*)psi, nseg, a, r.partials);
+    }
+    // result buffer holds 256 doubles; bins beyond that reduce into the tail of the segment buffer
+    double* dres = NB <= 128 ? r.result : r.scan;
+    k_final_dd<<<NB, 256, 0, s>>>(r.partials, nb, dres);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::vector<double> h(2 * NB);
+    if ((e = cudaMemcpyAsync(h.data(), dres, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    for (int m = 0; m < NB; ++m) out[m] = h[2 * m] + h[2 * m + 1];
+    return cudaSuccess;
+}
+
+cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
+                       double* zi, double* zz) {
+    cudaError_t e;
+    std::vector<double> T_S_X;  // T, S_0..S_{n-1}, X_0..X_{n-2} (each hi+lo)
+    if (n < kSegBits) {
+        if (dtype == QSIM_C64) k_zstats_small<float><<<1, 256, 0, s>>>((const float2*)psi, n, r.result);
+        else k_zstats_small<double><<<1, 256, 0, s>>>((const double2*)psi, n, r.result);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = fetch(r, 4 * n, s)) != cudaSuccess) return e;
+        const double T = r.hresult[0] + r.hresult[1];
+        for (int i = 0; i < n; ++i) zi[i] = T - 2.0 * (r.hresult[2 * (1 + i)] + r.hresult[2 * (1 + i) + 1]);
+        for (int i = 0; i + 1 < n; ++i) zz[i] = T - 2.0 * (r.hresult[2 * (n + 1 + i)] + r.hresult[2 * (n + 1 + i) + 1]);
+        return cudaSuccess;
+    }
+    const uint64_t nseg = 1ull << (n - kSegBits);
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 6, (int64_t)nseg));
+    double* W = r.seg;
+    double* W11 = r.seg + nseg;
+    if (dtype == QSIM_C64) k_zstats_seg<float><<<nb, 256, 0, s>>>((const float2*)psi, nseg, W, W11, r.partials);
+    else k_zstats_seg<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, W11, r.partials);
+    k_final_dd<<<kZQ, 256, 0, s>>>(r.partials, nb, r.result);
+    const int nh = n - kSegBits;
+    if (nh > 0) k_zstats_high<<<2 * nh, 256, 0, s>>>(W, W11, nseg, nh, r.result + 2 * kZQ);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = fetch(r, 2 * kZQ + 4 * nh, s)) != cudaSuccess) return e;
+    const double* h = r.hresult;
+    auto val = [&](int q) { return h[2 * q] + h[2 * q + 1]; };
+    const double T = val(0);
+    for (int i = 0; i < n; ++i) {
+        const double Si = i < kSegBits ? val(1 + i) : val(kZQ + (i - kSegBits));
+        zi[i] = T - 2.0 * Si;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+        double Xi;
+        if (i <= 10) Xi = val(13 + i);
+        else if (i == 11) Xi = val(kZQ + nh);
+        else Xi = val(kZQ + nh + 1 + (i - 12));
+        zz[i] = T - 2.0 * Xi;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_uniforms(uint64_t seed, int64_t count, double* out_dev, cudaStream_t s) {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 4096));
+    k_uniforms<<<blocks, 256, 0, s>>>(seed, count, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t run_sample(int dtype, const void* psi, int n, const double* u_dev, int64_t shots, uint64_t* out_dev,
+                       ReduceScratch& r, cudaStream_t s, const DevInfo& d) {
+    const int SB = std::min(n, kSegBits);
+    const uint64_t nseg = 1ull << (n - SB);
+    const int nchunk = (int)((nseg + 1023) / 1024);
+    double* W = r.seg;
+    double* C = r.scan;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)nseg));
+    if (dtype == QSIM_C64) k_segsum<float><<<nb, 256, 0, s>>>((const float2*)psi, SB, nseg, W);
+    else k_segsum<double><<<nb, 256, 0, s>>>((const double2*)psi, SB, nseg, W);
+    k_chunksum<<<nchunk, 256, 0, s>>>(W, nseg, C);
+    k_scan_small<<<1, 1024, 0, s>>>(C, nchunk);
+    const int sb = (int)std::max<int64_t>(1, std::min<int64_t>((shots * 32 + 255) / 256, (int64_t)d.num_sms * 8));
+    if (dtype == QSIM_C64) k_sample<float><<<sb, 256, 0, s>>>((const float2*)psi, SB, nseg, W, C, nchunk, u_dev, shots, out_dev);
+    else k_sample<double><<<sb, 256, 0, s>>>((const double2*)psi, SB, nseg, W, C, nchunk, u_dev, shots, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace qsim

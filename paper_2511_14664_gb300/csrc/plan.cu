@@ -1,0 +1,442 @@
+// plan.cu -- circuit planning and execution.
+//
+// Fusion (paper Sec. 2.1: gate fusion groups gate applications into one larger matrix, raising arithmetic
+// intensity; the best width depends on architecture and precision, Sec. 2.2 lists defaults 4/5/5): a greedy
+// pass collects, starting from the earliest unplaced gate, every later gate that (a) is not blocked by an
+// earlier unplaced gate sharing a qubit and (b) keeps the block within `max_fused` qubits. Diagonal gates
+// commute with each other, so a diagonal gate is blocked only by earlier unplaced NON-diagonal gates.
+// Each block becomes one device pass: a diagonal pass (only non-unit factors touched), a dense pass on CUDA
+// cores (k <= 4 register gather, k = 5, 6 shared-memory tile) or a tensor-core pass (complex64, k >= tc_min_k).
+// Block matrices are composed in FP64 on the device (k_compose.cu).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "capi_state.h"
+#include "internal.h"
+
+namespace qsim {
+
+enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3 };
+
+struct PlanOp {
+    int kind = OP_DENSE_SMALL;
+    int k = 0, nc = 0;
+    int targets[QSIM_MAX_TARGETS] = {0};
+    int controls[QSIM_MAX_CONTROLS] = {0};
+    std::vector<double> mat;   // OP_DENSE_SMALL: 2^k x 2^k; OP_DIAG: 2^k diagonal entries (FP64, interleaved)
+    std::vector<int> touch;    // OP_DIAG: patterns with a non-unit factor
+    size_t dev_off = 0;        // OP_DENSE_TILE, OP_TC: byte offset of the operand in the plan buffer
+    int precision = QSIM_PREC_SIMT;
+    int compose_idx = -1;      // block index in the composition (-1: a single input gate)
+    int64_t gates = 1;
+};
+
+}  // namespace qsim
+
+struct qsim_plan {
+    int n = 0;
+    int dtype = QSIM_C64;
+    std::vector<qsim::PlanOp> ops;
+    void* dbuf = nullptr;
+    size_t dbuf_bytes = 0;
+    qsim_plan_info info{};
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    const qsim_state* ghandle = nullptr;
+    void* gpsi = nullptr;
+    cudaStream_t gstream = nullptr;
+};
+
+namespace qsim {
+
+static inline int popcnt(uint64_t v) { return __builtin_popcountll(v); }
+
+static double op_bytes(const PlanOp& op, int n, size_t amp) {
+    const double groups = std::ldexp(1.0, n - op.k - op.nc);
+    if (op.kind == OP_DIAG) return 2.0 * amp * groups * (double)op.touch.size();
+    return 2.0 * amp * groups * (double)(1 << op.k);
+}
+
+static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size_t count = (size_t)-1) {
+    cudaError_t e = cudaSuccess;
+    const size_t last = std::min(p->ops.size(), count == (size_t)-1 ? p->ops.size() : first + count);
+    for (size_t oi = first; oi < last; ++oi) {
+        const PlanOp& op = p->ops[oi];
+        switch (op.kind) {
+            case OP_DENSE_SMALL:
+                e = launch_dense_small(h->dtype, h->psi, h->n, op.k, op.targets, op.nc, op.controls, op.mat.data(),
+                                       h->stream, h->dev);
+                break;
+            case OP_DIAG:
+                e = launch_diag(h->dtype, h->psi, h->n, op.k, op.targets, op.nc, op.controls, op.mat.data(), op.touch,
+                                h->stream, h->dev);
+                break;
+            case OP_DENSE_TILE:
+                e = launch_dense_tile(h->dtype, h->psi, h->n, op.k, op.targets, op.nc, op.controls,
+                                      static_cast<char*>(p->dbuf) + op.dev_off, h->stream, h->dev);
+                break;
+            case OP_TC:
+                e = launch_tc_apply(h->psi, h->n, op.k, op.targets, static_cast<char*>(p->dbuf) + op.dev_off,
+                                    op.precision, h->derr, h->stream, h->dev);
+                break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "plan pass launch");
+    }
+    return QSIM_OK;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts_in, void* stream_v,
+                     qsim_plan_h* out, qsim_plan_info* info) {
+    set_error("%s", "");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !out) { set_error("NULL argument"); return QSIM_EINVAL; }
+    *out = nullptr;
+    if (c->n < 1 || c->n > QSIM_MAX_QUBITS) { set_error("n = %d outside 1..%d", c->n, QSIM_MAX_QUBITS); return QSIM_EINVAL; }
+    if (dtype != QSIM_C64 && dtype != QSIM_C128) { set_error("unknown dtype"); return QSIM_EINVAL; }
+    if (c->num_gates < 0 || (c->num_gates > 0 && !c->gates)) { set_error("bad gate list"); return QSIM_EINVAL; }
+    qsim_run_opts opts{};
+    if (opts_in) opts = *opts_in;
+    if (opts.mode != QSIM_RUN_PLAIN && opts.mode != QSIM_RUN_FUSED) { set_error("unknown mode"); return QSIM_EINVAL; }
+    int kmax = opts.max_fused == 0 ? 5 : opts.max_fused;
+    if (kmax < 1 || kmax > 6) { set_error("max_fused must be 1..6"); return QSIM_EINVAL; }
+    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
+    const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
+    const int n = c->n;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    DevInfo dev;
+    cudaError_t e = cudaGetDevice(&dev.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&dev.num_sms, cudaDevAttrMultiProcessorCount, dev.device);
+    if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+
+    const int G = c->num_gates;
+    std::vector<uint64_t> gmask(G);
+    std::vector<char> gdiag(G);
+    for (int i = 0; i < G; ++i) {
+        const qsim_gate& g = c->gates[i];
+        if (g.k > 6 && g.k <= QSIM_MAX_TARGETS) { set_error("gate %d: more than 6 targets is not supported", i); return QSIM_EUNSUPPORTED; }
+        int rc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, 6);
+        if (rc) { set_error("gate %d: invalid qubits", i); return rc; }
+        if (!g.matrix) { set_error("gate %d: NULL matrix", i); return QSIM_EINVAL; }
+        if (!is_unitary(g.matrix, g.k, 1e-8 * (1 << g.k))) { set_error("gate %d: matrix is not unitary", i); return QSIM_EINVAL; }
+        uint64_t m = 0;
+        for (int j = 0; j < g.k; ++j) m |= 1ull << g.targets[j];
+        for (int j = 0; j < g.nc; ++j) m |= 1ull << g.controls[j];
+        gmask[i] = m;
+        gdiag[i] = is_diagonal(g.matrix, g.k);
+    }
+
+    qsim_plan* p = new (std::nothrow) qsim_plan();
+    if (!p) { set_error("out of host memory"); return QSIM_ENOMEM; }
+    p->n = n;
+    p->dtype = dtype;
+    p->use_graph = opts.use_graph != 0;
+
+    // ---- group gates into blocks -------------------------------------------------------------------------
+    std::vector<std::vector<int>> blocks;
+    if (opts.mode == QSIM_RUN_PLAIN) {
+        for (int i = 0; i < G; ++i) blocks.push_back({i});
+    } else {
+        std::vector<char> done(G, 0);
+        int first = 0;
+        while (true) {
+            while (first < G && done[first]) ++first;
+            if (first >= G) break;
+            uint64_t Q = 0, bany = 0, bdiag = 0;
+            std::vector<int> blk;
+            for (int i = first; i < G; ++i) {
+                if (done[i]) continue;
+                const uint64_t qs = gmask[i];
+                const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
+                if (!blocked && popcnt(Q | qs) <= kmax) {
+                    blk.push_back(i);
+                    done[i] = 1;
+                    Q |= qs;
+                } else if (blk.empty()) {  // wider than the fusion width: a block of its own
+                    blk.push_back(i);
+                    done[i] = 1;
+                    break;
+                } else if (gdiag[i]) {
+                    bdiag |= qs;
+                } else {
+                    bany |= qs;
+                }
+                if (popcnt(bany) == n) break;
+            }
+            blocks.push_back(std::move(blk));
+        }
+    }
+
+    // ---- decide each block's pass and lay out the device buffer --------------------------------------------
+    const size_t amp = dtype == QSIM_C64 ? 8 : 16;
+    std::vector<ComposeBlock> cblocks;
+    std::vector<ComposeGate> cgates;
+    std::vector<double> pool;  // gate matrices for composition (FP64 complex)
+    int64_t compose_out = 0;   // complex entries
+    int max_kb = 1;
+    size_t dev_bytes = 0;
+    auto align = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
+    struct Pending { int op; int kind; int kb; };  // device operand still to produce from a composed matrix
+    std::vector<Pending> pending;
+
+    for (const auto& blk : blocks) {
+        PlanOp op;
+        op.gates = (int64_t)blk.size();
+        if (blk.size() == 1) {
+            const qsim_gate& g = c->gates[blk[0]];
+            op.k = g.k;
+            op.nc = g.nc;
+            std::memcpy(op.targets, g.targets, sizeof(int) * g.k);
+            std::memcpy(op.controls, g.controls, sizeof(int) * g.nc);
+            const int D = 1 << g.k;
+            if (gdiag[blk[0]]) {
+                op.kind = OP_DIAG;
+                op.mat.resize(2 * D);
+                for (int i = 0; i < D; ++i) {
+                    op.mat[2 * i] = g.matrix[2 * (i * D + i)];
+                    op.mat[2 * i + 1] = g.matrix[2 * (i * D + i) + 1];
+                }
+                op.touch = nonunit_patterns(op.mat.data(), g.k);
+            } else if (g.k <= 4) {
+                op.kind = OP_DENSE_SMALL;
+                op.mat.assign(g.matrix, g.matrix + 2 * D * D);
+            } else {
+                // k = 5, 6 single gate: compose trivially (one gate) to reuse the device conversion path
+                op.kind = OP_DENSE_TILE;
+            }
+            if (op.kind == OP_DIAG || op.kind == OP_DENSE_SMALL) {
+                p->ops.push_back(std::move(op));
+                continue;
+            }
+        }
+        // multi-gate block (or a single wide gate): local qubit list Q ascending
+        uint64_t Q = 0;
+        bool all_diag = true;
+        for (int gi : blk) { Q |= gmask[gi]; all_diag = all_diag && gdiag[gi]; }
+        int qs[64], kb = 0, local[64];
+        for (int q = 0; q < n; ++q) if ((Q >> q) & 1) { local[q] = kb; qs[kb++] = q; }
+        if (blk.size() == 1 && !all_diag) {
+            // single k = 5/6 gate keeps its controls and target order
+            const qsim_gate& g = c->gates[blk[0]];
+            kb = g.k;
+            for (int j = 0; j < g.k; ++j) { qs[j] = g.targets[j]; local[g.targets[j]] = j; }
+        }
+        ComposeBlock cb;
+        cb.kb = kb;
+        cb.first_gate = (int)cgates.size();
+        cb.num_gates = (int)blk.size();
+        cb.out_off = compose_out;
+        compose_out += (int64_t)1 << (2 * kb);
+        max_kb = std::max(max_kb, kb);
+        for (int gi : blk) {
+            const qsim_gate& g = c->gates[gi];
+            ComposeGate cg;
+            cg.k = g.k;
+            cg.nc = (blk.size() == 1) ? 0 : g.nc;
+            for (int j = 0; j < g.k; ++j) cg.targets[j] = local[g.targets[j]];
+            for (int j = 0; j < cg.nc; ++j) cg.controls[j] = local[g.controls[j]];
+            cg.mat_off = (int64_t)pool.size() / 2;
+            pool.insert(pool.end(), g.matrix, g.matrix + (2 << (2 * g.k)));
+            cgates.push_back(cg);
+        }
+        op.compose_idx = (int)cblocks.size();
+        cblocks.push_back(cb);
+        op.k = kb;
+        op.nc = 0;
+        for (int j = 0; j < kb; ++j) op.targets[j] = qs[j];
+        if (blk.size() == 1) {
+            const qsim_gate& g = c->gates[blk[0]];
+            op.nc = g.nc;
+            std::memcpy(op.controls, g.controls, sizeof(int) * g.nc);
+        }
+        if (all_diag) {
+            op.kind = OP_DIAG;
+            // structural support: pattern m is touched if some gate's factor there is not exactly 1
+            const int D = 1 << kb;
+            for (int m = 0; m < D; ++m) {
+                bool nonunit = false;
+                for (int gi : blk) {
+                    const qsim_gate& g = c->gates[gi];
+                    bool ctl = true;
+                    for (int j = 0; j < g.nc; ++j) ctl = ctl && ((m >> local[g.controls[j]]) & 1);
+                    if (!ctl) continue;
+                    int t = 0;
+                    for (int j = 0; j < g.k; ++j) t |= ((m >> local[g.targets[j]]) & 1) << j;
+                    const int Dg = 1 << g.k;
+                    if (g.matrix[2 * (t * Dg + t)] != 1.0 || g.matrix[2 * (t * Dg + t) + 1] != 0.0) nonunit = true;
+                }
+                if (nonunit) op.touch.push_back(m);
+            }
+        } else if (dtype == QSIM_C64 && opts.precision != QSIM_PREC_SIMT && kb >= tc_min && op.nc == 0 &&
+                   tc_supported(kb, opts.precision) && n >= kb + 7) {
+            op.kind = OP_TC;
+            op.precision = opts.precision;
+            op.dev_off = dev_bytes;
+            dev_bytes = align(dev_bytes + tc_operand_bytes(kb, opts.precision));
+        } else if (kb <= 4) {
+            op.kind = OP_DENSE_SMALL;
+        } else {
+            op.kind = OP_DENSE_TILE;
+            op.dev_off = dev_bytes;
+            dev_bytes = align(dev_bytes + (amp << (2 * kb)));
+        }
+        pending.push_back({(int)p->ops.size(), op.kind, kb});
+        p->ops.push_back(std::move(op));
+    }
+
+    // ---- device buffer: [operands][compose out][pool][block descriptors][gate descriptors] -------------------
+    const size_t off_out = dev_bytes;
+    const size_t off_pool = align(off_out + sizeof(double) * 2 * (size_t)compose_out);
+    const size_t off_cb = align(off_pool + sizeof(double) * pool.size());
+    const size_t off_cg = align(off_cb + sizeof(ComposeBlock) * cblocks.size());
+    const size_t total = align(off_cg + sizeof(ComposeGate) * cgates.size()) + 1024;
+    e = cudaMalloc(&p->dbuf, total);
+    if (e != cudaSuccess) { delete p; set_error("plan buffer of %zu bytes", total); return QSIM_ENOMEM; }
+    p->dbuf_bytes = total;
+    char* base = static_cast<char*>(p->dbuf);
+    int rc = QSIM_OK;
+    if (!cblocks.empty()) {
+        e = cudaMemcpyAsync(base + off_pool, pool.data(), sizeof(double) * pool.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_cb, cblocks.data(), sizeof(ComposeBlock) * cblocks.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_cg, cgates.data(), sizeof(ComposeGate) * cgates.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors are pageable temporaries
+        if (e == cudaSuccess)
+            e = launch_compose(reinterpret_cast<ComposeBlock*>(base + off_cb), (int)cblocks.size(),
+                               reinterpret_cast<ComposeGate*>(base + off_cg), reinterpret_cast<double*>(base + off_pool),
+                               reinterpret_cast<double*>(base + off_out), max_kb, s);
+        // device operands and host copies of small composed matrices
+        std::vector<std::pair<int, std::vector<double>>> fetch;
+        for (const Pending& pd : pending) {
+            if (e != cudaSuccess) break;
+            PlanOp& op = p->ops[pd.op];
+            const double* U = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx].out_off;
+            const int D = 1 << pd.kb;
+            if (pd.kind == OP_TC) {
+                e = launch_tc_prepare(U, pd.kb, op.precision, base + op.dev_off, s);
+            } else if (pd.kind == OP_DENSE_TILE) {
+                e = launch_convert_matrix(dtype, U, base + op.dev_off, 2 * (int64_t)D * D, s);
+            } else {
+                op.mat.resize(2 * (size_t)D * D);
+                e = cudaMemcpyAsync(op.mat.data(), U, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToHost, s);
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) {
+            for (const Pending& pd : pending) {
+                PlanOp& op = p->ops[pd.op];
+                if (op.kind == OP_DIAG) {  // keep the diagonal only
+                    const int D = 1 << op.k;
+                    std::vector<double> dg(2 * D);
+                    for (int i = 0; i < D; ++i) { dg[2 * i] = op.mat[2 * (i * D + i)]; dg[2 * i + 1] = op.mat[2 * (i * D + i) + 1]; }
+                    op.mat.swap(dg);
+                }
+            }
+        }
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+    }
+    if (rc) { cudaFree(p->dbuf); delete p; return rc; }
+
+    // ---- statistics ---------------------------------------------------------------------------------------
+    qsim_plan_info& I = p->info;
+    I.input_gates = G;
+    for (const PlanOp& op : p->ops) {
+        ++I.passes;
+        if (op.kind == OP_DIAG) ++I.diag_blocks;
+        else if (op.kind == OP_TC) ++I.tc_blocks;
+        else ++I.dense_blocks;
+        I.algorithmic_bytes += op_bytes(op, n, amp);
+    }
+    I.host_plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = I;
+    *out = p;
+    return QSIM_OK;
+}
+
+int qsim_plan_execute(qsim_h h, qsim_plan_h p) {
+    if (!h || !p) { set_error("NULL argument"); return QSIM_EINVAL; }
+    set_error("%s", "");
+    if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
+    if (!p->use_graph || h->stream == nullptr) return enqueue_ops(h, p);
+    if (p->gexec && p->ghandle == h && p->gpsi == h->psi && p->gstream == h->stream) {
+        cudaError_t e = cudaGraphLaunch(p->gexec, h->stream);
+        return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "graph launch");
+    }
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    int rc = enqueue_ops(h, p);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { p->gexec = nullptr; return cuda_fail(e, "graph instantiate"); }
+    p->ghandle = h;
+    p->gpsi = h->psi;
+    p->gstream = h->stream;
+    e = cudaGraphLaunch(p->gexec, h->stream);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "graph launch");
+}
+
+int qsim_plan_num_passes(qsim_plan_h p, int64_t* out) {
+    if (!p || !out) { set_error("NULL argument"); return QSIM_EINVAL; }
+    *out = (int64_t)p->ops.size();
+    return QSIM_OK;
+}
+
+int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
+    if (!p || !out) { set_error("NULL argument"); return QSIM_EINVAL; }
+    if (i < 0 || i >= (int64_t)p->ops.size()) { set_error("pass index out of range"); return QSIM_EINVAL; }
+    const PlanOp& op = p->ops[i];
+    out->kind = op.kind;
+    out->k = op.k;
+    out->nc = op.nc;
+    out->precision = op.precision;
+    out->gates = op.gates;
+    out->algorithmic_bytes = op_bytes(op, p->n, p->dtype == QSIM_C64 ? 8 : 16);
+    return QSIM_OK;
+}
+
+int qsim_plan_execute_range(qsim_h h, qsim_plan_h p, int64_t first, int64_t count) {
+    if (!h || !p) { set_error("NULL argument"); return QSIM_EINVAL; }
+    set_error("%s", "");
+    if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
+    if (first < 0 || count < 0 || first + count > (int64_t)p->ops.size()) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
+    return enqueue_ops(h, p, (size_t)first, (size_t)count);
+}
+
+int qsim_plan_destroy(qsim_plan_h p) {
+    if (!p) return QSIM_OK;
+    cudaDeviceSynchronize();
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    cudaFree(p->dbuf);
+    delete p;
+    return QSIM_OK;
+}
+
+int qsim_run(qsim_h h, const qsim_circuit* c, const qsim_run_opts* opts, qsim_plan_info* info) {
+    if (!h || !c) { set_error("NULL argument"); return QSIM_EINVAL; }
+    if (c->n != h->n) { set_error("circuit has %d qubits, state has %d", c->n, h->n); return QSIM_EINVAL; }
+    qsim_run_opts o{};
+    if (opts) o = *opts;
+    o.use_graph = 0;
+    qsim_plan_h p = nullptr;
+    int rc = qsim_plan_create(c, h->dtype, &o, h->stream, &p, info);
+    if (rc) return rc;
+    rc = qsim_plan_execute(h, p);
+    cudaStreamSynchronize(h->stream);
+    qsim_plan_destroy(p);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,337 @@
+"""Python binding of libqsim (C ABI in include/qsim.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. PyTorch supplies device memory (the state tensor)
+and the CUDA stream. If the compiled library is missing it is built with nvcc on first use; if that is not
+possible the binding raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+C64, C128 = 0, 1
+PREC_SIMT, PREC_TF32X3, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3
+RUN_PLAIN, RUN_FUSED = 0, 1
+MAX_TARGETS = MAX_CONTROLS = 8
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+PRECISIONS = {"simt": PREC_SIMT, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+
+
+class QsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Gate(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("nc", ctypes.c_int32),
+                ("targets", ctypes.c_int32 * MAX_TARGETS), ("controls", ctypes.c_int32 * MAX_CONTROLS),
+                ("matrix", ctypes.POINTER(ctypes.c_double))]
+
+
+class Circuit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("num_gates", ctypes.c_int32), ("gates", ctypes.POINTER(Gate))]
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class PassInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("nc", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("gates", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double)]
+
+
+PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc"}
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("input_gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_blocks", ctypes.c_int64),
+                ("tc_blocks", ctypes.c_int64), ("diag_blocks", ctypes.c_int64), ("reorders", ctypes.c_int64),
+                ("algorithmic_bytes", ctypes.c_double), ("host_plan_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+# Every entry point the header declares, with its argument types.
+_P, _vp, _i, _u64, _i64, _sz = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "qsim_abi_version": ([], _i),
+    "qsim_last_error": ([], ctypes.c_char_p),
+    "qsim_state_bytes": ([_i, _i, _P(_sz)], _i),
+    "qsim_create": ([_i, _i, _vp, _sz, _vp, _P(_vp)], _i),
+    "qsim_destroy": ([_vp], _i),
+    "qsim_set_stream": ([_vp, _vp], _i),
+    "qsim_num_qubits": ([_vp, _P(_i)], _i),
+    "qsim_device_ptr": ([_vp, _P(_vp)], _i),
+    "qsim_set_basis": ([_vp, _u64], _i),
+    "qsim_set_state": ([_vp, _vp, _i], _i),
+    "qsim_get_state": ([_vp, _vp, _i], _i),
+    "qsim_synchronize": ([_vp], _i),
+    "qsim_apply_gate": ([_vp, _P(_i), _i, _P(_i), _i, _P(ctypes.c_double)], _i),
+    "qsim_apply_fused": ([_vp, _P(_i), _i, _P(ctypes.c_double), _i], _i),
+    "qsim_swap_qubits": ([_vp, _P(_i), _P(_i), _i], _i),
+    "qsim_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
+    "qsim_plan_execute": ([_vp, _vp], _i),
+    "qsim_plan_destroy": ([_vp], _i),
+    "qsim_plan_num_passes": ([_vp, _P(_i64)], _i),
+    "qsim_plan_pass_info": ([_vp, _i64, _P(PassInfo)], _i),
+    "qsim_plan_execute_range": ([_vp, _vp, _i64, _i64], _i),
+    "qsim_run": ([_vp, _P(Circuit), _P(RunOpts), _P(PlanInfo)], _i),
+    "qsim_norm": ([_vp, _P(ctypes.c_double)], _i),
+    "qsim_probs": ([_vp, _P(_i), _i, _P(ctypes.c_double)], _i),
+    "qsim_expect_pauli": ([_vp, ctypes.c_char_p, _P(ctypes.c_double)], _i),
+    "qsim_expect_z": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
+    "qsim_sample": ([_vp, _u64, _i64, _P(_u64)], _i),
+    "qsim_sample_uniforms": ([_vp, _P(ctypes.c_double), _i64, _P(_u64)], _i),
+    "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
+    "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
+    "qsim_batch_run": ([_P(Circuit), _i, _P(RunOpts), _vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double),
+                        _P(PlanInfo)], _i),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libqsim (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise QsimError(rc, lib().qsim_last_error().decode())
+
+
+def _ints(xs: Iterable[int]):
+    xs = [int(x) for x in xs]
+    return (ctypes.c_int * max(1, len(xs)))(*xs), len(xs)
+
+
+def _mat(U) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def state_bytes(n: int, dtype: int) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().qsim_state_bytes(n, dtype, ctypes.byref(out)))
+    return out.value
+
+
+class State:
+    """An n-qubit state whose amplitudes live in a torch tensor on the current CUDA device."""
+
+    def __init__(self, n: int, dtype: int = C64, tensor=None, stream=None):
+        import torch
+        self.n = n
+        self.dtype = dtype
+        tdt = torch.complex64 if dtype == C64 else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=tdt, device="cuda")
+        if tensor.dtype != tdt or tensor.numel() != (1 << n) or not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("state tensor must be a contiguous CUDA tensor of 2^n amplitudes of the state dtype")
+        self.tensor = tensor
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib().qsim_create(n, dtype, ctypes.c_void_p(tensor.data_ptr()),
+                                 tensor.numel() * tensor.element_size(), ctypes.c_void_p(_stream_ptr(stream)),
+                                 ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qsim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ----------------------------------------------------------------------------------------
+    def set_basis(self, x: int = 0):
+        _check(lib().qsim_set_basis(self.h, int(x)))
+        return self
+
+    def set_state(self, psi: np.ndarray):
+        dt = np.complex64 if self.dtype == C64 else np.complex128
+        a = np.ascontiguousarray(psi, dtype=dt)
+        _check(lib().qsim_set_state(self.h, ctypes.c_void_p(a.ctypes.data), 0))
+        return self
+
+    def get_state(self) -> np.ndarray:
+        dt = np.complex64 if self.dtype == C64 else np.complex128
+        out = np.empty(1 << self.n, dtype=dt)
+        _check(lib().qsim_get_state(self.h, ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def synchronize(self):
+        _check(lib().qsim_synchronize(self.h))
+
+    # -- gates ------------------------------------------------------------------------------------------
+    def apply_gate(self, targets: Sequence[int], controls: Sequence[int], U):
+        t, k = _ints(targets)
+        c, nc = _ints(controls)
+        m = _mat(U)
+        _check(lib().qsim_apply_gate(self.h, t, k, c, nc, _dptr(m)))
+        return self
+
+    def apply_fused(self, targets: Sequence[int], U, precision: int = PREC_SIMT):
+        t, k = _ints(targets)
+        m = _mat(U)
+        _check(lib().qsim_apply_fused(self.h, t, k, _dptr(m), int(precision)))
+        return self
+
+    def swap_qubits(self, a: Sequence[int], b: Sequence[int]):
+        pa, p = _ints(a)
+        pb, _ = _ints(b)
+        _check(lib().qsim_swap_qubits(self.h, pa, pb, p))
+        return self
+
+    def run(self, circuit, mode: int = RUN_PLAIN, max_fused: int = 5, precision: int = PREC_SIMT,
+            tc_min_k: int = 5):
+        cc = CircuitArgs(circuit)
+        o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k, use_graph=0)
+        info = PlanInfo()
+        _check(lib().qsim_run(self.h, ctypes.byref(cc.c), ctypes.byref(o), ctypes.byref(info)))
+        return info.as_dict()
+
+    # -- readout ----------------------------------------------------------------------------------------
+    def norm(self) -> float:
+        out = ctypes.c_double()
+        _check(lib().qsim_norm(self.h, ctypes.byref(out)))
+        return out.value
+
+    def probs(self, qubits: Sequence[int]) -> np.ndarray:
+        q, nq = _ints(qubits)
+        out = np.zeros(1 << nq, dtype=np.float64)
+        _check(lib().qsim_probs(self.h, q, nq, _dptr(out)))
+        return out
+
+    def expect_pauli(self, paulis: str) -> complex:
+        out = np.zeros(2, dtype=np.float64)
+        _check(lib().qsim_expect_pauli(self.h, paulis.encode(), _dptr(out)))
+        return complex(out[0], out[1])
+
+    def expect_z(self):
+        zi = np.zeros(self.n, dtype=np.float64)
+        zz = np.zeros(max(1, self.n - 1), dtype=np.float64)
+        _check(lib().qsim_expect_z(self.h, _dptr(zi), _dptr(zz)))
+        return zi, zz[: self.n - 1]
+
+    def sample(self, seed: int, shots: int) -> np.ndarray:
+        out = np.zeros(shots, dtype=np.uint64)
+        _check(lib().qsim_sample(self.h, seed & (2**64 - 1), shots,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def sample_uniforms(self, u: np.ndarray) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(len(u), dtype=np.uint64)
+        _check(lib().qsim_sample_uniforms(self.h, _dptr(u), len(u),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def inner(self, other: "State") -> complex:
+        out = np.zeros(2, dtype=np.float64)
+        _check(lib().qsim_inner(self.h, other.h, _dptr(out)))
+        return complex(out[0], out[1])
+
+
+class CircuitArgs:
+    """A workloads.Circuit marshalled into qsim_gate structs (keeps the matrices alive)."""
+
+    def __init__(self, circuit):
+        self.n = circuit.n
+        self.mats = []
+        gates = (Gate * max(1, len(circuit.gates)))()
+        for i, g in enumerate(circuit.gates):
+            m = _mat(g.matrix)
+            self.mats.append(m)
+            gates[i].k = len(g.targets)
+            gates[i].nc = len(g.controls)
+            for j, q in enumerate(g.targets):
+                gates[i].targets[j] = q
+            for j, q in enumerate(g.controls):
+                gates[i].controls[j] = q
+            gates[i].matrix = _dptr(m)
+        self.gates = gates
+        self.c = Circuit(n=circuit.n, num_gates=len(circuit.gates), gates=gates)
+
+
+class Plan:
+    """A planned circuit (fusion, kernel choice, FP64 block composition done once)."""
+
+    def __init__(self, circuit, dtype: int = C64, mode: int = RUN_PLAIN, max_fused: int = 5,
+                 precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None):
+        self.args = CircuitArgs(circuit)
+        o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
+                    use_graph=1 if use_graph else 0)
+        info = PlanInfo()
+        p = ctypes.c_void_p()
+        _check(lib().qsim_plan_create(ctypes.byref(self.args.c), dtype, ctypes.byref(o),
+                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(p), ctypes.byref(info)))
+        self.p = p
+        self.info = info.as_dict()
+
+    def execute(self, state: State):
+        _check(lib().qsim_plan_execute(state.h, self.p))
+
+    def execute_range(self, state: State, first: int, count: int):
+        _check(lib().qsim_plan_execute_range(state.h, self.p, int(first), int(count)))
+
+    def passes(self):
+        """Per-pass descriptions: kind, k, controls, precision, merged gates, algorithmic bytes."""
+        num = ctypes.c_int64()
+        _check(lib().qsim_plan_num_passes(self.p, ctypes.byref(num)))
+        out = []
+        for i in range(num.value):
+            pi = PassInfo()
+            _check(lib().qsim_plan_pass_info(self.p, i, ctypes.byref(pi)))
+            out.append({"kind": PASS_KINDS[pi.kind], "k": pi.k, "nc": pi.nc, "precision": pi.precision,
+                        "gates": pi.gates, "algorithmic_bytes": pi.algorithmic_bytes})
+        return out
+
+    def close(self):
+        if getattr(self, "p", None):
+            lib().qsim_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
