@@ -78,7 +78,7 @@ struct ReduceScratch {
     double* result = nullptr;    // 256 doubles (device)
     double* hresult = nullptr;   // 256 doubles (pinned host)
 };
-constexpr int64_t kPartialDoubles = 1 << 18;
+constexpr int64_t kPartialDoubles = 1 << 21;
 constexpr int kSegBits = 12;
 
 cudaError_t run_norm(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,

@@ -439,17 +439,15 @@ __global__ void __launch_bounds__(256) k_chunksum(const double* __restrict__ W, 
     if (threadIdx.x == 0) C[c] = acc.hi + acc.lo;
 }
 
-// Inclusive scan of C[0..m) in place, m <= 4096, one CTA of 1024 threads (double-double).
+// Inclusive scan of C[0..m) in place, one CTA of 1024 threads (double-double). Thread t owns the
+// contiguous run [t * per, (t + 1) * per), per = ceil(m / 1024).
 __global__ void __launch_bounds__(1024) k_scan_small(double* __restrict__ C, int m) {
     __shared__ dd sh[1024];
     const int t = threadIdx.x;
-    dd loc[4];
+    const int per = (m + 1023) / 1024;
+    const int i0 = t * per, i1 = min(m, i0 + per);
     dd run = {0.0, 0.0};
-    for (int j = 0; j < 4; ++j) {
-        const int i = 4 * t + j;
-        run = dd_add(run, dd{i < m ? C[i] : 0.0, 0.0});
-        loc[j] = run;
-    }
+    for (int i = i0; i < i1; ++i) run = dd_add(run, dd{C[i], 0.0});
     sh[t] = run;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -458,13 +456,10 @@ __global__ void __launch_bounds__(1024) k_scan_small(double* __restrict__ C, int
         sh[t] = dd_add(sh[t], v);
         __syncthreads();
     }
-    const dd before = t > 0 ? sh[t - 1] : dd{0.0, 0.0};
-    for (int j = 0; j < 4; ++j) {
-        const int i = 4 * t + j;
-        if (i < m) {
-            const dd v = dd_add(before, loc[j]);
-            C[i] = v.hi + v.lo;
-        }
+    dd acc = t > 0 ? sh[t - 1] : dd{0.0, 0.0};
+    for (int i = i0; i < i1; ++i) {
+        acc = dd_add(acc, dd{C[i], 0.0});
+        C[i] = acc.hi + acc.lo;
     }
 }
 
