@@ -1,12 +1,423 @@
-// k_tc.cu -- tensor-core fused block (placeholder until the tcgen05 kernel lands).
+// k_tc.cu -- a fused dense block on the 5th-generation tensor cores (tcgen05) with split precision.
+//
+// Paper Sec. 2.1: fusion merges gates into one larger matrix, which raises arithmetic intensity and moves
+// the work from bandwidth-bound towards balanced; Sec. 2.2: the fusion level suited to Blackwell at FP32 is 5.
+// For a block U (2^K x 2^K complex) on targets T, the amplitudes split into rows (the 7 lowest index bits
+// outside T; a tile of 128 rows) and columns (the 2^K combinations of T). Per tile, Y = X U^T with X the
+// [128 x 2^K] complex tile, computed as one real GEMM [128 x 2^(K+1)] . [2^(K+1) x 2^(K+1)] using the real
+// form [[Ur, Ui], [-Ui, Ur]] of U. Complex64 accuracy is recovered from low-precision products by splitting
+// both operands (Ootomo & Yokota 2022 for 3xTF32; Henry, Tang & Heinecke 2019 for BF16x3 / BF16x6), with
+// FP32 accumulation in tensor memory.
+//
+// Data flow per CTA (one per SM, persistent over tiles; 16 warps, warp w serves TMEM lanes 32 (w mod 4)..):
+//   B planes (the split U, pre-swizzled in global memory) -> shared memory once, SWIZZLE_128B K-major;
+//   tile t: 16 coalesced 8-byte loads per thread into registers (issued one tile ahead), split into hi / lo
+//   (/ mid) planes, tcgen05.st into TMEM as the A operand; one thread issues the MMAs (A from TMEM, B from
+//   shared memory, D in TMEM) and commits them to an mbarrier; the epilogue tcgen05.ld's D and stores the
+//   tile back in place. Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
+//   DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "common.cuh"
 #include "internal.h"
+#include "tmem_io.cuh"
 
 namespace qsim {
-bool tc_supported(int, int) { return false; }
-size_t tc_operand_bytes(int, int) { return 0; }
-cudaError_t launch_tc_prepare(const double*, int, int, void*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_tc_apply(void*, int, int, const int*, const void*, int, unsigned*, cudaStream_t, const DevInfo&) {
-    return cudaErrorNotSupported;
+namespace tc {
+
+template <int PREC> struct Cfg;
+template <> struct Cfg<QSIM_PREC_TF32X3> {
+    static constexpr int planes = 2, esize = 4, nprod = 3;
+    // small products first: lo*hi, hi*lo, hi*hi
+    __host__ __device__ static constexpr int pa(int i) { return i == 0 ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+template <> struct Cfg<QSIM_PREC_BF16X3> {
+    static constexpr int planes = 2, esize = 2, nprod = 3;
+    __host__ __device__ static constexpr int pa(int i) { return i == 0 ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+template <> struct Cfg<QSIM_PREC_BF16X6> {
+    static constexpr int planes = 3, esize = 2, nprod = 6;  // all products of planes i + j <= 2
+    // (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+    __host__ __device__ static constexpr int pa(int i) { return i == 0 ? 2 : (i == 1 || i == 3) ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int i) { return i == 2 ? 2 : (i == 1 || i == 4) ? 1 : 0; }
+};
+
+constexpr int kThreads = 512;
+constexpr int kRowBits = 7;  // 128 rows per tile (MMA M = 128)
+
+__host__ __device__ constexpr int plane_bytes(int K, int esize) { return (2 << K) * (2 << K) * esize; }
+__host__ __device__ constexpr uint32_t pow2_at_least(uint32_t v) {
+    uint32_t p = 32;
+    while (p < v) p <<= 1;
+    return p;
 }
+
+// Byte offset of element (n, kk) of an [NR x NR] K-major operand in the canonical SWIZZLE_128B layout:
+// K is cut into 128-byte atoms; atom a holds all NR rows, 8-row groups 1024 bytes apart, and the 16-byte
+// chunk index inside a 128-byte row is XOR-ed with (row mod 8).
+__host__ __device__ inline uint32_t sw128_offset(int n, int kk, int NR, int esize) {
+    const int epa = 128 / esize;
+    const int atom = kk / epa;
+    const int cb = (kk % epa) * esize;
+    const int chunk = cb >> 4, within = cb & 15;
+    const int g = n >> 3, r8 = n & 7;
+    return (uint32_t)(atom * (NR * 128) + g * 1024 + r8 * 128 + ((chunk ^ r8) << 4) + within);
+}
+
+// ---- PTX wrappers ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the mbarrier phase with a 2-second limit; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t phase) {
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(addr, phase)) {
+        if (globaltimer() - t0 > 2000000000ull) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// Shared-memory matrix descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc, uint32_t acc) {
+    if constexpr (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
+            :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(acc) : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
+            :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(acc) : "memory");
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[N]) {
+    if constexpr (N == 8) tmem_st_x8(taddr, v);
+    else if constexpr (N == 16) tmem_st_x16(taddr, v);
+    else tmem_st_x32(taddr, v);
+}
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
+    if constexpr (N == 8) tmem_ld_x8(taddr, v);
+    else if constexpr (N == 16) tmem_ld_x16(taddr, v);
+    else tmem_ld_x32(taddr, v);
+}
+
+struct Args {
+    int nS;            // K + 7 index bits covered by a tile
+    int spos[24];      // those bit positions, ascending (zeros inserted there to form a tile base)
+    int rpos[kRowBits];// row bit j <-> index bit rpos[j]
+    int tpos[8];       // column bit j <-> target j
+    uint64_t ntiles;
+};
+
+template <int K, int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
+           unsigned* __restrict__ err) {
+    using C = Cfg<PREC>;
+    constexpr bool BF16 = C::esize == 2;
+    constexpr int D = 1 << K, NR = 2 * D;
+    constexpr int PB = plane_bytes(K, C::esize);
+    constexpr int ATOM = NR * 128;                         // bytes of one 128-byte-wide K atom (all NR rows)
+    constexpr int KSTEPS = NR * C::esize / 32;             // each MMA consumes 32 bytes of K
+    constexpr int CPT = D / 4;                             // complex columns per thread (4 warps per quadrant)
+    constexpr int ACOLS = BF16 ? NR / 2 : NR;              // TMEM columns per A plane
+    constexpr uint32_t TCOLS = pow2_at_least(NR + C::planes * ACOLS);
+    constexpr int AV = BF16 ? CPT : 2 * CPT;               // 32-bit values per thread per A plane
+    constexpr uint32_t IDESC = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
+                               ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
+    uint64_t* mbar = sCol + D;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3;
+    const int c0 = (warp >> 2) * CPT;
+    const int r = quad * 32 + lane;
+
+    // B planes -> shared memory (already in the swizzled byte layout), column offsets, barrier, TMEM.
+    for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
+    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make B visible to the tensor cores
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+    const uint32_t mbar_addr = smem_u32(mbar);
+    const uint32_t sB = smem_u32(sb);
+    const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+
+    uint32_t phase = 0;
+    bool bad = false, have_prev = false;
+    uint64_t prev_base = 0;
+    float2 X[CPT];
+    uint64_t tile = blockIdx.x;
+    if (tile < a.ntiles) {
+        const uint64_t b0 = insert_zeros(tile, a.spos, a.nS) + rowoff;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) X[j] = psi[b0 + sCol[c0 + j]];
+    }
+
+    auto epilogue = [&](uint64_t base) {
+        uint32_t v[2 * CPT];
+        tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
+        wait_ld();
+        const uint64_t b = base + rowoff;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+            psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+    };
+
+    for (; tile < a.ntiles; tile += gridDim.x) {
+        const uint64_t base = insert_zeros(tile, a.spos, a.nS);
+        if (have_prev) {
+            int to = 0;
+            if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
+            if (__syncthreads_or(to)) { bad = true; break; }
+            phase ^= 1;
+            fence_after();
+            epilogue(prev_base);
+        }
+        // split the tile into the A planes (TMEM)
+        if constexpr (!BF16) {
+            uint32_t hi[AV], lo[AV];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                hi[2 * j] = tf32_rna(X[j].x);
+                hi[2 * j + 1] = tf32_rna(X[j].y);
+                lo[2 * j] = __float_as_uint(X[j].x - __uint_as_float(hi[2 * j]));
+                lo[2 * j + 1] = __float_as_uint(X[j].y - __uint_as_float(hi[2 * j + 1]));
+            }
+            tmem_st<AV>(tbase + tlane + NR + 0 * ACOLS + 2 * c0, hi);
+            tmem_st<AV>(tbase + tlane + NR + 1 * ACOLS + 2 * c0, lo);
+        } else {
+            uint32_t p0[AV], p1[AV];
+            [[maybe_unused]] uint32_t p2[AV];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const __nv_bfloat16 hr = __float2bfloat16_rn(X[j].x), hm = __float2bfloat16_rn(X[j].y);
+                const float rr = X[j].x - __bfloat162float(hr), ri = X[j].y - __bfloat162float(hm);
+                const __nv_bfloat16 mr = __float2bfloat16_rn(rr), mi = __float2bfloat16_rn(ri);
+                p0[j] = pack_bf16(hr, hm);
+                p1[j] = pack_bf16(mr, mi);
+                if constexpr (C::planes == 3) {
+                    p2[j] = pack_bf16(__float2bfloat16_rn(rr - __bfloat162float(mr)),
+                                      __float2bfloat16_rn(ri - __bfloat162float(mi)));
+                }
+            }
+            tmem_st<AV>(tbase + tlane + NR + 0 * ACOLS + c0, p0);
+            tmem_st<AV>(tbase + tlane + NR + 1 * ACOLS + c0, p1);
+            if constexpr (C::planes == 3) tmem_st<AV>(tbase + tlane + NR + 2 * ACOLS + c0, p2);
+        }
+        wait_st();
+        // issue the next tile's loads now so they overlap this tile's MMAs
+        const uint64_t next = tile + gridDim.x;
+        if (next < a.ntiles) {
+            const uint64_t b1 = insert_zeros(next, a.spos, a.nS) + rowoff;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) X[j] = psi[b1 + sCol[c0 + j]];
+        }
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            uint32_t acc = 0;
+#pragma unroll
+            for (int pr = 0; pr < C::nprod; ++pr) {
+                const uint32_t acol = tbase + NR + C::pa(pr) * ACOLS;
+                const uint32_t bpl = sB + C::pb(pr) * PB;
+#pragma unroll
+                for (int s = 0; s < KSTEPS; ++s) {
+                    mma_ts<BF16>(tbase, acol + 8 * s, sdesc_sw128(bpl + (s >> 2) * ATOM + (s & 3) * 32), IDESC, acc);
+                    acc = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(mbar_addr) : "memory");
+        }
+        prev_base = base;
+        have_prev = true;
+    }
+    if (have_prev && !bad) {
+        int to = 0;
+        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
+        if (__syncthreads_or(to)) {
+            bad = true;
+        } else {
+            fence_after();
+            epilogue(prev_base);
+        }
+    }
+    if (bad && tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        mbar_wait_bounded(mbar_addr, phase);  // give in-flight MMAs one more bounded chance to retire
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TCOLS) : "memory");
+    }
+}
+
+// B operand: Bt[n][kk] of the real form, Bt[2i][2c] = Re U_ic, Bt[2i][2c+1] = -Im U_ic, Bt[2i+1][2c] = Im U_ic,
+// Bt[2i+1][2c+1] = Re U_ic, split into planes and written in the swizzled shared-memory byte layout.
+template <int PREC>
+__global__ void k_tc_prepare(const double* __restrict__ U, int K, unsigned char* __restrict__ out) {
+    using C = Cfg<PREC>;
+    const int D = 1 << K, NR = 2 * D;
+    const int PB = plane_bytes(K, C::esize);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NR * NR; idx += gridDim.x * blockDim.x) {
+        const int n = idx / NR, kk = idx % NR;
+        const int i = n >> 1, c = kk >> 1;
+        const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
+        const double v = (n & 1) == 0 ? ((kk & 1) == 0 ? ur : -ui) : ((kk & 1) == 0 ? ui : ur);
+        const uint32_t off = sw128_offset(n, kk, NR, C::esize);
+        if constexpr (C::esize == 4) {
+            const uint32_t hi = tf32_rna((float)v);
+            const float lo = (float)(v - (double)__uint_as_float(hi));
+            *reinterpret_cast<uint32_t*>(out + off) = hi;
+            *reinterpret_cast<uint32_t*>(out + PB + off) = tf32_rna(lo);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+            const double r1 = v - (double)__bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+            *reinterpret_cast<__nv_bfloat16*>(out + off) = h;
+            *reinterpret_cast<__nv_bfloat16*>(out + PB + off) = m;
+            if constexpr (C::planes == 3) {
+                const double r2 = r1 - (double)__bfloat162float(m);
+                *reinterpret_cast<__nv_bfloat16*>(out + 2 * PB + off) = __float2bfloat16_rn((float)r2);
+            }
+        }
+    }
+}
+
+template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
+template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
+
+size_t smem_bytes(int K, int planes, int esize) {
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;
+    return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
+}
+
+template <int K, int PREC>
+cudaError_t apply_t(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
+    const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_block<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
+    k_tc_block<K, PREC><<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a,
+                                                       reinterpret_cast<const uint4*>(dB), err);
+    return cudaGetLastError();
+}
+
+}  // namespace tc
+
+bool tc_supported(int k, int precision) {
+    return (k == 5 || k == 6) &&
+           (precision == QSIM_PREC_TF32X3 || precision == QSIM_PREC_BF16X3 || precision == QSIM_PREC_BF16X6);
+}
+
+size_t tc_operand_bytes(int k, int precision) {
+    if (!tc_supported(k, precision)) return 0;
+    const int planes = precision == QSIM_PREC_BF16X6 ? 3 : 2;
+    const int esize = precision == QSIM_PREC_TF32X3 ? 4 : 2;
+    return (size_t)planes * tc::plane_bytes(k, esize);
+}
+
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s) {
+    if (!tc_supported(k, precision)) return cudaErrorInvalidValue;
+    unsigned char* out = static_cast<unsigned char*>(dB);
+    const int blocks = ((2 << k) * (2 << k) + 255) / 256;
+    switch (precision) {
+        case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, out); break;
+        case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, out); break;
+        default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, out); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
+                            unsigned* dev_err, cudaStream_t s, const DevInfo& d) {
+    if (!tc_supported(k, precision) || n < k + tc::kRowBits) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
+    tc::Args a;
+    std::memset(&a, 0, sizeof(a));
+    uint64_t tmask = 0;
+    for (int j = 0; j < k; ++j) { a.tpos[j] = targets[j]; tmask |= 1ull << targets[j]; }
+    int nr = 0;
+    for (int q = 0; q < n && nr < tc::kRowBits; ++q)
+        if (!((tmask >> q) & 1)) a.rpos[nr++] = q;
+    uint64_t smask = tmask;
+    for (int j = 0; j < tc::kRowBits; ++j) smask |= 1ull << a.rpos[j];
+    for (int q = 0; q < n; ++q)
+        if ((smask >> q) & 1) a.spos[a.nS++] = q;
+    a.ntiles = 1ull << (n - a.nS);
+    switch (precision * 8 + k) {
+        case QSIM_PREC_TF32X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_TF32X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_BF16X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_BF16X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_BF16X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_BF16X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_BF16X6 * 8 + 5: return tc::apply_t<5, QSIM_PREC_BF16X6>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_BF16X6 * 8 + 6: return tc::apply_t<6, QSIM_PREC_BF16X6>(psi, a, dB, dev_err, s, d);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace qsim
