@@ -232,6 +232,24 @@ int qsim_sample(qsim_h h, uint64_t seed, int64_t shots, uint64_t* out);
 /* Same with caller-supplied uniforms u[0..shots) in [0, 1) (host). */
 int qsim_sample_uniforms(qsim_h h, const double* u, int64_t shots, uint64_t* out);
 
+/*
+ * Sampling for callers that cannot allocate device memory (the paper has no counterpart; this is a library
+ * service). A framework that has reserved all GPU memory in its own pool, or a latency-critical path that
+ * cannot afford an allocation's implicit synchronisation, can draw samples from a state it owns without
+ * creating a handle: dev_state is its complex64 (dtype 0) or complex128 (dtype 1) state of 2^n amplitudes
+ * in device memory, dev_out a device buffer of `shots` uint64 that receives the indices, both owned by the
+ * caller. Results are those of qsim_sample with the same seed. The call only enqueues work on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and returns; dev_out is valid once the stream completes.
+ * It allocates nothing: its scratch is one fixed 8 MiB array inside the library image, present on every
+ * GPU that loads the library until the process exits. Requests needing more scratch than that (8 bytes
+ * per shot plus 8 bytes per 4096 amplitudes, rounded up per region) fail with QSIM_EINVAL before any work.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture. All calls share the array: calls whose work overlaps on the GPU race,
+ * so serialise them (one stream, one host thread at a time).
+ */
+int qsim_sample_noalloc(const void* dev_state, int n, int dtype, uint64_t seed, int64_t shots,
+                        uint64_t* dev_out, void* stream);
+
 /* <a|b> for two handles of equal n and dtype on the same device. out[0..1] = (re, im). Synchronises. */
 int qsim_inner(qsim_h a, qsim_h b, double* out);
 

@@ -93,6 +93,7 @@ SIGNATURES = {
     "qsim_sample": ([_vp, _u64, _i64, _P(_u64)], _i),
     "qsim_sample_uniforms": ([_vp, _P(ctypes.c_double), _i64, _P(_u64)], _i),
     "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
+    "qsim_sample_noalloc": ([_vp, _i, _i, _u64, _i64, _vp, _vp], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
     "qsim_batch_run": ([_P(Circuit), _i, _P(RunOpts), _vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double),
                         _P(PlanInfo)], _i),
