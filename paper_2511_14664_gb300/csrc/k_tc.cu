@@ -11,10 +11,11 @@
 //
 // Data flow per CTA (one per SM, persistent over tiles; 16 warps, warp w serves TMEM lanes 32 (w mod 4)..):
 //   B planes (the split U, pre-swizzled in global memory) -> shared memory once, SWIZZLE_128B K-major;
-//   tile t: 16 coalesced 8-byte loads per thread into registers (issued one tile ahead), split into hi / lo
-//   (/ mid) planes, tcgen05.st into TMEM as the A operand; one thread issues the MMAs (A from TMEM, B from
-//   shared memory, D in TMEM) and commits them to an mbarrier; the epilogue tcgen05.ld's D and stores the
-//   tile back in place. Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
+//   tile t: coalesced loads into registers (issued one tile ahead; 16-byte vectors when qubit 0 is the
+//   block's first target), split into hi / lo (/ mid) planes, tcgen05.st into TMEM as the A operand; one
+//   thread issues the MMAs (A from TMEM, B from shared memory) into one of two TMEM accumulators and commits
+//   them to an mbarrier; while the tensor cores work on tile t the warps load tile t+1 and run the epilogue
+//   of tile t-1 (tcgen05.ld of the other accumulator, stores back in place). Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
 //   DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
@@ -153,7 +154,7 @@ struct Args {
     uint64_t ntiles;
 };
 
-template <int K, int PREC>
+template <int K, int PREC, bool P0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
@@ -165,7 +166,8 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     constexpr int KSTEPS = NR * C::esize / 32;             // each MMA consumes 32 bytes of K
     constexpr int CPT = D / 4;                             // complex columns per thread (4 warps per quadrant)
     constexpr int ACOLS = BF16 ? NR / 2 : NR;              // TMEM columns per A plane
-    constexpr uint32_t TCOLS = pow2_at_least(NR + C::planes * ACOLS);
+    constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A planes after
+    constexpr uint32_t TCOLS = pow2_at_least(A0 + C::planes * ACOLS);
     constexpr int AV = BF16 ? CPT : 2 * CPT;               // 32-bit values per thread per A plane
     constexpr uint32_t IDESC = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
                                ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -203,51 +205,70 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     const uint32_t sB = smem_u32(sb);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
 
-    uint32_t phase = 0;
-    bool bad = false, have_prev = false;
-    uint64_t prev_base = 0;
+    // Thread (r, columns c0..c0+CPT) of a tile. With P0 (qubit 0 is target 0) columns 2i and 2i+1 are
+    // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
     float2 X[CPT];
-    uint64_t tile = blockIdx.x;
-    if (tile < a.ntiles) {
-        const uint64_t b0 = insert_zeros(tile, a.spos, a.nS) + rowoff;
+    auto load_tile = [&](uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+        if constexpr (P0) {
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) X[j] = psi[b0 + sCol[c0 + j]];
-    }
-
-    auto epilogue = [&](uint64_t base) {
+            for (int j = 0; j < CPT; j += 2) {
+                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
+                X[j] = make_float2(v.x, v.y);
+                X[j + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
+        }
+    };
+    auto epilogue = [&](uint64_t base, uint32_t dcol) {
         uint32_t v[2 * CPT];
-        tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
+        tmem_ld<2 * CPT>(tbase + tlane + dcol + 2 * c0, v);
         wait_ld();
         const uint64_t b = base + rowoff;
+        if constexpr (P0) {
 #pragma unroll
-        for (int j = 0; j < CPT; ++j)
-            psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+            for (int j = 0; j < CPT; j += 2)
+                *reinterpret_cast<float4*>(psi + b + sCol[c0 + j]) =
+                    make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
     };
 
-    for (; tile < a.ntiles; tile += gridDim.x) {
+    uint32_t phase = 0;
+    bool bad = false;
+    uint64_t prev_base = 0;
+    uint32_t it = 0;
+    uint64_t tile = blockIdx.x;
+    if (tile < a.ntiles) load_tile(tile);
+
+    // Pipeline per tile t: wait MMA(t-1) (A free, D[(t-1)&1] final) | split X(t) into A | MMA(t) -> D[t&1]
+    // | loads of tile t+1 | epilogue of tile t-1 from D[(t-1)&1], overlapping MMA(t).
+    for (; tile < a.ntiles; tile += gridDim.x, ++it) {
         const uint64_t base = insert_zeros(tile, a.spos, a.nS);
-        if (have_prev) {
+        if (it > 0) {
             int to = 0;
             if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
             if (__syncthreads_or(to)) { bad = true; break; }
             phase ^= 1;
             fence_after();
-            epilogue(prev_base);
         }
-        // split the tile into the A planes (TMEM)
         if constexpr (!BF16) {
             uint32_t hi[AV], lo[AV];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
                 hi[2 * j] = tf32_rna(X[j].x);
                 hi[2 * j + 1] = tf32_rna(X[j].y);
-                // the residual is rounded to TF32 here: left to the tensor core, its low bits would be
-                // truncated towards zero, a bias that shrinks the norm by ~2^-23 per element per block
                 lo[2 * j] = tf32_rna(X[j].x - __uint_as_float(hi[2 * j]));
                 lo[2 * j + 1] = tf32_rna(X[j].y - __uint_as_float(hi[2 * j + 1]));
             }
-            tmem_st<AV>(tbase + tlane + NR + 0 * ACOLS + 2 * c0, hi);
-            tmem_st<AV>(tbase + tlane + NR + 1 * ACOLS + 2 * c0, lo);
+            tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + 2 * c0, hi);
+            tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + 2 * c0, lo);
         } else {
             uint32_t p0[AV], p1[AV];
             [[maybe_unused]] uint32_t p2[AV];
@@ -263,47 +284,43 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                                       __float2bfloat16_rn(ri - __bfloat162float(mi)));
                 }
             }
-            tmem_st<AV>(tbase + tlane + NR + 0 * ACOLS + c0, p0);
-            tmem_st<AV>(tbase + tlane + NR + 1 * ACOLS + c0, p1);
-            if constexpr (C::planes == 3) tmem_st<AV>(tbase + tlane + NR + 2 * ACOLS + c0, p2);
+            tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + c0, p0);
+            tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + c0, p1);
+            if constexpr (C::planes == 3) tmem_st<AV>(tbase + tlane + A0 + 2 * ACOLS + c0, p2);
         }
         wait_st();
-        // issue the next tile's loads now so they overlap this tile's MMAs
-        const uint64_t next = tile + gridDim.x;
-        if (next < a.ntiles) {
-            const uint64_t b1 = insert_zeros(next, a.spos, a.nS) + rowoff;
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = psi[b1 + sCol[c0 + j]];
-        }
         fence_before();
         __syncthreads();
+        const uint32_t dcol = (it & 1) ? NR : 0;
         if (tid == 0) {
             fence_after();
             uint32_t acc = 0;
 #pragma unroll
             for (int pr = 0; pr < C::nprod; ++pr) {
-                const uint32_t acol = tbase + NR + C::pa(pr) * ACOLS;
+                const uint32_t acol = tbase + A0 + C::pa(pr) * ACOLS;
                 const uint32_t bpl = sB + C::pb(pr) * PB;
 #pragma unroll
                 for (int s = 0; s < KSTEPS; ++s) {
-                    mma_ts<BF16>(tbase, acol + 8 * s, sdesc_sw128(bpl + (s >> 2) * ATOM + (s & 3) * 32), IDESC, acc);
+                    mma_ts<BF16>(tbase + dcol, acol + 8 * s, sdesc_sw128(bpl + (s >> 2) * ATOM + (s & 3) * 32), IDESC, acc);
                     acc = 1;
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(mbar_addr) : "memory");
         }
+        const uint64_t next = tile + gridDim.x;
+        if (next < a.ntiles) load_tile(next);
+        if (it > 0) epilogue(prev_base, dcol ^ NR);
         prev_base = base;
-        have_prev = true;
     }
-    if (have_prev && !bad) {
+    if (it > 0 && !bad) {
         int to = 0;
         if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
         if (__syncthreads_or(to)) {
             bad = true;
         } else {
             fence_after();
-            epilogue(prev_base);
+            epilogue(prev_base, ((it - 1) & 1) ? NR : 0);
         }
     }
     if (bad && tid == 0) {
@@ -358,15 +375,21 @@ size_t smem_bytes(int K, int planes, int esize) {
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
-template <int K, int PREC>
-cudaError_t apply_t(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
+template <int K, int PREC, bool P0>
+cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_block<K, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_block<K, PREC, P0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
-    k_tc_block<K, PREC><<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a,
-                                                       reinterpret_cast<const uint4*>(dB), err);
+    k_tc_block<K, PREC, P0><<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a,
+                                                           reinterpret_cast<const uint4*>(dB), err);
     return cudaGetLastError();
+}
+
+template <int K, int PREC>
+cudaError_t apply_t(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
+    if (a.tpos[0] == 0) return apply_p<K, PREC, true>(psi, a, dB, err, s, d);
+    return apply_p<K, PREC, false>(psi, a, dB, err, s, d);
 }
 
 }  // namespace tc
