@@ -11,12 +11,11 @@
 //
 // Data flow per CTA (one per SM, persistent over tiles; 16 warps, warp w serves TMEM lanes 32 (w mod 4)..):
 //   B planes (the split U, pre-swizzled in global memory) -> shared memory once, SWIZZLE_128B K-major;
-//   tile t+2 streams into a shared-memory stage by 1-D bulk copies of its contiguous chunks (>= 1 KiB each,
-//   completion counted on an mbarrier); tile t+1 waits in registers; tile t is split into hi / lo (/ mid)
-//   planes and tcgen05.st'd into TMEM as the A operand; one thread issues the MMAs (A from TMEM, B from
-//   shared memory) into one of two TMEM accumulators and commits them to an mbarrier; while the tensor
-//   cores work on tile t the warps run the epilogue of tile t-1 (tcgen05.ld of the other accumulator,
-//   stores back in place; 16-byte vectors when qubit 0 is the block's first target). Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
+//   tile t: coalesced loads into registers (issued one tile ahead; 16-byte vectors when qubit 0 is the
+//   block's first target), split into hi / lo (/ mid) planes, tcgen05.st into TMEM as the A operand; one
+//   thread issues the MMAs (A from TMEM, B from shared memory) into one of two TMEM accumulators and commits
+//   them to an mbarrier; while the tensor cores work on tile t the warps load tile t+1 and run the epilogue
+//   of tile t-1 (tcgen05.ld of the other accumulator, stores back in place). Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
 //   DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
@@ -152,16 +151,8 @@ struct Args {
     int spos[24];      // those bit positions, ascending (zeros inserted there to form a tile base)
     int rpos[kRowBits];// row bit j <-> index bit rpos[j]
     int tpos[8];       // column bit j <-> target j
-    int rloc[kRowBits];// row bit j <-> bit rloc[j] of the tile's natural order (position among spos)
-    int tloc[8];       // column bit j <-> bit tloc[j] of the tile's natural order
-    int cbits;         // the tile is 2^(nS - cbits) contiguous chunks of 2^cbits amplitudes (cbits >= 7)
     uint64_t ntiles;
 };
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
 
 template <int K, int PREC, bool P0>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -178,38 +169,25 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A planes after
     constexpr uint32_t TCOLS = pow2_at_least(A0 + C::planes * ACOLS);
     constexpr int AV = BF16 ? CPT : 2 * CPT;               // 32-bit values per thread per A plane
-    constexpr uint32_t TILE_BYTES = 8u << (K + kRowBits);  // 128 rows x 2^K amplitudes
     constexpr uint32_t IDESC = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
                                ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
-    // shared memory: [B planes][tile stage][global column offsets][stage column offsets][chunk offsets][barriers]
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float2* stage = reinterpret_cast<float2*>(sb + C::planes * PB);
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB + TILE_BYTES);
-    uint32_t* sLoc = reinterpret_cast<uint32_t*>(sCol + D);
-    uint64_t* sChunk = reinterpret_cast<uint64_t*>(sLoc + D);
-    uint64_t* mbar = sChunk + 64;                          // [0]: MMA completion, [1]: stage filled
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
+    uint64_t* mbar = sCol + D;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
     const int c0 = (warp >> 2) * CPT;
     const int r = quad * 32 + lane;
-    const int nchunks = 1 << (a.nS - a.cbits);
-    const uint32_t chunk_bytes = 8u << a.cbits;
 
-    // B planes -> shared memory (already in the swizzled byte layout), offset tables, barriers, TMEM.
+    // B planes -> shared memory (already in the swizzled byte layout), column offsets, barrier, TMEM.
     for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
-    for (int c = tid; c < D; c += kThreads) {
-        sCol[c] = deposit((uint64_t)c, a.tpos, K);
-        sLoc[c] = (uint32_t)deposit((uint64_t)c, a.tloc, K);
-    }
-    for (int j = tid; j < nchunks; j += kThreads)
-        sChunk[j] = deposit((uint64_t)j, a.spos + a.cbits, a.nS - a.cbits);
+    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make B visible to the tensor cores
@@ -223,34 +201,25 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     fence_after();
     const uint32_t tbase = *tslot;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint32_t mma_bar = smem_u32(mbar), stage_bar = smem_u32(mbar + 1);
-    const uint32_t sB = smem_u32(sb), sStage = smem_u32(stage);
+    const uint32_t mbar_addr = smem_u32(mbar);
+    const uint32_t sB = smem_u32(sb);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
-    const uint32_t rowloc = (uint32_t)deposit((uint64_t)r, a.rloc, kRowBits);
 
-    // The stage is filled by warp 0 with 1-D bulk copies of the tile's contiguous chunks.
-    auto fill_stage = [&](uint64_t t) {
-        if (warp == 0) {
-            const uint64_t b = insert_zeros(t, a.spos, a.nS);
-            if (lane == 0)
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(stage_bar), "r"(TILE_BYTES) : "memory");
-            __syncwarp();
-            for (int j = lane; j < nchunks; j += 32)
-                bulk_g2s(sStage + (uint32_t)j * chunk_bytes, psi + b + sChunk[j], chunk_bytes, stage_bar);
-        }
-    };
+    // Thread (r, columns c0..c0+CPT) of a tile. With P0 (qubit 0 is target 0) columns 2i and 2i+1 are
+    // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
     float2 X[CPT];
-    auto read_stage = [&]() {
+    auto load_tile = [&](uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
         if constexpr (P0) {
 #pragma unroll
             for (int j = 0; j < CPT; j += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(stage + rowloc + sLoc[c0 + j]);
+                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
                 X[j] = make_float2(v.x, v.y);
                 X[j + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = stage[rowloc + sLoc[c0 + j]];
+            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
         }
     };
     auto epilogue = [&](uint64_t base, uint32_t dcol) {
@@ -271,31 +240,20 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         }
     };
 
-    uint32_t phase = 0, sphase = 0;
+    uint32_t phase = 0;
     bool bad = false;
     uint64_t prev_base = 0;
     uint32_t it = 0;
     uint64_t tile = blockIdx.x;
-    // prologue: tile -> registers (through the stage), then start staging the next tile
-    if (tile < a.ntiles) {
-        fill_stage(tile);
-        const bool ok = mbar_wait_bounded(stage_bar, sphase);
-        sphase ^= 1;
-        if (ok) read_stage();
-        if (__syncthreads_or(!ok)) bad = true;
-        else if (tile + gridDim.x < a.ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fill_stage(tile + gridDim.x);
-        }
-    }
+    if (tile < a.ntiles) load_tile(tile);
 
     // Pipeline per tile t: wait MMA(t-1) (A free, D[(t-1)&1] final) | split X(t) into A | MMA(t) -> D[t&1]
-    // | X <- stage (tile t+1) | stage <- bulk copies of tile t+2 | epilogue of tile t-1, overlapping MMA(t).
-    for (; !bad && tile < a.ntiles; tile += gridDim.x, ++it) {
+    // | loads of tile t+1 | epilogue of tile t-1 from D[(t-1)&1], overlapping MMA(t).
+    for (; tile < a.ntiles; tile += gridDim.x, ++it) {
         const uint64_t base = insert_zeros(tile, a.spos, a.nS);
         if (it > 0) {
             int to = 0;
-            if (tid == 0) to = !mbar_wait_bounded(mma_bar, phase);
+            if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
             if (__syncthreads_or(to)) { bad = true; break; }
             phase ^= 1;
             fence_after();
@@ -348,25 +306,16 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mma_bar) : "memory");
+                         :: "r"(mbar_addr) : "memory");
         }
         const uint64_t next = tile + gridDim.x;
-        if (next < a.ntiles) {
-            const bool ok = mbar_wait_bounded(stage_bar, sphase);
-            sphase ^= 1;
-            if (ok) read_stage();
-            if (__syncthreads_or(!ok)) { bad = true; }
-            else if (next + gridDim.x < a.ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fill_stage(next + gridDim.x);
-            }
-        }
+        if (next < a.ntiles) load_tile(next);
         if (it > 0) epilogue(prev_base, dcol ^ NR);
         prev_base = base;
     }
     if (it > 0 && !bad) {
         int to = 0;
-        if (tid == 0) to = !mbar_wait_bounded(mma_bar, phase);
+        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
         if (__syncthreads_or(to)) {
             bad = true;
         } else {
@@ -376,9 +325,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     }
     if (bad && tid == 0) {
         atomicOr(err, DEVERR_TIMEOUT);
-        // give in-flight MMAs and bulk copies one more bounded chance to retire before TMEM and smem go away
-        mbar_wait_bounded(mma_bar, phase);
-        mbar_wait_bounded(stage_bar, sphase);
+        mbar_wait_bounded(mbar_addr, phase);  // give in-flight MMAs one more bounded chance to retire
     }
     fence_before();
     __syncthreads();
@@ -424,8 +371,7 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t need = (size_t)planes * plane_bytes(K, esize) + ((size_t)8 << (K + kRowBits)) +
-                        (sizeof(uint64_t) + sizeof(uint32_t)) * (1 << K) + 64 * sizeof(uint64_t) + 64 + 1024;
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
@@ -485,14 +431,8 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
         if (!((tmask >> q) & 1)) a.rpos[nr++] = q;
     uint64_t smask = tmask;
     for (int j = 0; j < tc::kRowBits; ++j) smask |= 1ull << a.rpos[j];
-    int loc[64];
     for (int q = 0; q < n; ++q)
-        if ((smask >> q) & 1) { loc[q] = a.nS; a.spos[a.nS++] = q; }
-    for (int j = 0; j < tc::kRowBits; ++j) a.rloc[j] = loc[a.rpos[j]];
-    for (int j = 0; j < k; ++j) a.tloc[j] = loc[targets[j]];
-    a.cbits = 0;
-    while (a.cbits < a.nS && a.spos[a.cbits] == a.cbits) ++a.cbits;  // >= 7: bits below the 7th non-target
-    if (a.cbits < tc::kRowBits || a.nS - a.cbits > 6) return cudaErrorInvalidValue;  // at most 64 chunks
+        if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
     switch (precision * 8 + k) {
         case QSIM_PREC_TF32X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
