@@ -335,6 +335,163 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     }
 }
 
+// BF16 variants: their A planes take half the TMEM columns of TF32, so TMEM holds two A buffers and one
+// accumulator. While the tensor cores run tile i from A[i&1], the warps split tile i+1 into A[(i+1)&1] and
+// load tile i+2; after MMA(i) retires, D is drained into registers, MMA(i+1) is issued at once, and tile i's
+// stores overlap it. The tensor cores idle only for the short drain of D.
+template <int K, int PREC, bool P0>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
+              unsigned* __restrict__ err) {
+    using C = Cfg<PREC>;
+    static_assert(C::esize == 2, "double-buffered A is for the BF16 precisions");
+    constexpr int D = 1 << K, NR = 2 * D;
+    constexpr int PB = plane_bytes(K, C::esize);
+    constexpr int ATOM = NR * 128;
+    constexpr int KSTEPS = NR * C::esize / 32;
+    constexpr int CPT = D / 4;
+    constexpr int ACOLS = NR / 2;                      // packed bf16 pairs
+    constexpr int ABUF = C::planes * ACOLS;            // TMEM columns of one A buffer
+    constexpr uint32_t TCOLS = pow2_at_least(NR + 2 * ABUF);
+    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
+    uint64_t* mbar = sCol + D;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3;
+    const int c0 = (warp >> 2) * CPT;
+    const int r = quad * 32 + lane;
+
+    for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
+    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+    const uint32_t mbar_addr = smem_u32(mbar);
+    const uint32_t sB = smem_u32(sb);
+    const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+
+    float2 X[CPT];
+    auto load_tile = [&](uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+        if constexpr (P0) {
+#pragma unroll
+            for (int j = 0; j < CPT; j += 2) {
+                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
+                X[j] = make_float2(v.x, v.y);
+                X[j + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
+        }
+    };
+    auto split_into = [&](uint32_t abuf) {
+        uint32_t p0[CPT], p1[CPT];
+        [[maybe_unused]] uint32_t p2[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const __nv_bfloat16 hr = __float2bfloat16_rn(X[j].x), hm = __float2bfloat16_rn(X[j].y);
+            const float rr = X[j].x - __bfloat162float(hr), ri = X[j].y - __bfloat162float(hm);
+            const __nv_bfloat16 mr = __float2bfloat16_rn(rr), mi = __float2bfloat16_rn(ri);
+            p0[j] = pack_bf16(hr, hm);
+            p1[j] = pack_bf16(mr, mi);
+            if constexpr (C::planes == 3) {
+                p2[j] = pack_bf16(__float2bfloat16_rn(rr - __bfloat162float(mr)),
+                                  __float2bfloat16_rn(ri - __bfloat162float(mi)));
+            }
+        }
+        tmem_st<CPT>(tbase + tlane + abuf + 0 * ACOLS + c0, p0);
+        tmem_st<CPT>(tbase + tlane + abuf + 1 * ACOLS + c0, p1);
+        if constexpr (C::planes == 3) tmem_st<CPT>(tbase + tlane + abuf + 2 * ACOLS + c0, p2);
+        wait_st();
+    };
+    auto issue = [&](uint32_t abuf) {  // thread 0 only
+        fence_after();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int pr = 0; pr < C::nprod; ++pr) {
+            const uint32_t acol = tbase + abuf + C::pa(pr) * ACOLS;
+            const uint32_t bpl = sB + C::pb(pr) * PB;
+#pragma unroll
+            for (int s = 0; s < KSTEPS; ++s) {
+                mma_ts<true>(tbase, acol + 8 * s, sdesc_sw128(bpl + (s >> 2) * ATOM + (s & 3) * 32), IDESC, acc);
+                acc = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(mbar_addr) : "memory");
+    };
+
+    const uint64_t t0 = blockIdx.x, G = gridDim.x;
+    const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
+    uint32_t phase = 0;
+    bool bad = false;
+    if (m > 0) {
+        load_tile(t0);
+        split_into(NR);
+        if (m > 1) load_tile(t0 + G);
+        fence_before();
+        __syncthreads();
+        if (tid == 0) issue(NR);
+    }
+    for (uint64_t i = 0; i < m; ++i) {
+        const uint32_t anext = NR + (uint32_t)((i + 1) & 1) * ABUF;
+        if (i + 1 < m) split_into(anext);          // A[(i+1)&1] was read by MMA(i-1), which has retired
+        if (i + 2 < m) load_tile(t0 + (i + 2) * G);
+        int to = 0;
+        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
+        if (__syncthreads_or(to)) { bad = true; break; }
+        phase ^= 1;
+        fence_after();
+        uint32_t v[2 * CPT];
+        tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
+        wait_ld();
+        fence_before();
+        __syncthreads();                            // D drained by every warp, A[(i+1)&1] written
+        if (i + 1 < m && tid == 0) issue(anext);
+        const uint64_t b = insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
+        if constexpr (P0) {
+#pragma unroll
+            for (int j = 0; j < CPT; j += 2)
+                *reinterpret_cast<float4*>(psi + b + sCol[c0 + j]) =
+                    make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
+    }
+    if (bad && tid == 0) {
+        atomicOr(err, DEVERR_TIMEOUT);
+        mbar_wait_bounded(mbar_addr, phase);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TCOLS) : "memory");
+    }
+}
+
 // B operand: Bt[n][kk] of the real form, Bt[2i][2c] = Re U_ic, Bt[2i][2c+1] = -Im U_ic, Bt[2i+1][2c] = Im U_ic,
 // Bt[2i+1][2c+1] = Re U_ic, split into planes and written in the swizzled shared-memory byte layout.
 template <int PREC>
@@ -378,11 +535,12 @@ size_t smem_bytes(int K, int planes, int esize) {
 template <int K, int PREC, bool P0>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_block<K, PREC, P0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = Cfg<PREC>::esize == 2 ? k_tc_block_a2<K, PREC == QSIM_PREC_TF32X3 ? QSIM_PREC_BF16X3 : PREC, P0>
+                                      : k_tc_block<K, PREC, P0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
-    k_tc_block<K, PREC, P0><<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a,
-                                                           reinterpret_cast<const uint4*>(dB), err);
+    kern<<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
     return cudaGetLastError();
 }
 
