@@ -151,6 +151,9 @@ struct Args {
     int spos[24];      // those bit positions, ascending (zeros inserted there to form a tile base)
     int rpos[kRowBits];// row bit j <-> index bit rpos[j]
     int tpos[8];       // column bit j <-> target j
+    int rloc[kRowBits];// row bit j <-> bit rloc[j] of the tile's natural order (position among spos)
+    int tloc[8];       // column bit j <-> bit tloc[j] of the tile's natural order
+    int cbits;         // the tile is 2^(nS - cbits) contiguous chunks of 2^cbits amplitudes (cbits >= 7)
     uint64_t ntiles;
 };
 
@@ -335,10 +338,18 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     }
 }
 
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
 // BF16 variants: their A planes take half the TMEM columns of TF32, so TMEM holds two A buffers and one
-// accumulator. While the tensor cores run tile i from A[i&1], the warps split tile i+1 into A[(i+1)&1] and
-// load tile i+2; after MMA(i) retires, D is drained into registers, MMA(i+1) is issued at once, and tile i's
-// stores overlap it. The tensor cores idle only for the short drain of D.
+// accumulator, and shared memory has room for a tile stage next to B. Per CTA and tile i:
+//   stage  <- tile i+3 by 1-D bulk copies of its contiguous chunks (>= 1 KiB; completion on an mbarrier)
+//   X      <- tile i+2 read from the stage into registers
+//   A[(i+1)&1] <- split of tile i+1 (tcgen05.st), while the tensor cores run tile i from A[i&1]
+// After MMA(i) retires, D is drained into registers, MMA(i+1) is issued at once, and tile i's stores
+// overlap it; the tensor cores idle only for the drain of D.
 template <int K, int PREC, bool P0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
@@ -353,24 +364,36 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     constexpr int ACOLS = NR / 2;                      // packed bf16 pairs
     constexpr int ABUF = C::planes * ACOLS;            // TMEM columns of one A buffer
     constexpr uint32_t TCOLS = pow2_at_least(NR + 2 * ABUF);
+    constexpr uint32_t TILE_BYTES = 8u << (K + kRowBits);
     constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
 
+    // shared memory: [B planes][tile stage][global column offsets][stage column offsets][chunk offsets][barriers]
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
-    uint64_t* mbar = sCol + D;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    float2* stage = reinterpret_cast<float2*>(sb + C::planes * PB);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB + TILE_BYTES);
+    uint32_t* sLoc = reinterpret_cast<uint32_t*>(sCol + D);
+    uint64_t* sChunk = reinterpret_cast<uint64_t*>(sLoc + D);
+    uint64_t* mbar = sChunk + 64;                      // [0]: MMA completion, [1]: stage filled
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
     const int c0 = (warp >> 2) * CPT;
     const int r = quad * 32 + lane;
+    const int nchunks = 1 << (a.nS - a.cbits);
+    const uint32_t chunk_bytes = 8u << a.cbits;
 
     for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
-    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    for (int c = tid; c < D; c += kThreads) {
+        sCol[c] = deposit((uint64_t)c, a.tpos, K);
+        sLoc[c] = (uint32_t)deposit((uint64_t)c, a.tloc, K);
+    }
+    for (int j = tid; j < nchunks; j += kThreads) sChunk[j] = deposit((uint64_t)j, a.spos + a.cbits, a.nS - a.cbits);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -384,23 +407,34 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     fence_after();
     const uint32_t tbase = *tslot;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint32_t mbar_addr = smem_u32(mbar);
-    const uint32_t sB = smem_u32(sb);
+    const uint32_t mma_bar = smem_u32(mbar), stage_bar = smem_u32(mbar + 1);
+    const uint32_t sB = smem_u32(sb), sStage = smem_u32(stage);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+    const uint32_t rowloc = (uint32_t)deposit((uint64_t)r, a.rloc, kRowBits);
 
+    auto fill_stage = [&](uint64_t t) {  // all threads call it after a barrier; warp 0 issues the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (warp == 0) {
+            const uint64_t b = insert_zeros(t, a.spos, a.nS);
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(stage_bar), "r"(TILE_BYTES) : "memory");
+            __syncwarp();
+            for (int j = lane; j < nchunks; j += 32)
+                bulk_g2s(sStage + (uint32_t)j * chunk_bytes, psi + b + sChunk[j], chunk_bytes, stage_bar);
+        }
+    };
     float2 X[CPT];
-    auto load_tile = [&](uint64_t t) {
-        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+    auto read_stage = [&]() {
         if constexpr (P0) {
 #pragma unroll
             for (int j = 0; j < CPT; j += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
+                const float4 v = *reinterpret_cast<const float4*>(stage + rowloc + sLoc[c0 + j]);
                 X[j] = make_float2(v.x, v.y);
                 X[j + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
+            for (int j = 0; j < CPT; ++j) X[j] = stage[rowloc + sLoc[c0 + j]];
         }
     };
     auto split_into = [&](uint32_t abuf) {
@@ -437,27 +471,43 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(mbar_addr) : "memory");
+                     :: "r"(mma_bar) : "memory");
     };
 
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
-    uint32_t phase = 0;
+    uint32_t phase = 0, sphase = 0;
     bool bad = false;
     if (m > 0) {
-        load_tile(t0);
-        split_into(NR);
-        if (m > 1) load_tile(t0 + G);
+        fill_stage(t0);
+        bool ok = mbar_wait_bounded(stage_bar, sphase);
+        sphase ^= 1;
+        if (ok) { read_stage(); split_into(NR); }
         fence_before();
-        __syncthreads();
-        if (tid == 0) issue(NR);
+        if (__syncthreads_or(!ok)) bad = true;
+        if (!bad) {
+            if (tid == 0) issue(NR);
+            if (m > 1) {
+                fill_stage(t0 + G);
+                ok = mbar_wait_bounded(stage_bar, sphase);
+                sphase ^= 1;
+                if (ok) read_stage();
+                if (__syncthreads_or(!ok)) bad = true;
+                else if (m > 2) fill_stage(t0 + 2 * G);
+            }
+        }
     }
-    for (uint64_t i = 0; i < m; ++i) {
+    for (uint64_t i = 0; !bad && i < m; ++i) {
         const uint32_t anext = NR + (uint32_t)((i + 1) & 1) * ABUF;
         if (i + 1 < m) split_into(anext);          // A[(i+1)&1] was read by MMA(i-1), which has retired
-        if (i + 2 < m) load_tile(t0 + (i + 2) * G);
-        int to = 0;
-        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
+        bool ok = true;
+        if (i + 2 < m) {
+            ok = mbar_wait_bounded(stage_bar, sphase);
+            sphase ^= 1;
+            if (ok) read_stage();
+        }
+        int to = !ok;
+        if (tid == 0 && !mbar_wait_bounded(mma_bar, phase)) to = 1;
         if (__syncthreads_or(to)) { bad = true; break; }
         phase ^= 1;
         fence_after();
@@ -465,8 +515,9 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
         wait_ld();
         fence_before();
-        __syncthreads();                            // D drained by every warp, A[(i+1)&1] written
+        __syncthreads();                            // D drained, A[(i+1)&1] written, stage read by every warp
         if (i + 1 < m && tid == 0) issue(anext);
+        if (i + 3 < m) fill_stage(t0 + (i + 3) * G);
         const uint64_t b = insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
         if constexpr (P0) {
 #pragma unroll
@@ -482,7 +533,9 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     }
     if (bad && tid == 0) {
         atomicOr(err, DEVERR_TIMEOUT);
-        mbar_wait_bounded(mbar_addr, phase);
+        // let in-flight MMAs and bulk copies retire (bounded) before TMEM and shared memory are released
+        mbar_wait_bounded(mma_bar, phase);
+        mbar_wait_bounded(stage_bar, sphase);
     }
     fence_before();
     __syncthreads();
@@ -528,7 +581,8 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;
+    const size_t stage = esize == 2 ? ((size_t)8 << (K + kRowBits)) + sizeof(uint32_t) * (1 << K) + 64 * 8 : 0;
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + stage + sizeof(uint64_t) * (1 << K) + 64 + 1024;
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
@@ -589,8 +643,14 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
         if (!((tmask >> q) & 1)) a.rpos[nr++] = q;
     uint64_t smask = tmask;
     for (int j = 0; j < tc::kRowBits; ++j) smask |= 1ull << a.rpos[j];
+    int loc[64];
     for (int q = 0; q < n; ++q)
-        if ((smask >> q) & 1) a.spos[a.nS++] = q;
+        if ((smask >> q) & 1) { loc[q] = a.nS; a.spos[a.nS++] = q; }
+    for (int j = 0; j < tc::kRowBits; ++j) a.rloc[j] = loc[a.rpos[j]];
+    for (int j = 0; j < k; ++j) a.tloc[j] = loc[targets[j]];
+    a.cbits = 0;
+    while (a.cbits < a.nS && a.spos[a.cbits] == a.cbits) ++a.cbits;  // >= 7: bits below the 7th non-target
+    if (a.cbits < tc::kRowBits || a.nS - a.cbits > 6) return cudaErrorInvalidValue;  // at most 64 chunks
     a.ntiles = 1ull << (n - a.nS);
     switch (precision * 8 + k) {
         case QSIM_PREC_TF32X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
