@@ -338,18 +338,22 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     }
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(dst), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
 // BF16 variants: their A planes take half the TMEM columns of TF32, so TMEM holds two A buffers and one
-// accumulator, and shared memory has room for a tile stage next to B. Per CTA and tile i:
-//   stage  <- tile i+3 by 1-D bulk copies of its contiguous chunks (>= 1 KiB; completion on an mbarrier)
-//   X      <- tile i+2 read from the stage into registers
-//   A[(i+1)&1] <- split of tile i+1 (tcgen05.st), while the tensor cores run tile i from A[i&1]
-// After MMA(i) retires, D is drained into registers, MMA(i+1) is issued at once, and tile i's stores
-// overlap it; the tensor cores idle only for the drain of D.
+// accumulator, and shared memory has room for a two-tile ring next to B. Every thread streams exactly the
+// elements it will split (row r, columns c0..c0+CPT) with asynchronous copies into its own interleaved slots
+// of the ring (no barrier is needed to consume them), so two tiles of loads are always in flight.
+// Per CTA and tile i:  ring <- tile i+3 | A[(i+1)&1] <- split of tile i+1 (ring) while the tensor cores run
+// tile i from A[i&1] | after MMA(i) retires: drain D into registers, issue MMA(i+1), store tile i.
 template <int K, int PREC, bool P0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
@@ -364,36 +368,28 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     constexpr int ACOLS = NR / 2;                      // packed bf16 pairs
     constexpr int ABUF = C::planes * ACOLS;            // TMEM columns of one A buffer
     constexpr uint32_t TCOLS = pow2_at_least(NR + 2 * ABUF);
-    constexpr uint32_t TILE_BYTES = 8u << (K + kRowBits);
+    constexpr uint32_t SLOT = 8u * kThreads;           // bytes of one element index across all threads
+    constexpr uint32_t STAGE = SLOT * CPT;             // one tile (= 8 << (K + 7) bytes)
     constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
 
-    // shared memory: [B planes][tile stage][global column offsets][stage column offsets][chunk offsets][barriers]
+    // shared memory: [B planes][ring: 2 stages][global column offsets][barrier][TMEM slot]
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float2* stage = reinterpret_cast<float2*>(sb + C::planes * PB);
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB + TILE_BYTES);
-    uint32_t* sLoc = reinterpret_cast<uint32_t*>(sCol + D);
-    uint64_t* sChunk = reinterpret_cast<uint64_t*>(sLoc + D);
-    uint64_t* mbar = sChunk + 64;                      // [0]: MMA completion, [1]: stage filled
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    unsigned char* ring = sb + C::planes * PB;
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(ring + 2 * STAGE);
+    uint64_t* mbar = sCol + D;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
     const int c0 = (warp >> 2) * CPT;
     const int r = quad * 32 + lane;
-    const int nchunks = 1 << (a.nS - a.cbits);
-    const uint32_t chunk_bytes = 8u << a.cbits;
 
     for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
-    for (int c = tid; c < D; c += kThreads) {
-        sCol[c] = deposit((uint64_t)c, a.tpos, K);
-        sLoc[c] = (uint32_t)deposit((uint64_t)c, a.tloc, K);
-    }
-    for (int j = tid; j < nchunks; j += kThreads) sChunk[j] = deposit((uint64_t)j, a.spos + a.cbits, a.nS - a.cbits);
+    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -407,37 +403,41 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     fence_after();
     const uint32_t tbase = *tslot;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint32_t mma_bar = smem_u32(mbar), stage_bar = smem_u32(mbar + 1);
-    const uint32_t sB = smem_u32(sb), sStage = smem_u32(stage);
+    const uint32_t mma_bar = smem_u32(mbar);
+    const uint32_t sB = smem_u32(sb), sRing = smem_u32(ring);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
-    const uint32_t rowloc = (uint32_t)deposit((uint64_t)r, a.rloc, kRowBits);
+    uint64_t col[CPT];  // this thread's column offsets (fixed for the launch)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) col[j] = sCol[c0 + j];
 
-    auto fill_stage = [&](uint64_t t) {  // all threads call it after a barrier; warp 0 issues the copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (warp == 0) {
-            const uint64_t b = insert_zeros(t, a.spos, a.nS);
-            if (lane == 0)
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(stage_bar), "r"(TILE_BYTES) : "memory");
-            __syncwarp();
-            for (int j = lane; j < nchunks; j += 32)
-                bulk_g2s(sStage + (uint32_t)j * chunk_bytes, psi + b + sChunk[j], chunk_bytes, stage_bar);
-        }
-    };
-    float2 X[CPT];
-    auto read_stage = [&]() {
+    // Element j of this thread lives at ring + stage * STAGE + j * SLOT + 8 * tid (16-byte pairs with P0:
+    // pair q at + q * 2 * SLOT + 16 * tid): consecutive lanes touch consecutive words, no bank conflicts.
+    auto fetch = [&](uint64_t t, int st) {
+        const float2* src = psi + insert_zeros(t, a.spos, a.nS) + rowoff;
+        const uint32_t dst = sRing + (uint32_t)st * STAGE;
         if constexpr (P0) {
 #pragma unroll
-            for (int j = 0; j < CPT; j += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(stage + rowloc + sLoc[c0 + j]);
-                X[j] = make_float2(v.x, v.y);
-                X[j + 1] = make_float2(v.z, v.w);
+            for (int q = 0; q < CPT / 2; ++q) cp_async16(dst + q * 2 * SLOT + 16 * tid, src + col[2 * q]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) cp_async8(dst + j * SLOT + 8 * tid, src + col[j]);
+        }
+        cp_async_commit();
+    };
+    auto split_into = [&](int st, uint32_t abuf) {
+        const unsigned char* src = ring + (uint32_t)st * STAGE;
+        float2 X[CPT];
+        if constexpr (P0) {
+#pragma unroll
+            for (int q = 0; q < CPT / 2; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(src + q * 2 * SLOT + 16 * tid);
+                X[2 * q] = make_float2(v.x, v.y);
+                X[2 * q + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = stage[rowloc + sLoc[c0 + j]];
+            for (int j = 0; j < CPT; ++j) X[j] = *reinterpret_cast<const float2*>(src + j * SLOT + 8 * tid);
         }
-    };
-    auto split_into = [&](uint32_t abuf) {
         uint32_t p0[CPT], p1[CPT];
         [[maybe_unused]] uint32_t p2[CPT];
 #pragma unroll
@@ -476,38 +476,27 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
 
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
-    uint32_t phase = 0, sphase = 0;
+    uint32_t phase = 0;
     bool bad = false;
     if (m > 0) {
-        fill_stage(t0);
-        bool ok = mbar_wait_bounded(stage_bar, sphase);
-        sphase ^= 1;
-        if (ok) { read_stage(); split_into(NR); }
+        fetch(t0, 0);
+        if (m > 1) { fetch(t0 + G, 1); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
+        split_into(0, NR);
+        if (m > 2) fetch(t0 + 2 * G, 0);  // own slots only: this thread's reads of stage 0 are done
         fence_before();
-        if (__syncthreads_or(!ok)) bad = true;
-        if (!bad) {
-            if (tid == 0) issue(NR);
-            if (m > 1) {
-                fill_stage(t0 + G);
-                ok = mbar_wait_bounded(stage_bar, sphase);
-                sphase ^= 1;
-                if (ok) read_stage();
-                if (__syncthreads_or(!ok)) bad = true;
-                else if (m > 2) fill_stage(t0 + 2 * G);
-            }
-        }
+        __syncthreads();
+        if (tid == 0) issue(NR);
     }
-    for (uint64_t i = 0; !bad && i < m; ++i) {
+    for (uint64_t i = 0; i < m; ++i) {
         const uint32_t anext = NR + (uint32_t)((i + 1) & 1) * ABUF;
-        if (i + 1 < m) split_into(anext);          // A[(i+1)&1] was read by MMA(i-1), which has retired
-        bool ok = true;
-        if (i + 2 < m) {
-            ok = mbar_wait_bounded(stage_bar, sphase);
-            sphase ^= 1;
-            if (ok) read_stage();
+        if (i + 1 < m) {
+            // tile i+1 sits in stage (i+1)&1; tile i+2 (if any) may still be in flight
+            if (i + 2 < m) cp_async_wait<1>(); else cp_async_wait<0>();
+            split_into((int)((i + 1) & 1), anext);   // A[(i+1)&1] was read by MMA(i-1), which has retired
+            if (i + 3 < m) fetch(t0 + (i + 3) * G, (int)((i + 1) & 1));
         }
-        int to = !ok;
-        if (tid == 0 && !mbar_wait_bounded(mma_bar, phase)) to = 1;
+        int to = 0;
+        if (tid == 0) to = !mbar_wait_bounded(mma_bar, phase);
         if (__syncthreads_or(to)) { bad = true; break; }
         phase ^= 1;
         fence_after();
@@ -515,27 +504,25 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
         wait_ld();
         fence_before();
-        __syncthreads();                            // D drained, A[(i+1)&1] written, stage read by every warp
+        __syncthreads();                            // D drained and A[(i+1)&1] written by every warp
         if (i + 1 < m && tid == 0) issue(anext);
-        if (i + 3 < m) fill_stage(t0 + (i + 3) * G);
-        const uint64_t b = insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
+        float2* dst = psi + insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
         if constexpr (P0) {
 #pragma unroll
             for (int j = 0; j < CPT; j += 2)
-                *reinterpret_cast<float4*>(psi + b + sCol[c0 + j]) =
+                *reinterpret_cast<float4*>(dst + col[j]) =
                     make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                 __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
         } else {
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
-                psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                dst[col[j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
         }
     }
+    cp_async_wait<0>();  // no asynchronous copy may outlive the CTA's shared memory
     if (bad && tid == 0) {
         atomicOr(err, DEVERR_TIMEOUT);
-        // let in-flight MMAs and bulk copies retire (bounded) before TMEM and shared memory are released
-        mbar_wait_bounded(mma_bar, phase);
-        mbar_wait_bounded(stage_bar, sphase);
+        mbar_wait_bounded(mma_bar, phase);  // let in-flight MMAs retire (bounded) before TMEM is released
     }
     fence_before();
     __syncthreads();
@@ -581,7 +568,7 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t stage = esize == 2 ? ((size_t)8 << (K + kRowBits)) + sizeof(uint32_t) * (1 << K) + 64 * 8 : 0;
+    const size_t stage = esize == 2 ? ((size_t)16 << (K + kRowBits)) : 0;  // two-tile ring of the BF16 kernels
     const size_t need = (size_t)planes * plane_bytes(K, esize) + stage + sizeof(uint64_t) * (1 << K) + 64 + 1024;
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
