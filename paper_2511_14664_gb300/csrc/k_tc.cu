@@ -108,9 +108,16 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// Rounding of finite floats with integer ALU operations (the conversion instructions run on the much
+// narrower XU pipe). TF32, round to nearest with ties away from zero: add half a TF32 ulp to the magnitude
+// bits and clear the 13 dropped bits. BF16, round to nearest even: add 0x7FFF plus the lowest kept bit.
+__device__ __forceinline__ uint32_t tf32_rna_alu(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
 }
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t h) { return __uint_as_float(h << 16); }
+__device__ __forceinline__ uint32_t pack2(uint32_t lo16, uint32_t hi16) { return __byte_perm(lo16, hi16, 0x5410); }
 
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -265,10 +272,12 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
             uint32_t hi[AV], lo[AV];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                hi[2 * j] = tf32_rna(X[j].x);
-                hi[2 * j + 1] = tf32_rna(X[j].y);
-                lo[2 * j] = tf32_rna(X[j].x - __uint_as_float(hi[2 * j]));
-                lo[2 * j + 1] = tf32_rna(X[j].y - __uint_as_float(hi[2 * j + 1]));
+                // the residual is rounded to TF32 here: left to the tensor core, its low bits would be
+                // truncated towards zero
+                hi[2 * j] = tf32_rna_alu(X[j].x);
+                hi[2 * j + 1] = tf32_rna_alu(X[j].y);
+                lo[2 * j] = tf32_rna_alu(X[j].x - __uint_as_float(hi[2 * j]));
+                lo[2 * j + 1] = tf32_rna_alu(X[j].y - __uint_as_float(hi[2 * j + 1]));
             }
             tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + 2 * c0, hi);
             tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + 2 * c0, lo);
@@ -277,15 +286,13 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
             [[maybe_unused]] uint32_t p2[AV];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                const __nv_bfloat16 hr = __float2bfloat16_rn(X[j].x), hm = __float2bfloat16_rn(X[j].y);
-                const float rr = X[j].x - __bfloat162float(hr), ri = X[j].y - __bfloat162float(hm);
-                const __nv_bfloat16 mr = __float2bfloat16_rn(rr), mi = __float2bfloat16_rn(ri);
-                p0[j] = pack_bf16(hr, hm);
-                p1[j] = pack_bf16(mr, mi);
-                if constexpr (C::planes == 3) {
-                    p2[j] = pack_bf16(__float2bfloat16_rn(rr - __bfloat162float(mr)),
-                                      __float2bfloat16_rn(ri - __bfloat162float(mi)));
-                }
+                const uint32_t hr = bf16_rne_bits(X[j].x), hm = bf16_rne_bits(X[j].y);
+                const float rr = X[j].x - bf16_bits_to_float(hr), ri = X[j].y - bf16_bits_to_float(hm);
+                const uint32_t mr = bf16_rne_bits(rr), mi = bf16_rne_bits(ri);
+                p0[j] = pack2(hr, hm);
+                p1[j] = pack2(mr, mi);
+                if constexpr (C::planes == 3)
+                    p2[j] = pack2(bf16_rne_bits(rr - bf16_bits_to_float(mr)), bf16_rne_bits(ri - bf16_bits_to_float(mi)));
             }
             tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + c0, p0);
             tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + c0, p1);
@@ -406,9 +413,11 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     const uint32_t mma_bar = smem_u32(mbar);
     const uint32_t sB = smem_u32(sb), sRing = smem_u32(ring);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
-    uint64_t col[CPT];  // this thread's column offsets (fixed for the launch)
+    // this thread's column offsets (fixed for the launch); with P0 only the even columns are needed
+    constexpr int NCOL = P0 ? CPT / 2 : CPT;
+    uint64_t col[NCOL];
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) col[j] = sCol[c0 + j];
+    for (int j = 0; j < NCOL; ++j) col[j] = sCol[c0 + (P0 ? 2 * j : j)];
 
     // Element j of this thread lives at ring + stage * STAGE + j * SLOT + 8 * tid (16-byte pairs with P0:
     // pair q at + q * 2 * SLOT + 16 * tid): consecutive lanes touch consecutive words, no bank conflicts.
@@ -417,7 +426,7 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         const uint32_t dst = sRing + (uint32_t)st * STAGE;
         if constexpr (P0) {
 #pragma unroll
-            for (int q = 0; q < CPT / 2; ++q) cp_async16(dst + q * 2 * SLOT + 16 * tid, src + col[2 * q]);
+            for (int q = 0; q < CPT / 2; ++q) cp_async16(dst + q * 2 * SLOT + 16 * tid, src + col[q]);
         } else {
 #pragma unroll
             for (int j = 0; j < CPT; ++j) cp_async8(dst + j * SLOT + 8 * tid, src + col[j]);
@@ -442,15 +451,13 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         [[maybe_unused]] uint32_t p2[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-            const __nv_bfloat16 hr = __float2bfloat16_rn(X[j].x), hm = __float2bfloat16_rn(X[j].y);
-            const float rr = X[j].x - __bfloat162float(hr), ri = X[j].y - __bfloat162float(hm);
-            const __nv_bfloat16 mr = __float2bfloat16_rn(rr), mi = __float2bfloat16_rn(ri);
-            p0[j] = pack_bf16(hr, hm);
-            p1[j] = pack_bf16(mr, mi);
-            if constexpr (C::planes == 3) {
-                p2[j] = pack_bf16(__float2bfloat16_rn(rr - __bfloat162float(mr)),
-                                  __float2bfloat16_rn(ri - __bfloat162float(mi)));
-            }
+            const uint32_t hr = bf16_rne_bits(X[j].x), hm = bf16_rne_bits(X[j].y);
+            const float rr = X[j].x - bf16_bits_to_float(hr), ri = X[j].y - bf16_bits_to_float(hm);
+            const uint32_t mr = bf16_rne_bits(rr), mi = bf16_rne_bits(ri);
+            p0[j] = pack2(hr, hm);
+            p1[j] = pack2(mr, mi);
+            if constexpr (C::planes == 3)
+                p2[j] = pack2(bf16_rne_bits(rr - bf16_bits_to_float(mr)), bf16_rne_bits(ri - bf16_bits_to_float(mi)));
         }
         tmem_st<CPT>(tbase + tlane + abuf + 0 * ACOLS + c0, p0);
         tmem_st<CPT>(tbase + tlane + abuf + 1 * ACOLS + c0, p1);
@@ -510,7 +517,7 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         if constexpr (P0) {
 #pragma unroll
             for (int j = 0; j < CPT; j += 2)
-                *reinterpret_cast<float4*>(dst + col[j]) =
+                *reinterpret_cast<float4*>(dst + col[j / 2]) =
                     make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                 __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
         } else {
