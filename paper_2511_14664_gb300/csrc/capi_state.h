@@ -39,6 +39,12 @@ std::vector<int> nonunit_patterns(const double* diag, int k);
 int check_device_error(qsim_state* h);
 int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* controls, int nc, const double* m);
 
+// Greedy fusion (plan.cu): starting from the earliest unplaced gate, collect every later gate that is not
+// blocked by an earlier unplaced gate on a shared qubit (diagonal gates are blocked only by non-diagonal
+// ones) and keeps the block within kmax qubits. gmask[i] = qubits of gate i (targets and controls).
+std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
+                                          int kmax);
+
 }  // namespace qsim
 
 extern "C" int qsim_synchronize(qsim_h h);

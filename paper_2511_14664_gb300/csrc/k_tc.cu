@@ -345,22 +345,10 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     }
 }
 
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
-
 // BF16 variants: their A planes take half the TMEM columns of TF32, so TMEM holds two A buffers and one
-// accumulator, and shared memory has room for a two-tile ring next to B. Every thread streams exactly the
-// elements it will split (row r, columns c0..c0+CPT) with asynchronous copies into its own interleaved slots
-// of the ring (no barrier is needed to consume them), so two tiles of loads are always in flight.
-// Per CTA and tile i:  ring <- tile i+3 | A[(i+1)&1] <- split of tile i+1 (ring) while the tensor cores run
-// tile i from A[i&1] | after MMA(i) retires: drain D into registers, issue MMA(i+1), store tile i.
+// accumulator. While the tensor cores run tile i from A[i&1], the warps split tile i+1 into A[(i+1)&1] and
+// load tile i+2; after MMA(i) retires, D is drained into registers, MMA(i+1) is issued at once, and tile i's
+// stores overlap it. The tensor cores idle only for the short drain of D.
 template <int K, int PREC, bool P0>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
@@ -375,16 +363,12 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     constexpr int ACOLS = NR / 2;                      // packed bf16 pairs
     constexpr int ABUF = C::planes * ACOLS;            // TMEM columns of one A buffer
     constexpr uint32_t TCOLS = pow2_at_least(NR + 2 * ABUF);
-    constexpr uint32_t SLOT = 8u * kThreads;           // bytes of one element index across all threads
-    constexpr uint32_t STAGE = SLOT * CPT;             // one tile (= 8 << (K + 7) bytes)
     constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
 
-    // shared memory: [B planes][ring: 2 stages][global column offsets][barrier][TMEM slot]
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* ring = sb + C::planes * PB;
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(ring + 2 * STAGE);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
     uint64_t* mbar = sCol + D;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
@@ -410,43 +394,26 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     fence_after();
     const uint32_t tbase = *tslot;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint32_t mma_bar = smem_u32(mbar);
-    const uint32_t sB = smem_u32(sb), sRing = smem_u32(ring);
+    const uint32_t mbar_addr = smem_u32(mbar);
+    const uint32_t sB = smem_u32(sb);
     const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
-    // this thread's column offsets (fixed for the launch); with P0 only the even columns are needed
-    constexpr int NCOL = P0 ? CPT / 2 : CPT;
-    uint64_t col[NCOL];
-#pragma unroll
-    for (int j = 0; j < NCOL; ++j) col[j] = sCol[c0 + (P0 ? 2 * j : j)];
 
-    // Element j of this thread lives at ring + stage * STAGE + j * SLOT + 8 * tid (16-byte pairs with P0:
-    // pair q at + q * 2 * SLOT + 16 * tid): consecutive lanes touch consecutive words, no bank conflicts.
-    auto fetch = [&](uint64_t t, int st) {
-        const float2* src = psi + insert_zeros(t, a.spos, a.nS) + rowoff;
-        const uint32_t dst = sRing + (uint32_t)st * STAGE;
+    float2 X[CPT];
+    auto load_tile = [&](uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
         if constexpr (P0) {
 #pragma unroll
-            for (int q = 0; q < CPT / 2; ++q) cp_async16(dst + q * 2 * SLOT + 16 * tid, src + col[q]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) cp_async8(dst + j * SLOT + 8 * tid, src + col[j]);
-        }
-        cp_async_commit();
-    };
-    auto split_into = [&](int st, uint32_t abuf) {
-        const unsigned char* src = ring + (uint32_t)st * STAGE;
-        float2 X[CPT];
-        if constexpr (P0) {
-#pragma unroll
-            for (int q = 0; q < CPT / 2; ++q) {
-                const float4 v = *reinterpret_cast<const float4*>(src + q * 2 * SLOT + 16 * tid);
-                X[2 * q] = make_float2(v.x, v.y);
-                X[2 * q + 1] = make_float2(v.z, v.w);
+            for (int j = 0; j < CPT; j += 2) {
+                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
+                X[j] = make_float2(v.x, v.y);
+                X[j + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = *reinterpret_cast<const float2*>(src + j * SLOT + 8 * tid);
+            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
         }
+    };
+    auto split_into = [&](uint32_t abuf) {
         uint32_t p0[CPT], p1[CPT];
         [[maybe_unused]] uint32_t p2[CPT];
 #pragma unroll
@@ -478,7 +445,7 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
             }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(mma_bar) : "memory");
+                     :: "r"(mbar_addr) : "memory");
     };
 
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
@@ -486,24 +453,19 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
     uint32_t phase = 0;
     bool bad = false;
     if (m > 0) {
-        fetch(t0, 0);
-        if (m > 1) { fetch(t0 + G, 1); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
-        split_into(0, NR);
-        if (m > 2) fetch(t0 + 2 * G, 0);  // own slots only: this thread's reads of stage 0 are done
+        load_tile(t0);
+        split_into(NR);
+        if (m > 1) load_tile(t0 + G);
         fence_before();
         __syncthreads();
         if (tid == 0) issue(NR);
     }
     for (uint64_t i = 0; i < m; ++i) {
         const uint32_t anext = NR + (uint32_t)((i + 1) & 1) * ABUF;
-        if (i + 1 < m) {
-            // tile i+1 sits in stage (i+1)&1; tile i+2 (if any) may still be in flight
-            if (i + 2 < m) cp_async_wait<1>(); else cp_async_wait<0>();
-            split_into((int)((i + 1) & 1), anext);   // A[(i+1)&1] was read by MMA(i-1), which has retired
-            if (i + 3 < m) fetch(t0 + (i + 3) * G, (int)((i + 1) & 1));
-        }
+        if (i + 1 < m) split_into(anext);          // A[(i+1)&1] was read by MMA(i-1), which has retired
+        if (i + 2 < m) load_tile(t0 + (i + 2) * G);
         int to = 0;
-        if (tid == 0) to = !mbar_wait_bounded(mma_bar, phase);
+        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
         if (__syncthreads_or(to)) { bad = true; break; }
         phase ^= 1;
         fence_after();
@@ -511,25 +473,24 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
         tmem_ld<2 * CPT>(tbase + tlane + 2 * c0, v);
         wait_ld();
         fence_before();
-        __syncthreads();                            // D drained and A[(i+1)&1] written by every warp
+        __syncthreads();                            // D drained by every warp, A[(i+1)&1] written
         if (i + 1 < m && tid == 0) issue(anext);
-        float2* dst = psi + insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
+        const uint64_t b = insert_zeros(t0 + i * G, a.spos, a.nS) + rowoff;
         if constexpr (P0) {
 #pragma unroll
             for (int j = 0; j < CPT; j += 2)
-                *reinterpret_cast<float4*>(dst + col[j / 2]) =
+                *reinterpret_cast<float4*>(psi + b + sCol[c0 + j]) =
                     make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                 __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
         } else {
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
-                dst[col[j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
         }
     }
-    cp_async_wait<0>();  // no asynchronous copy may outlive the CTA's shared memory
     if (bad && tid == 0) {
         atomicOr(err, DEVERR_TIMEOUT);
-        mbar_wait_bounded(mma_bar, phase);  // let in-flight MMAs retire (bounded) before TMEM is released
+        mbar_wait_bounded(mbar_addr, phase);
     }
     fence_before();
     __syncthreads();
@@ -575,8 +536,7 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t stage = esize == 2 ? ((size_t)16 << (K + kRowBits)) : 0;  // two-tile ring of the BF16 kernels
-    const size_t need = (size_t)planes * plane_bytes(K, esize) + stage + sizeof(uint64_t) * (1 << K) + 64 + 1024;
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 

@@ -55,6 +55,41 @@ namespace qsim {
 
 static inline int popcnt(uint64_t v) { return __builtin_popcountll(v); }
 
+std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
+                                          int kmax) {
+    const int G = (int)gmask.size();
+    std::vector<std::vector<int>> blocks;
+    std::vector<char> done(G, 0);
+    int first = 0;
+    while (true) {
+        while (first < G && done[first]) ++first;
+        if (first >= G) break;
+        uint64_t Q = 0, bany = 0, bdiag = 0;
+        std::vector<int> blk;
+        for (int i = first; i < G; ++i) {
+            if (done[i]) continue;
+            const uint64_t qs = gmask[i];
+            const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
+            if (!blocked && popcnt(Q | qs) <= kmax) {
+                blk.push_back(i);
+                done[i] = 1;
+                Q |= qs;
+            } else if (blk.empty()) {  // wider than the fusion width: a block of its own
+                blk.push_back(i);
+                done[i] = 1;
+                break;
+            } else if (gdiag[i]) {
+                bdiag |= qs;
+            } else {
+                bany |= qs;
+            }
+            if (popcnt(bany) == n) break;
+        }
+        blocks.push_back(std::move(blk));
+    }
+    return blocks;
+}
+
 static double op_bytes(const PlanOp& op, int n, size_t amp) {
     const double groups = std::ldexp(1.0, n - op.k - op.nc);
     if (op.kind == OP_DIAG) return 2.0 * amp * groups * (double)op.touch.size();
@@ -146,34 +181,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        std::vector<char> done(G, 0);
-        int first = 0;
-        while (true) {
-            while (first < G && done[first]) ++first;
-            if (first >= G) break;
-            uint64_t Q = 0, bany = 0, bdiag = 0;
-            std::vector<int> blk;
-            for (int i = first; i < G; ++i) {
-                if (done[i]) continue;
-                const uint64_t qs = gmask[i];
-                const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
-                if (!blocked && popcnt(Q | qs) <= kmax) {
-                    blk.push_back(i);
-                    done[i] = 1;
-                    Q |= qs;
-                } else if (blk.empty()) {  // wider than the fusion width: a block of its own
-                    blk.push_back(i);
-                    done[i] = 1;
-                    break;
-                } else if (gdiag[i]) {
-                    bdiag |= qs;
-                } else {
-                    bany |= qs;
-                }
-                if (popcnt(bany) == n) break;
-            }
-            blocks.push_back(std::move(blk));
-        }
+        blocks = group_gates(gmask, gdiag, n, kmax);
     }
 
     // ---- decide each block's pass and lay out the device buffer --------------------------------------------
