@@ -256,16 +256,38 @@ int qsim_inner(qsim_h a, qsim_h b, double* out);
 /* ---- batches of independent circuits (one persistent launch) ---------------------------------------- */
 
 /*
- * Simulate `count` independent circuits (widths may differ; each n in 1..26, complex64) from |0...0>
- * and return, for circuit i, <Z_q> at zi[zi_off[i] + q] (q < n_i) and <Z_q Z_{q+1}> at
- * zz[zz_off[i] + q] (q < n_i - 1), where zi_off / zz_off are the running sums of n_i and n_i - 1.
- * Each circuit is fused with its own width k (0 in opts->max_fused = chosen per circuit by the
- * built-in tuner). States live in `dev_ws` (device, at least qsim_batch_workspace_bytes bytes). All
- * circuits run in one persistent kernel launch whose work queue is consumed with bounded waits.
+ * Many independent circuits in one launch (Sec. 1: many circuits, e.g. for iterative algorithms, are one
+ * reason to need large GPU resources). Every circuit starts from |0...0> (complex64); widths 1..26, gates on
+ * at most 4 qubits (targets plus controls). Each circuit is fused with width k (opts->max_fused; 0 = the
+ * width chosen for its qubit count by qsim_batch_autotune, default 4), composed in FP64 on the device, and
+ * run by one persistent launch of thread-block clusters: a cluster per circuit of more than 13 qubits (its
+ * state in the caller's workspace, passes separated by cluster barriers), then one CTA per smaller circuit
+ * with the whole state in shared memory. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
+ * <Z_q Z_{q+1}> at zz[zz_off(i) + q] (q < n_i - 1), the offsets being the running sums of n_i and n_i - 1
+ * in input order; sums are compensated (float-float per thread, double-double across threads).
  */
+typedef struct qsim_batch* qsim_batch_h;
+/* Device workspace (bytes) the circuits of more than 13 qubits need: sum of 2^n x 8 B, 256-byte aligned. */
 int qsim_batch_workspace_bytes(const qsim_circuit* cs, int count, size_t* out);
+/* Plan (fusion, FP64 composition on `stream`); the plan owns its device buffers. info may be NULL. */
+int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* stream,
+                           qsim_batch_h* out, qsim_plan_info* info);
+/* Enqueue the batch on `stream` (asynchronous). dev_ws: device workspace of at least the bytes above,
+   256-byte aligned, owned by the caller. use_graph = 1 replays a CUDA graph captured on first use. */
+int qsim_batch_execute(qsim_batch_h b, void* dev_ws, size_t ws_bytes, void* stream, int use_graph);
+/* Copy the last execution's <Z> values to host arrays zi, zz (see above for the layout). Synchronises. */
+int qsim_batch_results(qsim_batch_h b, void* stream, double* zi, double* zz);
+int qsim_batch_destroy(qsim_batch_h b);
+/* Plan, execute, fetch results and destroy in one call. */
 int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws,
                    size_t ws_bytes, void* stream, double* zi, double* zz, qsim_plan_info* info);
+/*
+ * Fusion-width tuner: for every width present in cs, time k = 1..4 on the first circuit of that width
+ * (median of three launches after a warm-up; a trial workspace is allocated and released here) and keep
+ * the fastest for later plans made with max_fused = 0 (process-wide). chosen (may be NULL) receives the k
+ * each circuit would now get.
+ */
+int qsim_batch_autotune(const qsim_circuit* cs, int count, void* stream, int* chosen);
 
 #ifdef __cplusplus
 }

@@ -1,17 +1,663 @@
-// batch.cu -- many independent circuits in one persistent launch (placeholder until the kernel lands).
+// batch.cu -- many independent circuits in one persistent launch (paper Sec. 1: simulating many circuits,
+// e.g. for iterative algorithms, is one reason for large GPU resources; Sec. 2.2 times circuits one by one).
+//
+// Each circuit is fused on the host (greedy, width k chosen per circuit width by a built-in tuner or given),
+// every block is composed in FP64 on the device and stored as a complex64 matrix. One launch of k_batch then
+// runs everything:
+//   * a persistent grid of thread-block clusters (8 CTAs); each cluster claims the next large circuit
+//     (n >= 14) from a device counter, keeps its state in the caller's workspace, applies the passes with
+//     hardware cluster barriers between them, and reduces <Z_i>, <Z_i Z_{i+1}> across the cluster through
+//     distributed shared memory;
+//   * once the large queue is empty, every CTA claims small circuits (n <= 13) one at a time and runs each
+//     entirely in its shared memory (64 KiB), with no global traffic for the state at all.
+// There are no spin waits: the only waits are hardware barriers (__syncthreads, cluster barriers).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
 #include "capi_state.h"
+#include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qsim {
+namespace batch {
+
+constexpr int kCluster = 8;
+constexpr int kThreads = 256;
+constexpr int kKmax = 4;
+constexpr int kSmallMax = 13;  // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
+
+struct Pass {
+    int k;
+    int targets[kKmax];  // ascending; bit j of the matrix index <-> targets[j]
+    int64_t mat_off;     // complex entries into the matrix pool
+};
+struct Circ {
+    int n;
+    int npass;
+    int64_t first_pass;
+    int64_t state_off;  // amplitudes into the workspace (large circuits only)
+    int zi_off, zz_off;
+};
+struct Args {
+    const Pass* passes;
+    const Circ* circs;  // large circuits first, then small ones
+    int nlarge, nsmall;
+    const float2* mats;
+    float2* ws;
+    double* zi;
+    double* zz;
+    int* counters;  // [0] next large circuit, [1] next small circuit
+};
+
+struct Shared {
+    float2 state[1 << kSmallMax];
+    float2 U[1 << (2 * kKmax)];
+    ff seg[8][24];
+    double segT, segS11;
+    dd red[64];
+    int claim;
+};
+
+// ---- dense pass: groups g0, g0 + stride, ... of psi (global or shared memory) ---------------------------
+template <int K>
+__device__ __noinline__ void apply_dense(float2* psi, int n, const int* tg, const float2* U, uint64_t g0, uint64_t stride) {
+    constexpr int D = 1 << K;
+    const uint64_t G = 1ull << (n - K);
+    uint64_t off[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) o |= (uint64_t)((m >> j) & 1) << tg[j];
+        off[m] = o;
+    }
+    for (uint64_t g = g0; g < G; g += stride) {
+        const uint64_t base = insert_zeros(g, tg, K);
+        float2 v[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) v[m] = psi[base + off[m]];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float2 u = U[r * D + c];
+                re = __fmaf_rn(u.x, v[c].x, re);
+                re = __fmaf_rn(-u.y, v[c].y, re);
+                im = __fmaf_rn(u.x, v[c].y, im);
+                im = __fmaf_rn(u.y, v[c].x, im);
+            }
+            psi[base + off[r]] = make_float2(re, im);
+        }
+    }
+}
+
+__device__ __noinline__ void apply_pass(float2* psi, int n, const Pass& P, const float2* U, uint64_t g0, uint64_t stride) {
+    switch (P.k) {
+        case 1: apply_dense<1>(psi, n, P.targets, U, g0, stride); break;
+        case 2: apply_dense<2>(psi, n, P.targets, U, g0, stride); break;
+        case 3: apply_dense<3>(psi, n, P.targets, U, g0, stride); break;
+        default: apply_dense<4>(psi, n, P.targets, U, g0, stride); break;
+    }
+}
+
+__device__ __forceinline__ ff p_of(const float2* psi, uint64_t i) {
+    const float2 v = psi[i];
+    return ff_abs2(v.x, v.y);
+}
+
+// One 4096-amplitude segment: the 24 quantities of index bits 0..11 (T, S_0..S_11, X_0..X_10; see
+// k_reduce.cu for the thread layout), block-reduced. Thread q < 24 receives quantity q; the segment total
+// and its S_11 part are left in sh.segT / sh.segS11.
+__device__ __noinline__ double segment_stats(const float2* psi, uint64_t s, Shared& sh) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t base = (s << 12) + 2 * t;
+    ff P[8], Q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const ff p0 = p_of(psi, base + 512 * j), p1 = p_of(psi, base + 512 * j + 1);
+        Q[j] = p1;
+        P[j] = ff_add(p0, p1);
+    }
+    ff T = P[0], S0 = Q[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) { T = ff_add(T, P[j]); S0 = ff_add(S0, Q[j]); }
+    const ff S9 = ff_add(ff_add(P[1], P[3]), ff_add(P[5], P[7]));
+    const ff Z = {0.f, 0.f};
+    ff c[24];
+    c[0] = T;
+    c[1] = S0;
+#pragma unroll
+    for (int i = 1; i <= 8; ++i) c[1 + i] = ((t >> (i - 1)) & 1) ? T : Z;
+    c[10] = S9;
+    c[11] = ff_add(ff_add(P[2], P[3]), ff_add(P[6], P[7]));
+    c[12] = ff_add(ff_add(P[4], P[5]), ff_add(P[6], P[7]));
+    c[13] = (t & 1) ? ff_add(T, ff_neg(S0)) : S0;
+#pragma unroll
+    for (int i = 1; i <= 7; ++i) c[13 + i] = (((t >> (i - 1)) ^ (t >> i)) & 1) ? T : Z;
+    c[21] = ((t >> 7) & 1) ? ff_add(T, ff_neg(S9)) : S9;
+    c[22] = ff_add(ff_add(P[1], P[2]), ff_add(P[5], P[6]));
+    c[23] = ff_add(ff_add(P[2], P[3]), ff_add(P[4], P[5]));
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+        const ff v = warp_sum_ff(c[q]);
+        if (lane == 0) sh.seg[warp][q] = v;
+    }
+    __syncthreads();
+    double val = 0.0;
+    if (t < 24) {
+        ff v = sh.seg[0][t];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) v = ff_add(v, sh.seg[w][t]);
+        val = (double)v.hi + (double)v.lo;
+        if (t == 0) sh.segT = val;
+        if (t == 12) sh.segS11 = val;
+    }
+    __syncthreads();
+    return val;
+}
+
+// Quantity layout of the partial sums red[0 .. 24 + 2 nh): [0, 24) bits 0..11 as in segment_stats; then
+// S_{12..n-1} (nh values), X_11, X_{12..n-2} (nh - 1 values); nh = n - 12.
+__device__ void zstats_segments(const float2* psi, int n, uint64_t s0, uint64_t sstride, Shared& sh) {
+    const int t = threadIdx.x;
+    const int nh = n - 12;
+    const uint64_t nseg = 1ull << nh;
+    dd acc = {0.0, 0.0};
+    for (uint64_t s = s0; s < nseg; s += sstride) {
+        const double v = segment_stats(psi, s, sh);
+        if (t < 24) {
+            acc = dd_add(acc, dd{v, 0.0});
+        } else if (t < 24 + 2 * nh) {
+            const int h = t - 24;
+            const double T = sh.segT, S11 = sh.segS11;
+            double add = 0.0;
+            if (h < nh) add = ((s >> h) & 1) ? T : 0.0;
+            else if (h == nh) add = (s & 1) ? T - S11 : S11;
+            else { const int r = h - nh - 1; add = (((s >> r) ^ (s >> (r + 1))) & 1) ? T : 0.0; }
+            acc = dd_add(acc, dd{add, 0.0});
+        }
+        __syncthreads();
+    }
+    if (t < 64) sh.red[t] = acc;
+    __syncthreads();
+}
+
+// Small widths (n < 12): quantity q = 0 -> T, 1..n -> S_{q-1}, n+1..2n-1 -> X_{q-n-1}, one thread each.
+__device__ __noinline__ void zstats_serial(const float2* psi, int n, Shared& sh) {
+    const int q = threadIdx.x;
+    if (q < 2 * n) {
+        ff acc = {0.f, 0.f};
+        const int N = 1 << n;
+        for (int x = 0; x < N; ++x) {
+            bool use;
+            if (q == 0) use = true;
+            else if (q <= n) use = (x >> (q - 1)) & 1;
+            else { const int i = q - n - 1; use = ((x >> i) ^ (x >> (i + 1))) & 1; }
+            if (use) acc = ff_add(acc, p_of(psi, x));
+        }
+        sh.red[q] = dd{(double)acc.hi + (double)acc.lo, 0.0};
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double dval(dd v) { return v.hi + v.lo; }
+
+// Write <Z_i>, <Z_i Z_{i+1}> from the quantity vector red (layout of zstats_segments / zstats_serial).
+__device__ void write_z(const dd* red, int n, double* zi, double* zz) {
+    const int t = threadIdx.x;
+    if (n < 12) {
+        const double T = dval(red[0]);
+        if (t < n) zi[t] = T - 2.0 * dval(red[1 + t]);
+        if (t < n - 1) zz[t] = T - 2.0 * dval(red[n + 1 + t]);
+        return;
+    }
+    const int nh = n - 12;
+    const double T = dval(red[0]);
+    if (t < n) zi[t] = T - 2.0 * dval(t < 12 ? red[1 + t] : red[24 + (t - 12)]);
+    if (t < n - 1) {
+        const dd X = t <= 10 ? red[13 + t] : (t == 11 ? red[24 + nh] : red[24 + nh + 1 + (t - 12)]);
+        zz[t] = T - 2.0 * dval(X);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_batch(const __grid_constant__ Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank(), CL = cl.num_blocks();
+    const int t = threadIdx.x;
+
+    // ---- large circuits: one cluster per circuit ------------------------------------------------------
+    while (true) {
+        if (rank == 0 && t == 0) sh.claim = atomicAdd(&a.counters[0], 1);
+        cl.sync();
+        const int idx = *cl.map_shared_rank(&sh.claim, 0);
+        cl.sync();
+        if (idx >= a.nlarge) break;
+        const Circ c = a.circs[idx];
+        float2* psi = a.ws + c.state_off;
+        const uint64_t N = 1ull << c.n;
+        const uint64_t gid = (uint64_t)rank * kThreads + t, gstride = (uint64_t)CL * kThreads;
+        for (uint64_t i = gid; i < N; i += gstride) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+        cl.sync();
+        for (int p = 0; p < c.npass; ++p) {
+            const Pass P = a.passes[c.first_pass + p];
+            const int DD = 1 << (2 * P.k);
+            for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
+            __syncthreads();
+            apply_pass(psi, c.n, P, sh.U, gid, gstride);
+            cl.sync();  // release / acquire at cluster scope: the next pass sees every CTA's stores
+        }
+        zstats_segments(psi, c.n, rank, CL, sh);
+        cl.sync();
+        if (rank == 0 && t < 24 + 2 * (c.n - 12)) {
+            dd v = sh.red[t];
+            for (unsigned r2 = 1; r2 < CL; ++r2) v = dd_add(v, cl.map_shared_rank(sh.red, r2)[t]);
+            sh.red[t] = v;
+        }
+        cl.sync();
+        if (rank == 0) write_z(sh.red, c.n, a.zi + c.zi_off, a.zz + c.zz_off);
+    }
+
+    // ---- small circuits: one CTA per circuit, the state in shared memory ---------------------------------
+    while (true) {
+        if (t == 0) sh.claim = atomicAdd(&a.counters[1], 1);
+        __syncthreads();
+        const int idx = sh.claim;
+        __syncthreads();
+        if (idx >= a.nsmall) break;
+        const Circ c = a.circs[a.nlarge + idx];
+        float2* psi = sh.state;
+        const int N = 1 << c.n;
+        for (int i = t; i < N; i += kThreads) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+        for (int p = 0; p < c.npass; ++p) {
+            const Pass P = a.passes[c.first_pass + p];
+            const int DD = 1 << (2 * P.k);
+            for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
+            __syncthreads();
+            apply_pass(psi, c.n, P, sh.U, t, kThreads);
+            __syncthreads();
+        }
+        if (c.n >= 12) zstats_segments(psi, c.n, 0, 1, sh);
+        else zstats_serial(psi, c.n, sh);
+        write_z(sh.red, c.n, a.zi + c.zi_off, a.zz + c.zz_off);
+        __syncthreads();
+    }
+}
+
+// ---- host side ----------------------------------------------------------------------------------------------
+std::mutex g_tune_mu;
+int g_tuned_k[QSIM_MAX_QUBITS + 1] = {0};
+
+int tuned_k(int n) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    return g_tuned_k[n] ? g_tuned_k[n] : kKmax;
+}
+
+}  // namespace batch
+}  // namespace qsim
+
+struct qsim_batch {
+    int count = 0;
+    std::vector<int> widths;
+    int nlarge = 0, nsmall = 0;
+    void* dbuf = nullptr;
+    qsim::batch::Args args{};
+    size_t ws_need = 0;
+    int total_zi = 0, total_zz = 0;
+    int grid = 0;
+    qsim_plan_info info{};
+    cudaGraphExec_t gexec = nullptr;
+    void* gws = nullptr;
+    cudaStream_t gstream = nullptr;
+};
 
 using namespace qsim;
 
+namespace {
+
+size_t small_state_bytes(int n) { return (size_t)8 << n; }
+
+int validate_batch(const qsim_circuit* cs, int count) {
+    if (!cs || count < 1) { set_error("need at least one circuit"); return QSIM_EINVAL; }
+    for (int i = 0; i < count; ++i) {
+        if (cs[i].n < 1 || cs[i].n > 26) { set_error("circuit %d: batched widths are 1..26", i); return QSIM_EINVAL; }
+        if (cs[i].num_gates < 0 || (cs[i].num_gates > 0 && !cs[i].gates)) { set_error("circuit %d: bad gate list", i); return QSIM_EINVAL; }
+    }
+    return QSIM_OK;
+}
+
+}  // namespace
+
 extern "C" {
-int qsim_batch_workspace_bytes(const qsim_circuit*, int, size_t*) {
-    set_error("batched execution is not built yet");
-    return QSIM_EUNSUPPORTED;
+
+int qsim_batch_workspace_bytes(const qsim_circuit* cs, int count, size_t* out) {
+    set_error("%s", "");
+    if (!out) { set_error("NULL output"); return QSIM_EINVAL; }
+    int rc = validate_batch(cs, count);
+    if (rc) return rc;
+    size_t b = 0;
+    for (int i = 0; i < count; ++i)
+        if (cs[i].n > batch::kSmallMax) b += (small_state_bytes(cs[i].n) + 255) & ~(size_t)255;
+    *out = b;
+    return QSIM_OK;
 }
-int qsim_batch_run(const qsim_circuit*, int, const qsim_run_opts*, void*, size_t, void*, double*, double*,
-                   qsim_plan_info*) {
-    set_error("batched execution is not built yet");
-    return QSIM_EUNSUPPORTED;
+
+int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opts* opts_in, void* stream_v,
+                           qsim_batch_h* out, qsim_plan_info* info) {
+    set_error("%s", "");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) { set_error("NULL output"); return QSIM_EINVAL; }
+    *out = nullptr;
+    int rc = validate_batch(cs, count);
+    if (rc) return rc;
+    qsim_run_opts opts{};
+    if (opts_in) opts = *opts_in;
+    if (opts.max_fused < 0 || opts.max_fused > batch::kKmax) { set_error("batched fusion width must be 0 (tuned) or 1..%d", batch::kKmax); return QSIM_EINVAL; }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+
+    // ---- plan every circuit ---------------------------------------------------------------------------
+    std::vector<ComposeBlock> cblocks;
+    std::vector<ComposeGate> cgates;
+    std::vector<double> pool;
+    std::vector<batch::Pass> passes;
+    std::vector<batch::Circ> circs(count);
+    int64_t compose_out = 0;
+    int64_t gates_total = 0;
+    double bytes = 0.0;
+    for (int ci = 0; ci < count; ++ci) {
+        const qsim_circuit& c = cs[ci];
+        const int n = c.n;
+        const int kmax = std::min(n, opts.max_fused ? opts.max_fused : batch::tuned_k(n));
+        std::vector<uint64_t> gmask(c.num_gates);
+        std::vector<char> gdiag(c.num_gates);
+        for (int i = 0; i < c.num_gates; ++i) {
+            const qsim_gate& g = c.gates[i];
+            rc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, batch::kKmax);
+            if (rc || g.k + g.nc > batch::kKmax) { set_error("circuit %d gate %d: batched gates act on at most %d qubits", ci, i, batch::kKmax); return QSIM_EINVAL; }
+            if (!g.matrix || !is_unitary(g.matrix, g.k, 1e-8 * (1 << g.k))) { set_error("circuit %d gate %d: matrix missing or not unitary", ci, i); return QSIM_EINVAL; }
+            uint64_t m = 0;
+            for (int j = 0; j < g.k; ++j) m |= 1ull << g.targets[j];
+            for (int j = 0; j < g.nc; ++j) m |= 1ull << g.controls[j];
+            gmask[i] = m;
+            gdiag[i] = is_diagonal(g.matrix, g.k);
+        }
+        gates_total += c.num_gates;
+        const auto blocks = group_gates(gmask, gdiag, n, kmax);
+        circs[ci].n = n;
+        circs[ci].npass = (int)blocks.size();
+        circs[ci].first_pass = (int64_t)passes.size();
+        for (const auto& blk : blocks) {
+            uint64_t Q = 0;
+            for (int gi : blk) Q |= gmask[gi];
+            int local[64], kb = 0;
+            batch::Pass P{};
+            for (int q = 0; q < n; ++q)
+                if ((Q >> q) & 1) { local[q] = kb; P.targets[kb++] = q; }
+            P.k = kb;
+            P.mat_off = compose_out;
+            ComposeBlock cb{kb, (int)cgates.size(), (int)blk.size(), compose_out};
+            compose_out += (int64_t)1 << (2 * kb);
+            for (int gi : blk) {
+                const qsim_gate& g = c.gates[gi];
+                ComposeGate cg_{};
+                cg_.k = g.k;
+                cg_.nc = g.nc;
+                for (int j = 0; j < g.k; ++j) cg_.targets[j] = local[g.targets[j]];
+                for (int j = 0; j < g.nc; ++j) cg_.controls[j] = local[g.controls[j]];
+                cg_.mat_off = (int64_t)pool.size() / 2;
+                pool.insert(pool.end(), g.matrix, g.matrix + (2 << (2 * g.k)));
+                cgates.push_back(cg_);
+            }
+            cblocks.push_back(cb);
+            passes.push_back(P);
+            if (n > batch::kSmallMax) bytes += 16.0 * std::ldexp(1.0, n);
+        }
+    }
+
+    // ---- order: large circuits (most work first), then small ones; workspace and output offsets ------------
+    qsim_batch* b = new (std::nothrow) qsim_batch();
+    if (!b) { set_error("out of host memory"); return QSIM_ENOMEM; }
+    b->count = count;
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i) b->widths.push_back(cs[i].n);
+    int zio = 0, zzo = 0;
+    for (int i = 0; i < count; ++i) {
+        circs[i].zi_off = zio;
+        circs[i].zz_off = zzo;
+        zio += cs[i].n;
+        zzo += std::max(0, cs[i].n - 1);
+    }
+    b->total_zi = zio;
+    b->total_zz = zzo;
+    std::vector<int> large, small;
+    for (int i = 0; i < count; ++i) (cs[i].n > batch::kSmallMax ? large : small).push_back(i);
+    std::stable_sort(large.begin(), large.end(), [&](int x, int y) {
+        return std::ldexp((double)circs[x].npass, circs[x].n) > std::ldexp((double)circs[y].npass, circs[y].n);
+    });
+    size_t wsoff = 0;
+    std::vector<batch::Circ> ordered;
+    for (int i : large) {
+        circs[i].state_off = (int64_t)(wsoff / 8);
+        wsoff += (small_state_bytes(circs[i].n) + 255) & ~(size_t)255;
+        ordered.push_back(circs[i]);
+    }
+    for (int i : small) { circs[i].state_off = -1; ordered.push_back(circs[i]); }
+    b->nlarge = (int)large.size();
+    b->nsmall = (int)small.size();
+    b->ws_need = wsoff;
+
+    // ---- device buffer: [passes][circuits][float matrices][FP64 composed][pool][descriptors][counters][zi][zz]
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    size_t o = 0;
+    const size_t o_pass = o; o = align(o + sizeof(batch::Pass) * passes.size());
+    const size_t o_circ = o; o = align(o + sizeof(batch::Circ) * ordered.size());
+    const size_t o_mat = o; o = align(o + sizeof(float2) * compose_out);
+    const size_t o_out = o; o = align(o + sizeof(double) * 2 * compose_out);
+    const size_t o_pool = o; o = align(o + sizeof(double) * pool.size());
+    const size_t o_cb = o; o = align(o + sizeof(ComposeBlock) * cblocks.size());
+    const size_t o_cg = o; o = align(o + sizeof(ComposeGate) * cgates.size());
+    const size_t o_cnt = o; o = align(o + sizeof(int) * 2);
+    const size_t o_zi = o; o = align(o + sizeof(double) * zio);
+    const size_t o_zz = o; o = align(o + sizeof(double) * std::max(1, zzo));
+    cudaError_t e = cudaMalloc(&b->dbuf, o);
+    if (e != cudaSuccess) { delete b; set_error("batch plan buffer of %zu bytes", o); return QSIM_ENOMEM; }
+    char* base = static_cast<char*>(b->dbuf);
+    e = cudaMemcpyAsync(base + o_pass, passes.data(), sizeof(batch::Pass) * passes.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_circ, ordered.data(), sizeof(batch::Circ) * ordered.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_pool, pool.data(), sizeof(double) * pool.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_cb, cblocks.data(), sizeof(ComposeBlock) * cblocks.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_cg, cgates.data(), sizeof(ComposeGate) * cgates.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors are temporaries
+    if (e == cudaSuccess)
+        e = launch_compose(reinterpret_cast<ComposeBlock*>(base + o_cb), (int)cblocks.size(),
+                           reinterpret_cast<ComposeGate*>(base + o_cg), reinterpret_cast<double*>(base + o_pool),
+                           reinterpret_cast<double*>(base + o_out), batch::kKmax, s);
+    if (e == cudaSuccess)
+        e = launch_convert_matrix(QSIM_C64, reinterpret_cast<double*>(base + o_out), base + o_mat, 2 * compose_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(batch::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(batch::Shared));
+    int nclusters = 0;
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = batch::kCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(batch::kCluster, 1, 1);
+        cfg.blockDim = dim3(batch::kThreads, 1, 1);
+        cfg.dynamicSmemBytes = sizeof(batch::Shared);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&nclusters, batch::k_batch, &cfg);
+    }
+    if (e != cudaSuccess || nclusters < 1) {
+        cudaFree(b->dbuf);
+        delete b;
+        return e != cudaSuccess ? cuda_fail(e, "batch plan preparation") : (set_error("no cluster of %d CTAs fits", batch::kCluster), QSIM_EUNSUPPORTED);
+    }
+    b->grid = nclusters * batch::kCluster;
+    b->args.passes = reinterpret_cast<const batch::Pass*>(base + o_pass);
+    b->args.circs = reinterpret_cast<const batch::Circ*>(base + o_circ);
+    b->args.nlarge = b->nlarge;
+    b->args.nsmall = b->nsmall;
+    b->args.mats = reinterpret_cast<const float2*>(base + o_mat);
+    b->args.zi = reinterpret_cast<double*>(base + o_zi);
+    b->args.zz = reinterpret_cast<double*>(base + o_zz);
+    b->args.counters = reinterpret_cast<int*>(base + o_cnt);
+
+    qsim_plan_info& I = b->info;
+    I.input_gates = gates_total;
+    I.passes = (int64_t)passes.size();
+    I.dense_blocks = (int64_t)passes.size();
+    I.algorithmic_bytes = bytes;  // state traffic of the large circuits; small ones never leave shared memory
+    I.host_plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = I;
+    *out = b;
+    return QSIM_OK;
 }
+
+static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
+    b->args.ws = static_cast<float2*>(dev_ws);
+    cudaError_t e = cudaMemsetAsync(b->args.counters, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch counters");
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = batch::kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(b->grid, 1, 1);
+    cfg.blockDim = dim3(batch::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(batch::Shared);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, batch::k_batch, b->args);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch launch");
 }
+
+int qsim_batch_execute(qsim_batch_h b, void* dev_ws, size_t ws_bytes, void* stream_v, int use_graph) {
+    if (!b) { set_error("NULL batch plan"); return QSIM_EINVAL; }
+    set_error("%s", "");
+    if (b->ws_need && (!dev_ws || ws_bytes < b->ws_need)) { set_error("workspace of %zu bytes < %zu needed", ws_bytes, b->ws_need); return QSIM_ENOMEM; }
+    if (dev_ws && (reinterpret_cast<uintptr_t>(dev_ws) & 255)) { set_error("workspace must be 256-byte aligned"); return QSIM_EINVAL; }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    if (!use_graph || s == nullptr) return batch_enqueue(b, dev_ws, s);
+    if (b->gexec && b->gws == dev_ws && b->gstream == s) {
+        cudaError_t e = cudaGraphLaunch(b->gexec, s);
+        return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch graph launch");
+    }
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    int rc = batch_enqueue(b, dev_ws, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->gexec = nullptr; return cuda_fail(e, "graph instantiate"); }
+    b->gws = dev_ws;
+    b->gstream = s;
+    e = cudaGraphLaunch(b->gexec, s);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch graph launch");
+}
+
+int qsim_batch_results(qsim_batch_h b, void* stream_v, double* zi, double* zz) {
+    if (!b || !zi || !zz) { set_error("NULL argument"); return QSIM_EINVAL; }
+    set_error("%s", "");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    cudaError_t e = cudaMemcpyAsync(zi, b->args.zi, sizeof(double) * b->total_zi, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && b->total_zz > 0)
+        e = cudaMemcpyAsync(zz, b->args.zz, sizeof(double) * b->total_zz, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch results");
+}
+
+int qsim_batch_destroy(qsim_batch_h b) {
+    if (!b) return QSIM_OK;
+    cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    cudaFree(b->dbuf);
+    delete b;
+    return QSIM_OK;
+}
+
+int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws, size_t ws_bytes,
+                   void* stream, double* zi, double* zz, qsim_plan_info* info) {
+    qsim_batch_h b = nullptr;
+    int rc = qsim_batch_plan_create(cs, count, opts, stream, &b, info);
+    if (rc) return rc;
+    rc = qsim_batch_execute(b, dev_ws, ws_bytes, stream, 0);
+    if (!rc) rc = qsim_batch_results(b, stream, zi, zz);
+    qsim_batch_destroy(b);
+    return rc;
+}
+
+// Built-in tuner: for every width present, time each fusion width k in 1..4 on the first circuit of that
+// width (the median of three launches after a warm-up) and keep the fastest; later plans created with
+// max_fused = 0 use it. The trial workspace is allocated here and released before returning.
+int qsim_batch_autotune(const qsim_circuit* cs, int count, void* stream_v, int* chosen) {
+    set_error("%s", "");
+    int rc = validate_batch(cs, count);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    std::vector<int> seen(QSIM_MAX_QUBITS + 1, -1);
+    for (int i = 0; i < count; ++i)
+        if (seen[cs[i].n] < 0) seen[cs[i].n] = i;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int n = 1; n <= QSIM_MAX_QUBITS; ++n) {
+        if (seen[n] < 0) continue;
+        const qsim_circuit* c = &cs[seen[n]];
+        size_t wsb = 0;
+        qsim_batch_workspace_bytes(c, 1, &wsb);
+        void* ws = nullptr;
+        if (wsb && cudaMalloc(&ws, wsb) != cudaSuccess) { cudaGetLastError(); rc = QSIM_ENOMEM; set_error("tuning workspace"); break; }
+        float best = 1e30f;
+        int bestk = batch::kKmax;
+        for (int k = 1; k <= std::min(n, batch::kKmax); ++k) {
+            qsim_run_opts o{};
+            o.mode = QSIM_RUN_FUSED;
+            o.max_fused = k;
+            qsim_batch_h b = nullptr;
+            if (qsim_batch_plan_create(c, 1, &o, stream_v, &b, nullptr)) continue;
+            float t[3];
+            qsim_batch_execute(b, ws, wsb, stream_v, 0);  // warm-up
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(e0, s);
+                qsim_batch_execute(b, ws, wsb, stream_v, 0);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t[r], e0, e1);
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best) { best = t[1]; bestk = k; }
+            qsim_batch_destroy(b);
+        }
+        if (ws) cudaFree(ws);
+        std::lock_guard<std::mutex> lock(batch::g_tune_mu);
+        batch::g_tuned_k[n] = bestk;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen)
+        for (int i = 0; i < count; ++i) chosen[i] = batch::tuned_k(cs[i].n);
+    return rc;
+}
+
+}  // extern "C"

@@ -95,8 +95,13 @@ SIGNATURES = {
     "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
     "qsim_sample_noalloc": ([_vp, _i, _i, _u64, _i64, _vp, _vp], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
+    "qsim_batch_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
+    "qsim_batch_execute": ([_vp, _vp, _sz, _vp, _i], _i),
+    "qsim_batch_results": ([_vp, _vp, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
+    "qsim_batch_destroy": ([_vp], _i),
     "qsim_batch_run": ([_P(Circuit), _i, _P(RunOpts), _vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double),
                         _P(PlanInfo)], _i),
+    "qsim_batch_autotune": ([_P(Circuit), _i, _vp, _P(_i)], _i),
 }
 
 
@@ -336,3 +341,64 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent circuits (each from |0...0>, complex64) in one persistent launch; returns the
+    per-circuit <Z_q> and <Z_q Z_{q+1}>."""
+
+    def __init__(self, circuits, max_fused: int = 0, stream=None):
+        import torch
+        self.circuits = list(circuits)
+        self.args = [CircuitArgs(c) for c in self.circuits]
+        arr = (Circuit * len(self.args))(*[a.c for a in self.args])
+        self.carr = arr
+        ws = ctypes.c_size_t()
+        _check(lib().qsim_batch_workspace_bytes(arr, len(self.args), ctypes.byref(ws)))
+        self.ws_bytes = ws.value
+        self.ws = torch.empty(max(1, self.ws_bytes // 8), dtype=torch.complex64, device="cuda")
+        o = RunOpts(mode=RUN_FUSED, max_fused=max_fused)
+        info = PlanInfo()
+        b = ctypes.c_void_p()
+        _check(lib().qsim_batch_plan_create(arr, len(self.args), ctypes.byref(o),
+                                            ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(b), ctypes.byref(info)))
+        self.b = b
+        self.info = info.as_dict()
+        self.stream = stream
+        self.nzi = sum(c.n for c in self.circuits)
+        self.nzz = sum(max(0, c.n - 1) for c in self.circuits)
+
+    def execute(self, use_graph: bool = False):
+        _check(lib().qsim_batch_execute(self.b, ctypes.c_void_p(self.ws.data_ptr()), self.ws_bytes,
+                                        ctypes.c_void_p(_stream_ptr(self.stream)), 1 if use_graph else 0))
+
+    def results(self):
+        zi = np.zeros(max(1, self.nzi))
+        zz = np.zeros(max(1, self.nzz))
+        _check(lib().qsim_batch_results(self.b, ctypes.c_void_p(_stream_ptr(self.stream)), _dptr(zi), _dptr(zz)))
+        out, a, b = [], 0, 0
+        for c in self.circuits:
+            out.append((zi[a:a + c.n].copy(), zz[b:b + c.n - 1].copy()))
+            a += c.n
+            b += max(0, c.n - 1)
+        return out
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().qsim_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(circuits, stream=None):
+    """Tune the batched fusion width per qubit count; returns the k each circuit now gets."""
+    args = [CircuitArgs(c) for c in circuits]
+    arr = (Circuit * len(args))(*[a.c for a in args])
+    chosen = (ctypes.c_int * len(args))()
+    _check(lib().qsim_batch_autotune(arr, len(args), ctypes.c_void_p(_stream_ptr(stream)), chosen))
+    return list(chosen)

@@ -1,0 +1,110 @@
+"""Batched circuits in one persistent launch (clusters for large circuits, shared memory for small ones)
+against the FP64 oracle: per-circuit <Z_i> and <Z_i Z_{i+1}> within 1e-5 (complex64 states, FP32 fused
+matrices)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qsim(gpu_lib):
+    from paper_2511_14664_gb300 import qsim as q
+    return q
+
+
+def oracle_z(c):
+    psi = oracle.run(c)
+    return oracle.expect_z_chain(psi, c.n)
+
+
+def check(results, circuits, tol=1e-5):
+    for (zi, zz), c in zip(results, circuits):
+        rzi, rzz = oracle_z(c)
+        np.testing.assert_allclose(zi, rzi, atol=tol, rtol=0)
+        np.testing.assert_allclose(zz, rzz, atol=tol, rtol=0)
+
+
+def tfim_mix(widths, steps, seed):
+    rng = np.random.default_rng(seed)
+    return [W.tfim_chain(n, s, float(rng.uniform(0, np.pi)), float(rng.uniform(0, np.pi)))
+            for n, s in zip(widths, steps)]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_tfim_batch_small_and_large(qsim, k):
+    widths = [10, 11, 12, 13, 14, 15, 16, 17, 10, 14, 12, 16]
+    steps = [3, 2, 4, 2, 3, 2, 2, 3, 5, 1, 2, 2]
+    cs = tfim_mix(widths, steps, seed=k)
+    b = qsim.Batch(cs, max_fused=k)
+    assert b.info["input_gates"] == sum(len(c) for c in cs)
+    b.execute()
+    check(b.results(), cs)
+
+
+def test_workspace_is_only_for_large_circuits(qsim):
+    cs = tfim_mix([10, 13, 14, 20], [1, 1, 1, 1], seed=0)
+    b = qsim.Batch(cs, max_fused=3)
+    assert b.ws_bytes == 8 * (2**14 + 2**20)
+
+
+def test_general_gates_with_controls(qsim):
+    rng = np.random.default_rng(5)
+    cs = []
+    for n in (9, 12, 13, 15, 18):
+        c = W.Circuit(n)
+        for _ in range(40):
+            c.append(W.random_gate(n, rng, kmax=2, cmax=1, diag_prob=0.3))
+        cs.append(c)
+    b = qsim.Batch(cs, max_fused=4)
+    b.execute()
+    check(b.results(), cs)
+
+
+def test_segment_high_bits_and_graph_replay(qsim):
+    cs = tfim_mix([22, 11, 19], [2, 3, 2], seed=9)
+    b = qsim.Batch(cs, max_fused=4)
+    b.execute(use_graph=True)
+    r1 = b.results()
+    b.execute(use_graph=True)  # replay of the captured graph
+    r2 = b.results()
+    for (a1, b1), (a2, b2) in zip(r1, r2):
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    check(r1, cs)
+
+
+def test_autotune_then_default_width(qsim):
+    cs = tfim_mix([12, 15, 17], [2, 2, 2], seed=3)
+    chosen = qsim.batch_autotune(cs)
+    assert all(1 <= k <= 4 for k in chosen)
+    b = qsim.Batch(cs, max_fused=0)
+    b.execute()
+    check(b.results(), cs)
+
+
+def test_rx_product_closed_form_many_widths(qsim):
+    """RX(phi) on every qubit: <Z_i> = cos(phi), <Z_i Z_{i+1}> = cos(phi)^2, for widths 1..20."""
+    phi = 0.7
+    cs = []
+    for n in range(1, 21):
+        c = W.Circuit(n)
+        for q in range(n):
+            c.append(W.Gate((q,), (), W.RX(phi), "rx"))
+        cs.append(c)
+    b = qsim.Batch(cs, max_fused=4)
+    b.execute()
+    for (zi, zz), c in zip(b.results(), cs):
+        np.testing.assert_allclose(zi, np.cos(phi), atol=1e-6)
+        np.testing.assert_allclose(zz, np.cos(phi) ** 2, atol=1e-6)
+
+
+def test_batch_rejects_bad_input(qsim):
+    with pytest.raises(qsim.QsimError):
+        qsim.Batch([W.Circuit(27)])
+    c = W.Circuit(6)
+    c.append(W.Gate((0, 1, 2), (3, 4), np.eye(8), "wide"))
+    with pytest.raises(qsim.QsimError):
+        qsim.Batch([c])
