@@ -50,6 +50,9 @@ def parse_args():
     p.add_argument("--no-accuracy", action="store_true", help="skip the 20-qubit infidelity check")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--workload", default="brickwork30",
+                   choices=["brickwork30", "qft28", "tfim_batch", "pairs34"],
+                   help="brickwork30 (the headline line), qft28, tfim_batch (256 TFIM circuits), pairs34")
     return p.parse_args()
 
 
@@ -470,10 +473,195 @@ def run_ours(args):
     return 0
 
 
+# ---- secondary workloads (their own JSON lines; the default run prints only the headline line) -----------------
+def _common_line(metric, value, unit, args, ms, dtype, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def _event_time(torch, fn, steps):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(steps):
+        fn(i)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_qft(args):
+    """28-qubit QFT of a seeded basis state: plain per-gate vs fused (k = 5), checked against the closed form
+    on sampled amplitudes (|QFT x>_y = 2^{-n/2} exp(2 pi i x y / 2^n))."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    n = args.n if args.n != 30 else 28
+    x = W.basis_index(n, 2)
+    c = W.qft(n)
+    st = qsim.State(n, qsim.C64)
+    peaks, _ = measured_peaks()
+    out = {}
+    for name, kw in [("plain", dict(mode=0, max_fused=1)), ("simt5", dict(mode=1, max_fused=5)),
+                     ("tf32x3_k5", dict(mode=1, max_fused=5, precision=1, tc_min_k=5)),
+                     ("bf16x6_k5", dict(mode=1, max_fused=5, precision=3, tc_min_k=5))]:
+        p = qsim.Plan(c, **kw)
+
+        def step(i, p=p):
+            st.set_basis(x)
+            p.execute(st)
+        for _ in range(max(1, args.warmup)):
+            step(0)
+        ms = _event_time(torch, step, max(1, args.steps))
+        rng = np.random.default_rng(1)
+        ys = np.sort(rng.choice(1 << n, size=4096, replace=False))
+        got = st.tensor[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+        ph = (np.uint64(x) * ys.astype(np.uint64)) & np.uint64((1 << n) - 1)
+        ref = np.exp(2j * math.pi * ph.astype(np.float64) / (1 << n)) / math.sqrt(1 << n)
+        out[name] = {"ms_per_step": ms, "gates_per_s": len(c) / (ms / 1000.0), "passes": p.info["passes"],
+                     "algorithmic_gb": p.info["algorithmic_bytes"] / 1e9,
+                     "achieved_gbs": p.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9,
+                     "max_err_sampled": float(np.max(np.abs(got - ref)))}
+    best = min((k for k in out if k != "plain"), key=lambda k: out[k]["ms_per_step"])
+    line = _common_line(f"gate-applications/s, {n}-qubit QFT (with swaps), complex64, fused k=5 vs plain",
+                        out[best]["gates_per_s"], UNIT, args, out[best]["ms_per_step"], "f32",
+                        {"workload": f"QFT n={n} from |x>, x={x}, {len(c)} gates", "path": best},
+                        paths=out, peak_hbm_gbs=peaks["hbm_gbs"])
+    print(json.dumps(line))
+    return 0
+
+
+def run_tfim_batch(args):
+    """256 Trotterised TFIM chains (widths U{10..24}, steps U{8..32}, theta, phi ~ U(0, pi); seed 4) in one
+    persistent launch (replayed from a CUDA graph), fusion width tuned per circuit width; per-circuit <Z_i>
+    and <Z_i Z_{i+1}>."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    batch = W.tfim_batch(256, seed=4)
+    cs = [c for c, _, _ in batch]
+    gates = sum(len(c) for c in cs)
+    t = time.perf_counter()
+    chosen = qsim.batch_autotune(cs)
+    tune_s = time.perf_counter() - t
+    b = qsim.Batch(cs, max_fused=0)
+    for _ in range(max(1, args.warmup)):
+        b.execute(use_graph=True)
+    ms = _event_time(torch, lambda i: b.execute(use_graph=True), max(1, args.steps))
+    res = b.results()
+    # end to end: plan from host circuits, one launch, results to host
+    t = time.perf_counter()
+    b2 = qsim.Batch(cs, max_fused=0)
+    b2.execute()
+    b2.results()
+    b2.close()
+    e2e_s = time.perf_counter() - t
+    peaks, src = measured_peaks()
+    gbs = b.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9
+    widths = sorted(set(c.n for c in cs))
+    kmap = {str(n): chosen[[c.n for c in cs].index(n)] for n in widths}
+    line = _common_line("gate-applications/s, batch of 256 TFIM chains (10-24 qubits, 8-32 Trotter steps), "
+                        "complex64, one persistent launch", gates / (ms / 1000.0), UNIT, args, ms, "f32",
+                        {"workload": f"256 TFIM chains seed 4, {gates} gates, "
+                                     f"{sum(1 for c in cs if c.n > 13)} circuits > 13 qubits",
+                         "fusion_k_by_width": kmap, "passes": b.info["passes"]},
+                        circuits_per_s=256 / (ms / 1000.0),
+                        roofline={"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch",
+                                  "note": "algorithmic bytes of the circuits > 13 qubits only; smaller ones stay "
+                                          "in shared memory", "peak_source": src},
+                        e2e={"value": gates / e2e_s, "unit": UNIT, "h2d_bytes_per_step":
+                             sum(16 * 4 ** len(g.targets) for c in cs for g in c.gates),
+                             "d2h_bytes_per_step": 8 * sum(2 * c.n - 1 for c in cs)},
+                        tune_s=tune_s, sample_zi0=list(res[0][0][:4]))
+    if not args.no_cpu:
+        import oracle as oracle_mod
+        # oracle on the smallest circuits until the time budget runs out; work ~ gates x 2^n
+        order = sorted(range(len(cs)), key=lambda i: cs[i].n)
+        done_work, t0, used = 0.0, time.perf_counter(), 0
+        for i in order:
+            psi = oracle_mod.run(cs[i])
+            oracle_mod.expect_z_chain(psi, cs[i].n)
+            done_work += len(cs[i]) * 2.0 ** cs[i].n
+            used += 1
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        dt = time.perf_counter() - t0
+        total_work = sum(len(c) * 2.0 ** c.n for c in cs)
+        est = dt * total_work / done_work
+        line["cpu_baseline"] = {"value": gates / est, "unit": UNIT, "cores": oracle_mod.num_threads(),
+                                "kind": "oracle", "sample": f"{used} smallest circuits in {dt:.1f} s, extrapolated "
+                                                            f"to the batch by work = gates x 2^n"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_pairs34(args):
+    """34-qubit complex64 state (128 GiB): 16 layers of Haar U(4) on seeded random matchings (seed 5), the top
+    4 qubits treated as global index bits (reorder passes before gates on them, identity order restored at
+    the end), then 10^5 samples (seed 6). Also timed: the same circuit addressing every qubit in place."""
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    n = args.n if args.n != 30 else 34
+    c = W.random_pairs(n, 16, seed=5)
+    st = qsim.State(n, qsim.C64)
+    out = {}
+    for name, local in [("reorder_L%d" % (n - 4), n - 4), ("in_place", 0)]:
+        p = qsim.Plan(c, mode=0, max_fused=2, local_qubits=local)
+        p.pass_list = p.passes()
+        st.set_basis(0)
+        p.execute(st)
+        st.sample(6, 100000)
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(p.pass_list) + 3)]
+        stream = torch.cuda.current_stream()
+        st.set_basis(0)
+        evs[0].record(stream)
+        for i in range(len(p.pass_list)):
+            p.execute_range(st, i, 1)
+            evs[i + 1].record(stream)
+        smp = st.sample(6, 100000)
+        evs[-1].record(stream)
+        torch.cuda.synchronize()
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(p.pass_list))]
+        total = evs[0].elapsed_time(evs[-1])
+        reo = sum(m for m, q in zip(per, p.pass_list) if q["kind"] == "reorder")
+        gate_ms = sum(m for m, q in zip(per, p.pass_list) if q["kind"] != "reorder")
+        gate_bytes = sum(q["algorithmic_bytes"] for q in p.pass_list if q["kind"] != "reorder")
+        reo_bytes = sum(q["algorithmic_bytes"] for q in p.pass_list if q["kind"] == "reorder")
+        out[name] = {"ms_total": total, "gates_per_s": len(c) / (total / 1000.0), "passes": len(p.pass_list),
+                     "reorder_passes": sum(1 for q in p.pass_list if q["kind"] == "reorder"),
+                     "reorder_ms": reo, "reorder_gbs": reo_bytes / (reo / 1000.0) / 1e9 if reo > 0 else None,
+                     "gate_pass_gbs": gate_bytes / (gate_ms / 1000.0) / 1e9,
+                     "sample_ms": evs[-2].elapsed_time(evs[-1]), "norm": st.norm()}
+        p.close()
+    main = "reorder_L%d" % (n - 4)
+    line = _common_line(f"gate-applications/s, {n}-qubit random U(4) pairs depth 16, complex64, reorder passes "
+                        f"for {4} global qubits, 1e5 samples", out[main]["gates_per_s"], UNIT, args,
+                        out[main]["ms_total"], "f32",
+                        {"workload": f"random pairs n={n} depth 16 seed 5, {len(c)} gates, 1e5 samples seed 6"},
+                        paths=out)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "qft28":
+        return run_qft(args)
+    if args.workload == "tfim_batch":
+        return run_tfim_batch(args)
+    if args.workload == "pairs34":
+        return run_pairs34(args)
     return run_ours(args)
 
 

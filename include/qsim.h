@@ -88,7 +88,13 @@ typedef struct {
     int32_t precision;  /* QSIM_PREC_* for dense blocks of >= tc_min_k qubits (complex64 states only) */
     int32_t tc_min_k;   /* smallest dense block sent to the tensor-core kernel (0 = 5) */
     int32_t use_graph;  /* 1: replay the plan's launches from a CUDA graph captured on first execution */
-    int32_t reserved[3];
+    /* > 0: treat qubits >= local_qubits as "global" index bits, as a state split over 2^(n - local_qubits)
+       devices would (Sec. 2.1: gates on the n - log2(m) local qubits need no exchange). Before a pass that
+       touches a global qubit, a reorder pass swaps it with an idle local qubit (least recently used) and
+       the plan tracks the logical -> physical qubit map; the identity order is restored at the end.
+       0 = off (every qubit is addressed in place). */
+    int32_t local_qubits;
+    int32_t reserved[2];
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */
@@ -183,6 +189,7 @@ int qsim_plan_destroy(qsim_plan_h plan);
 #define QSIM_PASS_DIAG 1        /* diagonal factors, non-unit entries only */
 #define QSIM_PASS_DENSE_TILE 2  /* dense k = 5, 6 on CUDA cores through shared memory */
 #define QSIM_PASS_TC 3          /* dense block on tensor cores (complex64) */
+#define QSIM_PASS_REORDER 4     /* qubit reorder (exchange of index-bit pairs) */
 typedef struct {
     int32_t kind;             /* QSIM_PASS_* */
     int32_t k;                /* qubits the pass's matrix acts on */

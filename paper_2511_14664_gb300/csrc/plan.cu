@@ -20,7 +20,7 @@
 
 namespace qsim {
 
-enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3 };
+enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4 };
 
 struct PlanOp {
     int kind = OP_DENSE_SMALL;
@@ -33,6 +33,8 @@ struct PlanOp {
     int precision = QSIM_PREC_SIMT;
     int compose_idx = -1;      // block index in the composition (-1: a single input gate)
     int64_t gates = 1;
+    int nswap = 0;             // OP_SWAP: exchange qubit swap_a[i] with swap_b[i]
+    int swap_a[8] = {0}, swap_b[8] = {0};
 };
 
 }  // namespace qsim
@@ -91,6 +93,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
 }
 
 static double op_bytes(const PlanOp& op, int n, size_t amp) {
+    if (op.kind == OP_SWAP) return 2.0 * amp * std::ldexp(1.0, n) * (1.0 - std::ldexp(1.0, -op.nswap));
     const double groups = std::ldexp(1.0, n - op.k - op.nc);
     if (op.kind == OP_DIAG) return 2.0 * amp * groups * (double)op.touch.size();
     return 2.0 * amp * groups * (double)(1 << op.k);
@@ -117,6 +120,9 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
             case OP_TC:
                 e = launch_tc_apply(h->psi, h->n, op.k, op.targets, static_cast<char*>(p->dbuf) + op.dev_off,
                                     op.precision, h->derr, h->stream, h->dev);
+                break;
+            case OP_SWAP:
+                e = launch_swap(h->dtype, h->psi, h->n, op.swap_a, op.swap_b, op.nswap, h->stream, h->dev, nullptr);
                 break;
         }
         if (e != cudaSuccess) return cuda_fail(e, "plan pass launch");
@@ -353,6 +359,91 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     }
     if (rc) { cudaFree(p->dbuf); delete p; return rc; }
 
+    // ---- global / local index bits: reorder before passes that touch a global qubit ------------------------
+    if (opts.local_qubits > 0 && opts.local_qubits < n) {
+        const int L = opts.local_qubits;
+        std::vector<int> phys(n), logi(n);  // logical -> physical position and back
+        std::vector<int64_t> last(n, -1);   // last pass that used each physical position
+        for (int q = 0; q < n; ++q) phys[q] = logi[q] = q;
+        std::vector<PlanOp> out_ops;
+        int64_t clock = 0;
+        auto emit_swaps = [&](const std::vector<std::pair<int, int>>& pairs) {
+            for (size_t i = 0; i < pairs.size(); i += 8) {
+                PlanOp sw;
+                sw.kind = OP_SWAP;
+                sw.gates = 0;
+                for (size_t j = i; j < pairs.size() && j < i + 8; ++j) {
+                    sw.swap_a[sw.nswap] = pairs[j].first;
+                    sw.swap_b[sw.nswap] = pairs[j].second;
+                    ++sw.nswap;
+                }
+                out_ops.push_back(std::move(sw));
+            }
+            for (const auto& pr : pairs) {  // positions pr.first and pr.second exchange their logical qubits
+                const int la = logi[pr.first], lb = logi[pr.second];
+                logi[pr.first] = lb; logi[pr.second] = la;
+                phys[la] = pr.second; phys[lb] = pr.first;
+            }
+        };
+        for (PlanOp& op : p->ops) {
+            std::vector<int> qs(op.targets, op.targets + op.k);
+            qs.insert(qs.end(), op.controls, op.controls + op.nc);
+            uint64_t used = 0;
+            std::vector<int> glob;
+            for (int q : qs) { used |= 1ull << phys[q]; if (phys[q] >= L) glob.push_back(phys[q]); }
+            if (!glob.empty()) {
+                std::vector<int> cand;  // idle local positions, least recently used first
+                for (int pp = 0; pp < L; ++pp) if (!((used >> pp) & 1)) cand.push_back(pp);
+                std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) { return last[x] < last[y]; });
+                if (cand.size() < glob.size()) {
+                    cudaFree(p->dbuf);
+                    delete p;
+                    set_error("local_qubits = %d leaves too few idle local qubits for a %d-qubit pass", L, (int)qs.size());
+                    return QSIM_EINVAL;
+                }
+                std::vector<std::pair<int, int>> pairs;
+                for (size_t i = 0; i < glob.size(); ++i) pairs.push_back({cand[i], glob[i]});
+                emit_swaps(pairs);
+            }
+            for (int j = 0; j < op.k; ++j) { op.targets[j] = phys[op.targets[j]]; last[op.targets[j]] = clock; }
+            for (int j = 0; j < op.nc; ++j) { op.controls[j] = phys[op.controls[j]]; last[op.controls[j]] = clock; }
+            ++clock;
+            out_ops.push_back(std::move(op));
+        }
+        std::vector<std::pair<int, int>> restore;
+        for (int q = 0; q < n; ++q) {
+            if (phys[q] == q) continue;
+            const int pq = phys[q];
+            restore.push_back({q, pq});
+            const int lo = logi[q];  // logical qubit now at position q moves to pq
+            logi[q] = q; logi[pq] = lo;
+            phys[lo] = pq; phys[q] = q;
+        }
+        // each restore transposition touches position q, which later ones never touch again, but later ones
+        // may touch pq; emit them one pair per pass where positions repeat, otherwise batch up to 8
+        {
+            size_t i = 0;
+            while (i < restore.size()) {
+                PlanOp sw;
+                sw.kind = OP_SWAP;
+                sw.gates = 0;
+                uint64_t busy = 0;
+                while (i < restore.size() && sw.nswap < 8) {
+                    const auto& pr = restore[i];
+                    const uint64_t m = (1ull << pr.first) | (1ull << pr.second);
+                    if (busy & m) break;
+                    busy |= m;
+                    sw.swap_a[sw.nswap] = pr.first;
+                    sw.swap_b[sw.nswap] = pr.second;
+                    ++sw.nswap;
+                    ++i;
+                }
+                out_ops.push_back(std::move(sw));
+            }
+        }
+        p->ops.swap(out_ops);
+    }
+
     // ---- statistics ---------------------------------------------------------------------------------------
     qsim_plan_info& I = p->info;
     I.input_gates = G;
@@ -360,6 +451,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         ++I.passes;
         if (op.kind == OP_DIAG) ++I.diag_blocks;
         else if (op.kind == OP_TC) ++I.tc_blocks;
+        else if (op.kind == OP_SWAP) ++I.reorders;
         else ++I.dense_blocks;
         I.algorithmic_bytes += op_bytes(op, n, amp);
     }

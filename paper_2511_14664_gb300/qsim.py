@@ -40,7 +40,8 @@ class Circuit(ctypes.Structure):
 
 class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PassInfo(ctypes.Structure):
@@ -48,7 +49,7 @@ class PassInfo(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("gates", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double)]
 
 
-PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc"}
+PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder"}
 
 
 class PlanInfo(ctypes.Structure):
@@ -228,9 +229,10 @@ class State:
         return self
 
     def run(self, circuit, mode: int = RUN_PLAIN, max_fused: int = 5, precision: int = PREC_SIMT,
-            tc_min_k: int = 5):
+            tc_min_k: int = 5, local_qubits: int = 0):
         cc = CircuitArgs(circuit)
-        o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k, use_graph=0)
+        o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k, use_graph=0,
+                    local_qubits=local_qubits)
         info = PlanInfo()
         _check(lib().qsim_run(self.h, ctypes.byref(cc.c), ctypes.byref(o), ctypes.byref(info)))
         return info.as_dict()
@@ -302,10 +304,11 @@ class Plan:
     """A planned circuit (fusion, kernel choice, FP64 block composition done once)."""
 
     def __init__(self, circuit, dtype: int = C64, mode: int = RUN_PLAIN, max_fused: int = 5,
-                 precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None):
+                 precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None,
+                 local_qubits: int = 0):
         self.args = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
-                    use_graph=1 if use_graph else 0)
+                    use_graph=1 if use_graph else 0, local_qubits=local_qubits)
         info = PlanInfo()
         p = ctypes.c_void_p()
         _check(lib().qsim_plan_create(ctypes.byref(self.args.c), dtype, ctypes.byref(o),

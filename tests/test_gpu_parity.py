@@ -339,3 +339,55 @@ def test_errors(qsim):
     with pytest.raises(qsim.QsimError):
         st.apply_gate((9,), (), np.eye(2))
     assert st.get_state()[3] == 1
+
+
+# ---- global / local index bits: reorder passes before gates on "global" qubits -------------------------------
+@pytest.mark.parametrize("mode,k,local", [(0, 1, 12), (0, 1, 10), (1, 4, 12), (1, 2, 9)])
+def test_local_qubits_reorder_plan(qsim, mode, k, local):
+    """Random U(4) layers on seeded matchings (most pairs span high qubits), run with the top qubits treated
+    as global index bits: the plan inserts reorder passes, and the result equals the oracle's."""
+    n = 16
+    c = W.random_pairs(n, 6, seed=5)
+    st = make_state(qsim, n, 0)
+    info = st.run(c, mode=mode, max_fused=k, local_qubits=local)
+    assert info["reorders"] > 0
+    close(st.get_state(), oracle.run(c), n, 0)
+
+
+def test_local_qubits_with_tensor_cores(qsim):
+    n = 17
+    c = W.brickwork(n, 8, seed=6)
+    st = make_state(qsim, n, 0)
+    info = st.run(c, mode=1, max_fused=6, precision=1, tc_min_k=5, local_qubits=14)
+    assert info["reorders"] > 0 and info["tc_blocks"] > 0
+    close(st.get_state(), oracle.run(c), n, 0)
+
+
+def test_full_size_34q_reorder_and_sampling(qsim):
+    """At the 34-qubit size (128 GiB complex64), in the configuration the benchmark times (top 4 qubits
+    global, reorder passes): properties that hold at any size -- the norm stays 1 and 10^5 samples follow
+    the GPU's own 8-qubit marginal (chi-square), and their indices are valid."""
+    import torch
+    from scipy.stats import chisquare
+    free = torch.cuda.mem_get_info()[0]
+    if free < (2**34) * 8 + (4 << 30):
+        pytest.skip("needs 132 GiB of free device memory")
+    n = 34
+    c = W.random_pairs(n, 2, seed=5)
+    st = make_state(qsim, n, 0)
+    info = st.run(c, mode=0, max_fused=2, local_qubits=30)
+    assert info["reorders"] > 0
+    assert abs(st.norm() - 1.0) <= 1e-4
+    qs = [0, 5, 11, 17, 22, 28, 31, 33]
+    marg = st.probs(qs)
+    s = st.sample(6, 100000).astype(np.int64)
+    assert s.max() < 2**n
+    idx = np.zeros(len(s), dtype=np.int64)
+    for j, q in enumerate(qs):
+        idx |= ((s >> q) & 1) << j
+    counts = np.bincount(idx, minlength=256)
+    expected = marg / marg.sum() * len(s)
+    keep = expected > 5
+    assert chisquare(counts[keep], expected[keep] * counts[keep].sum() / expected[keep].sum()).pvalue > 1e-4
+    del st
+    torch.cuda.empty_cache()
