@@ -620,7 +620,7 @@ def run_pairs34(args):
         p.execute(st)
         st.sample(6, 100000)
         torch.cuda.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(p.pass_list) + 3)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(p.pass_list) + 2)]
         stream = torch.cuda.current_stream()
         st.set_basis(0)
         evs[0].record(stream)
@@ -640,7 +640,7 @@ def run_pairs34(args):
                      "reorder_passes": sum(1 for q in p.pass_list if q["kind"] == "reorder"),
                      "reorder_ms": reo, "reorder_gbs": reo_bytes / (reo / 1000.0) / 1e9 if reo > 0 else None,
                      "gate_pass_gbs": gate_bytes / (gate_ms / 1000.0) / 1e9,
-                     "sample_ms": evs[-2].elapsed_time(evs[-1]), "norm": st.norm()}
+                     "sample_ms": evs[len(p.pass_list)].elapsed_time(evs[-1]), "norm": st.norm()}
         p.close()
     main = "reorder_L%d" % (n - 4)
     line = _common_line(f"gate-applications/s, {n}-qubit random U(4) pairs depth 16, complex64, reorder passes "
