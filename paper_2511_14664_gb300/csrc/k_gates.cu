@@ -247,6 +247,41 @@ k_swap_tile(typename Amp<R>::T* __restrict__ psi, uint64_t ntiles, const __grid_
     }
 }
 
+// Direct exchange when every swapped bit is >= 1 (complex64 16-byte vectors of two groups) or any (V = 1):
+// only amplitudes whose index changes are read and written. Items enumerate (moving pattern pair, group);
+// groups vary fastest, so a warp streams contiguous runs for a fixed pattern pair.
+struct SwapDirectArgs {
+    int nb;               // 2p swapped bit positions, ascending
+    int bits[16];
+    int npairs;           // moving pattern pairs (u, sigma(u)), u < sigma(u)
+    uint64_t off_u[120], off_v[120];
+};
+
+template <typename R, int V>
+__global__ void __launch_bounds__(256)
+k_swap_direct(typename Amp<R>::T* __restrict__ psi, uint64_t groups_v, const __grid_constant__ SwapDirectArgs a) {
+    using T = typename Amp<R>::T;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t total = groups_v * (uint64_t)a.npairs;
+    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
+        const uint64_t m = it / groups_v, gv = it - m * groups_v;
+        const uint64_t base = insert_zeros(gv * V, a.bits, a.nb);
+        if constexpr (V == 2) {
+            float4* pu = reinterpret_cast<float4*>(psi + base + a.off_u[m]);
+            float4* pv = reinterpret_cast<float4*>(psi + base + a.off_v[m]);
+            const float4 x = *pu, y = *pv;
+            *pu = y;
+            *pv = x;
+        } else {
+            T* pu = psi + base + a.off_u[m];
+            T* pv = psi + base + a.off_v[m];
+            const T x = *pu, y = *pv;
+            *pu = y;
+            *pv = x;
+        }
+    }
+}
+
 // ============================================================================================================
 // |x>
 // ============================================================================================================
@@ -470,8 +505,62 @@ static cudaError_t swap_pass(void* psi, int n, const int* a, const int* b, int p
     return cudaGetLastError();
 }
 
+// Direct exchange of p <= 4 pairs whose bits are all >= minbit; false if not applicable.
+template <typename R>
+static bool swap_direct(void* psi, int n, const int* a, const int* b, int p, cudaStream_t s, const DevInfo& d,
+                        cudaError_t* err) {
+    using T = typename Amp<R>::T;
+    if (p > 4) return false;
+    SwapDirectArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    int lo = 64;
+    for (int i = 0; i < p; ++i) {
+        sa.bits[sa.nb++] = a[i];
+        sa.bits[sa.nb++] = b[i];
+        lo = std::min(lo, std::min(a[i], b[i]));
+    }
+    const int minbit = sizeof(R) == 4 ? 4 : 3;  // runs of >= 128 bytes
+    if (lo < minbit) return false;
+    std::sort(sa.bits, sa.bits + sa.nb);
+    // pattern u: bit 2i <-> a[i], bit 2i+1 <-> b[i]; sigma exchanges the two bits of every pair
+    for (int u = 0; u < (1 << (2 * p)); ++u) {
+        int v = 0;
+        for (int i = 0; i < p; ++i) v |= (((u >> (2 * i)) & 1) << (2 * i + 1)) | (((u >> (2 * i + 1)) & 1) << (2 * i));
+        if (u < v) {
+            uint64_t ou = 0, ov = 0;
+            for (int i = 0; i < p; ++i) {
+                ou |= (uint64_t)((u >> (2 * i)) & 1) << a[i] | (uint64_t)((u >> (2 * i + 1)) & 1) << b[i];
+                ov |= (uint64_t)((v >> (2 * i)) & 1) << a[i] | (uint64_t)((v >> (2 * i + 1)) & 1) << b[i];
+            }
+            sa.off_u[sa.npairs] = ou;
+            sa.off_v[sa.npairs] = ov;
+            ++sa.npairs;
+        }
+    }
+    const uint64_t groups = 1ull << (n - sa.nb);
+    if constexpr (sizeof(R) == 4) {
+        const uint64_t gv = groups / 2;
+        k_swap_direct<R, 2><<<grid_for((int64_t)(gv * sa.npairs), 256, d.num_sms, 8), 256, 0, s>>>(
+            reinterpret_cast<T*>(psi), gv, sa);
+    } else {
+        k_swap_direct<R, 1><<<grid_for((int64_t)(groups * sa.npairs), 256, d.num_sms, 8), 256, 0, s>>>(
+            reinterpret_cast<T*>(psi), groups, sa);
+    }
+    *err = cudaGetLastError();
+    return true;
+}
+
 cudaError_t launch_swap(int dtype, void* psi, int n, const int* a, const int* b, int p, cudaStream_t s,
                         const DevInfo& d, int* passes) {
+    {
+        cudaError_t e = cudaSuccess;
+        const bool done = dtype == QSIM_C64 ? swap_direct<float>(psi, n, a, b, p, s, d, &e)
+                                            : swap_direct<double>(psi, n, a, b, p, s, d, &e);
+        if (done) {
+            if (passes) *passes = 1;
+            return e;
+        }
+    }
     const int max_bits = dtype == QSIM_C64 ? 13 : 12;
     int done = 0, np = 0;
     while (done < p) {

@@ -385,24 +385,45 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 phys[la] = pr.second; phys[lb] = pr.first;
             }
         };
-        for (PlanOp& op : p->ops) {
+        auto op_qubits = [](const PlanOp& op) {
             std::vector<int> qs(op.targets, op.targets + op.k);
             qs.insert(qs.end(), op.controls, op.controls + op.nc);
-            uint64_t used = 0;
-            std::vector<int> glob;
-            for (int q : qs) { used |= 1ull << phys[q]; if (phys[q] >= L) glob.push_back(phys[q]); }
-            if (!glob.empty()) {
-                std::vector<int> cand;  // idle local positions, least recently used first
-                for (int pp = 0; pp < L; ++pp) if (!((used >> pp) & 1)) cand.push_back(pp);
-                std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) { return last[x] < last[y]; });
+            return qs;
+        };
+        for (size_t i = 0; i < p->ops.size(); ++i) {
+            PlanOp& op = p->ops[i];
+            bool needs = false;
+            for (int q : op_qubits(op)) needs |= phys[q] >= L;
+            if (needs) {
+                // Look ahead: bring in, in one exchange pass, every global qubit needed by passes i..j, as long
+                // as those passes' qubits all fit among the local positions and at most 8 pairs are exchanged.
+                uint64_t bring = 0, protect = 0;
+                for (size_t j = i; j < p->ops.size(); ++j) {
+                    uint64_t qj = 0, gj = 0;
+                    for (int q : op_qubits(p->ops[j])) { qj |= 1ull << q; if (phys[q] >= L) gj |= 1ull << q; }
+                    if (__builtin_popcountll(bring | gj) > 8 || __builtin_popcountll(protect | qj) > L) break;
+                    bring |= gj;
+                    protect |= qj;
+                }
+                // victims: local positions holding unprotected qubits; least recently used first, positions >= 4
+                // before lower ones (large contiguous runs keep the exchange kernel streaming)
+                std::vector<int> cand;
+                for (int pp = 0; pp < L; ++pp) if (!((protect >> logi[pp]) & 1)) cand.push_back(pp);
+                std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+                    const bool lx = x < 4, ly = y < 4;
+                    if (lx != ly) return ly;
+                    return last[x] < last[y];
+                });
+                std::vector<int> glob;
+                for (int q = 0; q < n; ++q) if ((bring >> q) & 1) glob.push_back(phys[q]);
                 if (cand.size() < glob.size()) {
                     cudaFree(p->dbuf);
                     delete p;
-                    set_error("local_qubits = %d leaves too few idle local qubits for a %d-qubit pass", L, (int)qs.size());
+                    set_error("local_qubits = %d leaves too few idle local qubits for a %d-qubit pass", L, (int)op_qubits(op).size());
                     return QSIM_EINVAL;
                 }
                 std::vector<std::pair<int, int>> pairs;
-                for (size_t i = 0; i < glob.size(); ++i) pairs.push_back({cand[i], glob[i]});
+                for (size_t g = 0; g < glob.size(); ++g) pairs.push_back({cand[g], glob[g]});
                 emit_swaps(pairs);
             }
             for (int j = 0; j < op.k; ++j) { op.targets[j] = phys[op.targets[j]]; last[op.targets[j]] = clock; }

@@ -131,6 +131,7 @@ def test_diagonal_gates(qsim, dtype):
 # ---- qubit reorder --------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("pairs", [[(0, 13)], [(2, 3)], [(0, 5), (1, 14), (2, 9)], [(10, 11), (12, 13)],
+                                   [(4, 9), (5, 14), (15, 6)], [(3, 8), (4, 9), (5, 10), (6, 11)],
                                    [(0, 8), (1, 9), (2, 10), (3, 11), (4, 12), (5, 13), (6, 14), (7, 15)]])
 def test_swap_qubits_matches_swap_gates(qsim, dtype, pairs):
     n = 16
