@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of libqsim (declared in include/qsim.h): handles, argument validation, dispatch of
 // each gate to its kernel, and the readout entry points. No exception or CUDA error crosses the ABI: every
 // failure becomes a QSIM_E* code plus a thread-local message.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -173,7 +174,8 @@ int qsim_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream,
     }
     const uint64_t nseg = n > kSegBits ? (1ull << (n - kSegBits)) : 1ull;
     bool ok = cudaMalloc(&h->red.partials, sizeof(double) * kPartialDoubles) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->red.seg, sizeof(double) * 2 * nseg) == cudaSuccess;
+    const uint64_t nseg10 = n > 10 ? (1ull << (n - 10)) : 1ull;  // 1024-amplitude segments of the <Z> pass
+    ok = ok && cudaMalloc(&h->red.seg, sizeof(double) * std::max<uint64_t>(2 * nseg, nseg10)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->red.scan, sizeof(double) * (nseg + 8192)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->red.result, sizeof(double) * 256) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->red.hresult, sizeof(double) * 256) == cudaSuccess;

@@ -88,20 +88,44 @@ __global__ void __launch_bounds__(256) k_final_dd(const double* __restrict__ par
     }
 }
 
+// Amplitudes 2i and 2i+1 as float-float |a|^2 values (one 16-byte load for complex64).
+template <typename R>
+__device__ __forceinline__ void load_p2(const typename Amp<R>::T* psi, uint64_t i, ff& p0, ff& p1) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 v = reinterpret_cast<const float4*>(psi)[i];
+        p0 = ff_abs2(v.x, v.y);
+        p1 = ff_abs2(v.z, v.w);
+    } else {
+        const double2 a = psi[2 * i], b = psi[2 * i + 1];
+        const dd qa = Acc<double>::abs2(a.x, a.y), qb = Acc<double>::abs2(b.x, b.y);
+        const float ha = (float)qa.hi, hb = (float)qb.hi;
+        p0 = {ha, (float)(qa.hi - (double)ha + qa.lo)};
+        p1 = {hb, (float)(qb.hi - (double)hb + qb.lo)};
+    }
+}
+
 // ============================================================================================================
 // Norm and overlap
 // ============================================================================================================
+// sum |a|^2 over npairs amplitude pairs: four independent 16-byte loads in flight per thread.
 template <typename R>
-__global__ void __launch_bounds__(256) k_norm_partial(const typename Amp<R>::T* __restrict__ psi, uint64_t N, double* partials) {
+__global__ void __launch_bounds__(256) k_norm_pairs(const typename Amp<R>::T* __restrict__ psi, uint64_t npairs,
+                                                    double* partials) {
     __shared__ dd sm[32];
-    using A = typename Acc<R>::A;
-    A acc = Acc<R>::zero();
+    ff acc = {0.f, 0.f};
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const auto a = psi[i];
-        acc = Acc<R>::add(acc, Acc<R>::abs2(a.x, a.y));
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += 4 * stride) {
+        ff q[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t k = i + u * stride;
+            if (k < npairs) load_p2<R>(psi, k, q[2 * u], q[2 * u + 1]);
+            else q[2 * u] = q[2 * u + 1] = ff{0.f, 0.f};
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = ff_add(acc, q[u]);
     }
-    const dd r = block_sum_acc<R>(acc, sm);
+    const dd r = block_sum_acc<float>(acc, sm);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = r.hi;
         partials[2 * blockIdx.x + 1] = r.lo;
@@ -273,16 +297,6 @@ __global__ void __launch_bounds__(256) k_probs_small(const typename Amp<R>::T* _
     }
 }
 
-// ============================================================================================================
-// <Z_i> and <Z_i Z_{i+1}> in one pass. With p_x = |a_x|^2, T = sum p, S_i = sum p x_i and
-// X_i = sum p (x_i xor x_{i+1}): <Z_i> = T - 2 S_i, <Z_i Z_{i+1}> = T - 2 X_i.
-// Segment s (4096 amplitudes) is processed by one CTA; thread t reads amplitudes 2t + e + 512 j (e < 2,
-// j < 8), so index bits 1..8 come from t, bit 0 from e and bits 9..11 from j. Per segment the 24
-// quantities of bits 0..11 are block-reduced and accumulated per CTA; the segment total W[s] and its
-// S_11 part go to global memory, from which k_zstats_high forms the quantities of bits >= 12.
-// ============================================================================================================
-constexpr int kZQ = 24;
-
 template <typename R>
 __device__ __forceinline__ ff load_p(const typename Amp<R>::T* psi, uint64_t i) {
     const auto v = psi[i];
@@ -295,90 +309,91 @@ __device__ __forceinline__ ff load_p(const typename Amp<R>::T* psi, uint64_t i) 
     }
 }
 
+// ---- <Z> statistics with one warp per 1024-amplitude segment -------------------------------------------------
+// Lane l reads pairs l + 32 j (j < 16) of segment s, i.e. amplitudes x = 1024 s + 2 (l + 32 j) + e: index bit 0
+// is e, bits 1..5 are the lane, bits 6..9 are j. Every quantity of bits 0..9 accumulates per thread across all
+// its segments (no barrier per segment); X_9 (bits 9, 10) uses the segment's own split by bit 9; the segment
+// total goes to W[s] for the quantities of bits >= 10 (k_zstats_hi). Quantities per block at the end:
+// 0: T, 1..10: S_0..S_9, 11..20: X_0..X_9.
+constexpr int kZW = 21;
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_zstats_seg(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
-                                                    double* __restrict__ W, double* __restrict__ W11,
-                                                    double* __restrict__ partials) {
-    __shared__ ff sm[8][kZQ];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    dd cta = {0.0, 0.0};  // thread q < kZQ accumulates quantity q over this CTA's segments
-    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
-        const uint64_t base = (s << 12) + 2 * t;
-        ff P[8], Q[8];
+__global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
+                                                     double* __restrict__ W, double* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const ff Z = {0.f, 0.f};
+    ff T = Z, S0 = Z, S6 = Z, S7 = Z, S8 = Z, S9 = Z, X6 = Z, X7 = Z, X8 = Z, X9 = Z;
+    for (uint64_t s = warp0; s < nseg; s += nwarps) {
+        ff P[16], Q[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const ff p0 = load_p<R>(psi, base + 512 * j);
-            const ff p1 = load_p<R>(psi, base + 512 * j + 1);
-            Q[j] = p1;
-            P[j] = ff_add(p0, p1);
+        for (int j = 0; j < 16; ++j) load_p2<R>(psi, s * 512 + lane + 32 * j, P[j], Q[j]);  // P = even amp for now
+        ff Ts = Z, S9s = Z;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const ff pj = ff_add(P[j], Q[j]);
+            S0 = ff_add(S0, Q[j]);
+            Ts = ff_add(Ts, pj);
+            if (j & 1) S6 = ff_add(S6, pj);
+            if (j & 2) S7 = ff_add(S7, pj);
+            if (j & 4) S8 = ff_add(S8, pj);
+            if (j & 8) S9s = ff_add(S9s, pj);
+            if ((j ^ (j >> 1)) & 1) X6 = ff_add(X6, pj);
+            if (((j >> 1) ^ (j >> 2)) & 1) X7 = ff_add(X7, pj);
+            if (((j >> 2) ^ (j >> 3)) & 1) X8 = ff_add(X8, pj);
         }
-        ff T = P[0], S0 = Q[0];
-#pragma unroll
-        for (int j = 1; j < 8; ++j) { T = ff_add(T, P[j]); S0 = ff_add(S0, Q[j]); }
-        const ff S9 = ff_add(ff_add(P[1], P[3]), ff_add(P[5], P[7]));
-        const ff S10 = ff_add(ff_add(P[2], P[3]), ff_add(P[6], P[7]));
-        const ff S11 = ff_add(ff_add(P[4], P[5]), ff_add(P[6], P[7]));
-        const ff X9 = ff_add(ff_add(P[1], P[2]), ff_add(P[5], P[6]));
-        const ff X10 = ff_add(ff_add(P[2], P[3]), ff_add(P[4], P[5]));
-        const ff Z = {0.f, 0.f};
-        ff c[kZQ];
-        c[0] = T;
-        c[1] = S0;
-#pragma unroll
-        for (int i = 1; i <= 8; ++i) c[1 + i] = ((t >> (i - 1)) & 1) ? T : Z;
-        c[10] = S9; c[11] = S10; c[12] = S11;
-        c[13] = (t & 1) ? ff_add(T, ff_neg(S0)) : S0;
-#pragma unroll
-        for (int i = 1; i <= 7; ++i) c[13 + i] = (((t >> (i - 1)) ^ (t >> i)) & 1) ? T : Z;
-        c[21] = ((t >> 7) & 1) ? ff_add(T, ff_neg(S9)) : S9;
-        c[22] = X9;
-        c[23] = X10;
-#pragma unroll
-        for (int q = 0; q < kZQ; ++q) {
-            const ff v = warp_sum_ff(c[q]);
-            if (lane == 0) sm[warp][q] = v;
-        }
-        __syncthreads();
-        if (t < kZQ) {
-            ff v = sm[0][t];
-#pragma unroll
-            for (int w = 1; w < 8; ++w) v = ff_add(v, sm[w][t]);
-            const double vd = (double)v.hi + (double)v.lo;
-            cta = dd_add(cta, dd{vd, 0.0});
-            if (t == 0) W[s] = vd;
-            if (t == 12) W11[s] = vd;
-        }
-        __syncthreads();
+        T = ff_add(T, Ts);
+        S9 = ff_add(S9, S9s);
+        X9 = ff_add(X9, (s & 1) ? ff_add(Ts, ff_neg(S9s)) : S9s);
+        const ff tot = warp_sum_ff(Ts);
+        if (lane == 0) W[s] = (double)tot.hi + (double)tot.lo;
     }
-    if (t < kZQ) {
-        double* p = partials + 2 * ((int64_t)t * gridDim.x + blockIdx.x);
-        p[0] = cta.hi;
-        p[1] = cta.lo;
+    // per-thread contributions; lane bit b is index bit b + 1
+    ff c[kZW];
+    c[0] = T;
+    c[1] = S0;
+#pragma unroll
+    for (int i = 1; i <= 5; ++i) c[1 + i] = ((lane >> (i - 1)) & 1) ? T : Z;
+    c[7] = S6; c[8] = S7; c[9] = S8; c[10] = S9;
+    c[11] = (lane & 1) ? ff_add(T, ff_neg(S0)) : S0;
+#pragma unroll
+    for (int i = 1; i <= 4; ++i) c[11 + i] = (((lane >> (i - 1)) ^ (lane >> i)) & 1) ? T : Z;
+    c[16] = ((lane >> 4) & 1) ? ff_add(T, ff_neg(S6)) : S6;
+    c[17] = X6; c[18] = X7; c[19] = X8; c[20] = X9;
+    __shared__ ff sm[8][kZW];
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kZW; ++q) {
+        const ff v = warp_sum_ff(c[q]);
+        if (lane == 0) sm[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kZW) {
+        dd acc = {0.0, 0.0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            acc = dd_add(acc, dd{(double)sm[w][threadIdx.x].hi + (double)sm[w][threadIdx.x].lo, 0.0});
+        double* p = partials + 2 * ((int64_t)threadIdx.x * gridDim.x + blockIdx.x);
+        p[0] = acc.hi;
+        p[1] = acc.lo;
     }
 }
 
-__device__ __forceinline__ ff d2ff(double w) {
-    const float hi = (float)w;
-    return {hi, (float)(w - (double)hi)};
-}
-
-// Quantities of bits >= 12 from the segment totals W (one CTA per quantity; nh = n - 12):
-//   q < nh:            S_{12+q}      = sum_s W[s] bit_q(s)
-//   q == nh:           X_11          = sum_s (bit_0(s) ? W[s] - W11[s] : W11[s])
-//   nh < q < 2 nh:     X_{12+r}, r = q - nh - 1: sum_s W[s] (bit_r(s) xor bit_{r+1}(s))
-__global__ void __launch_bounds__(256) k_zstats_high(const double* __restrict__ W, const double* __restrict__ W11,
-                                                     uint64_t nseg, int nh, double* __restrict__ out) {
+// Quantities of bits >= B from the segment totals W (one CTA per quantity; nh = n - B):
+//   q < nh: S_{B+q} = sum_s W[s] bit_q(s);   nh <= q < 2 nh - 1: X_{B+r}, r = q - nh (bits r, r+1 of s).
+__global__ void __launch_bounds__(256) k_zstats_hi(const double* __restrict__ W, uint64_t nseg, int nh,
+                                                   double* __restrict__ out) {
     __shared__ dd sm[32];
     const int q = blockIdx.x;
     ff acc = {0.f, 0.f};
     for (uint64_t s = threadIdx.x; s < nseg; s += blockDim.x) {
-        if (q < nh) {
-            if ((s >> q) & 1) acc = ff_add(acc, d2ff(W[s]));
-        } else if (q == nh) {
-            acc = ff_add(acc, (s & 1) ? ff_add(d2ff(W[s]), ff_neg(d2ff(W11[s]))) : d2ff(W11[s]));
-        } else {
-            const int r = q - nh - 1;
-            if (((s >> r) ^ (s >> (r + 1))) & 1) acc = ff_add(acc, d2ff(W[s]));
+        bool use;
+        if (q < nh) use = (s >> q) & 1;
+        else { const int r = q - nh; use = ((s >> r) ^ (s >> (r + 1))) & 1; }
+        if (use) {
+            const double w = W[s];
+            const float hi = (float)w;
+            acc = ff_add(acc, ff{hi, (float)(w - (double)hi)});
         }
     }
     const dd v = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
@@ -416,16 +431,36 @@ __global__ void __launch_bounds__(256) k_zstats_small(const typename Amp<R>::T* 
 // Sampling: W[s] segment sums (2^SB amplitudes each), chunk sums of 1024 segments, inclusive scan of the
 // chunk sums; then one warp per uniform walks chunk -> segment -> amplitude.
 // ============================================================================================================
+// W[s] = sum of |a|^2 over segment s (2^SB amplitudes), one warp per segment, 16-byte loads eight at a time.
 template <typename R>
 __global__ void __launch_bounds__(256) k_segsum(const typename Amp<R>::T* __restrict__ psi, int SB, uint64_t nseg,
                                                 double* __restrict__ W) {
-    __shared__ dd sm[32];
-    const int S = 1 << SB;
-    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    if (SB == 0) {  // one amplitude per segment (n = 0 never happens; kept for completeness)
+        for (uint64_t s = warp0 * 32 + lane; s < nseg; s += nwarps * 32) {
+            const ff p = load_p<R>(psi, s);
+            W[s] = (double)p.hi + (double)p.lo;
+        }
+        return;
+    }
+    const uint64_t pairs = 1ull << (SB - 1);
+    for (uint64_t s = warp0; s < nseg; s += nwarps) {
         ff acc = {0.f, 0.f};
-        for (int i = threadIdx.x; i < S; i += blockDim.x) acc = ff_add(acc, load_p<R>(psi, (s << SB) + i));
-        const dd r = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
-        if (threadIdx.x == 0) W[s] = r.hi + r.lo;
+        for (uint64_t j = lane; j < pairs; j += 8 * 32) {
+            ff q[16];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t k = j + 32 * u;
+                if (k < pairs) load_p2<R>(psi, s * pairs + k, q[2 * u], q[2 * u + 1]);
+                else q[2 * u] = q[2 * u + 1] = ff{0.f, 0.f};
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc = ff_add(acc, q[u]);
+        }
+        const ff tot = warp_sum_ff(acc);
+        if (lane == 0) W[s] = (double)tot.hi + (double)tot.lo;
     }
 }
 
@@ -571,9 +606,9 @@ static int reduce_blocks(const DevInfo& d, uint64_t N, int nq) {
 
 cudaError_t run_norm(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d, double* out) {
     const uint64_t N = 1ull << n;
-    const int nb = reduce_blocks(d, N, 1);
-    if (dtype == QSIM_C64) k_norm_partial<float><<<nb, 256, 0, s>>>((const float2*)psi, N, r.partials);
-    else k_norm_partial<double><<<nb, 256, 0, s>>>((const double2*)psi, N, r.partials);
+    const int nb = reduce_blocks(d, N / 2, 1);
+    if (dtype == QSIM_C64) k_norm_pairs<float><<<nb, 256, 0, s>>>((const float2*)psi, N / 2, r.partials);
+    else k_norm_pairs<double><<<nb, 256, 0, s>>>((const double2*)psi, N / 2, r.partials);
     k_final_dd<<<1, 256, 0, s>>>(r.partials, nb, r.result);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -699,31 +734,22 @@ cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cuda
         for (int i = 0; i + 1 < n; ++i) zz[i] = T - 2.0 * (r.hresult[2 * (n + 1 + i)] + r.hresult[2 * (n + 1 + i) + 1]);
         return cudaSuccess;
     }
-    const uint64_t nseg = 1ull << (n - kSegBits);
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 6, (int64_t)nseg));
-    double* W = r.seg;
-    double* W11 = r.seg + nseg;
-    if (dtype == QSIM_C64) k_zstats_seg<float><<<nb, 256, 0, s>>>((const float2*)psi, nseg, W, W11, r.partials);
-    else k_zstats_seg<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, W11, r.partials);
-    k_final_dd<<<kZQ, 256, 0, s>>>(r.partials, nb, r.result);
-    const int nh = n - kSegBits;
-    if (nh > 0) k_zstats_high<<<2 * nh, 256, 0, s>>>(W, W11, nseg, nh, r.result + 2 * kZQ);
+    // warp segments of 1024 amplitudes (n >= 12 here): bits 0..9 per thread, bits >= 10 from W
+    const uint64_t nseg = 1ull << (n - 10);
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)((nseg + 7) / 8)));
+    double* W = r.seg;  // 2^(n-10) doubles
+    if (dtype == QSIM_C64) k_zstats_warp<float><<<nb, 256, 0, s>>>((const float2*)psi, nseg, W, r.partials);
+    else k_zstats_warp<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, r.partials);
+    k_final_dd<<<kZW, 256, 0, s>>>(r.partials, nb, r.result);
+    const int nh = n - 10;
+    if (nh > 0) k_zstats_hi<<<2 * nh - 1, 256, 0, s>>>(W, nseg, nh, r.result + 2 * kZW);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = fetch(r, 2 * kZQ + 4 * nh, s)) != cudaSuccess) return e;
+    if ((e = fetch(r, 2 * kZW + 2 * (2 * nh - 1), s)) != cudaSuccess) return e;
     const double* h = r.hresult;
     auto val = [&](int q) { return h[2 * q] + h[2 * q + 1]; };
     const double T = val(0);
-    for (int i = 0; i < n; ++i) {
-        const double Si = i < kSegBits ? val(1 + i) : val(kZQ + (i - kSegBits));
-        zi[i] = T - 2.0 * Si;
-    }
-    for (int i = 0; i + 1 < n; ++i) {
-        double Xi;
-        if (i <= 10) Xi = val(13 + i);
-        else if (i == 11) Xi = val(kZQ + nh);
-        else Xi = val(kZQ + nh + 1 + (i - 12));
-        zz[i] = T - 2.0 * Xi;
-    }
+    for (int i = 0; i < n; ++i) zi[i] = T - 2.0 * (i < 10 ? val(1 + i) : val(kZW + (i - 10)));
+    for (int i = 0; i + 1 < n; ++i) zz[i] = T - 2.0 * (i < 10 ? val(11 + i) : val(kZW + nh + (i - 10)));
     return cudaSuccess;
 }
 
@@ -740,7 +766,7 @@ cudaError_t run_sample(int dtype, const void* psi, int n, const double* u_dev, i
     const int nchunk = (int)((nseg + 1023) / 1024);
     double* W = r.seg;
     double* C = r.scan;
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)nseg));
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)((nseg + 7) / 8)));
     if (dtype == QSIM_C64) k_segsum<float><<<nb, 256, 0, s>>>((const float2*)psi, SB, nseg, W);
     else k_segsum<double><<<nb, 256, 0, s>>>((const double2*)psi, SB, nseg, W);
     k_chunksum<<<nchunk, 256, 0, s>>>(W, nseg, C);
