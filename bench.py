@@ -50,6 +50,8 @@ def parse_args():
     p.add_argument("--no-accuracy", action="store_true", help="skip the 20-qubit infidelity check")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--count", type=int, default=256, help="tfim_batch: number of circuits")
+    p.add_argument("--nmax", type=int, default=24, help="tfim_batch: largest circuit width")
     p.add_argument("--workload", default="brickwork30",
                    choices=["brickwork30", "qft28", "tfim_batch", "pairs34"],
                    help="brickwork30 (the headline line), qft28, tfim_batch (256 TFIM circuits), pairs34")
@@ -544,7 +546,7 @@ def run_tfim_batch(args):
     import torch
     import workloads as W
     from paper_2511_14664_gb300 import qsim
-    batch = W.tfim_batch(256, seed=4)
+    batch = W.tfim_batch(args.count, seed=4, nmax=args.nmax)
     cs = [c for c, _, _ in batch]
     gates = sum(len(c) for c in cs)
     t = time.perf_counter()
@@ -566,12 +568,12 @@ def run_tfim_batch(args):
     gbs = b.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9
     widths = sorted(set(c.n for c in cs))
     kmap = {str(n): chosen[[c.n for c in cs].index(n)] for n in widths}
-    line = _common_line("gate-applications/s, batch of 256 TFIM chains (10-24 qubits, 8-32 Trotter steps), "
-                        "complex64, one persistent launch", gates / (ms / 1000.0), UNIT, args, ms, "f32",
-                        {"workload": f"256 TFIM chains seed 4, {gates} gates, "
+    line = _common_line(f"gate-applications/s, batch of {len(cs)} TFIM chains (10-{args.nmax} qubits, 8-32 Trotter "
+                        "steps), complex64, one persistent launch", gates / (ms / 1000.0), UNIT, args, ms, "f32",
+                        {"workload": f"{len(cs)} TFIM chains seed 4, {gates} gates, "
                                      f"{sum(1 for c in cs if c.n > 13)} circuits > 13 qubits",
                          "fusion_k_by_width": kmap, "passes": b.info["passes"]},
-                        circuits_per_s=256 / (ms / 1000.0),
+                        circuits_per_s=len(cs) / (ms / 1000.0),
                         roofline={"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                   "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch",
                                   "note": "algorithmic bytes of the circuits > 13 qubits only; smaller ones stay "
