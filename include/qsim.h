@@ -267,9 +267,9 @@ int qsim_inner(qsim_h a, qsim_h b, double* out);
  * reason to need large GPU resources). Every circuit starts from |0...0> (complex64); widths 1..26, gates on
  * at most 4 qubits (targets plus controls). Each circuit is fused with width k (opts->max_fused; 0 = the
  * width chosen for its qubit count by qsim_batch_autotune, default 4), composed in FP64 on the device, and
- * run by one persistent launch of thread-block clusters: a cluster per circuit of 18 or more qubits (state in
- * the caller's workspace, passes separated by cluster barriers), then one CTA per narrower circuit (state in
- * the workspace for 14..17 qubits, entirely in shared memory for 13 or fewer). For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
+ * run by one persistent launch of thread-block clusters: a cluster per circuit of more than 13 qubits (its
+ * state in the caller's workspace, passes separated by cluster barriers), then one CTA per smaller circuit
+ * with the whole state in shared memory. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
  * <Z_q Z_{q+1}> at zz[zz_off(i) + q] (q < n_i - 1), the offsets being the running sums of n_i and n_i - 1
  * in input order; sums are compensated (float-float per thread, double-double across threads).
  */

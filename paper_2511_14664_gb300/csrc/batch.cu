@@ -4,13 +4,12 @@
 // Each circuit is fused on the host (greedy, width k chosen per circuit width by a built-in tuner or given),
 // every block is composed in FP64 on the device and stored as a complex64 matrix. One launch of k_batch then
 // runs everything:
-//   * a persistent grid of thread-block clusters (2-8 CTAs, the size that keeps the most CTAs resident);
-//     each cluster claims the next wide circuit (n >= 18) from a device counter, keeps its state in the caller's workspace, applies the passes with
+//   * a persistent grid of thread-block clusters (8 CTAs); each cluster claims the next large circuit
+//     (n >= 14) from a device counter, keeps its state in the caller's workspace, applies the passes with
 //     hardware cluster barriers between them, and reduces <Z_i>, <Z_i Z_{i+1}> across the cluster through
 //     distributed shared memory;
-//   * once that queue is empty, every CTA claims narrower circuits one at a time: 14..17 qubits with the
-//     state in the workspace (L2-resident, __syncthreads between passes), <= 13 qubits entirely in its
-//     shared memory (64 KiB), with no global traffic for the state at all.
+//   * once the large queue is empty, every CTA claims small circuits (n <= 13) one at a time and runs each
+//     entirely in its shared memory (64 KiB), with no global traffic for the state at all.
 // There are no spin waits: the only waits are hardware barriers (__syncthreads, cluster barriers).
 #include <cooperative_groups.h>
 
@@ -31,10 +30,10 @@ namespace cg = cooperative_groups;
 namespace qsim {
 namespace batch {
 
+constexpr int kCluster = 8;
 constexpr int kThreads = 256;
 constexpr int kKmax = 4;
-constexpr int kSmallMax = 13;    // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
-constexpr int kClusterMin = 18;  // circuits this wide or wider get a whole cluster; narrower ones one CTA
+constexpr int kSmallMax = 13;  // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
 
 struct Pass {
     int k;
@@ -50,13 +49,13 @@ struct Circ {
 };
 struct Args {
     const Pass* passes;
-    const Circ* circs;  // cluster circuits first, then one-CTA circuits (global-memory ones before shared-memory ones)
+    const Circ* circs;  // large circuits first, then small ones
     int nlarge, nsmall;
     const float2* mats;
     float2* ws;
     double* zi;
     double* zz;
-    int* counters;  // [0] next cluster circuit, [1] next one-CTA circuit
+    int* counters;  // [0] next large circuit, [1] next small circuit
 };
 
 struct Shared {
@@ -231,7 +230,7 @@ __device__ void write_z(const dd* red, int n, double* zi, double* zz) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(kThreads, 1) k_batch(const __grid_constant__ Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -270,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ A
         if (rank == 0) write_z(sh.red, c.n, a.zi + c.zi_off, a.zz + c.zz_off);
     }
 
-    // ---- narrower circuits: one CTA each, the state in shared memory (<= 13 qubits) or in the workspace ---
+    // ---- small circuits: one CTA per circuit, the state in shared memory ---------------------------------
     while (true) {
         if (t == 0) sh.claim = atomicAdd(&a.counters[1], 1);
         __syncthreads();
@@ -278,16 +277,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ A
         __syncthreads();
         if (idx >= a.nsmall) break;
         const Circ c = a.circs[a.nlarge + idx];
-        float2* psi = c.state_off >= 0 ? a.ws + c.state_off : sh.state;
-        const uint64_t N = 1ull << c.n;
-        for (uint64_t i = t; i < N; i += kThreads) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+        float2* psi = sh.state;
+        const int N = 1 << c.n;
+        for (int i = t; i < N; i += kThreads) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         for (int p = 0; p < c.npass; ++p) {
             const Pass P = a.passes[c.first_pass + p];
             const int DD = 1 << (2 * P.k);
             for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
             __syncthreads();
             apply_pass(psi, c.n, P, sh.U, t, kThreads);
-            __syncthreads();  // also orders this CTA's global-memory stores before the next pass reads them
+            __syncthreads();
         }
         if (c.n >= 12) zstats_segments(psi, c.n, 0, 1, sh);
         else zstats_serial(psi, c.n, sh);
@@ -317,7 +316,6 @@ struct qsim_batch {
     size_t ws_need = 0;
     int total_zi = 0, total_zz = 0;
     int grid = 0;
-    int cluster = 8;
     qsim_plan_info info{};
     cudaGraphExec_t gexec = nullptr;
     void* gws = nullptr;
@@ -443,23 +441,18 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     b->total_zi = zio;
     b->total_zz = zzo;
     std::vector<int> large, small;
-    for (int i = 0; i < count; ++i) (cs[i].n >= batch::kClusterMin ? large : small).push_back(i);
-    auto work = [&](int x) { return std::ldexp((double)circs[x].npass, circs[x].n); };
-    std::stable_sort(large.begin(), large.end(), [&](int x, int y) { return work(x) > work(y); });
-    std::stable_sort(small.begin(), small.end(), [&](int x, int y) { return work(x) > work(y); });
+    for (int i = 0; i < count; ++i) (cs[i].n > batch::kSmallMax ? large : small).push_back(i);
+    std::stable_sort(large.begin(), large.end(), [&](int x, int y) {
+        return std::ldexp((double)circs[x].npass, circs[x].n) > std::ldexp((double)circs[y].npass, circs[y].n);
+    });
     size_t wsoff = 0;
     std::vector<batch::Circ> ordered;
-    auto place = [&](int i) {
-        if (circs[i].n > batch::kSmallMax) {
-            circs[i].state_off = (int64_t)(wsoff / 8);
-            wsoff += (small_state_bytes(circs[i].n) + 255) & ~(size_t)255;
-        } else {
-            circs[i].state_off = -1;
-        }
+    for (int i : large) {
+        circs[i].state_off = (int64_t)(wsoff / 8);
+        wsoff += (small_state_bytes(circs[i].n) + 255) & ~(size_t)255;
         ordered.push_back(circs[i]);
-    };
-    for (int i : large) place(i);
-    for (int i : small) place(i);
+    }
+    for (int i : small) { circs[i].state_off = -1; ordered.push_back(circs[i]); }
     b->nlarge = (int)large.size();
     b->nsmall = (int)small.size();
     b->ws_need = wsoff;
@@ -494,32 +487,27 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         e = launch_convert_matrix(QSIM_C64, reinterpret_cast<double*>(base + o_out), base + o_mat, 2 * compose_out, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batch::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(batch::Shared));
-    // cluster size: the one that keeps the most CTAs resident (larger clusters first on ties)
-    int best_cl = 0, best_ctas = 0;
-    for (int cl : {8, 4, 2}) {
-        if (e != cudaSuccess) break;
+    int nclusters = 0;
+    if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.x = batch::kCluster;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(cl, 1, 1);
+        cfg.gridDim = dim3(batch::kCluster, 1, 1);
         cfg.blockDim = dim3(batch::kThreads, 1, 1);
         cfg.dynamicSmemBytes = sizeof(batch::Shared);
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        int ncl = 0;
-        e = cudaOccupancyMaxActiveClusters(&ncl, batch::k_batch, &cfg);
-        if (e == cudaSuccess && ncl * cl > best_ctas) { best_ctas = ncl * cl; best_cl = cl; }
+        e = cudaOccupancyMaxActiveClusters(&nclusters, batch::k_batch, &cfg);
     }
-    if (e != cudaSuccess || best_ctas < 1) {
+    if (e != cudaSuccess || nclusters < 1) {
         cudaFree(b->dbuf);
         delete b;
-        return e != cudaSuccess ? cuda_fail(e, "batch plan preparation") : (set_error("no thread-block cluster fits"), QSIM_EUNSUPPORTED);
+        return e != cudaSuccess ? cuda_fail(e, "batch plan preparation") : (set_error("no cluster of %d CTAs fits", batch::kCluster), QSIM_EUNSUPPORTED);
     }
-    b->cluster = best_cl;
-    b->grid = best_ctas;
+    b->grid = nclusters * batch::kCluster;
     b->args.passes = reinterpret_cast<const batch::Pass*>(base + o_pass);
     b->args.circs = reinterpret_cast<const batch::Circ*>(base + o_circ);
     b->args.nlarge = b->nlarge;
@@ -547,7 +535,7 @@ static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = b->cluster;
+    attr[0].val.clusterDim.x = batch::kCluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(b->grid, 1, 1);
