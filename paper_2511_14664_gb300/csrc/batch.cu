@@ -4,7 +4,8 @@
 // Each circuit is fused on the host (greedy, width k chosen per circuit width by a built-in tuner or given),
 // every block is composed in FP64 on the device and stored as a complex64 matrix. One launch of k_batch then
 // runs everything:
-//   * a persistent grid of thread-block clusters (8 CTAs); each cluster claims the next large circuit
+//   * a persistent grid of thread-block clusters (16 CTAs where the device co-schedules them, else 8);
+//     each cluster claims the next large circuit
 //     (n >= 14) from a device counter, keeps its state in the caller's workspace, applies the passes with
 //     hardware cluster barriers between them, and reduces <Z_i>, <Z_i Z_{i+1}> across the cluster through
 //     distributed shared memory;
@@ -30,7 +31,6 @@ namespace cg = cooperative_groups;
 namespace qsim {
 namespace batch {
 
-constexpr int kCluster = 8;
 constexpr int kThreads = 256;
 constexpr int kKmax = 4;
 constexpr int kSmallMax = 13;  // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
@@ -316,6 +316,7 @@ struct qsim_batch {
     size_t ws_need = 0;
     int total_zi = 0, total_zz = 0;
     int grid = 0;
+    int cluster = 8;
     qsim_plan_info info{};
     cudaGraphExec_t gexec = nullptr;
     void* gws = nullptr;
@@ -487,27 +488,36 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         e = launch_convert_matrix(QSIM_C64, reinterpret_cast<double*>(base + o_out), base + o_mat, 2 * compose_out, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(batch::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(batch::Shared));
-    int nclusters = 0;
-    if (e == cudaSuccess) {
+    // Cluster size: the widest circuits set the makespan, so prefer 16 CTAs (non-portable size, one CTA per
+    // SM) when the device co-schedules enough of them, else 8.
+    int nclusters = 0, clsize = 0;
+    if (e == cudaSuccess && cudaFuncSetAttribute(batch::k_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int cl : {16, 8}) {
+        if (e != cudaSuccess) break;
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = batch::kCluster;
+        attr[0].val.clusterDim.x = cl;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(batch::kCluster, 1, 1);
+        cfg.gridDim = dim3(cl, 1, 1);
         cfg.blockDim = dim3(batch::kThreads, 1, 1);
         cfg.dynamicSmemBytes = sizeof(batch::Shared);
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(&nclusters, batch::k_batch, &cfg);
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, batch::k_batch, &cfg) != cudaSuccess) { cudaGetLastError(); ncl = 0; }
+        if (ncl * cl >= 128) { nclusters = ncl; clsize = cl; break; }
+        if (ncl * cl > nclusters * clsize) { nclusters = ncl; clsize = cl; }
     }
     if (e != cudaSuccess || nclusters < 1) {
         cudaFree(b->dbuf);
         delete b;
-        return e != cudaSuccess ? cuda_fail(e, "batch plan preparation") : (set_error("no cluster of %d CTAs fits", batch::kCluster), QSIM_EUNSUPPORTED);
+        return e != cudaSuccess ? cuda_fail(e, "batch plan preparation") : (set_error("no thread-block cluster fits"), QSIM_EUNSUPPORTED);
     }
-    b->grid = nclusters * batch::kCluster;
+    b->cluster = clsize;
+    b->grid = nclusters * clsize;
     b->args.passes = reinterpret_cast<const batch::Pass*>(base + o_pass);
     b->args.circs = reinterpret_cast<const batch::Circ*>(base + o_circ);
     b->args.nlarge = b->nlarge;
@@ -535,7 +545,7 @@ static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = batch::kCluster;
+    attr[0].val.clusterDim.x = b->cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(b->grid, 1, 1);
