@@ -61,6 +61,7 @@ struct Args {
 struct Shared {
     float2 state[1 << kSmallMax];
     float2 U[1 << (2 * kKmax)];
+    uint64_t off[1 << kKmax];  // gather offsets of the current pass
     ff seg[8][24];
     double segT, segS11;
     dd red[64];
@@ -69,16 +70,32 @@ struct Shared {
 
 // ---- dense pass: groups g0, g0 + stride, ... of psi (global or shared memory) ---------------------------
 template <int K>
-__device__ __noinline__ void apply_dense(float2* psi, int n, const int* tg, const float2* U, uint64_t g0, uint64_t stride) {
+__device__ __noinline__ void apply_dense(float2* psi, int n, const int* tg, const float2* U, const uint64_t* off,
+                                        uint64_t g0, uint64_t stride) {
     constexpr int D = 1 << K;
     const uint64_t G = 1ull << (n - K);
-    uint64_t off[D];
+    if (tg[0] >= 1 && G >= 2) {
+        // qubit 0 is not a target: groups 2h and 2h+1 are adjacent amplitudes, one 16-byte vector each
+        for (uint64_t h = g0; h < G / 2; h += stride) {
+            const uint64_t base = insert_zeros(2 * h, tg, K);
+            float4 v[D];
 #pragma unroll
-    for (int m = 0; m < D; ++m) {
-        uint64_t o = 0;
+            for (int m = 0; m < D; ++m) v[m] = *reinterpret_cast<const float4*>(psi + base + off[m]);
 #pragma unroll
-        for (int j = 0; j < K; ++j) o |= (uint64_t)((m >> j) & 1) << tg[j];
-        off[m] = o;
+            for (int r = 0; r < D; ++r) {
+                float r0 = 0.f, i0 = 0.f, r1 = 0.f, i1 = 0.f;
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    const float2 u = U[r * D + c];
+                    r0 = __fmaf_rn(u.x, v[c].x, r0); r0 = __fmaf_rn(-u.y, v[c].y, r0);
+                    i0 = __fmaf_rn(u.x, v[c].y, i0); i0 = __fmaf_rn(u.y, v[c].x, i0);
+                    r1 = __fmaf_rn(u.x, v[c].z, r1); r1 = __fmaf_rn(-u.y, v[c].w, r1);
+                    i1 = __fmaf_rn(u.x, v[c].w, i1); i1 = __fmaf_rn(u.y, v[c].z, i1);
+                }
+                *reinterpret_cast<float4*>(psi + base + off[r]) = make_float4(r0, i0, r1, i1);
+            }
+        }
+        return;
     }
     for (uint64_t g = g0; g < G; g += stride) {
         const uint64_t base = insert_zeros(g, tg, K);
@@ -101,12 +118,25 @@ __device__ __noinline__ void apply_dense(float2* psi, int n, const int* tg, cons
     }
 }
 
-__device__ __noinline__ void apply_pass(float2* psi, int n, const Pass& P, const float2* U, uint64_t g0, uint64_t stride) {
+__device__ __noinline__ void apply_pass(float2* psi, int n, const Pass& P, const float2* U, const uint64_t* off,
+                                       uint64_t g0, uint64_t stride) {
     switch (P.k) {
-        case 1: apply_dense<1>(psi, n, P.targets, U, g0, stride); break;
-        case 2: apply_dense<2>(psi, n, P.targets, U, g0, stride); break;
-        case 3: apply_dense<3>(psi, n, P.targets, U, g0, stride); break;
-        default: apply_dense<4>(psi, n, P.targets, U, g0, stride); break;
+        case 1: apply_dense<1>(psi, n, P.targets, U, off, g0, stride); break;
+        case 2: apply_dense<2>(psi, n, P.targets, U, off, g0, stride); break;
+        case 3: apply_dense<3>(psi, n, P.targets, U, off, g0, stride); break;
+        default: apply_dense<4>(psi, n, P.targets, U, off, g0, stride); break;
+    }
+}
+
+// Load a pass's matrix and gather offsets into shared memory (the caller synchronises afterwards).
+__device__ __forceinline__ void load_pass(const Args& a, const Pass& P, Shared& sh) {
+    const int t = threadIdx.x;
+    const int DD = 1 << (2 * P.k);
+    for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
+    if (t < (1 << P.k)) {
+        uint64_t o = 0;
+        for (int j = 0; j < P.k; ++j) o |= (uint64_t)((t >> j) & 1) << P.targets[j];
+        sh.off[t] = o;
     }
 }
 
@@ -230,7 +260,7 @@ __device__ void write_z(const dd* red, int n, double* zi, double* zz) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_batch(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shared& sh = *reinterpret_cast<Shared*>(smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -252,10 +282,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(const __grid_constant__ A
         cl.sync();
         for (int p = 0; p < c.npass; ++p) {
             const Pass P = a.passes[c.first_pass + p];
-            const int DD = 1 << (2 * P.k);
-            for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
+            load_pass(a, P, sh);
             __syncthreads();
-            apply_pass(psi, c.n, P, sh.U, gid, gstride);
+            apply_pass(psi, c.n, P, sh.U, sh.off, gid, gstride);
             cl.sync();  // release / acquire at cluster scope: the next pass sees every CTA's stores
         }
         zstats_segments(psi, c.n, rank, CL, sh);
@@ -282,10 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(const __grid_constant__ A
         for (int i = t; i < N; i += kThreads) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         for (int p = 0; p < c.npass; ++p) {
             const Pass P = a.passes[c.first_pass + p];
-            const int DD = 1 << (2 * P.k);
-            for (int i = t; i < DD; i += kThreads) sh.U[i] = a.mats[P.mat_off + i];
+            load_pass(a, P, sh);
             __syncthreads();
-            apply_pass(psi, c.n, P, sh.U, t, kThreads);
+            apply_pass(psi, c.n, P, sh.U, sh.off, t, kThreads);
             __syncthreads();
         }
         if (c.n >= 12) zstats_segments(psi, c.n, 0, 1, sh);
