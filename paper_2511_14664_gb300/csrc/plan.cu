@@ -57,6 +57,42 @@ namespace qsim {
 
 static inline int popcnt(uint64_t v) { return __builtin_popcountll(v); }
 
+// One block: scan the unplaced gates in order and absorb every gate that is not blocked by an earlier
+// unplaced gate on a shared qubit (a diagonal gate is blocked only by non-diagonal ones) and that fits: with
+// a fixed window W, gates whose qubits lie inside W; otherwise (W = 0) gates that keep the growing qubit set
+// within kmax qubits, starting from `seed`.
+static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
+                                    const std::vector<char>& done, int first, int seed, uint64_t W, int kmax) {
+    const int G = (int)gmask.size();
+    std::vector<int> blk;
+    uint64_t Q = 0, bany = 0, bdiag = 0;
+    if (seed >= 0) { blk.push_back(seed); Q = gmask[seed]; }
+    for (int i = first; i < G; ++i) {
+        if (done[i] || i == seed) continue;
+        const uint64_t qs = gmask[i];
+        const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
+        const bool fits = W ? (qs & ~W) == 0 : popcnt(Q | qs) <= kmax;
+        if (!blocked && fits) {
+            blk.push_back(i);
+            Q |= qs;
+        } else if (gdiag[i]) {
+            bdiag |= qs;
+        } else {
+            bany |= qs;
+        }
+        // nothing further can join once every qubit a new gate could use is blocked by a non-diagonal gate
+        const uint64_t usable = W ? W : (popcnt(Q) >= kmax ? Q : ~0ull);
+        if ((usable & ~bany) == 0) break;
+    }
+    std::sort(blk.begin(), blk.end());
+    return blk;
+}
+
+// Fusion into blocks of at most kmax qubits. Each block is the largest (most gates) of these candidates:
+// every window of kmax consecutive qubits (all available gates inside it), and, for every qubit, its
+// earliest unplaced gate when no earlier unplaced gate blocks it, grown greedily. The plain greedy choice
+// (seeded at the earliest unplaced gate) is one of the candidates. On nearest-neighbour circuits the
+// windows tile the (qubit, time) plane in diamonds, about twice the gates per block of the plain greedy.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
                                           int kmax) {
     const int G = (int)gmask.size();
@@ -66,28 +102,34 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
     while (true) {
         while (first < G && done[first]) ++first;
         if (first >= G) break;
-        uint64_t Q = 0, bany = 0, bdiag = 0;
-        std::vector<int> blk;
-        for (int i = first; i < G; ++i) {
-            if (done[i]) continue;
-            const uint64_t qs = gmask[i];
-            const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
-            if (!blocked && popcnt(Q | qs) <= kmax) {
-                blk.push_back(i);
-                done[i] = 1;
-                Q |= qs;
-            } else if (blk.empty()) {  // wider than the fusion width: a block of its own
-                blk.push_back(i);
-                done[i] = 1;
-                break;
-            } else if (gdiag[i]) {
-                bdiag |= qs;
-            } else {
-                bany |= qs;
+        std::vector<int> best;
+        if (popcnt(gmask[first]) > kmax) {
+            best.push_back(first);  // wider than the fusion width: a block of its own
+        } else {
+            // windows
+            const int wmax = std::min(kmax, n);
+            for (int a0 = 0; a0 + wmax <= n; ++a0) {
+                const uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
+                auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax);
+                if (blk.size() > best.size()) best.swap(blk);
             }
-            if (popcnt(bany) == n) break;
+            // seeds: the earliest unplaced gate of every qubit line, if nothing earlier blocks it
+            uint64_t seen = 0, bany = 0, bdiag = 0;
+            for (int i = first; i < G && popcnt(seen) < n; ++i) {
+                if (done[i]) continue;
+                const uint64_t qs = gmask[i];
+                const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
+                if ((qs & ~seen) && !blocked && popcnt(qs) <= kmax) {
+                    auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax);
+                    if (blk.size() > best.size()) best.swap(blk);
+                }
+                seen |= qs;
+                if (gdiag[i]) bdiag |= qs; else bany |= qs;
+            }
+            if (best.empty()) best.push_back(first);
         }
-        blocks.push_back(std::move(blk));
+        for (int i : best) done[i] = 1;
+        blocks.push_back(std::move(best));
     }
     return blocks;
 }
