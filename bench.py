@@ -366,7 +366,9 @@ def run_ours(args):
                 continue
             variants[name] = {"ms_per_step": quick(name), "passes": len(plans[name].pass_list)}
     if args.path == "auto":
-        ok = [k for k in variants if (not acc or acc[k]["infidelity"] <= 1e-9)]
+        # equal accuracy: infidelity on the 20-qubit instance at least 10x inside the 1e-9 bar, since the
+        # 30-qubit state itself cannot be checked against the oracle
+        ok = [k for k in variants if (not acc or acc[k]["infidelity"] <= 1e-10)]
         main = min(ok, key=lambda k: variants[k]["ms_per_step"]) if ok else ("tf32x3" if "tf32x3" in plans else "simt4")
     else:
         main = args.path
@@ -450,7 +452,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if main in ("plain", "simt4", "simt5") else {"tf32x3": "tf32x3", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}[main],
+        "dtype": "f32" if main in ("plain", "simt4", "simt5") else {"tf32x3": "tf32", "bf16x3": "bf16", "bf16x6": "bf16"}[main],
+        "precision": main,
         "data": "synthetic",
         "config": {"workload": f"random brickwork n={n} depth={depth} seed={SEED}(+rank), {G} gates, complex64",
                    "path": main, "passes": len(plan.pass_list), "global_batch": ws, "seq_len": None,
