@@ -45,7 +45,7 @@ def parse_args():
     p.add_argument("--n", type=int, default=30)
     p.add_argument("--depth", type=int, default=40)
     p.add_argument("--shots", type=int, default=1000)
-    p.add_argument("--path", default="auto", help="auto | plain | simt4 | simt5 | tf32x3 | bf16x3 | bf16x6")
+    p.add_argument("--path", default="auto", help="auto | " + " | ".join(PATHS))
     p.add_argument("--no-variants", action="store_true", help="skip the secondary path measurements")
     p.add_argument("--no-accuracy", action="store_true", help="skip the 20-qubit infidelity check")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -196,6 +196,8 @@ PATHS = {
     "tf32x3": (1, 6, 1, 5),
     "bf16x3": (1, 6, 2, 5),
     "bf16x6": (1, 6, 3, 5),
+    "tf32x3_k5": (1, 5, 1, 5),
+    "bf16x6_k5": (1, 5, 3, 5),
 }
 
 
@@ -337,7 +339,7 @@ def run_ours(args):
     st = qsim.State(n, qsim.C64)
 
     # candidate paths (tensor-core variants only where the library supports them)
-    cands = ["tf32x3", "bf16x3", "bf16x6", "simt4", "simt5"]
+    cands = ["tf32x3", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
     plans = {}
     for name in cands + ["plain"]:
         try:
@@ -452,7 +454,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if main in ("plain", "simt4", "simt5") else {"tf32x3": "tf32", "bf16x3": "bf16", "bf16x6": "bf16"}[main],
+        "dtype": "f32" if main in ("plain", "simt4", "simt5") else main[:4],
         "precision": main,
         "data": "synthetic",
         "config": {"workload": f"random brickwork n={n} depth={depth} seed={SEED}(+rank), {G} gates, complex64",

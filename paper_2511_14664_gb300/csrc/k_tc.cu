@@ -9,14 +9,18 @@
 // both operands (Ootomo & Yokota 2022 for 3xTF32; Henry, Tang & Heinecke 2019 for BF16x3 / BF16x6), with
 // FP32 accumulation in tensor memory.
 //
-// Data flow per CTA (one per SM, persistent over tiles; 16 warps, warp w serves TMEM lanes 32 (w mod 4)..):
-//   B planes (the split U, pre-swizzled in global memory) -> shared memory once, SWIZZLE_128B K-major;
-//   tile t: coalesced loads into registers (issued one tile ahead; 16-byte vectors when qubit 0 is the
-//   block's first target), split into hi / lo (/ mid) planes, tcgen05.st into TMEM as the A operand; one
-//   thread issues the MMAs (A from TMEM, B from shared memory) into one of two TMEM accumulators and commits
-//   them to an mbarrier; while the tensor cores work on tile t the warps load tile t+1 and run the epilogue
-//   of tile t-1 (tcgen05.ld of the other accumulator, stores back in place). Every wait on the mbarrier is bounded (2 s); on expiry the kernel records
-//   DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory and returns.
+// Data flow per CTA (one per SM, persistent over tiles). B planes (the split U, pre-swizzled in global
+// memory) go to shared memory once, SWIZZLE_128B K-major. Every wait on an mbarrier is bounded (2 s); on
+// expiry the kernel records DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory
+// and returns.
+//   TF32 (k_tc_block): warp-specialised. Eight data warps (two per TMEM lane quadrant) load tiles into
+//   registers (coalesced; 16-byte vectors when qubit 0 is the block's first target; one tile ahead at K = 6,
+//   two at K = 5), split them into the lo and hi planes of the A operand in TMEM and run the epilogue
+//   (tcgen05.ld of the finished accumulator, stores back in place); a ninth warp issues the MMAs. The lo
+//   plane's product and the hi plane's products of a tile are separate phases with their own barriers, so
+//   the split of one plane overlaps the MMAs on the other, and two TMEM accumulators let the epilogue of
+//   tile t-1 overlap the MMAs of tile t.
+//   BF16 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -140,6 +144,16 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
     }
 }
 
+// TF32 MMA with the shared-memory descriptor given as its two 32-bit halves (the low half carries the
+// address field, so per-K-step offsets are one 32-bit add).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_lo, uint32_t b_hi,
+                                            uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 bd;\n\tsetp.ne.b32 p, %5, 0;\n\tmov.b64 bd, {%2, %3};\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], bd, %4, p;\n}"
+        :: "r"(d_tmem), "r"(a_tmem), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc) : "memory");
+}
+
 template <int N>
 __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&v)[N]) {
     if constexpr (N == 8) tmem_st_x8(taddr, v);
@@ -164,40 +178,55 @@ struct Args {
     uint64_t ntiles;
 };
 
+// TF32 variant, warp-specialised: warps 0..7 move data (tile loads, hi / lo split into TMEM, epilogue), warp
+// 8 issues the MMAs. They hand off through four mbarriers: full_lo / full_hi (one arrival per data warp once
+// its part of an A plane is in TMEM) and empty_lo / empty_hi (tcgen05.commit after the MMAs that read the
+// plane). The hi commit follows every MMA of a tile, so it also marks that tile's accumulator final.
+constexpr int kDataWarps = 8;  // two per TMEM lane quadrant; 9 warps leave room for a two-tile prefetch
+constexpr int kThreadsWS = (kDataWarps + 1) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(addr) : "memory");
+}
+
 template <int K, int PREC, bool P0>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
     using C = Cfg<PREC>;
-    constexpr bool BF16 = C::esize == 2;
+    static_assert(C::esize == 4 && C::planes == 2, "the TF32 hi / lo split");
     constexpr int D = 1 << K, NR = 2 * D;
-    constexpr int PB = plane_bytes(K, C::esize);
+    constexpr int PB = plane_bytes(K, 4);
     constexpr int ATOM = NR * 128;                         // bytes of one 128-byte-wide K atom (all NR rows)
-    constexpr int KSTEPS = NR * C::esize / 32;             // each MMA consumes 32 bytes of K
-    constexpr int CPT = D / 4;                             // complex columns per thread (4 warps per quadrant)
-    constexpr int ACOLS = BF16 ? NR / 2 : NR;              // TMEM columns per A plane
-    constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A planes after
-    constexpr uint32_t TCOLS = pow2_at_least(A0 + C::planes * ACOLS);
-    constexpr int AV = BF16 ? CPT : 2 * CPT;               // 32-bit values per thread per A plane
-    constexpr uint32_t IDESC = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
-                               ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    constexpr int KSTEPS = NR * 4 / 32;                    // each MMA consumes 32 bytes of K
+    constexpr int CPT = D / 2;                             // complex columns per thread (2 warps per quadrant)
+    constexpr int QC = 8;                                  // columns per tcgen05.st / tcgen05.ld (16 values)
+    constexpr int ACOLS = NR;                              // TMEM columns per A plane
+    constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A_hi, A_lo
+    constexpr uint32_t TCOLS = pow2_at_least(A0 + 2 * ACOLS);
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    static_assert(CPT % QC == 0, "whole chunks per thread");
+    constexpr int DEPTH = K >= 6 ? 1 : 2;                  // tiles of loads in flight (registers: CPT x 2 each)
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + C::planes * PB);
-    uint64_t* mbar = sCol + D;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
+    uint64_t* mbar = sCol + D;                             // empty_lo, empty_hi, full_lo, full_hi
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
-    const int c0 = (warp >> 2) * CPT;
+    const int c0 = ((warp >> 2) & 1) * CPT;
     const int r = quad * 32 + lane;
 
-    // B planes -> shared memory (already in the swizzled byte layout), column offsets, barrier, TMEM.
-    for (int i = tid; i < C::planes * PB / 16; i += kThreads) reinterpret_cast<uint4*>(sb)[i] = bops[i];
-    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    // B planes -> shared memory (already in the swizzled byte layout), column offsets, barriers, TMEM.
+    for (int i = tid; i < 2 * PB / 16; i += kThreadsWS) reinterpret_cast<uint4*>(sb)[i] = bops[i];
+    for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1) : "memory");
+        for (int j = 0; j < 4; ++j)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                         :: "r"(smem_u32(mbar + j)), "r"(j < 2 ? 1 : kDataWarps) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make B visible to the tensor cores
@@ -210,132 +239,180 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint32_t mbar_addr = smem_u32(mbar);
-    const uint32_t sB = smem_u32(sb);
-    const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+    const uint32_t empty_lo = smem_u32(mbar), empty_hi = smem_u32(mbar + 1);
+    const uint32_t full_lo = smem_u32(mbar + 2), full_hi = smem_u32(mbar + 3);
+    const uint64_t t0 = blockIdx.x, G = gridDim.x;
+    const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
 
-    // Thread (r, columns c0..c0+CPT) of a tile. With P0 (qubit 0 is target 0) columns 2i and 2i+1 are
-    // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
-    float2 X[CPT];
-    auto load_tile = [&](uint64_t t) {
-        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-        if constexpr (P0) {
+    if (warp == kDataWarps) {
+        // ---- MMA issuer (one thread) ----
+        if (lane == 0) {
+            const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
+            const uint32_t dhi = (uint32_t)(desc0 >> 32);
+            // The products of one A plane, smallest first as listed in Cfg; lo * hi starts the accumulator.
+            // Descriptor offsets are compile-time constants added to the address field (shared-memory
+            // addresses stay below 2^18 bytes, so the 14-bit field cannot carry). The base is passed through
+            // an empty asm so that the 16 to 32 descriptors are formed at each use rather than held in
+            // registers across the loop.
+            auto issue = [&](int plane, uint32_t dcol) {
+                uint32_t dlo = (uint32_t)desc0, tb = tbase;
+                asm volatile("" : "+r"(dlo), "+r"(tb));
+                uint32_t acc = plane ? 0u : 1u;
 #pragma unroll
-            for (int j = 0; j < CPT; j += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(psi + b + sCol[c0 + j]);
-                X[j] = make_float2(v.x, v.y);
-                X[j + 1] = make_float2(v.z, v.w);
+                for (int pr = 0; pr < C::nprod; ++pr) {
+                    if (C::pa(pr) != plane) continue;
+                    const uint32_t acol = tb + A0 + C::pa(pr) * ACOLS;
+#pragma unroll
+                    for (int s = 0; s < KSTEPS; ++s) {
+                        const uint32_t off = (uint32_t)(C::pb(pr) * PB + (s >> 2) * ATOM + (s & 3) * 32);
+                        mma_tf32_ts(tb + dcol, acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
+                        acc = 1;
+                    }
+                }
+            };
+            uint32_t last_bar = 0, last_par = 0;
+            bool bad = false;
+            for (uint64_t i = 0; i < m; ++i) {
+                const uint32_t dcol = (i & 1) ? NR : 0, par = (uint32_t)(i & 1);
+                if (!mbar_wait_bounded(full_lo, par)) { bad = true; break; }
+                fence_after();
+                issue(1, dcol);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(empty_lo) : "memory");
+                last_bar = empty_lo;
+                last_par = par;
+                if (!mbar_wait_bounded(full_hi, par)) { bad = true; break; }
+                fence_after();
+                issue(0, dcol);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(empty_hi) : "memory");
+                last_bar = empty_hi;
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) X[j] = psi[b + sCol[c0 + j]];
+            if (bad) {
+                atomicOr(err, DEVERR_TIMEOUT);
+                // the latest commit tracks every MMA issued before it: one more bounded wait on it
+                if (last_bar) mbar_wait_bounded(last_bar, last_par);
+            }
         }
-    };
-    auto epilogue = [&](uint64_t base, uint32_t dcol) {
-        uint32_t v[2 * CPT];
-        tmem_ld<2 * CPT>(tbase + tlane + dcol + 2 * c0, v);
-        wait_ld();
-        const uint64_t b = base + rowoff;
-        if constexpr (P0) {
-#pragma unroll
-            for (int j = 0; j < CPT; j += 2)
-                *reinterpret_cast<float4*>(psi + b + sCol[c0 + j]) =
-                    make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
-                                __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j)
-                psi[b + sCol[c0 + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-        }
-    };
+        __syncwarp();
+    } else {
+        // ---- data warps ----
+        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+        const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+        // Column offsets are re-read from shared memory at each use (one broadcast load) instead of being
+        // kept in 64-bit registers; the empty asm with a memory clobber between columns keeps the compiler
+        // from batching those reads ahead of the accesses they address.
+        const volatile uint64_t* vCol = sCol + c0;
 
-    uint32_t phase = 0;
-    bool bad = false;
-    uint64_t prev_base = 0;
-    uint32_t it = 0;
-    uint64_t tile = blockIdx.x;
-    if (tile < a.ntiles) load_tile(tile);
-
-    // Pipeline per tile t: wait MMA(t-1) (A free, D[(t-1)&1] final) | split X(t) into A | MMA(t) -> D[t&1]
-    // | loads of tile t+1 | epilogue of tile t-1 from D[(t-1)&1], overlapping MMA(t).
-    for (; tile < a.ntiles; tile += gridDim.x, ++it) {
-        const uint64_t base = insert_zeros(tile, a.spos, a.nS);
-        if (it > 0) {
-            int to = 0;
-            if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
-            if (__syncthreads_or(to)) { bad = true; break; }
-            phase ^= 1;
-            fence_after();
-        }
-        if constexpr (!BF16) {
-            uint32_t hi[AV], lo[AV];
+        // Thread (r, columns c0..c0+CPT) of a tile. With P0 (qubit 0 is target 0) columns 2i and 2i+1 are
+        // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
+        auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
+            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+            if constexpr (P0) {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                // the residual is rounded to TF32 here: left to the tensor core, its low bits would be
-                // truncated towards zero
-                hi[2 * j] = tf32_rna_alu(X[j].x);
-                hi[2 * j + 1] = tf32_rna_alu(X[j].y);
-                lo[2 * j] = tf32_rna_alu(X[j].x - __uint_as_float(hi[2 * j]));
-                lo[2 * j + 1] = tf32_rna_alu(X[j].y - __uint_as_float(hi[2 * j + 1]));
-            }
-            tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + 2 * c0, hi);
-            tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + 2 * c0, lo);
-        } else {
-            uint32_t p0[AV], p1[AV];
-            [[maybe_unused]] uint32_t p2[AV];
+                for (int j = 0; j < CPT; j += 2) {
+                    const float4 v = *reinterpret_cast<const float4*>(psi + b + vCol[j]);
+                    X[j] = make_float2(v.x, v.y);
+                    X[j + 1] = make_float2(v.z, v.w);
+                    asm volatile("" ::: "memory");
+                }
+            } else {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                const uint32_t hr = bf16_rne_bits(X[j].x), hm = bf16_rne_bits(X[j].y);
-                const float rr = X[j].x - bf16_bits_to_float(hr), ri = X[j].y - bf16_bits_to_float(hm);
-                const uint32_t mr = bf16_rne_bits(rr), mi = bf16_rne_bits(ri);
-                p0[j] = pack2(hr, hm);
-                p1[j] = pack2(mr, mi);
-                if constexpr (C::planes == 3)
-                    p2[j] = pack2(bf16_rne_bits(rr - bf16_bits_to_float(mr)), bf16_rne_bits(ri - bf16_bits_to_float(mi)));
-            }
-            tmem_st<AV>(tbase + tlane + A0 + 0 * ACOLS + c0, p0);
-            tmem_st<AV>(tbase + tlane + A0 + 1 * ACOLS + c0, p1);
-            if constexpr (C::planes == 3) tmem_st<AV>(tbase + tlane + A0 + 2 * ACOLS + c0, p2);
-        }
-        wait_st();
-        fence_before();
-        __syncthreads();
-        const uint32_t dcol = (it & 1) ? NR : 0;
-        if (tid == 0) {
-            fence_after();
-            uint32_t acc = 0;
-#pragma unroll
-            for (int pr = 0; pr < C::nprod; ++pr) {
-                const uint32_t acol = tbase + A0 + C::pa(pr) * ACOLS;
-                const uint32_t bpl = sB + C::pb(pr) * PB;
-#pragma unroll
-                for (int s = 0; s < KSTEPS; ++s) {
-                    mma_ts<BF16>(tbase + dcol, acol + 8 * s, sdesc_sw128(bpl + (s >> 2) * ATOM + (s & 3) * 32), IDESC, acc);
-                    acc = 1;
+                for (int j = 0; j < CPT; ++j) {
+                    X[j] = psi[b + vCol[j]];
+                    asm volatile("" ::: "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mbar_addr) : "memory");
-        }
-        const uint64_t next = tile + gridDim.x;
-        if (next < a.ntiles) load_tile(next);
-        if (it > 0) epilogue(prev_base, dcol ^ NR);
-        prev_base = base;
-    }
-    if (it > 0 && !bad) {
-        int to = 0;
-        if (tid == 0) to = !mbar_wait_bounded(mbar_addr, phase);
-        if (__syncthreads_or(to)) {
-            bad = true;
-        } else {
+        };
+        // One A plane of tile X: hi = TF32(x), lo = TF32(x - hi). Both roundings are explicit: left to the
+        // tensor core, the residual's low bits would be truncated towards zero. Then one arrival per warp.
+        auto store_plane = [&](const float2 (&X)[CPT], int plane, uint32_t full) {
+#pragma unroll
+            for (int h = 0; h < CPT / QC; ++h) {
+                uint32_t v[2 * QC];
+#pragma unroll
+                for (int j = 0; j < QC; ++j) {
+                    const float2 x = X[h * QC + j];
+                    const uint32_t hr = tf32_rna_alu(x.x), hm = tf32_rna_alu(x.y);
+                    v[2 * j] = plane ? tf32_rna_alu(x.x - __uint_as_float(hr)) : hr;
+                    v[2 * j + 1] = plane ? tf32_rna_alu(x.y - __uint_as_float(hm)) : hm;
+                }
+                tmem_st<2 * QC>(tbase + tlane + A0 + plane * ACOLS + 2 * (c0 + h * QC), v);
+            }
+            wait_st();
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full);
+        };
+        auto epilogue = [&](uint64_t t, uint32_t dcol) {
+            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+#pragma unroll
+            for (int h = 0; h < CPT / QC; ++h) {
+                uint32_t v[2 * QC];
+                tmem_ld<2 * QC>(tbase + tlane + dcol + 2 * (c0 + h * QC), v);
+                wait_ld();
+                if constexpr (P0) {
+#pragma unroll
+                    for (int j = 0; j < QC; j += 2) {
+                        *reinterpret_cast<float4*>(psi + b + vCol[h * QC + j]) =
+                            make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                        __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
+                        asm volatile("" ::: "memory");
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < QC; ++j) {
+                        psi[b + vCol[h * QC + j]] =
+                            make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                        asm volatile("" ::: "memory");
+                    }
+                }
+            }
+        };
+        // warp-uniform bounded wait (the TMEM accesses that follow are .sync.aligned)
+        auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+            const bool ok = !__any_sync(0xffffffffu, !mbar_wait_bounded(bar, par));
             fence_after();
-            epilogue(prev_base, ((it - 1) & 1) ? NR : 0);
+            return ok;
+        };
+
+        bool bad = false;
+        float2 XA[CPT], XB[CPT];
+        if (m > 0) load_tile(XA, t0);
+        if (DEPTH == 2 && m > 1) load_tile(XB, t0 + G);
+        // Tile i: wait lo(i-1) | A_lo(i) -> TMEM, arrive | wait hi(i-1) (tile i-1 final) | A_hi(i) -> TMEM,
+        // arrive | then, with DEPTH 2, the epilogue of tile i-1 and the loads of tile i+2 into the registers
+        // tile i used (tiles alternate between the register sets XA and XB); with DEPTH 1, the loads of tile
+        // i+1 first, so that the epilogue of tile i-1 covers part of their latency.
+        auto step = [&](uint64_t i, float2 (&X)[CPT]) -> bool {
+            const uint32_t pp = (uint32_t)((i - 1) & 1);
+            if (i > 0 && !wait(empty_lo, pp)) return false;
+            store_plane(X, 1, full_lo);
+            if (i > 0 && !wait(empty_hi, pp)) return false;
+            store_plane(X, 0, full_hi);
+            if constexpr (DEPTH == 2) {
+                if (i > 0) epilogue(t0 + (i - 1) * G, (i & 1) ? 0 : NR);
+                if (i + 2 < m) load_tile(X, t0 + (i + 2) * G);
+            } else {
+                if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);
+                if (i > 0) epilogue(t0 + (i - 1) * G, (i & 1) ? 0 : NR);
+            }
+            return true;
+        };
+        uint64_t i = 0;
+        if constexpr (DEPTH == 2) {
+            for (; i + 1 < m; i += 2) {
+                if (!step(i, XA) || !step(i + 1, XB)) { bad = true; break; }
+            }
         }
-    }
-    if (bad && tid == 0) {
-        atomicOr(err, DEVERR_TIMEOUT);
-        mbar_wait_bounded(mbar_addr, phase);  // give in-flight MMAs one more bounded chance to retire
+        for (; !bad && i < m; ++i) {
+            if (!step(i, XA)) bad = true;
+        }
+        if (!bad && m > 0) {
+            if (wait(empty_hi, (uint32_t)((m - 1) & 1))) epilogue(t0 + (m - 1) * G, ((m - 1) & 1) ? NR : 0);
+            else bad = true;
+        }
+        if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
     }
     fence_before();
     __syncthreads();
@@ -536,7 +613,7 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;  // + barriers, TMEM slot
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
@@ -544,11 +621,12 @@ template <int K, int PREC, bool P0>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
     auto kern = Cfg<PREC>::esize == 2 ? k_tc_block_a2<K, PREC == QSIM_PREC_TF32X3 ? QSIM_PREC_BF16X3 : PREC, P0>
-                                      : k_tc_block<K, PREC, P0>;
+                                      : k_tc_block<K, PREC == QSIM_PREC_TF32X3 ? PREC : QSIM_PREC_TF32X3, P0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
-    kern<<<grid, kThreads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
+    const int threads = Cfg<PREC>::esize == 2 ? kThreads : kThreadsWS;
+    kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
     return cudaGetLastError();
 }
 
