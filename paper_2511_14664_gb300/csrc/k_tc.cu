@@ -13,14 +13,13 @@
 // memory) go to shared memory once, SWIZZLE_128B K-major. Every wait on an mbarrier is bounded (2 s); on
 // expiry the kernel records DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory
 // and returns.
-//   TF32 (k_tc_block): warp-specialised. Eight data warps (two per TMEM lane quadrant) load tiles into
-//   registers (coalesced; 16-byte vectors when qubit 0 is the block's first target; one tile ahead at K = 6,
-//   two at K = 5), split them into the lo and hi planes of the A operand in TMEM and run the epilogue
-//   (tcgen05.ld of the finished accumulator, stores back in place); a ninth warp issues the MMAs. The lo
-//   plane's product and the hi plane's products of a tile are separate phases with their own barriers, so
-//   the split of one plane overlaps the MMAs on the other, and two TMEM accumulators let the epilogue of
-//   tile t-1 overlap the MMAs of tile t.
-//   BF16 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
+//   3xTF32 and BF16x3 (k_tc_block): warp-specialised. Eight data warps (two per TMEM lane quadrant) load
+//   tiles into registers (coalesced; 16-byte vectors when qubit 0 is the block's first target; one tile
+//   ahead at K = 6, two at K = 5), split them into the planes of the A operand in TMEM and run the epilogue
+//   (tcgen05.ld of the finished accumulator, stores back in place); a ninth warp issues the MMAs. Each A
+//   plane's products form a phase with its own barriers, so the split of one plane overlaps the MMAs on
+//   another, and two TMEM accumulators let the epilogue of tile t-1 overlap the MMAs of tile t.
+//   BF16x6 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -144,14 +143,22 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
     }
 }
 
-// TF32 MMA with the shared-memory descriptor given as its two 32-bit halves (the low half carries the
-// address field, so per-K-step offsets are one 32-bit add).
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_lo, uint32_t b_hi,
+// MMA (A from TMEM) with the shared-memory descriptor given as its two 32-bit halves (the low half carries
+// the address field, so per-K-step offsets are one 32-bit add).
+template <bool BF16>
+__device__ __forceinline__ void mma_ts_lohi(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_lo, uint32_t b_hi,
                                             uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 bd;\n\tsetp.ne.b32 p, %5, 0;\n\tmov.b64 bd, {%2, %3};\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], bd, %4, p;\n}"
-        :: "r"(d_tmem), "r"(a_tmem), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc) : "memory");
+    if constexpr (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 bd;\n\tsetp.ne.b32 p, %5, 0;\n\tmov.b64 bd, {%2, %3};\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], bd, %4, p;\n}"
+            :: "r"(d_tmem), "r"(a_tmem), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc) : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 bd;\n\tsetp.ne.b32 p, %5, 0;\n\tmov.b64 bd, {%2, %3};\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], bd, %4, p;\n}"
+            :: "r"(d_tmem), "r"(a_tmem), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(acc) : "memory");
+    }
 }
 
 template <int N>
@@ -178,10 +185,11 @@ struct Args {
     uint64_t ntiles;
 };
 
-// TF32 variant, warp-specialised: warps 0..7 move data (tile loads, hi / lo split into TMEM, epilogue), warp
-// 8 issues the MMAs. They hand off through four mbarriers: full_lo / full_hi (one arrival per data warp once
-// its part of an A plane is in TMEM) and empty_lo / empty_hi (tcgen05.commit after the MMAs that read the
-// plane). The hi commit follows every MMA of a tile, so it also marks that tile's accumulator final.
+// Warp-specialised block kernel, all precisions: warps 0..7 move data (tile loads, split into the A planes
+// in TMEM, epilogue), warp 8 issues the MMAs. A tile is processed in one phase per A plane, smallest plane
+// first; each phase has two mbarriers: full[p] (one arrival per data warp once its part of plane p is in
+// TMEM) and empty[p] (tcgen05.commit after the MMAs that read plane p). The commit of the last phase (the
+// hi plane) follows every MMA of the tile, so it also marks the tile's accumulator final.
 constexpr int kDataWarps = 8;  // two per TMEM lane quadrant; 9 warps leave room for a two-tile prefetch
 constexpr int kThreadsWS = (kDataWarps + 1) * 32;
 
@@ -194,26 +202,30 @@ __global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
     using C = Cfg<PREC>;
-    static_assert(C::esize == 4 && C::planes == 2, "the TF32 hi / lo split");
+    constexpr bool BF16 = C::esize == 2;
+    constexpr int P = C::planes;
     constexpr int D = 1 << K, NR = 2 * D;
-    constexpr int PB = plane_bytes(K, 4);
+    constexpr int PB = plane_bytes(K, C::esize);
     constexpr int ATOM = NR * 128;                         // bytes of one 128-byte-wide K atom (all NR rows)
-    constexpr int KSTEPS = NR * 4 / 32;                    // each MMA consumes 32 bytes of K
+    constexpr int KSTEPS = NR * C::esize / 32;             // each MMA consumes 32 bytes of K
     constexpr int CPT = D / 2;                             // complex columns per thread (2 warps per quadrant)
-    constexpr int QC = 8;                                  // columns per tcgen05.st / tcgen05.ld (16 values)
-    constexpr int ACOLS = NR;                              // TMEM columns per A plane
-    constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A_hi, A_lo
-    constexpr uint32_t TCOLS = pow2_at_least(A0 + 2 * ACOLS);
-    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NR >> 3) << 17) |
+    constexpr int QC = BF16 ? 16 : 8;                      // columns per tcgen05.st (16 32-bit values)
+    constexpr int QE = 8;                                  // columns per tcgen05.ld of the FP32 accumulator
+    constexpr int ACOLS = BF16 ? NR / 2 : NR;              // TMEM columns per A plane (BF16: re / im packed)
+    constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A planes
+    constexpr uint32_t TCOLS = pow2_at_least(A0 + P * ACOLS);
+    constexpr uint32_t FMT = BF16 ? 1u : 2u;
+    constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(NR >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
-    static_assert(CPT % QC == 0, "whole chunks per thread");
+    static_assert(CPT % QC == 0 && CPT % QE == 0, "whole chunks per thread");
+    static_assert(TCOLS <= 512, "TMEM holds two accumulators and every A plane");
     constexpr int DEPTH = K >= 6 ? 1 : 2;                  // tiles of loads in flight (registers: CPT x 2 each)
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
-    uint64_t* mbar = sCol + D;                             // empty_lo, empty_hi, full_lo, full_hi
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 4);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + P * PB);
+    uint64_t* mbar = sCol + D;                             // empty[0..P), full[0..P)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2 * P);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
@@ -221,12 +233,12 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     const int r = quad * 32 + lane;
 
     // B planes -> shared memory (already in the swizzled byte layout), column offsets, barriers, TMEM.
-    for (int i = tid; i < 2 * PB / 16; i += kThreadsWS) reinterpret_cast<uint4*>(sb)[i] = bops[i];
+    for (int i = tid; i < P * PB / 16; i += kThreadsWS) reinterpret_cast<uint4*>(sb)[i] = bops[i];
     for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 2 * P; ++j)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
-                         :: "r"(smem_u32(mbar + j)), "r"(j < 2 ? 1 : kDataWarps) : "memory");
+                         :: "r"(smem_u32(mbar + j)), "r"(j < P ? 1 : kDataWarps) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make B visible to the tensor cores
@@ -239,8 +251,9 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t empty_lo = smem_u32(mbar), empty_hi = smem_u32(mbar + 1);
-    const uint32_t full_lo = smem_u32(mbar + 2), full_hi = smem_u32(mbar + 3);
+    const uint32_t bar0 = smem_u32(mbar);
+    auto empty = [&](int p) { return bar0 + 8u * (uint32_t)p; };
+    auto full = [&](int p) { return bar0 + 8u * (uint32_t)(P + p); };
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
 
@@ -249,44 +262,41 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         if (lane == 0) {
             const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
             const uint32_t dhi = (uint32_t)(desc0 >> 32);
-            // The products of one A plane, smallest first as listed in Cfg; lo * hi starts the accumulator.
-            // Descriptor offsets are compile-time constants added to the address field (shared-memory
-            // addresses stay below 2^18 bytes, so the 14-bit field cannot carry). The base is passed through
-            // an empty asm so that the 16 to 32 descriptors are formed at each use rather than held in
+            // The products of A plane p in the order Cfg lists them; the first product of the tile starts the
+            // accumulator. Descriptor offsets are compile-time constants added to the address field
+            // (shared-memory addresses stay below 2^18 bytes, so the 14-bit field cannot carry). The base
+            // goes through an empty asm so that the descriptors are formed at each use rather than held in
             // registers across the loop.
-            auto issue = [&](int plane, uint32_t dcol) {
+            auto issue = [&](int p, uint32_t dcol) {
                 uint32_t dlo = (uint32_t)desc0, tb = tbase;
                 asm volatile("" : "+r"(dlo), "+r"(tb));
-                uint32_t acc = plane ? 0u : 1u;
+                uint32_t acc = p == P - 1 ? 0u : 1u;
 #pragma unroll
                 for (int pr = 0; pr < C::nprod; ++pr) {
-                    if (C::pa(pr) != plane) continue;
-                    const uint32_t acol = tb + A0 + C::pa(pr) * ACOLS;
+                    if (C::pa(pr) != p) continue;
+                    const uint32_t acol = tb + A0 + p * ACOLS;
 #pragma unroll
                     for (int s = 0; s < KSTEPS; ++s) {
                         const uint32_t off = (uint32_t)(C::pb(pr) * PB + (s >> 2) * ATOM + (s & 3) * 32);
-                        mma_tf32_ts(tb + dcol, acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
+                        mma_ts_lohi<BF16>(tb + dcol, acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
                         acc = 1;
                     }
                 }
             };
             uint32_t last_bar = 0, last_par = 0;
             bool bad = false;
-            for (uint64_t i = 0; i < m; ++i) {
+            for (uint64_t i = 0; i < m && !bad; ++i) {
                 const uint32_t dcol = (i & 1) ? NR : 0, par = (uint32_t)(i & 1);
-                if (!mbar_wait_bounded(full_lo, par)) { bad = true; break; }
-                fence_after();
-                issue(1, dcol);
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(empty_lo) : "memory");
-                last_bar = empty_lo;
-                last_par = par;
-                if (!mbar_wait_bounded(full_hi, par)) { bad = true; break; }
-                fence_after();
-                issue(0, dcol);
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(empty_hi) : "memory");
-                last_bar = empty_hi;
+#pragma unroll
+                for (int p = P - 1; p >= 0; --p) {
+                    if (!mbar_wait_bounded(full(p), par)) { bad = true; break; }
+                    fence_after();
+                    issue(p, dcol);
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(empty(p)) : "memory");
+                    last_bar = empty(p);
+                    last_par = par;
+                }
             }
             if (bad) {
                 atomicOr(err, DEVERR_TIMEOUT);
@@ -324,45 +334,63 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                 }
             }
         };
-        // One A plane of tile X: hi = TF32(x), lo = TF32(x - hi). Both roundings are explicit: left to the
-        // tensor core, the residual's low bits would be truncated towards zero. Then one arrival per warp.
-        auto store_plane = [&](const float2 (&X)[CPT], int plane, uint32_t full) {
+        // Plane p of the split of x: TF32 hi = TF32(x), lo = TF32(x - hi); BF16 successive residuals rounded
+        // to BF16 (p = 0, 1, 2). Every rounding is explicit: left to the tensor core, a residual's low bits
+        // would be truncated towards zero.
+        auto plane_of = [&](float x, int p) -> uint32_t {
+            if constexpr (BF16) {
+                uint32_t h = bf16_rne_bits(x);
+                for (int q = 0; q < p; ++q) {
+                    x -= bf16_bits_to_float(h);
+                    h = bf16_rne_bits(x);
+                }
+                return h;
+            } else {
+                const uint32_t h = tf32_rna_alu(x);
+                return p ? tf32_rna_alu(x - __uint_as_float(h)) : h;
+            }
+        };
+        // Plane p of tile X into TMEM, then one arrival per warp on full[p].
+        auto store_plane = [&](const float2 (&X)[CPT], int p) {
 #pragma unroll
             for (int h = 0; h < CPT / QC; ++h) {
-                uint32_t v[2 * QC];
+                uint32_t v[16];
 #pragma unroll
                 for (int j = 0; j < QC; ++j) {
                     const float2 x = X[h * QC + j];
-                    const uint32_t hr = tf32_rna_alu(x.x), hm = tf32_rna_alu(x.y);
-                    v[2 * j] = plane ? tf32_rna_alu(x.x - __uint_as_float(hr)) : hr;
-                    v[2 * j + 1] = plane ? tf32_rna_alu(x.y - __uint_as_float(hm)) : hm;
+                    if constexpr (BF16) {
+                        v[j] = pack2(plane_of(x.x, p), plane_of(x.y, p));
+                    } else {
+                        v[2 * j] = plane_of(x.x, p);
+                        v[2 * j + 1] = plane_of(x.y, p);
+                    }
                 }
-                tmem_st<2 * QC>(tbase + tlane + A0 + plane * ACOLS + 2 * (c0 + h * QC), v);
+                tmem_st<16>(tbase + tlane + A0 + p * ACOLS + (BF16 ? 1 : 2) * (c0 + h * QC), v);
             }
             wait_st();
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(full);
+            if (lane == 0) mbar_arrive(full(p));
         };
         auto epilogue = [&](uint64_t t, uint32_t dcol) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
 #pragma unroll
-            for (int h = 0; h < CPT / QC; ++h) {
-                uint32_t v[2 * QC];
-                tmem_ld<2 * QC>(tbase + tlane + dcol + 2 * (c0 + h * QC), v);
+            for (int h = 0; h < CPT / QE; ++h) {
+                uint32_t v[2 * QE];
+                tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
                 wait_ld();
                 if constexpr (P0) {
 #pragma unroll
-                    for (int j = 0; j < QC; j += 2) {
-                        *reinterpret_cast<float4*>(psi + b + vCol[h * QC + j]) =
+                    for (int j = 0; j < QE; j += 2) {
+                        *reinterpret_cast<float4*>(psi + b + vCol[h * QE + j]) =
                             make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                         __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
                         asm volatile("" ::: "memory");
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < QC; ++j) {
-                        psi[b + vCol[h * QC + j]] =
+                    for (int j = 0; j < QE; ++j) {
+                        psi[b + vCol[h * QE + j]] =
                             make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
                         asm volatile("" ::: "memory");
                     }
@@ -380,16 +408,18 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         float2 XA[CPT], XB[CPT];
         if (m > 0) load_tile(XA, t0);
         if (DEPTH == 2 && m > 1) load_tile(XB, t0 + G);
-        // Tile i: wait lo(i-1) | A_lo(i) -> TMEM, arrive | wait hi(i-1) (tile i-1 final) | A_hi(i) -> TMEM,
-        // arrive | then, with DEPTH 2, the epilogue of tile i-1 and the loads of tile i+2 into the registers
-        // tile i used (tiles alternate between the register sets XA and XB); with DEPTH 1, the loads of tile
-        // i+1 first, so that the epilogue of tile i-1 covers part of their latency.
+        // Tile i: per plane p (smallest first) wait for the MMAs of tile i-1 on plane p, store plane p of
+        // tile i, arrive; the last wait (hi plane) also makes tile i-1 final. Then, with DEPTH 2, the
+        // epilogue of tile i-1 and the loads of tile i+2 into the registers tile i used (tiles alternate
+        // between the register sets XA and XB); with DEPTH 1, the loads of tile i+1 first, so that the
+        // epilogue of tile i-1 covers part of their latency.
         auto step = [&](uint64_t i, float2 (&X)[CPT]) -> bool {
             const uint32_t pp = (uint32_t)((i - 1) & 1);
-            if (i > 0 && !wait(empty_lo, pp)) return false;
-            store_plane(X, 1, full_lo);
-            if (i > 0 && !wait(empty_hi, pp)) return false;
-            store_plane(X, 0, full_hi);
+#pragma unroll
+            for (int p = P - 1; p >= 0; --p) {
+                if (i > 0 && !wait(empty(p), pp)) return false;
+                store_plane(X, p);
+            }
             if constexpr (DEPTH == 2) {
                 if (i > 0) epilogue(t0 + (i - 1) * G, (i & 1) ? 0 : NR);
                 if (i + 2 < m) load_tile(X, t0 + (i + 2) * G);
@@ -409,7 +439,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
             if (!step(i, XA)) bad = true;
         }
         if (!bad && m > 0) {
-            if (wait(empty_hi, (uint32_t)((m - 1) & 1))) epilogue(t0 + (m - 1) * G, ((m - 1) & 1) ? NR : 0);
+            if (wait(empty(0), (uint32_t)((m - 1) & 1))) epilogue(t0 + (m - 1) * G, ((m - 1) & 1) ? NR : 0);
             else bad = true;
         }
         if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
@@ -620,14 +650,17 @@ size_t smem_bytes(int K, int planes, int esize) {
 template <int K, int PREC, bool P0>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
-    auto kern = Cfg<PREC>::esize == 2 ? k_tc_block_a2<K, PREC == QSIM_PREC_TF32X3 ? QSIM_PREC_BF16X3 : PREC, P0>
-                                      : k_tc_block<K, PREC == QSIM_PREC_TF32X3 ? PREC : QSIM_PREC_TF32X3, P0>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
-    const int threads = Cfg<PREC>::esize == 2 ? kThreads : kThreadsWS;
-    kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
-    return cudaGetLastError();
+    auto launch = [&](auto kern, int threads) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
+        return cudaGetLastError();
+    };
+    // BF16x6 (three A planes, the heaviest split) runs faster on 16 warps with two A buffers than on the
+    // 8 data warps of the warp-specialised kernel
+    if constexpr (PREC == QSIM_PREC_BF16X6) return launch(k_tc_block_a2<K, PREC, P0>, kThreads);
+    else return launch(k_tc_block<K, PREC, P0>, kThreadsWS);
 }
 
 template <int K, int PREC>
