@@ -165,7 +165,7 @@ def source_sha(kind):
 
 
 def profiled_traffic(kind, n):
-    """DRAM bytes per launch from a committed ncu summary (profiles/*.txt lines 'bench-traffic: {...}'),
+    """DRAM bytes per launch from a committed ncu summary (profiles/*.md or *.txt lines 'bench-traffic: {...}'),
     used only while the kernel source is unchanged since the capture; scaled by 2^(n - n_captured)."""
     sha = source_sha(kind)
     pdir = os.path.join(ROOT, "profiles")
@@ -536,7 +536,8 @@ def run_qft(args):
                      "max_err_sampled": float(np.max(np.abs(got - ref)))}
     best = min((k for k in out if k != "plain"), key=lambda k: out[k]["ms_per_step"])
     line = _common_line(f"gate-applications/s, {n}-qubit QFT (with swaps), complex64, fused k=5 vs plain",
-                        out[best]["gates_per_s"], UNIT, args, out[best]["ms_per_step"], "f32",
+                        out[best]["gates_per_s"], UNIT, args, out[best]["ms_per_step"],
+                        "f32" if best.startswith(("plain", "simt")) else best[:4],
                         {"workload": f"QFT n={n} from |x>, x={x}, {len(c)} gates", "path": best},
                         paths=out, peak_hbm_gbs=peaks["hbm_gbs"])
     print(json.dumps(line))
