@@ -212,8 +212,11 @@ int qsim_run(qsim_h h, const qsim_circuit* c, const qsim_run_opts* opts, qsim_pl
 int qsim_norm(qsim_h h, double* out);
 
 /*
- * Marginal probabilities over `qubits` (1 <= nq <= 12): out[m] = sum of |a_x|^2 over the x whose bit
- * qubits[j] equals bit j of m. out has 2^nq doubles (host). Compensated sums. Synchronises.
+ * Marginal probabilities over `qubits` (1 <= nq <= min(30, n), distinct): out[m] = sum of |a_x|^2 over the
+ * x whose bit qubits[j] equals bit j of m. out has 2^nq doubles (host, caller-owned). Compensated sums
+ * (float-float per segment, FP64 across segments). For nq > 12 the bins are formed in a temporary device
+ * buffer of 8 * 2^nq bytes from the stream-ordered allocator, released before return (QSIM_ECUDA if it
+ * cannot be had). Synchronises.
  */
 int qsim_probs(qsim_h h, const int* qubits, int nq, double* out);
 

@@ -321,7 +321,7 @@ int qsim_norm(qsim_h h, double* out) {
 int qsim_probs(qsim_h h, const int* qubits, int nq, double* out) {
     QSIM_CHECK_HANDLE(h);
     if (!out || !qubits) { set_error("NULL argument"); return QSIM_EINVAL; }
-    if (nq < 1 || nq > 12 || nq > h->n) { set_error("nq = %d outside 1..min(12, n)", nq); return QSIM_EINVAL; }
+    if (nq < 1 || nq > 30 || nq > h->n) { set_error("nq = %d outside 1..min(30, n)", nq); return QSIM_EINVAL; }
     uint64_t seen = 0;
     for (int j = 0; j < nq; ++j) {
         if (qubits[j] < 0 || qubits[j] >= h->n || ((seen >> qubits[j]) & 1)) { set_error("bad marginal qubit list"); return QSIM_EINVAL; }

@@ -275,6 +275,98 @@ __global__ void __launch_bounds__(256) k_probs_seg(const typename Amp<R>::T* __r
     }
 }
 
+// Marginals over more than 12 qubits (n >= 12): 2^nq bins no longer fit in shared memory. The marginal
+// bits at positions >= 12 ("high") pick a group of 2^nlow bins, and one virtual block owns a group (or one
+// of S chunks of it): it runs over the segments that differ only in non-marginal high bits, folds each one
+// as above and adds the 2^nlow sums into float-float bins in shared memory. With S = 1 the block writes
+// the final values; otherwise it writes per-chunk partials that k_probs_wide_final combines (FP64 TwoSum).
+// Output bins are written in the caller's bit order (m), so no host permutation is needed.
+struct ProbsWideArgs {
+    int nlow;             // marginal qubits below 12
+    int fold[12];         // non-marginal bits below 12, descending
+    int nfold;
+    int lowj[12];         // user index j of the r-th smallest low marginal qubit
+    int nhigh;
+    int highpos[32];      // marginal positions >= 12, ascending
+    int highj[32];        // their user index j
+    int nfh;
+    int fhpos[32];        // non-marginal positions >= 12, ascending
+    uint64_t S;           // chunks per bin group (a power of two dividing 2^nfh)
+    uint64_t nvb;         // virtual blocks: 2^nhigh * S
+};
+
+__device__ __forceinline__ uint64_t wide_bin(const ProbsWideArgs& a, uint64_t i, uint64_t mh) {
+    uint64_t m = 0;
+    for (int r = 0; r < a.nlow; ++r) m |= ((i >> r) & 1) << a.lowj[r];
+    for (int j = 0; j < a.nhigh; ++j) m |= ((mh >> j) & 1) << a.highj[j];
+    return m;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_probs_wide(const typename Amp<R>::T* __restrict__ psi,
+                                                    const __grid_constant__ ProbsWideArgs a,
+                                                    double* __restrict__ partials, double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ff* buf0 = reinterpret_cast<ff*>(smem_raw);
+    ff* buf1 = buf0 + 4096;
+    ff* bins = buf1 + 4096;
+    const int NL = 1 << a.nlow;
+    const uint64_t per = (1ull << a.nfh) / a.S;
+    for (uint64_t vb = blockIdx.x; vb < a.nvb; vb += gridDim.x) {
+        const uint64_t mh = vb / a.S, sc = vb % a.S;
+        uint64_t hbits = 0;
+        for (int j = 0; j < a.nhigh; ++j) hbits |= ((mh >> j) & 1) << a.highpos[j];
+        for (int i = threadIdx.x; i < NL; i += blockDim.x) bins[i] = {0.f, 0.f};
+        for (uint64_t f = sc * per; f < (sc + 1) * per; ++f) {
+            uint64_t base = hbits;
+            for (int j = 0; j < a.nfh; ++j) base |= ((f >> j) & 1) << a.fhpos[j];
+            for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+                const auto v = psi[base + i];
+                if constexpr (sizeof(R) == 4) {
+                    buf0[i] = ff_abs2(v.x, v.y);
+                } else {
+                    const dd p = Acc<double>::abs2(v.x, v.y);
+                    const float hi = (float)p.hi;
+                    buf0[i] = {hi, (float)(p.hi - (double)hi + p.lo)};
+                }
+            }
+            __syncthreads();
+            ff* src = buf0;
+            ff* dst = buf1;
+            int len = 4096;
+            for (int fb = 0; fb < a.nfold; ++fb) {
+                const int c = a.fold[fb];
+                len >>= 1;
+                for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                    const int j = (int)insert_zero((uint64_t)i, c);
+                    dst[i] = ff_add(src[j], src[j | (1 << c)]);
+                }
+                __syncthreads();
+                ff* t = src; src = dst; dst = t;
+            }
+            for (int i = threadIdx.x; i < NL; i += blockDim.x) bins[i] = ff_add(bins[i], src[i]);
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < NL; i += blockDim.x) {
+            const double v = (double)bins[i].hi + (double)bins[i].lo;
+            if (a.S == 1) out[wide_bin(a, (uint64_t)i, mh)] = v;
+            else partials[(mh * (uint64_t)NL + (uint64_t)i) * a.S + sc] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_probs_wide_final(const double* __restrict__ partials,
+                                                          const __grid_constant__ ProbsWideArgs a,
+                                                          double* __restrict__ out) {
+    const uint64_t NL = 1ull << a.nlow, nbins = NL << a.nhigh;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nbins; p += (uint64_t)gridDim.x * blockDim.x) {
+        dd acc = {0.0, 0.0};
+        for (uint64_t sc = 0; sc < a.S; ++sc) acc = dd_add(acc, dd{partials[p * a.S + sc], 0.0});
+        out[wide_bin(a, p % NL, p / NL)] = acc.hi + acc.lo;
+    }
+}
+
 // Small states (n < 12): one CTA; out[m] directly (dd), each bin summing its 2^(n-nq) amplitudes.
 template <typename R>
 __global__ void __launch_bounds__(256) k_probs_small(const typename Amp<R>::T* __restrict__ psi, int n,
@@ -662,6 +754,57 @@ cudaError_t run_pauli(int dtype, const void* psi, int n, const char* paulis, Red
     return cudaSuccess;
 }
 
+// nq > 12 (so n > 12): bins in a temporary device buffer (8 B x 2^nq, stream-ordered), one copy to the host.
+static cudaError_t run_probs_wide(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
+                                  cudaStream_t s, const DevInfo& d, double* out) {
+    ProbsWideArgs a;
+    std::memset(&a, 0, sizeof(a));
+    std::vector<std::pair<int, int>> low, high;  // (position, user index)
+    uint64_t marg = 0;
+    for (int j = 0; j < nq; ++j) {
+        marg |= 1ull << qubits[j];
+        (qubits[j] < kSegBits ? low : high).push_back({qubits[j], j});
+    }
+    std::sort(low.begin(), low.end());
+    std::sort(high.begin(), high.end());
+    a.nlow = (int)low.size();
+    for (int k = 0; k < a.nlow; ++k) a.lowj[k] = low[k].second;
+    for (int b = kSegBits - 1; b >= 0; --b)
+        if (!((marg >> b) & 1)) a.fold[a.nfold++] = b;
+    a.nhigh = (int)high.size();
+    for (int k = 0; k < a.nhigh; ++k) { a.highpos[k] = high[k].first; a.highj[k] = high[k].second; }
+    for (int b = kSegBits; b < n; ++b)
+        if (!((marg >> b) & 1)) a.fhpos[a.nfh++] = b;
+    // split the non-marginal high range only while the bin groups alone give too few blocks; the partials
+    // (2^nq x S doubles) must fit the scratch buffer
+    uint64_t S = 1;
+    while ((S << a.nhigh) < 256 && S < (1ull << a.nfh) && (uint64_t)(S * 2) << nq <= (uint64_t)kPartialDoubles) S <<= 1;
+    a.S = S;
+    a.nvb = S << a.nhigh;
+    const size_t bytes = sizeof(double) << nq;
+    double* dout = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dout), bytes, s);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)std::min<uint64_t>(a.nvb, (uint64_t)d.num_sms * 2);
+    const size_t smem = 3 * 4096 * sizeof(ff);
+    if (dtype == QSIM_C64) {
+        e = cudaFuncSetAttribute(k_probs_wide<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_probs_wide<float><<<nb, 256, smem, s>>>((const float2*)psi, a, r.partials, dout);
+    } else {
+        e = cudaFuncSetAttribute(k_probs_wide<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_probs_wide<double><<<nb, 256, smem, s>>>((const double2*)psi, a, r.partials, dout);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && S > 1) {
+        k_probs_wide_final<<<(unsigned)std::min<uint64_t>(((1ull << nq) + 255) / 256, 4096), 256, 0, s>>>(r.partials, a, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, s);
+    const cudaError_t ef = cudaFreeAsync(dout, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    return e != cudaSuccess ? e : (ef != cudaSuccess ? ef : es);
+}
+
 cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
                       cudaStream_t s, const DevInfo& d, double* out) {
     ProbsArgs a;
@@ -684,6 +827,7 @@ cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int 
         for (int m = 0; m < NB; ++m) out[m] = r.hresult[2 * m] + r.hresult[2 * m + 1];
         return cudaSuccess;
     }
+    if (nq > kSegBits) return run_probs_wide(dtype, psi, n, qubits, nq, r, s, d, out);
     std::vector<std::pair<int, int>> low;  // (position, user index)
     for (int j = 0; j < nq; ++j) {
         if (qubits[j] < kSegBits) low.push_back({qubits[j], j});

@@ -317,6 +317,50 @@ def test_inner_product(qsim):
 
 
 # ---- argument errors -----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n,qs", [
+    (17, "perm13"),      # 12 low marginal bits + 1 high: one bin group per high value, chunked (S > 1)
+    (17, "perm17"),      # the whole distribution in a permuted bit order (no fold, S = 1)
+    (25, "high13"),      # all marginal bits above the 4096-amplitude segment: every low bit folded
+    (20, "mixed15"),     # a mix of low and high marginal bits in random order
+])
+def test_probs_wide_marginals(qsim, dtype, n, qs):
+    """Marginals over more than 12 qubits (bins beyond shared memory) against the FP64 oracle."""
+    psi = random_state(n, 300 + n)
+    st = make_state(qsim, n, dtype, psi0=psi)
+    ref = st.get_state().astype(np.complex128)
+    rng = np.random.default_rng(len(qs) + n)
+    if qs == "perm13":
+        q = [int(x) for x in rng.permutation(12)] + [int(rng.integers(12, n))]
+    elif qs == "perm17":
+        q = [int(x) for x in rng.permutation(n)]
+    elif qs == "high13":
+        q = [int(x) for x in rng.permutation(np.arange(12, n))]
+    else:
+        q = [int(x) for x in rng.permutation(n)[:15]]
+    got = st.probs(q)
+    np.testing.assert_allclose(got, oracle.probs(ref, n, q), atol=1e-14, rtol=0)
+    if len(q) == n:
+        # the full distribution is |psi|^2 with the index bits permuted
+        m = np.arange(1 << n, dtype=np.int64)
+        x = np.zeros_like(m)
+        for j, qj in enumerate(q):
+            x |= ((m >> j) & 1) << qj
+        np.testing.assert_allclose(got, np.abs(ref[x]) ** 2, atol=1e-15, rtol=0)
+
+
+def test_probs_limits(qsim):
+    st = make_state(qsim, 14, 0)
+    with pytest.raises(qsim.QsimError) as e:
+        st.probs(list(range(14)) + [3])
+    assert e.value.code == 1
+    with pytest.raises(qsim.QsimError) as e:
+        st.probs(list(range(15)))  # more qubits than the state has
+    assert e.value.code == 1
+    p = st.probs(list(range(14)))  # |0...0>: all weight in bin 0
+    assert p[0] == 1.0 and p[1:].sum() == 0.0
+
+
 def test_errors(qsim):
     st = make_state(qsim, 6, 0)
     for t, c in [((6,), ()), ((1, 1), ()), ((2,), (2,)), ((-1,), ())]:
