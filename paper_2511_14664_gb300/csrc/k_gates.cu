@@ -4,6 +4,8 @@
 //   k_dense_small  dense U on k <= 4 targets (+ controls): each thread gathers the 2^k amplitudes of one
 //                  group (targets and controls masked out of the index), multiplies, scatters. With qubit 0
 //                  untouched, a complex64 thread handles two adjacent groups with 16-byte loads.
+//   k_dense_split  the same for small states: 2..16 lanes of a warp share one group, so that the
+//                  (complex128) arithmetic of a few thousand groups still spreads over every SM.
 //   k_butterfly    single-qubit dense U on a low target (1..4, complex64): every lane streams one
 //                  contiguous 16-byte pair of amplitudes and receives its partners by warp shuffles.
 //   k_diag         diagonal U: multiplies only the amplitudes whose diagonal factor is not exactly 1
@@ -78,6 +80,46 @@ k_dense_small(typename Amp<R>::T* __restrict__ psi, uint64_t nitems, const __gri
                 }
                 *reinterpret_cast<float4*>(psi + base + a.off[r]) = make_float4(r0, i0, r1, i1);
             }
+        }
+    }
+}
+
+// Small states (too few groups to fill the GPU; the complex128 arithmetic is then the limit): TPG lanes of
+// one warp share a group. Every lane loads the group's 2^K amplitudes (same-address loads are broadcast),
+// the warp synchronises (all reads before any write: the update is in place), and each lane computes and
+// stores the rows r = sub + j * TPG. nitems = groups * TPG is a multiple of 32, so warps run in lockstep.
+template <typename R, int K, int TPG>
+__global__ void __launch_bounds__(256)
+k_dense_split(typename Amp<R>::T* __restrict__ psi, uint64_t nitems, const __grid_constant__ DenseSmallArgs<R, K> a) {
+    using T = typename Amp<R>::T;
+    constexpr int D = 1 << K, RPL = D / TPG;
+    static_assert(TPG >= 2 && TPG <= D && 32 % TPG == 0, "a group's lanes sit in one warp");
+    // lanes of a warp read different rows of U: from shared memory (banked), not the constant bank
+    // (which serialises divergent addresses)
+    __shared__ R sU[2 * D * D];
+    for (int i = threadIdx.x; i < 2 * D * D; i += blockDim.x) sU[i] = a.m[i];
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int sub = threadIdx.x % TPG;
+    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += stride) {
+        const uint64_t base = insert_zeros(it / TPG, a.fixed, a.nf) | a.cmask;
+        T v[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) v[m] = psi[base + a.off[m]];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int r = sub + j * TPG;
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const R ur = sU[2 * (r * D + c)], ui = sU[2 * (r * D + c) + 1];
+                re = fmar(ur, v[c].x, re);
+                re = fmar(-ui, v[c].y, re);
+                im = fmar(ur, v[c].y, im);
+                im = fmar(ui, v[c].x, im);
+            }
+            psi[base + a.off[r]] = make_amp<R>(re, im);
         }
     }
 }
@@ -342,6 +384,23 @@ cudaError_t dense_small_t(void* psi, int n, const int* targets, const Fixed& f, 
     for (int i = 0; i < 2 * D * D; ++i) a.m[i] = (R)mat[i];
     const uint64_t ngroups = 1ull << (n - f.nf);
     using T = typename Amp<R>::T;
+    // Small states: spread each group over TPG lanes until about 1024 threads per SM are busy.
+    if (ngroups < (uint64_t)d.num_sms * 512) {
+        int tpg = 1;
+        while (tpg < D && ngroups * (uint64_t)tpg < (uint64_t)d.num_sms * 1024) tpg <<= 1;
+        const uint64_t items = ngroups * (uint64_t)tpg;
+        if (tpg > 1 && items % 32 == 0) {
+            const unsigned grid = grid_for((int64_t)items, 256, d.num_sms, 8);
+            T* p = reinterpret_cast<T*>(psi);
+            switch (tpg) {
+                case 2: k_dense_split<R, K, 2><<<grid, 256, 0, s>>>(p, items, a); break;
+                case 4: if constexpr (D >= 4) k_dense_split<R, K, 4><<<grid, 256, 0, s>>>(p, items, a); break;
+                case 8: if constexpr (D >= 8) k_dense_split<R, K, 8><<<grid, 256, 0, s>>>(p, items, a); break;
+                default: if constexpr (D >= 16) k_dense_split<R, K, 16><<<grid, 256, 0, s>>>(p, items, a); break;
+            }
+            return cudaGetLastError();
+        }
+    }
     if constexpr (sizeof(R) == 4) {
         if (f.lowest >= 1 && ngroups >= 2) {
             const uint64_t items = ngroups / 2;
