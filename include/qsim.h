@@ -148,17 +148,19 @@ int qsim_synchronize(qsim_h h);
 /* ---- gate application (the hot path; Sec. 2.1, cost O(g 2^n)) --------------------------------------- */
 
 /*
- * Apply U on `targets` (k of them, 1 <= k <= 6; 7..8 with QSIM_EUNSUPPORTED) controlled on `controls`
- * (nc of them, may be NULL when nc = 0). All qubits distinct and < n. Asynchronous.
- * Diagonal matrices (every off-diagonal entry exactly 0) touch only the amplitudes whose factor is not
- * exactly 1; single-qubit gates use vectorised streaming or warp-shuffle butterflies; k <= 4 gathers
- * 2^k amplitudes per thread; k = 5, 6 use a shared-memory tile kernel in the state's precision.
+ * Apply U on `targets` (k of them, 1 <= k <= QSIM_MAX_TARGETS = 8) controlled on `controls` (nc of them,
+ * may be NULL when nc = 0). All qubits distinct and < n. Asynchronous.
+ * Diagonal matrices (every off-diagonal entry exactly 0, k <= 6) touch only the amplitudes whose factor is
+ * not exactly 1; single-qubit gates use vectorised streaming or warp-shuffle butterflies; k <= 4 gathers
+ * 2^k amplitudes per thread (spread over several lanes for small states); k = 5, 6 use a shared-memory
+ * tile kernel and k = 7, 8 a kernel that streams U from L2 in column chunks, both in the state's precision.
  */
 int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, int nc, const double* matrix);
 
 /*
- * Apply a dense 2^k x 2^k block (1 <= k <= 6) on `targets` with the given QSIM_PREC_* arithmetic.
- * Tensor-core precisions need a complex64 state and k in 4..6; QSIM_PREC_SIMT works for both types.
+ * Apply a dense 2^k x 2^k block (1 <= k <= 8) on `targets` with the given QSIM_PREC_* arithmetic.
+ * Tensor-core precisions need a complex64 state and k in 5..6 (QSIM_EUNSUPPORTED otherwise);
+ * QSIM_PREC_SIMT works for both types and every k.
  * This is the single-block form of what QSIM_RUN_FUSED plans produce.
  */
 int qsim_apply_fused(qsim_h h, const int* targets, int k, const double* matrix, int precision);

@@ -91,7 +91,7 @@ int check_device_error(qsim_state* h) {
 // Apply one gate through the plain per-gate kernels (shared by qsim_apply_gate and plan execution).
 int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* controls, int nc, const double* m) {
     cudaError_t e;
-    if (is_diagonal(m, k)) {
+    if (k <= 6 && is_diagonal(m, k)) {
         std::vector<double> dg(2 << k);
         const int D = 1 << k;
         for (int i = 0; i < D; ++i) { dg[2 * i] = m[2 * (i * D + i)]; dg[2 * i + 1] = m[2 * (i * D + i) + 1]; }
@@ -103,7 +103,7 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
         e = launch_dense_small(h->dtype, h->psi, h->n, k, targets, nc, controls, m, h->stream, h->dev);
         return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "dense gate launch");
     }
-    // k = 5, 6: matrix to device scratch in the state precision
+    // k = 5..8: matrix to device scratch in the state precision
     const int D = 1 << k;
     const size_t cnt = 2 * (size_t)D * D;
     if (h->dtype == QSIM_C64) {
@@ -264,8 +264,7 @@ int qsim_synchronize(qsim_h h) {
 
 int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, int nc, const double* matrix) {
     QSIM_CHECK_HANDLE(h);
-    if (k > 6 && k <= QSIM_MAX_TARGETS) { set_error("gates on %d > 6 targets are not supported", k); return QSIM_EUNSUPPORTED; }
-    int rc = validate_qubits(h->n, targets, k, controls, nc, 6);
+    int rc = validate_qubits(h->n, targets, k, controls, nc, QSIM_MAX_TARGETS);
     if (rc) return rc;
     if (!matrix) { set_error("NULL matrix"); return QSIM_EINVAL; }
     if (!is_unitary(matrix, k, 1e-8 * (1 << k))) { set_error("matrix is not unitary (|U U^dagger - I| > %g)", 1e-8 * (1 << k)); return QSIM_EINVAL; }
@@ -274,7 +273,7 @@ int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, in
 
 int qsim_apply_fused(qsim_h h, const int* targets, int k, const double* matrix, int precision) {
     QSIM_CHECK_HANDLE(h);
-    int rc = validate_qubits(h->n, targets, k, nullptr, 0, 6);
+    int rc = validate_qubits(h->n, targets, k, nullptr, 0, QSIM_MAX_TARGETS);
     if (rc) return rc;
     if (!matrix) { set_error("NULL matrix"); return QSIM_EINVAL; }
     if (precision < QSIM_PREC_SIMT || precision > QSIM_PREC_BF16X6) { set_error("unknown precision %d", precision); return QSIM_EINVAL; }

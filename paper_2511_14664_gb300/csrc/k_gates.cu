@@ -11,6 +11,7 @@
 //   k_diag         diagonal U: multiplies only the amplitudes whose diagonal factor is not exactly 1
 //                  (CZ / controlled phase touch a quarter of the state).
 //   k_dense_tile   dense U on k = 5, 6 targets through shared memory (CUDA-core arithmetic).
+//   k_dense_big    dense U on k = 7, 8 targets: U streamed from L2 in column chunks, 32 groups per CTA.
 //   k_swap_tile    in-place qubit reorder through shared-memory tiles.
 //   k_set_basis    |x>.
 #include <algorithm>
@@ -342,6 +343,76 @@ __global__ void k_convert_matrix(const double* __restrict__ src, float* __restri
 }
 
 // ============================================================================================================
+// Dense k = 7, 8 (CUDA cores). The matrix (up to 256 x 256 complex, L2-resident) does not fit in shared
+// memory next to the amplitudes, so it is streamed in column chunks of C through a padded shared buffer;
+// each chunk serves the G = 32 groups a CTA holds in shared memory. Thread (row r, half h) accumulates row
+// r of its G / H groups in registers and writes them back after the last chunk (the update is in place;
+// every input of the iteration is in shared memory by then).
+// ============================================================================================================
+struct BigArgs {
+    int nf;
+    int fixed[kMaxFixed];
+    uint64_t cmask;
+    int tpos[8];
+};
+
+template <typename R, int K> struct BigCfg {
+    static constexpr int D = 1 << K, G = 32, C = K == 7 ? 32 : 16, H = 256 / D, GPT = G / H;
+    static constexpr size_t smem = sizeof(typename Amp<R>::T) * ((size_t)G * D + (size_t)D * (C + 1)) +
+                                   sizeof(uint64_t) * D;
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256)
+k_dense_big(typename Amp<R>::T* __restrict__ psi, uint64_t ngroups, const __grid_constant__ BigArgs a,
+            const typename Amp<R>::T* __restrict__ U) {
+    using T = typename Amp<R>::T;
+    using B = BigCfg<R, K>;
+    constexpr int D = B::D, G = B::G, C = B::C, GPT = B::GPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* V = reinterpret_cast<T*>(smem_raw);                             // [G][D] amplitudes
+    T* UC = V + G * D;                                                 // [D][C + 1] column chunk of U
+    uint64_t* offs = reinterpret_cast<uint64_t*>(UC + D * (C + 1));    // [D] index offset of column c
+    for (int i = threadIdx.x; i < D; i += blockDim.x) offs[i] = deposit((uint64_t)i, a.tpos, K);
+    const int r = threadIdx.x % D, h = threadIdx.x / D;
+    for (uint64_t g0 = (uint64_t)blockIdx.x * G; g0 < ngroups; g0 += (uint64_t)gridDim.x * G) {
+        __syncthreads();  // offsets ready; the previous iteration's reads of V and UC are done
+        for (int i = threadIdx.x; i < G * D; i += blockDim.x) {
+            const uint64_t g = g0 + (uint64_t)(i / D);
+            if (g < ngroups) V[i] = psi[(insert_zeros(g, a.fixed, a.nf) | a.cmask) + offs[i % D]];
+        }
+        R re[GPT], im[GPT];
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) re[j] = im[j] = 0;
+        for (int c0 = 0; c0 < D; c0 += C) {
+            __syncthreads();  // V loaded; the previous chunk consumed
+            for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+                const int rr = i / C, cc = i % C;
+                UC[rr * (C + 1) + cc] = U[(size_t)rr * D + c0 + cc];
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int cc = 0; cc < C; ++cc) {
+                const T u = UC[r * (C + 1) + cc];
+#pragma unroll
+                for (int j = 0; j < GPT; ++j) {
+                    const T v = V[(h * GPT + j) * D + c0 + cc];  // same address across the warp: broadcast
+                    re[j] = fmar(u.x, v.x, re[j]);
+                    re[j] = fmar(-u.y, v.y, re[j]);
+                    im[j] = fmar(u.x, v.y, im[j]);
+                    im[j] = fmar(u.y, v.x, im[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < GPT; ++j) {
+            const uint64_t g = g0 + (uint64_t)(h * GPT + j);
+            if (g < ngroups) psi[(insert_zeros(g, a.fixed, a.nf) | a.cmask) + offs[r]] = make_amp<R>(re[j], im[j]);
+        }
+    }
+}
+
+// ============================================================================================================
 // Host launchers
 // ============================================================================================================
 namespace {
@@ -503,9 +574,35 @@ static cudaError_t dense_tile_t(void* psi, int n, const int* targets, const Fixe
     return cudaGetLastError();
 }
 
+template <typename R, int K>
+static cudaError_t dense_big_t(void* psi, int n, const int* targets, const Fixed& f, const void* dmat,
+                               cudaStream_t s, const DevInfo& d) {
+    using T = typename Amp<R>::T;
+    BigArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nf = f.nf;
+    std::memcpy(a.fixed, f.pos, sizeof(int) * f.nf);
+    a.cmask = f.cmask;
+    std::memcpy(a.tpos, targets, sizeof(int) * K);
+    const size_t smem = BigCfg<R, K>::smem;
+    cudaError_t e = cudaFuncSetAttribute(k_dense_big<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t ngroups = 1ull << (n - f.nf);
+    const uint64_t nchunks = (ngroups + BigCfg<R, K>::G - 1) / BigCfg<R, K>::G;
+    k_dense_big<R, K><<<grid_for((int64_t)nchunks, 1, d.num_sms, smem > 110 * 1024 ? 1 : 2), 256, smem, s>>>(
+        reinterpret_cast<T*>(psi), ngroups, a, reinterpret_cast<const T*>(dmat));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dense_tile(int dtype, void* psi, int n, int k, const int* targets, int nc,
                               const int* controls, const void* dmat, cudaStream_t s, const DevInfo& d) {
     const Fixed f = make_fixed(k, targets, nc, controls);
+    if (k == 7 || k == 8) {
+        if (dtype == QSIM_C64) return k == 7 ? dense_big_t<float, 7>(psi, n, targets, f, dmat, s, d)
+                                             : dense_big_t<float, 8>(psi, n, targets, f, dmat, s, d);
+        return k == 7 ? dense_big_t<double, 7>(psi, n, targets, f, dmat, s, d)
+                      : dense_big_t<double, 8>(psi, n, targets, f, dmat, s, d);
+    }
     if (dtype == QSIM_C64) {
         if (k == 5) return dense_tile_t<float, 5>(psi, n, targets, f, dmat, s, d);
         if (k == 6) return dense_tile_t<float, 6>(psi, n, targets, f, dmat, s, d);

@@ -206,8 +206,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     std::vector<char> gdiag(G);
     for (int i = 0; i < G; ++i) {
         const qsim_gate& g = c->gates[i];
-        if (g.k > 6 && g.k <= QSIM_MAX_TARGETS) { set_error("gate %d: more than 6 targets is not supported", i); return QSIM_EUNSUPPORTED; }
-        int rc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, 6);
+        int rc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, QSIM_MAX_TARGETS);
         if (rc) { set_error("gate %d: invalid qubits", i); return rc; }
         if (!g.matrix) { set_error("gate %d: NULL matrix", i); return QSIM_EINVAL; }
         if (!is_unitary(g.matrix, g.k, 1e-8 * (1 << g.k))) { set_error("gate %d: matrix is not unitary", i); return QSIM_EINVAL; }
@@ -243,6 +242,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     auto align = [](size_t v) { return (v + 1023) & ~(size_t)1023; };
     struct Pending { int op; int kind; int kb; };  // device operand still to produce from a composed matrix
     std::vector<Pending> pending;
+    std::vector<int> direct;  // ops whose gate matrix is uploaded as it is (single gates on 7-8 qubits)
 
     for (const auto& blk : blocks) {
         PlanOp op;
@@ -254,6 +254,17 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             std::memcpy(op.targets, g.targets, sizeof(int) * g.k);
             std::memcpy(op.controls, g.controls, sizeof(int) * g.nc);
             const int D = 1 << g.k;
+            if (g.k >= 7) {
+                // 7 or 8 targets (diagonal or not): its own CUDA-core pass; the matrix is uploaded as given,
+                // in the state precision (no composition: one gate)
+                op.kind = OP_DENSE_TILE;
+                op.mat.assign(g.matrix, g.matrix + 2 * D * D);
+                op.dev_off = dev_bytes;
+                dev_bytes = align(dev_bytes + (amp << (2 * g.k)));
+                direct.push_back((int)p->ops.size());
+                p->ops.push_back(std::move(op));
+                continue;
+            }
             if (gdiag[blk[0]]) {
                 op.kind = OP_DIAG;
                 op.mat.resize(2 * D);
@@ -398,6 +409,22 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             }
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+    }
+    for (size_t di = 0; rc == QSIM_OK && di < direct.size(); ++di) {
+        PlanOp& op = p->ops[direct[di]];
+        const size_t cnt = (size_t)2 << (2 * op.k);
+        std::vector<float> f;
+        if (dtype == QSIM_C64) {
+            f.resize(cnt);
+            for (size_t i = 0; i < cnt; ++i) f[i] = (float)op.mat[i];
+            e = cudaMemcpyAsync(base + op.dev_off, f.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, s);
+        } else {
+            e = cudaMemcpyAsync(base + op.dev_off, op.mat.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pageable host sources
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+        op.mat.clear();
+        op.mat.shrink_to_fit();
     }
     if (rc) { cudaFree(p->dbuf); delete p; return rc; }
 

@@ -77,7 +77,7 @@ def test_single_qubit_every_target(qsim, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", DT)
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_dense_gates_with_controls(qsim, dtype, k):
     n = 12
     rng = np.random.default_rng(100 + k)
@@ -92,6 +92,58 @@ def test_dense_gates_with_controls(qsim, dtype, k):
         ref = psi0.copy()
         oracle.apply_gate(ref, n, t, c, U)
         close(st.get_state(), ref, n, dtype)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_wide_gates_single_group_diagonal_and_fused(qsim, dtype):
+    """7- and 8-qubit gates: one group only (n = k), a diagonal 7-qubit gate (dense path), and the
+    SIMT single-block entry point."""
+    rng = np.random.default_rng(78)
+    for n, k in ((7, 7), (8, 8), (9, 8)):
+        t = tuple(int(x) for x in rng.permutation(n)[:k])
+        U = W.haar_unitary(1 << k, rng)
+        psi0 = random_state(n, 11 * n + k)
+        st = make_state(qsim, n, dtype, psi0=psi0)
+        st.apply_gate(t, (), U)
+        ref = psi0.copy()
+        oracle.apply_gate(ref, n, t, (), U)
+        close(st.get_state(), ref, n, dtype)
+    n = 13
+    dg = np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, size=128)))
+    t = (12, 0, 5, 3, 9, 1, 7)
+    psi0 = random_state(n, 3)
+    st = make_state(qsim, n, dtype, psi0=psi0)
+    st.apply_gate(t, (2,), dg)
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, t, (2,), dg)
+    close(st.get_state(), ref, n, dtype)
+    U = W.haar_unitary(128, rng)
+    st = make_state(qsim, n, dtype, psi0=psi0)
+    st.apply_fused(t, U, qsim.PREC_SIMT)
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, t, (), U)
+    close(st.get_state(), ref, n, dtype)
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plans_with_wide_gates(qsim, dtype, mode):
+    """Circuits mixing 7- and 8-qubit gates with small ones, plain and fused (wider gates than max_fused
+    become passes of their own)."""
+    n = 14
+    rng = np.random.default_rng(4 + mode)
+    c = W.Circuit(n)
+    for i in range(30):
+        c.append(W.random_gate(n, rng, kmax=2, cmax=1, diag_prob=0.3))
+        if i % 10 == 4:
+            k = 7 + (i // 10) % 2
+            qs = rng.permutation(n)[: k + 1]
+            c.append(W.Gate(tuple(int(x) for x in qs[:k]), (int(qs[k]),) if i == 14 else (),
+                            W.haar_unitary(1 << k, rng), f"u{k}"))
+    psi0 = random_state(n, 40 + mode)
+    st = make_state(qsim, n, dtype, psi0=psi0)
+    st.run(c, mode=mode, max_fused=4)
+    close(st.get_state(), oracle.run(c, psi=psi0.copy()), n, dtype)
 
 
 @pytest.mark.parametrize("dtype", DT)
