@@ -208,162 +208,143 @@ __global__ void __launch_bounds__(256) k_pauli_partial(const typename Amp<R>::T*
 }
 
 // ============================================================================================================
-// Marginal probabilities, n >= 12: segments of 4096 amplitudes. Inside a segment the non-marginal low bits
-// are folded out pairwise (bit 11 first, down to bit 0), leaving 2^|Qlow| sums that go to the bins selected
-// by the segment's high marginal bits. Bins live in shared memory per CTA (float-float) and are written as
-// per-CTA partials.
+// Marginal probabilities
 // ============================================================================================================
 struct ProbsArgs {
     int nq;
-    int nlow;             // marginal qubits below 12
-    int fold[12];         // non-marginal bits below 12, descending
-    int nfold;
-    int lowj[12];         // user index j of the r-th smallest low marginal qubit
-    int nhigh;
-    int highpos[12];      // marginal qubits >= 12 (index positions)
-    int highj[12];        // their user index j
 };
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_probs_seg(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
-                                                   const __grid_constant__ ProbsArgs a, double* partials) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ff* buf0 = reinterpret_cast<ff*>(smem_raw);
-    ff* buf1 = buf0 + 4096;
-    ff* bins = buf1 + 4096;
-    const int NB = 1 << a.nq;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) bins[i] = {0.f, 0.f};
-    for (uint64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
-        const uint64_t base = s << 12;
-        for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
-            const auto v = psi[base + i];
-            if constexpr (sizeof(R) == 4) {
-                buf0[i] = ff_abs2(v.x, v.y);
-            } else {
-                const dd p = Acc<double>::abs2(v.x, v.y);
-                const float hi = (float)p.hi;
-                buf0[i] = {hi, (float)(p.hi - (double)hi + p.lo)};
-            }
-        }
-        __syncthreads();
-        ff* src = buf0;
-        ff* dst = buf1;
-        int len = 4096;
-        for (int f = 0; f < a.nfold; ++f) {
-            const int c = a.fold[f];
-            len >>= 1;
-            for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                const int j = (int)insert_zero((uint64_t)i, c);
-                dst[i] = ff_add(src[j], src[j | (1 << c)]);
-            }
-            __syncthreads();
-            ff* t = src; src = dst; dst = t;
-        }
-        int mhigh = 0;
-        for (int j = 0; j < a.nhigh; ++j) mhigh |= (int)((base >> a.highpos[j]) & 1) << a.highj[j];
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            int m = mhigh;
-            for (int r = 0; r < a.nlow; ++r) m |= ((i >> r) & 1) << a.lowj[r];
-            bins[m] = ff_add(bins[m], src[i]);
-        }
-        __syncthreads();
-    }
-    for (int m = threadIdx.x; m < NB; m += blockDim.x) {
-        double* p = partials + 2 * ((int64_t)m * gridDim.x + blockIdx.x);
-        p[0] = (double)bins[m].hi + (double)bins[m].lo;
-        p[1] = 0.0;
-    }
-}
-
-// Marginals over more than 12 qubits (n >= 12): 2^nq bins no longer fit in shared memory. The marginal
-// bits at positions >= 12 ("high") pick a group of 2^nlow bins, and one virtual block owns a group (or one
-// of S chunks of it): it runs over the segments that differ only in non-marginal high bits, folds each one
-// as above and adds the 2^nlow sums into float-float bins in shared memory. With S = 1 the block writes
-// the final values; otherwise it writes per-chunk partials that k_probs_wide_final combines (FP64 TwoSum).
-// Output bins are written in the caller's bit order (m), so no host permutation is needed.
-struct ProbsWideArgs {
-    int nlow;             // marginal qubits below 12
-    int fold[12];         // non-marginal bits below 12, descending
-    int nfold;
-    int lowj[12];         // user index j of the r-th smallest low marginal qubit
+// Marginals for n >= 12, every nq (1..30), in one pass at close to the norm's cost. Warp segments of 1024
+// amplitudes: lane l holds amplitudes 2 (32 j + l) + h of a segment (h = bit 0, l = bits 1..5, j = bits 6..9).
+// A work item is a bin group (the marginal bits >= 10 fixed: mh) and one of S chunks of the segments that
+// differ only in non-marginal bits >= 10. WPI warps share an item and stride over its segments, each lane
+// adding |a|^2 into registers indexed by (h, j) -- 16 float-float values, 32 when qubit 0 is marginal --
+// regardless of the marginal set. Only at the end of the item are the non-marginal bits among 0..9 folded
+// (register pairs for bits 6..9, lane shuffles for bits 1..5), the item's warps merged into shared-memory
+// bins, and its 2^nlow sums written: final values (S = 1) or per-chunk partials for k_probs_warp_final.
+struct ProbsWArgs {
+    int nlow;            // marginal bits among 0..9
+    int lowj[10];        // user index j of the r-th smallest of them
+    uint32_t lowmask;    // their positions, as a mask over bits 0..9
     int nhigh;
-    int highpos[32];      // marginal positions >= 12, ascending
-    int highj[32];        // their user index j
+    int highpos[32];     // marginal positions >= 10, ascending
+    int highj[32];       // their user index j
     int nfh;
-    int fhpos[32];        // non-marginal positions >= 12, ascending
-    uint64_t S;           // chunks per bin group (a power of two dividing 2^nfh)
-    uint64_t nvb;         // virtual blocks: 2^nhigh * S
+    int fhpos[32];       // non-marginal positions >= 10, ascending
+    uint64_t S;          // chunks per bin group (a power of two dividing 2^nfh)
+    uint64_t nitems;     // 2^nhigh * S
+    int wpi;             // warps per item (a power of two, <= warps per block)
 };
 
-__device__ __forceinline__ uint64_t wide_bin(const ProbsWideArgs& a, uint64_t i, uint64_t mh) {
+__device__ __forceinline__ uint64_t probs_bin(const ProbsWArgs& a, uint64_t i, uint64_t mh) {
     uint64_t m = 0;
     for (int r = 0; r < a.nlow; ++r) m |= ((i >> r) & 1) << a.lowj[r];
     for (int j = 0; j < a.nhigh; ++j) m |= ((mh >> j) & 1) << a.highj[j];
     return m;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_probs_wide(const typename Amp<R>::T* __restrict__ psi,
-                                                    const __grid_constant__ ProbsWideArgs a,
-                                                    double* __restrict__ partials, double* __restrict__ out) {
+template <typename R, bool M0>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_probs_warp(const typename Amp<R>::T* __restrict__ psi,
+                                                       const __grid_constant__ ProbsWArgs a,
+                                                       double* __restrict__ partials, double* __restrict__ out) {
+    constexpr int NV = M0 ? 32 : 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ff* buf0 = reinterpret_cast<ff*>(smem_raw);
-    ff* buf1 = buf0 + 4096;
-    ff* bins = buf1 + 4096;
+    ff* bins = reinterpret_cast<ff*>(smem_raw);  // [items per block][2^nlow]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int ipb = nwarps / a.wpi;               // items per block
+    const int sub = warp % a.wpi, slot = warp / a.wpi;
     const int NL = 1 << a.nlow;
     const uint64_t per = (1ull << a.nfh) / a.S;
-    for (uint64_t vb = blockIdx.x; vb < a.nvb; vb += gridDim.x) {
-        const uint64_t mh = vb / a.S, sc = vb % a.S;
-        uint64_t hbits = 0;
-        for (int j = 0; j < a.nhigh; ++j) hbits |= ((mh >> j) & 1) << a.highpos[j];
-        for (int i = threadIdx.x; i < NL; i += blockDim.x) bins[i] = {0.f, 0.f};
-        for (uint64_t f = sc * per; f < (sc + 1) * per; ++f) {
-            uint64_t base = hbits;
-            for (int j = 0; j < a.nfh; ++j) base |= ((f >> j) & 1) << a.fhpos[j];
-            for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
-                const auto v = psi[base + i];
-                if constexpr (sizeof(R) == 4) {
-                    buf0[i] = ff_abs2(v.x, v.y);
-                } else {
-                    const dd p = Acc<double>::abs2(v.x, v.y);
-                    const float hi = (float)p.hi;
-                    buf0[i] = {hi, (float)(p.hi - (double)hi + p.lo)};
+    for (uint64_t it0 = (uint64_t)blockIdx.x * ipb; it0 < a.nitems; it0 += (uint64_t)gridDim.x * ipb) {
+        const uint64_t it = it0 + slot;
+        const bool active = it < a.nitems;
+        const uint64_t mh = active ? it / a.S : 0, sc = active ? it % a.S : 0;
+        uint64_t hbits = 0;  // segment-index bits (position - 10)
+        for (int j = 0; j < a.nhigh; ++j) hbits |= ((mh >> j) & 1) << (a.highpos[j] - 10);
+        ff v[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = {0.f, 0.f};
+        if (active) {
+            for (uint64_t f = sc * per + sub; f < (sc + 1) * per; f += a.wpi) {
+                uint64_t sidx = hbits;
+                for (int j = 0; j < a.nfh; ++j) sidx |= ((f >> j) & 1) << (a.fhpos[j] - 10);
+                const uint64_t base = sidx * 512 + lane;  // amplitude-pair index
+                constexpr int NB = M0 ? 4 : 8;  // loads per batch (registers: NV accumulators + 4 NB values)
+#pragma unroll
+                for (int hh = 0; hh < 16 / NB; ++hh) {
+                    ff p[NB], q[NB];
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) load_p2<R>(psi, base + 32 * (NB * hh + j), p[j], q[j]);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        if constexpr (M0) {
+                            v[NB * hh + j] = ff_add(v[NB * hh + j], p[j]);
+                            v[16 + NB * hh + j] = ff_add(v[16 + NB * hh + j], q[j]);
+                        } else {
+                            v[NB * hh + j] = ff_add(v[NB * hh + j], ff_add(p[j], q[j]));
+                        }
+                    }
                 }
             }
-            __syncthreads();
-            ff* src = buf0;
-            ff* dst = buf1;
-            int len = 4096;
-            for (int fb = 0; fb < a.nfold; ++fb) {
-                const int c = a.fold[fb];
-                len >>= 1;
-                for (int i = threadIdx.x; i < len; i += blockDim.x) {
-                    const int j = (int)insert_zero((uint64_t)i, c);
-                    dst[i] = ff_add(src[j], src[j | (1 << c)]);
+        }
+        // fold the non-marginal bits 6..9 (register index bits), then 1..5 (lane bits)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+            if (!((a.lowmask >> (6 + bb)) & 1)) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if ((j >> bb) & 1) continue;
+                    v[j] = ff_add(v[j], v[j | (1 << bb)]);
+                    if constexpr (M0) v[16 + j] = ff_add(v[16 + j], v[16 + (j | (1 << bb))]);
                 }
-                __syncthreads();
-                ff* t = src; src = dst; dst = t;
             }
-            for (int i = threadIdx.x; i < NL; i += blockDim.x) bins[i] = ff_add(bins[i], src[i]);
-            __syncthreads();
         }
-        for (int i = threadIdx.x; i < NL; i += blockDim.x) {
-            const double v = (double)bins[i].hi + (double)bins[i].lo;
-            if (a.S == 1) out[wide_bin(a, (uint64_t)i, mh)] = v;
-            else partials[(mh * (uint64_t)NL + (uint64_t)i) * a.S + sc] = v;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            if (!((a.lowmask >> (1 + b)) & 1)) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) v[k] = ff_add(v[k], shfl_xor_ff(v[k], 1 << b));
+            }
         }
+        // merge the item's warps into its bins (index = the marginal bits among 0..9, in position order)
+        ff* mybins = bins + (size_t)slot * NL;
+        for (int i = threadIdx.x; i < ipb * NL; i += blockDim.x) bins[i] = {0.f, 0.f};
         __syncthreads();
+        const uint32_t lbits = (uint32_t)lane << 1;
+        for (int r = 0; r < a.wpi; ++r) {
+            if (sub == r && active && (lbits & ~a.lowmask & 0x3Eu) == 0) {
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const uint32_t x = ((uint32_t)(k & 15) << 6) | lbits | (uint32_t)(k >> 4);
+                    if ((x & ~a.lowmask & 0x3C0u) != 0) continue;  // a register folded into another
+                    int idx = 0, o = 0;
+                    for (int b = 0; b < 10; ++b)
+                        if ((a.lowmask >> b) & 1) { idx |= (int)((x >> b) & 1) << o; ++o; }
+                    mybins[idx] = ff_add(mybins[idx], v[k]);
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < ipb * NL; i += blockDim.x) {
+            const uint64_t its = it0 + (uint64_t)(i / NL);
+            if (its >= a.nitems) continue;
+            const uint64_t mhs = its / a.S, scs = its % a.S, bi = (uint64_t)(i % NL);
+            const double val = (double)bins[i].hi + (double)bins[i].lo;
+            if (a.S == 1) out[probs_bin(a, bi, mhs)] = val;
+            else partials[((mhs << a.nlow) + bi) * a.S + scs] = val;
+        }
+        __syncthreads();  // the bins are reused by the next items
     }
 }
 
-__global__ void __launch_bounds__(256) k_probs_wide_final(const double* __restrict__ partials,
-                                                          const __grid_constant__ ProbsWideArgs a,
+__global__ void __launch_bounds__(256) k_probs_warp_final(const double* __restrict__ partials,
+                                                          const __grid_constant__ ProbsWArgs a,
                                                           double* __restrict__ out) {
     const uint64_t NL = 1ull << a.nlow, nbins = NL << a.nhigh;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nbins; p += (uint64_t)gridDim.x * blockDim.x) {
         dd acc = {0.0, 0.0};
         for (uint64_t sc = 0; sc < a.S; ++sc) acc = dd_add(acc, dd{partials[p * a.S + sc], 0.0});
-        out[wide_bin(a, p % NL, p / NL)] = acc.hi + acc.lo;
+        out[probs_bin(a, p % NL, p / NL)] = acc.hi + acc.lo;
     }
 }
 
@@ -754,53 +735,61 @@ cudaError_t run_pauli(int dtype, const void* psi, int n, const char* paulis, Red
     return cudaSuccess;
 }
 
-// nq > 12 (so n > 12): bins in a temporary device buffer (8 B x 2^nq, stream-ordered), one copy to the host.
-static cudaError_t run_probs_wide(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
+// n >= 12: k_probs_warp (see above); the 2^nq results go to r.scan (nq <= 12) or to a temporary device
+// buffer of 8 x 2^nq bytes from the stream-ordered allocator, then one copy to the host.
+static cudaError_t run_probs_warp(int dtype, const void* psi, int n, const int* qubits, int nq, ReduceScratch& r,
                                   cudaStream_t s, const DevInfo& d, double* out) {
-    ProbsWideArgs a;
+    ProbsWArgs a;
     std::memset(&a, 0, sizeof(a));
     std::vector<std::pair<int, int>> low, high;  // (position, user index)
     uint64_t marg = 0;
     for (int j = 0; j < nq; ++j) {
         marg |= 1ull << qubits[j];
-        (qubits[j] < kSegBits ? low : high).push_back({qubits[j], j});
+        (qubits[j] < 10 ? low : high).push_back({qubits[j], j});
     }
     std::sort(low.begin(), low.end());
     std::sort(high.begin(), high.end());
     a.nlow = (int)low.size();
-    for (int k = 0; k < a.nlow; ++k) a.lowj[k] = low[k].second;
-    for (int b = kSegBits - 1; b >= 0; --b)
-        if (!((marg >> b) & 1)) a.fold[a.nfold++] = b;
+    for (int k = 0; k < a.nlow; ++k) { a.lowj[k] = low[k].second; a.lowmask |= 1u << low[k].first; }
     a.nhigh = (int)high.size();
     for (int k = 0; k < a.nhigh; ++k) { a.highpos[k] = high[k].first; a.highj[k] = high[k].second; }
-    for (int b = kSegBits; b < n; ++b)
+    for (int b = 10; b < n; ++b)
         if (!((marg >> b) & 1)) a.fhpos[a.nfh++] = b;
-    // split the non-marginal high range only while the bin groups alone give too few blocks; the partials
-    // (2^nq x S doubles) must fit the scratch buffer
+    // chunks per bin group: split while the items alone keep too few warps busy, each item still spans
+    // at least 16 segments, and the partials (2^nq x S doubles) fit the scratch buffer
+    const uint64_t F = 1ull << a.nfh, target_warps = (uint64_t)d.num_sms * 32;
     uint64_t S = 1;
-    while ((S << a.nhigh) < 256 && S < (1ull << a.nfh) && (uint64_t)(S * 2) << nq <= (uint64_t)kPartialDoubles) S <<= 1;
+    while (F / S >= 16 && ((S << a.nhigh) * 8) < target_warps && ((S * 2) << nq) <= (uint64_t)kPartialDoubles) S <<= 1;
     a.S = S;
-    a.nvb = S << a.nhigh;
+    a.nitems = S << a.nhigh;
+    a.wpi = (int)std::min<uint64_t>(8, F / S);
+    const int ipb = 8 / a.wpi;
+    const size_t smem = sizeof(ff) * (size_t)ipb << a.nlow;
+    const int nb = (int)std::max<uint64_t>(1, std::min<uint64_t>((a.nitems + ipb - 1) / ipb, (uint64_t)d.num_sms * 2));
     const size_t bytes = sizeof(double) << nq;
-    double* dout = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dout), bytes, s);
-    if (e != cudaSuccess) return e;
-    const int nb = (int)std::min<uint64_t>(a.nvb, (uint64_t)d.num_sms * 2);
-    const size_t smem = 3 * 4096 * sizeof(ff);
-    if (dtype == QSIM_C64) {
-        e = cudaFuncSetAttribute(k_probs_wide<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) k_probs_wide<float><<<nb, 256, smem, s>>>((const float2*)psi, a, r.partials, dout);
-    } else {
-        e = cudaFuncSetAttribute(k_probs_wide<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) k_probs_wide<double><<<nb, 256, smem, s>>>((const double2*)psi, a, r.partials, dout);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
+    double* dout = r.scan;
+    cudaError_t e = cudaSuccess;
+    const bool tmp = nq > kSegBits;
+    if (tmp && (e = cudaMallocAsync(reinterpret_cast<void**>(&dout), bytes, s)) != cudaSuccess) return e;
+    const bool m0 = (a.lowmask & 1u) != 0;
+    auto launch = [&](auto kern, auto typed_psi) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) {
+            kern<<<nb, 256, smem, s>>>(typed_psi, a, r.partials, dout);
+            err = cudaGetLastError();
+        }
+        return err;
+    };
+    const float2* p32 = static_cast<const float2*>(psi);
+    const double2* p64 = static_cast<const double2*>(psi);
+    if (dtype == QSIM_C64) e = m0 ? launch(k_probs_warp<float, true>, p32) : launch(k_probs_warp<float, false>, p32);
+    else e = m0 ? launch(k_probs_warp<double, true>, p64) : launch(k_probs_warp<double, false>, p64);
     if (e == cudaSuccess && S > 1) {
-        k_probs_wide_final<<<(unsigned)std::min<uint64_t>(((1ull << nq) + 255) / 256, 4096), 256, 0, s>>>(r.partials, a, dout);
+        k_probs_warp_final<<<(unsigned)std::min<uint64_t>(((1ull << nq) + 255) / 256, 4096), 256, 0, s>>>(r.partials, a, dout);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, s);
-    const cudaError_t ef = cudaFreeAsync(dout, s);
+    const cudaError_t ef = tmp ? cudaFreeAsync(dout, s) : cudaSuccess;
     const cudaError_t es = cudaStreamSynchronize(s);
     return e != cudaSuccess ? e : (ef != cudaSuccess ? ef : es);
 }
@@ -822,46 +811,13 @@ cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int 
         if (dtype == QSIM_C64) k_probs_small<float><<<1, 256, 0, s>>>((const float2*)psi, n, a, dq, r.partials);
         else k_probs_small<double><<<1, 256, 0, s>>>((const double2*)psi, n, a, dq, r.partials);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(r.hresult, r.partials, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        std::vector<double> h(2 * (size_t)NB);  // up to 2 x 2^11 values: more than the pinned result buffer
+        if ((e = cudaMemcpyAsync(h.data(), r.partials, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-        for (int m = 0; m < NB; ++m) out[m] = r.hresult[2 * m] + r.hresult[2 * m + 1];
+        for (int m = 0; m < NB; ++m) out[m] = h[2 * m] + h[2 * m + 1];
         return cudaSuccess;
     }
-    if (nq > kSegBits) return run_probs_wide(dtype, psi, n, qubits, nq, r, s, d, out);
-    std::vector<std::pair<int, int>> low;  // (position, user index)
-    for (int j = 0; j < nq; ++j) {
-        if (qubits[j] < kSegBits) low.push_back({qubits[j], j});
-        else { a.highpos[a.nhigh] = qubits[j]; a.highj[a.nhigh] = j; ++a.nhigh; }
-    }
-    std::sort(low.begin(), low.end());
-    a.nlow = (int)low.size();
-    for (int r2 = 0; r2 < a.nlow; ++r2) a.lowj[r2] = low[r2].second;
-    for (int b = kSegBits - 1; b >= 0; --b) {
-        bool marg = false;
-        for (auto& pr : low) marg |= pr.first == b;
-        if (!marg) a.fold[a.nfold++] = b;
-    }
-    const uint64_t nseg = 1ull << (n - kSegBits);
-    int nb = (int)std::min<int64_t>((int64_t)d.num_sms * 2, (int64_t)nseg);
-    nb = (int)std::min<int64_t>(nb, kPartialDoubles / (2 * NB));
-    nb = std::max(1, nb);
-    const size_t smem = 2 * 4096 * sizeof(ff) + (size_t)NB * sizeof(ff);
-    if (dtype == QSIM_C64) {
-        if ((e = cudaFuncSetAttribute(k_probs_seg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        k_probs_seg<float><<<nb, 256, smem, s>>>((const float2*)psi, nseg, a, r.partials);
-    } else {
-        if ((e = cudaFuncSetAttribute(k_probs_seg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-        k_probs_seg<double><<<nb, 256, smem, s>>>((const double2*)psi, nseg, a, r.partials);
-    }
-    // result buffer holds 256 doubles; bins beyond that reduce into the tail of the segment buffer
-    double* dres = NB <= 128 ? r.result : r.scan;
-    k_final_dd<<<NB, 256, 0, s>>>(r.partials, nb, dres);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    std::vector<double> h(2 * NB);
-    if ((e = cudaMemcpyAsync(h.data(), dres, sizeof(double) * 2 * NB, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    for (int m = 0; m < NB; ++m) out[m] = h[2 * m] + h[2 * m + 1];
-    return cudaSuccess;
+    return run_probs_warp(dtype, psi, n, qubits, nq, r, s, d, out);
 }
 
 cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,

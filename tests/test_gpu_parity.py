@@ -401,6 +401,19 @@ def test_probs_wide_marginals(qsim, dtype, n, qs):
         np.testing.assert_allclose(got, np.abs(ref[x]) ** 2, atol=1e-15, rtol=0)
 
 
+@pytest.mark.parametrize("dtype", DT)
+def test_probs_small_state_many_bins(qsim, dtype):
+    """n < 12 with 8..11 marginal qubits (more results than the fixed-size result buffer holds)."""
+    n = 11
+    psi = random_state(n, 5)
+    st = make_state(qsim, n, dtype, psi0=psi)
+    ref = st.get_state().astype(np.complex128)
+    rng = np.random.default_rng(9)
+    for nq in (8, 11):
+        q = [int(x) for x in rng.permutation(n)[:nq]]
+        np.testing.assert_allclose(st.probs(q), oracle.probs(ref, n, q), atol=1e-14, rtol=0)
+
+
 def test_probs_limits(qsim):
     st = make_state(qsim, 14, 0)
     with pytest.raises(qsim.QsimError) as e:
