@@ -593,7 +593,9 @@ def run_qft(args):
     out = {}
     for name, kw in [("plain", dict(mode=0, max_fused=1)), ("simt5", dict(mode=1, max_fused=5)),
                      ("tf32x3_k5", dict(mode=1, max_fused=5, precision=1, tc_min_k=5)),
-                     ("bf16x6_k5", dict(mode=1, max_fused=5, precision=3, tc_min_k=5))]:
+                     ("bf16x6_k5", dict(mode=1, max_fused=5, precision=3, tc_min_k=5)),
+                     ("tf32x3_k6", dict(mode=1, max_fused=6, precision=1, tc_min_k=5)),
+                     ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5))]:
         p = qsim.Plan(c, **kw)
 
         def step(i, p=p):
@@ -612,7 +614,7 @@ def run_qft(args):
                      "achieved_gbs": p.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9,
                      "max_err_sampled": float(np.max(np.abs(got - ref)))}
     best = min((k for k in out if k != "plain"), key=lambda k: out[k]["ms_per_step"])
-    line = _common_line(f"gate-applications/s, {n}-qubit QFT (with swaps), complex64, fused k=5 vs plain",
+    line = _common_line(f"gate-applications/s, {n}-qubit QFT (with swaps), complex64, fused (k = 5, 6) vs plain",
                         out[best]["gates_per_s"], UNIT, args, out[best]["ms_per_step"],
                         "f32" if best.startswith(("plain", "simt")) else best[:4],
                         {"workload": f"QFT n={n} from |x>, x={x}, {len(c)} gates", "path": best},

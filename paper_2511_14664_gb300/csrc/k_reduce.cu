@@ -104,6 +104,17 @@ __device__ __forceinline__ void load_p2(const typename Amp<R>::T* psi, uint64_t 
     }
 }
 
+// Sum of N float-float values as a pairwise tree (depth log2 N instead of a serial chain of N adds).
+template <int N>
+__device__ __forceinline__ ff ff_tree_sum(ff (&q)[N]) {
+#pragma unroll
+    for (int w = N / 2; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) q[i] = ff_add(q[i], q[i + w]);
+    }
+    return q[0];
+}
+
 // ============================================================================================================
 // Norm and overlap
 // ============================================================================================================
@@ -122,8 +133,7 @@ __global__ void __launch_bounds__(256) k_norm_pairs(const typename Amp<R>::T* __
             if (k < npairs) load_p2<R>(psi, k, q[2 * u], q[2 * u + 1]);
             else q[2 * u] = q[2 * u + 1] = ff{0.f, 0.f};
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc = ff_add(acc, q[u]);
+        acc = ff_add(acc, ff_tree_sum(q));
     }
     const dd r = block_sum_acc<float>(acc, sm);
     if (threadIdx.x == 0) {
@@ -384,10 +394,11 @@ __device__ __forceinline__ ff load_p(const typename Amp<R>::T* psi, uint64_t i) 
 
 // ---- <Z> statistics with one warp per 1024-amplitude segment -------------------------------------------------
 // Lane l reads pairs l + 32 j (j < 16) of segment s, i.e. amplitudes x = 1024 s + 2 (l + 32 j) + e: index bit 0
-// is e, bits 1..5 are the lane, bits 6..9 are j. Every quantity of bits 0..9 accumulates per thread across all
-// its segments (no barrier per segment); X_9 (bits 9, 10) uses the segment's own split by bit 9; the segment
-// total goes to W[s] for the quantities of bits >= 10 (k_zstats_hi). Quantities per block at the end:
-// 0: T, 1..10: S_0..S_9, 11..20: X_0..X_9.
+// is e, bits 1..5 are the lane, bits 6..9 are j. Each lane keeps, across all its segments (no barrier per
+// segment), V[j] = sum of |a|^2 over its amplitudes with that j, plus S_0 (e = 1); the quantities of bits 6..9
+// follow from V at the end. Per segment, two 8-term trees give the halves split by bit 9 (for X_9, bits 9 and
+// 10) and the segment total, which goes to W[s] for the quantities of bits >= 10 (k_zstats_hi). Quantities per
+// block at the end: 0: T, 1..10: S_0..S_9, 11..20: X_0..X_9.
 constexpr int kZW = 21;
 
 template <typename R>
@@ -397,30 +408,45 @@ __global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* _
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const ff Z = {0.f, 0.f};
-    ff T = Z, S0 = Z, S6 = Z, S7 = Z, S8 = Z, S9 = Z, X6 = Z, X7 = Z, X8 = Z, X9 = Z;
+    ff V[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) V[j] = Z;
+    ff S0 = Z, X9 = Z;
     for (uint64_t s = warp0; s < nseg; s += nwarps) {
-        ff P[16], Q[16];
+        ff pj[16], qj[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) load_p2<R>(psi, s * 512 + lane + 32 * j, P[j], Q[j]);  // P = even amp for now
-        ff Ts = Z, S9s = Z;
+        for (int hh = 0; hh < 2; ++hh) {
+            ff P[8], Q[8];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const ff pj = ff_add(P[j], Q[j]);
-            S0 = ff_add(S0, Q[j]);
-            Ts = ff_add(Ts, pj);
-            if (j & 1) S6 = ff_add(S6, pj);
-            if (j & 2) S7 = ff_add(S7, pj);
-            if (j & 4) S8 = ff_add(S8, pj);
-            if (j & 8) S9s = ff_add(S9s, pj);
-            if ((j ^ (j >> 1)) & 1) X6 = ff_add(X6, pj);
-            if (((j >> 1) ^ (j >> 2)) & 1) X7 = ff_add(X7, pj);
-            if (((j >> 2) ^ (j >> 3)) & 1) X8 = ff_add(X8, pj);
+            for (int j = 0; j < 8; ++j) load_p2<R>(psi, s * 512 + lane + 32 * (8 * hh + j), P[j], Q[j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                pj[8 * hh + j] = ff_add(P[j], Q[j]);
+                qj[8 * hh + j] = Q[j];
+                V[8 * hh + j] = ff_add(V[8 * hh + j], pj[8 * hh + j]);
+            }
         }
-        T = ff_add(T, Ts);
-        S9 = ff_add(S9, S9s);
-        X9 = ff_add(X9, (s & 1) ? ff_add(Ts, ff_neg(S9s)) : S9s);
-        const ff tot = warp_sum_ff(Ts);
+        S0 = ff_add(S0, ff_tree_sum(qj));
+        ff lo8[8], hi8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { lo8[j] = pj[j]; hi8[j] = pj[8 + j]; }
+        const ff lo = ff_tree_sum(lo8), hi = ff_tree_sum(hi8);  // bit 9 clear / set
+        X9 = ff_add(X9, (s & 1) ? lo : hi);
+        const ff tot = warp_sum_ff(ff_add(lo, hi));
         if (lane == 0) W[s] = (double)tot.hi + (double)tot.lo;
+    }
+    // bits 6..9 from V: S_{6+b} = sum over j with bit b set; X_{6+b} = sum over j with bits b, b+1 different
+    ff T = Z, S6 = Z, S7 = Z, S8 = Z, S9 = Z, X6 = Z, X7 = Z, X8 = Z;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        T = ff_add(T, V[j]);
+        if (j & 1) S6 = ff_add(S6, V[j]);
+        if (j & 2) S7 = ff_add(S7, V[j]);
+        if (j & 4) S8 = ff_add(S8, V[j]);
+        if (j & 8) S9 = ff_add(S9, V[j]);
+        if ((j ^ (j >> 1)) & 1) X6 = ff_add(X6, V[j]);
+        if (((j >> 1) ^ (j >> 2)) & 1) X7 = ff_add(X7, V[j]);
+        if (((j >> 2) ^ (j >> 3)) & 1) X8 = ff_add(X8, V[j]);
     }
     // per-thread contributions; lane bit b is index bit b + 1
     ff c[kZW];
@@ -529,8 +555,7 @@ __global__ void __launch_bounds__(256) k_segsum(const typename Amp<R>::T* __rest
                 if (k < pairs) load_p2<R>(psi, s * pairs + k, q[2 * u], q[2 * u + 1]);
                 else q[2 * u] = q[2 * u + 1] = ff{0.f, 0.f};
             }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) acc = ff_add(acc, q[u]);
+            acc = ff_add(acc, ff_tree_sum(q));
         }
         const ff tot = warp_sum_ff(acc);
         if (lane == 0) W[s] = (double)tot.hi + (double)tot.lo;
@@ -672,7 +697,7 @@ static cudaError_t fetch(ReduceScratch& r, int nvals, cudaStream_t s) {
 }
 
 static int reduce_blocks(const DevInfo& d, uint64_t N, int nq) {
-    int64_t b = std::min<int64_t>((int64_t)d.num_sms * 4, (int64_t)((N + 255) / 256));
+    int64_t b = std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)((N + 255) / 256));
     b = std::min<int64_t>(b, kPartialDoubles / (2 * std::max(1, nq)));
     return (int)std::max<int64_t>(1, b);
 }
