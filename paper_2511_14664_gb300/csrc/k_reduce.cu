@@ -118,19 +118,22 @@ __device__ __forceinline__ ff ff_tree_sum(ff (&q)[N]) {
 // ============================================================================================================
 // Norm and overlap
 // ============================================================================================================
-// sum |a|^2 over npairs amplitude pairs: four independent 16-byte loads in flight per thread.
+// sum |a|^2 over npairs amplitude pairs. Each block reads one contiguous slice of the state (so the blocks
+// in flight spread over the whole vector rather than sweeping it as one narrow window), eight independent
+// 16-byte loads in flight per thread, summed as a tree.
 template <typename R>
 __global__ void __launch_bounds__(256) k_norm_pairs(const typename Amp<R>::T* __restrict__ psi, uint64_t npairs,
                                                     double* partials) {
     __shared__ dd sm[32];
     ff acc = {0.f, 0.f};
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += 4 * stride) {
+    const uint64_t per = (npairs + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = (uint64_t)blockIdx.x * per, hi = min(npairs, lo + per);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += 4 * blockDim.x) {
         ff q[8];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint64_t k = i + u * stride;
-            if (k < npairs) load_p2<R>(psi, k, q[2 * u], q[2 * u + 1]);
+            const uint64_t k = i + u * blockDim.x;
+            if (k < hi) load_p2<R>(psi, k, q[2 * u], q[2 * u + 1]);
             else q[2 * u] = q[2 * u + 1] = ff{0.f, 0.f};
         }
         acc = ff_add(acc, ff_tree_sum(q));
