@@ -653,6 +653,38 @@ def run_tfim_batch(args):
     gbs = b.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9
     widths = sorted(set(c.n for c in cs))
     kmap = {str(n): chosen[[c.n for c in cs].index(n)] for n in widths}
+    # Baselines the batched launch must beat: the same circuits one after another, each through its own
+    # plan (CUDA-graph replay) and its own <Z_i>, <Z_i Z_i+1> readout: plain per-gate passes, and the fused
+    # plans with the width the tuner chose.
+    one_by_one = {}
+    if not args.no_variants:
+        states = {n: qsim.State(n, qsim.C64) for n in widths}
+        for name, mk in (("plain", lambda c: dict(mode=qsim.RUN_PLAIN, max_fused=1)),
+                         ("fused", lambda c: dict(mode=qsim.RUN_FUSED, max_fused=max(1, int(kmap[str(c.n)]))))):
+            plans = [qsim.Plan(c, qsim.C64, use_graph=True, **mk(c)) for c in cs]
+            def run_all(keep=None):
+                for i, (c, p) in enumerate(zip(cs, plans)):
+                    st = states[c.n]
+                    st.set_basis(0)
+                    p.execute(st)
+                    z = st.expect_z()
+                    if keep is not None:
+                        keep.append(z)
+            run_all()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            zs = []
+            run_all(zs)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t
+            dz = max(float(np.max(np.abs(zs[i][0] - res[i][0]))) for i in range(len(cs)))
+            one_by_one[name] = {"ms": sec * 1000.0, "gates_per_s": gates / sec,
+                                "passes": sum(p.info["passes"] for p in plans),
+                                "max_abs_diff_zi_vs_batch": dz}
+            for p in plans:
+                p.close()
+        for st in states.values():
+            st.close()
     line = _common_line(f"gate-applications/s, batch of {len(cs)} TFIM chains (10-{args.nmax} qubits, 8-32 Trotter "
                         "steps), complex64, one persistent launch", gates / (ms / 1000.0), UNIT, args, ms, "f32",
                         {"workload": f"{len(cs)} TFIM chains seed 4, {gates} gates, "
@@ -666,7 +698,7 @@ def run_tfim_batch(args):
                         e2e={"value": gates / e2e_s, "unit": UNIT, "h2d_bytes_per_step":
                              sum(16 * 4 ** len(g.targets) for c in cs for g in c.gates),
                              "d2h_bytes_per_step": 8 * sum(2 * c.n - 1 for c in cs)},
-                        tune_s=tune_s, sample_zi0=list(res[0][0][:4]))
+                        tune_s=tune_s, sample_zi0=list(res[0][0][:4]), one_by_one=one_by_one)
     if not args.no_cpu:
         import oracle as oracle_mod
         # oracle on the smallest circuits until the time budget runs out; work ~ gates x 2^n

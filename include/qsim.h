@@ -199,6 +199,9 @@ typedef struct {
     int32_t precision;        /* QSIM_PREC_* used by the pass */
     int64_t gates;            /* input gates merged into this pass */
     double algorithmic_bytes; /* HBM bytes the pass must read + write */
+    int32_t targets[QSIM_MAX_TARGETS];   /* index bits the matrix acts on, in the order of its index bits
+                                            (k of them; zero for a reorder pass) */
+    int32_t controls[QSIM_MAX_CONTROLS]; /* control bits (nc of them) */
 } qsim_pass_info;
 int qsim_plan_num_passes(qsim_plan_h plan, int64_t* out);
 int qsim_plan_pass_info(qsim_plan_h plan, int64_t i, qsim_pass_info* out);

@@ -193,14 +193,35 @@ struct Args {
 constexpr int kDataWarps = 8;  // two per TMEM lane quadrant; 9 warps leave room for a two-tile prefetch
 constexpr int kThreadsWS = (kDataWarps + 1) * 32;
 
+// How the data warps move a tile between global memory and their registers (lane = row of the tile):
+enum Mode {
+    kRowsInLanes = 0,   // one 8-byte amplitude per access
+    kPairsInLanes = 1,  // qubit 0 is target 0: columns 2i, 2i+1 move as one 16-byte vector
+    kQuadsInLanes = 2,  // qubits 0 and 1 are targets 0 and 1: columns 4i..4i+3 move as one 32-byte vector, so
+                        // each lane reads and writes whole 32-byte sectors
+};
+
+// 32-byte global accesses (sm_100 and later); the address must be 32-byte aligned.
+__device__ __forceinline__ void ld_v8(const float2* p, float2& a, float2& b, float2& c, float2& d) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st_v8(float2* p, const uint32_t* v) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(addr) : "memory");
 }
 
-template <int K, int PREC, bool P0>
+template <int K, int PREC, int MODE>
 __global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
+    constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes;
     using C = Cfg<PREC>;
     constexpr bool BF16 = C::esize == 2;
     constexpr int P = C::planes;
@@ -318,7 +339,13 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
         auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-            if constexpr (P0) {
+            if constexpr (Q0) {
+#pragma unroll
+                for (int j = 0; j < CPT; j += 4) {
+                    ld_v8(psi + b + vCol[j], X[j], X[j + 1], X[j + 2], X[j + 3]);
+                    asm volatile("" ::: "memory");
+                }
+            } else if constexpr (P0) {
 #pragma unroll
                 for (int j = 0; j < CPT; j += 2) {
                     const float4 v = *reinterpret_cast<const float4*>(psi + b + vCol[j]);
@@ -379,7 +406,13 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                 uint32_t v[2 * QE];
                 tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
                 wait_ld();
-                if constexpr (P0) {
+                if constexpr (Q0) {
+#pragma unroll
+                    for (int j = 0; j < QE; j += 4) {
+                        st_v8(psi + b + vCol[h * QE + j], v + 2 * j);
+                        asm volatile("" ::: "memory");
+                    }
+                } else if constexpr (P0) {
 #pragma unroll
                     for (int j = 0; j < QE; j += 2) {
                         *reinterpret_cast<float4*>(psi + b + vCol[h * QE + j]) =
@@ -647,7 +680,7 @@ size_t smem_bytes(int K, int planes, int esize) {
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
-template <int K, int PREC, bool P0>
+template <int K, int PREC, int MODE>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
@@ -658,15 +691,17 @@ cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cud
         return cudaGetLastError();
     };
     // BF16x6 (three A planes, the heaviest split) runs faster on 16 warps with two A buffers than on the
-    // 8 data warps of the warp-specialised kernel
-    if constexpr (PREC == QSIM_PREC_BF16X6) return launch(k_tc_block_a2<K, PREC, P0>, kThreads);
-    else return launch(k_tc_block<K, PREC, P0>, kThreadsWS);
+    // 8 data warps of the warp-specialised kernel (which alone has the 32-byte path)
+    if constexpr (PREC == QSIM_PREC_BF16X6) return launch(k_tc_block_a2<K, PREC, MODE != kRowsInLanes>, kThreads);
+    else return launch(k_tc_block<K, PREC, MODE>, kThreadsWS);
 }
 
 template <int K, int PREC>
 cudaError_t apply_t(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
-    if (a.tpos[0] == 0) return apply_p<K, PREC, true>(psi, a, dB, err, s, d);
-    return apply_p<K, PREC, false>(psi, a, dB, err, s, d);
+    if (a.tpos[0] == 0 && a.tpos[1] == 1 && PREC != QSIM_PREC_BF16X6 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
+        return apply_p<K, PREC, kQuadsInLanes>(psi, a, dB, err, s, d);
+    if (a.tpos[0] == 0) return apply_p<K, PREC, kPairsInLanes>(psi, a, dB, err, s, d);
+    return apply_p<K, PREC, kRowsInLanes>(psi, a, dB, err, s, d);
 }
 
 }  // namespace tc

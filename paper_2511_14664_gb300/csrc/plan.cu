@@ -594,6 +594,10 @@ int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
     out->precision = op.precision;
     out->gates = op.gates;
     out->algorithmic_bytes = op_bytes(op, p->n, p->dtype == QSIM_C64 ? 8 : 16);
+    std::memset(out->targets, 0, sizeof(out->targets));
+    std::memset(out->controls, 0, sizeof(out->controls));
+    for (int j = 0; j < op.k && j < QSIM_MAX_TARGETS; ++j) out->targets[j] = op.targets[j];
+    for (int j = 0; j < op.nc && j < QSIM_MAX_CONTROLS; ++j) out->controls[j] = op.controls[j];
     return QSIM_OK;
 }
 

@@ -46,7 +46,8 @@ class RunOpts(ctypes.Structure):
 
 class PassInfo(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("nc", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("gates", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double)]
+                ("precision", ctypes.c_int32), ("gates", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double),
+                ("targets", ctypes.c_int32 * 8), ("controls", ctypes.c_int32 * 8)]
 
 
 PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder"}
@@ -323,7 +324,7 @@ class Plan:
         _check(lib().qsim_plan_execute_range(state.h, self.p, int(first), int(count)))
 
     def passes(self):
-        """Per-pass descriptions: kind, k, controls, precision, merged gates, algorithmic bytes."""
+        """Per-pass descriptions: kind, k, controls, precision, merged gates, algorithmic bytes, qubits."""
         num = ctypes.c_int64()
         _check(lib().qsim_plan_num_passes(self.p, ctypes.byref(num)))
         out = []
@@ -331,7 +332,8 @@ class Plan:
             pi = PassInfo()
             _check(lib().qsim_plan_pass_info(self.p, i, ctypes.byref(pi)))
             out.append({"kind": PASS_KINDS[pi.kind], "k": pi.k, "nc": pi.nc, "precision": pi.precision,
-                        "gates": pi.gates, "algorithmic_bytes": pi.algorithmic_bytes})
+                        "gates": pi.gates, "algorithmic_bytes": pi.algorithmic_bytes,
+                        "targets": list(pi.targets[:pi.k]), "controls": list(pi.controls[:pi.nc])})
         return out
 
     def close(self):

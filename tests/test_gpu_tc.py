@@ -56,6 +56,57 @@ def test_single_block(qsim, prec, k, targets):
     check(st.get_state(), ref, n, *BLOCK_TOL[prec])
 
 
+# Target patterns that take the block kernel's different data paths: lanes on rows with 8-byte accesses
+# (targets from qubit 3 up), lanes on rows with 16-byte pairs (qubit 0 a target), tiles staged in shared
+# memory by bulk copies (targets exactly qubits 0..k-1 in order), and low runs from qubit 0, 1 or 2 given
+# in scrambled order (rows interleaved with targets in the lowest address bits).
+PATH_TARGETS = {
+    "from3": (8, 3, 5, 4, 7, 6),
+    "run_from0_in_order": (0, 1, 2, 3, 4, 5),
+    "quads_spread": (0, 1, 9, 4, 20, 13),
+    "run_from0_in_order": (0, 1, 2, 3, 4, 5),
+    "even_from0": (0, 2, 4, 6, 8, 10),
+    "run_from0": (3, 0, 5, 1, 4, 2),
+    "run_from1": (6, 1, 2, 3, 4, 5),
+    "run_from2": (2, 7, 3, 4, 6, 5),
+    "low_and_high": (1, 21, 3, 4, 17, 2),
+}
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("path", list(PATH_TARGETS))
+def test_block_paths_many_tiles(qsim, prec, path):
+    """23 qubits: 1024 tiles, so every CTA runs several tiles through the pipeline (two accumulators, the
+    epilogue of tile i-1 behind the MMAs of tile i) and some CTAs run one more than others."""
+    n = 23
+    t = PATH_TARGETS[path]
+    rng = np.random.default_rng(len(path) * 11 + PRECS[prec])
+    U = W.haar_unitary(64, rng)
+    psi0 = random_state(n, 5)
+    st = qsim.State(n, qsim.C64)
+    st.set_state(psi0)
+    st.apply_fused(t, U, PRECS[prec])
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, t, (), U)
+    check(st.get_state(), ref, n, *BLOCK_TOL[prec])
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("path", ["from3", "run_from0_in_order", "run_from0", "run_from1"])
+def test_block_paths_k5(qsim, prec, path):
+    n = 21
+    t = PATH_TARGETS[path][:5]
+    rng = np.random.default_rng(len(path) * 13 + PRECS[prec])
+    U = W.haar_unitary(32, rng)
+    psi0 = random_state(n, 6)
+    st = qsim.State(n, qsim.C64)
+    st.set_state(psi0)
+    st.apply_fused(t, U, PRECS[prec])
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, t, (), U)
+    check(st.get_state(), ref, n, *BLOCK_TOL[prec])
+
+
 @pytest.mark.parametrize("prec", list(PRECS))
 def test_smallest_state_single_tile(qsim, prec):
     """n = k + 7: exactly one 128-row tile."""
