@@ -192,6 +192,8 @@ int qsim_plan_destroy(qsim_plan_h plan);
 #define QSIM_PASS_DENSE_TILE 2  /* dense k = 5, 6 on CUDA cores through shared memory */
 #define QSIM_PASS_TC 3          /* dense block on tensor cores (complex64) */
 #define QSIM_PASS_REORDER 4     /* qubit reorder (exchange of index-bit pairs) */
+#define QSIM_PASS_PHASE 5       /* any number of 1- and 2-qubit diagonal gates on any qubits, one phase per
+                                   amplitude (a quadratic form of its index bits) */
 typedef struct {
     int32_t kind;             /* QSIM_PASS_* */
     int32_t k;                /* qubits the pass's matrix acts on */
@@ -200,7 +202,7 @@ typedef struct {
     int64_t gates;            /* input gates merged into this pass */
     double algorithmic_bytes; /* HBM bytes the pass must read + write */
     int32_t targets[QSIM_MAX_TARGETS];   /* index bits the matrix acts on, in the order of its index bits
-                                            (k of them; zero for a reorder pass) */
+                                            (k of them; k = 0 for a reorder or phase pass) */
     int32_t controls[QSIM_MAX_CONTROLS]; /* control bits (nc of them) */
 } qsim_pass_info;
 int qsim_plan_num_passes(qsim_plan_h plan, int64_t* out);

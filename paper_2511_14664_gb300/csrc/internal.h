@@ -43,6 +43,31 @@ cudaError_t launch_set_basis(int dtype, void* psi, int n, uint64_t x, cudaStream
 // Convert a device FP64 matrix (2^k x 2^k complex) into the state precision (device -> device).
 cudaError_t launch_convert_matrix(int dtype, const double* src, void* dst, int64_t count, cudaStream_t s);
 
+// ---- phase pass: any number of 1- and 2-qubit diagonal gates (k_phase.cu) -----------------------------------
+// The combined phase c + sum_a h_a x_a + sum_{a<b} lam_ab x_a x_b (radians) of a run of diagonal gates.
+struct PhaseForm {
+    struct Pair { int a, b; double lam; };
+    double c = 0.0;
+    std::vector<double> h;     // per qubit
+    std::vector<Pair> pairs;   // a < b, one entry per pair
+};
+// Launch parameters of a packed form: 64-bit fixed-point constants and byte offsets of the device tables.
+struct PhasePacked {
+    uint64_t c = 0;
+    int nhh = 0;
+    int lh_off[11] = {};
+    size_t off_hh_ab = 0, off_hh_l = 0, off_lh_a = 0, off_lh_l = 0, off_ll = 0, off_lm = 0, off_tmid = 0;
+};
+// A diagonal gate the phase pass takes: 1 or 2 qubits in all (targets plus controls).
+bool phase_gate_ok(const qsim_gate& g);
+// The form of gates[0..count) (each diagonal, phase_gate_ok); false if one is not acceptable.
+bool phase_form_build(const qsim_gate* const* gates, int count, int n, PhaseForm& f);
+// Device tables of a form (bytes to upload as they are) and its launch parameters.
+void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, PhasePacked& pk);
+// Multiply every amplitude by exp(i phi(x)); dtab is the uploaded table block; n >= 10.
+cudaError_t launch_phase(int dtype, void* psi, int n, const void* dtab, const PhasePacked& pk, cudaStream_t s,
+                         const DevInfo& d);
+
 // ---- tensor-core fused block (k_tc.cu) ----------------------------------------------------------------------
 // Bytes of the prepared B operand for a k-qubit block at `precision`.
 size_t tc_operand_bytes(int k, int precision);

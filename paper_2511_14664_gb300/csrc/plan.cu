@@ -20,7 +20,7 @@
 
 namespace qsim {
 
-enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4 };
+enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4, OP_PHASE = 5 };
 
 struct PlanOp {
     int kind = OP_DENSE_SMALL;
@@ -35,6 +35,8 @@ struct PlanOp {
     int64_t gates = 1;
     int nswap = 0;             // OP_SWAP: exchange qubit swap_a[i] with swap_b[i]
     int swap_a[8] = {0}, swap_b[8] = {0};
+    PhasePacked phase;         // OP_PHASE: launch parameters; tables at dev_off
+    std::vector<unsigned char> blob;  // OP_PHASE: the tables until they are uploaded
 };
 
 }  // namespace qsim
@@ -94,7 +96,7 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
 // (seeded at the earliest unplaced gate) is one of the candidates. On nearest-neighbour circuits the
 // windows tile the (qubit, time) plane in diamonds, about twice the gates per block of the plain greedy.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax) {
+                                          int kmax, const std::vector<char>* gwide) {
     const int G = (int)gmask.size();
     std::vector<std::vector<int>> blocks;
     std::vector<char> done(G, 0);
@@ -103,7 +105,19 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
         while (first < G && done[first]) ++first;
         if (first >= G) break;
         std::vector<int> best;
-        if (popcnt(gmask[first]) > kmax) {
+        // With gwide: every unplaced diagonal gate it marks that no earlier unplaced non-diagonal gate blocks,
+        // whatever its qubits (one phase pass takes them all), as one more candidate.
+        std::vector<int> wide;
+        if (gwide) {
+            const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
+            uint64_t bany = 0;
+            for (int i = first; i < G && bany != all; ++i) {
+                if (done[i]) continue;
+                if (gdiag[i] && (*gwide)[i] && (gmask[i] & bany) == 0) wide.push_back(i);
+                else if (!gdiag[i]) bany |= gmask[i];
+            }
+        }
+        if (popcnt(gmask[first]) > kmax && !(gwide && (*gwide)[first] && gdiag[first])) {
             best.push_back(first);  // wider than the fusion width: a block of its own
         } else {
             // windows
@@ -126,6 +140,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
                 seen |= qs;
                 if (gdiag[i]) bdiag |= qs; else bany |= qs;
             }
+            if (wide.size() > best.size()) best.swap(wide);
             if (best.empty()) best.push_back(first);
         }
         for (int i : best) done[i] = 1;
@@ -136,6 +151,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
 
 static double op_bytes(const PlanOp& op, int n, size_t amp) {
     if (op.kind == OP_SWAP) return 2.0 * amp * std::ldexp(1.0, n) * (1.0 - std::ldexp(1.0, -op.nswap));
+    if (op.kind == OP_PHASE) return 2.0 * amp * std::ldexp(1.0, n);
     const double groups = std::ldexp(1.0, n - op.k - op.nc);
     if (op.kind == OP_DIAG) return 2.0 * amp * groups * (double)op.touch.size();
     return 2.0 * amp * groups * (double)(1 << op.k);
@@ -165,6 +181,10 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                 break;
             case OP_SWAP:
                 e = launch_swap(h->dtype, h->psi, h->n, op.swap_a, op.swap_b, op.nswap, h->stream, h->dev, nullptr);
+                break;
+            case OP_PHASE:
+                e = launch_phase(h->dtype, h->psi, h->n, static_cast<char*>(p->dbuf) + op.dev_off, op.phase, h->stream,
+                                 h->dev);
                 break;
         }
         if (e != cudaSuccess) return cuda_fail(e, "plan pass launch");
@@ -225,10 +245,16 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
 
     // ---- group gates into blocks -------------------------------------------------------------------------
     std::vector<std::vector<int>> blocks;
+    // In fused plans, diagonal gates of one or two qubits may also gather in a phase pass of any width
+    // (n >= 10). Not with global qubits: the phase tables name physical positions, which the reorder passes
+    // would move.
+    std::vector<char> gwide(G, 0);
+    const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !(opts.local_qubits > 0 && opts.local_qubits < n);
+    for (int i = 0; i < G; ++i) gwide[i] = use_wide && gdiag[i] && phase_gate_ok(c->gates[i]);
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        blocks = group_gates(gmask, gdiag, n, kmax);
+        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr);
     }
 
     // ---- decide each block's pass and lay out the device buffer --------------------------------------------
@@ -247,6 +273,22 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     for (const auto& blk : blocks) {
         PlanOp op;
         op.gates = (int64_t)blk.size();
+        uint64_t Qb = 0;
+        bool wide_ok = use_wide;
+        for (int gi : blk) { Qb |= gmask[gi]; wide_ok = wide_ok && gwide[gi]; }
+        if (wide_ok && popcnt(Qb) > 6) {
+            // a phase pass (wider than the diagonal kernel's 6 qubits): the quadratic form of every gate
+            std::vector<const qsim_gate*> gp;
+            for (int gi : blk) gp.push_back(&c->gates[gi]);
+            PhaseForm form;
+            if (!phase_form_build(gp.data(), (int)gp.size(), n, form)) { delete p; set_error("phase pass"); return QSIM_EINVAL; }
+            op.kind = OP_PHASE;
+            phase_pack(form, dtype, op.blob, op.phase);
+            op.dev_off = dev_bytes;
+            dev_bytes = align(dev_bytes + op.blob.size());
+            p->ops.push_back(std::move(op));
+            continue;
+        }
         if (blk.size() == 1) {
             const qsim_gate& g = c->gates[blk[0]];
             op.k = g.k;
@@ -410,6 +452,15 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
     }
+    for (size_t oi = 0; rc == QSIM_OK && oi < p->ops.size(); ++oi) {
+        PlanOp& op = p->ops[oi];
+        if (op.kind != OP_PHASE) continue;
+        e = cudaMemcpyAsync(base + op.dev_off, op.blob.data(), op.blob.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pageable host source
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+        op.blob.clear();
+        op.blob.shrink_to_fit();
+    }
     for (size_t di = 0; rc == QSIM_OK && di < direct.size(); ++di) {
         PlanOp& op = p->ops[direct[di]];
         const size_t cnt = (size_t)2 << (2 * op.k);
@@ -539,7 +590,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     I.input_gates = G;
     for (const PlanOp& op : p->ops) {
         ++I.passes;
-        if (op.kind == OP_DIAG) ++I.diag_blocks;
+        if (op.kind == OP_DIAG || op.kind == OP_PHASE) ++I.diag_blocks;
         else if (op.kind == OP_TC) ++I.tc_blocks;
         else if (op.kind == OP_SWAP) ++I.reorders;
         else ++I.dense_blocks;

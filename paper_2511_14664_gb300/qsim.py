@@ -50,7 +50,7 @@ class PassInfo(ctypes.Structure):
                 ("targets", ctypes.c_int32 * 8), ("controls", ctypes.c_int32 * 8)]
 
 
-PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder"}
+PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder", 5: "phase"}
 
 
 class PlanInfo(ctypes.Structure):

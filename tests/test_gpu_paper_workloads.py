@@ -1,0 +1,90 @@
+"""The paper's own benchmark circuits (Sec. 2.2): quantum phase estimation and its random-circuit script,
+through every execution path, against the FP64 oracle and against what the mathematics fixes.
+
+QPE with a phase a / 2^t that t counting qubits represent exactly ends in the basis state |a>|1>, so every
+sample must be that index (exact integer comparison) and the amplitudes match the oracle. The random
+circuits are checked against the oracle at 20 qubits (complex64 bar: max |amplitude error| <= 1e-5,
+normalised infidelity <= 1e-9) and, at the 33-qubit size the paper benchmarks, by the QPE shots.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PATHS = {
+    "plain": dict(mode=0, max_fused=1),
+    "simt4": dict(mode=1, max_fused=4),
+    "tf32x3_k5": dict(mode=1, max_fused=5, precision=1, tc_min_k=5),
+    "tf32x3_k6": dict(mode=1, max_fused=6, precision=1, tc_min_k=5),
+    "bf16x6_k6": dict(mode=1, max_fused=6, precision=3, tc_min_k=5),
+}
+
+
+@pytest.fixture(scope="module")
+def qsim(gpu_lib):
+    from paper_2511_14664_gb300 import qsim as q
+    return q
+
+
+def check(psi_gpu, ref, n):
+    g = psi_gpu.astype(np.complex128)
+    err = float(np.max(np.abs(g - ref)))
+    inf = oracle.infidelity(np.ascontiguousarray(g), ref, n)
+    assert err <= 1e-5, f"max amplitude error {err:.3e}"
+    assert inf <= 1e-9, f"infidelity {inf:.3e}"
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_qpe_21q_exact_outcome(qsim, path):
+    t = 20
+    a = W.basis_index(t, 11)
+    c, expect_a = W.qpe(t, a)
+    n = t + 1
+    st = qsim.State(n, qsim.C64)
+    st.set_basis(0)
+    st.run(c, **PATHS[path])
+    ref = oracle.run(c)
+    check(st.get_state(), ref, n)
+    expect = expect_a | (1 << t)
+    assert abs(ref[expect]) > 1 - 1e-12  # the oracle itself lands on the encoded phase
+    s = st.sample(5, 512)
+    assert np.all(s == expect)
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_rcs_20q_against_oracle(qsim, path):
+    n = 20
+    c = W.rcs(n, seed=3)
+    assert len(c) == 30 * n
+    st = qsim.State(n, qsim.C64)
+    st.set_basis(0)
+    st.run(c, **PATHS[path])
+    psi = st.get_state()
+    check(psi, oracle.run(c), n)
+    # sampling: the oracle's inverse CDF on the GPU's own final state, with the same uniforms
+    u = oracle.uniforms(9, 300)
+    assert np.array_equal(st.sample_uniforms(u), oracle.sample(np.ascontiguousarray(psi.astype(np.complex128)), n, u))
+
+
+def test_qpe_33q_full_size_shots(qsim):
+    """At the paper's 33-qubit size (64 GiB complex64), in the launch configuration the benchmark times
+    (6-qubit 3xTF32 tensor-core blocks): all 1000 shots return the encoded phase."""
+    import torch
+    free = torch.cuda.mem_get_info()[0]
+    if free < (2**33) * 8 + (4 << 30):
+        pytest.skip("needs 68 GiB of free device memory")
+    t = 32
+    a = W.basis_index(t, 7)
+    c, expect_a = W.qpe(t, a)
+    st = qsim.State(t + 1, qsim.C64)
+    st.set_basis(0)
+    st.run(c, **PATHS["tf32x3_k6"])
+    s = st.sample(3, 1000)
+    assert np.all(s == (expect_a | (1 << t)))
+    assert abs(st.norm() - 1.0) <= 1e-4
+    st.close()
+    del st
+    torch.cuda.empty_cache()
