@@ -1,5 +1,6 @@
-"""The paper's own benchmark circuits (Sec. 2.2): quantum phase estimation and its random-circuit script,
-through every execution path, against the FP64 oracle and against what the mathematics fixes.
+"""The paper's own benchmark circuits (Sec. 2.2): quantum phase estimation, its random-circuit script and a
+TFIM Trotter evolution on a 2-D periodic lattice, through every execution path, against the FP64 oracle
+and against what the mathematics fixes.
 
 QPE with a phase a / 2^t that t counting qubits represent exactly ends in the basis state |a>|1>, so every
 sample must be that index (exact integer comparison) and the amplitudes match the oracle. The random
@@ -67,6 +68,23 @@ def test_rcs_20q_against_oracle(qsim, path):
     # sampling: the oracle's inverse CDF on the GPU's own final state, with the same uniforms
     u = oracle.uniforms(9, 300)
     assert np.array_equal(st.sample_uniforms(u), oracle.sample(np.ascontiguousarray(psi.astype(np.complex128)), n, u))
+
+
+@pytest.mark.parametrize("path", list(PATHS))
+def test_tfim_lattice_15q_against_oracle(qsim, path):
+    """Trotter evolution on a 5 x 3 periodic triangular lattice (45 bonds): the RZZ layers go to phase
+    passes in the fused plans."""
+    c = W.tfim_lattice(5, 3, 4, 0.8, 1.9)
+    n = c.n
+    st = qsim.State(n, qsim.C64)
+    st.set_basis(0)
+    st.run(c, **PATHS[path])
+    psi = st.get_state()
+    ref = oracle.run(c)
+    check(psi, ref, n)
+    zi, zz = st.expect_z()
+    rzi, rzz = oracle.expect_z_chain(ref, n)
+    assert np.max(np.abs(zi - rzi)) <= 1e-5 and np.max(np.abs(zz - rzz)) <= 1e-5
 
 
 def test_qpe_33q_full_size_shots(qsim):

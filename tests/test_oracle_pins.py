@@ -143,6 +143,30 @@ def test_tfim_trotter_matches_expm():
     assert np.max(np.abs(psi - ref)) <= 1e-12
 
 
+@pytest.mark.parametrize("lx,ly", [(3, 3), (4, 2)])
+def test_tfim_lattice_trotter_matches_expm(lx, ly):
+    """The periodic triangular-lattice TFIM: bonds (each site's three forward neighbours, wrapping; every
+    site of a lattice with lx, ly >= 3 has six neighbours) and the Trotter circuit against expm of Eq. 1's
+    two terms built from those bonds."""
+    from scipy.linalg import expm
+    n, steps, th, ph = lx * ly, 3, 0.9, 0.35
+    bonds = W.triangular_bonds(lx, ly)
+    if lx >= 3 and ly >= 3:
+        assert len(bonds) == 3 * n
+        deg = np.bincount(np.array(bonds).ravel(), minlength=n)
+        assert np.all(deg == 6)
+    assert len(set(bonds)) == len(bonds) and all(a < b for a, b in bonds)
+    psi = oracle.run(W.tfim_lattice(lx, ly, steps, th, ph))
+    Hzz = sum(pauli_dense("".join("Z" if q in (a, b) else "I" for q in range(n))) for a, b in bonds)
+    Hx = sum(pauli_dense("".join("X" if q == i else "I" for q in range(n))) for i in range(n))
+    Ustep = expm(-0.5j * ph * Hx) @ expm(-0.5j * th * Hzz)
+    ref = np.zeros(1 << n, dtype=np.complex128)
+    ref[0] = 1
+    for _ in range(steps):
+        ref = Ustep @ ref
+    assert np.max(np.abs(psi - ref)) <= 1e-12
+
+
 # ---- observables ------------------------------------------------------------------------------------
 @pytest.mark.parametrize("phi", [0.0, 0.4, 1.1, 2.9])
 def test_rx_product_expectations(phi):

@@ -201,6 +201,40 @@ def tfim_batch(count: int, seed: int, nmin: int = 10, nmax: int = 24, smin: int 
     return out
 
 
+def triangular_bonds(lx: int, ly: int) -> List[Tuple[int, int]]:
+    """Bonds of an lx x ly triangular lattice with periodic boundaries (site (x, y) is qubit y * lx + x):
+    each site couples to (x+1, y), (x, y+1) and (x+1, y+1), wrapping around; duplicate bonds of narrow
+    lattices are kept once. 3 lx ly bonds when lx, ly >= 3."""
+    bonds = []
+    seen = set()
+    for y in range(ly):
+        for x in range(lx):
+            a = y * lx + x
+            for dx, dy in ((1, 0), (0, 1), (1, 1)):
+                b = ((y + dy) % ly) * lx + (x + dx) % lx
+                key = (min(a, b), max(a, b))
+                if a != b and key not in seen:
+                    seen.add(key)
+                    bonds.append(key)
+    return bonds
+
+
+def tfim_lattice(lx: int, ly: int, steps: int, theta: float, phi: float) -> Circuit:
+    """First-order Trotter evolution under Eq. 1 on a periodic triangular lattice (Sec. 2.2's HamLib TFIM is
+    a 2-D lattice of this kind; its data file is not available): each step applies RZZ(theta) on every bond,
+    then RX(phi) on every site (theta = 2 J dt, phi = 2 h dt), from |0...0>."""
+    n = lx * ly
+    c = Circuit(n, name=f"tfim_tri_{lx}x{ly}_s{steps}")
+    zz, rx = RZZ(theta), RX(phi)
+    bonds = triangular_bonds(lx, ly)
+    for _ in range(steps):
+        for a, b in bonds:
+            c.append(Gate((a, b), (), zz, "rzz"))
+        for q in range(n):
+            c.append(Gate((q,), (), rx, "rx"))
+    return c
+
+
 def random_pairs(n: int, depth: int, seed: int) -> Circuit:
     """Each layer is a seeded random perfect matching of the n qubits (n even; one qubit idles when odd)
     with a Haar U(4) on every pair, so most gates span high-order qubits."""
