@@ -54,9 +54,9 @@ struct PhaseForm {
 // Launch parameters of a packed form: 64-bit fixed-point constants and byte offsets of the device tables.
 struct PhasePacked {
     uint64_t c = 0;
-    int nhh = 0;
-    int lh_off[11] = {};
-    size_t off_hh_ab = 0, off_hh_l = 0, off_lh_a = 0, off_lh_l = 0, off_ll = 0, off_lm = 0, off_tmid = 0;
+    int nb = 0, ntt = 0;
+    int lt_off[15] = {};
+    size_t off_tt_ab = 0, off_tt_l = 0, off_lt_a = 0, off_lt_l = 0, off_small = 0, off_tmid = 0;
 };
 // A diagonal gate the phase pass takes: 1 or 2 qubits in all (targets plus controls).
 bool phase_gate_ok(const qsim_gate& g);

@@ -8,16 +8,18 @@
 // because every 1- or 2-qubit diagonal unitary is exp(i (p0 + p1 x_a + p2 x_b + p3 x_a x_b)).
 //
 // Phases are 64-bit fixed-point turns (2^64 = one turn): sums wrap around exactly (mod 2 pi) and need no FP64
-// arithmetic, which is scarce on GB300. Each warp owns a range of 1024 consecutive amplitudes (index bits
-// 10 and up fixed): lanes are index bits 0..4 (coalesced 256-byte accesses), and each lane's 32 amplitudes
-// differ in bits 5..9. Per range the warp reduces the terms that involve the fixed high bits into
-// s (a phase) and mu_j (a coefficient for each low bit j < 10); per lane this leaves
+// arithmetic, which is scarce on GB300. A range is 1024 consecutive amplitudes: lanes are index bits 0..4
+// (coalesced 256-byte accesses) and each lane's 32 amplitudes differ in bits 5..9. A warp owns a group of
+// 16 consecutive ranges (bits 10..13): it reduces the terms on the group's fixed top bits once, into a
+// constant and a coefficient for each bit below (warp shuffles), and folds in the 4 range bits from small
+// shared-memory tables per range. Per lane this leaves
 //     phi(lane, m) = s_lane + sum_e nu_e m_e + M(m)   (m = bits 5..9),
 // evaluated as products of unit complex numbers in a depth-5 tree (no per-amplitude sin / cos).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -28,18 +30,23 @@ namespace phase {
 constexpr int kLowBits = 10;  // a warp's range: 2^10 amplitudes
 constexpr int kLaneBits = 5;
 
+// Index bits: 0..4 lane, 5..9 the lane's 32 amplitudes (mid), 10..10+nb-1 the range within a warp's group
+// of 2^nb ranges (block), the rest fixed per group (top). Terms are split by the bit groups they touch.
+constexpr int kBlockBits = 4;
+
 struct Args {
     uint64_t c;
-    int nhh;                       // terms on two high bits (a single high bit appears as a == b)
-    int lh_off[kLowBits + 1];      // terms (low bit j, high bit a) for j: [lh_off[j], lh_off[j+1])
-    const uint32_t* hh_ab;         // a | b << 8
-    const uint64_t* hh_l;
-    const uint32_t* lh_a;          // the high bit
-    const uint64_t* lh_l;
-    const uint64_t* ll_lane;       // [32]: phase of the lane bits (bits 0..4) alone
-    const uint64_t* lm;            // [32][5]: coefficient of bit 5+e given the lane bits (h and lane-mid terms)
+    int nb;                        // block bits (min(4, n - 10))
+    int ntt;                       // terms on two top bits (a single top bit appears as a == b)
+    int lt_off[kLowBits + kBlockBits + 1];  // terms (low or block bit j, top bit a): [lt_off[j], lt_off[j+1])
+    const uint32_t* tt_ab;         // a | b << 8
+    const uint64_t* tt_l;
+    const uint32_t* lt_a;          // the top bit
+    const uint64_t* lt_l;
+    const uint64_t* small;         // ll_lane[32] | lm[32][5] | sb[16] | mb[16][10]  (see phase_pack)
     const void* tmid;              // [32] complex (state precision): exp(i * mid-mid terms of bits 5..9)
 };
+constexpr int kSmallWords = 32 + 32 * 5 + 16 + 16 * kLowBits;
 
 // exp(2 pi i t) for t = x / 2^64 turns.
 __device__ __forceinline__ float2 unit_phase(float, uint64_t x) {
@@ -82,46 +89,78 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_phase(typename Amp<R>::T* __restrict__ psi, int n, const Args a) {
     using T = typename Amp<R>::T;
-    constexpr int M = 1 << (kLowBits - kLaneBits);  // 32 amplitudes per lane
-    const int lane = threadIdx.x & 31;
+    constexpr int M = 1 << (kLowBits - kLaneBits);  // 32 amplitudes per lane, in two halves of 16
+    constexpr int H = M / 2;
+    constexpr int NMU = kLowBits + kBlockBits;
+    __shared__ uint64_t sm[kSmallWords];
+    __shared__ uint64_t smu[8][NMU];                // per warp: coefficients of the low and block bits
+    __shared__ T stmid[M];
+    for (int i = threadIdx.x; i < kSmallWords; i += blockDim.x) sm[i] = a.small[i];
+    if (threadIdx.x < M) stmid[threadIdx.x] = static_cast<const T*>(a.tmid)[threadIdx.x];
+    __syncthreads();
+    const uint64_t* ll_lane = sm;
+    const uint64_t* lm = sm + 32;
+    const uint64_t* sb = lm + 32 * 5;
+    const uint64_t* mb = sb + 16;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint64_t* mu = smu[wib];
+    const int gbits = kLowBits + a.nb;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    const uint64_t nr = 1ull << (n - kLowBits);
-    const T* tmid = static_cast<const T*>(a.tmid);
-    for (uint64_t rg = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rg < nr; rg += warps) {
-        const uint64_t base = rg << kLowBits;
-        T v[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = psi[base + ((uint64_t)m << kLaneBits) + lane];
-        // terms on the fixed high bits
+    const uint64_t ngroups = 1ull << (n - gbits);
+    for (uint64_t gp = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib; gp < ngroups; gp += warps) {
+        const uint64_t gbase = gp << gbits;
+        // terms on the group's fixed top bits: a constant and a coefficient for each low and block bit
         uint64_t s = 0;
-        for (int i = lane; i < a.nhh; i += 32) {
-            const uint32_t ab = a.hh_ab[i];
-            if ((base >> (ab & 0xFF)) & (base >> (ab >> 8)) & 1) s += a.hh_l[i];
+        for (int i = lane; i < a.ntt; i += 32) {
+            const uint32_t ab = a.tt_ab[i];
+            if ((gbase >> (ab & 0xFF)) & (gbase >> (ab >> 8)) & 1) s += a.tt_l[i];
         }
         s = warp_sum64(s) + a.c;
-        uint64_t mu[kLowBits];
-#pragma unroll
-        for (int j = 0; j < kLowBits; ++j) {
+        __syncwarp();  // the previous group's readers of mu are done
+        for (int j = 0; j < NMU; ++j) {
             uint64_t t = 0;
-            for (int i = a.lh_off[j] + lane; i < a.lh_off[j + 1]; i += 32)
-                if ((base >> a.lh_a[i]) & 1) t += a.lh_l[i];
-            mu[j] = warp_sum64(t);
+            for (int i = a.lt_off[j] + lane; i < a.lt_off[j + 1]; i += 32)
+                if ((gbase >> a.lt_a[i]) & 1) t += a.lt_l[i];
+            t = warp_sum64(t);
+            if (lane == 0) mu[j] = t;
         }
-        // this lane's constant phase and the coefficients of bits 5..9
-        uint64_t sl = s + a.ll_lane[lane];
+        __syncwarp();
+        const uint64_t lane_c = ll_lane[lane] + s;
+        for (int bv = 0; bv < (1 << a.nb); ++bv) {
+            const uint64_t base = gbase | ((uint64_t)bv << kLowBits);
+            const uint64_t* mbv = mb + bv * kLowBits;
+            // this range's constant for the lane, with the block bits bv folded in
+            uint64_t sl = lane_c + sb[bv];
+            for (int k = 0; k < a.nb; ++k)
+                if ((bv >> k) & 1) sl += mu[kLowBits + k];
 #pragma unroll
-        for (int j = 0; j < kLaneBits; ++j)
-            if ((lane >> j) & 1) sl += mu[j];
-        T F[M];
-        F[0] = unit_phase(R(0), sl);
+            for (int j = 0; j < kLaneBits; ++j)
+                if ((lane >> j) & 1) sl += mu[j] + mbv[j];
+            auto coef = [&](int e) { return mu[kLaneBits + e] + mbv[kLaneBits + e] + lm[lane * (kLowBits - kLaneBits) + e]; };
+            // factors of the first half (m < 16) by a depth-4 tree; the second half adds bit 9's factor
+            T F[H];
+            F[0] = unit_phase(R(0), sl);
 #pragma unroll
-        for (int e = 0; e < kLowBits - kLaneBits; ++e) {
-            const T B = unit_phase(R(0), mu[kLaneBits + e] + a.lm[lane * (kLowBits - kLaneBits) + e]);
+            for (int e = 0; e < 4; ++e) {
+                const T B = unit_phase(R(0), coef(e));
 #pragma unroll
-            for (int m = 0; m < (1 << e); ++m) F[(1 << e) + m] = cmul(F[m], B);
+                for (int m = 0; m < (1 << e); ++m) F[(1 << e) + m] = cmul(F[m], B);
+            }
+            const T B4 = unit_phase(R(0), coef(4));
+            auto apply_half = [&](auto hc) {
+                constexpr int half = decltype(hc)::value;
+                T v[H];
+#pragma unroll
+                for (int m = 0; m < H; ++m) v[m] = psi[base + ((uint64_t)(half * H + m) << kLaneBits) + lane];
+#pragma unroll
+                for (int m = 0; m < H; ++m) {
+                    const T f = half ? cmul(cmul(F[m], B4), stmid[H + m]) : cmul(F[m], stmid[m]);
+                    psi[base + ((uint64_t)(half * H + m) << kLaneBits) + lane] = cmul(v[m], f);
+                }
+            };
+            apply_half(std::integral_constant<int, 0>{});
+            apply_half(std::integral_constant<int, 1>{});
         }
-#pragma unroll
-        for (int m = 0; m < M; ++m) psi[base + ((uint64_t)m << kLaneBits) + lane] = cmul(v[m], cmul(F[m], tmid[m]));
     }
 }
 
@@ -178,66 +217,80 @@ bool phase_form_build(const qsim_gate* const* gates, int count, int n, PhaseForm
 void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, PhasePacked& pk) {
     using namespace phase;
     const int n = (int)f.h.size();
-    std::vector<uint32_t> hh_ab, lh_a;
-    std::vector<uint64_t> hh_l, lh_l;
-    std::vector<std::vector<std::pair<uint32_t, uint64_t>>> lh(kLowBits);
-    uint64_t c = to_turns(f.c);
-    std::vector<uint64_t> hlow(kLowBits, 0);
+    const int nb = std::max(0, std::min(kBlockBits, n - kLowBits));
+    const int G = kLowBits + nb;  // bits below the top bits
+    std::vector<uint32_t> tt_ab, lt_a;
+    std::vector<uint64_t> tt_l, lt_l;
+    std::vector<std::vector<std::pair<uint32_t, uint64_t>>> lt(kLowBits + kBlockBits);
+    std::vector<uint64_t> hg(G, 0);  // single-bit terms of the low and block bits
     for (int a = 0; a < n; ++a) {
         if (f.h[a] == 0.0) continue;
-        if (a >= kLowBits) { hh_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); hh_l.push_back(to_turns(f.h[a])); }
-        else hlow[a] = to_turns(f.h[a]);
+        if (a >= G) { tt_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); tt_l.push_back(to_turns(f.h[a])); }
+        else hg[a] = to_turns(f.h[a]);
     }
-    // low-low terms: lane-lane, lane-mid, mid-mid
-    std::vector<uint64_t> ll_lane(32, 0), lm(32 * 5, 0);
+    // pair terms by the groups of their bits (a < b)
+    std::vector<uint64_t> small(kSmallWords, 0);
+    uint64_t* ll_lane = small.data();
+    uint64_t* lm = ll_lane + 32;
+    uint64_t* sb = lm + 32 * 5;
+    uint64_t* mb = sb + 16;
     double midmid[5][5] = {};
     uint64_t lanelane[5][5] = {};
     for (const auto& p : f.pairs) {
-        if (p.a >= kLowBits) { hh_ab.push_back((uint32_t)p.a | ((uint32_t)p.b << 8)); hh_l.push_back(to_turns(p.lam)); }
-        else if (p.b >= kLowBits) lh[p.a].push_back({(uint32_t)p.b, to_turns(p.lam)});
-        else if (p.b < kLaneBits) lanelane[p.a][p.b] += to_turns(p.lam);
-        else if (p.a < kLaneBits) {
+        const uint64_t L = to_turns(p.lam);
+        if (p.a >= G) { tt_ab.push_back((uint32_t)p.a | ((uint32_t)p.b << 8)); tt_l.push_back(L); }
+        else if (p.b >= G) lt[p.a].push_back({(uint32_t)p.b, L});           // low/block x top
+        else if (p.a >= kLowBits) {                                        // block x block
+            for (int bv = 0; bv < (1 << nb); ++bv)
+                if (((bv >> (p.a - kLowBits)) & 1) && ((bv >> (p.b - kLowBits)) & 1)) sb[bv] += L;
+        } else if (p.b >= kLowBits) {                                      // low x block
+            for (int bv = 0; bv < (1 << nb); ++bv)
+                if ((bv >> (p.b - kLowBits)) & 1) mb[bv * kLowBits + p.a] += L;
+        } else if (p.b < kLaneBits) lanelane[p.a][p.b] += L;              // lane x lane
+        else if (p.a < kLaneBits) {                                        // lane x mid
             for (int l = 0; l < 32; ++l)
-                if ((l >> p.a) & 1) lm[l * 5 + (p.b - kLaneBits)] += to_turns(p.lam);
+                if ((l >> p.a) & 1) lm[l * 5 + (p.b - kLaneBits)] += L;
         } else {
-            midmid[p.a - kLaneBits][p.b - kLaneBits] += p.lam;
+            midmid[p.a - kLaneBits][p.b - kLaneBits] += p.lam;             // mid x mid
         }
     }
+    for (int bv = 0; bv < (1 << nb); ++bv)
+        for (int k = 0; k < nb; ++k)
+            if ((bv >> k) & 1) sb[bv] += hg[kLowBits + k];
     for (int l = 0; l < 32; ++l) {
         uint64_t v = 0;
         for (int j = 0; j < kLaneBits; ++j) {
             if (!((l >> j) & 1)) continue;
-            v += hlow[j];
+            v += hg[j];
             for (int k = j + 1; k < kLaneBits; ++k)
                 if ((l >> k) & 1) v += lanelane[j][k];
         }
         ll_lane[l] = v;
-        for (int e = 0; e < 5; ++e) lm[l * 5 + e] += hlow[kLaneBits + e];
+        for (int e = 0; e < 5; ++e) lm[l * 5 + e] += hg[kLaneBits + e];
     }
-    for (int j = 0; j < kLowBits; ++j)
-        for (const auto& t : lh[j]) { lh_a.push_back(t.first); lh_l.push_back(t.second); }
-    pk.c = c;
-    pk.nhh = (int)hh_ab.size();
-    pk.lh_off[0] = 0;
-    for (int j = 0; j < kLowBits; ++j) pk.lh_off[j + 1] = pk.lh_off[j] + (int)lh[j].size();
+    for (int j = 0; j < kLowBits + kBlockBits; ++j)
+        for (const auto& t : lt[j]) { lt_a.push_back(t.first); lt_l.push_back(t.second); }
+    pk.c = to_turns(f.c);
+    pk.nb = nb;
+    pk.ntt = (int)tt_ab.size();
+    pk.lt_off[0] = 0;
+    for (int j = 0; j < kLowBits + kBlockBits; ++j) pk.lt_off[j + 1] = pk.lt_off[j] + (int)lt[j].size();
     // byte layout (16-byte aligned sections)
     auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
     size_t off = 0;
-    pk.off_hh_ab = off; off = al(off + 4 * hh_ab.size());
-    pk.off_hh_l = off;  off = al(off + 8 * hh_l.size());
-    pk.off_lh_a = off;  off = al(off + 4 * lh_a.size());
-    pk.off_lh_l = off;  off = al(off + 8 * lh_l.size());
-    pk.off_ll = off;    off = al(off + 8 * 32);
-    pk.off_lm = off;    off = al(off + 8 * 32 * 5);
+    pk.off_tt_ab = off; off = al(off + 4 * tt_ab.size());
+    pk.off_tt_l = off;  off = al(off + 8 * tt_l.size());
+    pk.off_lt_a = off;  off = al(off + 4 * lt_a.size());
+    pk.off_lt_l = off;  off = al(off + 8 * lt_l.size());
+    pk.off_small = off; off = al(off + 8 * small.size());
     pk.off_tmid = off;  off = al(off + (dtype == QSIM_C64 ? 8 : 16) * 32);
     out.assign(off, 0);
     auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(out.data() + o, src, bytes); };
-    put(pk.off_hh_ab, hh_ab.data(), 4 * hh_ab.size());
-    put(pk.off_hh_l, hh_l.data(), 8 * hh_l.size());
-    put(pk.off_lh_a, lh_a.data(), 4 * lh_a.size());
-    put(pk.off_lh_l, lh_l.data(), 8 * lh_l.size());
-    put(pk.off_ll, ll_lane.data(), 8 * 32);
-    put(pk.off_lm, lm.data(), 8 * 32 * 5);
+    put(pk.off_tt_ab, tt_ab.data(), 4 * tt_ab.size());
+    put(pk.off_tt_l, tt_l.data(), 8 * tt_l.size());
+    put(pk.off_lt_a, lt_a.data(), 4 * lt_a.size());
+    put(pk.off_lt_l, lt_l.data(), 8 * lt_l.size());
+    put(pk.off_small, small.data(), 8 * small.size());
     for (int m = 0; m < 32; ++m) {
         double ph = 0.0;
         for (int j = 0; j < 5; ++j)
@@ -256,21 +309,22 @@ void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, 
 
 cudaError_t launch_phase(int dtype, void* psi, int n, const void* dtab, const PhasePacked& pk, cudaStream_t s,
                          const DevInfo& d) {
-    if (n < phase::kLowBits) return cudaErrorInvalidValue;
+    if (n < phase::kLowBits || pk.nb != std::max(0, std::min(phase::kBlockBits, n - phase::kLowBits)))
+        return cudaErrorInvalidValue;
     const unsigned char* b = static_cast<const unsigned char*>(dtab);
     phase::Args a;
     a.c = pk.c;
-    a.nhh = pk.nhh;
-    for (int j = 0; j <= phase::kLowBits; ++j) a.lh_off[j] = pk.lh_off[j];
-    a.hh_ab = reinterpret_cast<const uint32_t*>(b + pk.off_hh_ab);
-    a.hh_l = reinterpret_cast<const uint64_t*>(b + pk.off_hh_l);
-    a.lh_a = reinterpret_cast<const uint32_t*>(b + pk.off_lh_a);
-    a.lh_l = reinterpret_cast<const uint64_t*>(b + pk.off_lh_l);
-    a.ll_lane = reinterpret_cast<const uint64_t*>(b + pk.off_ll);
-    a.lm = reinterpret_cast<const uint64_t*>(b + pk.off_lm);
+    a.nb = pk.nb;
+    a.ntt = pk.ntt;
+    for (int j = 0; j <= phase::kLowBits + phase::kBlockBits; ++j) a.lt_off[j] = pk.lt_off[j];
+    a.tt_ab = reinterpret_cast<const uint32_t*>(b + pk.off_tt_ab);
+    a.tt_l = reinterpret_cast<const uint64_t*>(b + pk.off_tt_l);
+    a.lt_a = reinterpret_cast<const uint32_t*>(b + pk.off_lt_a);
+    a.lt_l = reinterpret_cast<const uint64_t*>(b + pk.off_lt_l);
+    a.small = reinterpret_cast<const uint64_t*>(b + pk.off_small);
     a.tmid = b + pk.off_tmid;
-    const int64_t ranges = (int64_t)1 << (n - phase::kLowBits);
-    const unsigned grid = grid_for(ranges * 32, 256, d.num_sms, 8);
+    const int64_t groups = (int64_t)1 << (n - phase::kLowBits - pk.nb);
+    const unsigned grid = grid_for(groups * 32, 256, d.num_sms, 8);
     if (dtype == QSIM_C64) phase::k_phase<float><<<grid, 256, 0, s>>>(static_cast<float2*>(psi), n, a);
     else phase::k_phase<double><<<grid, 256, 0, s>>>(static_cast<double2*>(psi), n, a);
     return cudaGetLastError();
