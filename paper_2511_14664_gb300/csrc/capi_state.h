@@ -42,9 +42,10 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
 // Greedy fusion (plan.cu): starting from the earliest unplaced gate, collect every later gate that is not
 // blocked by an earlier unplaced gate on a shared qubit (diagonal gates are blocked only by non-diagonal
 // ones) and keeps the block within kmax qubits. gmask[i] = qubits of gate i (targets and controls). With
-// gwide, the diagonal gates it marks may also form one block of any width (a phase pass).
+// gwide, the diagonal gates it marks may also form one block of any width (a phase pass), chosen when it
+// holds more than wide_factor times the gates of the best other candidate.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax, const std::vector<char>* gwide = nullptr);
+                                          int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1);
 
 }  // namespace qsim
 

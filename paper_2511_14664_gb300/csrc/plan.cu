@@ -96,7 +96,7 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
 // (seeded at the earliest unplaced gate) is one of the candidates. On nearest-neighbour circuits the
 // windows tile the (qubit, time) plane in diamonds, about twice the gates per block of the plain greedy.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax, const std::vector<char>* gwide) {
+                                          int kmax, const std::vector<char>* gwide, int wide_factor) {
     const int G = (int)gmask.size();
     std::vector<std::vector<int>> blocks;
     std::vector<char> done(G, 0);
@@ -140,7 +140,10 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
                 seen |= qs;
                 if (gdiag[i]) bdiag |= qs; else bany |= qs;
             }
-            if (wide.size() > best.size()) best.swap(wide);
+            // A phase pass costs a full pass whatever it holds, and it only grows while dense blocks make
+            // progress (each one frees the diagonal gates behind it): it wins against dense blocks of less
+            // than 1 / wide_factor of its size.
+            if (wide.size() > (size_t)wide_factor * best.size()) best.swap(wide);
             if (best.empty()) best.push_back(first);
         }
         for (int i : best) done[i] = 1;
@@ -254,7 +257,13 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr);
+        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, 1);
+        // whether a phase pass should wait for more diagonal gates depends on the circuit: keep the grouping
+        // with the fewest blocks
+        for (int f = 2; use_wide && f <= 4; f *= 2) {
+            auto alt = group_gates(gmask, gdiag, n, kmax, &gwide, f);
+            if (alt.size() < blocks.size()) blocks.swap(alt);
+        }
     }
 
     // ---- decide each block's pass and lay out the device buffer --------------------------------------------
