@@ -126,6 +126,45 @@ __device__ __forceinline__ dd warp_sum_dd(dd v) {
     return v;
 }
 
+// ---- phases as 64-bit fixed-point turns ----------------------------------------------------------------------
+// A phase stored as x / 2^64 turns adds with wraparound (mod 2 pi, exact). unit_phase returns exp(2 pi i x/2^64).
+__device__ __forceinline__ float2 unit_phase(float, uint64_t x) {
+    // top 16 bits of the turn exactly in a float, the rest (under 2^-16 turns) by a short series
+    const int32_t top = (int32_t)(x >> 32);
+    const int32_t hi = top & (int32_t)0xFFFF0000;
+    const float th = (float)hi * 0x1p-32f;
+    const float tl = ((float)(top - hi) + (float)(uint32_t)x * 0x1p-32f) * 0x1p-32f;
+    float sa, ca;
+    sincospif(2.0f * th, &sa, &ca);
+    const float b = tl * 6.28318530717958648f;
+    const float sb = b - b * b * b * (1.0f / 6.0f), cb = 1.0f - 0.5f * b * b;
+    return make_float2(ca * cb - sa * sb, sa * cb + ca * sb);
+}
+__device__ __forceinline__ double2 unit_phase(double, uint64_t x) {
+    const double t = (double)(int64_t)x * 0x1p-64;
+    double s, c;
+    sincospi(2.0 * t, &s, &c);
+    return make_double2(c, s);
+}
+
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += shfl_xor64(v, m);
+    return v;
+}
+
 // ---- device error word -------------------------------------------------------------------------------------
 // Kernels with bounded waits report expiry by OR-ing a code into a device word the host reads back.
 enum : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_BAD_ITEM = 2u, DEVERR_TMEM = 4u };

@@ -58,6 +58,8 @@ struct PhasePacked {
     int lt_off[15] = {};
     size_t off_tt_ab = 0, off_tt_l = 0, off_lt_a = 0, off_lt_l = 0, off_small = 0, off_tmid = 0;
 };
+// A phase in radians as 64-bit fixed-point turns (2^64 = one turn), reduced to [0, 1) turn.
+uint64_t phase_turns(double phi);
 // A diagonal gate the phase pass takes: 1 or 2 qubits in all (targets plus controls).
 bool phase_gate_ok(const qsim_gate& g);
 // The form of gates[0..count) (each diagonal, phase_gate_ok); false if one is not acceptable.
@@ -69,13 +71,29 @@ cudaError_t launch_phase(int dtype, void* psi, int n, const void* dtab, const Ph
                          const DevInfo& d);
 
 // ---- tensor-core fused block (k_tc.cu) ----------------------------------------------------------------------
+// Launch parameters of a phase epilogue (a phase form applied to the block's output): byte offsets of the
+// device tables and the counts.
+struct TcEpiPacked {
+    uint64_t c = 0;
+    int ntt = 0;
+    int off[14] = {};
+    size_t off_rowphase = 0, off_tt_ab = 0, off_tt_l = 0, off_tb_t = 0, off_tb_l = 0, off_thr = 0;
+};
+// Tables of a phase epilogue for a k-qubit block on `targets` (the order launch_tc_apply gets) in an n-qubit
+// state. The terms on target bits alone become row phases of U (off_rowphase, for launch_tc_prepare); each
+// launch writes the per-tile factors to a scratch of tc_epi_scratch_bytes.
+void tc_epi_pack(int n, int k, const int* targets, const PhaseForm& f, std::vector<unsigned char>& out,
+                 TcEpiPacked& pk);
+size_t tc_epi_scratch_bytes(int n, int k);
 // Bytes of the prepared B operand for a k-qubit block at `precision`.
 size_t tc_operand_bytes(int k, int precision);
 // Build the B operand (tensor-core layout) from a device FP64 matrix U (2^k x 2^k complex).
-cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s);
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s,
+                              const double* rowphase = nullptr);
 // Apply the prepared block to a complex64 state. dev_err receives DEVERR_* bits on a bounded-wait expiry.
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
-                            unsigned* dev_err, cudaStream_t s, const DevInfo& d);
+                            unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab = nullptr,
+                            const TcEpiPacked* epi = nullptr, void* epi_scratch = nullptr);
 bool tc_supported(int k, int precision);
 
 // ---- fused-block composition (k_compose.cu) -------------------------------------------------------------------

@@ -48,44 +48,6 @@ struct Args {
 };
 constexpr int kSmallWords = 32 + 32 * 5 + 16 + 16 * kLowBits;
 
-// exp(2 pi i t) for t = x / 2^64 turns.
-__device__ __forceinline__ float2 unit_phase(float, uint64_t x) {
-    // top 16 bits of the turn exactly in a float, the rest (under 2^-16 turns) by a short series
-    const int32_t top = (int32_t)(x >> 32);
-    const int32_t hi = top & (int32_t)0xFFFF0000;
-    const float th = (float)hi * 0x1p-32f;
-    const float tl = ((float)(top - hi) + (float)(uint32_t)x * 0x1p-32f) * 0x1p-32f;
-    float sa, ca;
-    sincospif(2.0f * th, &sa, &ca);
-    const float b = tl * 6.28318530717958648f;
-    const float sb = b - b * b * b * (1.0f / 6.0f), cb = 1.0f - 0.5f * b * b;
-    return make_float2(ca * cb - sa * sb, sa * cb + ca * sb);
-}
-__device__ __forceinline__ double2 unit_phase(double, uint64_t x) {
-    const double t = (double)(int64_t)x * 0x1p-64;
-    double s, c;
-    sincospi(2.0 * t, &s, &c);
-    return make_double2(c, s);
-}
-
-template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
-    V r;
-    r.x = a.x * b.x - a.y * b.y;
-    r.y = a.x * b.y + a.y * b.x;
-    return r;
-}
-
-__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
-    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
-    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
-    return ((uint64_t)hi << 32) | lo;
-}
-__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) v += shfl_xor64(v, m);
-    return v;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(256) k_phase(typename Amp<R>::T* __restrict__ psi, int n, const Args a) {
     using T = typename Amp<R>::T;
@@ -167,18 +129,12 @@ __global__ void __launch_bounds__(256) k_phase(typename Amp<R>::T* __restrict__ 
 }  // namespace phase
 
 // ---- host: the quadratic form of a run of diagonal gates -------------------------------------------------------
-namespace {
-
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-uint64_t to_turns(double phi) {
-    double t = phi / kTwoPi;
+uint64_t phase_turns(double phi) {
+    double t = phi / 6.283185307179586476925286766559;
     t -= std::floor(t);
     if (!(t < 1.0)) t = 0.0;
     return (uint64_t)std::ldexp(t, 64);  // t < 1, so the value fits; 53 significant bits
 }
-
-}  // namespace
 
 bool phase_gate_ok(const qsim_gate& g) {
     return g.k >= 1 && g.k + g.nc <= 2;
@@ -225,8 +181,8 @@ void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, 
     std::vector<uint64_t> hg(G, 0);  // single-bit terms of the low and block bits
     for (int a = 0; a < n; ++a) {
         if (f.h[a] == 0.0) continue;
-        if (a >= G) { tt_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); tt_l.push_back(to_turns(f.h[a])); }
-        else hg[a] = to_turns(f.h[a]);
+        if (a >= G) { tt_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); tt_l.push_back(phase_turns(f.h[a])); }
+        else hg[a] = phase_turns(f.h[a]);
     }
     // pair terms by the groups of their bits (a < b)
     std::vector<uint64_t> small(kSmallWords, 0);
@@ -237,7 +193,7 @@ void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, 
     double midmid[5][5] = {};
     uint64_t lanelane[5][5] = {};
     for (const auto& p : f.pairs) {
-        const uint64_t L = to_turns(p.lam);
+        const uint64_t L = phase_turns(p.lam);
         if (p.a >= G) { tt_ab.push_back((uint32_t)p.a | ((uint32_t)p.b << 8)); tt_l.push_back(L); }
         else if (p.b >= G) lt[p.a].push_back({(uint32_t)p.b, L});           // low/block x top
         else if (p.a >= kLowBits) {                                        // block x block
@@ -270,7 +226,7 @@ void phase_pack(const PhaseForm& f, int dtype, std::vector<unsigned char>& out, 
     }
     for (int j = 0; j < kLowBits + kBlockBits; ++j)
         for (const auto& t : lt[j]) { lt_a.push_back(t.first); lt_l.push_back(t.second); }
-    pk.c = to_turns(f.c);
+    pk.c = phase_turns(f.c);
     pk.nb = nb;
     pk.ntt = (int)tt_ab.size();
     pk.lt_off[0] = 0;

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -174,15 +175,23 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
     else tmem_ld_x32(taddr, v);
 }
 
+constexpr int kEpiGroups = kRowBits + 1 + 5;  // row bits, the half bit, up to 5 other column bits
+constexpr int kEpiTile = 1 + kEpiGroups;     // factors per tile
+
 struct Args {
     int nS;            // K + 7 index bits covered by a tile
     int spos[24];      // those bit positions, ascending (zeros inserted there to form a tile base)
     int rpos[kRowBits];// row bit j <-> index bit rpos[j]
     int tpos[8];       // column bit j <-> target j
-    int rloc[kRowBits];// row bit j <-> bit rloc[j] of the tile's natural order (position among spos)
-    int tloc[8];       // column bit j <-> bit tloc[j] of the tile's natural order
-    int cbits;         // the tile is 2^(nS - cbits) contiguous chunks of 2^cbits amplitudes (cbits >= 7)
     uint64_t ntiles;
+    // Phase epilogue: every output amplitude x is multiplied by exp(i phi(x)), phi a quadratic form of its
+    // index bits (a run of diagonal gates that follows the block). Terms on target bits alone are folded
+    // into U; the rest come as unit complex factors. Bit groups: tile bits (outside the tile), row bits
+    // 0..6, the column bit that selects a warp's half (target K-1, "H"), the other column bits (V).
+    const float2* epi_tiles;              // [ntiles][14]: the tile's factors: tile-only terms, then the factor
+                                          // of each row bit, H and each V bit given the tile's bits
+    const float2* epi_thr;                // [2][128][6]: per (half, row): row / H-only terms, then each V bit's
+                                          // factor given the row and H bits
 };
 
 // Warp-specialised block kernel, all precisions: warps 0..7 move data (tile loads, split into the A planes
@@ -217,7 +226,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(addr) : "memory");
 }
 
-template <int K, int PREC, int MODE>
+template <int K, int PREC, int MODE, bool EPI>
 __global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
@@ -399,13 +408,49 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
             __syncwarp();
             if (lane == 0) mbar_arrive(full(p));
         };
+        // EPI: this thread's unit factors for tile t: E[0] for every amplitude (tile-only, row and H terms),
+        // E[1 + v] for column bit v (its cross terms with the tile, row and H bits).
+        constexpr int NV = K - 1;
+        const int half = (warp >> 2) & 1;
+        auto epi_factors = [&](uint64_t t, float2 (&E)[NV + 1]) {
+            const float2* tf = a.epi_tiles + t * kEpiTile;
+            const float2* th = a.epi_thr + (uint64_t)(half * 128 + r) * 6;
+            float2 e0 = cmul(tf[0], th[0]);
+#pragma unroll
+            for (int g = 0; g < kRowBits; ++g)
+                if ((r >> g) & 1) e0 = cmul(e0, tf[1 + g]);
+            if (half) e0 = cmul(e0, tf[1 + kRowBits]);
+            E[0] = e0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) E[1 + v] = cmul(tf[2 + kRowBits + v], th[1 + v]);
+        };
         auto epilogue = [&](uint64_t t, uint32_t dcol) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+            [[maybe_unused]] float2 E[NV + 1];
+            if constexpr (EPI) epi_factors(t, E);
 #pragma unroll
             for (int h = 0; h < CPT / QE; ++h) {
                 uint32_t v[2 * QE];
                 tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
                 wait_ld();
+                if constexpr (EPI) {
+                    // factors of the chunk's 8 columns: column bits 0..2 vary inside it, bits 3.. are h
+                    float2 f[QE];
+                    f[0] = E[0];
+#pragma unroll
+                    for (int v2 = 3; v2 < NV; ++v2)
+                        if ((h >> (v2 - 3)) & 1) f[0] = cmul(f[0], E[1 + v2]);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e)
+#pragma unroll
+                        for (int q = 0; q < (1 << e); ++q) f[(1 << e) + q] = cmul(f[q], E[1 + e]);
+#pragma unroll
+                    for (int j = 0; j < QE; ++j) {
+                        const float2 x = cmul(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])), f[j]);
+                        v[2 * j] = __float_as_uint(x.x);
+                        v[2 * j + 1] = __float_as_uint(x.y);
+                    }
+                }
                 if constexpr (Q0) {
 #pragma unroll
                     for (int j = 0; j < QE; j += 4) {
@@ -642,15 +687,25 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
 
 // B operand: Bt[n][kk] of the real form, Bt[2i][2c] = Re U_ic, Bt[2i][2c+1] = -Im U_ic, Bt[2i+1][2c] = Im U_ic,
 // Bt[2i+1][2c+1] = Re U_ic, split into planes and written in the swizzled shared-memory byte layout.
+// With rowphase (device, 2^K radians), row i of U is multiplied by exp(i rowphase[i]) first: the phase
+// epilogue's terms on target bits alone.
 template <int PREC>
-__global__ void k_tc_prepare(const double* __restrict__ U, int K, unsigned char* __restrict__ out) {
+__global__ void k_tc_prepare(const double* __restrict__ U, int K, const double* __restrict__ rowphase,
+                             unsigned char* __restrict__ out) {
     using C = Cfg<PREC>;
     const int D = 1 << K, NR = 2 * D;
     const int PB = plane_bytes(K, C::esize);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NR * NR; idx += gridDim.x * blockDim.x) {
         const int n = idx / NR, kk = idx % NR;
         const int i = n >> 1, c = kk >> 1;
-        const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
+        double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
+        if (rowphase) {
+            double sp, cp;
+            sincos(rowphase[i], &sp, &cp);
+            const double r2 = ur * cp - ui * sp;
+            ui = ur * sp + ui * cp;
+            ur = r2;
+        }
         const double v = (n & 1) == 0 ? ((kk & 1) == 0 ? ur : -ui) : ((kk & 1) == 0 ? ui : ur);
         const uint32_t off = sw128_offset(n, kk, NR, C::esize);
         if constexpr (C::esize == 4) {
@@ -680,7 +735,7 @@ size_t smem_bytes(int K, int planes, int esize) {
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
-template <int K, int PREC, int MODE>
+template <int K, int PREC, int MODE, bool EPI>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
@@ -692,19 +747,111 @@ cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cud
     };
     // BF16x6 (three A planes, the heaviest split) runs faster on 16 warps with two A buffers than on the
     // 8 data warps of the warp-specialised kernel (which alone has the 32-byte path)
-    if constexpr (PREC == QSIM_PREC_BF16X6) return launch(k_tc_block_a2<K, PREC, MODE != kRowsInLanes>, kThreads);
-    else return launch(k_tc_block<K, PREC, MODE>, kThreadsWS);
+    if constexpr (PREC == QSIM_PREC_BF16X6) {
+        if constexpr (EPI) return cudaErrorInvalidValue;  // the 16-warp kernel has no phase epilogue
+        else return launch(k_tc_block_a2<K, PREC, MODE != kRowsInLanes>, kThreads);
+    } else {
+        return launch(k_tc_block<K, PREC, MODE, EPI>, kThreadsWS);
+    }
+}
+
+template <int K, int PREC, bool EPI>
+cudaError_t apply_e(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
+    if (a.tpos[0] == 0 && a.tpos[1] == 1 && PREC != QSIM_PREC_BF16X6 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
+        return apply_p<K, PREC, kQuadsInLanes, EPI>(psi, a, dB, err, s, d);
+    if (a.tpos[0] == 0) return apply_p<K, PREC, kPairsInLanes, EPI>(psi, a, dB, err, s, d);
+    return apply_p<K, PREC, kRowsInLanes, EPI>(psi, a, dB, err, s, d);
 }
 
 template <int K, int PREC>
 cudaError_t apply_t(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
-    if (a.tpos[0] == 0 && a.tpos[1] == 1 && PREC != QSIM_PREC_BF16X6 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
-        return apply_p<K, PREC, kQuadsInLanes>(psi, a, dB, err, s, d);
-    if (a.tpos[0] == 0) return apply_p<K, PREC, kPairsInLanes>(psi, a, dB, err, s, d);
-    return apply_p<K, PREC, kRowsInLanes>(psi, a, dB, err, s, d);
+    if (a.epi_tiles) return apply_e<K, PREC, true>(psi, a, dB, err, s, d);
+    return apply_e<K, PREC, false>(psi, a, dB, err, s, d);
 }
 
 }  // namespace tc
+
+void tc_epi_pack(int n, int k, const int* targets, const PhaseForm& f, std::vector<unsigned char>& out,
+                 TcEpiPacked& pk) {
+    // group of each index bit as the kernel sees it: row bit j -> j, the half column bit (target k-1) -> 7,
+    // column bit v < k-1 -> 8 + v, tile bits -> -1
+    std::vector<int> grp(n, -1);
+    uint64_t tmask = 0;
+    for (int j = 0; j < k; ++j) tmask |= 1ull << targets[j];
+    int nr = 0;
+    for (int q = 0; q < n && nr < tc::kRowBits; ++q)
+        if (!((tmask >> q) & 1)) grp[q] = nr++;
+    grp[targets[k - 1]] = tc::kRowBits;
+    for (int v = 0; v < k - 1; ++v) grp[targets[v]] = tc::kRowBits + 1 + v;
+    auto colbit = [&](int g) { return g == tc::kRowBits ? k - 1 : g - tc::kRowBits - 1; };  // g >= 7: column bit
+    auto bit = [](int g, int half, int r) { return g < tc::kRowBits ? (r >> g) & 1 : half; };
+    std::vector<double> rowphase(1 << k, f.c);          // terms on target bits alone (and the constant)
+    std::vector<uint32_t> tt_ab;
+    std::vector<uint64_t> tt_l;
+    std::vector<std::vector<std::pair<uint32_t, uint64_t>>> tb(tc::kEpiGroups);
+    std::vector<double> thr(2 * 128 * 6, 0.0);          // radians: slot 0 row / H terms, 1 + v: V-bit coefficients
+    auto thr_add = [&](int slot, double L, int g1, int g2) {  // conditions on row / H groups (g < 0: none)
+        for (int half = 0; half < 2; ++half)
+            for (int r = 0; r < 128; ++r)
+                if ((g1 < 0 || bit(g1, half, r)) && (g2 < 0 || bit(g2, half, r))) thr[(half * 128 + r) * 6 + slot] += L;
+    };
+    auto rowphase_add = [&](double L, int c1, int c2) {  // column bits c1, c2 (c2 < 0: a single bit)
+        for (int m = 0; m < (1 << k); ++m)
+            if (((m >> c1) & 1) && (c2 < 0 || ((m >> c2) & 1))) rowphase[m] += L;
+    };
+    for (int a = 0; a < n; ++a) {
+        if (f.h[a] == 0.0) continue;
+        const int g = grp[a];
+        if (g < 0) { tt_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); tt_l.push_back(phase_turns(f.h[a])); }
+        else if (g < tc::kRowBits) thr_add(0, f.h[a], g, -1);
+        else rowphase_add(f.h[a], colbit(g), -1);
+    }
+    for (const auto& p : f.pairs) {
+        const int ga = grp[p.a], gb = grp[p.b];
+        if (ga < 0 && gb < 0) { tt_ab.push_back((uint32_t)p.a | ((uint32_t)p.b << 8)); tt_l.push_back(phase_turns(p.lam)); }
+        else if (ga < 0) tb[gb].push_back({(uint32_t)p.a, phase_turns(p.lam)});
+        else if (gb < 0) tb[ga].push_back({(uint32_t)p.b, phase_turns(p.lam)});
+        else if (ga >= tc::kRowBits && gb >= tc::kRowBits) rowphase_add(p.lam, colbit(ga), colbit(gb));  // both targets
+        else if (ga < tc::kRowBits && gb < tc::kRowBits) thr_add(0, p.lam, ga, gb);                      // both rows
+        else {
+            const int gr = ga < tc::kRowBits ? ga : gb, gc = ga < tc::kRowBits ? gb : ga;  // a row bit and a column bit
+            if (gc == tc::kRowBits) thr_add(0, p.lam, gr, gc);                            // the H bit: per thread
+            else thr_add(1 + gc - tc::kRowBits - 1, p.lam, gr, -1);                      // a V bit: its coefficient
+        }
+    }
+    std::vector<uint32_t> tb_t;
+    std::vector<uint64_t> tb_l;
+    pk.off[0] = 0;
+    for (int g = 0; g < tc::kEpiGroups; ++g) {
+        for (const auto& t : tb[g]) { tb_t.push_back(t.first); tb_l.push_back(t.second); }
+        pk.off[g + 1] = (int)tb_t.size();
+    }
+    pk.c = 0;  // the constant went into U with the target-only terms
+    pk.ntt = (int)tt_ab.size();
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    size_t off = 0;
+    pk.off_rowphase = off; off = al(off + 8 * rowphase.size());
+    pk.off_tt_ab = off; off = al(off + 4 * tt_ab.size());
+    pk.off_tt_l = off;  off = al(off + 8 * tt_l.size());
+    pk.off_tb_t = off;  off = al(off + 4 * tb_t.size());
+    pk.off_tb_l = off;  off = al(off + 8 * tb_l.size());
+    pk.off_thr = off;   off = al(off + 8 * thr.size());
+    out.assign(off, 0);
+    auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(out.data() + o, src, bytes); };
+    put(pk.off_rowphase, rowphase.data(), 8 * rowphase.size());
+    put(pk.off_tt_ab, tt_ab.data(), 4 * tt_ab.size());
+    put(pk.off_tt_l, tt_l.data(), 8 * tt_l.size());
+    put(pk.off_tb_t, tb_t.data(), 4 * tb_t.size());
+    put(pk.off_tb_l, tb_l.data(), 8 * tb_l.size());
+    for (size_t i = 0; i < thr.size(); ++i) {
+        const float v2[2] = {(float)std::cos(thr[i]), (float)std::sin(thr[i])};
+        put(pk.off_thr + 8 * i, v2, 8);
+    }
+}
+
+size_t tc_epi_scratch_bytes(int n, int k) {
+    return sizeof(float2) * tc::kEpiTile * ((size_t)1 << (n - k - tc::kRowBits));
+}
 
 bool tc_supported(int k, int precision) {
     return (k == 5 || k == 6) &&
@@ -718,24 +865,52 @@ size_t tc_operand_bytes(int k, int precision) {
     return (size_t)planes * tc::plane_bytes(k, esize);
 }
 
-cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s) {
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s,
+                              const double* rowphase) {
     if (!tc_supported(k, precision)) return cudaErrorInvalidValue;
     unsigned char* out = static_cast<unsigned char*>(dB);
     const int blocks = ((2 << k) * (2 << k) + 255) / 256;
     switch (precision) {
-        case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, out); break;
-        case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, out); break;
-        default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, out); break;
+        case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
+        case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
+        default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
     }
     return cudaGetLastError();
 }
 
+// The phase epilogue's per-tile factors (one thread per tile): exp(i * terms on tile bits alone) and, for each
+// row bit, H and V bit, exp(i * its cross terms with the tile's bits).
+__global__ void k_tc_epi_tiles(uint64_t ntiles, tc::Args a, TcEpiPacked pk, const unsigned char* __restrict__ tab,
+                               float2* __restrict__ out) {
+    const uint32_t* tt_ab = reinterpret_cast<const uint32_t*>(tab + pk.off_tt_ab);
+    const uint64_t* tt_l = reinterpret_cast<const uint64_t*>(tab + pk.off_tt_l);
+    const uint32_t* tb_t = reinterpret_cast<const uint32_t*>(tab + pk.off_tb_t);
+    const uint64_t* tb_l = reinterpret_cast<const uint64_t*>(tab + pk.off_tb_l);
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t tb = insert_zeros(t, a.spos, a.nS);
+        uint64_t s = pk.c;
+        for (int i = 0; i < pk.ntt; ++i)
+            if ((tb >> (tt_ab[i] & 0xFF)) & (tb >> (tt_ab[i] >> 8)) & 1) s += tt_l[i];
+        float2* o = out + t * tc::kEpiTile;
+        o[0] = unit_phase(0.0f, s);
+        for (int g = 0; g < tc::kEpiGroups; ++g) {
+            uint64_t k = 0;
+            for (int i = pk.off[g]; i < pk.off[g + 1]; ++i)
+                if ((tb >> tb_t[i]) & 1) k += tb_l[i];
+            o[1 + g] = unit_phase(0.0f, k);
+        }
+    }
+}
+
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
-                            unsigned* dev_err, cudaStream_t s, const DevInfo& d) {
+                            unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab,
+                            const TcEpiPacked* epi, void* epi_scratch) {
     if (!tc_supported(k, precision) || n < k + tc::kRowBits) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
+    if (epi && (!epi_tab || !epi_scratch || precision == QSIM_PREC_BF16X6)) return cudaErrorInvalidValue;
     tc::Args a;
     std::memset(&a, 0, sizeof(a));
+
     uint64_t tmask = 0;
     for (int j = 0; j < k; ++j) { a.tpos[j] = targets[j]; tmask |= 1ull << targets[j]; }
     int nr = 0;
@@ -743,15 +918,20 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
         if (!((tmask >> q) & 1)) a.rpos[nr++] = q;
     uint64_t smask = tmask;
     for (int j = 0; j < tc::kRowBits; ++j) smask |= 1ull << a.rpos[j];
-    int loc[64];
     for (int q = 0; q < n; ++q)
-        if ((smask >> q) & 1) { loc[q] = a.nS; a.spos[a.nS++] = q; }
-    for (int j = 0; j < tc::kRowBits; ++j) a.rloc[j] = loc[a.rpos[j]];
-    for (int j = 0; j < k; ++j) a.tloc[j] = loc[targets[j]];
-    a.cbits = 0;
-    while (a.cbits < a.nS && a.spos[a.cbits] == a.cbits) ++a.cbits;  // >= 7: bits below the 7th non-target
-    if (a.cbits < tc::kRowBits || a.nS - a.cbits > 6) return cudaErrorInvalidValue;  // at most 64 chunks
+        if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
+    if (epi) {
+        // the tile factors go to the scratch (tc_epi_scratch_bytes), read by the block kernel that follows
+        const unsigned char* b = static_cast<const unsigned char*>(epi_tab);
+        float2* tiles = static_cast<float2*>(epi_scratch);
+        const unsigned grid = grid_for((int64_t)a.ntiles, 256, d.num_sms, 4);
+        k_tc_epi_tiles<<<grid, 256, 0, s>>>(a.ntiles, a, *epi, b, tiles);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.epi_tiles = tiles;
+        a.epi_thr = reinterpret_cast<const float2*>(b + epi->off_thr);
+    }
     switch (precision * 8 + k) {
         case QSIM_PREC_TF32X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
         case QSIM_PREC_TF32X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);

@@ -20,7 +20,8 @@
 
 namespace qsim {
 
-enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4, OP_PHASE = 5 };
+enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4, OP_PHASE = 5,
+              OP_MERGED = 6 /* a phase pass folded into the tensor-core block before it; dropped from the plan */ };
 
 struct PlanOp {
     int kind = OP_DENSE_SMALL;
@@ -36,7 +37,15 @@ struct PlanOp {
     int nswap = 0;             // OP_SWAP: exchange qubit swap_a[i] with swap_b[i]
     int swap_a[8] = {0}, swap_b[8] = {0};
     PhasePacked phase;         // OP_PHASE: launch parameters; tables at dev_off
-    std::vector<unsigned char> blob;  // OP_PHASE: the tables until they are uploaded
+    std::vector<unsigned char> blob;  // OP_PHASE, OP_TC with a phase epilogue: the tables until uploaded
+    PhaseForm form;            // OP_PHASE (and the epilogue it becomes): the combined phase
+    bool has_epi = false;      // OP_TC: the output gets the phase of `form` (the pass that followed it)
+    TcEpiPacked epi;           // OP_TC with has_epi: launch parameters; tables at epi_off
+    size_t epi_off = 0;
+};
+
+struct PlanExtra {
+    size_t epi_scratch_off = 0;  // per-tile factors of phase epilogues (shared: passes run in order)
 };
 
 }  // namespace qsim
@@ -53,6 +62,7 @@ struct qsim_plan {
     const qsim_state* ghandle = nullptr;
     void* gpsi = nullptr;
     cudaStream_t gstream = nullptr;
+    qsim::PlanExtra extra;
 };
 
 namespace qsim {
@@ -180,7 +190,12 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                 break;
             case OP_TC:
                 e = launch_tc_apply(h->psi, h->n, op.k, op.targets, static_cast<char*>(p->dbuf) + op.dev_off,
-                                    op.precision, h->derr, h->stream, h->dev);
+                                    op.precision, h->derr, h->stream, h->dev,
+                                    op.has_epi ? static_cast<char*>(p->dbuf) + op.epi_off : nullptr,
+                                    op.has_epi ? &op.epi : nullptr,
+                                    op.has_epi ? static_cast<char*>(p->dbuf) + p->extra.epi_scratch_off : nullptr);
+                break;
+            case OP_MERGED:
                 break;
             case OP_SWAP:
                 e = launch_swap(h->dtype, h->psi, h->n, op.swap_a, op.swap_b, op.nswap, h->stream, h->dev, nullptr);
@@ -265,6 +280,38 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             if (alt.size() < blocks.size()) blocks.swap(alt);
         }
     }
+    // A diagonal block moves after a tensor-core block that follows it when they share no qubit (so they
+    // commute), and neighbouring diagonal blocks merge (diagonal gates commute): a phase pass then follows
+    // the tensor-core block and becomes its epilogue.
+    if (use_wide && opts.precision != QSIM_PREC_SIMT && dtype == QSIM_C64) {
+        auto qubits = [&](const std::vector<int>& blk) { uint64_t m = 0; for (int gi : blk) m |= gmask[gi]; return m; };
+        auto all_wide = [&](const std::vector<int>& blk) {
+            for (int gi : blk) if (!gwide[gi]) return false;
+            return true;
+        };
+        auto tc_like = [&](const std::vector<int>& blk) {
+            const int kb = popcnt(qubits(blk));
+            bool diag = true;
+            for (int gi : blk) diag = diag && gdiag[gi];
+            return !diag && kb >= tc_min && kb <= 6 && tc_supported(kb, opts.precision) && n >= kb + 7 &&
+                   !(blk.size() == 1 && c->gates[blk[0]].nc > 0);
+        };
+        for (bool changed = true; changed;) {
+            changed = false;
+            for (size_t i = 0; i + 1 < blocks.size(); ++i) {
+                if (!all_wide(blocks[i])) continue;
+                if (all_wide(blocks[i + 1])) {
+                    blocks[i].insert(blocks[i].end(), blocks[i + 1].begin(), blocks[i + 1].end());
+                    blocks.erase(blocks.begin() + (long)i + 1);
+                    changed = true;
+                } else if (tc_like(blocks[i + 1]) && (qubits(blocks[i]) & qubits(blocks[i + 1])) == 0) {
+                    std::swap(blocks[i], blocks[i + 1]);
+                    ++i;  // the diagonal block now sits at i + 1; look at what follows it on the next sweep
+                    changed = true;
+                }
+            }
+        }
+    }
 
     // ---- decide each block's pass and lay out the device buffer --------------------------------------------
     const size_t amp = dtype == QSIM_C64 ? 8 : 16;
@@ -289,12 +336,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             // a phase pass (wider than the diagonal kernel's 6 qubits): the quadratic form of every gate
             std::vector<const qsim_gate*> gp;
             for (int gi : blk) gp.push_back(&c->gates[gi]);
-            PhaseForm form;
-            if (!phase_form_build(gp.data(), (int)gp.size(), n, form)) { delete p; set_error("phase pass"); return QSIM_EINVAL; }
+            if (!phase_form_build(gp.data(), (int)gp.size(), n, op.form)) { delete p; set_error("phase pass"); return QSIM_EINVAL; }
             op.kind = OP_PHASE;
-            phase_pack(form, dtype, op.blob, op.phase);
-            op.dev_off = dev_bytes;
-            dev_bytes = align(dev_bytes + op.blob.size());
             p->ops.push_back(std::move(op));
             continue;
         }
@@ -411,6 +454,34 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         p->ops.push_back(std::move(op));
     }
 
+    // ---- phase passes: one right after a tensor-core block becomes that block's epilogue (it multiplies
+    // the block's output in registers instead of taking a pass of its own); the others keep their pass ----
+    for (size_t oi = 0; oi < p->ops.size(); ++oi) {
+        PlanOp& op = p->ops[oi];
+        if (op.kind != OP_PHASE) continue;
+        PlanOp* prev = oi > 0 ? &p->ops[oi - 1] : nullptr;
+        if (prev && prev->kind == OP_TC && !prev->has_epi && prev->precision != QSIM_PREC_BF16X6) {
+            prev->has_epi = true;
+            prev->form = std::move(op.form);
+            prev->gates += op.gates;
+            op.kind = OP_MERGED;
+            continue;
+        }
+        phase_pack(op.form, dtype, op.blob, op.phase);
+        op.dev_off = dev_bytes;
+        dev_bytes = align(dev_bytes + op.blob.size());
+    }
+    size_t epi_scratch = 0;
+    for (PlanOp& op : p->ops) {
+        if (op.kind != OP_TC || !op.has_epi) continue;
+        tc_epi_pack(n, op.k, op.targets, op.form, op.blob, op.epi);
+        op.epi_off = dev_bytes;
+        dev_bytes = align(dev_bytes + op.blob.size());
+        epi_scratch = std::max(epi_scratch, tc_epi_scratch_bytes(n, op.k));
+    }
+    p->extra.epi_scratch_off = dev_bytes;
+    dev_bytes = align(dev_bytes + epi_scratch);
+
     // ---- device buffer: [operands][compose out][pool][block descriptors][gate descriptors] -------------------
     const size_t off_out = dev_bytes;
     const size_t off_pool = align(off_out + sizeof(double) * 2 * (size_t)compose_out);
@@ -422,7 +493,18 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     p->dbuf_bytes = total;
     char* base = static_cast<char*>(p->dbuf);
     int rc = QSIM_OK;
-    if (!cblocks.empty()) {
+    // phase tables first: the row phases of an epilogue go into its block's operand below
+    for (size_t oi = 0; rc == QSIM_OK && oi < p->ops.size(); ++oi) {
+        PlanOp& op = p->ops[oi];
+        if (op.kind != OP_PHASE && !(op.kind == OP_TC && op.has_epi)) continue;
+        e = cudaMemcpyAsync(base + (op.kind == OP_PHASE ? op.dev_off : op.epi_off), op.blob.data(), op.blob.size(),
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pageable host source
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+        op.blob.clear();
+        op.blob.shrink_to_fit();
+    }
+    if (rc == QSIM_OK && !cblocks.empty()) {
         e = cudaMemcpyAsync(base + off_pool, pool.data(), sizeof(double) * pool.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_cb, cblocks.data(), sizeof(ComposeBlock) * cblocks.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_cg, cgates.data(), sizeof(ComposeGate) * cgates.size(), cudaMemcpyHostToDevice, s);
@@ -439,7 +521,9 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             const double* U = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx].out_off;
             const int D = 1 << pd.kb;
             if (pd.kind == OP_TC) {
-                e = launch_tc_prepare(U, pd.kb, op.precision, base + op.dev_off, s);
+                e = launch_tc_prepare(U, pd.kb, op.precision, base + op.dev_off, s,
+                                      op.has_epi ? reinterpret_cast<const double*>(base + op.epi_off + op.epi.off_rowphase)
+                                                 : nullptr);
             } else if (pd.kind == OP_DENSE_TILE) {
                 e = launch_convert_matrix(dtype, U, base + op.dev_off, 2 * (int64_t)D * D, s);
             } else {
@@ -460,15 +544,6 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             }
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
-    }
-    for (size_t oi = 0; rc == QSIM_OK && oi < p->ops.size(); ++oi) {
-        PlanOp& op = p->ops[oi];
-        if (op.kind != OP_PHASE) continue;
-        e = cudaMemcpyAsync(base + op.dev_off, op.blob.data(), op.blob.size(), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pageable host source
-        if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
-        op.blob.clear();
-        op.blob.shrink_to_fit();
     }
     for (size_t di = 0; rc == QSIM_OK && di < direct.size(); ++di) {
         PlanOp& op = p->ops[direct[di]];
@@ -593,6 +668,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         }
         p->ops.swap(out_ops);
     }
+
+    // drop the phase passes that became epilogues
+    p->ops.erase(std::remove_if(p->ops.begin(), p->ops.end(), [](const PlanOp& op) { return op.kind == OP_MERGED; }),
+                 p->ops.end());
 
     // ---- statistics ---------------------------------------------------------------------------------------
     qsim_plan_info& I = p->info;
