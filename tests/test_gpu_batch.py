@@ -108,3 +108,19 @@ def test_batch_rejects_bad_input(qsim):
     c.append(W.Gate((0, 1, 2), (3, 4), np.eye(8), "wide"))
     with pytest.raises(qsim.QsimError):
         qsim.Batch([c])
+
+
+def test_full_size_batch_256_tfim_chains(qsim):
+    """The benchmark's batch (256 chains, 10-24 qubits, 8-32 Trotter steps, seed 4) in one launch: every
+    <Z> in [-1, 1] and finite, and the circuits of up to 16 qubits against the oracle."""
+    batch = W.tfim_batch(256, seed=4, nmax=24)
+    cs = [c for c, _, _ in batch]
+    b = qsim.Batch(cs, max_fused=0)
+    b.execute(use_graph=True)
+    res = b.results()
+    for (zi, zz), c in zip(res, cs):
+        assert np.all(np.isfinite(zi)) and np.all(np.abs(zi) <= 1 + 1e-5)
+        assert np.all(np.isfinite(zz)) and np.all(np.abs(zz) <= 1 + 1e-5)
+    small = [i for i, c in enumerate(cs) if c.n <= 16][:24]
+    assert len(small) >= 10
+    check([res[i] for i in small], [cs[i] for i in small])

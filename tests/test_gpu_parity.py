@@ -243,6 +243,38 @@ def test_qft_closed_form(qsim, mode, k):
     close(st.get_state(), qft_closed_form(n, x), n, 0)
 
 
+def test_full_size_qft28_tensor_cores_closed_form(qsim):
+    """The 28-qubit QFT of the benchmark (2 GiB complex64), in the configuration it times (6-qubit 3xTF32
+    blocks with phase epilogues and phase passes): 8192 sampled amplitudes against the closed form."""
+    import torch
+    n = 28
+    x = W.basis_index(n, 2)
+    p = qsim.Plan(W.qft(n), qsim.C64, mode=1, max_fused=6, precision=1, tc_min_k=5, use_graph=True)
+    st = make_state(qsim, n, 0, basis=x)
+    p.execute(st)
+    rng = np.random.default_rng(5)
+    ys = np.sort(rng.choice(1 << n, size=8192, replace=False))
+    got = st.tensor[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
+    ph = (np.uint64(x) * ys.astype(np.uint64)) & np.uint64((1 << n) - 1)
+    ref = np.exp(2j * math.pi * ph.astype(np.float64) / (1 << n)) / math.sqrt(1 << n)
+    assert float(np.max(np.abs(got - ref))) <= 1e-6
+    assert abs(st.norm() - 1.0) <= 1e-4
+
+
+def test_brickwork_14q_complex128_fused_graph(qsim):
+    """The 14-qubit complex128 brickwork in the benchmark's configuration (4-qubit SIMT fusion, CUDA graph
+    replay): full state against the oracle at the complex128 bar, twice in a row."""
+    n = 14
+    c = W.brickwork(n, 20, seed=1)
+    ref = oracle.run(c)
+    p = qsim.Plan(c, 1, mode=1, max_fused=4, use_graph=True)
+    st = make_state(qsim, n, 1)
+    for _ in range(2):
+        st.set_basis(0)
+        p.execute(st)
+        close(st.get_state(), ref, n, 1)
+
+
 @pytest.mark.parametrize("dtype", DT)
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_fused_simt_random_circuit(qsim, dtype, k):
