@@ -14,11 +14,14 @@
 // expiry the kernel records DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees its tensor memory
 // and returns.
 //   3xTF32 and BF16x3 (k_tc_block): warp-specialised. Eight data warps (two per TMEM lane quadrant) load
-//   tiles into registers (coalesced; 16-byte vectors when qubit 0 is the block's first target; one tile
-//   ahead at K = 6, two at K = 5), split them into the planes of the A operand in TMEM and run the epilogue
-//   (tcgen05.ld of the finished accumulator, stores back in place); a ninth warp issues the MMAs. Each A
-//   plane's products form a phase with its own barriers, so the split of one plane overlaps the MMAs on
-//   another, and two TMEM accumulators let the epilogue of tile t-1 overlap the MMAs of tile t.
+//   tiles into registers (one tile ahead at K = 6, two at K = 5), split them into the planes of the A
+//   operand in TMEM and run the epilogue (tcgen05.ld of the finished accumulator, stores back in place); a
+//   ninth warp issues the MMAs. Each A plane's products form a phase with its own barriers, so the split of
+//   one plane overlaps the MMAs on another, and two TMEM accumulators let the epilogue of tile t-1 overlap
+//   the MMAs of tile t. A thread owns one row of a tile (its TMEM lane); how its amplitudes move (Mode):
+//   8-byte accesses, 16-byte pairs when qubit 0 is the first target, 32-byte quads (whole sectors) when
+//   qubits 0 and 1 are the first two. With a phase epilogue (EPI) every output amplitude is multiplied by
+//   unit complex factors of its tile, row and column bits before it is stored.
 //   BF16x6 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
 #include <cuda_bf16.h>
 
