@@ -94,7 +94,11 @@ typedef struct {
        the plan tracks the logical -> physical qubit map; the identity order is restored at the end.
        0 = off (every qubit is addressed in place). */
     int32_t local_qubits;
-    int32_t reserved[2];
+    /* 1 (qsim_plan_create only): plan on the host and stop before any device work (no device needed):
+       the plan lists its passes (qsim_plan_num_passes, qsim_plan_pass_info, qsim_plan_info) but cannot be
+       executed (QSIM_EINVAL). */
+    int32_t dry_run;
+    int32_t reserved;
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */

@@ -63,6 +63,7 @@ struct qsim_plan {
     void* gpsi = nullptr;
     cudaStream_t gstream = nullptr;
     qsim::PlanExtra extra;
+    bool dry = false;  // planned on the host only: no device buffer, cannot execute
 };
 
 namespace qsim {
@@ -234,10 +235,14 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
     const int n = c->n;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    const bool dry = opts.dry_run != 0;
     DevInfo dev;
-    cudaError_t e = cudaGetDevice(&dev.device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&dev.num_sms, cudaDevAttrMultiProcessorCount, dev.device);
-    if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+    cudaError_t e = cudaSuccess;
+    if (!dry) {
+        e = cudaGetDevice(&dev.device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&dev.num_sms, cudaDevAttrMultiProcessorCount, dev.device);
+        if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+    }
 
     const int G = c->num_gates;
     std::vector<uint64_t> gmask(G);
@@ -489,6 +494,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     p->extra.epi_scratch_off = dev_bytes;
     dev_bytes = align(dev_bytes + epi_scratch);
 
+    p->dry = dry;
+    if (!dry) {
     // ---- device buffer: [operands][compose out][pool][block descriptors][gate descriptors] -------------------
     const size_t off_out = dev_bytes;
     const size_t off_pool = align(off_out + sizeof(double) * 2 * (size_t)compose_out);
@@ -569,6 +576,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         op.mat.shrink_to_fit();
     }
     if (rc) { cudaFree(p->dbuf); delete p; return rc; }
+    }  // !dry
 
     // ---- global / local index bits: reorder before passes that touch a global qubit ------------------------
     if (opts.local_qubits > 0 && opts.local_qubits < n) {
@@ -700,6 +708,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
 int qsim_plan_execute(qsim_h h, qsim_plan_h p) {
     if (!h || !p) { set_error("NULL argument"); return QSIM_EINVAL; }
     set_error("%s", "");
+    if (p->dry) { set_error("plan was created as a dry run"); return QSIM_EINVAL; }
     if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
     if (!p->use_graph || h->stream == nullptr) return enqueue_ops(h, p);
     if (p->gexec && p->ghandle == h && p->gpsi == h->psi && p->gstream == h->stream) {
@@ -750,6 +759,7 @@ int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
 int qsim_plan_execute_range(qsim_h h, qsim_plan_h p, int64_t first, int64_t count) {
     if (!h || !p) { set_error("NULL argument"); return QSIM_EINVAL; }
     set_error("%s", "");
+    if (p->dry) { set_error("plan was created as a dry run"); return QSIM_EINVAL; }
     if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
     if (first < 0 || count < 0 || first + count > (int64_t)p->ops.size()) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
     return enqueue_ops(h, p, (size_t)first, (size_t)count);
@@ -757,6 +767,7 @@ int qsim_plan_execute_range(qsim_h h, qsim_plan_h p, int64_t first, int64_t coun
 
 int qsim_plan_destroy(qsim_plan_h p) {
     if (!p) return QSIM_OK;
+    if (p->dry) { delete p; return QSIM_OK; }
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     cudaFree(p->dbuf);

@@ -41,7 +41,7 @@ class Circuit(ctypes.Structure):
 class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("dry_run", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PassInfo(ctypes.Structure):
@@ -306,14 +306,16 @@ class Plan:
 
     def __init__(self, circuit, dtype: int = C64, mode: int = RUN_PLAIN, max_fused: int = 5,
                  precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None,
-                 local_qubits: int = 0):
+                 local_qubits: int = 0, dry_run: bool = False):
+        """dry_run: plan on the host only (no device needed); the plan lists its passes but cannot run."""
         self.args = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
-                    use_graph=1 if use_graph else 0, local_qubits=local_qubits)
+                    use_graph=1 if use_graph else 0, local_qubits=local_qubits, dry_run=1 if dry_run else 0)
         info = PlanInfo()
         p = ctypes.c_void_p()
         _check(lib().qsim_plan_create(ctypes.byref(self.args.c), dtype, ctypes.byref(o),
-                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(p), ctypes.byref(info)))
+                                      ctypes.c_void_p(0 if dry_run else _stream_ptr(stream)), ctypes.byref(p),
+                                      ctypes.byref(info)))
         self.p = p
         self.info = info.as_dict()
 

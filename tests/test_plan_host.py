@@ -1,0 +1,134 @@
+"""The fusion planner (host C++) without a GPU: plans made with dry_run list their passes, so their structure
+is checked here. Every plan keeps every input gate exactly once, each pass's qubits are valid, and the
+benchmarked circuits get the pass structure the kernels are built around (tensor-core blocks of 6 qubits,
+phase passes or epilogues for runs of diagonal gates)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+TC6 = dict(mode=1, max_fused=6, precision=1, tc_min_k=5)
+
+
+@pytest.fixture(scope="module")
+def qsim():
+    from paper_2511_14664_gb300 import qsim as q
+    q.lib()  # builds and loads the library (no device needed for dry runs)
+    return q
+
+
+def plan(qsim, c, dtype=0, **kw):
+    p = qsim.Plan(c, dtype, dry_run=True, **kw)
+    ps = p.passes()
+    assert sum(q["gates"] for q in ps) == len(c)
+    for q in ps:
+        qubits = q["targets"] + q["controls"]
+        assert len(set(qubits)) == len(qubits) and all(0 <= x < c.n for x in qubits)
+    return p, ps
+
+
+def test_plain_plan_is_one_pass_per_gate(qsim):
+    c = W.qft(12)
+    p, ps = plan(qsim, c, mode=0, max_fused=1)
+    assert len(ps) == len(c)
+    for q, g in zip(ps, c.gates):
+        diag = np.allclose(g.matrix, np.diag(np.diag(g.matrix)))
+        assert q["kind"] == ("diag" if diag else "dense_small")
+        assert q["gates"] == 1
+
+
+def test_brickwork_30q_tensor_core_blocks(qsim):
+    """The benchmark's 30-qubit brickwork: every pass a 6-qubit tensor-core block, each moving the whole state
+    once (the last one carries the final CZ layer in its epilogue; a 4-qubit block is padded to 6)."""
+    c = W.brickwork(30, 40, seed=3)
+    p, ps = plan(qsim, c, **TC6)
+    assert all(q["kind"] == "tc" and q["k"] == 6 for q in ps)
+    assert len(ps) <= 64
+    full = 2 * 8 * 2.0 ** 30
+    assert all(q["algorithmic_bytes"] == full for q in ps)
+    assert p.info["algorithmic_bytes"] == full * len(ps)
+
+
+def test_qft_phases_fold_into_blocks(qsim):
+    """28-qubit QFT: the controlled phases that link a block to lower qubits ride on the block's epilogue;
+    no separate phase or diagonal pass remains."""
+    c = W.qft(28)
+    p, ps = plan(qsim, c, **TC6)
+    assert all(q["kind"] == "tc" for q in ps)
+    assert len(ps) <= 9
+    # without tensor cores the phases need passes of their own
+    p2, ps2 = plan(qsim, c, mode=1, max_fused=6)
+    assert any(q["kind"] == "phase" for q in ps2) and len(ps2) > len(ps)
+
+
+def test_qpe_33q_passes(qsim):
+    c, _ = W.qpe(32, W.basis_index(32, 7))
+    p, ps = plan(qsim, c, **TC6)
+    assert len(ps) <= 18 and all(q["kind"] == "tc" for q in ps)
+
+
+def test_lattice_tfim_one_phase_per_step(qsim):
+    """The 33-site triangular lattice: the 99 RZZ gates of a Trotter step gather in one phase pass (or an
+    epilogue); the RX layers go to 6-qubit blocks."""
+    c = W.tfim_lattice(11, 3, 10, 0.27, 0.74)
+    p, ps = plan(qsim, c, **TC6)
+    assert len(ps) <= 63
+    assert sum(1 for q in ps if q["kind"] == "phase") <= 10
+
+
+def test_phase_pass_any_width(qsim):
+    """A run of diagonal gates on 20 qubits after CUDA-core blocks: one phase pass (no epilogue without
+    tensor cores) carrying those the dense blocks did not take in (a gate whose qubits both lie in a
+    block's window may join that block)."""
+    rng = np.random.default_rng(1)
+    n = 20
+    c = W.Circuit(n)
+    for q in range(n):
+        c.append(W.Gate((q,), (), W.haar_unitary(2, rng), "u"))
+    diag = 0
+    for _ in range(40):
+        a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+        c.append(W.Gate((a, b), (), W.RZZ(float(rng.uniform(0, math.pi))), "rzz"))
+        diag += 1
+    p, ps = plan(qsim, c, mode=1, max_fused=4)
+    phases = [q for q in ps if q["kind"] == "phase"]
+    assert len(phases) == 1 and phases[0]["gates"] >= diag // 2 and phases[0]["k"] == 0
+    assert phases[0]["algorithmic_bytes"] == 2 * 8 * 2.0 ** n
+
+
+def test_four_qubit_block_padded_for_tensor_cores(qsim):
+    n = 16
+    rng = np.random.default_rng(2)
+    c = W.Circuit(n)
+    for _ in range(3):
+        for q in (3, 4, 5, 6):
+            c.append(W.Gate((q,), (), W.haar_unitary(2, rng), "u"))
+        c.append(W.Gate((3, 4), (), W.haar_unitary(4, rng), "u4"))
+        c.append(W.Gate((5, 6), (), W.haar_unitary(4, rng), "u4"))
+    p, ps = plan(qsim, c, **TC6)
+    assert len(ps) == 1 and ps[0]["kind"] == "tc" and ps[0]["k"] == 6
+    assert set(ps[0]["targets"]) == {3, 4, 5, 6, 14, 15}
+    p2, ps2 = plan(qsim, c, mode=1, max_fused=6)  # CUDA cores: stays a 4-qubit pass
+    assert len(ps2) == 1 and ps2[0]["kind"] == "dense_small" and ps2[0]["k"] == 4
+
+
+def test_global_qubits_plan(qsim):
+    """local_qubits: before a pass touches a global qubit a reorder brings it in; every non-reorder pass
+    then works on local positions only, and diagonal runs stay within the fusion width."""
+    n, L = 24, 20
+    c = W.random_pairs(n, 4, seed=5)
+    p, ps = plan(qsim, c, mode=1, max_fused=4, local_qubits=L)
+    assert any(q["kind"] == "reorder" for q in ps)
+    for q in ps:
+        if q["kind"] != "reorder":
+            assert all(x < L for x in q["targets"] + q["controls"])
+        assert q["kind"] != "phase"
+
+
+def test_dry_run_needs_no_device_and_reports_info(qsim):
+    c = W.brickwork(14, 6, seed=1)
+    p, ps = plan(qsim, c, 1, mode=1, max_fused=4)
+    assert p.info["passes"] == len(ps) and p.info["input_gates"] == len(c)
+    assert p.info["host_plan_ms"] >= 0.0
