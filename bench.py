@@ -233,8 +233,7 @@ def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
                 evs[i + 1].record(stream)
         else:
             plan.execute(st)
-        st.expect_z()
-        st.sample(1000 + s, shots)
+        st.expect_z_and_sample(1000 + s, shots)   # <Z_i>, <Z_i Z_i+1> and the shots, one read of the state
         if per_pass:
             torch.cuda.synchronize()
             for i in range(npass):
@@ -453,8 +452,7 @@ def run_ours(args):
         p = make_plan(qsim, circuit, main)   # host gate list -> device (planning, upload, FP64 composition)
         st.set_basis(0)
         p.execute(st)
-        zi, zz = st.expect_z()
-        smp = st.sample(5000 + s, shots)     # device -> host
+        zi, zz, smp = st.expect_z_and_sample(5000 + s, shots)     # device -> host
         p.close()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t) / e2e_steps

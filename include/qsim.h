@@ -252,6 +252,13 @@ int qsim_expect_z(qsim_h h, double* zi, double* zz);
 int qsim_sample(qsim_h h, uint64_t seed, int64_t shots, uint64_t* out);
 /* Same with caller-supplied uniforms u[0..shots) in [0, 1) (host). */
 int qsim_sample_uniforms(qsim_h h, const double* u, int64_t shots, uint64_t* out);
+/*
+ * qsim_expect_z followed by qsim_sample (same outputs, same seed convention) with one read of the state:
+ * the <Z> pass also leaves the probability of every segment of 1024 amplitudes, and the sampler searches
+ * those instead of summing the state again (Sec. 2.1: sampling and expectation values are the readouts of
+ * a run). Samples equal qsim_sample's up to rounding at segment boundaries. Synchronises.
+ */
+int qsim_expect_z_and_sample(qsim_h h, double* zi, double* zz, uint64_t seed, int64_t shots, uint64_t* out);
 
 /*
  * Sampling for callers that cannot allocate device memory (the paper has no counterpart; this is a library

@@ -353,7 +353,8 @@ int qsim_expect_z(qsim_h h, double* zi, double* zz) {
     return check_device_error(h);
 }
 
-static int sample_common(qsim_h h, int64_t shots, uint64_t* out, const double* u_host, uint64_t seed) {
+static int sample_common(qsim_h h, int64_t shots, uint64_t* out, const double* u_host, uint64_t seed,
+                         int seg_ready_bits = 0) {
     if (!out) { set_error("NULL output"); return QSIM_EINVAL; }
     if (shots < 0 || shots > (1ll << 31)) { set_error("shots outside 0..2^31"); return QSIM_EINVAL; }
     if (shots == 0) return QSIM_OK;
@@ -374,7 +375,8 @@ static int sample_common(qsim_h h, int64_t shots, uint64_t* out, const double* u
     cudaError_t e;
     if (u_host) e = cudaMemcpyAsync(h->du, u_host, sizeof(double) * shots, cudaMemcpyHostToDevice, h->stream);
     else e = launch_uniforms(seed, shots, h->du, h->stream);
-    if (e == cudaSuccess) e = run_sample(h->dtype, h->psi, h->n, h->du, shots, h->dsamples, h->red, h->stream, h->dev);
+    if (e == cudaSuccess)
+        e = run_sample(h->dtype, h->psi, h->n, h->du, shots, h->dsamples, h->red, h->stream, h->dev, seg_ready_bits);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->dsamples, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "sample");
@@ -384,6 +386,18 @@ static int sample_common(qsim_h h, int64_t shots, uint64_t* out, const double* u
 int qsim_sample(qsim_h h, uint64_t seed, int64_t shots, uint64_t* out) {
     QSIM_CHECK_HANDLE(h);
     return sample_common(h, shots, out, nullptr, seed);
+}
+
+int qsim_expect_z_and_sample(qsim_h h, double* zi, double* zz, uint64_t seed, int64_t shots, uint64_t* out) {
+    QSIM_CHECK_HANDLE(h);
+    if (!zi || (!zz && h->n > 1) || (!out && shots > 0)) { set_error("NULL output"); return QSIM_EINVAL; }
+    if (shots < 0 || shots > (1ll << 31)) { set_error("shots outside 0..2^31"); return QSIM_EINVAL; }
+    std::vector<double> zz_dummy(1);
+    cudaError_t e = run_zstats(h->dtype, h->psi, h->n, h->red, h->stream, h->dev, zi, zz ? zz : zz_dummy.data());
+    if (e != cudaSuccess) return cuda_fail(e, "expect_z_and_sample");
+    const int rc = check_device_error(h);
+    if (rc) return rc;
+    return sample_common(h, shots, out, nullptr, seed, zstats_segment_bits(h->n));
 }
 
 int qsim_sample_uniforms(qsim_h h, const double* u, int64_t shots, uint64_t* out) {

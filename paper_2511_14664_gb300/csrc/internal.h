@@ -136,7 +136,10 @@ cudaError_t run_inner(int dtype, const void* a, const void* b, int n, ReduceScra
                       const DevInfo& d, double* out);
 // Samples: u_dev (device, shots doubles) -> out_dev (device, shots uint64).
 cudaError_t run_sample(int dtype, const void* psi, int n, const double* u_dev, int64_t shots, uint64_t* out_dev,
-                       ReduceScratch& r, cudaStream_t s, const DevInfo& d);
+                       ReduceScratch& r, cudaStream_t s, const DevInfo& d,
+                       int seg_ready_bits = 0);
+// Bits of the segments whose sums run_zstats leaves in r.seg (0: none).
+int zstats_segment_bits(int n);
 cudaError_t launch_uniforms(uint64_t seed, int64_t count, double* out_dev, cudaStream_t s);
 
 }  // namespace qsim

@@ -848,6 +848,8 @@ cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int 
     return run_probs_warp(dtype, psi, n, qubits, nq, r, s, d, out);
 }
 
+int zstats_segment_bits(int n) { return n < kSegBits ? 0 : 10; }
+
 cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
                        double* zi, double* zz) {
     cudaError_t e;
@@ -888,15 +890,19 @@ cudaError_t launch_uniforms(uint64_t seed, int64_t count, double* out_dev, cudaS
 }
 
 cudaError_t run_sample(int dtype, const void* psi, int n, const double* u_dev, int64_t shots, uint64_t* out_dev,
-                       ReduceScratch& r, cudaStream_t s, const DevInfo& d) {
-    const int SB = std::min(n, kSegBits);
+                       ReduceScratch& r, cudaStream_t s, const DevInfo& d, int seg_ready_bits) {
+    // seg_ready_bits > 0: r.seg already holds the sums of segments of 2^seg_ready_bits amplitudes (from the
+    // <Z> pass), so the state is read again only inside the sampled segments
+    const int SB = seg_ready_bits > 0 ? seg_ready_bits : std::min(n, kSegBits);
     const uint64_t nseg = 1ull << (n - SB);
     const int nchunk = (int)((nseg + 1023) / 1024);
     double* W = r.seg;
     double* C = r.scan;
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)((nseg + 7) / 8)));
-    if (dtype == QSIM_C64) k_segsum<float><<<nb, 256, 0, s>>>((const float2*)psi, SB, nseg, W);
-    else k_segsum<double><<<nb, 256, 0, s>>>((const double2*)psi, SB, nseg, W);
+    if (seg_ready_bits <= 0) {
+        if (dtype == QSIM_C64) k_segsum<float><<<nb, 256, 0, s>>>((const float2*)psi, SB, nseg, W);
+        else k_segsum<double><<<nb, 256, 0, s>>>((const double2*)psi, SB, nseg, W);
+    }
     k_chunksum<<<nchunk, 256, 0, s>>>(W, nseg, C);
     k_scan_small<<<1, 1024, 0, s>>>(C, nchunk);
     const int sb = (int)std::max<int64_t>(1, std::min<int64_t>((shots * 32 + 255) / 256, (int64_t)d.num_sms * 8));

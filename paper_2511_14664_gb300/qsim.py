@@ -94,6 +94,7 @@ SIGNATURES = {
     "qsim_expect_z": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
     "qsim_sample": ([_vp, _u64, _i64, _P(_u64)], _i),
     "qsim_sample_uniforms": ([_vp, _P(ctypes.c_double), _i64, _P(_u64)], _i),
+    "qsim_expect_z_and_sample": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _u64, _i64, _P(_u64)], _i),
     "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
     "qsim_sample_noalloc": ([_vp, _i, _i, _u64, _i64, _vp, _vp], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
@@ -266,6 +267,15 @@ class State:
         _check(lib().qsim_sample(self.h, seed & (2**64 - 1), shots,
                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
         return out
+
+    def expect_z_and_sample(self, seed: int, shots: int):
+        """(<Z_i>, <Z_i Z_i+1>, samples) with one read of the state."""
+        zi = np.zeros(self.n)
+        zz = np.zeros(max(1, self.n - 1))
+        out = np.zeros(max(1, shots), dtype=np.uint64)
+        _check(lib().qsim_expect_z_and_sample(self.h, _dptr(zi), _dptr(zz), seed & (2**64 - 1), shots,
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return zi, zz[: max(0, self.n - 1)], out[:shots]
 
     def sample_uniforms(self, u: np.ndarray) -> np.ndarray:
         u = np.ascontiguousarray(u, dtype=np.float64)

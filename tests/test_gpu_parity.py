@@ -392,6 +392,22 @@ def test_sampling_matches_oracle(qsim, dtype, n):
     assert np.array_equal(got2, exp)
 
 
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [9, 12, 17, 21])
+def test_expect_z_and_sample_one_pass(qsim, dtype, n):
+    """The combined readout equals the separate calls: <Z> exactly, and the shots are the oracle's inverse
+    CDF on the GPU's own state with the same uniforms (segment sums from the <Z> pass)."""
+    c = W.brickwork(n, 6, seed=n)
+    st = make_state(qsim, n, dtype)
+    st.run(c, mode=1, max_fused=4)
+    zi, zz, smp = st.expect_z_and_sample(17, 700)
+    zi2, zz2 = st.expect_z()
+    assert np.array_equal(zi, zi2) and np.array_equal(zz, zz2)
+    psi = np.ascontiguousarray(st.get_state().astype(np.complex128))
+    assert np.array_equal(smp, oracle.sample(psi, n, oracle.uniforms(17, 700)))
+    assert np.array_equal(st.sample(17, 700), smp)
+
+
 def test_inner_product(qsim):
     n = 15
     a, b = random_state(n, 1), random_state(n, 2)
