@@ -188,6 +188,11 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                      qsim_plan_h* out, qsim_plan_info* info);
 /* Enqueue every pass of the plan on h's stream. Asynchronous. */
 int qsim_plan_execute(qsim_h h, qsim_plan_h plan);
+/* qsim_set_basis(h, x) then passes [0, count) of the plan (count < 0: all of them), on h's stream (no
+   graph). When the plan starts with a tensor-core block (3xTF32 or BF16x3) that block generates |x> as its
+   input instead of reading the state, and writes every amplitude, so neither the set-up pass nor the
+   block's reads happen. QSIM_EINVAL for x >= 2^n or count > the number of passes. */
+int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h plan, uint64_t x, int64_t count);
 int qsim_plan_destroy(qsim_plan_h plan);
 
 /* One pass of a plan, for per-kernel timing and roofline accounting. */
@@ -208,6 +213,9 @@ typedef struct {
     int32_t targets[QSIM_MAX_TARGETS];   /* index bits the matrix acts on, in the order of its index bits
                                             (k of them; k = 0 for a reorder or phase pass) */
     int32_t controls[QSIM_MAX_CONTROLS]; /* control bits (nc of them) */
+    int32_t launches;         /* kernel launches one execution of the pass makes (2 for a tensor-core block
+                                 with a phase epilogue: a small kernel computes its per-tile factors first) */
+    int32_t reserved;
 } qsim_pass_info;
 int qsim_plan_num_passes(qsim_plan_h plan, int64_t* out);
 int qsim_plan_pass_info(qsim_plan_h plan, int64_t i, qsim_pass_info* out);

@@ -91,9 +91,12 @@ size_t tc_operand_bytes(int k, int precision);
 cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s,
                               const double* rowphase = nullptr);
 // Apply the prepared block to a complex64 state. dev_err receives DEVERR_* bits on a bounded-wait expiry.
+// With from_basis the block's input is the basis state |*from_basis>, generated instead of read (the block
+// writes the whole state).
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
                             unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab = nullptr,
-                            const TcEpiPacked* epi = nullptr, void* epi_scratch = nullptr);
+                            const TcEpiPacked* epi = nullptr, void* epi_scratch = nullptr,
+                            const uint64_t* from_basis = nullptr);
 bool tc_supported(int k, int precision);
 
 // ---- fused-block composition (k_compose.cu) -------------------------------------------------------------------

@@ -195,6 +195,10 @@ struct Args {
                                           // of each row bit, H and each V bit given the tile's bits
     const float2* epi_thr;                // [2][128][6]: per (half, row): row / H-only terms, then each V bit's
                                           // factor given the row and H bits
+    // from_basis: the input is the basis state |basis> (amplitude 1 there, 0 elsewhere), generated in
+    // registers instead of read; the block writes every amplitude, so the state needs no prior set-up.
+    int from_basis;
+    uint64_t basis;
 };
 
 // Warp-specialised block kernel, all precisions: warps 0..7 move data (tile loads, split into the A planes
@@ -351,6 +355,11 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
         auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+            if (a.from_basis) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) X[j] = make_float2(b + vCol[j] == a.basis ? 1.0f : 0.0f, 0.0f);
+                return;
+            }
             if constexpr (Q0) {
 #pragma unroll
                 for (int j = 0; j < CPT; j += 4) {
@@ -907,7 +916,7 @@ __global__ void k_tc_epi_tiles(uint64_t ntiles, tc::Args a, TcEpiPacked pk, cons
 
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
                             unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab,
-                            const TcEpiPacked* epi, void* epi_scratch) {
+                            const TcEpiPacked* epi, void* epi_scratch, const uint64_t* from_basis) {
     if (!tc_supported(k, precision) || n < k + tc::kRowBits) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
     if (epi && (!epi_tab || !epi_scratch || precision == QSIM_PREC_BF16X6)) return cudaErrorInvalidValue;
@@ -924,6 +933,11 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
     for (int q = 0; q < n; ++q)
         if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
+    if (from_basis) {
+        if (precision == QSIM_PREC_BF16X6) return cudaErrorInvalidValue;  // the 16-warp kernel always reads
+        a.from_basis = 1;
+        a.basis = *from_basis;
+    }
     if (epi) {
         // the tile factors go to the scratch (tc_epi_scratch_bytes), read by the block kernel that follows
         const unsigned char* b = static_cast<const unsigned char*>(epi_tab);

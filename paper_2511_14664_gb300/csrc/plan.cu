@@ -171,11 +171,13 @@ static double op_bytes(const PlanOp& op, int n, size_t amp) {
     return 2.0 * amp * groups * (double)(1 << op.k);
 }
 
-static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size_t count = (size_t)-1) {
+static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size_t count = (size_t)-1,
+                       const uint64_t* first_from_basis = nullptr) {
     cudaError_t e = cudaSuccess;
     const size_t last = std::min(p->ops.size(), count == (size_t)-1 ? p->ops.size() : first + count);
     for (size_t oi = first; oi < last; ++oi) {
         const PlanOp& op = p->ops[oi];
+        const uint64_t* fb = oi == first ? first_from_basis : nullptr;
         switch (op.kind) {
             case OP_DENSE_SMALL:
                 e = launch_dense_small(h->dtype, h->psi, h->n, op.k, op.targets, op.nc, op.controls, op.mat.data(),
@@ -194,7 +196,8 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                                     op.precision, h->derr, h->stream, h->dev,
                                     op.has_epi ? static_cast<char*>(p->dbuf) + op.epi_off : nullptr,
                                     op.has_epi ? &op.epi : nullptr,
-                                    op.has_epi ? static_cast<char*>(p->dbuf) + p->extra.epi_scratch_off : nullptr);
+                                    op.has_epi ? static_cast<char*>(p->dbuf) + p->extra.epi_scratch_off : nullptr,
+                                    fb);
                 break;
             case OP_MERGED:
                 break;
@@ -753,6 +756,8 @@ int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
     std::memset(out->controls, 0, sizeof(out->controls));
     for (int j = 0; j < op.k && j < QSIM_MAX_TARGETS; ++j) out->targets[j] = op.targets[j];
     for (int j = 0; j < op.nc && j < QSIM_MAX_CONTROLS; ++j) out->controls[j] = op.controls[j];
+    out->launches = op.kind == OP_TC && op.has_epi ? 2 : 1;
+    out->reserved = 0;
     return QSIM_OK;
 }
 
@@ -763,6 +768,23 @@ int qsim_plan_execute_range(qsim_h h, qsim_plan_h p, int64_t first, int64_t coun
     if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
     if (first < 0 || count < 0 || first + count > (int64_t)p->ops.size()) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
     return enqueue_ops(h, p, (size_t)first, (size_t)count);
+}
+
+int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h p, uint64_t x, int64_t count) {
+    if (!h || !p) { set_error("NULL argument"); return QSIM_EINVAL; }
+    set_error("%s", "");
+    if (p->dry) { set_error("plan was created as a dry run"); return QSIM_EINVAL; }
+    if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
+    if (h->n < 64 && (x >> h->n) != 0) { set_error("basis index out of range"); return QSIM_EINVAL; }
+    const int64_t nops = (int64_t)p->ops.size();
+    if (count < 0) count = nops;
+    if (count > nops) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
+    // a first tensor-core block (3xTF32 / BF16x3) generates |x> as its input and writes every amplitude
+    if (count > 0 && p->ops[0].kind == OP_TC && p->ops[0].precision != QSIM_PREC_BF16X6)
+        return enqueue_ops(h, p, 0, (size_t)count, &x);
+    const int rc = qsim_set_basis(h, x);
+    if (rc) return rc;
+    return enqueue_ops(h, p, 0, (size_t)count);
 }
 
 int qsim_plan_destroy(qsim_plan_h p) {

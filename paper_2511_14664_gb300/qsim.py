@@ -47,7 +47,8 @@ class RunOpts(ctypes.Structure):
 class PassInfo(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32), ("nc", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("gates", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_double),
-                ("targets", ctypes.c_int32 * 8), ("controls", ctypes.c_int32 * 8)]
+                ("targets", ctypes.c_int32 * 8), ("controls", ctypes.c_int32 * 8),
+                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder", 5: "phase"}
@@ -86,6 +87,7 @@ SIGNATURES = {
     "qsim_plan_destroy": ([_vp], _i),
     "qsim_plan_num_passes": ([_vp, _P(_i64)], _i),
     "qsim_plan_pass_info": ([_vp, _i64, _P(PassInfo)], _i),
+    "qsim_plan_execute_from_basis": ([_vp, _vp, _u64, _i64], _i),
     "qsim_plan_execute_range": ([_vp, _vp, _i64, _i64], _i),
     "qsim_run": ([_vp, _P(Circuit), _P(RunOpts), _P(PlanInfo)], _i),
     "qsim_norm": ([_vp, _P(ctypes.c_double)], _i),
@@ -332,6 +334,11 @@ class Plan:
     def execute(self, state: State):
         _check(lib().qsim_plan_execute(state.h, self.p))
 
+    def execute_from_basis(self, state: State, x: int = 0, count: int = -1):
+        """set_basis(x), then passes [0, count) (all for count < 0); a first tensor-core block generates |x>
+        itself instead of reading it."""
+        _check(lib().qsim_plan_execute_from_basis(state.h, self.p, int(x), int(count)))
+
     def execute_range(self, state: State, first: int, count: int):
         _check(lib().qsim_plan_execute_range(state.h, self.p, int(first), int(count)))
 
@@ -345,7 +352,8 @@ class Plan:
             _check(lib().qsim_plan_pass_info(self.p, i, ctypes.byref(pi)))
             out.append({"kind": PASS_KINDS[pi.kind], "k": pi.k, "nc": pi.nc, "precision": pi.precision,
                         "gates": pi.gates, "algorithmic_bytes": pi.algorithmic_bytes,
-                        "targets": list(pi.targets[:pi.k]), "controls": list(pi.controls[:pi.nc])})
+                        "targets": list(pi.targets[:pi.k]), "controls": list(pi.controls[:pi.nc]),
+                        "launches": pi.launches})
         return out
 
     def close(self):
