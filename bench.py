@@ -211,9 +211,9 @@ def make_plan(qsim, circuit, path, use_graph=False):
 
 def count_readout_launches(n):
     """Kernels of one expect_z_and_sample call: <Z> statistics (one kernel below 12 qubits; else warp
-    segments, final sum, high-bit pairs), then uniforms, segment sums (left by the <Z> pass from 12 qubits
-    on), chunk sums, scan, sample."""
-    return 1 + 5 if n < 12 else 3 + 4
+    segments, their final sum, high-bit partials, their final sum), then uniforms, segment sums (left by the
+    <Z> pass from 12 qubits on), chunk sums, scan, sample."""
+    return 1 + 5 if n < 12 else 4 + 4
 
 
 def count_step_launches(plan, n):

@@ -290,8 +290,11 @@ int qsim_apply_fused(qsim_h h, const int* targets, int k, const double* matrix, 
     const size_t cnt = (size_t)2 << (2 * k);
     cudaError_t e = cudaMemcpyAsync(h->dmat64, matrix, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess) e = launch_tc_prepare(h->dmat64, k, precision, h->dmat, h->stream);
-    if (e == cudaSuccess) e = launch_tc_apply(h->psi, h->n, k, targets, h->dmat, precision, h->derr, h->stream, h->dev);
+    const bool lines = tc_line_groups(k, targets, precision, false);
+    if (e == cudaSuccess) e = launch_tc_prepare(h->dmat64, k, precision, lines, h->dmat, h->stream);
+    if (e == cudaSuccess)
+        e = launch_tc_apply(h->psi, h->n, k, targets, h->dmat, precision, h->derr, h->stream, h->dev, nullptr, nullptr,
+                            nullptr, nullptr, lines);
     return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "tensor-core block");
 }
 

@@ -87,16 +87,23 @@ void tc_epi_pack(int n, int k, const int* targets, const PhaseForm& f, std::vect
 size_t tc_epi_scratch_bytes(int n, int k);
 // Bytes of the prepared B operand for a k-qubit block at `precision`.
 size_t tc_operand_bytes(int k, int precision);
-// Build the B operand (tensor-core layout) from a device FP64 matrix U (2^k x 2^k complex).
-cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s,
+// Build the B operand (tensor-core layout) from a device FP64 matrix U (2^k x 2^k complex) for a block on
+// `targets` (their order decides the data path, and with it the column order of B).
+// cudaErrorInvalidValue for an unsupported k or precision, or `lines` with a precision or epilogue that has
+// no line-group path.
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, bool lines, void* dB, cudaStream_t s,
                               const double* rowphase = nullptr);
+// True when a block on `targets` may run the line-group data path (qubits 0..3 are targets 0..3, 3xTF32, no
+// phase epilogue). The operand must then be prepared with lines = true and applied with lines = true.
+bool tc_line_groups(int k, const int* targets, int precision, bool epi);
 // Apply the prepared block to a complex64 state. dev_err receives DEVERR_* bits on a bounded-wait expiry.
 // With from_basis the block's input is the basis state |*from_basis>, generated instead of read (the block
-// writes the whole state).
+// writes the whole state). lines: the operand was prepared for the line-group path (tc_line_groups must hold
+// for these targets, else cudaErrorInvalidValue).
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
                             unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab = nullptr,
                             const TcEpiPacked* epi = nullptr, void* epi_scratch = nullptr,
-                            const uint64_t* from_basis = nullptr);
+                            const uint64_t* from_basis = nullptr, bool lines = false);
 bool tc_supported(int k, int precision);
 
 // ---- fused-block composition (k_compose.cu) -------------------------------------------------------------------

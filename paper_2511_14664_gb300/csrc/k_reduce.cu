@@ -481,14 +481,17 @@ __global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* _
     }
 }
 
-// Quantities of bits >= B from the segment totals W (one CTA per quantity; nh = n - B):
+// Quantities of bits >= B from the segment totals W (nh = n - B), as partial sums: CTA (p, q) takes the p-th of
+// gridDim.x equal contiguous ranges of segments and quantity q:
 //   q < nh: S_{B+q} = sum_s W[s] bit_q(s);   nh <= q < 2 nh - 1: X_{B+r}, r = q - nh (bits r, r+1 of s).
+// The partial goes to partials[q * gridDim.x + p] (hi, lo), for k_final_dd.
 __global__ void __launch_bounds__(256) k_zstats_hi(const double* __restrict__ W, uint64_t nseg, int nh,
-                                                   double* __restrict__ out) {
+                                                   double* __restrict__ partials) {
     __shared__ dd sm[32];
-    const int q = blockIdx.x;
+    const int q = blockIdx.y;
+    const uint64_t len = nseg / gridDim.x, s0 = (uint64_t)blockIdx.x * len;
     ff acc = {0.f, 0.f};
-    for (uint64_t s = threadIdx.x; s < nseg; s += blockDim.x) {
+    for (uint64_t s = s0 + threadIdx.x; s < s0 + len; s += blockDim.x) {
         bool use;
         if (q < nh) use = (s >> q) & 1;
         else { const int r = q - nh; use = ((s >> r) ^ (s >> (r + 1))) & 1; }
@@ -500,8 +503,9 @@ __global__ void __launch_bounds__(256) k_zstats_hi(const double* __restrict__ W,
     }
     const dd v = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
     if (threadIdx.x == 0) {
-        out[2 * q] = v.hi;
-        out[2 * q + 1] = v.lo;
+        double* o = partials + 2 * ((int64_t)q * gridDim.x + blockIdx.x);
+        o[0] = v.hi;
+        o[1] = v.lo;
     }
 }
 
@@ -872,7 +876,12 @@ cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cuda
     else k_zstats_warp<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, r.partials);
     k_final_dd<<<kZW, 256, 0, s>>>(r.partials, nb, r.result);
     const int nh = n - 10;
-    if (nh > 0) k_zstats_hi<<<2 * nh - 1, 256, 0, s>>>(W, nseg, nh, r.result + 2 * kZW);
+    if (nh > 0) {
+        // after k_final_dd above has consumed the warp partials (same stream), the buffer takes the high bits'
+        const unsigned P = (unsigned)std::min<uint64_t>(32, nseg);
+        k_zstats_hi<<<dim3(P, 2 * nh - 1), 256, 0, s>>>(W, nseg, nh, r.partials);
+        k_final_dd<<<2 * nh - 1, 256, 0, s>>>(r.partials, (int)P, r.result + 2 * kZW);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = fetch(r, 2 * kZW + 2 * (2 * nh - 1), s)) != cudaSuccess) return e;
     const double* h = r.hresult;

@@ -20,8 +20,11 @@
 //   one plane overlaps the MMAs on another, and two TMEM accumulators let the epilogue of tile t-1 overlap
 //   the MMAs of tile t. A thread owns one row of a tile (its TMEM lane); how its amplitudes move (Mode):
 //   8-byte accesses, 16-byte pairs when qubit 0 is the first target, 32-byte quads (whole sectors) when
-//   qubits 0 and 1 are the first two. With a phase epilogue (EPI) every output amplitude is multiplied by
-//   unit complex factors of its tile, row and column bits before it is stored.
+//   qubits 0 and 1 are the first two. When qubits 0..3 are the first four targets (3xTF32) four threads
+//   share a row instead (line groups): each moves 32 bytes of the row's 128-byte line, and the tile goes to
+//   and from TMEM in 16x256b fragments with B's columns permuted to match. With a phase epilogue (EPI)
+//   every output amplitude is multiplied by unit complex factors of its tile, row and column bits before it
+//   is stored.
 //   BF16x6 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
 #include <cuda_bf16.h>
 
@@ -199,6 +202,7 @@ struct Args {
     // registers instead of read; the block writes every amplitude, so the state needs no prior set-up.
     int from_basis;
     uint64_t basis;
+    int lines;                            // host side: run the line-group data path
 };
 
 // Warp-specialised block kernel, all precisions: warps 0..7 move data (tile loads, split into the A planes
@@ -215,7 +219,31 @@ enum Mode {
     kPairsInLanes = 1,  // qubit 0 is target 0: columns 2i, 2i+1 move as one 16-byte vector
     kQuadsInLanes = 2,  // qubits 0 and 1 are targets 0 and 1: columns 4i..4i+3 move as one 32-byte vector, so
                         // each lane reads and writes whole 32-byte sectors
+    kLineGroups = 3,    // qubits 0..3 are targets 0..3 (3xTF32, no epilogue): four lanes share a row and move
+                        // its 16 adjacent amplitudes (one 128-byte line) with 32-byte accesses; the tile goes
+                        // to and from TMEM with the 16x256b shape, so a warp access touches 8 whole lines
+                        // instead of 32 partial ones
 };
+
+// kLineGroups column order: tile column slot s holds natural column index line_perm(s) (bits 0,1 and 2,3
+// swapped), so that the slots a thread owns in the 16x256b fragment (s = 4j + lane % 4) are 4 adjacent
+// amplitudes for j = 4m .. 4m + 3. The B operand is prepared in the same order.
+__host__ __device__ constexpr int line_perm(int s) { return (s & ~15) | ((s & 3) << 2) | ((s >> 2) & 3); }
+
+__device__ __forceinline__ void tmem_st_16x256b_x4(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15, %16};"
+                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                    "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                    "r"(v[15]) : "memory");
+}
+__device__ __forceinline__ void tmem_ld_16x256b_x4(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]) : "r"(taddr));
+}
 
 // 32-byte global accesses (sm_100 and later); the address must be 32-byte aligned.
 __device__ __forceinline__ void ld_v8(const float2* p, float2& a, float2& b, float2& c, float2& d) {
@@ -237,7 +265,7 @@ template <int K, int PREC, int MODE, bool EPI>
 __global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
-    constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes;
+    constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes, LG = MODE == kLineGroups;
     using C = Cfg<PREC>;
     constexpr bool BF16 = C::esize == 2;
     constexpr int P = C::planes;
@@ -256,6 +284,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                                ((uint32_t)(128 >> 4) << 24);
     static_assert(CPT % QC == 0 && CPT % QE == 0, "whole chunks per thread");
     static_assert(TCOLS <= 512, "TMEM holds two accumulators and every A plane");
+    static_assert(!LG || (!BF16 && !EPI && CPT % 16 == 0), "line groups: TF32 planes, no epilogue");
     constexpr int DEPTH = K >= 6 ? 1 : 2;                  // tiles of loads in flight (registers: CPT x 2 each)
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -271,7 +300,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
 
     // B planes -> shared memory (already in the swizzled byte layout), column offsets, barriers, TMEM.
     for (int i = tid; i < P * PB / 16; i += kThreadsWS) reinterpret_cast<uint4*>(sb)[i] = bops[i];
-    for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)(LG ? line_perm(c) : c), a.tpos, K);
     if (tid == 0) {
         for (int j = 0; j < 2 * P; ++j)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
@@ -345,7 +374,15 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     } else {
         // ---- data warps ----
         const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-        const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+        const uint64_t rowoff = LG ? 0 : deposit((uint64_t)r, a.rpos, kRowBits);
+        // LG: this thread's rows quad * 32 + 8 rho + lane / 4 (rho = 0..3) and its slot lane % 4 of each 4
+        [[maybe_unused]] uint64_t ro[4];
+        [[maybe_unused]] const int li = lane & 3;
+        if constexpr (LG) {
+#pragma unroll
+            for (int rho = 0; rho < 4; ++rho) ro[rho] = deposit((uint64_t)(quad * 32 + 8 * rho + (lane >> 2)), a.rpos, kRowBits);
+        }
+        constexpr int LPR = CPT / 4;  // LG: values per row in X (X[rho * LPR + j] is slot c0 + 4 j + lane % 4)
         // Column offsets are re-read from shared memory at each use (one broadcast load) instead of being
         // kept in 64-bit registers; the empty asm with a memory clobber between columns keeps the compiler
         // from batching those reads ahead of the accesses they address.
@@ -355,12 +392,25 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         // adjacent amplitudes and move as one 16-byte vector; otherwise lanes hold consecutive rows.
         auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-            if (a.from_basis) {
+            if constexpr (LG) {
+#pragma unroll
+                for (int rho = 0; rho < 4; ++rho)
+#pragma unroll
+                    for (int m = 0; m < CPT / 16; ++m) {
+                        float2* x = X + rho * LPR + 4 * m;
+                        const uint64_t o = b + ro[rho] + vCol[16 * m + li];  // 4 adjacent amplitudes from o
+                        if (a.from_basis) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) x[e] = make_float2(o + e == a.basis ? 1.0f : 0.0f, 0.0f);
+                        } else {
+                            ld_v8(psi + o, x[0], x[1], x[2], x[3]);
+                        }
+                        asm volatile("" ::: "memory");
+                    }
+            } else if (a.from_basis) {
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) X[j] = make_float2(b + vCol[j] == a.basis ? 1.0f : 0.0f, 0.0f);
-                return;
-            }
-            if constexpr (Q0) {
+            } else if constexpr (Q0) {
 #pragma unroll
                 for (int j = 0; j < CPT; j += 4) {
                     ld_v8(psi + b + vCol[j], X[j], X[j + 1], X[j + 2], X[j + 3]);
@@ -400,20 +450,40 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         };
         // Plane p of tile X into TMEM, then one arrival per warp on full[p].
         auto store_plane = [&](const float2 (&X)[CPT], int p) {
+            if constexpr (LG) {
+                // 16x256b: rows rho = 2 pr (TMEM lane quad * 32 + 16 pr + lane / 4) and 2 pr + 1 (8 lanes further);
+                // repetition j' of chunk m holds slot c0 + 16 m + 4 j' + lane % 4 (re, im) for both rows
 #pragma unroll
-            for (int h = 0; h < CPT / QC; ++h) {
-                uint32_t v[16];
+                for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-                for (int j = 0; j < QC; ++j) {
-                    const float2 x = X[h * QC + j];
-                    if constexpr (BF16) {
-                        v[j] = pack2(plane_of(x.x, p), plane_of(x.y, p));
-                    } else {
-                        v[2 * j] = plane_of(x.x, p);
-                        v[2 * j + 1] = plane_of(x.y, p);
+                    for (int m = 0; m < CPT / 16; ++m) {
+                        uint32_t v[16];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const float2 xe = X[(2 * pr) * LPR + 4 * m + jj], xo = X[(2 * pr + 1) * LPR + 4 * m + jj];
+                            v[4 * jj] = plane_of(xe.x, p);
+                            v[4 * jj + 1] = plane_of(xe.y, p);
+                            v[4 * jj + 2] = plane_of(xo.x, p);
+                            v[4 * jj + 3] = plane_of(xo.y, p);
+                        }
+                        tmem_st_16x256b_x4(tbase + tlane + ((uint32_t)(16 * pr) << 16) + A0 + p * ACOLS + 2 * (c0 + 16 * m), v);
                     }
+            } else {
+#pragma unroll
+                for (int h = 0; h < CPT / QC; ++h) {
+                    uint32_t v[16];
+#pragma unroll
+                    for (int j = 0; j < QC; ++j) {
+                        const float2 x = X[h * QC + j];
+                        if constexpr (BF16) {
+                            v[j] = pack2(plane_of(x.x, p), plane_of(x.y, p));
+                        } else {
+                            v[2 * j] = plane_of(x.x, p);
+                            v[2 * j + 1] = plane_of(x.y, p);
+                        }
+                    }
+                    tmem_st<16>(tbase + tlane + A0 + p * ACOLS + (BF16 ? 1 : 2) * (c0 + h * QC), v);
                 }
-                tmem_st<16>(tbase + tlane + A0 + p * ACOLS + (BF16 ? 1 : 2) * (c0 + h * QC), v);
             }
             wait_st();
             fence_before();
@@ -438,51 +508,69 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         };
         auto epilogue = [&](uint64_t t, uint32_t dcol) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-            [[maybe_unused]] float2 E[NV + 1];
-            if constexpr (EPI) epi_factors(t, E);
+            if constexpr (LG) {
 #pragma unroll
-            for (int h = 0; h < CPT / QE; ++h) {
-                uint32_t v[2 * QE];
-                tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
-                wait_ld();
-                if constexpr (EPI) {
-                    // factors of the chunk's 8 columns: column bits 0..2 vary inside it, bits 3.. are h
-                    float2 f[QE];
-                    f[0] = E[0];
+                for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
-                    for (int v2 = 3; v2 < NV; ++v2)
-                        if ((h >> (v2 - 3)) & 1) f[0] = cmul(f[0], E[1 + v2]);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e)
-#pragma unroll
-                        for (int q = 0; q < (1 << e); ++q) f[(1 << e) + q] = cmul(f[q], E[1 + e]);
-#pragma unroll
-                    for (int j = 0; j < QE; ++j) {
-                        const float2 x = cmul(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])), f[j]);
-                        v[2 * j] = __float_as_uint(x.x);
-                        v[2 * j + 1] = __float_as_uint(x.y);
-                    }
-                }
-                if constexpr (Q0) {
-#pragma unroll
-                    for (int j = 0; j < QE; j += 4) {
-                        st_v8(psi + b + vCol[h * QE + j], v + 2 * j);
+                    for (int m = 0; m < CPT / 16; ++m) {
+                        uint32_t v[16];
+                        tmem_ld_16x256b_x4(tbase + tlane + ((uint32_t)(16 * pr) << 16) + dcol + 2 * (c0 + 16 * m), v);
+                        wait_ld();
+                        const uint64_t o = b + vCol[16 * m + li];
+                        const uint32_t ve[8] = {v[0], v[1], v[4], v[5], v[8], v[9], v[12], v[13]};
+                        const uint32_t vo[8] = {v[2], v[3], v[6], v[7], v[10], v[11], v[14], v[15]};
+                        st_v8(psi + o + ro[2 * pr], ve);
+                        asm volatile("" ::: "memory");
+                        st_v8(psi + o + ro[2 * pr + 1], vo);
                         asm volatile("" ::: "memory");
                     }
-                } else if constexpr (P0) {
+            } else {
+                [[maybe_unused]] float2 E[NV + 1];
+                if constexpr (EPI) epi_factors(t, E);
 #pragma unroll
-                    for (int j = 0; j < QE; j += 2) {
-                        *reinterpret_cast<float4*>(psi + b + vCol[h * QE + j]) =
-                            make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
-                                        __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
-                        asm volatile("" ::: "memory");
+                for (int h = 0; h < CPT / QE; ++h) {
+                    uint32_t v[2 * QE];
+                    tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
+                    wait_ld();
+                    if constexpr (EPI) {
+                        // factors of the chunk's 8 columns: column bits 0..2 vary inside it, bits 3.. are h
+                        float2 f[QE];
+                        f[0] = E[0];
+#pragma unroll
+                        for (int v2 = 3; v2 < NV; ++v2)
+                            if ((h >> (v2 - 3)) & 1) f[0] = cmul(f[0], E[1 + v2]);
+#pragma unroll
+                        for (int e = 0; e < 3; ++e)
+#pragma unroll
+                            for (int q = 0; q < (1 << e); ++q) f[(1 << e) + q] = cmul(f[q], E[1 + e]);
+#pragma unroll
+                        for (int j = 0; j < QE; ++j) {
+                            const float2 x = cmul(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])), f[j]);
+                            v[2 * j] = __float_as_uint(x.x);
+                            v[2 * j + 1] = __float_as_uint(x.y);
+                        }
                     }
-                } else {
+                    if constexpr (Q0) {
 #pragma unroll
-                    for (int j = 0; j < QE; ++j) {
-                        psi[b + vCol[h * QE + j]] =
-                            make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-                        asm volatile("" ::: "memory");
+                        for (int j = 0; j < QE; j += 4) {
+                            st_v8(psi + b + vCol[h * QE + j], v + 2 * j);
+                            asm volatile("" ::: "memory");
+                        }
+                    } else if constexpr (P0) {
+#pragma unroll
+                        for (int j = 0; j < QE; j += 2) {
+                            *reinterpret_cast<float4*>(psi + b + vCol[h * QE + j]) =
+                                make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                            __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
+                            asm volatile("" ::: "memory");
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < QE; ++j) {
+                            psi[b + vCol[h * QE + j]] =
+                                make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                            asm volatile("" ::: "memory");
+                        }
                     }
                 }
             }
@@ -698,18 +786,20 @@ k_tc_block_a2(float2* __restrict__ psi, const __grid_constant__ Args a, const ui
 }
 
 // B operand: Bt[n][kk] of the real form, Bt[2i][2c] = Re U_ic, Bt[2i][2c+1] = -Im U_ic, Bt[2i+1][2c] = Im U_ic,
-// Bt[2i+1][2c+1] = Re U_ic, split into planes and written in the swizzled shared-memory byte layout.
+// Bt[2i+1][2c+1] = Re U_ic, split into planes and written in the swizzled shared-memory byte layout (i, c taken
+// through line_perm for the line-group data path).
 // With rowphase (device, 2^K radians), row i of U is multiplied by exp(i rowphase[i]) first: the phase
 // epilogue's terms on target bits alone.
 template <int PREC>
-__global__ void k_tc_prepare(const double* __restrict__ U, int K, const double* __restrict__ rowphase,
+__global__ void k_tc_prepare(const double* __restrict__ U, int K, const double* __restrict__ rowphase, int perm,
                              unsigned char* __restrict__ out) {
     using C = Cfg<PREC>;
     const int D = 1 << K, NR = 2 * D;
     const int PB = plane_bytes(K, C::esize);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NR * NR; idx += gridDim.x * blockDim.x) {
         const int n = idx / NR, kk = idx % NR;
-        const int i = n >> 1, c = kk >> 1;
+        // perm: output and input slots in the line-group column order
+        const int i = perm ? line_perm(n >> 1) : n >> 1, c = perm ? line_perm(kk >> 1) : kk >> 1;
         double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
         if (rowphase) {
             double sp, cp;
@@ -769,6 +859,10 @@ cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cud
 
 template <int K, int PREC, bool EPI>
 cudaError_t apply_e(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
+    if (a.lines) {
+        if constexpr (PREC == QSIM_PREC_TF32X3 && !EPI) return apply_p<K, PREC, kLineGroups, EPI>(psi, a, dB, err, s, d);
+        else return cudaErrorInvalidValue;
+    }
     if (a.tpos[0] == 0 && a.tpos[1] == 1 && PREC != QSIM_PREC_BF16X6 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
         return apply_p<K, PREC, kQuadsInLanes, EPI>(psi, a, dB, err, s, d);
     if (a.tpos[0] == 0) return apply_p<K, PREC, kPairsInLanes, EPI>(psi, a, dB, err, s, d);
@@ -877,15 +971,22 @@ size_t tc_operand_bytes(int k, int precision) {
     return (size_t)planes * tc::plane_bytes(k, esize);
 }
 
-cudaError_t launch_tc_prepare(const double* dU, int k, int precision, void* dB, cudaStream_t s,
+bool tc_line_groups(int k, const int* targets, int precision, bool epi) {
+    return precision == QSIM_PREC_TF32X3 && !epi && (k == 5 || k == 6) && targets[0] == 0 && targets[1] == 1 &&
+           targets[2] == 2 && targets[3] == 3;
+}
+
+cudaError_t launch_tc_prepare(const double* dU, int k, int precision, bool lines, void* dB, cudaStream_t s,
                               const double* rowphase) {
     if (!tc_supported(k, precision)) return cudaErrorInvalidValue;
+    if (lines && (precision != QSIM_PREC_TF32X3 || rowphase)) return cudaErrorInvalidValue;
     unsigned char* out = static_cast<unsigned char*>(dB);
     const int blocks = ((2 << k) * (2 << k) + 255) / 256;
+    const int perm = lines ? 1 : 0;
     switch (precision) {
-        case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
-        case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
-        default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, rowphase, out); break;
+        case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
+        case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
+        default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
     }
     return cudaGetLastError();
 }
@@ -916,8 +1017,9 @@ __global__ void k_tc_epi_tiles(uint64_t ntiles, tc::Args a, TcEpiPacked pk, cons
 
 cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const void* dB, int precision,
                             unsigned* dev_err, cudaStream_t s, const DevInfo& d, const void* epi_tab,
-                            const TcEpiPacked* epi, void* epi_scratch, const uint64_t* from_basis) {
+                            const TcEpiPacked* epi, void* epi_scratch, const uint64_t* from_basis, bool lines) {
     if (!tc_supported(k, precision) || n < k + tc::kRowBits) return cudaErrorInvalidValue;
+    if (lines && !tc_line_groups(k, targets, precision, epi != nullptr)) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
     if (epi && (!epi_tab || !epi_scratch || precision == QSIM_PREC_BF16X6)) return cudaErrorInvalidValue;
     tc::Args a;
@@ -933,6 +1035,7 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
     for (int q = 0; q < n; ++q)
         if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
+    a.lines = lines ? 1 : 0;
     if (from_basis) {
         if (precision == QSIM_PREC_BF16X6) return cudaErrorInvalidValue;  // the 16-warp kernel always reads
         a.from_basis = 1;

@@ -40,6 +40,7 @@ struct PlanOp {
     std::vector<unsigned char> blob;  // OP_PHASE, OP_TC with a phase epilogue: the tables until uploaded
     PhaseForm form;            // OP_PHASE (and the epilogue it becomes): the combined phase
     bool has_epi = false;      // OP_TC: the output gets the phase of `form` (the pass that followed it)
+    bool lines = false;        // OP_TC: line-group data path (B prepared in its column order)
     TcEpiPacked epi;           // OP_TC with has_epi: launch parameters; tables at epi_off
     size_t epi_off = 0;
 };
@@ -197,7 +198,7 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                                     op.has_epi ? static_cast<char*>(p->dbuf) + op.epi_off : nullptr,
                                     op.has_epi ? &op.epi : nullptr,
                                     op.has_epi ? static_cast<char*>(p->dbuf) + p->extra.epi_scratch_off : nullptr,
-                                    fb);
+                                    fb, op.lines);
                 break;
             case OP_MERGED:
                 break;
@@ -275,7 +276,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // (n >= 10). Not with global qubits: the phase tables name physical positions, which the reorder passes
     // would move.
     std::vector<char> gwide(G, 0);
-    const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !(opts.local_qubits > 0 && opts.local_qubits < n);
+    const bool remap_later = opts.local_qubits > 0 && opts.local_qubits < n;  // global qubits: targets remapped
+    const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !remap_later;
     for (int i = 0; i < G; ++i) gwide[i] = use_wide && gdiag[i] && phase_gate_ok(c->gates[i]);
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
@@ -538,7 +540,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             const double* U = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx].out_off;
             const int D = 1 << pd.kb;
             if (pd.kind == OP_TC) {
-                e = launch_tc_prepare(U, pd.kb, op.precision, base + op.dev_off, s,
+                // decided on the targets as they are now: a plan with global qubits remaps them later, so it
+                // keeps the row-per-thread paths
+                op.lines = !remap_later && tc_line_groups(pd.kb, op.targets, op.precision, op.has_epi);
+                e = launch_tc_prepare(U, pd.kb, op.precision, op.lines, base + op.dev_off, s,
                                       op.has_epi ? reinterpret_cast<const double*>(base + op.epi_off + op.epi.off_rowphase)
                                                  : nullptr);
             } else if (pd.kind == OP_DENSE_TILE) {

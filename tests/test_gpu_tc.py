@@ -57,14 +57,16 @@ def test_single_block(qsim, prec, k, targets):
 
 
 # Target patterns that take the block kernel's different data paths: lanes on rows with 8-byte accesses
-# (targets from qubit 3 up), lanes on rows with 16-byte pairs (qubit 0 a target), tiles staged in shared
-# memory by bulk copies (targets exactly qubits 0..k-1 in order), and low runs from qubit 0, 1 or 2 given
-# in scrambled order (rows interleaved with targets in the lowest address bits).
+# (targets from qubit 3 up), lanes on rows with 16-byte pairs (qubit 0 the first target), 32-byte quads
+# (qubits 0 and 1 the first two), line groups (qubits 0..3 the first four, 3xTF32: four lanes per row,
+# 16x256b TMEM fragments, permuted column order), and low runs from qubit 0, 1 or 2 given in scrambled
+# order (rows interleaved with targets in the lowest address bits).
 PATH_TARGETS = {
     "from3": (8, 3, 5, 4, 7, 6),
     "run_from0_in_order": (0, 1, 2, 3, 4, 5),
+    "lines_spread": (0, 1, 2, 3, 19, 11),
     "quads_spread": (0, 1, 9, 4, 20, 13),
-    "run_from0_in_order": (0, 1, 2, 3, 4, 5),
+    "almost_lines": (0, 1, 2, 4, 3, 5),
     "even_from0": (0, 2, 4, 6, 8, 10),
     "run_from0": (3, 0, 5, 1, 4, 2),
     "run_from1": (6, 1, 2, 3, 4, 5),
@@ -92,7 +94,7 @@ def test_block_paths_many_tiles(qsim, prec, path):
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
-@pytest.mark.parametrize("path", ["from3", "run_from0_in_order", "run_from0", "run_from1"])
+@pytest.mark.parametrize("path", ["from3", "run_from0_in_order", "lines_spread", "run_from0", "run_from1"])
 def test_block_paths_k5(qsim, prec, path):
     n = 21
     t = PATH_TARGETS[path][:5]
@@ -108,11 +110,11 @@ def test_block_paths_k5(qsim, prec, path):
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
-def test_smallest_state_single_tile(qsim, prec):
+@pytest.mark.parametrize("t", [(12, 0, 5, 9, 3, 7), (0, 1, 2, 3, 4, 5)])
+def test_smallest_state_single_tile(qsim, prec, t):
     """n = k + 7: exactly one 128-row tile."""
     k, n = 6, 13
     rng = np.random.default_rng(1)
-    t = (12, 0, 5, 9, 3, 7)
     U = W.haar_unitary(64, rng)
     psi0 = random_state(n, 8)
     st = qsim.State(n, qsim.C64)
