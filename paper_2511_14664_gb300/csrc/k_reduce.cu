@@ -491,14 +491,21 @@ __global__ void __launch_bounds__(256) k_zstats_hi(const double* __restrict__ W,
     const int q = blockIdx.y;
     const uint64_t len = nseg / gridDim.x, s0 = (uint64_t)blockIdx.x * len;
     ff acc = {0.f, 0.f};
-    for (uint64_t s = s0 + threadIdx.x; s < s0 + len; s += blockDim.x) {
-        bool use;
-        if (q < nh) use = (s >> q) & 1;
-        else { const int r = q - nh; use = ((s >> r) ^ (s >> (r + 1))) & 1; }
-        if (use) {
-            const double w = W[s];
-            const float hi = (float)w;
-            acc = ff_add(acc, ff{hi, (float)(w - (double)hi)});
+    constexpr int U = 8;  // loads in flight per thread
+    for (uint64_t s = s0 + threadIdx.x; s < s0 + len; s += U * blockDim.x) {
+        double w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t su = s + (uint64_t)u * blockDim.x;
+            bool use = su < s0 + len;
+            if (q < nh) use = use && ((su >> q) & 1);
+            else { const int r = q - nh; use = use && (((su >> r) ^ (su >> (r + 1))) & 1); }
+            w[u] = use ? W[su] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float hi = (float)w[u];
+            acc = ff_add(acc, ff{hi, (float)(w[u] - (double)hi)});
         }
     }
     const dd v = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
