@@ -643,8 +643,9 @@ def run_qft(args):
 
 def run_tfim_batch(args):
     """256 Trotterised TFIM chains (widths U{10..24}, steps U{8..32}, theta, phi ~ U(0, pi); seed 4) in one
-    persistent launch (replayed from a CUDA graph), fusion width tuned per circuit width; per-circuit <Z_i>
-    and <Z_i Z_{i+1}>."""
+    enqueue replayed from a CUDA graph: the persistent launch (fusion width tuned per circuit width) for the
+    circuits below 20 qubits, 3xTF32 tensor-core plans for the wider ones; per-circuit <Z_i> and
+    <Z_i Z_{i+1}>."""
     import numpy as np
     import torch
     import workloads as W
@@ -655,14 +656,26 @@ def run_tfim_batch(args):
     t = time.perf_counter()
     chosen = qsim.batch_autotune(cs)
     tune_s = time.perf_counter() - t
-    b = qsim.Batch(cs, max_fused=0)
+    # circuits of >= 20 qubits as 3xTF32 tensor-core plans, the rest in the persistent launch
+    tc_prec, tc_min_n = 1, 20
+    b = qsim.Batch(cs, max_fused=0, precision=tc_prec, tc_min_n=tc_min_n)
     for _ in range(max(1, args.warmup)):
         b.execute(use_graph=True)
     ms = _event_time(torch, lambda i: b.execute(use_graph=True), max(1, args.steps))
     res = b.results()
+    # the same batch with every circuit in the persistent launch (CUDA cores only)
+    simt_only = None
+    if not args.no_variants:
+        bs = qsim.Batch(cs, max_fused=0)
+        bs.execute(use_graph=True)
+        ms_s = _event_time(torch, lambda i: bs.execute(use_graph=True), max(1, args.steps))
+        rs = bs.results()
+        simt_only = {"ms": ms_s, "gates_per_s": gates / (ms_s / 1000.0),
+                     "max_abs_diff_zi_vs_main": max(float(np.max(np.abs(rs[i][0] - res[i][0]))) for i in range(len(cs)))}
+        bs.close()
     # end to end: plan from host circuits, one launch, results to host
     t = time.perf_counter()
-    b2 = qsim.Batch(cs, max_fused=0)
+    b2 = qsim.Batch(cs, max_fused=0, precision=tc_prec, tc_min_n=tc_min_n)
     b2.execute()
     b2.results()
     b2.close()
@@ -707,16 +720,19 @@ def run_tfim_batch(args):
                         "steps), complex64, one persistent launch", gates / (ms / 1000.0), UNIT, args, ms, "f32",
                         {"workload": f"{len(cs)} TFIM chains seed 4, {gates} gates, "
                                      f"{sum(1 for c in cs if c.n > 13)} circuits > 13 qubits",
-                         "fusion_k_by_width": kmap, "passes": b.info["passes"]},
+                         "fusion_k_by_width": kmap, "passes": b.info["passes"],
+                         "tensor_core_plans": f"{sum(1 for c in cs if c.n >= tc_min_n)} circuits of >= {tc_min_n} "
+                                              f"qubits, 3xTF32 k = 6, {b.info['tc_blocks']} blocks"},
                         circuits_per_s=len(cs) / (ms / 1000.0),
                         roofline={"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                  "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch",
+                                  "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_batch + k_tc_block",
                                   "note": "algorithmic bytes of the circuits > 13 qubits only; smaller ones stay "
                                           "in shared memory", "peak_source": src},
                         e2e={"value": gates / e2e_s, "unit": UNIT, "h2d_bytes_per_step":
                              sum(16 * 4 ** len(g.targets) for c in cs for g in c.gates),
                              "d2h_bytes_per_step": 8 * sum(2 * c.n - 1 for c in cs)},
-                        tune_s=tune_s, sample_zi0=list(res[0][0][:4]), one_by_one=one_by_one)
+                        tune_s=tune_s, sample_zi0=list(res[0][0][:4]), one_by_one=one_by_one,
+                        persistent_launch_only=simt_only)
     if not args.no_cpu:
         import oracle as oracle_mod
         # oracle on the smallest circuits until the time budget runs out; work ~ gates x 2^n

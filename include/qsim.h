@@ -98,7 +98,11 @@ typedef struct {
        the plan lists its passes (qsim_plan_num_passes, qsim_plan_pass_info, qsim_plan_info) but cannot be
        executed (QSIM_EINVAL). */
     int32_t dry_run;
-    int32_t reserved;
+    /* Batches only (qsim_batch_plan_create): with a tensor-core precision, circuits of at least this many
+       qubits run as fused tensor-core plans (6-qubit blocks, every pass on the whole GPU) inside the same
+       enqueue, instead of on one cluster of the persistent launch (0 = 20; at least 13). Ignored for
+       QSIM_PREC_SIMT. */
+    int32_t batch_tc_min_n;
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */
@@ -298,9 +302,15 @@ int qsim_inner(qsim_h a, qsim_h b, double* out);
  * width chosen for its qubit count by qsim_batch_autotune, default 4), composed in FP64 on the device, and
  * run by one persistent launch of thread-block clusters: a cluster per circuit of more than 13 qubits (its
  * state in the caller's workspace, passes separated by cluster barriers), then one CTA per smaller circuit
- * with the whole state in shared memory. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
+ * with the whole state in shared memory. With opts->precision a tensor-core precision, circuits of at
+ * least opts->batch_tc_min_n qubits (default 20) are planned as fused tensor-core plans instead (k = 6
+ * blocks, their state in the workspace) and enqueued after the persistent launch, with their <Z> values
+ * reduced on the device: one cluster streams a wide state at a fraction of the GPU's bandwidth, a plan's
+ * passes use all of it. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
  * <Z_q Z_{q+1}> at zz[zz_off(i) + q] (q < n_i - 1), the offsets being the running sums of n_i and n_i - 1
- * in input order; sums are compensated (float-float per thread, double-double across threads).
+ * in input order; sums are compensated (float-float per thread, double-double across threads), and the
+ * values are those of the normalised state (divided by the computed squared norm, which FP32 arithmetic
+ * moves away from 1 by up to ~1e-5 over hundreds of tensor-core blocks).
  */
 typedef struct qsim_batch* qsim_batch_h;
 /* Device workspace (bytes) the circuits of more than 13 qubits need: sum of 2^n x 8 B, 256-byte aligned. */

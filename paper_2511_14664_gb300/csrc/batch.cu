@@ -12,6 +12,11 @@
 //   * once the large queue is empty, every CTA claims small circuits (n <= 13) one at a time and runs each
 //     entirely in its shared memory (64 KiB), with no global traffic for the state at all.
 // There are no spin waits: the only waits are hardware barriers (__syncthreads, cluster barriers).
+// With a tensor-core precision, circuits of at least batch_tc_min_n qubits (default 20) leave the persistent
+// launch: one cluster streams a state at a fraction of the GPU's bandwidth (about 0.44 TB/s for a 16-CTA
+// cluster on a 24-qubit state, where the whole GPU does 6.5), so each becomes a fused tensor-core plan
+// (6-qubit blocks) enqueued after the launch, its first block generating |0>, its <Z> values reduced on the
+// device into the same output arrays. The whole enqueue is one CUDA graph when replayed.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -242,21 +247,23 @@ __device__ __noinline__ void zstats_serial(const float2* psi, int n, Shared& sh)
 
 __device__ __forceinline__ double dval(dd v) { return v.hi + v.lo; }
 
-// Write <Z_i>, <Z_i Z_{i+1}> from the quantity vector red (layout of zstats_segments / zstats_serial).
+// Write <Z_i>, <Z_i Z_{i+1}> from the quantity vector red (layout of zstats_segments / zstats_serial),
+// normalised by the state's squared norm T: the exact state of a circuit from |0...0> has norm 1, and
+// dividing by T removes the FP32 drift of the norm from the reported values.
 __device__ void write_z(const dd* red, int n, double* zi, double* zz) {
     const int t = threadIdx.x;
     if (n < 12) {
         const double T = dval(red[0]);
-        if (t < n) zi[t] = T - 2.0 * dval(red[1 + t]);
-        if (t < n - 1) zz[t] = T - 2.0 * dval(red[n + 1 + t]);
+        if (t < n) zi[t] = (T - 2.0 * dval(red[1 + t])) / T;
+        if (t < n - 1) zz[t] = (T - 2.0 * dval(red[n + 1 + t])) / T;
         return;
     }
     const int nh = n - 12;
     const double T = dval(red[0]);
-    if (t < n) zi[t] = T - 2.0 * dval(t < 12 ? red[1 + t] : red[24 + (t - 12)]);
+    if (t < n) zi[t] = (T - 2.0 * dval(t < 12 ? red[1 + t] : red[24 + (t - 12)])) / T;
     if (t < n - 1) {
         const dd X = t <= 10 ? red[13 + t] : (t == 11 ? red[24 + nh] : red[24 + nh + 1 + (t - 12)]);
-        zz[t] = T - 2.0 * dval(X);
+        zz[t] = (T - 2.0 * dval(X)) / T;
     }
 }
 
@@ -349,6 +356,14 @@ struct qsim_batch {
     cudaGraphExec_t gexec = nullptr;
     void* gws = nullptr;
     cudaStream_t gstream = nullptr;
+    // wide circuits as tensor-core plans: plan, width, state offset (amplitudes), <Z> offsets
+    std::vector<qsim_plan_h> wide_plans;
+    std::vector<int> wide_n;
+    std::vector<int64_t> wide_state_off;
+    std::vector<int> wide_zi_off, wide_zz_off;
+    qsim::ReduceScratch red{};  // their <Z> reductions (device buffers; hresult unused)
+    unsigned* derr = nullptr;   // device error word of their tensor-core launches
+    qsim::DevInfo dev;
 };
 
 using namespace qsim;
@@ -393,7 +408,12 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     qsim_run_opts opts{};
     if (opts_in) opts = *opts_in;
     if (opts.max_fused < 0 || opts.max_fused > batch::kKmax) { set_error("batched fusion width must be 0 (tuned) or 1..%d", batch::kKmax); return QSIM_EINVAL; }
+    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    // circuits this wide run as tensor-core plans (6-qubit blocks need n >= 13)
+    const int tc_min_n = opts.precision == QSIM_PREC_SIMT ? 1000 : (opts.batch_tc_min_n > 0 ? std::max(13, opts.batch_tc_min_n) : 20);
+    std::vector<char> wide(count, 0);
+    for (int ci = 0; ci < count; ++ci) wide[ci] = cs[ci].n >= tc_min_n;
 
     // ---- plan every circuit ---------------------------------------------------------------------------
     std::vector<ComposeBlock> cblocks;
@@ -422,8 +442,9 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             gdiag[i] = is_diagonal(g.matrix, g.k);
         }
         gates_total += c.num_gates;
-        const auto blocks = group_gates(gmask, gdiag, n, kmax);
         circs[ci].n = n;
+        if (wide[ci]) { circs[ci].npass = 0; circs[ci].first_pass = (int64_t)passes.size(); continue; }
+        const auto blocks = group_gates(gmask, gdiag, n, kmax);
         circs[ci].npass = (int)blocks.size();
         circs[ci].first_pass = (int64_t)passes.size();
         for (const auto& blk : blocks) {
@@ -469,8 +490,8 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     }
     b->total_zi = zio;
     b->total_zz = zzo;
-    std::vector<int> large, small;
-    for (int i = 0; i < count; ++i) (cs[i].n > batch::kSmallMax ? large : small).push_back(i);
+    std::vector<int> large, small, wides;
+    for (int i = 0; i < count; ++i) (wide[i] ? wides : cs[i].n > batch::kSmallMax ? large : small).push_back(i);
     std::stable_sort(large.begin(), large.end(), [&](int x, int y) {
         return std::ldexp((double)circs[x].npass, circs[x].n) > std::ldexp((double)circs[y].npass, circs[y].n);
     });
@@ -482,6 +503,13 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         ordered.push_back(circs[i]);
     }
     for (int i : small) { circs[i].state_off = -1; ordered.push_back(circs[i]); }
+    for (int i : wides) {
+        b->wide_n.push_back(cs[i].n);
+        b->wide_state_off.push_back((int64_t)(wsoff / 8));
+        b->wide_zi_off.push_back(circs[i].zi_off);
+        b->wide_zz_off.push_back(circs[i].zz_off);
+        wsoff += (small_state_bytes(cs[i].n) + 255) & ~(size_t)255;
+    }
     b->nlarge = (int)large.size();
     b->nsmall = (int)small.size();
     b->ws_need = wsoff;
@@ -560,14 +588,85 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     I.passes = (int64_t)passes.size();
     I.dense_blocks = (int64_t)passes.size();
     I.algorithmic_bytes = bytes;  // state traffic of the large circuits; small ones never leave shared memory
+
+    // ---- wide circuits: fused tensor-core plans, <Z> scratch, device error word ---------------------------
+    if (!wides.empty()) {
+        auto fail = [&](int code) {
+            qsim_batch_destroy(b);
+            return code;
+        };
+        int nmax = 0;
+        for (int n : b->wide_n) nmax = std::max(nmax, n);
+        int optin = 0;
+        bool ok = cudaGetDevice(&b->dev.device) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&b->dev.num_sms, cudaDevAttrMultiProcessorCount, b->dev.device) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev.device) == cudaSuccess;
+        b->dev.smem_optin = (size_t)optin;
+        // k_zstats_warp partials (kZW per block, at most 8 blocks per SM) and the high-bit partials
+        const size_t npart = (size_t)2 * 21 * 8 * std::max(1, b->dev.num_sms) + 8192;
+        ok = ok && cudaMalloc(&b->red.partials, sizeof(double) * npart) == cudaSuccess;
+        ok = ok && cudaMalloc(&b->red.seg, sizeof(double) * ((size_t)1 << (nmax - 10))) == cudaSuccess;
+        ok = ok && cudaMalloc(&b->red.result, sizeof(double) * 256) == cudaSuccess;
+        ok = ok && cudaMalloc(&b->derr, sizeof(unsigned)) == cudaSuccess;
+        ok = ok && cudaMemset(b->derr, 0, sizeof(unsigned)) == cudaSuccess;
+        if (!ok) { set_error("batch: scratch for the tensor-core plans"); return fail(QSIM_ENOMEM); }
+        for (int i : wides) {
+            qsim_run_opts po{};
+            po.mode = QSIM_RUN_FUSED;
+            po.max_fused = 6;
+            po.precision = opts.precision;
+            po.tc_min_k = 5;
+            qsim_plan_h ph = nullptr;
+            qsim_plan_info pi{};
+            const int prc = qsim_plan_create(&cs[i], QSIM_C64, &po, stream_v, &ph, &pi);
+            if (prc) return fail(prc);
+            b->wide_plans.push_back(ph);
+            I.passes += pi.passes;
+            I.tc_blocks += pi.tc_blocks;
+            I.dense_blocks += pi.dense_blocks;
+            I.diag_blocks += pi.diag_blocks;
+            I.algorithmic_bytes += pi.algorithmic_bytes;
+            // the first block generates |0> (execute_from_basis) and only writes
+            qsim_pass_info p0{};
+            if (pi.passes > 0 && qsim_plan_pass_info(ph, 0, &p0) == QSIM_OK && p0.kind == QSIM_PASS_TC &&
+                p0.precision != QSIM_PREC_BF16X6)
+                I.algorithmic_bytes -= std::ldexp(8.0, cs[i].n);
+        }
+    }
     I.host_plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = I;
     *out = b;
     return QSIM_OK;
 }
 
+static int batch_launch(qsim_batch_h b, cudaStream_t s);
+
 static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
     b->args.ws = static_cast<float2*>(dev_ws);
+    if (b->nlarge + b->nsmall > 0) {
+        const int rc = batch_launch(b, s);
+        if (rc) return rc;
+    }
+    // wide circuits: each plan from |0> (its first block generates the basis state), then its <Z> values
+    for (size_t w = 0; w < b->wide_plans.size(); ++w) {
+        qsim_state st;
+        st.n = b->wide_n[w];
+        st.dtype = QSIM_C64;
+        st.psi = static_cast<float2*>(dev_ws) + b->wide_state_off[w];
+        st.bytes = small_state_bytes(st.n);
+        st.stream = s;
+        st.dev = b->dev;
+        st.derr = b->derr;
+        int rc = qsim_plan_execute_from_basis(&st, b->wide_plans[w], 0, -1);
+        if (rc) return rc;
+        cudaError_t e = run_zstats_device(QSIM_C64, st.psi, st.n, b->red, s, b->dev, b->args.zi + b->wide_zi_off[w],
+                                          b->args.zz + b->wide_zz_off[w], true);
+        if (e != cudaSuccess) return cuda_fail(e, "batch <Z> of a tensor-core plan");
+    }
+    return QSIM_OK;
+}
+
+static int batch_launch(qsim_batch_h b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b->args.counters, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "batch counters");
     cudaLaunchConfig_t cfg{};
@@ -622,13 +721,24 @@ int qsim_batch_results(qsim_batch_h b, void* stream_v, double* zi, double* zz) {
     if (e == cudaSuccess && b->total_zz > 0)
         e = cudaMemcpyAsync(zz, b->args.zz, sizeof(double) * b->total_zz, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch results");
+    if (e != cudaSuccess) return cuda_fail(e, "batch results");
+    if (b->derr) {  // a bounded wait of a tensor-core launch expired
+        qsim_state st;
+        st.derr = b->derr;
+        return check_device_error(&st);
+    }
+    return QSIM_OK;
 }
 
 int qsim_batch_destroy(qsim_batch_h b) {
     if (!b) return QSIM_OK;
     cudaDeviceSynchronize();
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (qsim_plan_h p : b->wide_plans) qsim_plan_destroy(p);
+    cudaFree(b->red.partials);
+    cudaFree(b->red.seg);
+    cudaFree(b->red.result);
+    cudaFree(b->derr);
     cudaFree(b->dbuf);
     delete b;
     return QSIM_OK;

@@ -142,6 +142,10 @@ cudaError_t run_pauli(int dtype, const void* psi, int n, const char* paulis, Red
                       const DevInfo& d, double* out);
 cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
                        double* zi, double* zz);
+// The same values written to device arrays zi_dev[n], zz_dev[n - 1] on `s` (no host synchronisation);
+// normalise: divided by the squared norm (the values of the normalised state).
+cudaError_t run_zstats_device(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s,
+                              const DevInfo& d, double* zi_dev, double* zz_dev, bool normalise);
 cudaError_t run_inner(int dtype, const void* a, const void* b, int n, ReduceScratch& r, cudaStream_t s,
                       const DevInfo& d, double* out);
 // Samples: u_dev (device, shots doubles) -> out_dev (device, shots uint64).

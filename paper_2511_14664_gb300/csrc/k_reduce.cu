@@ -861,19 +861,14 @@ cudaError_t run_probs(int dtype, const void* psi, int n, const int* qubits, int 
 
 int zstats_segment_bits(int n) { return n < kSegBits ? 0 : 10; }
 
-cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
-                       double* zi, double* zz) {
-    cudaError_t e;
-    std::vector<double> T_S_X;  // T, S_0..S_{n-1}, X_0..X_{n-2} (each hi+lo)
+// The <Z> kernels: r.result receives, as (hi, lo) pairs, T, S_0..S_{n-1}, X_0..X_{n-2} for n < 12 (one CTA),
+// else the kZW warp-segment quantities (T, S_0..S_9, X_0..X_9) followed by S_10..S_{n-1}, X_10..X_{n-2}.
+static cudaError_t enqueue_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s,
+                                  const DevInfo& d) {
     if (n < kSegBits) {
         if (dtype == QSIM_C64) k_zstats_small<float><<<1, 256, 0, s>>>((const float2*)psi, n, r.result);
         else k_zstats_small<double><<<1, 256, 0, s>>>((const double2*)psi, n, r.result);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = fetch(r, 4 * n, s)) != cudaSuccess) return e;
-        const double T = r.hresult[0] + r.hresult[1];
-        for (int i = 0; i < n; ++i) zi[i] = T - 2.0 * (r.hresult[2 * (1 + i)] + r.hresult[2 * (1 + i) + 1]);
-        for (int i = 0; i + 1 < n; ++i) zz[i] = T - 2.0 * (r.hresult[2 * (n + 1 + i)] + r.hresult[2 * (n + 1 + i) + 1]);
-        return cudaSuccess;
+        return cudaGetLastError();
     }
     // warp segments of 1024 amplitudes (n >= 12 here): bits 0..9 per thread, bits >= 10 from W
     const uint64_t nseg = 1ull << (n - 10);
@@ -883,20 +878,54 @@ cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cuda
     else k_zstats_warp<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, r.partials);
     k_final_dd<<<kZW, 256, 0, s>>>(r.partials, nb, r.result);
     const int nh = n - 10;
-    if (nh > 0) {
-        // after k_final_dd above has consumed the warp partials (same stream), the buffer takes the high bits'
-        const unsigned P = (unsigned)std::min<uint64_t>(32, nseg);
-        k_zstats_hi<<<dim3(P, 2 * nh - 1), 256, 0, s>>>(W, nseg, nh, r.partials);
-        k_final_dd<<<2 * nh - 1, 256, 0, s>>>(r.partials, (int)P, r.result + 2 * kZW);
+    // after k_final_dd above has consumed the warp partials (same stream), the buffer takes the high bits'
+    const unsigned P = (unsigned)std::min<uint64_t>(32, nseg);
+    k_zstats_hi<<<dim3(P, 2 * nh - 1), 256, 0, s>>>(W, nseg, nh, r.partials);
+    k_final_dd<<<2 * nh - 1, 256, 0, s>>>(r.partials, (int)P, r.result + 2 * kZW);
+    return cudaGetLastError();
+}
+
+static int zstats_result_values(int n) { return n < kSegBits ? 4 * n : 2 * kZW + 2 * (2 * (n - 10) - 1); }
+
+// <Z_i> = T - 2 S_i and <Z_i Z_{i+1}> = T - 2 X_i from the quantities enqueue_zstats leaves (h: (hi, lo) pairs).
+__host__ __device__ inline double zstats_value(const double* h, int q) { return h[2 * q] + h[2 * q + 1]; }
+__host__ __device__ inline double zstats_zi(const double* h, int n, int i) {
+    const double T = zstats_value(h, 0);
+    if (n < kSegBits) return T - 2.0 * zstats_value(h, 1 + i);
+    return T - 2.0 * (i < 10 ? zstats_value(h, 1 + i) : zstats_value(h, kZW + (i - 10)));
+}
+__host__ __device__ inline double zstats_zz(const double* h, int n, int i) {
+    const double T = zstats_value(h, 0);
+    if (n < kSegBits) return T - 2.0 * zstats_value(h, n + 1 + i);
+    return T - 2.0 * (i < 10 ? zstats_value(h, 11 + i) : zstats_value(h, kZW + (n - 10) + (i - 10)));
+}
+
+// normalise: divide by T (the squared norm), i.e. report the values of the normalised state
+__global__ void k_zstats_finish(const double* __restrict__ h, int n, int normalise, double* __restrict__ zi,
+                                double* __restrict__ zz) {
+    const double inv = normalise ? 1.0 / zstats_value(h, 0) : 1.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        zi[i] = normalise ? zstats_zi(h, n, i) * inv : zstats_zi(h, n, i);
+        if (i + 1 < n) zz[i] = normalise ? zstats_zz(h, n, i) * inv : zstats_zz(h, n, i);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = fetch(r, 2 * kZW + 2 * (2 * nh - 1), s)) != cudaSuccess) return e;
-    const double* h = r.hresult;
-    auto val = [&](int q) { return h[2 * q] + h[2 * q + 1]; };
-    const double T = val(0);
-    for (int i = 0; i < n; ++i) zi[i] = T - 2.0 * (i < 10 ? val(1 + i) : val(kZW + (i - 10)));
-    for (int i = 0; i + 1 < n; ++i) zz[i] = T - 2.0 * (i < 10 ? val(11 + i) : val(kZW + nh + (i - 10)));
+}
+
+cudaError_t run_zstats(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s, const DevInfo& d,
+                       double* zi, double* zz) {
+    cudaError_t e = enqueue_zstats(dtype, psi, n, r, s, d);
+    if (e != cudaSuccess) return e;
+    if ((e = fetch(r, zstats_result_values(n), s)) != cudaSuccess) return e;
+    for (int i = 0; i < n; ++i) zi[i] = zstats_zi(r.hresult, n, i);
+    for (int i = 0; i + 1 < n; ++i) zz[i] = zstats_zz(r.hresult, n, i);
     return cudaSuccess;
+}
+
+cudaError_t run_zstats_device(int dtype, const void* psi, int n, ReduceScratch& r, cudaStream_t s,
+                              const DevInfo& d, double* zi_dev, double* zz_dev, bool normalise) {
+    cudaError_t e = enqueue_zstats(dtype, psi, n, r, s, d);
+    if (e != cudaSuccess) return e;
+    k_zstats_finish<<<1, 64, 0, s>>>(r.result, n, normalise ? 1 : 0, zi_dev, zz_dev);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_uniforms(uint64_t seed, int64_t count, double* out_dev, cudaStream_t s) {

@@ -41,7 +41,7 @@ class Circuit(ctypes.Structure):
 class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
-                ("dry_run", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("dry_run", ctypes.c_int32), ("batch_tc_min_n", ctypes.c_int32)]
 
 
 class PassInfo(ctypes.Structure):
@@ -370,9 +370,10 @@ class Plan:
 
 class Batch:
     """Many independent circuits (each from |0...0>, complex64) in one persistent launch; returns the
-    per-circuit <Z_q> and <Z_q Z_{q+1}>."""
+    per-circuit <Z_q> and <Z_q Z_{q+1}>. With a tensor-core precision, circuits of at least tc_min_n qubits
+    (0 = 20) run as fused tensor-core plans in the same enqueue."""
 
-    def __init__(self, circuits, max_fused: int = 0, stream=None):
+    def __init__(self, circuits, max_fused: int = 0, stream=None, precision: int = 0, tc_min_n: int = 0):
         import torch
         self.circuits = list(circuits)
         self.args = [CircuitArgs(c) for c in self.circuits]
@@ -382,7 +383,7 @@ class Batch:
         _check(lib().qsim_batch_workspace_bytes(arr, len(self.args), ctypes.byref(ws)))
         self.ws_bytes = ws.value
         self.ws = torch.empty(max(1, self.ws_bytes // 8), dtype=torch.complex64, device="cuda")
-        o = RunOpts(mode=RUN_FUSED, max_fused=max_fused)
+        o = RunOpts(mode=RUN_FUSED, max_fused=max_fused, precision=precision, batch_tc_min_n=tc_min_n)
         info = PlanInfo()
         b = ctypes.c_void_p()
         _check(lib().qsim_batch_plan_create(arr, len(self.args), ctypes.byref(o),

@@ -124,3 +124,40 @@ def test_full_size_batch_256_tfim_chains(qsim):
     small = [i for i, c in enumerate(cs) if c.n <= 16][:24]
     assert len(small) >= 10
     check([res[i] for i in small], [cs[i] for i in small])
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_wide_circuits_as_tensor_core_plans(qsim, prec):
+    """With a tensor-core precision, circuits of at least tc_min_n qubits run as fused tensor-core plans
+    (their <Z> reduced on the device into the batch's outputs); the rest stay in the persistent launch."""
+    widths = [10, 13, 14, 16, 17, 19, 15, 18]
+    steps = [3, 2, 2, 3, 2, 2, 1, 2]
+    cs = tfim_mix(widths, steps, seed=11)
+    b = qsim.Batch(cs, max_fused=4, precision=prec, tc_min_n=16)
+    assert b.info["tc_blocks"] > 0 and b.info["input_gates"] == sum(len(c) for c in cs)
+    b.execute()
+    r1 = b.results()
+    check(r1, cs)
+    b.execute(use_graph=True)
+    b.execute(use_graph=True)  # replay: the tensor-core plans are captured with the persistent launch
+    r2 = b.results()
+    for (a1, b1), (a2, b2) in zip(r1, r2):
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+
+
+def test_only_wide_circuits(qsim):
+    cs = tfim_mix([16, 17], [2, 2], seed=12)
+    b = qsim.Batch(cs, max_fused=4, precision=1, tc_min_n=13)
+    b.execute(use_graph=True)
+    check(b.results(), cs)
+
+
+def test_deep_wide_circuit_normalised(qsim):
+    """A 20-qubit chain with 32 Trotter steps (1248 gates) as a tensor-core plan inside a batch: its blocks'
+    FP32 accumulation moves the norm by ~1e-5; the batch reports the normalised state's values, which stay
+    within 1e-5 of the FP64 oracle."""
+    cs = tfim_mix([20, 12], [32, 3], seed=13)
+    b = qsim.Batch(cs, max_fused=4, precision=1, tc_min_n=20)
+    assert b.info["tc_blocks"] > 20
+    b.execute()
+    check(b.results(), cs)
