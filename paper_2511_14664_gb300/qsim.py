@@ -292,25 +292,47 @@ class State:
         return complex(out[0], out[1])
 
 
+# numpy image of the qsim_gate struct, so that a whole gate list is packed with array operations
+_GATE_NP = np.dtype({"names": ["k", "nc", "targets", "controls", "matrix"],
+                     "formats": ["<i4", "<i4", ("<i4", (MAX_TARGETS,)), ("<i4", (MAX_CONTROLS,)), "<u8"],
+                     "offsets": [Gate.k.offset, Gate.nc.offset, Gate.targets.offset, Gate.controls.offset,
+                                 Gate.matrix.offset],
+                     "itemsize": ctypes.sizeof(Gate)})
+
+
 class CircuitArgs:
-    """A workloads.Circuit marshalled into qsim_gate structs (keeps the matrices alive)."""
+    """A workloads.Circuit marshalled into qsim_gate structs: one record array for the gates and, per gate
+    width, one array holding those gates' matrices (all kept alive here)."""
 
     def __init__(self, circuit):
         self.n = circuit.n
-        self.mats = []
-        gates = (Gate * max(1, len(circuit.gates)))()
-        for i, g in enumerate(circuit.gates):
-            m = _mat(g.matrix)
-            self.mats.append(m)
-            gates[i].k = len(g.targets)
-            gates[i].nc = len(g.controls)
-            for j, q in enumerate(g.targets):
-                gates[i].targets[j] = q
-            for j, q in enumerate(g.controls):
-                gates[i].controls[j] = q
-            gates[i].matrix = _dptr(m)
-        self.gates = gates
-        self.c = Circuit(n=circuit.n, num_gates=len(circuit.gates), gates=gates)
+        gs = circuit.gates
+        G = len(gs)
+        rec = np.zeros(max(1, G), dtype=_GATE_NP)
+        self.pools = []
+        if G:
+            ks = np.fromiter((len(g.targets) for g in gs), dtype=np.int32, count=G)
+            ncs = np.fromiter((len(g.controls) for g in gs), dtype=np.int32, count=G)
+            if int(ks.max()) > MAX_TARGETS or int(ncs.max()) > MAX_CONTROLS:
+                raise ValueError("a gate has more than %d targets or controls" % MAX_TARGETS)
+            rec["k"][:G] = ks
+            rec["nc"][:G] = ncs
+            for k in np.unique(ks):  # gates of one width share an array of matrices
+                idx = np.nonzero(ks == k)[0]
+                sub = [gs[i] for i in idx]
+                rec["targets"][idx, :k] = np.array([g.targets for g in sub], dtype=np.int32).reshape(len(idx), k)
+                M = np.ascontiguousarray(np.array([g.matrix for g in sub], dtype=np.complex128))
+                if M.shape[1:] != (1 << int(k), 1 << int(k)):
+                    raise ValueError("a %d-qubit gate needs a %dx%d matrix" % (k, 1 << int(k), 1 << int(k)))
+                self.pools.append(M)
+                rec["matrix"][idx] = M.ctypes.data + np.arange(len(idx), dtype=np.uint64) * np.uint64(M[0].nbytes)
+            for c in np.unique(ncs):
+                if c:
+                    idx = np.nonzero(ncs == c)[0]
+                    rec["controls"][idx, :c] = np.array([gs[i].controls for i in idx], dtype=np.int32).reshape(len(idx), c)
+        self.rec = rec
+        self.gates = ctypes.cast(rec.ctypes.data, ctypes.POINTER(Gate))
+        self.c = Circuit(n=circuit.n, num_gates=G, gates=self.gates)
 
 
 class Plan:

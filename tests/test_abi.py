@@ -67,3 +67,27 @@ def test_null_handles_are_rejected():
     assert L.qsim_norm(None, None) == 1
     assert L.qsim_destroy(None) == 0
     assert L.qsim_plan_destroy(None) == 0
+
+
+def test_circuit_marshalling_matches_the_gate_struct():
+    """The binding packs a gate list with array operations into records laid out as qsim_gate; every field
+    and every matrix pointer must read back as the gate it came from (mixed widths, controls, diagonals)."""
+    import ctypes
+    import numpy as np
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    assert qsim._GATE_NP.itemsize == ctypes.sizeof(qsim.Gate)
+    rng = np.random.default_rng(3)
+    c = W.Circuit(12)
+    for _ in range(300):
+        c.append(W.random_gate(12, rng, kmax=3, cmax=2, diag_prob=0.3))
+    a = qsim.CircuitArgs(c)
+    assert a.c.n == 12 and a.c.num_gates == len(c)
+    for i, g in enumerate(c.gates):
+        r = a.gates[i]
+        assert r.k == len(g.targets) and r.nc == len(g.controls)
+        assert list(r.targets[:r.k]) == list(g.targets) and list(r.controls[:r.nc]) == list(g.controls)
+        m = np.ctypeslib.as_array(r.matrix, shape=(2 << (2 * r.k),)).view(np.complex128)
+        assert np.array_equal(m.reshape(g.matrix.shape), g.matrix)
+    empty = qsim.CircuitArgs(W.Circuit(5))
+    assert empty.c.num_gates == 0
