@@ -290,24 +290,24 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + P * PB);
-    uint64_t* mbar = sCol + D;                             // empty[0..P), full[0..P)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2 * P);
+    uint64_t* mbar = sCol + D;                             // empty[0..P), full[0..P), then B loaded
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2 * P + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
     const int c0 = ((warp >> 2) & 1) * CPT;
     const int r = quad * 32 + lane;
 
-    // B planes -> shared memory (already in the swizzled byte layout), column offsets, barriers, TMEM.
-    for (int i = tid; i < P * PB / 16; i += kThreadsWS) reinterpret_cast<uint4*>(sb)[i] = bops[i];
+    // Column offsets, barriers, TMEM. The B planes (already in the swizzled byte layout) come by bulk copies
+    // issued after the barrier below; only the MMA issuer waits for them, so the data warps' first tile
+    // loads overlap the copy.
     for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)(LG ? line_perm(c) : c), a.tpos, K);
     if (tid == 0) {
-        for (int j = 0; j < 2 * P; ++j)
+        for (int j = 0; j < 2 * P + 1; ++j)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
-                         :: "r"(smem_u32(mbar + j)), "r"(j < P ? 1 : kDataWarps) : "memory");
+                         :: "r"(smem_u32(mbar + j)), "r"(j < P || j == 2 * P ? 1 : kDataWarps) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // make B visible to the tensor cores
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tslot)), "r"(TCOLS) : "memory");
@@ -320,6 +320,22 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     const uint32_t bar0 = smem_u32(mbar);
     auto empty = [&](int p) { return bar0 + 8u * (uint32_t)p; };
     auto full = [&](int p) { return bar0 + 8u * (uint32_t)(P + p); };
+    const uint32_t bbar = bar0 + 8u * (uint32_t)(2 * P);
+    // Launched as a programmatic dependent of the kernel before it: everything above (offsets, barriers,
+    // TMEM) overlapped that kernel's tail; from here on its writes are visible. The next block kernel may
+    // be scheduled at once: it cannot share this SM (shared memory), so its CTAs start where ours finish.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (tid == 0) {
+        constexpr uint32_t kChunk = 16384, kBytes = (uint32_t)(P * PB);
+        static_assert(kBytes % kChunk == 0, "whole chunks");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bbar), "r"(kBytes) : "memory");
+#pragma unroll 1
+        for (uint32_t o = 0; o < kBytes; o += kChunk)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(sb) + o), "l"(reinterpret_cast<const char*>(bops) + o), "r"(kChunk),
+                            "r"(bbar) : "memory");
+    }
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
 
@@ -350,7 +366,8 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                 }
             };
             uint32_t last_bar = 0, last_par = 0;
-            bool bad = false;
+            bool bad = !mbar_wait_bounded(bbar, 0);  // B in shared memory
+            if (bad) mbar_wait_bounded(bbar, 0);     // once more for the copy still in flight
             for (uint64_t i = 0; i < m && !bad; ++i) {
                 const uint32_t dcol = (i & 1) ? NR : 0, par = (uint32_t)(i & 1);
 #pragma unroll
@@ -841,19 +858,34 @@ template <int K, int PREC, int MODE, bool EPI>
 cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cudaStream_t s, const DevInfo& d) {
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
-    auto launch = [&](auto kern, int threads) {
+    auto launch = [&](auto kern, int threads, bool pdl) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
-        return cudaGetLastError();
+        if (!pdl) {
+            kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
+            return cudaGetLastError();
+        }
+        // programmatic dependent launch: the prologue overlaps the tail of the kernel before (k_tc_block
+        // waits for it with griddepcontrol.wait before it touches memory that kernel may write)
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = dim3(grid, 1, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);
     };
     // BF16x6 (three A planes, the heaviest split) runs faster on 16 warps with two A buffers than on the
     // 8 data warps of the warp-specialised kernel (which alone has the 32-byte path)
     if constexpr (PREC == QSIM_PREC_BF16X6) {
         if constexpr (EPI) return cudaErrorInvalidValue;  // the 16-warp kernel has no phase epilogue
-        else return launch(k_tc_block_a2<K, PREC, MODE != kRowsInLanes>, kThreads);
+        else return launch(k_tc_block_a2<K, PREC, MODE != kRowsInLanes>, kThreads, false);
     } else {
-        return launch(k_tc_block<K, PREC, MODE, EPI>, kThreadsWS);
+        return launch(k_tc_block<K, PREC, MODE, EPI>, kThreadsWS, true);
     }
 }
 
