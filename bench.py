@@ -230,36 +230,51 @@ def generates_input(plan):
 
 
 def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
-    """Run `steps` steps; returns (total_ms, per-pass ms list summed over steps)."""
+    """Run `steps` steps; returns (total_ms, per-pass ms list summed over steps). With per_pass, CUDA events
+    time the passes: around every pass, or, when every pass is of one kind, around the run of passes as a
+    whole (an event between two block kernels would stop the second from overlapping the first one's tail
+    as a programmatic dependent launch); the run's time is then shared equally among its passes."""
     stream = torch.cuda.current_stream()
     npass = len(plan.pass_list)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     pass_ms = [0.0] * npass
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] if per_pass else None
+    uniform = len({q["kind"] for q in plan.pass_list}) == 1
+    nev = 2 if uniform else npass + 1
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)] if per_pass else None
     gen = generates_input(plan)
     torch.cuda.synchronize()
     t0.record(stream)
     for s in range(steps):
         # |0>, then the plan: a first tensor-core block generates |0> itself instead of reading a set-up state
         if per_pass:
+            ev = evs[s]
             if not gen:
                 st.set_basis(0)
-            evs[0].record(stream)
-            plan.execute_from_basis(st, 0, 1)
-            evs[1].record(stream)
-            for i in range(1, npass):
-                plan.execute_range(st, i, 1)
-                evs[i + 1].record(stream)
+            ev[0].record(stream)
+            if uniform:
+                plan.execute_from_basis(st, 0)
+                ev[1].record(stream)
+            else:
+                plan.execute_from_basis(st, 0, 1)
+                ev[1].record(stream)
+                for i in range(1, npass):
+                    plan.execute_range(st, i, 1)
+                    ev[i + 1].record(stream)
         else:
             plan.execute_from_basis(st, 0)
         st.expect_z_and_sample(1000 + s, shots)   # <Z_i>, <Z_i Z_i+1> and the shots, one read of the state
-        if per_pass:
-            torch.cuda.synchronize()
-            for i in range(npass):
-                pass_ms[i] += evs[i].elapsed_time(evs[i + 1])
     t1.record(stream)
     torch.cuda.synchronize()
+    if per_pass:
+        for ev in evs:
+            if uniform:
+                share = ev[0].elapsed_time(ev[1]) / npass
+                for i in range(npass):
+                    pass_ms[i] += share
+            else:
+                for i in range(npass):
+                    pass_ms[i] += ev[i].elapsed_time(ev[i + 1])
     return t0.elapsed_time(t1), pass_ms
 
 
@@ -289,9 +304,9 @@ def infidelity_at(qsim, W, n_small, depth, path, ref_cache):
 
 
 def cpu_baseline(oracle_mod, W, n_full, depth, seconds):
-    """The FP64 oracle on the host cores: the first gates of the 24-qubit instance of the same generator,
-    run until `seconds` elapse; gate-applications/s scaled by 2^(24 - n_full) (work per gate ~ 2^n)."""
-    n_s = min(24, n_full)
+    """The FP64 oracle on the host cores: the first gates of the 25-qubit instance of the same generator,
+    run until `seconds` elapse; gate-applications/s scaled by 2^(n_s - n_full) (work per gate ~ 2^n)."""
+    n_s = min(25, n_full)
     c = W.brickwork(n_s, depth, seed=SEED)
     psi = oracle_mod.basis(n_s, 0)
     t = time.perf_counter()

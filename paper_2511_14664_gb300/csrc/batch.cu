@@ -605,7 +605,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         // k_zstats_warp partials (kZW per block, at most 8 blocks per SM) and the high-bit partials
         const size_t npart = (size_t)2 * 21 * 8 * std::max(1, b->dev.num_sms) + 8192;
         ok = ok && cudaMalloc(&b->red.partials, sizeof(double) * npart) == cudaSuccess;
-        ok = ok && cudaMalloc(&b->red.seg, sizeof(double) * ((size_t)1 << (nmax - 10))) == cudaSuccess;
+        ok = ok && cudaMalloc(&b->red.seg, sizeof(double) * ((size_t)2 << (nmax - 10))) == cudaSuccess;
         ok = ok && cudaMalloc(&b->red.result, sizeof(double) * 256) == cudaSuccess;
         ok = ok && cudaMalloc(&b->derr, sizeof(unsigned)) == cudaSuccess;
         ok = ok && cudaMemset(b->derr, 0, sizeof(unsigned)) == cudaSuccess;

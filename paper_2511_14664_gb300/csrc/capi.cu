@@ -175,7 +175,7 @@ int qsim_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream,
     const uint64_t nseg = n > kSegBits ? (1ull << (n - kSegBits)) : 1ull;
     bool ok = cudaMalloc(&h->red.partials, sizeof(double) * kPartialDoubles) == cudaSuccess;
     const uint64_t nseg10 = n > 10 ? (1ull << (n - 10)) : 1ull;  // 1024-amplitude segments of the <Z> pass
-    ok = ok && cudaMalloc(&h->red.seg, sizeof(double) * std::max<uint64_t>(2 * nseg, nseg10)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->red.seg, sizeof(double) * std::max<uint64_t>(2 * nseg, 2 * nseg10)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->red.scan, sizeof(double) * (nseg + 8192)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->red.result, sizeof(double) * 256) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->red.hresult, sizeof(double) * 256) == cudaSuccess;

@@ -126,7 +126,7 @@ cudaError_t launch_compose(const ComposeBlock* dblocks, int nblocks, const Compo
 // ---- reductions and sampling (k_reduce.cu) ------------------------------------------------------------------------
 struct ReduceScratch {
     double* partials = nullptr;  // kPartialDoubles doubles
-    double* seg = nullptr;       // max(2 * 2^(n-12), 2^(n-10)) doubles: segment sums
+    double* seg = nullptr;       // 2 * 2^(n-10) doubles: segment sums (doubles, then float-float pairs)
     double* scan = nullptr;      // max(1, 2^(n-12)) + 4096 doubles
     double* result = nullptr;    // 256 doubles (device)
     double* hresult = nullptr;   // 256 doubles (pinned host)

@@ -406,7 +406,8 @@ constexpr int kZW = 21;
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* __restrict__ psi, uint64_t nseg,
-                                                     double* __restrict__ W, double* __restrict__ partials) {
+                                                     double* __restrict__ W, float2* __restrict__ Wf,
+                                                     double* __restrict__ partials) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -436,7 +437,10 @@ __global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* _
         const ff lo = ff_tree_sum(lo8), hi = ff_tree_sum(hi8);  // bit 9 clear / set
         X9 = ff_add(X9, (s & 1) ? lo : hi);
         const ff tot = warp_sum_ff(ff_add(lo, hi));
-        if (lane == 0) W[s] = (double)tot.hi + (double)tot.lo;
+        if (lane == 0) {
+            W[s] = (double)tot.hi + (double)tot.lo;  // for the sampler
+            Wf[s] = make_float2(tot.hi, tot.lo);     // for k_zstats_hi (no FP64 arithmetic there)
+        }
     }
     // bits 6..9 from V: S_{6+b} = sum over j with bit b set; X_{6+b} = sum over j with bits b, b+1 different
     ff T = Z, S6 = Z, S7 = Z, S8 = Z, S9 = Z, X6 = Z, X7 = Z, X8 = Z;
@@ -481,38 +485,41 @@ __global__ void __launch_bounds__(256) k_zstats_warp(const typename Amp<R>::T* _
     }
 }
 
-// Quantities of bits >= B from the segment totals W (nh = n - B), as partial sums: CTA (p, q) takes the p-th of
+// Quantities of bits >= B from the segment totals Wf (float-float; nh = n - B), as partial sums: CTA (p, q) takes the p-th of
 // gridDim.x equal contiguous ranges of segments and quantity q:
 //   q < nh: S_{B+q} = sum_s W[s] bit_q(s);   nh <= q < 2 nh - 1: X_{B+r}, r = q - nh (bits r, r+1 of s).
 // The partial goes to partials[q * gridDim.x + p] (hi, lo), for k_final_dd.
-__global__ void __launch_bounds__(256) k_zstats_hi(const double* __restrict__ W, uint64_t nseg, int nh,
+__global__ void __launch_bounds__(256) k_zstats_hi(const float2* __restrict__ Wf, uint64_t nseg, int nh,
                                                    double* __restrict__ partials) {
-    __shared__ dd sm[32];
+    __shared__ ff smf[8];
     const int q = blockIdx.y;
     const uint64_t len = nseg / gridDim.x, s0 = (uint64_t)blockIdx.x * len;
     ff acc = {0.f, 0.f};
     constexpr int U = 8;  // loads in flight per thread
     for (uint64_t s = s0 + threadIdx.x; s < s0 + len; s += U * blockDim.x) {
-        double w[U];
+        float2 w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t su = s + (uint64_t)u * blockDim.x;
             bool use = su < s0 + len;
             if (q < nh) use = use && ((su >> q) & 1);
             else { const int r = q - nh; use = use && (((su >> r) ^ (su >> (r + 1))) & 1); }
-            w[u] = use ? W[su] : 0.0;
+            w[u] = use ? Wf[su] : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const float hi = (float)w[u];
-            acc = ff_add(acc, ff{hi, (float)(w[u] - (double)hi)});
-        }
+        for (int u = 0; u < U; ++u) acc = ff_add(acc, ff{w[u].x, w[u].y});
     }
-    const dd v = block_sum_dd(dd{(double)acc.hi + (double)acc.lo, 0.0}, sm);
+    // block sum in float-float (FP64 is a small fraction of GB300's FP32 rate); partials combine in FP64
+    acc = warp_sum_ff(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) smf[warp] = acc;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        ff v = smf[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = ff_add(v, smf[w]);
         double* o = partials + 2 * ((int64_t)q * gridDim.x + blockIdx.x);
-        o[0] = v.hi;
-        o[1] = v.lo;
+        o[0] = (double)v.hi;
+        o[1] = (double)v.lo;
     }
 }
 
@@ -873,14 +880,15 @@ static cudaError_t enqueue_zstats(int dtype, const void* psi, int n, ReduceScrat
     // warp segments of 1024 amplitudes (n >= 12 here): bits 0..9 per thread, bits >= 10 from W
     const uint64_t nseg = 1ull << (n - 10);
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)d.num_sms * 8, (int64_t)((nseg + 7) / 8)));
-    double* W = r.seg;  // 2^(n-10) doubles
-    if (dtype == QSIM_C64) k_zstats_warp<float><<<nb, 256, 0, s>>>((const float2*)psi, nseg, W, r.partials);
-    else k_zstats_warp<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, r.partials);
+    double* W = r.seg;                                   // 2^(n-10) doubles
+    float2* Wf = reinterpret_cast<float2*>(r.seg + nseg);  // then the same sums as float-float
+    if (dtype == QSIM_C64) k_zstats_warp<float><<<nb, 256, 0, s>>>((const float2*)psi, nseg, W, Wf, r.partials);
+    else k_zstats_warp<double><<<nb, 256, 0, s>>>((const double2*)psi, nseg, W, Wf, r.partials);
     k_final_dd<<<kZW, 256, 0, s>>>(r.partials, nb, r.result);
     const int nh = n - 10;
     // after k_final_dd above has consumed the warp partials (same stream), the buffer takes the high bits'
     const unsigned P = (unsigned)std::min<uint64_t>(32, nseg);
-    k_zstats_hi<<<dim3(P, 2 * nh - 1), 256, 0, s>>>(W, nseg, nh, r.partials);
+    k_zstats_hi<<<dim3(P, 2 * nh - 1), 256, 0, s>>>(Wf, nseg, nh, r.partials);
     k_final_dd<<<2 * nh - 1, 256, 0, s>>>(r.partials, (int)P, r.result + 2 * kZW);
     return cudaGetLastError();
 }
