@@ -16,7 +16,9 @@
 // launch: one cluster streams a state at a fraction of the GPU's bandwidth (about 0.44 TB/s for a 16-CTA
 // cluster on a 24-qubit state, where the whole GPU does 6.5), so each becomes a fused tensor-core plan
 // (6-qubit blocks) enqueued after the launch, its first block generating |0>, its <Z> values reduced on the
-// device into the same output arrays. The whole enqueue is one CUDA graph when replayed.
+// device into the same output arrays. These plans run on four worker streams forked from the caller's
+// stream and joined back, so that one circuit's pipeline fill and drain overlap another's passes. The whole
+// enqueue is one CUDA graph when replayed.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -39,6 +41,7 @@ namespace batch {
 constexpr int kThreads = 256;
 constexpr int kKmax = 4;
 constexpr int kSmallMax = 13;  // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
+constexpr size_t kWideStreams = 4;  // worker streams for the circuits run as tensor-core plans
 
 struct Pass {
     int k;
@@ -361,9 +364,16 @@ struct qsim_batch {
     std::vector<int> wide_n;
     std::vector<int64_t> wide_state_off;
     std::vector<int> wide_zi_off, wide_zz_off;
-    qsim::ReduceScratch red{};  // their <Z> reductions (device buffers; hresult unused)
     unsigned* derr = nullptr;   // device error word of their tensor-core launches
     qsim::DevInfo dev;
+    // The wide circuits are independent: they run on a few worker streams forked from the caller's stream
+    // and joined back (one graph branch each), so that one circuit's pipeline fill and drain overlap
+    // another's passes. Per worker: its stream, <Z> scratch (device buffers; hresult unused), join event.
+    std::vector<cudaStream_t> wstreams;
+    std::vector<qsim::ReduceScratch> reds;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<int> wide_worker;  // worker of each wide circuit (longest first, to the least-loaded worker)
 };
 
 using namespace qsim;
@@ -602,14 +612,24 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
                   cudaDeviceGetAttribute(&b->dev.num_sms, cudaDevAttrMultiProcessorCount, b->dev.device) == cudaSuccess &&
                   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev.device) == cudaSuccess;
         b->dev.smem_optin = (size_t)optin;
+        const int nworkers = (int)std::min<size_t>(batch::kWideStreams, wides.size());
+        b->reds.resize(nworkers);
+        b->wstreams.assign(nworkers, nullptr);
+        b->join_ev.assign(nworkers, nullptr);
         // k_zstats_warp partials (kZW per block, at most 8 blocks per SM) and the high-bit partials
         const size_t npart = (size_t)2 * 21 * 8 * std::max(1, b->dev.num_sms) + 8192;
-        ok = ok && cudaMalloc(&b->red.partials, sizeof(double) * npart) == cudaSuccess;
-        ok = ok && cudaMalloc(&b->red.seg, sizeof(double) * ((size_t)2 << (nmax - 10))) == cudaSuccess;
-        ok = ok && cudaMalloc(&b->red.result, sizeof(double) * 256) == cudaSuccess;
+        for (int k = 0; k < nworkers; ++k) {
+            ok = ok && cudaMalloc(&b->reds[k].partials, sizeof(double) * npart) == cudaSuccess;
+            ok = ok && cudaMalloc(&b->reds[k].seg, sizeof(double) * ((size_t)2 << (nmax - 10))) == cudaSuccess;
+            ok = ok && cudaMalloc(&b->reds[k].result, sizeof(double) * 256) == cudaSuccess;
+            ok = ok && cudaStreamCreateWithFlags(&b->wstreams[k], cudaStreamNonBlocking) == cudaSuccess;
+            ok = ok && cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        }
+        ok = ok && cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaMalloc(&b->derr, sizeof(unsigned)) == cudaSuccess;
         ok = ok && cudaMemset(b->derr, 0, sizeof(unsigned)) == cudaSuccess;
-        if (!ok) { set_error("batch: scratch for the tensor-core plans"); return fail(QSIM_ENOMEM); }
+        if (!ok) { set_error("batch: scratch and streams for the tensor-core plans"); return fail(QSIM_ENOMEM); }
+        std::vector<double> wide_work;
         for (int i : wides) {
             qsim_run_opts po{};
             po.mode = QSIM_RUN_FUSED;
@@ -621,6 +641,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             const int prc = qsim_plan_create(&cs[i], QSIM_C64, &po, stream_v, &ph, &pi);
             if (prc) return fail(prc);
             b->wide_plans.push_back(ph);
+            wide_work.push_back(std::ldexp((double)pi.passes, cs[i].n));
             I.passes += pi.passes;
             I.tc_blocks += pi.tc_blocks;
             I.dense_blocks += pi.dense_blocks;
@@ -631,6 +652,17 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             if (pi.passes > 0 && qsim_plan_pass_info(ph, 0, &p0) == QSIM_OK && p0.kind == QSIM_PASS_TC &&
                 p0.precision != QSIM_PREC_BF16X6)
                 I.algorithmic_bytes -= std::ldexp(8.0, cs[i].n);
+        }
+        // longest processing time first: each circuit, most work first, to the least-loaded worker
+        std::vector<int> byw(wide_work.size());
+        for (size_t w = 0; w < byw.size(); ++w) byw[w] = (int)w;
+        std::stable_sort(byw.begin(), byw.end(), [&](int x, int y) { return wide_work[x] > wide_work[y]; });
+        std::vector<double> load(nworkers, 0.0);
+        b->wide_worker.assign(wide_work.size(), 0);
+        for (int w : byw) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->wide_worker[w] = k;
+            load[k] += wide_work[w];
         }
     }
     I.host_plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -647,23 +679,36 @@ static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
         const int rc = batch_launch(b, s);
         if (rc) return rc;
     }
-    // wide circuits: each plan from |0> (its first block generates the basis state), then its <Z> values
-    for (size_t w = 0; w < b->wide_plans.size(); ++w) {
+    if (b->wide_plans.empty()) return QSIM_OK;
+    // wide circuits on the worker streams (fork from s, join back into s): each plan from |0> (its first
+    // block generates the basis state), then its <Z> values
+    cudaError_t e = cudaEventRecord(b->fork_ev, s);
+    for (size_t k = 0; e == cudaSuccess && k < b->wstreams.size(); ++k) e = cudaStreamWaitEvent(b->wstreams[k], b->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    int rc = QSIM_OK;
+    for (size_t w = 0; w < b->wide_plans.size() && rc == QSIM_OK; ++w) {
+        const int k = b->wide_worker[w];
         qsim_state st;
         st.n = b->wide_n[w];
         st.dtype = QSIM_C64;
         st.psi = static_cast<float2*>(dev_ws) + b->wide_state_off[w];
         st.bytes = small_state_bytes(st.n);
-        st.stream = s;
+        st.stream = b->wstreams[k];
         st.dev = b->dev;
         st.derr = b->derr;
-        int rc = qsim_plan_execute_from_basis(&st, b->wide_plans[w], 0, -1);
-        if (rc) return rc;
-        cudaError_t e = run_zstats_device(QSIM_C64, st.psi, st.n, b->red, s, b->dev, b->args.zi + b->wide_zi_off[w],
-                                          b->args.zz + b->wide_zz_off[w], true);
-        if (e != cudaSuccess) return cuda_fail(e, "batch <Z> of a tensor-core plan");
+        rc = qsim_plan_execute_from_basis(&st, b->wide_plans[w], 0, -1);
+        if (rc) break;
+        e = run_zstats_device(QSIM_C64, st.psi, st.n, b->reds[k], st.stream, b->dev, b->args.zi + b->wide_zi_off[w],
+                              b->args.zz + b->wide_zz_off[w], true);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch <Z> of a tensor-core plan");
     }
-    return QSIM_OK;
+    // join every worker back into s, also after an error (a capture must end with all branches joined)
+    for (size_t k = 0; k < b->wstreams.size(); ++k) {
+        cudaError_t ej = cudaEventRecord(b->join_ev[k], b->wstreams[k]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, b->join_ev[k], 0);
+        if (ej != cudaSuccess && rc == QSIM_OK) rc = cuda_fail(ej, "batch join");
+    }
+    return rc;
 }
 
 static int batch_launch(qsim_batch_h b, cudaStream_t s) {
@@ -735,9 +780,16 @@ int qsim_batch_destroy(qsim_batch_h b) {
     cudaDeviceSynchronize();
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (qsim_plan_h p : b->wide_plans) qsim_plan_destroy(p);
-    cudaFree(b->red.partials);
-    cudaFree(b->red.seg);
-    cudaFree(b->red.result);
+    for (auto& r : b->reds) {
+        cudaFree(r.partials);
+        cudaFree(r.seg);
+        cudaFree(r.result);
+    }
+    for (cudaStream_t st : b->wstreams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     cudaFree(b->derr);
     cudaFree(b->dbuf);
     delete b;
