@@ -22,7 +22,10 @@
 //   8-byte accesses, 16-byte pairs when qubit 0 is the first target, 32-byte quads (whole sectors) when
 //   qubits 0 and 1 are the first two. When qubits 0..3 are the first four targets (3xTF32) four threads
 //   share a row instead (line groups): each moves 32 bytes of the row's 128-byte line, and the tile goes to
-//   and from TMEM in 16x256b fragments with B's columns permuted to match. With a phase epilogue (EPI)
+//   and from TMEM in 16x256b fragments with B's columns permuted to match. When qubit 0 is not a target
+//   but one of qubits 1..3 is (3xTF32, no epilogue) the 16x256b fragments carry pair rows: a thread's two
+//   rows differ in qubit 0 and move as one 16-byte vector, and lanes l % 4 take the two lowest targets, so
+//   every warp access covers whole lines whichever low qubits the block acts on. With a phase epilogue (EPI)
 //   every output amplitude is multiplied by unit complex factors of its tile, row and column bits before it
 //   is stored.
 //   BF16x6 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
@@ -223,6 +226,10 @@ enum Mode {
                         // its 16 adjacent amplitudes (one 128-byte line) with 32-byte accesses; the tile goes
                         // to and from TMEM with the 16x256b shape, so a warp access touches 8 whole lines
                         // instead of 32 partial ones
+    kPairRows = 4,      // qubit 0 is not a target, one of 1..3 is (3xTF32, no epilogue): 16x256b fragments, a thread's two
+                        // fragment rows differ in qubit 0 (row bit 3 is mapped to it) and move as one 16-byte
+                        // vector per column; lanes l % 4 take the two lowest targets and l / 4 three more row
+                        // qubits, so low targets no longer split a warp access over partly used lines
 };
 
 // kLineGroups column order: tile column slot s holds natural column index line_perm(s) (bits 0,1 and 2,3
@@ -265,7 +272,8 @@ template <int K, int PREC, int MODE, bool EPI>
 __global__ void __launch_bounds__(kThreadsWS, 1)
 k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
            unsigned* __restrict__ err) {
-    constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes, LG = MODE == kLineGroups;
+    constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes, LG = MODE == kLineGroups,
+                   PR = MODE == kPairRows;
     using C = Cfg<PREC>;
     constexpr bool BF16 = C::esize == 2;
     constexpr int P = C::planes;
@@ -284,7 +292,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                                ((uint32_t)(128 >> 4) << 24);
     static_assert(CPT % QC == 0 && CPT % QE == 0, "whole chunks per thread");
     static_assert(TCOLS <= 512, "TMEM holds two accumulators and every A plane");
-    static_assert(!LG || (!BF16 && !EPI && CPT % 16 == 0), "line groups: TF32 planes, no epilogue");
+    static_assert(!(LG || PR) || (!BF16 && !EPI && CPT % 16 == 0), "16x256b paths: TF32 planes, no epilogue");
     constexpr int DEPTH = K >= 6 ? 1 : 2;                  // tiles of loads in flight (registers: CPT x 2 each)
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -391,13 +399,19 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     } else {
         // ---- data warps ----
         const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-        const uint64_t rowoff = LG ? 0 : deposit((uint64_t)r, a.rpos, kRowBits);
+        const uint64_t rowoff = (LG || PR) ? 0 : deposit((uint64_t)r, a.rpos, kRowBits);
         // LG: this thread's rows quad * 32 + 8 rho + lane / 4 (rho = 0..3) and its slot lane % 4 of each 4
         [[maybe_unused]] uint64_t ro[4];
         [[maybe_unused]] const int li = lane & 3;
         if constexpr (LG) {
 #pragma unroll
             for (int rho = 0; rho < 4; ++rho) ro[rho] = deposit((uint64_t)(quad * 32 + 8 * rho + (lane >> 2)), a.rpos, kRowBits);
+        }
+        // PR: rows quad * 32 + 16 pr + 8 e + lane / 4; row bit 3 (e) is qubit 0, so ro[pr] (e = 0) starts a
+        // 16-byte pair of amplitudes
+        if constexpr (PR) {
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) ro[pr] = deposit((uint64_t)(quad * 32 + 16 * pr + (lane >> 2)), a.rpos, kRowBits);
         }
         constexpr int LPR = CPT / 4;  // LG: values per row in X (X[rho * LPR + j] is slot c0 + 4 j + lane % 4)
         // Column offsets are re-read from shared memory at each use (one broadcast load) instead of being
@@ -424,6 +438,26 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                         }
                         asm volatile("" ::: "memory");
                     }
+            } else if constexpr (PR) {
+                // X[pr * (CPT / 2) + 8 m + 2 jj + e]: slot c0 + 16 m + 4 jj + lane % 4, row bit 3 = e
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+                    for (int m = 0; m < CPT / 16; ++m)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            float2* x = X + pr * (CPT / 2) + 8 * m + 2 * jj;
+                            const uint64_t o = b + ro[pr] + vCol[16 * m + 4 * jj + li];
+                            if (a.from_basis) {
+                                x[0] = make_float2(o == a.basis ? 1.0f : 0.0f, 0.0f);
+                                x[1] = make_float2(o + 1 == a.basis ? 1.0f : 0.0f, 0.0f);
+                            } else {
+                                const float4 v = *reinterpret_cast<const float4*>(psi + o);
+                                x[0] = make_float2(v.x, v.y);
+                                x[1] = make_float2(v.z, v.w);
+                            }
+                            asm volatile("" ::: "memory");
+                        }
             } else if (a.from_basis) {
 #pragma unroll
                 for (int j = 0; j < CPT; ++j) X[j] = make_float2(b + vCol[j] == a.basis ? 1.0f : 0.0f, 0.0f);
@@ -485,6 +519,24 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                         }
                         tmem_st_16x256b_x4(tbase + tlane + ((uint32_t)(16 * pr) << 16) + A0 + p * ACOLS + 2 * (c0 + 16 * m), v);
                     }
+            } else if constexpr (PR) {
+                // 16x256b: repetition jj of chunk m holds slot c0 + 16 m + 4 jj + lane % 4 (re, im) for the
+                // rows e = 0 (lane quad * 32 + 16 pr + lane / 4) and e = 1 (8 lanes further)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+                    for (int m = 0; m < CPT / 16; ++m) {
+                        uint32_t v[16];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const float2 x0 = X[pr * (CPT / 2) + 8 * m + 2 * jj], x1 = X[pr * (CPT / 2) + 8 * m + 2 * jj + 1];
+                            v[4 * jj] = plane_of(x0.x, p);
+                            v[4 * jj + 1] = plane_of(x0.y, p);
+                            v[4 * jj + 2] = plane_of(x1.x, p);
+                            v[4 * jj + 3] = plane_of(x1.y, p);
+                        }
+                        tmem_st_16x256b_x4(tbase + tlane + ((uint32_t)(16 * pr) << 16) + A0 + p * ACOLS + 2 * (c0 + 16 * m), v);
+                    }
             } else {
 #pragma unroll
                 for (int h = 0; h < CPT / QC; ++h) {
@@ -540,6 +592,23 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                         asm volatile("" ::: "memory");
                         st_v8(psi + o + ro[2 * pr + 1], vo);
                         asm volatile("" ::: "memory");
+                    }
+            } else if constexpr (PR) {
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+                    for (int m = 0; m < CPT / 16; ++m) {
+                        uint32_t v[16];
+                        tmem_ld_16x256b_x4(tbase + tlane + ((uint32_t)(16 * pr) << 16) + dcol + 2 * (c0 + 16 * m), v);
+                        wait_ld();
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            // (re, im) of rows e = 0 and e = 1: two adjacent amplitudes
+                            *reinterpret_cast<float4*>(psi + b + ro[pr] + vCol[16 * m + 4 * jj + li]) =
+                                make_float4(__uint_as_float(v[4 * jj]), __uint_as_float(v[4 * jj + 1]),
+                                            __uint_as_float(v[4 * jj + 2]), __uint_as_float(v[4 * jj + 3]));
+                            asm volatile("" ::: "memory");
+                        }
                     }
             } else {
                 [[maybe_unused]] float2 E[NV + 1];
@@ -894,6 +963,22 @@ cudaError_t apply_e(void* psi, const Args& a, const void* dB, unsigned* err, cud
     if (a.lines) {
         if constexpr (PREC == QSIM_PREC_TF32X3 && !EPI) return apply_p<K, PREC, kLineGroups, EPI>(psi, a, dB, err, s, d);
         else return cudaErrorInvalidValue;
+    }
+    if constexpr (PREC == QSIM_PREC_TF32X3 && !EPI) {
+        // Pair rows when qubit 0 is not a target but one of qubits 1..3 is (lanes on rows would split each
+        // warp access over partly used lines; measured 2.6 vs 2.7-4.6 ms at 30 qubits). With targets from
+        // qubit 4 up, lanes on rows stay faster (2.6 vs 2.9-3.1 ms): each of their accesses covers two
+        // adjacent lines of one column rather than single lines of four columns.
+        bool low = false;
+        for (int j = 0; j < K; ++j) low = low || (a.tpos[j] >= 1 && a.tpos[j] <= 3);
+        if (a.rpos[0] == 0 && low) {  // pair rows, with row bit 3 moved to qubit 0
+            Args b = a;
+            b.rpos[0] = a.rpos[1];
+            b.rpos[1] = a.rpos[2];
+            b.rpos[2] = a.rpos[3];
+            b.rpos[3] = a.rpos[0];
+            return apply_p<K, PREC, kPairRows, EPI>(psi, b, dB, err, s, d);
+        }
     }
     if (a.tpos[0] == 0 && a.tpos[1] == 1 && PREC != QSIM_PREC_BF16X6 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
         return apply_p<K, PREC, kQuadsInLanes, EPI>(psi, a, dB, err, s, d);

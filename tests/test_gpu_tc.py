@@ -56,11 +56,13 @@ def test_single_block(qsim, prec, k, targets):
     check(st.get_state(), ref, n, *BLOCK_TOL[prec])
 
 
-# Target patterns that take the block kernel's different data paths: lanes on rows with 8-byte accesses
-# (targets from qubit 3 up), lanes on rows with 16-byte pairs (qubit 0 the first target), 32-byte quads
+# Target patterns that take the block kernel's different data paths: with qubit 0 not a target but one of
+# qubits 1..3 a target, pair rows (3xTF32: 16x256b TMEM fragments whose two rows differ in qubit 0, lanes
+# l % 4 on the two lowest targets); lanes on rows with 8-byte accesses (targets from qubit 4 up, or BF16x3);
+# 16-byte pairs (qubit 0 the first target), 32-byte quads
 # (qubits 0 and 1 the first two), line groups (qubits 0..3 the first four, 3xTF32: four lanes per row,
-# 16x256b TMEM fragments, permuted column order), and low runs from qubit 0, 1 or 2 given in scrambled
-# order (rows interleaved with targets in the lowest address bits).
+# permuted column order), and low runs from qubit 0, 1 or 2 given in scrambled order (rows interleaved with
+# targets in the lowest address bits).
 PATH_TARGETS = {
     "from3": (8, 3, 5, 4, 7, 6),
     "run_from0_in_order": (0, 1, 2, 3, 4, 5),
@@ -72,6 +74,8 @@ PATH_TARGETS = {
     "run_from1": (6, 1, 2, 3, 4, 5),
     "run_from2": (2, 7, 3, 4, 6, 5),
     "low_and_high": (1, 21, 3, 4, 17, 2),
+    "pair_rows_low": (2, 3, 8, 9, 14, 15),
+    "rows_high": (4, 9, 12, 15, 18, 21),
 }
 
 
