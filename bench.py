@@ -867,6 +867,7 @@ def run_paper33(args, kind):
     ys = torch.from_numpy(np.sort(rng.choice(1 << n, size=4096, replace=False))).cuda()
     for name, kw in [("plain", dict(mode=0, max_fused=1)), ("tf32x3_k5", dict(mode=1, max_fused=5, precision=1, tc_min_k=5)),
                      ("tf32x3_k6", dict(mode=1, max_fused=6, precision=1, tc_min_k=5)),
+                     ("tf32x3_k6_lookahead", dict(mode=1, max_fused=6, precision=1, tc_min_k=5, plan_effort=1)),
                      ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5))]:
         if name == "plain" and args.no_variants:
             continue
@@ -886,6 +887,7 @@ def run_paper33(args, kind):
         if ref_amps is None:
             ref_amps = amps
         rec = {"ms_per_step": ms, "gates_per_s": len(c) / (ms / 1000.0), "passes": p.info["passes"],
+               "host_plan_ms": p.info["host_plan_ms"],
                "algorithmic_gb": p.info["algorithmic_bytes"] / 1e9,
                "achieved_gbs": p.info["algorithmic_bytes"] / (ms / 1000.0) / 1e9,
                "max_abs_diff_sampled_vs_first": float(np.max(np.abs(amps - ref_amps))), "norm": st.norm()}

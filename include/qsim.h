@@ -103,6 +103,11 @@ typedef struct {
        enqueue, instead of on one cluster of the persistent launch (0 = 20; at least 13). Ignored for
        QSIM_PREC_SIMT. */
     int32_t batch_tc_min_n;
+    /* Planning effort: 0 = greedy fusion (the largest candidate block at each step); 1 = also fuse with
+       one block of look-ahead and keep the grouping with fewer blocks (planning about 4x slower; e.g. the
+       33-qubit triangular-lattice TFIM goes from 63 to 58 passes). */
+    int32_t plan_effort;
+    int32_t reserved;
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */

@@ -43,9 +43,11 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
 // blocked by an earlier unplaced gate on a shared qubit (diagonal gates are blocked only by non-diagonal
 // ones) and keeps the block within kmax qubits. gmask[i] = qubits of gate i (targets and controls). With
 // gwide, the diagonal gates it marks may also form one block of any width (a phase pass), chosen when it
-// holds more than wide_factor times the gates of the best other candidate.
+// holds more than wide_factor times the gates of the best other candidate. lookahead > 0: choose among the
+// `lookahead` largest candidates by their size plus that of the best block after them.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1);
+                                          int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1,
+                                          int lookahead = 0);
 
 }  // namespace qsim
 

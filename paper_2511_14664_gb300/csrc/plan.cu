@@ -102,62 +102,103 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
     return blk;
 }
 
-// Fusion into blocks of at most kmax qubits. Each block is the largest (most gates) of these candidates:
+// Candidates for the next block (group_gates keeps the largest, or looks one step ahead):
 // every window of kmax consecutive qubits (all available gates inside it), and, for every qubit, its
 // earliest unplaced gate when no earlier unplaced gate blocks it, grown greedily. The plain greedy choice
 // (seeded at the earliest unplaced gate) is one of the candidates. On nearest-neighbour circuits the
 // windows tile the (qubit, time) plane in diamonds, about twice the gates per block of the plain greedy.
-std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax, const std::vector<char>* gwide, int wide_factor) {
+static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
+                                                int n, int kmax, const std::vector<char>* gwide, int wide_factor,
+                                                const std::vector<char>& done, int first) {
     const int G = (int)gmask.size();
+    std::vector<std::vector<int>> out;
+    std::vector<int> wide;
+    if (gwide) {
+        const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
+        uint64_t bany = 0;
+        for (int i = first; i < G && bany != all; ++i) {
+            if (done[i]) continue;
+            if (gdiag[i] && (*gwide)[i] && (gmask[i] & bany) == 0) wide.push_back(i);
+            else if (!gdiag[i]) bany |= gmask[i];
+        }
+    }
+    if (popcnt(gmask[first]) > kmax && !(gwide && (*gwide)[first] && gdiag[first])) {
+        out.push_back({first});  // wider than the fusion width: a block of its own
+        return out;
+    }
+    size_t best = 0;
+    const int wmax = std::min(kmax, n);
+    for (int a0 = 0; a0 + wmax <= n; ++a0) {
+        const uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
+        auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax);
+        best = std::max(best, blk.size());
+        if (!blk.empty()) out.push_back(std::move(blk));
+    }
+    uint64_t seen = 0, bany = 0, bdiag = 0;
+    for (int i = first; i < G && popcnt(seen) < n; ++i) {
+        if (done[i]) continue;
+        const uint64_t qs = gmask[i];
+        const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
+        if ((qs & ~seen) && !blocked && popcnt(qs) <= kmax) {
+            auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax);
+            best = std::max(best, blk.size());
+            if (!blk.empty()) out.push_back(std::move(blk));
+        }
+        seen |= qs;
+        if (gdiag[i]) bdiag |= qs; else bany |= qs;
+    }
+    // A phase pass costs a full pass whatever it holds, and it only grows while dense blocks make progress
+    // (each one frees the diagonal gates behind it): it wins against dense blocks of less than
+    // 1 / wide_factor of its size.
+    if (wide.size() > (size_t)wide_factor * best) { out.clear(); out.push_back(std::move(wide)); }
+    if (out.empty()) out.push_back({first});
+    return out;
+}
+
+// Fusion into blocks of at most kmax qubits: at each step the largest candidate, or, with lookahead > 0,
+// the candidate among the `lookahead` largest distinct ones whose size plus the size of the best block
+// after it is largest (one step of look-ahead; slower planning, sometimes fewer blocks).
+std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
+                                          int kmax, const std::vector<char>* gwide, int wide_factor, int lookahead) {
+    const int G = (int)gmask.size();
+    const int LA = lookahead;
     std::vector<std::vector<int>> blocks;
     std::vector<char> done(G, 0);
     int first = 0;
+    auto next_first = [&](int f) { while (f < G && done[f]) ++f; return f; };
     while (true) {
-        while (first < G && done[first]) ++first;
+        first = next_first(first);
         if (first >= G) break;
-        std::vector<int> best;
-        // With gwide: every unplaced diagonal gate it marks that no earlier unplaced non-diagonal gate blocks,
-        // whatever its qubits (one phase pass takes them all), as one more candidate.
-        std::vector<int> wide;
-        if (gwide) {
-            const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
-            uint64_t bany = 0;
-            for (int i = first; i < G && bany != all; ++i) {
-                if (done[i]) continue;
-                if (gdiag[i] && (*gwide)[i] && (gmask[i] & bany) == 0) wide.push_back(i);
-                else if (!gdiag[i]) bany |= gmask[i];
-            }
-        }
-        if (popcnt(gmask[first]) > kmax && !(gwide && (*gwide)[first] && gdiag[first])) {
-            best.push_back(first);  // wider than the fusion width: a block of its own
-        } else {
-            // windows
-            const int wmax = std::min(kmax, n);
-            for (int a0 = 0; a0 + wmax <= n; ++a0) {
-                const uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
-                auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax);
-                if (blk.size() > best.size()) best.swap(blk);
-            }
-            // seeds: the earliest unplaced gate of every qubit line, if nothing earlier blocks it
-            uint64_t seen = 0, bany = 0, bdiag = 0;
-            for (int i = first; i < G && popcnt(seen) < n; ++i) {
-                if (done[i]) continue;
-                const uint64_t qs = gmask[i];
-                const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
-                if ((qs & ~seen) && !blocked && popcnt(qs) <= kmax) {
-                    auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax);
-                    if (blk.size() > best.size()) best.swap(blk);
+        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first);
+        size_t pick = 0;
+        for (size_t c = 1; c < cands.size(); ++c)
+            if (cands[c].size() > cands[pick].size()) pick = c;
+        if (LA > 0 && cands.size() > 1) {
+            // one step of look-ahead among the LA largest distinct candidates: size + best next size
+            std::vector<size_t> order(cands.size());
+            for (size_t c = 0; c < order.size(); ++c) order[c] = c;
+            std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cands[x].size() > cands[y].size(); });
+            double best_score = -1;
+            int tried = 0;
+            for (size_t oi = 0; oi < order.size() && tried < LA; ++oi) {
+                const auto& cb = cands[order[oi]];
+                bool dup = false;
+                for (size_t oj = 0; oj < oi && !dup; ++oj) dup = cands[order[oj]] == cb;
+                if (dup) continue;
+                ++tried;
+                for (int g : cb) done[g] = 1;
+                const int f2 = next_first(first);
+                size_t nxt = 0;
+                if (f2 < G) {
+                    auto c2 = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, f2);
+                    for (const auto& b2 : c2) nxt = std::max(nxt, b2.size());
                 }
-                seen |= qs;
-                if (gdiag[i]) bdiag |= qs; else bany |= qs;
+                for (int g : cb) done[g] = 0;
+                const double score = (double)cb.size() + (double)nxt;
+                if (score > best_score) { best_score = score; pick = order[oi]; }
             }
-            // A phase pass costs a full pass whatever it holds, and it only grows while dense blocks make
-            // progress (each one frees the diagonal gates behind it): it wins against dense blocks of less
-            // than 1 / wide_factor of its size.
-            if (wide.size() > (size_t)wide_factor * best.size()) best.swap(wide);
-            if (best.empty()) best.push_back(first);
         }
+        std::vector<int> best = std::move(cands[pick]);
         for (int i : best) done[i] = 1;
         blocks.push_back(std::move(best));
     }
@@ -283,12 +324,14 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
         blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, 1);
-        // whether a phase pass should wait for more diagonal gates depends on the circuit: keep the grouping
-        // with the fewest blocks
-        for (int f = 2; use_wide && f <= 4; f *= 2) {
-            auto alt = group_gates(gmask, gdiag, n, kmax, &gwide, f);
-            if (alt.size() < blocks.size()) blocks.swap(alt);
-        }
+        // whether a phase pass should wait for more diagonal gates depends on the circuit, and so does
+        // whether looking one block ahead pays: keep the grouping with the fewest blocks
+        for (int la = 0; la <= (opts.plan_effort > 0 ? 4 : 0); la += 4)
+            for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
+                if (la == 0 && f == 1) continue;  // the first grouping above
+                auto alt = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f, la);
+                if (alt.size() < blocks.size()) blocks.swap(alt);
+            }
     }
     // A diagonal block moves after a tensor-core block that follows it when they share no qubit (so they
     // commute), and neighbouring diagonal blocks merge (diagonal gates commute): a phase pass then follows

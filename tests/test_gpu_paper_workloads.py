@@ -21,6 +21,7 @@ PATHS = {
     "tf32x3_k5": dict(mode=1, max_fused=5, precision=1, tc_min_k=5),
     "tf32x3_k6": dict(mode=1, max_fused=6, precision=1, tc_min_k=5),
     "bf16x6_k6": dict(mode=1, max_fused=6, precision=3, tc_min_k=5),
+    "tf32x3_k6_lookahead": dict(mode=1, max_fused=6, precision=1, tc_min_k=5, plan_effort=1),
 }
 
 

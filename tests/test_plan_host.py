@@ -132,3 +132,17 @@ def test_dry_run_needs_no_device_and_reports_info(qsim):
     p, ps = plan(qsim, c, 1, mode=1, max_fused=4)
     assert p.info["passes"] == len(ps) and p.info["input_gates"] == len(c)
     assert p.info["host_plan_ms"] >= 0.0
+
+
+def test_plan_effort_lookahead_never_more_passes(qsim):
+    """plan_effort 1 adds groupings with one block of look-ahead and keeps the one with the fewest blocks:
+    never more passes than greedy fusion, every gate still placed once; on the 33-site lattice TFIM it
+    saves passes."""
+    cases = [W.tfim_lattice(11, 3, 10, 0.27, 0.74), W.brickwork(20, 40, seed=3), W.qft(16), W.rcs(18, seed=3)]
+    for c in cases:
+        _, ps0 = plan(qsim, c, **TC6)
+        _, ps1 = plan(qsim, c, plan_effort=1, **TC6)
+        assert len(ps1) <= len(ps0)
+    _, a = plan(qsim, cases[0], **TC6)
+    _, b = plan(qsim, cases[0], plan_effort=1, **TC6)
+    assert len(b) < len(a)
