@@ -311,7 +311,8 @@ int qsim_inner(qsim_h a, qsim_h b, double* out);
  * least opts->batch_tc_min_n qubits (default 20) are planned as fused tensor-core plans instead (k = 6
  * blocks, their state in the workspace) and enqueued after the persistent launch, with their <Z> values
  * reduced on the device: one cluster streams a wide state at a fraction of the GPU's bandwidth, a plan's
- * passes use all of it. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
+ * passes use all of it. Those plans run on four streams the batch owns, forked from the caller's stream
+ * and joined back into it, so all work of an execution is ordered before later work on that stream. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
  * <Z_q Z_{q+1}> at zz[zz_off(i) + q] (q < n_i - 1), the offsets being the running sums of n_i and n_i - 1
  * in input order; sums are compensated (float-float per thread, double-double across threads), and the
  * values are those of the normalised state (divided by the computed squared norm, which FP32 arithmetic
