@@ -15,6 +15,7 @@
 //   k_swap_tile    in-place qubit reorder through shared-memory tiles.
 //   k_set_basis    |x>.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -304,24 +305,33 @@ template <typename R, int V>
 __global__ void __launch_bounds__(256)
 k_swap_direct(typename Amp<R>::T* __restrict__ psi, uint64_t groups_v, const __grid_constant__ SwapDirectArgs a) {
     using T = typename Amp<R>::T;
+    using X = typename std::conditional<V == 2, float4, T>::type;  // one access: V adjacent amplitudes
+    constexpr int U = 4;  // items per thread and round: every load of a round is issued before its stores
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t total = groups_v * (uint64_t)a.npairs;
-    for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
-        const uint64_t m = it / groups_v, gv = it - m * groups_v;
-        const uint64_t base = insert_zeros(gv * V, a.bits, a.nb);
-        if constexpr (V == 2) {
-            float4* pu = reinterpret_cast<float4*>(psi + base + a.off_u[m]);
-            float4* pv = reinterpret_cast<float4*>(psi + base + a.off_v[m]);
-            const float4 x = *pu, y = *pv;
-            *pu = y;
-            *pv = x;
-        } else {
-            T* pu = psi + base + a.off_u[m];
-            T* pv = psi + base + a.off_v[m];
-            const T x = *pu, y = *pv;
-            *pu = y;
-            *pv = x;
+    for (uint64_t it0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it0 < total; it0 += U * stride) {
+        X* pu[U];
+        X* pv[U];
+        X x[U], y[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint64_t it = it0 + (uint64_t)k * stride;
+            pu[k] = pv[k] = nullptr;
+            if (it < total) {
+                const uint64_t m = it / groups_v, gv = it - m * groups_v;
+                const uint64_t base = insert_zeros(gv * V, a.bits, a.nb);
+                pu[k] = reinterpret_cast<X*>(psi + base + a.off_u[m]);
+                pv[k] = reinterpret_cast<X*>(psi + base + a.off_v[m]);
+                x[k] = *pu[k];
+                y[k] = *pv[k];
+            }
         }
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (pu[k]) {
+                *pu[k] = y[k];
+                *pv[k] = x[k];
+            }
     }
 }
 
