@@ -773,7 +773,8 @@ def run_tfim_batch(args):
 def run_pairs34(args):
     """34-qubit complex64 state (128 GiB): 16 layers of Haar U(4) on seeded random matchings (seed 5), the top
     4 qubits treated as global index bits (reorder passes before gates on them, identity order restored at
-    the end), then 10^5 samples (seed 6). Also timed: the same circuit addressing every qubit in place."""
+    the end), then 10^5 samples (seed 6): fused 6-qubit 3xTF32 blocks, and the plain per-gate path. Also
+    timed: the same circuit addressing every qubit in place."""
     import torch
     import workloads as W
     from paper_2511_14664_gb300 import qsim
@@ -781,8 +782,15 @@ def run_pairs34(args):
     c = W.random_pairs(n, 16, seed=5)
     st = qsim.State(n, qsim.C64)
     out = {}
-    for name, local in [("reorder_L%d" % (n - 4), n - 4), ("in_place", 0)]:
-        p = qsim.Plan(c, mode=0, max_fused=2, local_qubits=local)
+    L = n - 4
+    tc6 = dict(mode=1, max_fused=6, precision=1, tc_min_k=5)
+    variants = [("tf32x3_k6_reorder_L%d" % L, dict(tc6, local_qubits=L)), ("tf32x3_k6_in_place", dict(tc6)),
+                ("plain_reorder_L%d" % L, dict(mode=0, max_fused=2, local_qubits=L)),
+                ("plain_in_place", dict(mode=0, max_fused=2))]
+    if args.no_variants:
+        variants = variants[:1]
+    for name, kw in variants:
+        p = qsim.Plan(c, **kw)
         p.pass_list = p.passes()
         st.set_basis(0)
         p.execute(st)
@@ -810,11 +818,12 @@ def run_pairs34(args):
                      "gate_pass_gbs": gate_bytes / (gate_ms / 1000.0) / 1e9,
                      "sample_ms": evs[len(p.pass_list)].elapsed_time(evs[-1]), "norm": st.norm()}
         p.close()
-    main = "reorder_L%d" % (n - 4)
+    main = "tf32x3_k6_reorder_L%d" % L
     line = _common_line(f"gate-applications/s, {n}-qubit random U(4) pairs depth 16, complex64, reorder passes "
                         f"for {4} global qubits, 1e5 samples", out[main]["gates_per_s"], UNIT, args,
-                        out[main]["ms_total"], "f32",
-                        {"workload": f"random pairs n={n} depth 16 seed 5, {len(c)} gates, 1e5 samples seed 6"},
+                        out[main]["ms_total"], "tf32",
+                        {"workload": f"random pairs n={n} depth 16 seed 5, {len(c)} gates, 1e5 samples seed 6",
+                         "path": main},
                         paths=out)
     print(json.dumps(line))
     return 0

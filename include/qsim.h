@@ -214,13 +214,14 @@ int qsim_plan_destroy(qsim_plan_h plan);
                                    amplitude (a quadratic form of its index bits) */
 typedef struct {
     int32_t kind;             /* QSIM_PASS_* */
-    int32_t k;                /* qubits the pass's matrix acts on */
-    int32_t nc;               /* control qubits (not part of the matrix) */
+    int32_t k;                /* qubits the pass's matrix acts on (a reorder pass: exchanged pairs) */
+    int32_t nc;               /* control qubits (not part of the matrix; a reorder pass: = k) */
     int32_t precision;        /* QSIM_PREC_* used by the pass */
     int64_t gates;            /* input gates merged into this pass */
     double algorithmic_bytes; /* HBM bytes the pass must read + write */
     int32_t targets[QSIM_MAX_TARGETS];   /* index bits the matrix acts on, in the order of its index bits
-                                            (k of them; k = 0 for a reorder or phase pass) */
+                                            (k of them; k = 0 for a phase pass; a reorder pass exchanges
+                                            index bit targets[i] with controls[i], i < k) */
     int32_t controls[QSIM_MAX_CONTROLS]; /* control bits (nc of them) */
     int32_t launches;         /* kernel launches one execution of the pass makes (2 for a tensor-core block
                                  with a phase epilogue: a small kernel computes its per-tile factors first) */

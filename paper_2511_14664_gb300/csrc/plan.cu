@@ -804,6 +804,13 @@ int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
     std::memset(out->controls, 0, sizeof(out->controls));
     for (int j = 0; j < op.k && j < QSIM_MAX_TARGETS; ++j) out->targets[j] = op.targets[j];
     for (int j = 0; j < op.nc && j < QSIM_MAX_CONTROLS; ++j) out->controls[j] = op.controls[j];
+    if (op.kind == OP_SWAP) {  // the exchanged index-bit pairs: targets[i] <-> controls[i]
+        out->k = out->nc = op.nswap;
+        for (int j = 0; j < op.nswap && j < QSIM_MAX_TARGETS; ++j) {
+            out->targets[j] = op.swap_a[j];
+            out->controls[j] = op.swap_b[j];
+        }
+    }
     out->launches = op.kind == OP_TC && op.has_epi ? 2 : 1;
     out->reserved = 0;
     return QSIM_OK;

@@ -124,6 +124,10 @@ def test_global_qubits_plan(qsim):
     for q in ps:
         if q["kind"] != "reorder":
             assert all(x < L for x in q["targets"] + q["controls"])
+        else:  # exchanged index-bit pairs (the passes that restore the identity order may pair two local bits)
+            assert q["k"] == q["nc"] >= 1
+            assert any((a >= L) != (b >= L) for a, b in zip(q["targets"], q["controls"])) or q is ps[-1] or \
+                all(x["kind"] == "reorder" for x in ps[ps.index(q):])
         assert q["kind"] != "phase"
 
 
