@@ -667,13 +667,22 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             if (needs) {
                 // Look ahead: bring in, in one exchange pass, every global qubit needed by passes i..j, as long
                 // as those passes' qubits all fit among the local positions and at most 8 pairs are exchanged.
+                // Beyond pass i, also stop before the protected set leaves fewer idle local positions >= 4 than
+                // qubits to bring in: an exchange with a position below 4 moves runs shorter than 128 bytes
+                // and takes the slower shared-memory path.
                 uint64_t bring = 0, protect = 0;
                 for (size_t j = i; j < p->ops.size(); ++j) {
                     uint64_t qj = 0, gj = 0;
                     for (int q : op_qubits(p->ops[j])) { qj |= 1ull << q; if (phys[q] >= L) gj |= 1ull << q; }
-                    if (__builtin_popcountll(bring | gj) > 8 || __builtin_popcountll(protect | qj) > L) break;
-                    bring |= gj;
-                    protect |= qj;
+                    const uint64_t nb = bring | gj, np = protect | qj;
+                    if (__builtin_popcountll(nb) > 8 || __builtin_popcountll(np) > L) break;
+                    if (j > i) {
+                        int idle_hi = 0;
+                        for (int pp = 4; pp < L; ++pp) idle_hi += !((np >> logi[pp]) & 1);
+                        if (idle_hi < __builtin_popcountll(nb)) break;
+                    }
+                    bring = nb;
+                    protect = np;
                 }
                 // victims: local positions holding unprotected qubits; least recently used first, positions >= 4
                 // before lower ones (large contiguous runs keep the exchange kernel streaming)
@@ -701,36 +710,48 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             ++clock;
             out_ops.push_back(std::move(op));
         }
-        std::vector<std::pair<int, int>> restore;
-        for (int q = 0; q < n; ++q) {
-            if (phys[q] == q) continue;
-            const int pq = phys[q];
-            restore.push_back({q, pq});
-            const int lo = logi[q];  // logical qubit now at position q moves to pq
-            logi[q] = q; logi[pq] = lo;
-            phys[lo] = pq; phys[q] = q;
-        }
-        // each restore transposition touches position q, which later ones never touch again, but later ones
-        // may touch pq; emit them one pair per pass where positions repeat, otherwise batch up to 8
+        // Restore the identity order. The positions form cycles under "the logical qubit at position c belongs
+        // at position logi[c]"; a cycle (c_0 .. c_{k-1}), c_{i+1} = logi[c_i], is the product of two
+        // reflections: exchanging c_i with c_{-i}, then c_i with c_{1-i} (indices mod k), moves the content of
+        // every c_i to c_{i+1}. So two sets of disjoint exchanges restore any order; each set is emitted as
+        // passes of at most 4 pairs (the direct exchange kernel's limit).
         {
-            size_t i = 0;
-            while (i < restore.size()) {
-                PlanOp sw;
-                sw.kind = OP_SWAP;
-                sw.gates = 0;
-                uint64_t busy = 0;
-                while (i < restore.size() && sw.nswap < 8) {
-                    const auto& pr = restore[i];
-                    const uint64_t m = (1ull << pr.first) | (1ull << pr.second);
-                    if (busy & m) break;
-                    busy |= m;
-                    sw.swap_a[sw.nswap] = pr.first;
-                    sw.swap_b[sw.nswap] = pr.second;
-                    ++sw.nswap;
-                    ++i;
+            std::vector<std::pair<int, int>> inv1, inv2;
+            std::vector<char> seen(n, 0);
+            for (int c = 0; c < n; ++c) {
+                if (seen[c] || logi[c] == c) { seen[c] = 1; continue; }
+                std::vector<int> cyc;
+                for (int x = c; !seen[x]; x = logi[x]) { seen[x] = 1; cyc.push_back(x); }
+                const int k = (int)cyc.size();
+                for (int a = 0; a < k; ++a) {
+                    const int b1 = (k - a) % k, b2 = (1 - a + k) % k;
+                    if (a < b1) inv1.push_back({cyc[a], cyc[b1]});
+                    if (a < b2) inv2.push_back({cyc[a], cyc[b2]});
                 }
-                out_ops.push_back(std::move(sw));
             }
+            // check on a copy: both sets applied in order leave every position holding its own qubit
+            std::vector<int> chk = logi;
+            for (const auto* inv : {&inv1, &inv2})
+                for (const auto& pr : *inv) std::swap(chk[pr.first], chk[pr.second]);
+            for (int q = 0; q < n; ++q)
+                if (chk[q] != q) {
+                    cudaFree(p->dbuf);
+                    delete p;
+                    set_error("internal error: qubit order restore");
+                    return QSIM_EINVAL;
+                }
+            for (const auto* inv : {&inv1, &inv2})
+                for (size_t a = 0; a < inv->size(); a += 4) {
+                    PlanOp sw;
+                    sw.kind = OP_SWAP;
+                    sw.gates = 0;
+                    for (size_t b = a; b < inv->size() && b < a + 4; ++b) {
+                        sw.swap_a[sw.nswap] = (*inv)[b].first;
+                        sw.swap_b[sw.nswap] = (*inv)[b].second;
+                        ++sw.nswap;
+                    }
+                    out_ops.push_back(std::move(sw));
+                }
         }
         p->ops.swap(out_ops);
     }
