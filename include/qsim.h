@@ -42,7 +42,7 @@ extern "C" {
 #define QSIM_ENOMEM 2       /* device or host allocation failed, or the caller's buffer is too small */
 #define QSIM_ECUDA 3        /* a CUDA runtime call or kernel launch failed */
 #define QSIM_ETIMEOUT 4     /* a bounded device-side wait expired; the kernel stopped and reported it */
-#define QSIM_EUNSUPPORTED 5 /* valid request that this build does not implement (e.g. k too large) */
+#define QSIM_EUNSUPPORTED 5 /* valid request that the library does not implement (e.g. k too large) */
 
 /* Amplitude types. */
 #define QSIM_C64 0  /* complex64: float32 real and imaginary parts */
