@@ -186,6 +186,8 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
 
 constexpr int kEpiGroups = kRowBits + 1 + 5;  // row bits, the half bit, up to 5 other column bits
 constexpr int kEpiTile = 1 + kEpiGroups;     // factors per tile
+constexpr int kBarBytes = 64;                 // shared memory for the mbarriers and the TMEM slot
+constexpr int kEpiThrBytes = 2 * 128 * 6 * 8; // the epilogue's per-thread factors (float2)
 
 struct Args {
     int nS;            // K + 7 index bits covered by a tile
@@ -300,6 +302,9 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + P * PB);
     uint64_t* mbar = sCol + D;                             // empty[0..P), full[0..P), then B loaded
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2 * P + 1);
+    // EPI: the per-thread factors (row / H term and V-bit coefficients of each (half, row)), transposed so
+    // that a warp reads 32 consecutive entries: sTh[k * 256 + half * 128 + row]
+    [[maybe_unused]] float2* sTh = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(sCol + D) + kBarBytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;
@@ -310,6 +315,9 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     // issued after the barrier below; only the MMA issuer waits for them, so the data warps' first tile
     // loads overlap the copy.
     for (int c = tid; c < D; c += kThreadsWS) sCol[c] = deposit((uint64_t)(LG ? line_perm(c) : c), a.tpos, K);
+    if constexpr (EPI) {  // plan data, written before the kernels that precede this one
+        for (int i = tid; i < 2 * 128 * 6; i += kThreadsWS) sTh[(i % 6) * 256 + i / 6] = a.epi_thr[i];
+    }
     if (tid == 0) {
         for (int j = 0; j < 2 * P + 1; ++j)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
@@ -565,7 +573,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
         const int half = (warp >> 2) & 1;
         auto epi_factors = [&](uint64_t t, float2 (&E)[NV + 1]) {
             const float2* tf = a.epi_tiles + t * kEpiTile;
-            const float2* th = a.epi_thr + (uint64_t)(half * 128 + r) * 6;
+            const float2* th = sTh + half * 128 + r;  // th[k * 256]: factor k of this thread's (half, row)
             float2 e0 = cmul(tf[0], th[0]);
 #pragma unroll
             for (int g = 0; g < kRowBits; ++g)
@@ -573,7 +581,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
             if (half) e0 = cmul(e0, tf[1 + kRowBits]);
             E[0] = e0;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) E[1 + v] = cmul(tf[2 + kRowBits + v], th[1 + v]);
+            for (int v = 0; v < NV; ++v) E[1 + v] = cmul(tf[2 + kRowBits + v], th[256 * (1 + v)]);
         };
         auto epilogue = [&](uint64_t t, uint32_t dcol) {
             const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
@@ -919,7 +927,9 @@ template <int PREC> constexpr int planes_of() { return Cfg<PREC>::planes; }
 template <int PREC> constexpr int esize_of() { return Cfg<PREC>::esize; }
 
 size_t smem_bytes(int K, int planes, int esize) {
-    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + 64 + 1024;  // + barriers, TMEM slot
+    // B planes, column offsets, barriers and the TMEM slot, the epilogue's per-thread factors, alignment
+    const size_t need = (size_t)planes * plane_bytes(K, esize) + sizeof(uint64_t) * (1 << K) + kBarBytes +
+                        kEpiThrBytes + 1024;
     return std::max<size_t>(need, 120 * 1024);  // at most one CTA (and one TMEM owner) per SM
 }
 
