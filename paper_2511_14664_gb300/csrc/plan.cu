@@ -637,12 +637,14 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         for (int q = 0; q < n; ++q) phys[q] = logi[q] = q;
         std::vector<PlanOp> out_ops;
         int64_t clock = 0;
+        // passes of at most 4 pairs: the direct exchange kernel's limit (more pairs take the slower
+        // shared-memory path, so two direct passes cost less than one of 5..8 pairs)
         auto emit_swaps = [&](const std::vector<std::pair<int, int>>& pairs) {
-            for (size_t i = 0; i < pairs.size(); i += 8) {
+            for (size_t i = 0; i < pairs.size(); i += 4) {
                 PlanOp sw;
                 sw.kind = OP_SWAP;
                 sw.gates = 0;
-                for (size_t j = i; j < pairs.size() && j < i + 8; ++j) {
+                for (size_t j = i; j < pairs.size() && j < i + 4; ++j) {
                     sw.swap_a[sw.nswap] = pairs[j].first;
                     sw.swap_b[sw.nswap] = pairs[j].second;
                     ++sw.nswap;
@@ -665,8 +667,9 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             bool needs = false;
             for (int q : op_qubits(op)) needs |= phys[q] >= L;
             if (needs) {
-                // Look ahead: bring in, in one exchange pass, every global qubit needed by passes i..j, as long
-                // as those passes' qubits all fit among the local positions and at most 8 pairs are exchanged.
+                // Look ahead: bring in, in one exchange, every global qubit needed by passes i..j, as long as
+                // those passes' qubits all fit among the local positions and at most 4 pairs are exchanged
+                // (pass i alone may need up to 8).
                 // Beyond pass i, also stop before the protected set leaves fewer idle local positions >= 4 than
                 // qubits to bring in: an exchange with a position below 4 moves runs shorter than 128 bytes
                 // and takes the slower shared-memory path.
@@ -675,7 +678,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                     uint64_t qj = 0, gj = 0;
                     for (int q : op_qubits(p->ops[j])) { qj |= 1ull << q; if (phys[q] >= L) gj |= 1ull << q; }
                     const uint64_t nb = bring | gj, np = protect | qj;
-                    if (__builtin_popcountll(nb) > 8 || __builtin_popcountll(np) > L) break;
+                    if (__builtin_popcountll(nb) > (j > i ? 4 : 8) || __builtin_popcountll(np) > L) break;
                     if (j > i) {
                         int idle_hi = 0;
                         for (int pp = 4; pp < L; ++pp) idle_hi += !((np >> logi[pp]) & 1);

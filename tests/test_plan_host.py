@@ -150,3 +150,24 @@ def test_plan_effort_lookahead_never_more_passes(qsim):
     _, a = plan(qsim, cases[0], **TC6)
     _, b = plan(qsim, cases[0], plan_effort=1, **TC6)
     assert len(b) < len(a)
+
+
+@pytest.mark.parametrize("L", [16, 18, 22])
+def test_global_qubit_reorders_restore_identity(qsim, L):
+    """Following a plan's reorder passes as exchanges of index bits, every gate pass must find its qubits
+    at local positions and the order must be the identity again after the last pass; the exchanges use
+    positions >= 4 and at most 4 pairs per pass (the direct exchange kernel)."""
+    n = 24
+    c = W.random_pairs(n, 6, seed=7)
+    for kw in (dict(mode=1, max_fused=6, precision=1, tc_min_k=5), dict(mode=0, max_fused=2)):
+        p, ps = plan(qsim, c, local_qubits=L, **kw)
+        logi = list(range(n))  # position -> logical qubit
+        for q in ps:
+            if q["kind"] == "reorder":
+                assert 1 <= q["k"] <= 4
+                for a, b in zip(q["targets"], q["controls"]):
+                    assert a >= 4 and b >= 4
+                    logi[a], logi[b] = logi[b], logi[a]
+            else:
+                assert all(x < L for x in q["targets"] + q["controls"])
+        assert logi == list(range(n))
