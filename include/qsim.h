@@ -124,9 +124,11 @@ typedef struct {
 
 /* ---- version and errors ------------------------------------------------------------------------------ */
 
+/* Version of this ABI (library service, no passage). */
 int qsim_abi_version(void);
 
-/* Message of the last failed call on this thread ("" if none). Valid until the next call. */
+/* Message of the last failed call on this thread ("" if none). Valid until the next call. Library service, no
+   passage. */
 const char* qsim_last_error(void);
 
 /* Bytes of a 2^n state of `dtype` (8 or 16 bytes per amplitude; Sec. 1: 2^(n-27) GiB at FP32). */
@@ -135,7 +137,8 @@ int qsim_state_bytes(int n, int dtype, size_t* out);
 /* ---- state lifetime ---------------------------------------------------------------------------------- */
 
 /*
- * Create a handle for an n-qubit state (1 <= n <= QSIM_MAX_QUBITS) of `dtype`.
+ * Create a handle for an n-qubit state (1 <= n <= QSIM_MAX_QUBITS) of `dtype` (Sec. 2.1 "State-Vector
+ * Simulation": the 2^n-amplitude vector the simulation stores; Sec. 1: its memory doubles per qubit).
  * dev_buf: device buffer of at least qsim_state_bytes(n, dtype) bytes, 256-byte aligned, owned by the
  *          caller, who keeps it alive until qsim_destroy; or NULL, in which case the library allocates
  *          (and later frees) the state with cudaMalloc.
@@ -144,19 +147,33 @@ int qsim_state_bytes(int n, int dtype, size_t* out);
  * small device workspace for reductions (about 2^(n-9) bytes + 4 MiB).
  */
 int qsim_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, qsim_h* out);
+/* Release the handle (after its stream completes) and the state if the library allocated it. Library
+   service, no passage. NULL is accepted. */
 int qsim_destroy(qsim_h h);
+/* Bind later calls to another cudaStream_t. Library service, no passage. */
 int qsim_set_stream(qsim_h h, void* stream);
+/* The handle's n (Sec. 2.1: the number of qubits fixes the vector length 2^n). */
 int qsim_num_qubits(qsim_h h, int* n);
+/* Device address of amplitude 0 (layout above). Library service, no passage. */
 int qsim_device_ptr(qsim_h h, void** out);
 
 /* |x>: amplitude x = 1, all others 0 (Sec. 2.1: a basis state). x < 2^n. */
 int qsim_set_basis(qsim_h h, uint64_t x);
-/* Copy a whole state in (src) or out (dst); *_on_device = 1 for device pointers, 0 for host. */
+/* Copy a whole state in (src) or out (dst); *_on_device = 1 for device pointers, 0 for host (Sec. 2.1
+   "State-Vector Simulation": the full amplitude vector; also a checkpoint of a run). Copies to the host
+   synchronise and report a set device error word. */
 int qsim_set_state(qsim_h h, const void* src, int src_on_device);
 int qsim_get_state(qsim_h h, void* dst, int dst_on_device);
 /* Wait for all work enqueued on h's stream and report any device-side error (QSIM_ETIMEOUT when a
-   bounded wait expired, QSIM_ECUDA for a CUDA error). */
+   bounded wait expired, QSIM_ECUDA for a CUDA error). Library service, no passage. */
 int qsim_synchronize(qsim_h h);
+/* Failure injection for tests of a caller's recovery path (a library service; the paper has no counterpart).
+   After the work already enqueued on h's stream completes, `code` (nonzero; bit 0 = "a bounded device-side
+   wait expired") is written into h's device error word from the host, exactly as a kernel whose bounded wait
+   ran out would leave it. No kernel runs and nothing waits on the GPU. The next call that checks the word
+   (qsim_synchronize, a readout, qsim_get_state to host) returns QSIM_ETIMEOUT and clears it; the handle stays
+   usable. Synchronises. */
+int qsim_inject_device_error(qsim_h h, unsigned code);
 
 /* ---- gate application (the hot path; Sec. 2.1, cost O(g 2^n)) --------------------------------------- */
 
@@ -188,20 +205,23 @@ int qsim_swap_qubits(qsim_h h, const int* a, const int* b, int p);
 /* ---- circuits and plans ---------------------------------------------------------------------------- */
 
 /*
- * Plan a circuit for states of c->n qubits and `dtype`: fusion into blocks (QSIM_RUN_FUSED), choice of
+ * Plan a circuit (Sec. 2.1: gate fusion merges gates into larger matrices; Sec. 2.2: the fusion level is
+ * tuned per architecture and precision) for states of c->n qubits and `dtype`: fusion into blocks (QSIM_RUN_FUSED), choice of
  * kernel per block, and FP64 composition of each fused block on the device (enqueued on `stream`).
  * The plan owns its device buffers; it can be executed on any handle with matching n and dtype.
  * info may be NULL.
  */
 int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts, void* stream,
                      qsim_plan_h* out, qsim_plan_info* info);
-/* Enqueue every pass of the plan on h's stream. Asynchronous. */
+/* Enqueue every pass of the plan on h's stream (Sec. 2.1: the gates applied to the state in order).
+   Asynchronous. */
 int qsim_plan_execute(qsim_h h, qsim_plan_h plan);
 /* qsim_set_basis(h, x) then passes [0, count) of the plan (count < 0: all of them), on h's stream (no
    graph). When the plan starts with a tensor-core block (3xTF32 or BF16x3) that block generates |x> as its
    input instead of reading the state, and writes every amplitude, so neither the set-up pass nor the
    block's reads happen. QSIM_EINVAL for x >= 2^n or count > the number of passes. */
 int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h plan, uint64_t x, int64_t count);
+/* Release a plan and its device buffers. Library service, no passage. NULL is accepted. */
 int qsim_plan_destroy(qsim_plan_h plan);
 
 /* One pass of a plan, for per-kernel timing and roofline accounting. */
@@ -227,12 +247,14 @@ typedef struct {
                                  with a phase epilogue: a small kernel computes its per-tile factors first) */
     int32_t reserved;
 } qsim_pass_info;
+/* Number of passes and the description of pass i (Sec. 2.1: after fusion, each pass is one application of a
+   fused matrix to the whole vector). Host only; also for dry-run plans. */
 int qsim_plan_num_passes(qsim_plan_h plan, int64_t* out);
 int qsim_plan_pass_info(qsim_plan_h plan, int64_t i, qsim_pass_info* out);
-/* Enqueue passes [first, first + count) of the plan on h's stream (no graph). */
+/* Enqueue passes [first, first + count) of the plan on h's stream (no graph; Sec. 2.1, gates in order). */
 int qsim_plan_execute_range(qsim_h h, qsim_plan_h plan, int64_t first, int64_t count);
-/* Plan, execute and destroy in one call (the plan's device buffers are released after the stream
-   completes the run). */
+/* Plan, execute and destroy in one call (Sec. 2.1: fusion, then the fused gates applied in order; the plan's
+   device buffers are released after the stream completes the run). */
 int qsim_run(qsim_h h, const qsim_circuit* c, const qsim_run_opts* opts, qsim_plan_info* info);
 
 /* ---- readout (Sec. 2.1 "Measurement and Sampling"; Sec. 2.5 expectation values) --------------------- */
@@ -288,7 +310,11 @@ int qsim_expect_z_and_sample(qsim_h h, double* zi, double* zz, uint64_t seed, in
  * (a cudaStream_t; NULL = legacy default stream) and returns; dev_out is valid once the stream completes.
  * It allocates nothing: its scratch is one fixed 8 MiB array inside the library image, present on every
  * GPU that loads the library until the process exits. Requests needing more scratch than that (8 bytes
- * per shot plus 8 bytes per 4096 amplitudes, rounded up per region) fail with QSIM_EINVAL before any work.
+ * per shot plus 8 bytes per 4096 amplitudes, each region rounded up to 256 bytes) fail with QSIM_EINVAL
+ * before any work: so n >= 32 is always refused (the 2^(n-12) segment sums alone fill the array), n = 31
+ * allows 523 776 shots, n = 30 786 176, n = 22 1 047 520, and no n more than 2^20 = 1 048 576.
+ * dev_state must be 256-byte aligned (like a state buffer given to qsim_create) and dev_out 8-byte
+ * aligned; QSIM_EINVAL otherwise, before any work.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture. All calls share the array: calls whose work overlaps on the GPU race,
  * so serialise them (one stream, one host thread at a time).
@@ -296,7 +322,8 @@ int qsim_expect_z_and_sample(qsim_h h, double* zi, double* zz, uint64_t seed, in
 int qsim_sample_noalloc(const void* dev_state, int n, int dtype, uint64_t seed, int64_t shots,
                         uint64_t* dev_out, void* stream);
 
-/* <a|b> for two handles of equal n and dtype on the same device. out[0..1] = (re, im). Synchronises. */
+/* <a|b> = sum_x conj(a_x) b_x for two handles of equal n and dtype on the same device (Sec. 2.1: the
+   amplitudes of the two state vectors; the overlap behind a fidelity). out[0..1] = (re, im). Synchronises. */
 int qsim_inner(qsim_h a, qsim_h b, double* out);
 
 /* ---- batches of independent circuits (one persistent launch) ---------------------------------------- */
@@ -330,6 +357,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
 int qsim_batch_execute(qsim_batch_h b, void* dev_ws, size_t ws_bytes, void* stream, int use_graph);
 /* Copy the last execution's <Z> values to host arrays zi, zz (see above for the layout). Synchronises. */
 int qsim_batch_results(qsim_batch_h b, void* stream, double* zi, double* zz);
+/* Release a batch plan and its device buffers. Library service, no passage. NULL is accepted. */
 int qsim_batch_destroy(qsim_batch_h b);
 /* Plan, execute, fetch results and destroy in one call. */
 int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws,

@@ -262,6 +262,15 @@ int qsim_synchronize(qsim_h h) {
     return check_device_error(h);
 }
 
+int qsim_inject_device_error(qsim_h h, unsigned code) {
+    QSIM_CHECK_HANDLE(h);
+    if (!code) { set_error("code must be nonzero"); return QSIM_EINVAL; }
+    // after the work already enqueued, so that the word is not cleared or overwritten behind the caller
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h->derr, &code, sizeof(unsigned), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "writing the device error word");
+}
+
 int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, int nc, const double* matrix) {
     QSIM_CHECK_HANDLE(h);
     int rc = validate_qubits(h->n, targets, k, controls, nc, QSIM_MAX_TARGETS);

@@ -56,6 +56,19 @@ extern "C" int qsim_sample_noalloc(const void* dev_state, int n, int dtype, uint
     if (n < 1 || n > QSIM_MAX_QUBITS) { set_error("n = %d outside 1..%d", n, QSIM_MAX_QUBITS); return QSIM_EINVAL; }
     if (dtype != QSIM_C64 && dtype != QSIM_C128) { set_error("unknown dtype %d", dtype); return QSIM_EINVAL; }
     if (shots < 0) { set_error("negative number of shots"); return QSIM_EINVAL; }
+    // Before any size arithmetic: a request for more shots than the scratch holds uniforms fails here, so
+    // 8 * shots below cannot wrap around.
+    if ((uint64_t)shots > kNoAllocBytes / 8) {
+        set_error("%lld shots exceed the %zu uniforms the static scratch can hold", (long long)shots,
+                  kNoAllocBytes / 8);
+        return QSIM_EINVAL;
+    }
+    // The sampling kernels read the state with 16-byte vector loads and write 8-byte indices.
+    if (reinterpret_cast<uintptr_t>(dev_state) & 255) {
+        set_error("dev_state must be 256-byte aligned (as a state buffer given to qsim_create)");
+        return QSIM_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(dev_out) & 7) { set_error("dev_out must be 8-byte aligned"); return QSIM_EINVAL; }
     if (shots == 0) return QSIM_OK;
     // Scratch layout: uniforms (shots doubles) | segment sums (nseg) | chunk prefix sums (nchunk), each
     // region 256-byte aligned.

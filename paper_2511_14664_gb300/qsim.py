@@ -80,6 +80,7 @@ SIGNATURES = {
     "qsim_set_state": ([_vp, _vp, _i], _i),
     "qsim_get_state": ([_vp, _vp, _i], _i),
     "qsim_synchronize": ([_vp], _i),
+    "qsim_inject_device_error": ([_vp, ctypes.c_uint], _i),
     "qsim_apply_gate": ([_vp, _P(_i), _i, _P(_i), _i, _P(ctypes.c_double)], _i),
     "qsim_apply_fused": ([_vp, _P(_i), _i, _P(ctypes.c_double), _i], _i),
     "qsim_swap_qubits": ([_vp, _P(_i), _P(_i), _i], _i),

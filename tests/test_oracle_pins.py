@@ -248,6 +248,57 @@ def test_splitmix64_uniforms():
     assert oracle.splitmix64(2024, 5) >> 11 == int(round(u[5] * 2**53))
 
 
+def test_splitmix64_published_vector():
+    """The oracle's generator against the published SplitMix64 outputs for seed 1234567 (a wrong increment,
+    shift or finaliser constant changes every one of them), and the uniforms as their top 53 bits."""
+    g = load_golden("splitmix64.json")
+    want = [int(v) for v in g["outputs"]]
+    assert [oracle.splitmix64(g["seed"], i) for i in range(len(want))] == want
+    u = oracle.uniforms(g["seed"], len(want))
+    assert [int(x * 2**53) for x in u] == [v >> 11 for v in want]
+
+
+# ---- inner product and infidelity (the checker behind every GPU parity bound) ------------------------------
+def test_inner_hand_values():
+    """<a|b> = sum_x conj(a_x) b_x (Sec. 2.1: amplitudes of basis states), on values fixed by hand: the
+    conjugate sits on the left operand, so <a|i a> = +i and <i a|a> = -i."""
+    s = 1 / math.sqrt(2)
+    zero = np.array([1, 0], dtype=np.complex128)
+    plus = np.array([s, s], dtype=np.complex128)
+    assert abs(oracle.inner(zero, plus, 1) - s) <= 1e-16
+    a = np.array([0.6, 0.8j], dtype=np.complex128)      # |a|^2 = 1
+    assert abs(oracle.inner(a, a, 1) - 1.0) <= 1e-15
+    assert abs(oracle.inner(a, 1j * a, 1) - 1j) <= 1e-15
+    assert abs(oracle.inner(1j * a, a, 1) + 1j) <= 1e-15
+    b = np.array([1, 1j], dtype=np.complex128)          # <a|b> = 0.6 + conj(0.8 i) i = 0.6 + 0.8
+    assert abs(oracle.inner(a, b, 1) - 1.4) <= 1e-15
+    c = np.array([1j, 0], dtype=np.complex128)          # <a|c> = 0.6 i, <c|a> = -0.6 i
+    assert abs(oracle.inner(a, c, 1) - 0.6j) <= 1e-15
+    assert abs(oracle.inner(c, a, 1) + 0.6j) <= 1e-15
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_inner_matches_numpy_vdot(seed):
+    n = 9
+    a, b = random_state(n, seed), random_state(n, seed + 100) * (0.3 - 0.7j)
+    assert abs(oracle.inner(a, b, n) - np.vdot(a, b)) <= 1e-13
+
+
+def test_infidelity_special_cases():
+    """1 - |<a|b>|^2 / (<a|a><b|b>) (normalised) and 1 - |<a|b>|^2 (unnormalised) on closed forms."""
+    zero = np.array([1, 0], dtype=np.complex128)
+    one = np.array([0, 1], dtype=np.complex128)
+    assert oracle.infidelity(zero, one, 1) == pytest.approx(1.0, abs=1e-15)         # orthogonal
+    psi = random_state(8, 5)
+    assert oracle.infidelity(psi, np.exp(0.7j) * psi, 8) <= 1e-14                   # global phase
+    for th in (0.0, 0.3, 1.0, math.pi / 3):
+        v = np.array([math.cos(th), math.sin(th)], dtype=np.complex128)
+        assert oracle.infidelity(v, zero, 1) == pytest.approx(math.sin(th) ** 2, abs=1e-15)
+    two = 2.0 * psi                                                                  # norms 1 and 4
+    assert oracle.infidelity(psi, two, 8) <= 1e-14
+    assert oracle.infidelity(psi, two, 8, normalised=False) == pytest.approx(1.0 - 4.0, abs=1e-12)
+
+
 # ---- QPE with exactly representable phases ------------------------------------------------------------
 @pytest.mark.parametrize("t,a", [(3, 5), (5, 17), (7, 100), (8, 255)])
 def test_qpe_exact_phase(t, a):
