@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--no-variants", action="store_true", help="skip the secondary path measurements")
     p.add_argument("--no-accuracy", action="store_true", help="skip the 20-qubit infidelity check")
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other configurations' runs after the headline line (N = 1 only)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--count", type=int, default=256, help="tfim_batch: number of circuits")
     p.add_argument("--nmax", type=int, default=24, help="tfim_batch: largest circuit width")
@@ -190,6 +192,25 @@ def profiled_traffic(kind, n):
     return None
 
 
+def tensor_rates(qsim, uuid, seconds):
+    """Dense tensor-core rates of this GPU, measured live: an MMA-only tcgen05 loop on every SM in the form the
+    block kernels issue (A in tensor memory, B in shared memory, M = N = 128, FP32 accumulation), `seconds`
+    per operand type, SM clocks sampled meanwhile."""
+    clocks = Clocks(uuid)
+    clocks.start()
+    out = {}
+    for kind in ("tf32", "bf16", "fp16"):
+        out[kind] = qsim.tc_peak(kind, 128, seconds)[0]
+    clk = clocks.stop()
+    out.update({"unit": "TFLOP/s", "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+                "how": f"tcgen05 MMA-only loop, one CTA per SM, A in TMEM, B in SMEM (SW128), M = N = 128, "
+                       f"{seconds:g} s per type, CUDA events"})
+    return out
+
+
+PREC_RATE = {1: "tf32", 2: "bf16", 3: "bf16"}
+
+
 # ---- the simulation step -------------------------------------------------------------------------------------
 PATHS = {
     # name: (mode, max_fused, precision, tc_min_k)
@@ -278,29 +299,53 @@ def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
     return t0.elapsed_time(t1), pass_ms
 
 
-def infidelity_at(qsim, W, n_small, depth, path, ref_cache):
-    """Accuracy of a path on the n_small-qubit instance of the same generator, against the complex128
-    per-gate path of this library (itself checked against the FP64 oracle by the test suite):
-    normalised infidelity 1 - |<ref|psi>|^2 / (<ref|ref><psi|psi>), max amplitude error, norm deviation."""
-    import numpy as np
+def path_states_at(qsim, W, n_small, depth, paths):
+    """Final complex64 states of every path on the n_small-qubit instance of the same generator (accuracy is
+    judged on this instance: the full-size state has no FP64 reference)."""
     c = W.brickwork(n_small, depth, seed=SEED)
-    if "ref" not in ref_cache:
-        rp = qsim.Plan(c, qsim.C128, mode=0, max_fused=1)
-        rs = qsim.State(n_small, qsim.C128)
-        rs.set_basis(0)
-        rp.execute(rs)
-        ref_cache["ref"] = rs.get_state()
-    ref = ref_cache["ref"]
-    plan = make_plan(qsim, c, path)
+    out = {}
     st = qsim.State(n_small, qsim.C64)
-    st.set_basis(0)
-    plan.execute(st)
-    psi = st.get_state().astype(np.complex128)
-    err = float(np.max(np.abs(psi - ref)))
-    nr, npsi = float(np.vdot(ref, ref).real), float(np.vdot(psi, psi).real)
-    inf = max(0.0, 1.0 - abs(np.vdot(ref, psi)) ** 2 / (nr * npsi))
-    return {"n": n_small, "infidelity": inf, "max_amp_err": err, "norm_dev": abs(npsi - 1.0),
-            "reference": "complex128 per-gate path"}
+    for path in paths:
+        plan = make_plan(qsim, c, path)
+        st.set_basis(0)
+        plan.execute(st)
+        out[path] = st.get_state().astype("complex128")
+        plan.close()
+    st.close()
+    return c, out
+
+
+def accuracy_vs(ref, states, label):
+    """Per path: normalised infidelity 1 - |<ref|psi>|^2 / (<ref|ref><psi|psi>), max amplitude error and norm
+    deviation against `ref`."""
+    import numpy as np
+    acc = {}
+    nr = float(np.vdot(ref, ref).real)
+    for name, psi in states.items():
+        npsi = float(np.vdot(psi, psi).real)
+        inf = max(0.0, 1.0 - abs(np.vdot(ref, psi)) ** 2 / (nr * npsi))
+        acc[name] = {"n": int(round(math.log2(len(ref)))), "infidelity": inf,
+                     "max_amp_err": float(np.max(np.abs(psi - ref))), "norm_dev": abs(npsi - 1.0), "reference": label}
+    return acc
+
+
+def gpu_c128_reference(qsim, c):
+    """The library's complex128 per-gate path on the same circuit (used only when the oracle leg is off)."""
+    rp = qsim.Plan(c, qsim.C128, mode=0, max_fused=1)
+    rs = qsim.State(c.n, qsim.C128)
+    rs.set_basis(0)
+    rp.execute(rs)
+    ref = rs.get_state()
+    rp.close()
+    rs.close()
+    return ref
+
+
+def oracle_reference(oracle_mod, c):
+    """cpu_baseline leg: the FP64 oracle's final state of the accuracy instance, and the seconds it took."""
+    t = time.perf_counter()
+    ref = oracle_mod.run(c)
+    return ref, time.perf_counter() - t
 
 
 def cpu_baseline(oracle_mod, W, n_full, depth, seconds):
@@ -392,12 +437,17 @@ def run_ours(args):
             plans[name].pass_list = plans[name].passes()
         except qsim.QsimError:
             pass
-    # accuracy of each path on the 20-qubit instance (equal-accuracy comparison)
-    acc = {}
+    # accuracy of each path on the 20-qubit instance (equal-accuracy comparison), against the FP64 oracle
+    # (the cpu_baseline leg, rank 0 at N = 1) or else the library's complex128 per-gate path
+    acc, oracle_acc_s = {}, None
     if rank == 0 and not args.no_accuracy:
-        cache = {}
-        for name in plans:
-            acc[name] = infidelity_at(qsim, W, min(20, n), depth, name, cache)
+        c_small, states = path_states_at(qsim, W, min(20, n), depth, list(plans))
+        if ws == 1 and not args.no_cpu:
+            import oracle as oracle_mod
+            ref, oracle_acc_s = oracle_reference(oracle_mod, c_small)
+            acc = accuracy_vs(ref, states, "FP64 oracle")
+        else:
+            acc = accuracy_vs(gpu_c128_reference(qsim, c_small), states, "complex128 per-gate path of this library")
 
     def quick(name, steps=1, warm=1):
         p = plans[name]
@@ -419,6 +469,8 @@ def run_ours(args):
     else:
         main = args.path
     plan = plans[main]
+
+    rates = tensor_rates(qsim, uuid, 1.5 if args.steps >= 3 else 0.5)
 
     # ---- the timed region -------------------------------------------------------------------------------
     timed_steps(qsim, torch, st, plan, args.warmup, shots, per_pass=True)
@@ -458,9 +510,10 @@ def run_ours(args):
     if dom == "tc" and dk["flops"] > 0:
         tflops = dk["flops"] / dk["launches"] / avg_s / 1e12
         prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == "tc"][0]]["precision"]
-        # tf32 rate = measured bf16 rate x nominal tf32/bf16 ratio (1.1 / 2.25)
-        tpeak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25 if prec == 1 else 1.0)
-        roof["tensor"] = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak}
+        # the rate of the products' operand type, measured on this GPU in this run (tensor_rates)
+        tpeak = rates[PREC_RATE[prec]]
+        roof["tensor"] = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                          "peak_source": f"measured: {PREC_RATE[prec]} MMA-only loop on this GPU, this run"}
         if tflops / tpeak > hbm_frac:
             roof = {**roof, "bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": tflops / tpeak}
@@ -512,15 +565,64 @@ def run_ours(args):
         "variants": variants,
         "accuracy": acc,
         "plan_ms": plan.info["host_plan_ms"],
+        "tensor_rates": rates,
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle as oracle_mod
         line["cpu_baseline"] = cpu_baseline(oracle_mod, W, n, depth, args.cpu_seconds)
+        if oracle_acc_s is not None:
+            line["cpu_baseline"]["accuracy_reference"] = (
+                f"FP64 oracle on the {min(20, n)}-qubit instance of the generator ({oracle_acc_s:.1f} s on "
+                f"{oracle_mod.num_threads()} cores); every path's accuracy line is measured against it")
+    if rank == 0 and ws == 1 and not args.no_configs:
+        # the other configurations, each in a process of its own after this one's timed region: full lines
+        # to gpurun_out/bench_configs.jsonl, a summary of each in this line
+        del st, plans, plan
+        torch.cuda.empty_cache()
+        line["configs"] = run_other_configs()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+OTHER_CONFIGS = [
+    # (workload, extra arguments): bounded runs of the other configurations of the benchmark set
+    ("brick14", ["--steps", "10", "--warmup", "3"]),
+    ("qft28", ["--steps", "3", "--warmup", "1"]),
+    ("tfim_batch", ["--steps", "5", "--warmup", "2", "--no-variants", "--cpu-seconds", "3"]),
+    ("pairs34", ["--steps", "1", "--warmup", "1", "--no-variants"]),
+]
+
+
+def run_other_configs():
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    os.makedirs(out_dir, exist_ok=True)
+    summary = {}
+    with open(os.path.join(out_dir, "bench_configs.jsonl"), "w") as f:
+        for wl, extra in OTHER_CONFIGS:
+            cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", wl, *extra]
+            t = time.perf_counter()
+            try:
+                r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+                lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+                rec = json.loads(lines[-1]) if (r.returncode == 0 and lines) else None
+                err = None if rec else (r.stderr.strip().splitlines() or ["no output"])[-1][:300]
+            except Exception as e:  # a failed secondary run must not take the headline line with it
+                rec, err = None, f"{type(e).__name__}: {e}"[:300]
+            wall = time.perf_counter() - t
+            if rec is None:
+                summary[wl] = {"error": err, "wall_s": wall}
+                continue
+            f.write(json.dumps(rec) + "\n")
+            summary[wl] = {k: rec.get(k) for k in ("metric", "value", "unit", "ms_per_step", "dtype")}
+            summary[wl]["path"] = rec.get("config", {}).get("path")
+            summary[wl]["wall_s"] = wall
+            for k in ("roofline", "accuracy_vs_oracle", "e2e"):
+                if k in rec:
+                    summary[wl][k] = rec[k]
+    return summary
 
 
 # ---- secondary workloads (their own JSON lines; the default run prints only the headline line) -----------------
@@ -560,6 +662,7 @@ def run_brick14(args):
     peaks, _ = measured_peaks()
     out = {}
     ref = None
+    finals = {}
     for name, kw in [("plain", dict(mode=0, max_fused=1)), ("simt2", dict(mode=1, max_fused=2)),
                      ("simt3", dict(mode=1, max_fused=3)), ("simt4", dict(mode=1, max_fused=4)),
                      ("simt5", dict(mode=1, max_fused=5))]:
@@ -573,6 +676,7 @@ def run_brick14(args):
         steps = max(10, args.steps)
         ms = _event_time(torch, step, steps)
         psi = st.get_state()
+        finals[name] = psi
         if ref is None:
             ref = psi
         out[name] = {"ms_per_step": ms, "gates_per_s": len(c) / (ms / 1000.0), "passes": p.info["passes"],
@@ -607,6 +711,20 @@ def run_brick14(args):
                              "d2h_bytes_per_step": int(v.nbytes)})
     line["steps"] = max(10, args.steps)
     line["warmup"] = max(3, args.warmup)
+    if not args.no_cpu:
+        # cpu_baseline leg: the FP64 oracle on the same circuit (timed), and every path's final vector against it
+        import oracle as oracle_mod
+        t = time.perf_counter()
+        ref = oracle_mod.run(c)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": len(c) / dt, "unit": UNIT, "cores": oracle_mod.num_threads(),
+                                "kind": "oracle", "sample": f"the whole {len(c)}-gate circuit once ({dt * 1e3:.1f} ms)"}
+        acc = {}
+        for name, psi in finals.items():
+            ov = np.vdot(ref, psi)
+            acc[name] = {"max_abs_err": float(np.max(np.abs(psi - ref))),
+                         "infidelity": max(0.0, 1.0 - abs(ov) ** 2 / (np.vdot(ref, ref).real * np.vdot(psi, psi).real))}
+        line["accuracy_vs_oracle"] = acc
     print(json.dumps(line))
     return 0
 
@@ -766,6 +884,17 @@ def run_tfim_batch(args):
         line["cpu_baseline"] = {"value": gates / est, "unit": UNIT, "cores": oracle_mod.num_threads(),
                                 "kind": "oracle", "sample": f"{used} smallest circuits in {dt:.1f} s, extrapolated "
                                                             f"to the batch by work = gates x 2^n"}
+        # accuracy: <Z_i>, <Z_i Z_i+1> of the circuits the oracle ran, plus the two shortest circuits among
+        # those planned for the tensor cores (>= tc_min_n qubits), against the oracle's
+        wide = sorted((i for i in range(len(cs)) if cs[i].n >= tc_min_n), key=lambda i: len(cs[i]) * 2.0 ** cs[i].n)[:2]
+        dzi = dzz = 0.0
+        for i in order[:used] + wide:
+            zi_r, zz_r = oracle_mod.expect_z_chain(oracle_mod.run(cs[i]), cs[i].n)
+            dzi = max(dzi, float(np.max(np.abs(res[i][0] - zi_r))))
+            dzz = max(dzz, float(np.max(np.abs(res[i][1] - zz_r)))) if cs[i].n > 1 else dzz
+        line["accuracy_vs_oracle"] = {"max_abs_dzi": dzi, "max_abs_dzz": dzz, "circuits": used + len(wide),
+                                      "widths": sorted({cs[i].n for i in order[:used] + wide}),
+                                      "tensor_core_circuits": [cs[i].n for i in wide]}
     print(json.dumps(line))
     return 0
 

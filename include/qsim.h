@@ -51,7 +51,10 @@ extern "C" {
 /* Arithmetic used for fused dense blocks (Sec. 2.1: fusion trades flops for arithmetic intensity). */
 #define QSIM_PREC_SIMT 0   /* CUDA-core FMA in the state's own precision */
 #define QSIM_PREC_TF32X3 1 /* tensor cores: 3 TF32 products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
-#define QSIM_PREC_BF16X3 2 /* tensor cores: 2-way BF16 split, 3 products, FP32 accumulation */
+#define QSIM_PREC_BF16X3 2 /* tensor cores: 2-way BF16 split, 3 products, FP32 accumulation. REDUCED
+                              accuracy (~16 significant bits per product, not complex64 level): ~1e-8
+                              infidelity per block on a random state, 7.9e-10 after the 64 blocks of the
+                              20-qubit depth-40 brickwork; never reported as a complex64-accuracy result */
 #define QSIM_PREC_BF16X6 3 /* tensor cores: 3-way BF16 split, 6 products, FP32 accumulation */
 
 /* Run modes. */
@@ -325,6 +328,19 @@ int qsim_sample_noalloc(const void* dev_state, int n, int dtype, uint64_t seed, 
 /* <a|b> = sum_x conj(a_x) b_x for two handles of equal n and dtype on the same device (Sec. 2.1: the
    amplitudes of the two state vectors; the overlap behind a fidelity). out[0..1] = (re, im). Synchronises. */
 int qsim_inner(qsim_h a, qsim_h b, double* out);
+
+/* ---- roofline calibration -------------------------------------------------------------------------------- */
+
+/*
+ * Dense tensor-core rate of the current GPU (a measurement service for roofline accounting; the paper has no
+ * counterpart, its fusion level is chosen per architecture and precision, Sec. 2.2). Every SM runs one CTA
+ * that issues tcgen05 MMAs back to back in the form the fused-block kernels use (A in tensor memory, B in
+ * shared memory, M = 128, N = n_cols, FP32 accumulation) on resident operands, for about `seconds` seconds.
+ * kind: 0 = TF32, 1 = BF16, 2 = FP16; n_cols: 128 or 256. *tflops receives 2 M N K x MMAs / elapsed time
+ * (CUDA events); *ms (may be NULL) the elapsed time. Runs on a private stream, allocates 4 bytes, and
+ * synchronises; QSIM_ETIMEOUT if a bounded wait of the probe expired.
+ */
+int qsim_tc_peak(int kind, int n_cols, double seconds, double* tflops, double* ms);
 
 /* ---- batches of independent circuits (one persistent launch) ---------------------------------------- */
 

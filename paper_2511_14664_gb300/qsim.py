@@ -101,6 +101,7 @@ SIGNATURES = {
     "qsim_expect_z_and_sample": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _u64, _i64, _P(_u64)], _i),
     "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
     "qsim_sample_noalloc": ([_vp, _i, _i, _u64, _i64, _vp, _vp], _i),
+    "qsim_tc_peak": ([_i, _i, ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
     "qsim_batch_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
     "qsim_batch_execute": ([_vp, _vp, _sz, _vp, _i], _i),
@@ -392,6 +393,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def tc_peak(kind: str = "tf32", n_cols: int = 128, seconds: float = 1.0):
+    """Measured dense tensor-core rate (TFLOP/s, elapsed ms) of an MMA-only loop on every SM."""
+    k = {"tf32": 0, "bf16": 1, "fp16": 2}[kind]
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qsim_tc_peak(k, int(n_cols), float(seconds), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 class Batch:

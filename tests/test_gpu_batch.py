@@ -126,6 +126,26 @@ def test_full_size_batch_256_tfim_chains(qsim):
     check([res[i] for i in small], [cs[i] for i in small])
 
 
+def test_full_size_batch_tensor_core_circuits_against_oracle(qsim):
+    """The same batch in the benchmark's configuration (3xTF32 tensor-core plans for the circuits of >= 20
+    qubits, on worker streams, graph replay): four of those circuits -- the two cheapest of 20-21 qubits and
+    the two cheapest of 22-24 qubits -- and twelve persistent-launch circuits against the oracle."""
+    batch = W.tfim_batch(256, seed=4, nmax=24)
+    cs = [c for c, _, _ in batch]
+    b = qsim.Batch(cs, max_fused=0, precision=1, tc_min_n=20)
+    assert b.info["tc_blocks"] > 0
+    b.execute(use_graph=True)
+    b.execute(use_graph=True)
+    res = b.results()
+    work = lambda i: len(cs[i]) * 2.0 ** cs[i].n
+    mid = sorted((i for i, c in enumerate(cs) if 20 <= c.n <= 21), key=work)[:2]
+    top = sorted((i for i, c in enumerate(cs) if c.n >= 22), key=work)[:2]
+    assert len(mid) == 2 and len(top) == 2
+    rest = [i for i, c in enumerate(cs) if c.n < 20][::9][:12]
+    pick = mid + top + rest
+    check([res[i] for i in pick], [cs[i] for i in pick])
+
+
 @pytest.mark.parametrize("prec", [1, 3])
 def test_wide_circuits_as_tensor_core_plans(qsim, prec):
     """With a tensor-core precision, circuits of at least tc_min_n qubits run as fused tensor-core plans

@@ -257,7 +257,11 @@ def test_full_size_qft28_tensor_cores_closed_form(qsim):
     got = st.tensor[torch.from_numpy(ys).cuda()].cpu().numpy().astype(np.complex128)
     ph = (np.uint64(x) * ys.astype(np.uint64)) & np.uint64((1 << n) - 1)
     ref = np.exp(2j * math.pi * ph.astype(np.float64) / (1 << n)) / math.sqrt(1 << n)
-    assert float(np.max(np.abs(got - ref))) <= 1e-6
+    # relative 1e-5 of the amplitudes' magnitude 2^-14 (6.1e-10 absolute), and the normalised infidelity of
+    # the sampled sub-vector
+    assert float(np.max(np.abs(got - ref))) <= 1e-5 * 2.0 ** (-n / 2)
+    ov = np.vdot(ref, got)
+    assert 1.0 - abs(ov) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real) <= 1e-9
     assert abs(st.norm() - 1.0) <= 1e-4
 
 
@@ -312,6 +316,26 @@ def test_plan_graph_replay(qsim):
         st.set_basis(0)
         p.execute(st)
         close(st.get_state(), ref, 16, 0)
+
+
+@pytest.mark.parametrize("mode,k", [(0, 1), (1, 4)])
+def test_complex128_large_state_elementwise(qsim, mode, k):
+    """Complex128 at 21 qubits, where dense gates on up to 4 targets (without controls) leave 2^17 or more
+    groups and so take the large-state register-gather kernel rather than the lane-split one: every
+    amplitude against the oracle at the complex128 bar, per-gate and fused."""
+    n = 21
+    rng = np.random.default_rng(210 + k)
+    c = W.Circuit(n)
+    for _ in range(24):
+        c.append(W.random_gate(n, rng, kmax=4, cmax=0, diag_prob=0.0))
+    for _ in range(12):
+        c.append(W.random_gate(n, rng, kmax=2, cmax=1, diag_prob=0.3))
+    for g in W.brickwork(n, 4, seed=k).gates:
+        c.append(g)
+    psi0 = random_state(n, 5)
+    st = make_state(qsim, n, 1, psi0=psi0)
+    st.run(c, mode=mode, max_fused=k)
+    close(st.get_state(), oracle.run(c, psi=psi0.copy()), n, 1)
 
 
 def test_circuit_then_inverse_large(qsim):

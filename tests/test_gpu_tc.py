@@ -1,8 +1,9 @@
 """Tensor-core fused blocks (tcgen05, split precision) against the FP64 oracle.
 
 Tolerances: 3xTF32 and BF16x6 are held to the complex64 bar (max |amplitude error| <= 1e-5, normalised
-infidelity <= 1e-9); BF16x3 carries ~16 significant bits per product, so a single block is held to
-max error <= 1e-5 and infidelity <= 1e-8, and a whole circuit only reports its infidelity (<= 1e-5).
+infidelity <= 1e-9). BF16x3 is a reduced-accuracy precision (~16 significant bits per product): a single
+block on a random state is held to max error <= 1e-5 and infidelity <= 1e-8, and the 20-qubit depth-40
+benchmark circuit (64 blocks) to the complex64 bar of 1e-9.
 """
 import numpy as np
 import pytest
@@ -154,11 +155,8 @@ def test_brickwork_20q_depth40_fused_tc(qsim, prec):
     g = st.get_state().astype(np.complex128)
     inf = oracle.infidelity(g, ref, n)
     err = float(np.max(np.abs(g - ref)))
-    if prec == "bf16x3":
-        assert inf <= 1e-5 and err <= 1e-4
-    else:
-        assert inf <= 1e-9, inf
-        assert err <= 1e-5, err
+    assert inf <= 1e-9, inf
+    assert err <= 1e-5, err
 
 
 def test_repeated_launches_and_plan_reuse(qsim):
