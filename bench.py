@@ -57,7 +57,8 @@ def parse_args():
     p.add_argument("--count", type=int, default=256, help="tfim_batch: number of circuits")
     p.add_argument("--nmax", type=int, default=24, help="tfim_batch: largest circuit width")
     p.add_argument("--workload", default="brickwork30",
-                   choices=["brickwork30", "qft28", "tfim_batch", "pairs34", "brick14", "qpe33", "rcs33", "tfim33"],
+                   choices=["brickwork30", "qft28", "tfim_batch", "pairs34", "brick14", "qpe33", "rcs33", "tfim33",
+                            "spill33"],
                    help="brickwork30 (the headline line), qft28, tfim_batch (256 TFIM circuits), pairs34, "
                         "brick14 (14-qubit complex128, latency-bound)")
     return p.parse_args()
@@ -1066,6 +1067,44 @@ def run_paper33(args, kind):
     return 0
 
 
+def run_spill(args):
+    """A state larger than a device window held in host memory (Sec. 2.5): the 30-qubit-generator brickwork at
+    n = 33 (64 GiB complex64, page-locked host memory), streamed through three device windows of 2^28
+    amplitudes, fused 3xTF32 blocks in every window. Reports gate-applications/s and the host-link bytes per
+    second of the streamed run (both directions counted), beside the same circuit run in device memory."""
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    n = args.n if args.n != 30 else 33
+    window = 28
+    c = W.brickwork(n, 4, seed=SEED)
+    kw = dict(mode=1, max_fused=6, precision=1)
+    host = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
+    runs = []
+    for i in range(max(1, args.warmup) + max(1, args.steps)):
+        host.zero_()
+        host[0] = 1.0
+        runs.append(qsim.spill_run(host, c, 0, window_qubits=window, **kw))
+    timed = runs[max(1, args.warmup):]
+    ms = sum(r["elapsed_ms"] for r in timed) / len(timed)
+    gbs = sum(r["host_bytes"] for r in timed) / (sum(r["elapsed_ms"] for r in timed) / 1000.0) / 1e9
+    st = qsim.State(n, qsim.C64)
+    p = qsim.Plan(c, qsim.C64, **kw)
+    dev_ms = _event_time(torch, lambda i: (st.set_basis(0), p.execute(st)), 2)
+    r = timed[-1]
+    line = _common_line(f"gate-applications/s, {n}-qubit random brickwork depth 4 held in host memory, streamed "
+                        f"through 2^{window}-amplitude device windows", len(c) / (ms / 1000.0), UNIT, args, ms, "tf32",
+                        {"workload": f"random brickwork n={n} depth 4 seed={SEED}, {len(c)} gates, complex64, "
+                                     f"host state {8 * 2 ** n / 2 ** 30:.0f} GiB page-locked", "path": "tf32x3_k6",
+                         "window_qubits": window, "global_slots": r["global_slots"]},
+                        segments=r["segments"], windows=r["windows"], passes_per_window=r["passes"] / r["windows"],
+                        host_link={"bytes_per_run": r["host_bytes"], "gbs": gbs,
+                                   "note": "host<->device bytes / wall time of the streamed run, both directions"},
+                        in_device_ms=dev_ms, plan_ms=r["host_plan_ms"])
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1082,6 +1121,8 @@ def main():
         return run_paper33(args, args.workload[:3])
     if args.workload == "tfim33":
         return run_paper33(args, "tfim")
+    if args.workload == "spill33":
+        return run_spill(args)
     return run_ours(args)
 
 

@@ -329,6 +329,56 @@ int qsim_sample_noalloc(const void* dev_state, int n, int dtype, uint64_t seed, 
    amplitudes of the two state vectors; the overlap behind a fidelity). out[0..1] = (re, im). Synchronises. */
 int qsim_inner(qsim_h a, qsim_h b, double* out);
 
+/* ---- states in host memory (Sec. 2.5: host memory supplements GPU memory) ------------------------------ */
+
+/*
+ * Out-of-core execution for states larger than the device can hold (Sec. 2.5: host memory can supplement GPU
+ * memory, at 4x or more per two extra qubits; Sec. 2.1: a state cut by its top index bits needs no exchange
+ * for gates on the other qubits). The state stays in HOST memory (caller-owned, 2^n amplitudes in the
+ * layout above; page-locked memory -- cudaHostAlloc, torch pin_memory -- lets the copies run asynchronously
+ * and overlap, pageable memory works but serialises them). It is cut into slices of 2^L amplitudes by its top
+ * n - L index bits, L = window_qubits - global_slots. The circuit is split into segments, each a set of
+ * gates (dependencies kept) touching at most global_slots of those top bits; for every value of the other
+ * top bits, the slices that differ only in the segment's bits are copied into a device window of
+ * 2^window_qubits amplitudes, the segment's plan (made once per segment by the ordinary planner with
+ * opts->run) runs there, and the window is copied back. Each segment reads and writes the whole state over
+ * the host link once. Three windows are allocated (3 x 2^window_qubits amplitudes of device memory) and
+ * rotate so that copies in, passes and copies out overlap.
+ */
+typedef struct {
+    int32_t window_qubits;  /* W: index bits of a device window (14 <= W; W >= n: the state fits one window) */
+    int32_t global_slots;   /* h: top index bits a window holds (0 = min(4, W - 12); 1..8, W - h >= 10) */
+    qsim_run_opts run;      /* planning options for every segment (use_graph, dry_run, local_qubits ignored) */
+} qsim_spill_opts;
+typedef struct {
+    int64_t segments;       /* stream-throughs of the whole state */
+    int64_t windows;        /* window loads in all */
+    int64_t passes;         /* kernel passes run on windows, summed over windows */
+    double host_bytes;      /* bytes copied between host and device (in + out) */
+    double elapsed_ms;      /* wall time of the call (it synchronises) */
+    double host_plan_ms;    /* host time spent segmenting and planning */
+    int32_t window_qubits;  /* W actually used (min(W, n)) */
+    int32_t global_slots;   /* h actually used (0 when the state fits one window) */
+} qsim_spill_info;
+/* Run circuit c (c->n qubits) on the host state in place. The work is ordered after earlier work on `stream`
+   (a cudaStream_t) and the call returns when it has completed. QSIM_EUNSUPPORTED when a gate has more than
+   h qubits among the top n - L index bits. info may be NULL. */
+int qsim_spill_run(void* host_state, const qsim_circuit* c, int dtype, const qsim_spill_opts* opts, void* stream,
+                   qsim_spill_info* info);
+/* The segmentation qsim_spill_run would use, on the host only (no device): seg_of_gate[i] = segment of gate i
+   (c->num_gates entries); used_global (may be NULL; room for c->num_gates masks) = per segment, the qubit mask
+   of the top index bits its gates touch; *nseg = number of segments. Gates of one segment run in their
+   input order; any two gates sharing a qubit run in input order. */
+int qsim_spill_segments(const qsim_circuit* c, int window_qubits, int global_slots, int32_t* seg_of_gate,
+                        uint64_t* used_global, int64_t* nseg);
+/* Sampling from a host state (Sec. 2.1 "Measurement and Sampling"): slices of 2^min(window_qubits, n)
+   amplitudes are streamed through the device to sum |a_x|^2 per slice (compensated sums); each shot's uniform
+   (the SplitMix64 stream of qsim_sample for `seed`) picks its slice by the FP64 prefix sums of the slice
+   totals and is rescaled into that slice, which is then sampled on the device as qsim_sample_uniforms does.
+   out: `shots` uint64 indices (host); *norm (may be NULL) = sum_x |a_x|^2. Synchronises. */
+int qsim_spill_sample(const void* host_state, int n, int dtype, int window_qubits, uint64_t seed, int64_t shots,
+                      uint64_t* out, double* norm);
+
 /* ---- roofline calibration -------------------------------------------------------------------------------- */
 
 /*

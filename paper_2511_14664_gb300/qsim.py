@@ -52,6 +52,19 @@ class PassInfo(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class SpillOpts(ctypes.Structure):
+    _fields_ = [("window_qubits", ctypes.c_int32), ("global_slots", ctypes.c_int32), ("run", RunOpts)]
+
+
+class SpillInfo(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_int64), ("windows", ctypes.c_int64), ("passes", ctypes.c_int64),
+                ("host_bytes", ctypes.c_double), ("elapsed_ms", ctypes.c_double), ("host_plan_ms", ctypes.c_double),
+                ("window_qubits", ctypes.c_int32), ("global_slots", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder", 5: "phase"}
 
 
@@ -101,6 +114,9 @@ SIGNATURES = {
     "qsim_expect_z_and_sample": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _u64, _i64, _P(_u64)], _i),
     "qsim_inner": ([_vp, _vp, _P(ctypes.c_double)], _i),
     "qsim_sample_noalloc": ([_vp, _i, _i, _u64, _i64, _vp, _vp], _i),
+    "qsim_spill_run": ([_vp, _P(Circuit), _i, _P(SpillOpts), _vp, _P(SpillInfo)], _i),
+    "qsim_spill_segments": ([_P(Circuit), _i, _i, _P(ctypes.c_int32), _P(_u64), _P(_i64)], _i),
+    "qsim_spill_sample": ([_vp, _i, _i, _i, _u64, _i64, _P(_u64), _P(ctypes.c_double)], _i),
     "qsim_tc_peak": ([_i, _i, ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
     "qsim_batch_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
@@ -393,6 +409,54 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _host_ptr(state) -> int:
+    """Address of a host state: a numpy array or a CPU torch tensor (page-locked ones let copies overlap)."""
+    if isinstance(state, np.ndarray):
+        if not state.flags.c_contiguous:
+            raise ValueError("host state must be contiguous")
+        return state.ctypes.data
+    if getattr(state, "is_cuda", False) or not state.is_contiguous():
+        raise ValueError("host state must be a contiguous CPU tensor or numpy array")
+    return state.data_ptr()
+
+
+def spill_run(host_state, circuit, dtype: int = C64, window_qubits: int = 28, global_slots: int = 0,
+              mode: int = RUN_FUSED, max_fused: int = 6, precision: int = PREC_TF32X3, tc_min_k: int = 5,
+              plan_effort: int = 0, stream=None) -> dict:
+    """Run `circuit` in place on a state held in host memory, streamed through device windows of
+    2^window_qubits amplitudes (three of them); returns the run's counters (segments, windows, bytes, ms)."""
+    cc = CircuitArgs(circuit)
+    o = SpillOpts(window_qubits=window_qubits, global_slots=global_slots,
+                  run=RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
+                              plan_effort=plan_effort))
+    info = SpillInfo()
+    _check(lib().qsim_spill_run(ctypes.c_void_p(_host_ptr(host_state)), ctypes.byref(cc.c), dtype, ctypes.byref(o),
+                                ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def spill_segments(circuit, window_qubits: int, global_slots: int = 0):
+    """Host-only segmentation of an out-of-core run: (segment of every gate, top-bit qubit mask per segment)."""
+    cc = CircuitArgs(circuit)
+    G = len(circuit.gates)
+    seg = (ctypes.c_int32 * max(1, G))()
+    used = (ctypes.c_uint64 * max(1, G))()
+    ns = ctypes.c_int64()
+    _check(lib().qsim_spill_segments(ctypes.byref(cc.c), int(window_qubits), int(global_slots), seg, used,
+                                     ctypes.byref(ns)))
+    return np.array(seg[:G], dtype=np.int64), [int(used[i]) for i in range(ns.value)]
+
+
+def spill_sample(host_state, n: int, dtype: int, window_qubits: int, seed: int, shots: int):
+    """Samples (and the squared norm) of a host state, streamed through the device by slices."""
+    out = np.zeros(max(1, shots), dtype=np.uint64)
+    nrm = ctypes.c_double()
+    _check(lib().qsim_spill_sample(ctypes.c_void_p(_host_ptr(host_state)), int(n), int(dtype), int(window_qubits),
+                                   seed & (2**64 - 1), int(shots), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   ctypes.byref(nrm)))
+    return out[:shots], nrm.value
 
 
 def tc_peak(kind: str = "tf32", n_cols: int = 128, seconds: float = 1.0):
