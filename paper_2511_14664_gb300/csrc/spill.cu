@@ -230,10 +230,13 @@ extern "C" int qsim_spill_run(void* host_state, const qsim_circuit* c, int dtype
         for (qsim_plan_h p : plans) qsim_plan_destroy(p);
         return r;
     };
-    double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    double plan_ms = 0.0;
     int64_t windows = 0, passes = 0;
     double host_bytes = 0.0;
     uint64_t wcount = 0;
+    // every segment's plan first (plan creation allocates device memory, which would wait for the copies in
+    // flight if it happened between segments)
+    std::vector<int64_t> seg_passes;
     for (const SpillSeg& sg : segs) {
         // the segment's gates on the window: local qubit q stays q, global qubit act[j] becomes L + j
         std::vector<int> slot(n, -1);
@@ -246,12 +249,16 @@ extern "C" int qsim_spill_run(void* host_state, const qsim_circuit* c, int dtype
             for (int j = 0; j < sub[i].nc; ++j) sub[i].controls[j] = slot[sub[i].controls[j]];
         }
         const qsim_circuit sc{Wq, (int32_t)sub.size(), sub.data()};
-        const auto tp = std::chrono::steady_clock::now();
         qsim_plan_h plan = nullptr;
         qsim_plan_info pi{};
         if ((rc = qsim_plan_create(&sc, dtype, &ro, win.s_comp, &plan, &pi)) != QSIM_OK) return cleanup(rc);
         plans.push_back(plan);
-        plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp).count();
+        seg_passes.push_back(pi.passes);
+    }
+    plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (size_t si = 0; si < segs.size(); ++si) {
+        const SpillSeg& sg = segs[si];
+        qsim_plan_h plan = plans[si];
         // the other global bits, as positions relative to L
         std::vector<int> other, actrel;
         for (int q = L; q < n; ++q)
@@ -280,7 +287,7 @@ extern "C" int qsim_spill_run(void* host_state, const qsim_circuit* c, int dtype
             if (e == cudaSuccess) e = cudaEventRecord(win.ev_out[b], win.s_out);
             if (e != cudaSuccess) return cleanup(cuda_fail(e, "window copy out"));
             ++windows;
-            passes += pi.passes;
+            passes += seg_passes[si];
             host_bytes += 2.0 * (double)win.bytes;
         }
         // the next segment reads slices this one writes: wait for every copy out
