@@ -25,8 +25,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <atomic>
 #include <mutex>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "capi_state.h"
@@ -391,6 +395,34 @@ int validate_batch(const qsim_circuit* cs, int count) {
     return QSIM_OK;
 }
 
+// Run fn(i, t) for i in [0, count) on up to `threads` host threads (t = the thread's index, each thread with
+// `device` current). The first failure (lowest i) is reported on the calling thread, with its message.
+int parallel_for(int count, int threads, int device, const std::function<int(int, int)>& fn) {
+    threads = std::max(1, std::min(threads, count));
+    std::vector<int> rcs(count, QSIM_OK);
+    std::vector<std::string> msgs(count);
+    std::atomic<int> next{0};
+    auto work = [&](int t) {
+        if (t > 0) cudaSetDevice(device);
+        for (int i = next++; i < count; i = next++) {
+            rcs[i] = fn(i, t);
+            if (rcs[i]) msgs[i] = qsim_last_error();
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < count; ++i)
+        if (rcs[i]) { set_error("%s", msgs[i].c_str()); return rcs[i]; }
+    return QSIM_OK;
+}
+
+int host_threads(int work_items) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    return (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)std::max(1, work_items / 4));
+}
+
 }  // namespace
 
 extern "C" {
@@ -434,16 +466,21 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     int64_t compose_out = 0;
     int64_t gates_total = 0;
     double bytes = 0.0;
-    for (int ci = 0; ci < count; ++ci) {
+    // validation and fusion of every circuit, on several host threads (circuits are independent)
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) { cudaGetLastError(); device = 0; }
+    std::vector<std::vector<uint64_t>> gmasks(count);
+    std::vector<std::vector<std::vector<int>>> cblk(count);
+    rc = parallel_for(count, host_threads(count), device, [&](int ci, int) -> int {
         const qsim_circuit& c = cs[ci];
         const int n = c.n;
-        const int kmax = std::min(n, opts.max_fused ? opts.max_fused : batch::tuned_k(n));
-        std::vector<uint64_t> gmask(c.num_gates);
+        std::vector<uint64_t>& gmask = gmasks[ci];
+        gmask.resize(c.num_gates);
         std::vector<char> gdiag(c.num_gates);
         for (int i = 0; i < c.num_gates; ++i) {
             const qsim_gate& g = c.gates[i];
-            rc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, batch::kKmax);
-            if (rc || g.k + g.nc > batch::kKmax) { set_error("circuit %d gate %d: batched gates act on at most %d qubits", ci, i, batch::kKmax); return QSIM_EINVAL; }
+            const int vrc = validate_qubits(n, g.targets, g.k, g.controls, g.nc, batch::kKmax);
+            if (vrc || g.k + g.nc > batch::kKmax) { set_error("circuit %d gate %d: batched gates act on at most %d qubits", ci, i, batch::kKmax); return QSIM_EINVAL; }
             if (!g.matrix || !is_unitary(g.matrix, g.k, 1e-8 * (1 << g.k))) { set_error("circuit %d gate %d: matrix missing or not unitary", ci, i); return QSIM_EINVAL; }
             uint64_t m = 0;
             for (int j = 0; j < g.k; ++j) m |= 1ull << g.targets[j];
@@ -451,10 +488,21 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             gmask[i] = m;
             gdiag[i] = is_diagonal(g.matrix, g.k);
         }
+        if (!wide[ci]) {
+            const int kmax = std::min(n, opts.max_fused ? opts.max_fused : batch::tuned_k(n));
+            cblk[ci] = group_gates(gmask, gdiag, n, kmax);
+        }
+        return QSIM_OK;
+    });
+    if (rc) return rc;
+    for (int ci = 0; ci < count; ++ci) {
+        const qsim_circuit& c = cs[ci];
+        const int n = c.n;
+        const std::vector<uint64_t>& gmask = gmasks[ci];
         gates_total += c.num_gates;
         circs[ci].n = n;
         if (wide[ci]) { circs[ci].npass = 0; circs[ci].first_pass = (int64_t)passes.size(); continue; }
-        const auto blocks = group_gates(gmask, gdiag, n, kmax);
+        const auto& blocks = cblk[ci];
         circs[ci].npass = (int)blocks.size();
         circs[ci].first_pass = (int64_t)passes.size();
         for (const auto& blk : blocks) {
@@ -629,18 +677,40 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         ok = ok && cudaMalloc(&b->derr, sizeof(unsigned)) == cudaSuccess;
         ok = ok && cudaMemset(b->derr, 0, sizeof(unsigned)) == cudaSuccess;
         if (!ok) { set_error("batch: scratch and streams for the tensor-core plans"); return fail(QSIM_ENOMEM); }
-        std::vector<double> wide_work;
-        for (int i : wides) {
+        // one plan per wide circuit, made on several host threads, each thread on its own stream (a plan's
+        // creation synchronises its stream); ordered after the caller's earlier work on `stream`
+        const int nw = (int)wides.size();
+        const int nth = host_threads(nw * 4);
+        std::vector<cudaStream_t> pst(nth, nullptr);
+        cudaEvent_t ord = nullptr;
+        ok = cudaEventCreateWithFlags(&ord, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ord, s) == cudaSuccess;
+        for (int t = 0; t < nth && ok; ++t)
+            ok = cudaStreamCreateWithFlags(&pst[t], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamWaitEvent(pst[t], ord, 0) == cudaSuccess;
+        std::vector<qsim_plan_h> wph(nw, nullptr);
+        std::vector<qsim_plan_info> wpi(nw);
+        const int prc = !ok ? QSIM_ENOMEM : parallel_for(nw, nth, device, [&](int w, int my_slot) -> int {
             qsim_run_opts po{};
             po.mode = QSIM_RUN_FUSED;
             po.max_fused = 6;
             po.precision = opts.precision;
             po.tc_min_k = 5;
-            qsim_plan_h ph = nullptr;
-            qsim_plan_info pi{};
-            const int prc = qsim_plan_create(&cs[i], QSIM_C64, &po, stream_v, &ph, &pi);
-            if (prc) return fail(prc);
-            b->wide_plans.push_back(ph);
+            const int r = qsim_plan_create(&cs[wides[w]], QSIM_C64, &po, pst[my_slot], &wph[w], &wpi[w]);
+            if (r == QSIM_OK && cudaStreamSynchronize(pst[my_slot]) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "tensor-core plan of a wide circuit");
+            return r;
+        });
+        for (cudaStream_t st : pst)
+            if (st) cudaStreamDestroy(st);
+        if (ord) cudaEventDestroy(ord);
+        for (qsim_plan_h ph : wph)
+            if (ph) b->wide_plans.push_back(ph);
+        if (!ok) { set_error("batch: streams for planning the tensor-core circuits"); return fail(QSIM_ENOMEM); }
+        if (prc) return fail(prc);
+        std::vector<double> wide_work;
+        for (int w = 0; w < nw; ++w) {
+            const int i = wides[w];
+            const qsim_plan_info& pi = wpi[w];
             wide_work.push_back(std::ldexp((double)pi.passes, cs[i].n));
             I.passes += pi.passes;
             I.tc_blocks += pi.tc_blocks;
@@ -649,7 +719,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             I.algorithmic_bytes += pi.algorithmic_bytes;
             // the first block generates |0> (execute_from_basis) and only writes
             qsim_pass_info p0{};
-            if (pi.passes > 0 && qsim_plan_pass_info(ph, 0, &p0) == QSIM_OK && p0.kind == QSIM_PASS_TC &&
+            if (pi.passes > 0 && qsim_plan_pass_info(wph[w], 0, &p0) == QSIM_OK && p0.kind == QSIM_PASS_TC &&
                 p0.precision != QSIM_PREC_BF16X6)
                 I.algorithmic_bytes -= std::ldexp(8.0, cs[i].n);
         }

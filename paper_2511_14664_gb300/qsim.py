@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+from itertools import chain
 from typing import Iterable, Optional, Sequence
 
 import numpy as np
@@ -319,39 +320,70 @@ _GATE_NP = np.dtype({"names": ["k", "nc", "targets", "controls", "matrix"],
                      "itemsize": ctypes.sizeof(Gate)})
 
 
+def _pack_gates(gs):
+    """Gate records in the qsim_gate layout for the list `gs`, plus the matrix arrays they point into (one
+    per gate width, so that all gates of a width are copied with one array operation)."""
+    G = len(gs)
+    rec = np.zeros(max(1, G), dtype=_GATE_NP)
+    pools = []
+    if G:
+        ks = np.fromiter((len(g.targets) for g in gs), dtype=np.int32, count=G)
+        ncs = np.fromiter((len(g.controls) for g in gs), dtype=np.int32, count=G)
+        if int(ks.max()) > MAX_TARGETS or int(ncs.max()) > MAX_CONTROLS:
+            raise ValueError("a gate has more than %d targets or controls" % MAX_TARGETS)
+        rec["k"][:G] = ks
+        rec["nc"][:G] = ncs
+        for k in np.unique(ks):  # gates of one width share an array of matrices
+            idx = np.nonzero(ks == k)[0]
+            k = int(k)
+            sub = [gs[i] for i in idx]
+            rec["targets"][idx, :k] = np.fromiter(chain.from_iterable(g.targets for g in sub), dtype=np.int32,
+                                                  count=len(idx) * k).reshape(len(idx), k)
+            # one copy per distinct matrix object (circuits often reuse one array for many gates)
+            ids = np.fromiter((id(g.matrix) for g in sub), dtype=np.int64, count=len(sub))
+            uniq, first, inv = np.unique(ids, return_index=True, return_inverse=True)
+            M = np.ascontiguousarray(np.array([sub[j].matrix for j in first], dtype=np.complex128))
+            if M.shape[1:] != (1 << k, 1 << k):
+                raise ValueError("a %d-qubit gate needs a %dx%d matrix" % (k, 1 << k, 1 << k))
+            pools.append(M)
+            rec["matrix"][idx] = M.ctypes.data + inv.astype(np.uint64).ravel() * np.uint64(M[0].nbytes)
+        for c in np.unique(ncs):
+            if c:
+                idx = np.nonzero(ncs == c)[0]
+                c = int(c)
+                rec["controls"][idx, :c] = np.fromiter(chain.from_iterable(gs[i].controls for i in idx),
+                                                       dtype=np.int32, count=len(idx) * c).reshape(len(idx), c)
+    return rec, pools
+
+
 class CircuitArgs:
     """A workloads.Circuit marshalled into qsim_gate structs: one record array for the gates and, per gate
     width, one array holding those gates' matrices (all kept alive here)."""
 
     def __init__(self, circuit):
         self.n = circuit.n
-        gs = circuit.gates
-        G = len(gs)
-        rec = np.zeros(max(1, G), dtype=_GATE_NP)
-        self.pools = []
-        if G:
-            ks = np.fromiter((len(g.targets) for g in gs), dtype=np.int32, count=G)
-            ncs = np.fromiter((len(g.controls) for g in gs), dtype=np.int32, count=G)
-            if int(ks.max()) > MAX_TARGETS or int(ncs.max()) > MAX_CONTROLS:
-                raise ValueError("a gate has more than %d targets or controls" % MAX_TARGETS)
-            rec["k"][:G] = ks
-            rec["nc"][:G] = ncs
-            for k in np.unique(ks):  # gates of one width share an array of matrices
-                idx = np.nonzero(ks == k)[0]
-                sub = [gs[i] for i in idx]
-                rec["targets"][idx, :k] = np.array([g.targets for g in sub], dtype=np.int32).reshape(len(idx), k)
-                M = np.ascontiguousarray(np.array([g.matrix for g in sub], dtype=np.complex128))
-                if M.shape[1:] != (1 << int(k), 1 << int(k)):
-                    raise ValueError("a %d-qubit gate needs a %dx%d matrix" % (k, 1 << int(k), 1 << int(k)))
-                self.pools.append(M)
-                rec["matrix"][idx] = M.ctypes.data + np.arange(len(idx), dtype=np.uint64) * np.uint64(M[0].nbytes)
-            for c in np.unique(ncs):
-                if c:
-                    idx = np.nonzero(ncs == c)[0]
-                    rec["controls"][idx, :c] = np.array([gs[i].controls for i in idx], dtype=np.int32).reshape(len(idx), c)
-        self.rec = rec
-        self.gates = ctypes.cast(rec.ctypes.data, ctypes.POINTER(Gate))
-        self.c = Circuit(n=circuit.n, num_gates=G, gates=self.gates)
+        self.rec, self.pools = _pack_gates(circuit.gates)
+        self.gates = ctypes.cast(self.rec.ctypes.data, ctypes.POINTER(Gate))
+        self.c = Circuit(n=circuit.n, num_gates=len(circuit.gates), gates=self.gates)
+
+
+class CircuitsArgs:
+    """Many circuits marshalled at once (all their gates packed in one pass): `arr` is the qsim_circuit array
+    the batch entry points take."""
+
+    def __init__(self, circuits):
+        circuits = list(circuits)
+        allg = [g for c in circuits for g in c.gates]
+        self.rec, self.pools = _pack_gates(allg)
+        base = self.rec.ctypes.data
+        size = ctypes.sizeof(Gate)
+        self.arr = (Circuit * max(1, len(circuits)))()
+        off = 0
+        for i, c in enumerate(circuits):
+            G = len(c.gates)
+            self.arr[i] = Circuit(n=c.n, num_gates=G, gates=ctypes.cast(base + off * size, ctypes.POINTER(Gate)))
+            off += G
+        self.count = len(circuits)
 
 
 class Plan:
@@ -475,17 +507,16 @@ class Batch:
     def __init__(self, circuits, max_fused: int = 0, stream=None, precision: int = 0, tc_min_n: int = 0):
         import torch
         self.circuits = list(circuits)
-        self.args = [CircuitArgs(c) for c in self.circuits]
-        arr = (Circuit * len(self.args))(*[a.c for a in self.args])
-        self.carr = arr
+        self.args = CircuitsArgs(self.circuits)
+        arr = self.args.arr
         ws = ctypes.c_size_t()
-        _check(lib().qsim_batch_workspace_bytes(arr, len(self.args), ctypes.byref(ws)))
+        _check(lib().qsim_batch_workspace_bytes(arr, self.args.count, ctypes.byref(ws)))
         self.ws_bytes = ws.value
         self.ws = torch.empty(max(1, self.ws_bytes // 8), dtype=torch.complex64, device="cuda")
         o = RunOpts(mode=RUN_FUSED, max_fused=max_fused, precision=precision, batch_tc_min_n=tc_min_n)
         info = PlanInfo()
         b = ctypes.c_void_p()
-        _check(lib().qsim_batch_plan_create(arr, len(self.args), ctypes.byref(o),
+        _check(lib().qsim_batch_plan_create(arr, self.args.count, ctypes.byref(o),
                                             ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(b), ctypes.byref(info)))
         self.b = b
         self.info = info.as_dict()
@@ -522,8 +553,7 @@ class Batch:
 
 def batch_autotune(circuits, stream=None):
     """Tune the batched fusion width per qubit count; returns the k each circuit now gets."""
-    args = [CircuitArgs(c) for c in circuits]
-    arr = (Circuit * len(args))(*[a.c for a in args])
-    chosen = (ctypes.c_int * len(args))()
-    _check(lib().qsim_batch_autotune(arr, len(args), ctypes.c_void_p(_stream_ptr(stream)), chosen))
-    return list(chosen)
+    args = CircuitsArgs(circuits)
+    chosen = (ctypes.c_int * max(1, args.count))()
+    _check(lib().qsim_batch_autotune(args.arr, args.count, ctypes.c_void_p(_stream_ptr(stream)), chosen))
+    return list(chosen)[:args.count]
