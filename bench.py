@@ -1096,6 +1096,28 @@ def run_spill(args):
     timed = runs[max(1, args.warmup):]
     ms = sum(r["elapsed_ms"] for r in timed) / len(timed)
     gbs = sum(r["host_bytes"] for r in timed) / (sum(r["elapsed_ms"] for r in timed) / 1000.0) / 1e9
+    # the link itself: 2 GiB page-locked copies host -> device, device -> host, and both at once (two streams)
+    nb = 1 << 28
+    hsrc = host[:nb]
+    hdst = torch.empty(nb, dtype=torch.complex64, pin_memory=True)
+    d0 = torch.empty(nb, dtype=torch.complex64, device="cuda")
+    d1 = torch.empty(nb, dtype=torch.complex64, device="cuda")
+    s_a, s_b = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def link(h2d, d2h, reps=3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            if h2d:
+                with torch.cuda.stream(s_a):
+                    d0.copy_(hsrc, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s_b):
+                    hdst.copy_(d1, non_blocking=True)
+        torch.cuda.synchronize()
+        return reps * 8 * nb * (int(h2d) + int(d2h)) / (time.perf_counter() - t) / 1e9
+    link_gbs = {"h2d": link(True, False), "d2h": link(False, True), "both": link(True, True)}
+    del d0, d1, hdst
     st = qsim.State(n, qsim.C64)
     p = qsim.Plan(c, qsim.C64, **kw)
     dev_ms = _event_time(torch, lambda i: (st.set_basis(0), p.execute(st)), 2)
@@ -1107,7 +1129,8 @@ def run_spill(args):
                          "window_qubits": window, "global_slots": r["global_slots"]},
                         segments=r["segments"], windows=r["windows"], passes_per_window=r["passes"] / r["windows"],
                         host_link={"bytes_per_run": r["host_bytes"], "gbs": gbs,
-                                   "note": "host<->device bytes / wall time of the streamed run, both directions"},
+                                   "note": "host<->device bytes / wall time of the streamed run, both directions",
+                                   "copy_gbs": link_gbs, "fraction_of_both": gbs / link_gbs["both"]},
                         in_device_ms=dev_ms, plan_ms=r["host_plan_ms"])
     print(json.dumps(line))
     return 0

@@ -108,7 +108,10 @@ typedef struct {
     int32_t batch_tc_min_n;
     /* Planning effort: 0 = greedy fusion (the largest candidate block at each step); 1 = also fuse with
        one block of look-ahead and keep the grouping with fewer blocks (planning about 4x slower; e.g. the
-       33-qubit triangular-lattice TFIM goes from 63 to 58 passes). */
+       33-qubit triangular-lattice TFIM goes from 63 to 58 passes); 2 / 3 = also a beam search over
+       groupings (beam 8 / 32: the partial groupings that placed the most gates), fewest blocks kept
+       (30-qubit brickwork 64 -> 62 passes, 33-qubit paper random circuit 45 -> 44 / 42; planning 5-20x
+       slower than greedy). */
     int32_t plan_effort;
     int32_t reserved;
 } qsim_run_opts;

@@ -205,6 +205,82 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
     return blocks;
 }
 
+// Fusion by beam search: keep the `beam` partial groupings (all with the same number of blocks) that have
+// placed the most gates, extend each by every candidate of its next block, and stop at the first grouping
+// that places every gate (so none with fewer blocks was pruned while it was still ahead). Partial groupings
+// that placed the same set of gates are kept once (Zobrist hash of the placed set).
+std::vector<std::vector<int>> group_gates_beam(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
+                                               int n, int kmax, const std::vector<char>* gwide, int wide_factor,
+                                               int beam) {
+    const int G = (int)gmask.size();
+    if (G == 0) return {};
+    std::vector<uint64_t> zob(G);
+    uint64_t z = 0x243F6A8885A308D3ull;
+    for (int i = 0; i < G; ++i) {  // SplitMix64 steps: a fixed, well-mixed 64-bit key per gate
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        zob[i] = x ^ (x >> 31);
+    }
+    struct State {
+        std::vector<char> done;
+        std::vector<std::vector<int>> blocks;
+        int placed = 0, first = 0;
+        uint64_t hash = 0;
+    };
+    struct Child {
+        int parent;
+        std::vector<int> blk;
+        int placed, first;
+        uint64_t hash;
+    };
+    std::vector<State> cur(1);
+    cur[0].done.assign(G, 0);
+    while (true) {
+        for (const State& st : cur)
+            if (st.placed == G) return st.blocks;
+        std::vector<Child> kids;
+        for (int pi = 0; pi < (int)cur.size(); ++pi) {
+            State& st = cur[pi];
+            auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, st.done, st.first);
+            for (size_t c = 0; c < cands.size(); ++c) {
+                bool dup = false;
+                for (size_t d = 0; d < c && !dup; ++d) dup = cands[d] == cands[c];
+                if (dup) continue;
+                uint64_t h = st.hash;
+                for (int g : cands[c]) { h ^= zob[g]; st.done[g] = 1; }
+                int f = st.first;
+                while (f < G && st.done[f]) ++f;
+                for (int g : cands[c]) st.done[g] = 0;
+                kids.push_back({pi, std::move(cands[c]), st.placed, f, h});
+                kids.back().placed += (int)kids.back().blk.size();
+            }
+        }
+        // most gates placed first; among equals, the one whose earliest unplaced gate is latest
+        std::stable_sort(kids.begin(), kids.end(), [](const Child& a, const Child& b) {
+            return a.placed != b.placed ? a.placed > b.placed : a.first > b.first;
+        });
+        std::vector<State> nxt;
+        std::vector<uint64_t> seen;
+        for (const Child& k : kids) {
+            if ((int)nxt.size() >= beam) break;
+            if (std::find(seen.begin(), seen.end(), k.hash) != seen.end()) continue;
+            seen.push_back(k.hash);
+            State ns;
+            ns.done = cur[k.parent].done;
+            ns.blocks = cur[k.parent].blocks;
+            for (int g : k.blk) ns.done[g] = 1;
+            ns.blocks.push_back(k.blk);
+            ns.placed = k.placed;
+            ns.first = k.first;
+            ns.hash = k.hash;
+            nxt.push_back(std::move(ns));
+        }
+        cur.swap(nxt);
+    }
+}
+
 static double op_bytes(const PlanOp& op, int n, size_t amp) {
     if (op.kind == OP_SWAP) return 2.0 * amp * std::ldexp(1.0, n) * (1.0 - std::ldexp(1.0, -op.nswap));
     if (op.kind == OP_PHASE) return 2.0 * amp * std::ldexp(1.0, n);
@@ -330,6 +406,12 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
                 if (la == 0 && f == 1) continue;  // the first grouping above
                 auto alt = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f, la);
+                if (alt.size() < blocks.size()) blocks.swap(alt);
+            }
+        if (opts.plan_effort >= 2)
+            for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
+                auto alt = group_gates_beam(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f,
+                                            opts.plan_effort >= 3 ? 32 : 8);
                 if (alt.size() < blocks.size()) blocks.swap(alt);
             }
     }

@@ -152,6 +152,21 @@ def test_plan_effort_lookahead_never_more_passes(qsim):
     assert len(b) < len(a)
 
 
+def test_plan_effort_beam_never_more_passes_and_places_every_gate(qsim):
+    """plan_effort 2 adds a beam search over groupings (the partial groupings that placed the most gates)
+    and keeps the grouping with the fewest blocks: never more passes than greedy or look-ahead fusion, the
+    merged gate counts add up to the circuit's, and on the 30-qubit brickwork it saves passes."""
+    cases = [W.brickwork(30, 40, seed=3), W.rcs(20, seed=3), W.qft(18)]
+    for c in cases:
+        _, ps1 = plan(qsim, c, plan_effort=1, **TC6)
+        _, ps2 = plan(qsim, c, plan_effort=2, **TC6)
+        assert len(ps2) <= len(ps1)
+        assert sum(q["gates"] for q in ps2) == len(c)
+    _, a = plan(qsim, cases[0], **TC6)
+    _, b = plan(qsim, cases[0], plan_effort=2, **TC6)
+    assert len(b) < len(a)
+
+
 @pytest.mark.parametrize("L", [16, 18, 22])
 def test_global_qubit_reorders_restore_identity(qsim, L):
     """Following a plan's reorder passes as exchanges of index bits, every gate pass must find its qubits
