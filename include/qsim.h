@@ -87,7 +87,7 @@ typedef struct {
 /* Options for planning a circuit. Zero-initialise, then set fields. */
 typedef struct {
     int32_t mode;       /* QSIM_RUN_PLAIN or QSIM_RUN_FUSED */
-    int32_t max_fused;  /* fusion width k for QSIM_RUN_FUSED: 1..6 (0 = 5) */
+    int32_t max_fused;  /* fusion width k for QSIM_RUN_FUSED: 1..6 (0 = 5); dry runs also 7, 8 (pass counts) */
     int32_t precision;  /* QSIM_PREC_* for dense blocks of >= tc_min_k qubits (complex64 states only) */
     int32_t tc_min_k;   /* smallest dense block sent to the tensor-core kernel (0 = 5) */
     int32_t use_graph;  /* 1: replay the plan's launches from a CUDA graph captured on first execution */

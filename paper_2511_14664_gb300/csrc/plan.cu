@@ -351,7 +351,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts_in) opts = *opts_in;
     if (opts.mode != QSIM_RUN_PLAIN && opts.mode != QSIM_RUN_FUSED) { set_error("unknown mode"); return QSIM_EINVAL; }
     int kmax = opts.max_fused == 0 ? 5 : opts.max_fused;
-    if (kmax < 1 || kmax > 6) { set_error("max_fused must be 1..6"); return QSIM_EINVAL; }
+    // dry runs (host-only pass counts) may also plan 7- and 8-qubit blocks, for sizing the fusion width
+    if (kmax < 1 || kmax > (opts.dry_run ? 8 : 6)) { set_error("max_fused must be 1..6 (1..8 in a dry run)"); return QSIM_EINVAL; }
     if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
     const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
     const int n = c->n;
