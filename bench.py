@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--no-configs", action="store_true",
                    help="skip the other configurations' runs after the headline line (N = 1 only)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--probe-seconds", type=float, default=1.5,
+                   help="seconds per operand type of the tensor-core rate probe (0: skip it, no tensor fraction)")
     p.add_argument("--count", type=int, default=256, help="tfim_batch: number of circuits")
     p.add_argument("--nmax", type=int, default=24, help="tfim_batch: largest circuit width")
     p.add_argument("--workload", default="brickwork30",
@@ -162,12 +164,16 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-KERNEL_SOURCES = {"dense_small": "k_gates.cu", "diag": "k_gates.cu", "dense_tile": "k_gates.cu", "tc": "k_tc.cu"}
+KERNEL_SOURCES = {"dense_small": ["k_gates.cu"], "diag": ["k_gates.cu"], "dense_tile": ["k_gates.cu"],
+                  "tc": ["k_tc.cu", "tc_ptx.cuh", "tmem_io.cuh"]}
 
 
 def source_sha(kind):
-    p = os.path.join(ROOT, "paper_2511_14664_gb300", "csrc", KERNEL_SOURCES[kind])
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:12]
+    """Hash of the sources a kernel kind is built from (a profile's counters apply only while it holds)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        h.update(open(os.path.join(ROOT, "paper_2511_14664_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def profiled_traffic(kind, n):
@@ -471,7 +477,8 @@ def run_ours(args):
         main = args.path
     plan = plans[main]
 
-    rates = tensor_rates(qsim, uuid, 1.5 if args.steps >= 3 else 0.5)
+    rates = tensor_rates(qsim, uuid, args.probe_seconds if args.steps >= 3 else min(args.probe_seconds, 0.5)) \
+        if args.probe_seconds > 0 else None
 
     # ---- the timed region -------------------------------------------------------------------------------
     timed_steps(qsim, torch, st, plan, args.warmup, shots, per_pass=True)
@@ -508,7 +515,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
             "traffic": profiled_traffic(dom, n), "kernel": dom, "launches_per_step": dk["launches"] // args.steps,
             "avg_launch_ms": avg_s * 1000.0, "share_of_step": dk["ms"] / total_ms, "peak_source": peak_src}
-    if dom == "tc" and dk["flops"] > 0:
+    if dom == "tc" and dk["flops"] > 0 and rates is not None:
         tflops = dk["flops"] / dk["launches"] / avg_s / 1e12
         prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == "tc"][0]]["precision"]
         # the rate of the products' operand type, measured on this GPU in this run (tensor_rates)
@@ -1116,6 +1123,7 @@ def run_spill(args):
                     hdst.copy_(d1, non_blocking=True)
         torch.cuda.synchronize()
         return reps * 8 * nb * (int(h2d) + int(d2h)) / (time.perf_counter() - t) / 1e9
+    link(True, True, 1)  # first use of the device buffers and streams, untimed
     link_gbs = {"h2d": link(True, False), "d2h": link(False, True), "both": link(True, True)}
     del d0, d1, hdst
     st = qsim.State(n, qsim.C64)

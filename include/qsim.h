@@ -438,6 +438,24 @@ int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts,
  * each circuit would now get.
  */
 int qsim_batch_autotune(const qsim_circuit* cs, int count, void* stream, int* chosen);
+/*
+ * Tuner for the width from which batched circuits run as tensor-core plans (a library service beside the
+ * fusion-width tuner; Sec. 2.2: the fusion setting is tuned per architecture and precision): the whole batch
+ * cs is planned and replayed (graph, median of three after a warm-up) with batch_tc_min_n = 14, 16, ..., 24
+ * and 27 (no circuit leaves the persistent launch), for `precision` (a tensor-core one); the fastest
+ * threshold is kept process-wide for plans made with batch_tc_min_n = 0 and returned in *best_min_n (may be
+ * NULL). Allocates a trial workspace and releases it.
+ */
+int qsim_batch_autotune_threshold(const qsim_circuit* cs, int count, int precision, void* stream, int* best_min_n);
+/*
+ * The process-wide tuning (fusion width per circuit width, tensor-core threshold per precision) to and from a
+ * small JSON file (library service). Load validates every entry (QSIM_EINVAL for a file that is not such a
+ * table; nothing is changed then). With the environment variable QSIM_TUNE_CACHE set to a path, the table is
+ * read from it before the first batch plan or tuning of the process (if the file exists) and written to it
+ * after every successful tuning.
+ */
+int qsim_batch_tune_save(const char* path);
+int qsim_batch_tune_load(const char* path);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <atomic>
@@ -340,10 +342,124 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ A
 // ---- host side ----------------------------------------------------------------------------------------------
 std::mutex g_tune_mu;
 int g_tuned_k[QSIM_MAX_QUBITS + 1] = {0};
+int g_tuned_tc_min_n[4] = {0, 0, 0, 0};  // per tensor-core precision; 0 = not tuned (default 20)
+bool g_cache_loaded = false;
 
 int tuned_k(int n) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     return g_tuned_k[n] ? g_tuned_k[n] : kKmax;
+}
+
+int tuned_tc_min_n(int precision) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const int v = (precision >= 1 && precision <= 3) ? g_tuned_tc_min_n[precision] : 0;
+    return v ? v : 20;
+}
+
+// The tuning table as a small JSON object: fusion width per circuit width, and per tensor-core precision the
+// smallest width that runs as a tensor-core plan.
+std::string tune_json() {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::string o = "{\"format\": \"qsim-batch-tune-1\", \"k_by_width\": {";
+    bool first = true;
+    for (int n = 1; n <= QSIM_MAX_QUBITS; ++n)
+        if (g_tuned_k[n]) {
+            o += (first ? "\"" : ", \"") + std::to_string(n) + "\": " + std::to_string(g_tuned_k[n]);
+            first = false;
+        }
+    o += "}, \"tc_min_n\": {";
+    first = true;
+    for (int p = 1; p <= 3; ++p)
+        if (g_tuned_tc_min_n[p]) {
+            o += (first ? "\"" : ", \"") + std::to_string(p) + "\": " + std::to_string(g_tuned_tc_min_n[p]);
+            first = false;
+        }
+    return o + "}}\n";
+}
+
+// Read the "key": value integer pairs of the object that follows `name` in `text` (the format tune_json
+// writes); false if the object is missing or malformed.
+bool read_int_object(const std::string& text, const char* name, std::vector<std::pair<int, int>>& out) {
+    const std::string key = std::string("\"") + name + "\"";
+    size_t i = text.find(key);
+    if (i == std::string::npos) return false;
+    i = text.find('{', i + key.size());
+    const size_t end = i == std::string::npos ? i : text.find('}', i);
+    if (end == std::string::npos) return false;
+    const std::string body = text.substr(i + 1, end - i - 1);
+    size_t j = 0;
+    while (true) {
+        const size_t q0 = body.find('"', j);
+        if (q0 == std::string::npos) return true;
+        const size_t q1 = body.find('"', q0 + 1);
+        const size_t colon = q1 == std::string::npos ? q1 : body.find(':', q1);
+        if (colon == std::string::npos) return false;
+        char* e1 = nullptr;
+        char* e2 = nullptr;
+        const long k = std::strtol(body.c_str() + q0 + 1, &e1, 10);
+        const long v = std::strtol(body.c_str() + colon + 1, &e2, 10);
+        if (e1 != body.c_str() + q1 || e2 == body.c_str() + colon + 1) return false;
+        out.emplace_back((int)k, (int)v);
+        j = (size_t)(e2 - body.c_str());
+    }
+}
+
+int tune_load_file(const char* path) {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) { set_error("cannot open tuning file %s", path); return QSIM_EINVAL; }
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (1u << 20)) text.append(buf, got);
+    std::fclose(f);
+    std::vector<std::pair<int, int>> ks, ts;
+    if (text.find("qsim-batch-tune-1") == std::string::npos || !read_int_object(text, "k_by_width", ks) ||
+        !read_int_object(text, "tc_min_n", ts)) {
+        set_error("%s is not a batch tuning file", path);
+        return QSIM_EINVAL;
+    }
+    for (const auto& kv : ks)
+        if (kv.first < 1 || kv.first > QSIM_MAX_QUBITS || kv.second < 1 || kv.second > kKmax) {
+            set_error("%s: fusion width %d for %d qubits out of range", path, kv.second, kv.first);
+            return QSIM_EINVAL;
+        }
+    for (const auto& kv : ts)
+        if (kv.first < 1 || kv.first > 3 || kv.second < 13 || kv.second > 27) {
+            set_error("%s: tc_min_n %d for precision %d out of range", path, kv.second, kv.first);
+            return QSIM_EINVAL;
+        }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : ks) g_tuned_k[kv.first] = kv.second;
+    for (const auto& kv : ts) g_tuned_tc_min_n[kv.first] = kv.second;
+    return QSIM_OK;
+}
+
+int tune_save_file(const char* path) {
+    const std::string j = tune_json();
+    FILE* f = std::fopen(path, "wb");
+    if (!f) { set_error("cannot write tuning file %s", path); return QSIM_EINVAL; }
+    const bool ok = std::fwrite(j.data(), 1, j.size(), f) == j.size();
+    if (std::fclose(f) != 0 || !ok) { set_error("writing tuning file %s failed", path); return QSIM_EINVAL; }
+    return QSIM_OK;
+}
+
+// QSIM_TUNE_CACHE names a tuning file: read once before the first batch plan, written after every tuning.
+void tune_cache_autoload() {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (g_cache_loaded) return;
+        g_cache_loaded = true;
+    }
+    const char* p = std::getenv("QSIM_TUNE_CACHE");
+    if (p && *p) {
+        FILE* f = std::fopen(p, "rb");
+        if (f) { std::fclose(f); tune_load_file(p); }
+    }
+}
+
+void tune_cache_autosave() {
+    const char* p = std::getenv("QSIM_TUNE_CACHE");
+    if (p && *p) tune_save_file(p);
 }
 
 }  // namespace batch
@@ -452,8 +568,10 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     if (opts.max_fused < 0 || opts.max_fused > batch::kKmax) { set_error("batched fusion width must be 0 (tuned) or 1..%d", batch::kKmax); return QSIM_EINVAL; }
     if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
-    // circuits this wide run as tensor-core plans (6-qubit blocks need n >= 13)
-    const int tc_min_n = opts.precision == QSIM_PREC_SIMT ? 1000 : (opts.batch_tc_min_n > 0 ? std::max(13, opts.batch_tc_min_n) : 20);
+    // circuits this wide run as tensor-core plans (6-qubit blocks need n >= 13); 0 = the tuned threshold
+    batch::tune_cache_autoload();
+    const int tc_min_n = opts.precision == QSIM_PREC_SIMT ? 1000
+                         : (opts.batch_tc_min_n > 0 ? std::max(13, opts.batch_tc_min_n) : batch::tuned_tc_min_n(opts.precision));
     std::vector<char> wide(count, 0);
     for (int ci = 0; ci < count; ++ci) wide[ci] = cs[ci].n >= tc_min_n;
 
@@ -885,6 +1003,7 @@ int qsim_batch_autotune(const qsim_circuit* cs, int count, void* stream_v, int* 
     int rc = validate_batch(cs, count);
     if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    batch::tune_cache_autoload();
     std::vector<int> seen(QSIM_MAX_QUBITS + 1, -1);
     for (int i = 0; i < count; ++i)
         if (seen[cs[i].n] < 0) seen[cs[i].n] = i;
@@ -927,7 +1046,75 @@ int qsim_batch_autotune(const qsim_circuit* cs, int count, void* stream_v, int* 
     cudaEventDestroy(e1);
     if (chosen)
         for (int i = 0; i < count; ++i) chosen[i] = batch::tuned_k(cs[i].n);
+    if (rc == QSIM_OK) batch::tune_cache_autosave();
     return rc;
+}
+
+int qsim_batch_autotune_threshold(const qsim_circuit* cs, int count, int precision, void* stream_v, int* best_min_n) {
+    set_error("%s", "");
+    int rc = validate_batch(cs, count);
+    if (rc) return rc;
+    if (precision < QSIM_PREC_TF32X3 || precision > QSIM_PREC_BF16X6) { set_error("a tensor-core precision is needed"); return QSIM_EINVAL; }
+    batch::tune_cache_autoload();
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
+    size_t wsb = 0;
+    if ((rc = qsim_batch_workspace_bytes(cs, count, &wsb)) != QSIM_OK) return rc;
+    void* ws = nullptr;
+    if (wsb && cudaMalloc(&ws, wsb) != cudaSuccess) { cudaGetLastError(); set_error("tuning workspace"); return QSIM_ENOMEM; }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, cs[i].n);
+    float best = 1e30f;
+    int bestn = 0;
+    // every candidate threshold, timed on the whole batch (median of three replays after a warm-up); a
+    // threshold above the widest circuit keeps every circuit in the persistent launch
+    for (int th : {14, 16, 18, 20, 22, 24, 27}) {
+        if (th > nmax + 1 && th != 27) continue;
+        qsim_run_opts o{};
+        o.mode = QSIM_RUN_FUSED;
+        o.precision = precision;
+        o.batch_tc_min_n = th;
+        qsim_batch_h b = nullptr;
+        if ((rc = qsim_batch_plan_create(cs, count, &o, stream_v, &b, nullptr)) != QSIM_OK) break;
+        float t[3] = {0, 0, 0};
+        rc = qsim_batch_execute(b, ws, wsb, stream_v, 1);
+        for (int r = 0; r < 3 && rc == QSIM_OK; ++r) {
+            cudaEventRecord(e0, s);
+            rc = qsim_batch_execute(b, ws, wsb, stream_v, 1);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        qsim_batch_destroy(b);
+        if (rc) break;
+        std::sort(t, t + 3);
+        if (t[1] < best) { best = t[1]; bestn = th; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ws) cudaFree(ws);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(batch::g_tune_mu);
+        batch::g_tuned_tc_min_n[precision] = bestn;
+    }
+    if (best_min_n) *best_min_n = bestn;
+    batch::tune_cache_autosave();
+    return QSIM_OK;
+}
+
+int qsim_batch_tune_save(const char* path) {
+    set_error("%s", "");
+    if (!path) { set_error("NULL path"); return QSIM_EINVAL; }
+    return batch::tune_save_file(path);
+}
+
+int qsim_batch_tune_load(const char* path) {
+    set_error("%s", "");
+    if (!path) { set_error("NULL path"); return QSIM_EINVAL; }
+    return batch::tune_load_file(path);
 }
 
 }  // extern "C"

@@ -127,6 +127,9 @@ SIGNATURES = {
     "qsim_batch_run": ([_P(Circuit), _i, _P(RunOpts), _vp, _sz, _vp, _P(ctypes.c_double), _P(ctypes.c_double),
                         _P(PlanInfo)], _i),
     "qsim_batch_autotune": ([_P(Circuit), _i, _vp, _P(_i)], _i),
+    "qsim_batch_autotune_threshold": ([_P(Circuit), _i, _i, _vp, _P(_i)], _i),
+    "qsim_batch_tune_save": ([ctypes.c_char_p], _i),
+    "qsim_batch_tune_load": ([ctypes.c_char_p], _i),
 }
 
 
@@ -557,3 +560,20 @@ def batch_autotune(circuits, stream=None):
     chosen = (ctypes.c_int * max(1, args.count))()
     _check(lib().qsim_batch_autotune(args.arr, args.count, ctypes.c_void_p(_stream_ptr(stream)), chosen))
     return list(chosen)[:args.count]
+
+
+def batch_autotune_threshold(circuits, precision: int = PREC_TF32X3, stream=None) -> int:
+    """Tune (and keep process-wide) the width from which batched circuits run as tensor-core plans."""
+    args = CircuitsArgs(circuits)
+    best = ctypes.c_int()
+    _check(lib().qsim_batch_autotune_threshold(args.arr, args.count, int(precision),
+                                               ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(best)))
+    return best.value
+
+
+def batch_tune_save(path: str) -> None:
+    _check(lib().qsim_batch_tune_save(os.fsencode(path)))
+
+
+def batch_tune_load(path: str) -> None:
+    _check(lib().qsim_batch_tune_load(os.fsencode(path)))

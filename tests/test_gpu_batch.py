@@ -181,3 +181,21 @@ def test_deep_wide_circuit_normalised(qsim):
     assert b.info["tc_blocks"] > 20
     b.execute()
     check(b.results(), cs)
+
+
+def test_threshold_tuner_and_tuning_file(qsim, tmp_path):
+    """The tensor-core threshold tuner times the whole batch per candidate and keeps the fastest; plans made
+    with the default threshold then use it, and stay correct; the table survives a save and load."""
+    cs = tfim_mix([12, 14, 16, 17, 18, 19, 20, 21, 15, 13], [2, 2, 2, 3, 2, 2, 2, 2, 3, 2], seed=21)
+    best = qsim.batch_autotune_threshold(cs, precision=1)
+    assert best in (14, 16, 18, 20, 22, 24, 27)
+    b = qsim.Batch(cs, max_fused=0, precision=1)            # tc_min_n = 0: the tuned threshold
+    wide = sum(1 for c in cs if c.n >= best)
+    assert (b.info["tc_blocks"] > 0) == (wide > 0)
+    b.execute(use_graph=True)
+    check(b.results(), cs)
+    path = tmp_path / "tune.json"
+    qsim.batch_tune_save(str(path))
+    qsim.batch_tune_load(str(path))
+    import json
+    assert json.loads(path.read_text())["tc_min_n"]["1"] == best
