@@ -165,7 +165,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {"dense_small": ["k_gates.cu"], "diag": ["k_gates.cu"], "dense_tile": ["k_gates.cu"],
-                  "tc": ["k_tc.cu", "tc_ptx.cuh", "tmem_io.cuh"]}
+                  "tc": ["k_tc.cu", "tc_ptx.cuh", "tmem_io.cuh"],
+                  "tc_pair": ["k_tc_pair.cu", "tc_ptx.cuh", "tmem_io.cuh"]}
 
 
 def source_sha(kind):
@@ -215,7 +216,7 @@ def tensor_rates(qsim, uuid, seconds):
     return out
 
 
-PREC_RATE = {1: "tf32", 2: "bf16", 3: "bf16"}
+PREC_RATE = {1: "tf32", 2: "bf16", 3: "bf16", 4: "fp16"}
 
 
 # ---- the simulation step -------------------------------------------------------------------------------------
@@ -229,6 +230,7 @@ PATHS = {
     "bf16x6": (1, 6, 3, 5),
     "tf32x3_k5": (1, 5, 1, 5),
     "bf16x6_k5": (1, 5, 3, 5),
+    "fp16x3": (1, 6, 4, 5),   # pairs of 6-qubit blocks in one pass (FP16 split products), other blocks 3xTF32
 }
 
 
@@ -254,7 +256,7 @@ def generates_input(plan):
     """True when the plan's first pass is a 3xTF32 / BF16x3 tensor-core block, which execute_from_basis runs
     on a generated basis state (its algorithmic bytes are then the writes alone)."""
     q = plan.pass_list[0] if plan.pass_list else None
-    return bool(q) and q["kind"] == "tc" and q["precision"] != 3
+    return bool(q) and q["kind"] in ("tc", "tc_pair") and q["precision"] != 3
 
 
 def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
@@ -436,7 +438,7 @@ def run_ours(args):
     st = qsim.State(n, qsim.C64)
 
     # candidate paths (tensor-core variants only where the library supports them)
-    cands = ["tf32x3", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
+    cands = ["fp16x3", "tf32x3", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
     plans = {}
     for name in cands + ["plain"]:
         try:
@@ -502,10 +504,11 @@ def run_ours(args):
         d["ms"] += ms
         d["bytes"] += info["algorithmic_bytes"] * (0.5 if (i == 0 and gen) else 1.0) * args.steps
         d["launches"] += args.steps
-        if info["kind"] == "tc":
-            mult = {1: 3, 2: 3, 3: 6}[info["precision"]]
+        if info["kind"] in ("tc", "tc_pair"):
+            mult = {1: 3, 2: 3, 3: 6, 4: 3}[info["precision"]]
+            blocks = 2 if info["kind"] == "tc_pair" else 1
             # real GEMM per amplitude: 2 * (2 * 2^k) MACs per complex output -> 8 * 2^k flops x split products
-            d["flops"] += (2.0 ** n) * 8 * (2 ** info["k"]) * mult * args.steps
+            d["flops"] += (2.0 ** n) * 8 * (2 ** info["k"]) * mult * blocks * args.steps
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     dk = by_kind[dom]
     avg_s = dk["ms"] / dk["launches"] / 1000.0
@@ -515,9 +518,9 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
             "traffic": profiled_traffic(dom, n), "kernel": dom, "launches_per_step": dk["launches"] // args.steps,
             "avg_launch_ms": avg_s * 1000.0, "share_of_step": dk["ms"] / total_ms, "peak_source": peak_src}
-    if dom == "tc" and dk["flops"] > 0 and rates is not None:
+    if dom in ("tc", "tc_pair") and dk["flops"] > 0 and rates is not None:
         tflops = dk["flops"] / dk["launches"] / avg_s / 1e12
-        prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == "tc"][0]]["precision"]
+        prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == dom][0]]["precision"]
         # the rate of the products' operand type, measured on this GPU in this run (tensor_rates)
         tpeak = rates[PREC_RATE[prec]]
         roof["tensor"] = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,

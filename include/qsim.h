@@ -56,6 +56,12 @@ extern "C" {
                               infidelity per block on a random state, 7.9e-10 after the 64 blocks of the
                               20-qubit depth-40 brickwork; never reported as a complex64-accuracy result */
 #define QSIM_PREC_BF16X6 3 /* tensor cores: 3-way BF16 split, 6 products, FP32 accumulation */
+/* Plans only: consecutive 6-qubit blocks whose targets together span at most 12 qubits run as ONE pass over
+   the state (two tensor-core products per tile while it is on chip) with FP16 split products: amplitudes
+   scaled by 2^15 and matrix entries by 2^14, each split into two FP16 parts, three products, FP32
+   accumulation (3xTF32-level accuracy; the state must be normalised, |amplitude| <= 1). The plan's other
+   tensor-core blocks run as QSIM_PREC_TF32X3. */
+#define QSIM_PREC_FP16X3 4
 
 /* Run modes. */
 #define QSIM_RUN_PLAIN 0 /* one device pass per gate (diagonal gates touch only their non-unit entries) */
@@ -238,6 +244,8 @@ int qsim_plan_destroy(qsim_plan_h plan);
 #define QSIM_PASS_REORDER 4     /* qubit reorder (exchange of index-bit pairs) */
 #define QSIM_PASS_PHASE 5       /* any number of 1- and 2-qubit diagonal gates on any qubits, one phase per
                                    amplitude (a quadratic form of its index bits) */
+#define QSIM_PASS_TC_PAIR 6     /* two 6-qubit tensor-core blocks in one pass (QSIM_PREC_FP16X3): targets[] holds
+                                   the first block's targets, controls[] (nc = 6) the second's */
 typedef struct {
     int32_t kind;             /* QSIM_PASS_* */
     int32_t k;                /* qubits the pass's matrix acts on (a reorder pass: exchanged pairs) */

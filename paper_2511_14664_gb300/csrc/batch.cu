@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(const __grid_constant__ A
 // ---- host side ----------------------------------------------------------------------------------------------
 std::mutex g_tune_mu;
 int g_tuned_k[QSIM_MAX_QUBITS + 1] = {0};
-int g_tuned_tc_min_n[4] = {0, 0, 0, 0};  // per tensor-core precision; 0 = not tuned (default 20)
+int g_tuned_tc_min_n[5] = {0, 0, 0, 0, 0};  // per tensor-core precision; 0 = not tuned (default 20)
 bool g_cache_loaded = false;
 
 int tuned_k(int n) {
@@ -352,7 +352,7 @@ int tuned_k(int n) {
 
 int tuned_tc_min_n(int precision) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    const int v = (precision >= 1 && precision <= 3) ? g_tuned_tc_min_n[precision] : 0;
+    const int v = (precision >= 1 && precision <= 4) ? g_tuned_tc_min_n[precision] : 0;
     return v ? v : 20;
 }
 
@@ -369,7 +369,7 @@ std::string tune_json() {
         }
     o += "}, \"tc_min_n\": {";
     first = true;
-    for (int p = 1; p <= 3; ++p)
+    for (int p = 1; p <= 4; ++p)
         if (g_tuned_tc_min_n[p]) {
             o += (first ? "\"" : ", \"") + std::to_string(p) + "\": " + std::to_string(g_tuned_tc_min_n[p]);
             first = false;
@@ -424,7 +424,7 @@ int tune_load_file(const char* path) {
             return QSIM_EINVAL;
         }
     for (const auto& kv : ts)
-        if (kv.first < 1 || kv.first > 3 || kv.second < 13 || kv.second > 27) {
+        if (kv.first < 1 || kv.first > 4 || kv.second < 13 || kv.second > 27) {
             set_error("%s: tc_min_n %d for precision %d out of range", path, kv.second, kv.first);
             return QSIM_EINVAL;
         }
@@ -566,7 +566,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     qsim_run_opts opts{};
     if (opts_in) opts = *opts_in;
     if (opts.max_fused < 0 || opts.max_fused > batch::kKmax) { set_error("batched fusion width must be 0 (tuned) or 1..%d", batch::kKmax); return QSIM_EINVAL; }
-    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
+    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_FP16X3) { set_error("unknown precision"); return QSIM_EINVAL; }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
     // circuits this wide run as tensor-core plans (6-qubit blocks need n >= 13); 0 = the tuned threshold
     batch::tune_cache_autoload();
@@ -1054,7 +1054,7 @@ int qsim_batch_autotune_threshold(const qsim_circuit* cs, int count, int precisi
     set_error("%s", "");
     int rc = validate_batch(cs, count);
     if (rc) return rc;
-    if (precision < QSIM_PREC_TF32X3 || precision > QSIM_PREC_BF16X6) { set_error("a tensor-core precision is needed"); return QSIM_EINVAL; }
+    if (precision < QSIM_PREC_TF32X3 || precision > QSIM_PREC_FP16X3) { set_error("a tensor-core precision is needed"); return QSIM_EINVAL; }
     batch::tune_cache_autoload();
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
     size_t wsb = 0;

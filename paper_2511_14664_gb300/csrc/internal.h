@@ -106,6 +106,18 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
                             const uint64_t* from_basis = nullptr, bool lines = false);
 bool tc_supported(int k, int precision);
 
+// ---- two 6-qubit blocks in one pass (k_tc_pair.cu, FP16 split products) -------------------------------------
+// True when blocks on t1 and then t2 (6 targets each, in their matrices' index order) fit one 13-bit tile of
+// an n-qubit state (|t1 u t2| <= 12, n >= 13).
+bool tc_pair_supported(int n, const int* t1, int k1, const int* t2, int k2);
+// Bytes of a pair's prepared operands: the real forms of U1 and U2 as FP16 hi / lo planes (4 x 32 KiB).
+size_t tc_pair_operand_bytes();
+// Prepare the operands from device FP64 matrices U1, U2 (64 x 64 complex each) into dops.
+cudaError_t launch_tc_pair_prepare(const double* dU1, const double* dU2, void* dops, cudaStream_t s);
+// Apply U1 on t1, then U2 on t2, to a complex64 state in one pass. from_basis: the input is that basis state.
+cudaError_t launch_tc_pair(void* psi, int n, const int* t1, const int* t2, const void* dops, unsigned* dev_err,
+                           cudaStream_t s, const DevInfo& d, const uint64_t* from_basis = nullptr);
+
 // ---- fused-block composition (k_compose.cu) -------------------------------------------------------------------
 struct ComposeGate {
     int k, nc;

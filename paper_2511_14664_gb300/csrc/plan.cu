@@ -21,7 +21,9 @@
 namespace qsim {
 
 enum OpKind { OP_DENSE_SMALL = 0, OP_DIAG = 1, OP_DENSE_TILE = 2, OP_TC = 3, OP_SWAP = 4, OP_PHASE = 5,
-              OP_MERGED = 6 /* a phase pass folded into the tensor-core block before it; dropped from the plan */ };
+              OP_MERGED = 6 /* a pass folded into the pass before it (phase epilogue, second block of a pair);
+                               dropped from the plan */,
+              OP_TC_PAIR = 7 /* two 6-qubit tensor-core blocks in one pass */ };
 
 struct PlanOp {
     int kind = OP_DENSE_SMALL;
@@ -43,6 +45,8 @@ struct PlanOp {
     bool lines = false;        // OP_TC: line-group data path (B prepared in its column order)
     TcEpiPacked epi;           // OP_TC with has_epi: launch parameters; tables at epi_off
     size_t epi_off = 0;
+    int targets2[6] = {0};     // OP_TC_PAIR: the second block's targets (the first block's are `targets`)
+    int compose_idx2 = -1;     // OP_TC_PAIR: the second block's composition
 };
 
 struct PlanExtra {
@@ -317,6 +321,10 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                                     op.has_epi ? static_cast<char*>(p->dbuf) + p->extra.epi_scratch_off : nullptr,
                                     fb, op.lines);
                 break;
+            case OP_TC_PAIR:
+                e = launch_tc_pair(h->psi, h->n, op.targets, op.targets2, static_cast<char*>(p->dbuf) + op.dev_off,
+                                   h->derr, h->stream, h->dev, fb);
+                break;
             case OP_MERGED:
                 break;
             case OP_SWAP:
@@ -353,7 +361,11 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     int kmax = opts.max_fused == 0 ? 5 : opts.max_fused;
     // dry runs (host-only pass counts) may also plan 7- and 8-qubit blocks, for sizing the fusion width
     if (kmax < 1 || kmax > (opts.dry_run ? 8 : 6)) { set_error("max_fused must be 1..6 (1..8 in a dry run)"); return QSIM_EINVAL; }
-    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_BF16X6) { set_error("unknown precision"); return QSIM_EINVAL; }
+    if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_FP16X3) { set_error("unknown precision"); return QSIM_EINVAL; }
+    // FP16X3: consecutive 6-qubit blocks are paired into one pass where they fit a tile; every other
+    // tensor-core block of the plan runs as a 3xTF32 block
+    const bool pair_blocks = opts.precision == QSIM_PREC_FP16X3;
+    if (pair_blocks) opts.precision = QSIM_PREC_TF32X3;
     const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
     const int n = c->n;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
@@ -614,6 +626,28 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         op.dev_off = dev_bytes;
         dev_bytes = align(dev_bytes + op.blob.size());
     }
+    // ---- pairs: two consecutive 6-qubit tensor-core blocks without epilogue whose tile fits take one pass ----
+    if (pair_blocks && !remap_later && dtype == QSIM_C64) {
+        for (size_t oi = 0; oi < p->ops.size(); ++oi) {
+            PlanOp& a = p->ops[oi];
+            if (a.kind != OP_TC || a.has_epi || a.k != 6 || a.nc != 0) continue;
+            size_t oj = oi + 1;
+            while (oj < p->ops.size() && p->ops[oj].kind == OP_MERGED) ++oj;
+            if (oj >= p->ops.size()) break;
+            PlanOp& b = p->ops[oj];
+            if (b.kind != OP_TC || b.has_epi || b.k != 6 || b.nc != 0 || !tc_pair_supported(n, a.targets, 6, b.targets, 6))
+                continue;
+            a.kind = OP_TC_PAIR;
+            std::memcpy(a.targets2, b.targets, sizeof(a.targets2));
+            a.compose_idx2 = b.compose_idx;
+            a.gates += b.gates;
+            a.precision = QSIM_PREC_FP16X3;
+            a.dev_off = dev_bytes;
+            dev_bytes = align(dev_bytes + tc_pair_operand_bytes());
+            b.kind = OP_MERGED;
+            oi = oj;
+        }
+    }
     size_t epi_scratch = 0;
     for (PlanOp& op : p->ops) {
         if (op.kind != OP_TC || !op.has_epi) continue;
@@ -663,6 +697,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         for (const Pending& pd : pending) {
             if (e != cudaSuccess) break;
             PlanOp& op = p->ops[pd.op];
+            if (op.kind == OP_TC_PAIR || op.kind == OP_MERGED) continue;  // pairs are prepared below
             const double* U = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx].out_off;
             const int D = 1 << pd.kb;
             if (pd.kind == OP_TC) {
@@ -678,6 +713,13 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 op.mat.resize(2 * (size_t)D * D);
                 e = cudaMemcpyAsync(op.mat.data(), U, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToHost, s);
             }
+        }
+        for (PlanOp& op : p->ops) {
+            if (e != cudaSuccess) break;
+            if (op.kind != OP_TC_PAIR) continue;
+            const double* U1 = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx].out_off;
+            const double* U2 = reinterpret_cast<double*>(base + off_out) + 2 * cblocks[op.compose_idx2].out_off;
+            e = launch_tc_pair_prepare(U1, U2, base + op.dev_off, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) {
@@ -853,6 +895,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         ++I.passes;
         if (op.kind == OP_DIAG || op.kind == OP_PHASE) ++I.diag_blocks;
         else if (op.kind == OP_TC) ++I.tc_blocks;
+        else if (op.kind == OP_TC_PAIR) I.tc_blocks += 2;
         else if (op.kind == OP_SWAP) ++I.reorders;
         else ++I.dense_blocks;
         I.algorithmic_bytes += op_bytes(op, n, amp);
@@ -918,6 +961,11 @@ int qsim_plan_pass_info(qsim_plan_h p, int64_t i, qsim_pass_info* out) {
             out->controls[j] = op.swap_b[j];
         }
     }
+    if (op.kind == OP_TC_PAIR) {  // the second block's targets in controls[]
+        out->kind = QSIM_PASS_TC_PAIR;
+        out->nc = 6;
+        for (int j = 0; j < 6; ++j) out->controls[j] = op.targets2[j];
+    }
     out->launches = op.kind == OP_TC && op.has_epi ? 2 : 1;
     out->reserved = 0;
     return QSIM_OK;
@@ -942,7 +990,7 @@ int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h p, uint64_t x, int64_t co
     if (count < 0) count = nops;
     if (count > nops) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
     // a first tensor-core block (3xTF32 / BF16x3) generates |x> as its input and writes every amplitude
-    if (count > 0 && p->ops[0].kind == OP_TC && p->ops[0].precision != QSIM_PREC_BF16X6)
+    if (count > 0 && ((p->ops[0].kind == OP_TC && p->ops[0].precision != QSIM_PREC_BF16X6) || p->ops[0].kind == OP_TC_PAIR))
         return enqueue_ops(h, p, 0, (size_t)count, &x);
     const int rc = qsim_set_basis(h, x);
     if (rc) return rc;

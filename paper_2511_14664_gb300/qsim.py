@@ -16,11 +16,12 @@ import numpy as np
 from . import build as _build
 
 C64, C128 = 0, 1
-PREC_SIMT, PREC_TF32X3, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3
+PREC_SIMT, PREC_TF32X3, PREC_BF16X3, PREC_BF16X6, PREC_FP16X3 = 0, 1, 2, 3, 4
 RUN_PLAIN, RUN_FUSED = 0, 1
 MAX_TARGETS = MAX_CONTROLS = 8
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
-PRECISIONS = {"simt": PREC_SIMT, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+PRECISIONS = {"simt": PREC_SIMT, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6,
+              "fp16x3": PREC_FP16X3}
 
 
 class QsimError(RuntimeError):
@@ -66,7 +67,7 @@ class SpillInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder", 5: "phase"}
+PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder", 5: "phase", 6: "tc_pair"}
 
 
 class PlanInfo(ctypes.Structure):

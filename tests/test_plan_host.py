@@ -24,8 +24,10 @@ def plan(qsim, c, dtype=0, **kw):
     ps = p.passes()
     assert sum(q["gates"] for q in ps) == len(c)
     for q in ps:
-        qubits = q["targets"] + q["controls"]
-        assert len(set(qubits)) == len(qubits) and all(0 <= x < c.n for x in qubits)
+        # a pair pass lists its second block's targets as controls: each block's qubits are distinct
+        groups = [q["targets"], q["controls"]] if q["kind"] == "tc_pair" else [q["targets"] + q["controls"]]
+        for qubits in groups:
+            assert len(set(qubits)) == len(qubits) and all(0 <= x < c.n for x in qubits)
     return p, ps
 
 
@@ -165,6 +167,28 @@ def test_plan_effort_beam_never_more_passes_and_places_every_gate(qsim):
     _, a = plan(qsim, cases[0], **TC6)
     _, b = plan(qsim, cases[0], plan_effort=2, **TC6)
     assert len(b) < len(a)
+
+
+@pytest.mark.parametrize("make", [lambda: W.brickwork(30, 40, seed=3), lambda: W.rcs(33, seed=3), lambda: W.qft(28),
+                                  lambda: W.tfim_lattice(11, 3, 10, 0.27, 0.74)])
+def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
+    """A QSIM_PREC_FP16X3 plan pairs consecutive 6-qubit blocks: with every pair unrolled into its two
+    blocks, the pass sequence is exactly the 3xTF32 plan's, each pair's targets span at most 12 qubits,
+    and the merged gate counts add up."""
+    c = make()
+    _, single = plan(qsim, c, **TC6)
+    _, paired = plan(qsim, c, mode=1, max_fused=6, precision=4, tc_min_k=5)
+    unrolled = []
+    for q in paired:
+        if q["kind"] == "tc_pair":
+            assert q["k"] == 6 and q["nc"] == 6 and len(set(q["targets"]) | set(q["controls"])) <= 12
+            unrolled.append(("tc", q["targets"]))
+            unrolled.append(("tc", q["controls"]))
+        else:
+            unrolled.append((q["kind"], q["targets"]))
+    assert unrolled == [(q["kind"], q["targets"]) for q in single]
+    assert sum(q["gates"] for q in paired) == len(c)
+    assert sum(1 for q in paired if q["kind"] == "tc_pair") >= len(single) // 4
 
 
 @pytest.mark.parametrize("L", [16, 18, 22])
