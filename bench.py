@@ -60,7 +60,7 @@ def parse_args():
     p.add_argument("--nmax", type=int, default=24, help="tfim_batch: largest circuit width")
     p.add_argument("--workload", default="brickwork30",
                    choices=["brickwork30", "qft28", "tfim_batch", "pairs34", "brick14", "qpe33", "rcs33", "tfim33",
-                            "spill33"],
+                            "spill33", "passes"],
                    help="brickwork30 (the headline line), qft28, tfim_batch (256 TFIM circuits), pairs34, "
                         "brick14 (14-qubit complex128, latency-bound)")
     return p.parse_args()
@@ -1147,6 +1147,41 @@ def run_spill(args):
     return 0
 
 
+def run_passes(args):
+    """Every pass of the brickwork plan timed on its own (CUDA events around five repeats of the pass, after
+    one untimed), for the paths named by --path (comma-separated; default tf32x3,fp16x3): per pass its kind,
+    qubits and milliseconds. A profiling aid: it shows which passes of a plan are slow."""
+    import torch
+    import workloads as W
+    from paper_2511_14664_gb300 import qsim
+    n, depth = args.n, args.depth
+    c = W.brickwork(n, depth, seed=SEED)
+    st = qsim.State(n, qsim.C64)
+    paths = ["tf32x3", "fp16x3"] if args.path == "auto" else args.path.split(",")
+    out = {}
+    for name in paths:
+        p = make_plan(qsim, c, name)
+        ps = p.passes()
+        st.set_basis(0)
+        p.execute(st)
+        torch.cuda.synchronize()
+        rows = []
+        for i, q in enumerate(ps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p.execute_range(st, i, 1)
+            e0.record()
+            for _ in range(5):
+                p.execute_range(st, i, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            rows.append({"kind": q["kind"], "targets": q["targets"], "second": q["controls"] if q["kind"] == "tc_pair" else [],
+                         "ms": e0.elapsed_time(e1) / 5})
+        out[name] = {"passes": rows, "total_ms": sum(r["ms"] for r in rows)}
+        p.close()
+    print(json.dumps({"workload": f"random brickwork n={n} depth={depth} seed={SEED}", "per_pass": out}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1165,6 +1200,8 @@ def main():
         return run_paper33(args, "tfim")
     if args.workload == "spill33":
         return run_spill(args)
+    if args.workload == "passes":
+        return run_passes(args)
     return run_ours(args)
 
 

@@ -5,7 +5,7 @@
 // memory traffic of the pair. Blocks U1 (targets T1) and then U2 (targets T2) with |T1 u T2| <= 12 share a
 // tile of 13 index bits S (T1 u T2 plus the lowest other qubits): 8192 amplitudes, read once and written once.
 //
-// Per tile (one CTA per SM, 8 data warps + 1 MMA-issuing warp):
+// Per tile (one CTA per SM, 16 data warps + 1 MMA-issuing warp):
 //   1. The data warps load the tile as X[r1][c1] -- rows r1 over the 7 bits R1 = S \ T1 (TMEM lanes), columns
 //      over T1 -- and store its FP16 planes (below) in tensor memory as the A operand.
 //   2. MMA 1: D1 = A1 . B1^T with B1 the real form of U1 in shared memory: D1[r1][i] = (U1 x_{r1})_i.
@@ -39,7 +39,10 @@ using namespace qsim::tc;
 
 constexpr int kTileBits = 13;
 constexpr int kRowBits = 7;
-constexpr int kDataWarps = 8;
+constexpr int kDataWarps = 16;                    // four per TMEM lane quadrant
+constexpr int kCPT = 64 / (kDataWarps / 4);       // complex columns of the first product per thread (16)
+constexpr int kNPT = 128 / (kDataWarps / 4);      // accumulator columns of the second product per thread (32)
+constexpr int kDataThreads = kDataWarps * 32;
 constexpr int kThreads = (kDataWarps + 1) * 32;
 constexpr int kPlane = 128 * 128 * 2;             // one FP16 plane of a 128 x 128 real-form operand (32 KiB)
 constexpr int kAtom = 128 * 128;                  // bytes of one 128-byte-wide K atom of a 128-row operand
@@ -61,6 +64,12 @@ struct PairArgs {
     // (value - 8) of n2
     uint8_t r1_to[kRowBits];
     uint8_t t1_to[6];
+    // output staging: amplitude at tile index t (13 bits, S order) goes to the 8-byte word t ^ f(t >> 4) of
+    // the staging buffer, f linear with f(bit j) = fmask[j]: chosen per pair so that the scattered writes of
+    // a warp fall in distinct bank groups
+    uint8_t t2s[6];       // position in S of t2pos[j]
+    uint8_t r2s[kRowBits];// position in S of r2pos[j]
+    uint8_t fmask[kTileBits - 4];
     uint64_t ntiles;
     int from_basis;
     uint64_t basis;
@@ -112,7 +121,7 @@ __device__ __forceinline__ void commit_to(uint32_t bar) {
 }
 
 // TMEM: two slots of 256 columns; slot s holds A1 hi (cols 0..63), A1 lo (64..127) and the accumulator
-// (128..255), which MMA 1 and MMA 2 use in turn. A tile i lives in slot i & 1 from its load to its store.
+// (128..255), which MMA 1 and MMA 2 use in turn. A tile j lives in slot j & 1 from its load to its store.
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_pair(float2* __restrict__ psi, const __grid_constant__ PairArgs a, const uint4* __restrict__ ops,
           unsigned* __restrict__ err) {
@@ -120,20 +129,46 @@ k_tc_pair(float2* __restrict__ psi, const __grid_constant__ PairArgs a, const ui
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* sCol1 = reinterpret_cast<uint64_t*>(sb + kOffTab);  // [64] index offset of T1 column c
-    uint64_t* sN2 = sCol1 + 64;                                   // [128] index offset of R2 column n2
-    uint32_t* sMap1 = reinterpret_cast<uint32_t*>(sN2 + 128);     // [64] T1 column c -> t2 bits | n2 bits << 8
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sMap1 + 64);     // full1[2] done1[2] full2 done2[2] bops
+    uint64_t* sDepLo = sCol1 + 64;                                // [512] index offset of tile bits 0..8
+    uint64_t* sDepHi = sDepLo + 512;                              // [16] index offset of tile bits 9..12
+    uint32_t* sP2 = reinterpret_cast<uint32_t*>(sDepHi + 16);     // [64] T1 column c: B2 byte offset part | xor part << 16
+    uint32_t* sStN2 = sP2 + 64;                                   // [128] staging word part of R2 column n2
+    uint32_t* sFj = sStN2 + 128;                                  // [16] f of tile bits 9..12
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sFj + 16);       // full1[2] done1[2] full2 done2[2] bops
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto fswz = [&](uint32_t hi9) {  // f of tile bits 4..12 (given shifted down by 4)
+        uint32_t f = 0;
+        for (int b = 0; b < kTileBits - 4; ++b) if ((hi9 >> b) & 1) f ^= a.fmask[b];
+        return f;
+    };
+    // B2 byte offset of (n2, t2) = additive part + ((xor part) << 4): the SWIZZLE_128B offset of element
+    // (n2, 2 t2) splits over disjoint bit sets of (n2, t2), and the row's and the column's parts combine so
+    // (the 16-byte chunk index is t2 bits 2..4 XOR n2 bits 0..2)
+    auto b2part = [](uint32_t n2, uint32_t t2, uint32_t& add, uint32_t& x) {
+        add = (t2 >> 5) * (uint32_t)kAtom + (n2 >> 3) * 1024u + (n2 & 7u) * 128u + 4u * (t2 & 3u);
+        x = ((t2 >> 2) & 7u) ^ (n2 & 7u);
+    };
     for (int c = tid; c < 64; c += kThreads) {
         sCol1[c] = deposit((uint64_t)c, a.t1pos, 6);
         uint32_t t2 = 0, n2 = 0;
         for (int j = 0; j < 6; ++j)
             if ((c >> j) & 1) { if (a.t1_to[j] < 8) t2 |= 1u << a.t1_to[j]; else n2 |= 1u << (a.t1_to[j] - 8); }
-        sMap1[c] = t2 | (n2 << 8);
+        uint32_t add, x;
+        b2part(n2, t2, add, x);
+        sP2[c] = add | (x << 16);
     }
-    for (int c = tid; c < 128; c += kThreads) sN2[c] = deposit((uint64_t)c, a.r2pos, kRowBits);
+    for (int c = tid; c < 512; c += kThreads) sDepLo[c] = deposit((uint64_t)c, a.spos, 9);
+    for (int c = tid; c < 16; c += kThreads) {
+        sDepHi[c] = deposit((uint64_t)c, a.spos + 9, kTileBits - 9);
+        sFj[c] = fswz((uint32_t)c << 5);
+    }
+    for (int c = tid; c < 128; c += kThreads) {
+        uint32_t t = 0;
+        for (int j = 0; j < kRowBits; ++j) if ((c >> j) & 1) t |= 1u << a.r2s[j];
+        sStN2[c] = t ^ fswz(t >> 4);
+    }
     if (tid == 0) {
         for (int j = 0; j < 8; ++j) {
             const uint32_t cnt = (j < 2 || j == 4) ? kDataWarps : 1;  // full1[0..1], full2: one arrival per data warp
@@ -238,17 +273,24 @@ k_tc_pair(float2* __restrict__ psi, const __grid_constant__ PairArgs a, const ui
         }
         __syncwarp();
     } else {
-        // ---- data warps: thread = TMEM lane r of its quadrant, half of the columns ----
-        const int quad = warp & 3, half = (warp >> 2) & 1;
+        // ---- data warps: thread = TMEM lane r of its quadrant; four warps per quadrant split the columns ----
+        const int quad = warp & 3, grp = warp >> 2;
         const int r = quad * 32 + lane;
         const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-        const int c0 = half * 32;
+        const int c0 = grp * kCPT;  // first-product columns c0 .. c0 + 15
         const uint64_t rowoff1 = deposit((uint64_t)r, a.r1pos, kRowBits);
         uint32_t t2r = 0, n2r = 0;  // this row's bits in the second product's coordinates
         for (int j = 0; j < kRowBits; ++j)
             if ((r >> j) & 1) { if (a.r1_to[j] < 8) t2r |= 1u << a.r1_to[j]; else n2r |= 1u << (a.r1_to[j] - 8); }
+        uint32_t addr_r, xr;
+        b2part(n2r, t2r, addr_r, xr);
         const int ro = r & 1;
-        const uint64_t outoff = deposit((uint64_t)(r >> 1), a.t2pos, 6);
+        uint32_t wi2 = 0;  // staging word part of this lane's output row i2 = r / 2
+        for (int j = 0; j < 6; ++j) if (((r >> 1) >> j) & 1) wi2 |= 1u << a.t2s[j];
+        wi2 ^= fswz(wi2 >> 4);
+        const int k = tid;  // 0..511: this thread's staging reads are tile indices k + 512 jj
+        const uint64_t deplo = sDepLo[k];
+        const uint32_t fk = fswz((uint32_t)k >> 4);
         const volatile uint64_t* vCol = sCol1 + c0;
         const uint32_t sB2 = smem_u32(sb + kOffB2);
         auto wait = [&](uint32_t bar, uint32_t par) -> bool {
@@ -256,42 +298,44 @@ k_tc_pair(float2* __restrict__ psi, const __grid_constant__ PairArgs a, const ui
             fence_after();
             return ok;
         };
-        float2 X[32];
+        auto data_sync = [&]() { asm volatile("bar.sync 1, %0;" :: "r"(kDataThreads) : "memory"); };
+        float2 X[kCPT];
         auto load = [&](uint64_t t) {
             const uint64_t b = insert_zeros(t, a.spos, kTileBits) + rowoff1;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < kCPT; ++j) {
                 const uint64_t o = b + vCol[j];
                 X[j] = a.from_basis ? make_float2(o == a.basis ? 1.0f : 0.0f, 0.0f) : psi[o];
                 asm volatile("" ::: "memory");
             }
         };
-        // 1: FP16 planes of the tile into A1 of slot s
-        auto p1 = [&](int s) {
-            uint32_t hi[32], lo[32];
+        // FP16 planes of the tile in X into A1 of slot s (arrival on full1[s] comes later: the slot's
+        // accumulator may still hold the previous tile's output)
+        auto p1_write = [&](int s) {
+            uint32_t hi[kCPT], lo[kCPT];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) split_f16x2(X[j].x * kScaleX, X[j].y * kScaleX, hi[j], lo[j]);
-            tmem_st_x32(tbase + tlane + 256u * s + (uint32_t)c0, hi);
-            tmem_st_x32(tbase + tlane + 256u * s + 64u + (uint32_t)c0, lo);
+            for (int j = 0; j < kCPT; ++j) split_f16x2(X[j].x * kScaleX, X[j].y * kScaleX, hi[j], lo[j]);
+            tmem_st_x16(tbase + tlane + 256u * s + (uint32_t)c0, hi);
+            tmem_st_x16(tbase + tlane + 256u * s + 64u + (uint32_t)c0, lo);
             wait_st();
+        };
+        auto p1_arrive = [&](int s) {
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(full1(s));
         };
-        // 3: D1 of slot s into the B operand of the second product (rows n2, K = 2 t2 + part)
+        // D1 of slot s into the B operand of the second product (rows n2, K = 2 t2 + part)
         auto p2 = [&](int s, uint32_t par) -> bool {
             if (!wait(done1(s), par)) return false;
-            uint32_t v[64];
-            tmem_ld_x32(tbase + tlane + 256u * s + 128u + 2u * c0, *reinterpret_cast<uint32_t(*)[32]>(v));
-            tmem_ld_x32(tbase + tlane + 256u * s + 160u + 2u * c0, *reinterpret_cast<uint32_t(*)[32]>(v + 32));
+            uint32_t v[2 * kCPT];
+            tmem_ld_x32(tbase + tlane + 256u * s + 128u + 2u * c0, v);
             wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const uint32_t mp = sMap1[c0 + j];
-                const uint32_t t2 = t2r | (mp & 0xFFu), n2 = n2r | (mp >> 8);
+            for (int j = 0; j < kCPT; ++j) {
+                const uint32_t mp = sP2[c0 + j];
+                const uint32_t off = addr_r + (mp & 0xFFFFu) + ((xr ^ (mp >> 16)) << 4);
                 uint32_t hi, lo;
                 split_f16x2(__uint_as_float(v[2 * j]) * kX1toX2, __uint_as_float(v[2 * j + 1]) * kX1toX2, hi, lo);
-                const uint32_t off = sw128_f16((int)n2, (int)(2 * t2));
                 asm volatile("st.shared.u32 [%0], %1;" :: "r"(sB2 + off), "r"(hi) : "memory");
                 asm volatile("st.shared.u32 [%0], %1;" :: "r"(sB2 + (uint32_t)kPlane + off), "r"(lo) : "memory");
             }
@@ -301,39 +345,57 @@ k_tc_pair(float2* __restrict__ psi, const __grid_constant__ PairArgs a, const ui
             if (lane == 0) mbar_arrive(full2);
             return true;
         };
-        // 4: D2 of slot s to the state (real and imaginary parts paired across adjacent lanes)
+        // D2 of slot s to the state: real and imaginary parts paired across adjacent lanes, staged in tile
+        // order in the (now free) B2 buffer, then stored in tile order so that a warp writes the longest
+        // contiguous runs the tile has
         auto p3 = [&](int s, uint32_t par, uint64_t t) -> bool {
             if (!wait(done2(s), par)) return false;
-            uint32_t w[64];
-            tmem_ld_x32(tbase + tlane + 256u * s + 128u + 64u * half, *reinterpret_cast<uint32_t(*)[32]>(w));
-            tmem_ld_x32(tbase + tlane + 256u * s + 160u + 64u * half, *reinterpret_cast<uint32_t(*)[32]>(w + 32));
+            uint32_t w[kNPT];
+            tmem_ld_x32(tbase + tlane + 256u * s + 128u + (uint32_t)(kNPT * grp), w);
             wait_ld();
             fence_before();
-            const uint64_t b = insert_zeros(t, a.spos, kTileBits) + outoff;
-            const int nb = 64 * half + (ro ? 32 : 0);  // this lane's 32 columns after the exchange
+            constexpr int H = kNPT / 2;
+            const int nb = kNPT * grp + (ro ? H : 0);  // this lane's 16 columns after the exchange
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float mine = __uint_as_float(ro ? w[32 + j] : w[j]);
-                const float got = __shfl_xor_sync(0xffffffffu, __uint_as_float(ro ? w[j] : w[32 + j]), 1);
+            for (int j = 0; j < H; ++j) {
+                const float mine = __uint_as_float(ro ? w[H + j] : w[j]);
+                const float got = __shfl_xor_sync(0xffffffffu, __uint_as_float(ro ? w[j] : w[H + j]), 1);
                 const float re = ro ? got : mine, im = ro ? mine : got;
-                psi[b + sN2[nb + j]] = make_float2(re * kOut, im * kOut);
-                asm volatile("" ::: "memory");
+                const uint32_t word = wi2 ^ sStN2[nb + j];
+                asm volatile("st.shared.v2.f32 [%0], {%1, %2};" :: "r"(sB2 + 8u * word), "f"(re * kOut), "f"(im * kOut)
+                             : "memory");
             }
+            data_sync();
+            const uint64_t b = insert_zeros(t, a.spos, kTileBits) + deplo;
+#pragma unroll 8
+            for (int jj = 0; jj < 16; ++jj) {
+                const uint32_t word = ((uint32_t)(k + 512 * jj)) ^ (fk ^ sFj[jj]);
+                float2 y;
+                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(y.x), "=f"(y.y) : "r"(sB2 + 8u * word) : "memory");
+                psi[b + sDepHi[jj]] = y;
+            }
+            data_sync();  // the staging buffer is the next tile's B2
             return true;
         };
+        // Tile j lives in TMEM slot j & 1. Per iteration: finish MMA 1 of tile j (p2), fill tile j + 2's A1
+        // while MMA 2 of tile j runs, store tile j (p3), then release slot j & 1 to tile j + 2.
         bool bad = false;
-        if (m > 0) load(t0);
-        for (uint64_t i = 0; i < m && !bad; ++i) {
-            p1((int)(i & 1));
-            if (i + 1 < m) load(t0 + (i + 1) * G);
-            if (i >= 1) {
-                const uint64_t j = i - 1;
-                bad = !p2((int)(j & 1), (uint32_t)((j >> 1) & 1)) || !p3((int)(j & 1), (uint32_t)((j >> 1) & 1), t0 + j * G);
-            }
+        for (uint64_t j = 0; j < 2 && j < m; ++j) {
+            load(t0 + j * G);
+            p1_write((int)j);
+            p1_arrive((int)j);
         }
-        if (!bad && m > 0) {
-            const uint64_t j = m - 1;
-            bad = !p2((int)(j & 1), (uint32_t)((j >> 1) & 1)) || !p3((int)(j & 1), (uint32_t)((j >> 1) & 1), t0 + j * G);
+        if (m > 2) load(t0 + 2 * G);
+        for (uint64_t j = 0; j < m && !bad; ++j) {
+            const int s = (int)(j & 1);
+            const uint32_t par = (uint32_t)((j >> 1) & 1);
+            if (!p2(s, par)) { bad = true; break; }
+            if (j + 2 < m) p1_write(s);
+            if (!p3(s, par, t0 + j * G)) { bad = true; break; }
+            if (j + 2 < m) {
+                p1_arrive(s);
+                if (j + 3 < m) load(t0 + (j + 3) * G);
+            }
         }
         if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
     }
@@ -376,6 +438,25 @@ bool pair_geometry(int n, const int* t1, const int* t2, tcp::PairArgs& a) {
     };
     for (int j = 0; j < tcp::kRowBits; ++j) a.r1_to[j] = to2(a.r1pos[j]);
     for (int j = 0; j < 6; ++j) a.t1_to[j] = to2(a.t1pos[j]);
+    auto in_s = [&](int q) -> uint8_t {
+        for (int j = 0; j < tcp::kTileBits; ++j) if (a.spos[j] == q) return (uint8_t)j;
+        return 0xFF;
+    };
+    for (int j = 0; j < 6; ++j) a.t2s[j] = in_s(a.t2pos[j]);
+    for (int j = 0; j < tcp::kRowBits; ++j) a.r2s[j] = in_s(a.r2pos[j]);
+    // The staging writes of a half-warp (8-byte accesses are served per half-warp) vary, per lane bit 0..3,
+    // in tile bits: n2 bit 4 (which half of a thread's columns), then t2 bits 0..2 (lane bit 4, t2 bit 3,
+    // only separates the half-warps). Tile bits 0..3 index bank groups directly; each higher one of these
+    // four gets a unit vector the lower ones leave free, so the 16 lanes hit 16 different bank groups.
+    const int vary[4] = {a.r2s[4], a.t2s[0], a.t2s[1], a.t2s[2]};
+    unsigned used = 0;
+    for (int v : vary) if (v < 4) used |= 1u << v;
+    for (int v : vary) {
+        if (v < 4) continue;
+        int unit = -1;
+        for (int u = 0; u < 4 && unit < 0; ++u) if (!((used >> u) & 1)) unit = u;
+        if (unit >= 0) { a.fmask[v - 4] = (uint8_t)(1u << unit); used |= 1u << unit; }
+    }
     a.ntiles = 1ull << (n - tcp::kTileBits);
     return true;
 }
@@ -403,7 +484,8 @@ cudaError_t launch_tc_pair(void* psi, int n, const int* t1, const int* t2, const
     if ((reinterpret_cast<uintptr_t>(dops) & 15) != 0) return cudaErrorInvalidValue;
     if (from_basis) { a.from_basis = 1; a.basis = *from_basis; }
     // operands, tables and barriers; at least 120 KiB, so that one CTA (one TMEM owner) runs per SM
-    const size_t smem = std::max<size_t>((size_t)tcp::kOffTab + 64 * 8 + 128 * 8 + 64 * 4 + 8 * 8 + 16 + 1024, 120 * 1024);
+    const size_t smem = std::max<size_t>((size_t)tcp::kOffTab + (64 + 512 + 16) * 8 + (64 + 128 + 16) * 4 + 8 * 8 + 16 + 1024,
+                                         120 * 1024);
     cudaError_t e = cudaFuncSetAttribute(tcp::k_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
