@@ -230,13 +230,16 @@ PATHS = {
     "bf16x6": (1, 6, 3, 5),
     "tf32x3_k5": (1, 5, 1, 5),
     "bf16x6_k5": (1, 5, 3, 5),
-    "fp16x3": (1, 6, 4, 5),   # pairs of 6-qubit blocks in one pass (FP16 split products), other blocks 3xTF32
+    "fp16x3": (1, 6, 4, 5),        # FP16 split products (3xTF32 where a block has the line-group / pair-rows path)
+    "fp16x3_pairs": (1, 6, 4, 5, 1),  # the same, consecutive blocks paired into one pass
 }
 
 
 def make_plan(qsim, circuit, path, use_graph=False):
-    mode, k, prec, tcmin = PATHS[path]
-    return qsim.Plan(circuit, qsim.C64, mode=mode, max_fused=k, precision=prec, tc_min_k=tcmin, use_graph=use_graph)
+    mode, k, prec, tcmin = PATHS[path][:4]
+    pairs = len(PATHS[path]) > 4 and PATHS[path][4] == 1
+    return qsim.Plan(circuit, qsim.C64, mode=mode, max_fused=k, precision=prec, tc_min_k=tcmin, use_graph=use_graph,
+                     pair_blocks=pairs)
 
 
 def count_readout_launches(n):
@@ -438,7 +441,7 @@ def run_ours(args):
     st = qsim.State(n, qsim.C64)
 
     # candidate paths (tensor-core variants only where the library supports them)
-    cands = ["fp16x3", "tf32x3", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
+    cands = ["fp16x3", "tf32x3", "fp16x3_pairs", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
     plans = {}
     for name in cands + ["plain"]:
         try:
@@ -1149,7 +1152,7 @@ def run_spill(args):
 
 def run_passes(args):
     """Every pass of the brickwork plan timed on its own (CUDA events around five repeats of the pass, after
-    one untimed), for the paths named by --path (comma-separated; default tf32x3,fp16x3): per pass its kind,
+    one untimed), for the paths named by --path (comma-separated; default tf32x3,fp16x3,fp16x3_pairs): per pass its kind,
     qubits and milliseconds. A profiling aid: it shows which passes of a plan are slow."""
     import torch
     import workloads as W
@@ -1157,7 +1160,7 @@ def run_passes(args):
     n, depth = args.n, args.depth
     c = W.brickwork(n, depth, seed=SEED)
     st = qsim.State(n, qsim.C64)
-    paths = ["tf32x3", "fp16x3"] if args.path == "auto" else args.path.split(",")
+    paths = ["tf32x3", "fp16x3", "fp16x3_pairs"] if args.path == "auto" else args.path.split(",")
     out = {}
     for name in paths:
         p = make_plan(qsim, c, name)

@@ -56,11 +56,11 @@ extern "C" {
                               infidelity per block on a random state, 7.9e-10 after the 64 blocks of the
                               20-qubit depth-40 brickwork; never reported as a complex64-accuracy result */
 #define QSIM_PREC_BF16X6 3 /* tensor cores: 3-way BF16 split, 6 products, FP32 accumulation */
-/* Plans only: consecutive 6-qubit blocks whose targets together span at most 12 qubits run as ONE pass over
-   the state (two tensor-core products per tile while it is on chip) with FP16 split products: amplitudes
-   scaled by 2^15 and matrix entries by 2^14, each split into two FP16 parts, three products, FP32
-   accumulation (3xTF32-level accuracy; the state must be normalised, |amplitude| <= 1). The plan's other
-   tensor-core blocks run as QSIM_PREC_TF32X3. */
+/* tensor cores: FP16 split products with fixed scales -- amplitudes x 2^15 (the state must be normalised,
+   |amplitude| <= 1), matrix entries x 2^14, each split into two FP16 parts (22 significant bits, as 3xTF32),
+   three products, FP32 accumulation. Half the tensor cycles and A-operand traffic of 3xTF32. In plans,
+   blocks whose 3xTF32 form has the line-group or pair-rows data path (low qubits among the targets) run as
+   QSIM_PREC_TF32X3; see also qsim_run_opts.pair_blocks. */
 #define QSIM_PREC_FP16X3 4
 
 /* Run modes. */
@@ -119,7 +119,10 @@ typedef struct {
        (30-qubit brickwork 64 -> 62 passes, 33-qubit paper random circuit 45 -> 44 / 42; planning 5-20x
        slower than greedy). */
     int32_t plan_effort;
-    int32_t reserved;
+    /* QSIM_PREC_FP16X3 plans only: 1 = also run consecutive 6-qubit blocks whose targets together span at most
+       12 qubits as ONE pass (both products per tile while it is on chip). Correct, but measured slower than
+       two single passes on GB300 (the pass is bound by instruction issue, not memory); for study. */
+    int32_t pair_blocks;
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */
@@ -201,7 +204,8 @@ int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, in
 
 /*
  * Apply a dense 2^k x 2^k block (1 <= k <= 8) on `targets` with the given QSIM_PREC_* arithmetic.
- * Tensor-core precisions need a complex64 state and k in 5..6 (QSIM_EUNSUPPORTED otherwise);
+ * Tensor-core precisions (TF32X3, BF16X3, BF16X6, FP16X3) need a complex64 state and k in 5..6
+ * (QSIM_EUNSUPPORTED otherwise);
  * QSIM_PREC_SIMT works for both types and every k.
  * This is the single-block form of what QSIM_RUN_FUSED plans produce.
  */

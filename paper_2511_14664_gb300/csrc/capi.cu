@@ -285,7 +285,7 @@ int qsim_apply_fused(qsim_h h, const int* targets, int k, const double* matrix, 
     int rc = validate_qubits(h->n, targets, k, nullptr, 0, QSIM_MAX_TARGETS);
     if (rc) return rc;
     if (!matrix) { set_error("NULL matrix"); return QSIM_EINVAL; }
-    if (precision < QSIM_PREC_SIMT || precision > QSIM_PREC_BF16X6) { set_error("unknown precision %d", precision); return QSIM_EINVAL; }
+    if (precision < QSIM_PREC_SIMT || precision > QSIM_PREC_FP16X3) { set_error("unknown precision %d", precision); return QSIM_EINVAL; }
     if (precision == QSIM_PREC_SIMT) {
         if (k <= 4) {
             cudaError_t e = launch_dense_small(h->dtype, h->psi, h->n, k, targets, 0, nullptr, matrix, h->stream, h->dev);

@@ -30,6 +30,7 @@
 //   is stored.
 //   BF16x6 (k_tc_block_a2): 16 warps; two A buffers and one accumulator; one thread issues the MMAs.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -55,6 +56,18 @@ template <> struct Cfg<QSIM_PREC_BF16X3> {
     __host__ __device__ static constexpr int pa(int i) { return i == 0 ? 1 : 0; }
     __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
+// FP16 split products: amplitudes scaled by 2^15 (|a| <= 1 for a normalised state) and matrix entries by
+// 2^14, each split into two FP16 parts (hardware conversion), three products, FP32 accumulation; the output
+// is scaled back by 2^-29. 22 significant bits like 3xTF32, at the FP16 tensor rate and with half the
+// tensor-memory traffic for A.
+template <> struct Cfg<QSIM_PREC_FP16X3> {
+    static constexpr int planes = 2, esize = 2, nprod = 3;
+    __host__ __device__ static constexpr int pa(int i) { return i == 0 ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
+};
+constexpr float kF16ScaleX = 32768.0f;              // 2^15
+constexpr double kF16ScaleU = 16384.0;              // 2^14
+constexpr float kF16Out = 1.0f / (32768.0f * 16384.0f);
 template <> struct Cfg<QSIM_PREC_BF16X6> {
     static constexpr int planes = 3, esize = 2, nprod = 6;  // all products of planes i + j <= 2
     // (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
@@ -158,7 +171,8 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     constexpr bool P0 = MODE == kPairsInLanes, Q0 = MODE == kQuadsInLanes, LG = MODE == kLineGroups,
                    PR = MODE == kPairRows;
     using C = Cfg<PREC>;
-    constexpr bool BF16 = C::esize == 2;
+    constexpr bool BF16 = C::esize == 2;                   // any 16-bit operand type (packed re / im pairs)
+    constexpr bool F16 = PREC == QSIM_PREC_FP16X3;         // FP16 with fixed scales
     constexpr int P = C::planes;
     constexpr int D = 1 << K, NR = 2 * D;
     constexpr int PB = plane_bytes(K, C::esize);
@@ -170,7 +184,7 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
     constexpr int ACOLS = BF16 ? NR / 2 : NR;              // TMEM columns per A plane (BF16: re / im packed)
     constexpr int A0 = 2 * NR;                             // TMEM: D0 [0, NR), D1 [NR, 2 NR), A planes
     constexpr uint32_t TCOLS = pow2_at_least(A0 + P * ACOLS);
-    constexpr uint32_t FMT = BF16 ? 1u : 2u;
+    constexpr uint32_t FMT = F16 ? 0u : (BF16 ? 1u : 2u);
     constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(NR >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
     static_assert(CPT % QC == 0 && CPT % QE == 0, "whole chunks per thread");
@@ -433,7 +447,17 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
 #pragma unroll
                     for (int j = 0; j < QC; ++j) {
                         const float2 x = X[h * QC + j];
-                        if constexpr (BF16) {
+                        if constexpr (F16) {
+                            // (re, im) scaled; plane 0 = FP16 value, plane 1 = FP16 residual (re in the low half)
+                            const float re = x.x * kF16ScaleX, im = x.y * kF16ScaleX;
+                            uint32_t h;
+                            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(im), "f"(re));
+                            if (p) {
+                                const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&h));
+                                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(im - hf.y), "f"(re - hf.x));
+                            }
+                            v[j] = h;
+                        } else if constexpr (BF16) {
                             v[j] = pack2(plane_of(x.x, p), plane_of(x.y, p));
                         } else {
                             v[2 * j] = plane_of(x.x, p);
@@ -507,6 +531,10 @@ k_tc_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4
                     uint32_t v[2 * QE];
                     tmem_ld<2 * QE>(tbase + tlane + dcol + 2 * (c0 + h * QE), v);
                     wait_ld();
+                    if constexpr (F16) {  // undo the operands' scales
+#pragma unroll
+                        for (int j = 0; j < 2 * QE; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * kF16Out);
+                    }
                     if constexpr (EPI) {
                         // factors of the chunk's 8 columns: column bits 0..2 vary inside it, bits 3.. are h
                         float2 f[QE];
@@ -785,7 +813,12 @@ __global__ void k_tc_prepare(const double* __restrict__ U, int K, const double* 
         }
         const double v = (n & 1) == 0 ? ((kk & 1) == 0 ? ur : -ui) : ((kk & 1) == 0 ? ui : ur);
         const uint32_t off = sw128_offset(n, kk, NR, C::esize);
-        if constexpr (C::esize == 4) {
+        if constexpr (PREC == QSIM_PREC_FP16X3) {
+            const double w = kF16ScaleU * v;
+            const __half h = __float2half_rn((float)w);
+            *reinterpret_cast<__half*>(out + off) = h;
+            *reinterpret_cast<__half*>(out + PB + off) = __float2half_rn((float)(w - (double)__half2float(h)));
+        } else if constexpr (C::esize == 4) {
             const uint32_t hi = tf32_rna((float)v);
             const float lo = (float)(v - (double)__uint_as_float(hi));
             *reinterpret_cast<uint32_t*>(out + off) = hi;
@@ -969,7 +1002,8 @@ size_t tc_epi_scratch_bytes(int n, int k) {
 
 bool tc_supported(int k, int precision) {
     return (k == 5 || k == 6) &&
-           (precision == QSIM_PREC_TF32X3 || precision == QSIM_PREC_BF16X3 || precision == QSIM_PREC_BF16X6);
+           (precision == QSIM_PREC_TF32X3 || precision == QSIM_PREC_BF16X3 || precision == QSIM_PREC_BF16X6 ||
+            precision == QSIM_PREC_FP16X3);
 }
 
 size_t tc_operand_bytes(int k, int precision) {
@@ -994,6 +1028,7 @@ cudaError_t launch_tc_prepare(const double* dU, int k, int precision, bool lines
     switch (precision) {
         case QSIM_PREC_TF32X3: tc::k_tc_prepare<QSIM_PREC_TF32X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
         case QSIM_PREC_BF16X3: tc::k_tc_prepare<QSIM_PREC_BF16X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
+        case QSIM_PREC_FP16X3: tc::k_tc_prepare<QSIM_PREC_FP16X3><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
         default: tc::k_tc_prepare<QSIM_PREC_BF16X6><<<blocks, 256, 0, s>>>(dU, k, rowphase, perm, out); break;
     }
     return cudaGetLastError();
@@ -1065,6 +1100,8 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
         case QSIM_PREC_TF32X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_TF32X3>(psi, a, dB, dev_err, s, d);
         case QSIM_PREC_BF16X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_BF16X3>(psi, a, dB, dev_err, s, d);
         case QSIM_PREC_BF16X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_BF16X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_FP16X3 * 8 + 5: return tc::apply_t<5, QSIM_PREC_FP16X3>(psi, a, dB, dev_err, s, d);
+        case QSIM_PREC_FP16X3 * 8 + 6: return tc::apply_t<6, QSIM_PREC_FP16X3>(psi, a, dB, dev_err, s, d);
         case QSIM_PREC_BF16X6 * 8 + 5: return tc::apply_t<5, QSIM_PREC_BF16X6>(psi, a, dB, dev_err, s, d);
         case QSIM_PREC_BF16X6 * 8 + 6: return tc::apply_t<6, QSIM_PREC_BF16X6>(psi, a, dB, dev_err, s, d);
     }

@@ -362,10 +362,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // dry runs (host-only pass counts) may also plan 7- and 8-qubit blocks, for sizing the fusion width
     if (kmax < 1 || kmax > (opts.dry_run ? 8 : 6)) { set_error("max_fused must be 1..6 (1..8 in a dry run)"); return QSIM_EINVAL; }
     if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_FP16X3) { set_error("unknown precision"); return QSIM_EINVAL; }
-    // FP16X3: consecutive 6-qubit blocks are paired into one pass where they fit a tile; every other
-    // tensor-core block of the plan runs as a 3xTF32 block
-    const bool pair_blocks = opts.precision == QSIM_PREC_FP16X3;
-    if (pair_blocks) opts.precision = QSIM_PREC_TF32X3;
+    // FP16X3 with pair_blocks: consecutive 6-qubit blocks are paired into one pass where they fit a tile
+    const bool pair_blocks = opts.precision == QSIM_PREC_FP16X3 && opts.pair_blocks != 0;
     const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
     const int n = c->n;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_v);
@@ -625,6 +623,18 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         phase_pack(op.form, dtype, op.blob, op.phase);
         op.dev_off = dev_bytes;
         dev_bytes = align(dev_bytes + op.blob.size());
+    }
+    // ---- FP16X3: blocks whose targets give a 3xTF32 block its line-group or pair-rows data path (qubits 0..3
+    // the first four targets; or qubit 0 idle and one of 1..3 a target) keep 3xTF32 -- those paths have no
+    // FP16 form, and the 16-bit paths move such tiles over partly used lines ----
+    if (opts.precision == QSIM_PREC_FP16X3) {
+        for (PlanOp& op : p->ops) {
+            if (op.kind != OP_TC) continue;
+            bool q0 = false, low = false;
+            for (int j = 0; j < op.k; ++j) { q0 = q0 || op.targets[j] == 0; low = low || (op.targets[j] >= 1 && op.targets[j] <= 3); }
+            if ((!remap_later && tc_line_groups(op.k, op.targets, QSIM_PREC_TF32X3, false)) || (!q0 && low))
+                op.precision = QSIM_PREC_TF32X3;
+        }
     }
     // ---- pairs: two consecutive 6-qubit tensor-core blocks without epilogue whose tile fits take one pass ----
     if (pair_blocks && !remap_later && dtype == QSIM_C64) {

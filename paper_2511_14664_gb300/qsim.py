@@ -44,7 +44,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
                 ("dry_run", ctypes.c_int32), ("batch_tc_min_n", ctypes.c_int32),
-                ("plan_effort", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("plan_effort", ctypes.c_int32), ("pair_blocks", ctypes.c_int32)]
 
 
 class PassInfo(ctypes.Structure):
@@ -257,10 +257,10 @@ class State:
         return self
 
     def run(self, circuit, mode: int = RUN_PLAIN, max_fused: int = 5, precision: int = PREC_SIMT,
-            tc_min_k: int = 5, local_qubits: int = 0, plan_effort: int = 0):
+            tc_min_k: int = 5, local_qubits: int = 0, plan_effort: int = 0, pair_blocks: bool = False):
         cc = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k, use_graph=0,
-                    local_qubits=local_qubits, plan_effort=plan_effort)
+                    local_qubits=local_qubits, plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0)
         info = PlanInfo()
         _check(lib().qsim_run(self.h, ctypes.byref(cc.c), ctypes.byref(o), ctypes.byref(info)))
         return info.as_dict()
@@ -395,13 +395,14 @@ class Plan:
 
     def __init__(self, circuit, dtype: int = C64, mode: int = RUN_PLAIN, max_fused: int = 5,
                  precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None,
-                 local_qubits: int = 0, dry_run: bool = False, plan_effort: int = 0):
+                 local_qubits: int = 0, dry_run: bool = False, plan_effort: int = 0, pair_blocks: bool = False):
         """dry_run: plan on the host only (no device needed); the plan lists its passes but cannot run.
-        plan_effort 1: also try fusion with one block of look-ahead, keep the grouping with fewer blocks."""
+        plan_effort 1: also try fusion with one block of look-ahead, keep the grouping with fewer blocks.
+        pair_blocks (with PREC_FP16X3): two consecutive 6-qubit blocks per pass where they fit a tile."""
         self.args = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
                     use_graph=1 if use_graph else 0, local_qubits=local_qubits, dry_run=1 if dry_run else 0,
-                    plan_effort=plan_effort)
+                    plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0)
         info = PlanInfo()
         p = ctypes.c_void_p()
         _check(lib().qsim_plan_create(ctypes.byref(self.args.c), dtype, ctypes.byref(o),

@@ -1,6 +1,6 @@
-"""Two fused 6-qubit blocks in one pass (QSIM_PREC_FP16X3: FP16 split products, the second block applied while
-the tile is still on chip) against the FP64 oracle, at the complex64 bar: max |amplitude error| <= 1e-5 and
-normalised infidelity <= 1e-9.
+"""Two fused 6-qubit blocks in one pass (QSIM_PREC_FP16X3 with pair_blocks: FP16 split products, the second
+block applied while the tile is still on chip) against the FP64 oracle, at the complex64 bar: max |amplitude
+error| <= 1e-5 and normalised infidelity <= 1e-9.
 """
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ CASES = [
 @pytest.mark.parametrize("n,t1,t2", CASES)
 def test_pair_of_blocks_against_oracle(qsim, n, t1, t2):
     c = two_blocks(n, t1, t2, n)
-    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5)
+    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5, pair_blocks=True)
     ps = p.passes()
     assert [q["kind"] for q in ps] == ["tc_pair"]
     assert ps[0]["targets"] == sorted(t1) and sorted(ps[0]["controls"]) == sorted(t2)
@@ -65,7 +65,7 @@ def test_pair_generates_the_basis_state(qsim):
     """A plan starting with a pair generates |x> in its first tile loads (no set-up pass, no reads)."""
     n = 17
     c = two_blocks(n, [2, 3, 4, 5, 6, 7], [6, 7, 8, 9, 10, 11], 5)
-    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5)
+    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5, pair_blocks=True)
     st = qsim.State(n, qsim.C64)
     x = 0b10110011100101011
     st.set_state(random_state(n, 1))  # garbage the first pass must not read
@@ -78,7 +78,7 @@ def test_brickwork_20q_depth40_with_pairs(qsim, seed):
     """The 20-qubit instance of the benchmark generator with pairing: complex64 bar against the oracle."""
     n = 20
     c = W.brickwork(n, 40, seed=seed)
-    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5)
+    p = qsim.Plan(c, qsim.C64, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5, pair_blocks=True)
     kinds = [q["kind"] for q in p.passes()]
     assert kinds.count("tc_pair") >= 10
     st = qsim.State(n, qsim.C64)
@@ -91,7 +91,7 @@ def test_paper_random_circuit_with_pairs(qsim):
     c = W.rcs(n, seed=5)
     st = qsim.State(n, qsim.C64)
     st.set_basis(0)
-    info = st.run(c, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5)
+    info = st.run(c, mode=1, max_fused=6, precision=FP16X3, tc_min_k=5, pair_blocks=True)
     assert info["tc_blocks"] > 0
     check(st.get_state(), oracle.run(c), n)
 
@@ -102,7 +102,7 @@ def test_full_size_pairs_forward_inverse(qsim):
     c = W.brickwork(n, 4, seed=3)
     st = qsim.State(n, qsim.C64)
     st.set_basis(0)
-    kw = dict(mode=1, max_fused=6, precision=FP16X3, tc_min_k=5)
+    kw = dict(mode=1, max_fused=6, precision=FP16X3, tc_min_k=5, pair_blocks=True)
     st.run(c, **kw)
     info = st.run(W.inverse(c), **kw)
     norm = st.norm()

@@ -14,8 +14,8 @@ from helpers import random_state
 
 pytestmark = pytest.mark.gpu
 
-PRECS = {"tf32x3": 1, "bf16x3": 2, "bf16x6": 3}
-BLOCK_TOL = {"tf32x3": (1e-5, 1e-9), "bf16x3": (1e-5, 1e-8), "bf16x6": (1e-5, 1e-9)}
+PRECS = {"tf32x3": 1, "bf16x3": 2, "bf16x6": 3, "fp16x3": 4}
+BLOCK_TOL = {"tf32x3": (1e-5, 1e-9), "bf16x3": (1e-5, 1e-8), "bf16x6": (1e-5, 1e-9), "fp16x3": (1e-5, 1e-9)}
 
 
 @pytest.fixture(scope="module")

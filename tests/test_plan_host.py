@@ -172,12 +172,12 @@ def test_plan_effort_beam_never_more_passes_and_places_every_gate(qsim):
 @pytest.mark.parametrize("make", [lambda: W.brickwork(30, 40, seed=3), lambda: W.rcs(33, seed=3), lambda: W.qft(28),
                                   lambda: W.tfim_lattice(11, 3, 10, 0.27, 0.74)])
 def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
-    """A QSIM_PREC_FP16X3 plan pairs consecutive 6-qubit blocks: with every pair unrolled into its two
+    """A QSIM_PREC_FP16X3 plan with pair_blocks pairs consecutive 6-qubit blocks: with every pair unrolled into its two
     blocks, the pass sequence is exactly the 3xTF32 plan's, each pair's targets span at most 12 qubits,
     and the merged gate counts add up."""
     c = make()
     _, single = plan(qsim, c, **TC6)
-    _, paired = plan(qsim, c, mode=1, max_fused=6, precision=4, tc_min_k=5)
+    _, paired = plan(qsim, c, mode=1, max_fused=6, precision=4, tc_min_k=5, pair_blocks=True)
     unrolled = []
     for q in paired:
         if q["kind"] == "tc_pair":
@@ -187,6 +187,15 @@ def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
         else:
             unrolled.append((q["kind"], q["targets"]))
     assert unrolled == [(q["kind"], q["targets"]) for q in single]
+    # without pair_blocks, the same plan has no pairs, and its blocks keep 3xTF32 exactly where their 3xTF32
+    # form has a line-group or pair-rows path
+    _, fp16 = plan(qsim, c, mode=1, max_fused=6, precision=4, tc_min_k=5)
+    assert [(q["kind"], q["targets"]) for q in fp16] == [(q["kind"], q["targets"]) for q in single]
+    for q in fp16:
+        if q["kind"] == "tc":
+            t = q["targets"]
+            keep_tf32 = t[:4] == [0, 1, 2, 3] or (0 not in t and any(x in t for x in (1, 2, 3)))
+            assert q["precision"] == (1 if keep_tf32 else 4), (t, q["precision"])
     assert sum(q["gates"] for q in paired) == len(c)
     assert sum(1 for q in paired if q["kind"] == "tc_pair") >= len(single) // 4
 
