@@ -595,7 +595,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             op.kind = OP_TC;
             op.precision = opts.precision;
             op.dev_off = dev_bytes;
-            dev_bytes = align(dev_bytes + tc_operand_bytes(kb, opts.precision));
+            // an FP16X3 block may still become a 3xTF32 one below (its line-group / pair-rows path): room for
+            // the larger operand
+            const int room_prec = opts.precision == QSIM_PREC_FP16X3 ? QSIM_PREC_TF32X3 : opts.precision;
+            dev_bytes = align(dev_bytes + tc_operand_bytes(kb, room_prec));
         } else if (kb <= 4) {
             op.kind = OP_DENSE_SMALL;
         } else {
