@@ -503,7 +503,7 @@ def run_ours(args):
     by_kind = {}
     gen = generates_input(plan)
     for i, (info, ms) in enumerate(zip(plan.pass_list, pass_ms)):
-        d = by_kind.setdefault(info["kind"], {"ms": 0.0, "bytes": 0.0, "launches": 0, "flops": 0.0})
+        d = by_kind.setdefault(info["kind"], {"ms": 0.0, "bytes": 0.0, "launches": 0, "flops": 0.0, "floor_s": 0.0})
         d["ms"] += ms
         d["bytes"] += info["algorithmic_bytes"] * (0.5 if (i == 0 and gen) else 1.0) * args.steps
         d["launches"] += args.steps
@@ -511,7 +511,10 @@ def run_ours(args):
             mult = {1: 3, 2: 3, 3: 6, 4: 3}[info["precision"]]
             blocks = 2 if info["kind"] == "tc_pair" else 1
             # real GEMM per amplitude: 2 * (2 * 2^k) MACs per complex output -> 8 * 2^k flops x split products
-            d["flops"] += (2.0 ** n) * 8 * (2 ** info["k"]) * mult * blocks * args.steps
+            f = (2.0 ** n) * 8 * (2 ** info["k"]) * mult * blocks * args.steps
+            d["flops"] += f
+            if rates is not None:  # the time these flops take at the measured rate of this block's operand type
+                d["floor_s"] += f / (rates[PREC_RATE[info["precision"]]] * 1e12)
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     dk = by_kind[dom]
     avg_s = dk["ms"] / dk["launches"] / 1000.0
@@ -523,11 +526,13 @@ def run_ours(args):
             "avg_launch_ms": avg_s * 1000.0, "share_of_step": dk["ms"] / total_ms, "peak_source": peak_src}
     if dom in ("tc", "tc_pair") and dk["flops"] > 0 and rates is not None:
         tflops = dk["flops"] / dk["launches"] / avg_s / 1e12
-        prec = plan.pass_list[[i for i, p in enumerate(plan.pass_list) if p["kind"] == dom][0]]["precision"]
-        # the rate of the products' operand type, measured on this GPU in this run (tensor_rates)
-        tpeak = rates[PREC_RATE[prec]]
+        # the rate of each block's operand type, measured on this GPU in this run (tensor_rates); a plan that
+        # mixes types gets the rate that takes the same time for the same flops
+        used = sorted({PREC_RATE[p["precision"]] for p in plan.pass_list if p["kind"] == dom})
+        tpeak = dk["flops"] / dk["floor_s"] / 1e12
         roof["tensor"] = {"achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
-                          "peak_source": f"measured: {PREC_RATE[prec]} MMA-only loop on this GPU, this run"}
+                          "peak_source": f"measured: {' + '.join(used)} MMA-only loop on this GPU, this run"
+                                         + (" (flop-weighted over the blocks' types)" if len(used) > 1 else "")}
         if tflops / tpeak > hbm_frac:
             roof = {**roof, "bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
                     "frac": tflops / tpeak}

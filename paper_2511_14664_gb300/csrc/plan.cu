@@ -635,7 +635,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             if (op.kind != OP_TC) continue;
             bool q0 = false, low = false;
             for (int j = 0; j < op.k; ++j) { q0 = q0 || op.targets[j] == 0; low = low || (op.targets[j] >= 1 && op.targets[j] <= 3); }
-            if ((!remap_later && tc_line_groups(op.k, op.targets, QSIM_PREC_TF32X3, false)) || (!q0 && low))
+            // (a block with a phase epilogue has neither path: it runs on lanes on rows and stays FP16)
+            if ((!remap_later && tc_line_groups(op.k, op.targets, QSIM_PREC_TF32X3, op.has_epi)) || (!q0 && low && !op.has_epi))
                 op.precision = QSIM_PREC_TF32X3;
         }
     }
