@@ -232,6 +232,7 @@ PATHS = {
     "bf16x6_k5": (1, 5, 3, 5),
     "fp16x3": (1, 6, 4, 5),        # FP16 split products (3xTF32 where a block has the line-group / pair-rows path)
     "fp16x3_pairs": (1, 6, 4, 5, 1),  # the same, consecutive blocks paired into one pass
+    "fp16x3_k7": (1, 7, 4, 5),     # FP16 split products with 7-qubit blocks (fewer passes)
 }
 
 
@@ -441,7 +442,7 @@ def run_ours(args):
     st = qsim.State(n, qsim.C64)
 
     # candidate paths (tensor-core variants only where the library supports them)
-    cands = ["fp16x3", "tf32x3", "fp16x3_pairs", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
+    cands = ["fp16x3_k7", "fp16x3", "tf32x3", "fp16x3_pairs", "bf16x3", "bf16x6", "tf32x3_k5", "bf16x6_k5", "simt4", "simt5"]
     plans = {}
     for name in cands + ["plain"]:
         try:

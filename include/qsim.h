@@ -60,7 +60,8 @@ extern "C" {
    |amplitude| <= 1), matrix entries x 2^14, each split into two FP16 parts (22 significant bits, as 3xTF32),
    three products, FP32 accumulation. Half the tensor cycles and A-operand traffic of 3xTF32. In plans,
    blocks whose 3xTF32 form has the line-group or pair-rows data path (low qubits among the targets) run as
-   QSIM_PREC_TF32X3; see also qsim_run_opts.pair_blocks. */
+   QSIM_PREC_TF32X3; see also qsim_run_opts.pair_blocks. The one precision with 7-qubit tensor-core blocks
+   (qsim_apply_fused with k = 7, plans with max_fused = 7). */
 #define QSIM_PREC_FP16X3 4
 
 /* Run modes. */
@@ -93,7 +94,9 @@ typedef struct {
 /* Options for planning a circuit. Zero-initialise, then set fields. */
 typedef struct {
     int32_t mode;       /* QSIM_RUN_PLAIN or QSIM_RUN_FUSED */
-    int32_t max_fused;  /* fusion width k for QSIM_RUN_FUSED: 1..6 (0 = 5); dry runs also 7, 8 (pass counts) */
+    int32_t max_fused;  /* fusion width k for QSIM_RUN_FUSED: 1..6 (0 = 5); 7 with QSIM_PREC_FP16X3 on a
+                           complex64 state (7-qubit tensor-core blocks; plans of < 14 qubits or with global
+                           qubits keep 6); dry runs also 7, 8 at any precision (pass counts) */
     int32_t precision;  /* QSIM_PREC_* for dense blocks of >= tc_min_k qubits (complex64 states only) */
     int32_t tc_min_k;   /* smallest dense block sent to the tensor-core kernel (0 = 5) */
     int32_t use_graph;  /* 1: replay the plan's launches from a CUDA graph captured on first execution */
@@ -204,8 +207,8 @@ int qsim_apply_gate(qsim_h h, const int* targets, int k, const int* controls, in
 
 /*
  * Apply a dense 2^k x 2^k block (1 <= k <= 8) on `targets` with the given QSIM_PREC_* arithmetic.
- * Tensor-core precisions (TF32X3, BF16X3, BF16X6, FP16X3) need a complex64 state and k in 5..6
- * (QSIM_EUNSUPPORTED otherwise);
+ * Tensor-core precisions (TF32X3, BF16X3, BF16X6, FP16X3) need a complex64 state of n >= k + 7 qubits and
+ * k in 5..6, or k = 7 with FP16X3 (QSIM_EUNSUPPORTED otherwise);
  * QSIM_PREC_SIMT works for both types and every k.
  * This is the single-block form of what QSIM_RUN_FUSED plans produce.
  */

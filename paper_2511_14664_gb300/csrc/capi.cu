@@ -180,7 +180,7 @@ int qsim_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream,
     ok = ok && cudaMalloc(&h->red.result, sizeof(double) * 256) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->red.hresult, sizeof(double) * 256) == cudaSuccess;
     ok = ok && cudaMalloc(&h->dmat, kDevMatBytes) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->dmat64, sizeof(double) * 2 * 4096) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->dmat64, sizeof(double) * 2 * 16384) == cudaSuccess;  // a 7-qubit block
     ok = ok && cudaMalloc(&h->derr, sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMemset(h->derr, 0, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {

@@ -106,6 +106,13 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
                             const uint64_t* from_basis = nullptr, bool lines = false);
 bool tc_supported(int k, int precision);
 
+// ---- 7-qubit blocks (k_tc7.cu, FP16 split products; reached through the tensor-core entry points above
+// with k = 7 and QSIM_PREC_FP16X3) ----------------------------------------------------------------------------
+size_t tc7_operand_bytes();
+cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s);
+cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* dB, unsigned* dev_err, cudaStream_t s,
+                             const DevInfo& d, const uint64_t* from_basis);
+
 // ---- two 6-qubit blocks in one pass (k_tc_pair.cu, FP16 split products) -------------------------------------
 // True when blocks on t1 and then t2 (6 targets each, in their matrices' index order) fit one 13-bit tile of
 // an n-qubit state (|t1 u t2| <= 12, n >= 13).

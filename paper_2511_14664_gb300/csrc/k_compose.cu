@@ -3,8 +3,9 @@
 //
 // For a block on kb local qubits with gates G_1..G_g (each on a subset of those qubits, with controls),
 // U = G_g ... G_1 is built column by column: start from the identity and apply every gate to all 2^kb
-// columns at once, exactly like applying it to 2^kb small state vectors. One CTA per block; the matrix
-// ping-pongs between two shared-memory buffers (2 x 64 KiB for kb = 6).
+// columns at once, exactly like applying it to 2^kb small state vectors. The columns evolve independently,
+// so a block's columns may be spread over several CTAs (grid y): each CTA holds W of them and ping-pongs
+// them between two shared-memory buffers (W = 2^kb up to kb = 6, 2 x 64 KiB; W = 32 for kb = 7, 2 x 64 KiB).
 #include <algorithm>
 
 #include "common.cuh"
@@ -14,13 +15,16 @@ namespace qsim {
 
 __global__ void __launch_bounds__(256) k_compose(const ComposeBlock* __restrict__ blocks,
                                                  const ComposeGate* __restrict__ gates,
-                                                 const double* __restrict__ pool, double* __restrict__ out) {
+                                                 const double* __restrict__ pool, double* __restrict__ out,
+                                                 int cols_max) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const ComposeBlock b = blocks[blockIdx.x];
-    const int D = 1 << b.kb, E = D * D;
+    const int D = 1 << b.kb, W = D < cols_max ? D : cols_max, E = D * W;
+    const int c_lo = (int)blockIdx.y * W;  // this CTA's columns c_lo .. c_lo + W - 1, stored [row][column]
+    if (c_lo >= D) return;
     double2* A = reinterpret_cast<double2*>(smem_raw);
     double2* B = A + E;
-    for (int i = threadIdx.x; i < E; i += blockDim.x) A[i] = make_double2((i / D) == (i % D) ? 1.0 : 0.0, 0.0);
+    for (int i = threadIdx.x; i < E; i += blockDim.x) A[i] = make_double2((i / W) == c_lo + (i % W) ? 1.0 : 0.0, 0.0);
     __syncthreads();
     for (int gi = 0; gi < b.num_gates; ++gi) {
         const ComposeGate g = gates[b.first_gate + gi];
@@ -30,7 +34,7 @@ __global__ void __launch_bounds__(256) k_compose(const ComposeBlock* __restrict_
         for (int j = 0; j < g.k; ++j) tmask |= 1 << g.targets[j];
         for (int j = 0; j < g.nc; ++j) cmask |= 1 << g.controls[j];
         for (int i = threadIdx.x; i < E; i += blockDim.x) {
-            const int r = i / D, c = i % D;
+            const int r = i / W, c = i % W;
             if ((r & cmask) != cmask) {
                 B[i] = A[i];
                 continue;
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(256) k_compose(const ComposeBlock* __restrict_
                 int src = base;
                 for (int j = 0; j < g.k; ++j) src |= ((m >> j) & 1) << g.targets[j];
                 const double gr = G[2 * (mr * dg + m)], gim = G[2 * (mr * dg + m) + 1];
-                const double2 a = A[src * D + c];
+                const double2 a = A[src * W + c];
                 re = __fma_rn(gr, a.x, re);
                 re = __fma_rn(-gim, a.y, re);
                 im = __fma_rn(gr, a.y, im);
@@ -55,16 +59,19 @@ __global__ void __launch_bounds__(256) k_compose(const ComposeBlock* __restrict_
         double2* t = A; A = B; B = t;
     }
     double2* o = reinterpret_cast<double2*>(out) + b.out_off;
-    for (int i = threadIdx.x; i < E; i += blockDim.x) o[i] = A[i];
+    for (int i = threadIdx.x; i < E; i += blockDim.x) o[(i / W) * D + c_lo + i % W] = A[i];
 }
 
 cudaError_t launch_compose(const ComposeBlock* dblocks, int nblocks, const ComposeGate* dgates,
                            const double* dpool, double* dout, int max_kb, cudaStream_t s) {
     if (nblocks == 0) return cudaSuccess;
-    const size_t smem = 2 * sizeof(double2) * ((size_t)1 << (2 * max_kb));
+    if (max_kb < 1 || max_kb > 7) return cudaErrorInvalidValue;
+    const int Dm = 1 << max_kb, cols_max = max_kb <= 6 ? Dm : 32;
+    const size_t smem = 2 * sizeof(double2) * (size_t)Dm * (size_t)cols_max;
     cudaError_t e = cudaFuncSetAttribute(k_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_compose<<<nblocks, 256, smem, s>>>(dblocks, dgates, dpool, dout);
+    k_compose<<<dim3((unsigned)nblocks, (unsigned)(Dm / cols_max), 1), 256, smem, s>>>(dblocks, dgates, dpool, dout,
+                                                                                   cols_max);
     return cudaGetLastError();
 }
 

@@ -85,18 +85,6 @@ __host__ __device__ constexpr uint32_t pow2_at_least(uint32_t v) {
     return p;
 }
 
-// Byte offset of element (n, kk) of an [NR x NR] K-major operand in the canonical SWIZZLE_128B layout:
-// K is cut into 128-byte atoms; atom a holds all NR rows, 8-row groups 1024 bytes apart, and the 16-byte
-// chunk index inside a 128-byte row is XOR-ed with (row mod 8).
-__host__ __device__ inline uint32_t sw128_offset(int n, int kk, int NR, int esize) {
-    const int epa = 128 / esize;
-    const int atom = kk / epa;
-    const int cb = (kk % epa) * esize;
-    const int chunk = cb >> 4, within = cb & 15;
-    const int g = n >> 3, r8 = n & 7;
-    return (uint32_t)(atom * (NR * 128) + g * 1024 + r8 * 128 + ((chunk ^ r8) << 4) + within);
-}
-
 constexpr int kEpiGroups = kRowBits + 1 + 5;  // row bits, the half bit, up to 5 other column bits
 constexpr int kEpiTile = 1 + kEpiGroups;     // factors per tile
 constexpr int kBarBytes = 64;                 // shared memory for the mbarriers and the TMEM slot
@@ -151,18 +139,6 @@ enum Mode {
 // swapped), so that the slots a thread owns in the 16x256b fragment (s = 4j + lane % 4) are 4 adjacent
 // amplitudes for j = 4m .. 4m + 3. The B operand is prepared in the same order.
 __host__ __device__ constexpr int line_perm(int s) { return (s & ~15) | ((s & 3) << 2) | ((s >> 2) & 3); }
-
-// 32-byte global accesses (sm_100 and later); the address must be 32-byte aligned.
-__device__ __forceinline__ void ld_v8(const float2* p, float2& a, float2& b, float2& c, float2& d) {
-    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
-                 : "l"(p));
-}
-__device__ __forceinline__ void st_v8(float2* p, const uint32_t* v) {
-    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                 :: "l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
 
 template <int K, int PREC, int MODE, bool EPI>
 __global__ void __launch_bounds__(kThreadsWS, 1)
@@ -1001,6 +977,7 @@ size_t tc_epi_scratch_bytes(int n, int k) {
 }
 
 bool tc_supported(int k, int precision) {
+    if (k == 7) return precision == QSIM_PREC_FP16X3;  // k_tc7.cu
     return (k == 5 || k == 6) &&
            (precision == QSIM_PREC_TF32X3 || precision == QSIM_PREC_BF16X3 || precision == QSIM_PREC_BF16X6 ||
             precision == QSIM_PREC_FP16X3);
@@ -1008,6 +985,7 @@ bool tc_supported(int k, int precision) {
 
 size_t tc_operand_bytes(int k, int precision) {
     if (!tc_supported(k, precision)) return 0;
+    if (k == 7) return tc7_operand_bytes();
     const int planes = precision == QSIM_PREC_BF16X6 ? 3 : 2;
     const int esize = precision == QSIM_PREC_TF32X3 ? 4 : 2;
     return (size_t)planes * tc::plane_bytes(k, esize);
@@ -1022,6 +1000,7 @@ cudaError_t launch_tc_prepare(const double* dU, int k, int precision, bool lines
                               const double* rowphase) {
     if (!tc_supported(k, precision)) return cudaErrorInvalidValue;
     if (lines && (precision != QSIM_PREC_TF32X3 || rowphase)) return cudaErrorInvalidValue;
+    if (k == 7) return rowphase || lines ? cudaErrorInvalidValue : launch_tc7_prepare(dU, dB, s);
     unsigned char* out = static_cast<unsigned char*>(dB);
     const int blocks = ((2 << k) * (2 << k) + 255) / 256;
     const int perm = lines ? 1 : 0;
@@ -1065,6 +1044,10 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
     if (lines && !tc_line_groups(k, targets, precision, epi != nullptr)) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
     if (epi && (!epi_tab || !epi_scratch || precision == QSIM_PREC_BF16X6)) return cudaErrorInvalidValue;
+    if (k == 7) {  // FP16X3 only; no phase epilogue, no line groups
+        if (epi || lines) return cudaErrorInvalidValue;
+        return launch_tc7_apply(psi, n, targets, dB, dev_err, s, d, from_basis);
+    }
     tc::Args a;
     std::memset(&a, 0, sizeof(a));
 

@@ -1,0 +1,382 @@
+// k_tc7.cu -- a fused 7-qubit block on the tensor cores with FP16 split products (QSIM_PREC_FP16X3).
+//
+// Paper Sec. 2.1: fusion merges gates into one larger matrix; every fused block costs one read and one write
+// of the state, so wider blocks mean fewer passes (the 30-qubit random brickwork of depth 40 needs 64
+// blocks of 6 qubits but 49 of at most 7). Sec. 2.2 ties the useful fusion width to the arithmetic rate: at
+// 7 qubits a block does 3072 tensor FLOP per amplitude in three FP16 products, 1.5 ms at 30 qubits at the
+// FP16 rate, under the 2.5 ms it takes to stream the state once.
+//
+// Operands. A tile is 128 rows (the 7 lowest index bits outside the targets) by the 128 columns of the
+// targets, and Y = X U^T per tile. The real form of U (256 x 256) would take 256 KiB of shared memory as two
+// FP16 planes, more than a CTA has, so the real and imaginary parts of X are separate A operands (K = 128
+// each) and B stacks three 128 x 128 blocks, [Im U; Re U; -Im U] by output row (192 KiB as two planes):
+// Re X multiplies B rows 0..255 and Im X rows 128..383, each an N = 256 MMA into one FP32 accumulator whose
+// columns 0..127 are Im Y and 128..255 Re Y:
+//     Im Y = Re X (Im U)^T + Im X (Re U)^T,   Re Y = Re X (Re U)^T + Im X (-Im U)^T.
+// Scaling and split as in the 6-qubit FP16X3 block: amplitudes x 2^15, U x 2^14, each split into its FP16
+// rounding and the FP16 rounding of the residual, products lo*hi + hi*lo + hi*hi, output x 2^-29.
+//
+// Tensor memory (512 columns, the whole of it): the accumulator in [0, 256), A planes in [256, 512):
+// plane p (0 hi, 1 lo), part (0 Re, 1 Im) at 256 + 128 p + 64 part, two FP16 values per column (even K in
+// the low half). Nothing is double-buffered, so per tile: the warps drain the previous tile's accumulator,
+// write this tile's A planes and arrive on `full`; lane 0 of warp 0 then issues 48 MMAs (3 products x 2
+// parts x 8 K-steps of 16) and commits them to `done`; meanwhile every warp loads the next tile into
+// registers. The MMAs of a tile (3.6 us per SM at the measured FP16 rate) take less than the tile's share
+// of the HBM time (5.9 us), so the drain and the A writes fit in the gap.
+//
+// Sixteen warps (four per TMEM lane quadrant, 32 columns each; no separate MMA warp, whose seventeenth
+// slot would cap every thread at 96 registers), one CTA per SM (persistent over tiles). A thread owns one
+// row of a tile; like the 6-qubit block its amplitudes move as
+// 8-byte values, 16-byte pairs when qubit 0 is the first target, or 32-byte quads when qubits 0 and 1 are
+// the first two. Every mbarrier wait is bounded (2 s); on expiry the kernel records DEVERR_TIMEOUT, waits
+// once more (bounded) for its MMAs, frees its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace qsim {
+namespace tc7 {
+
+using namespace qsim::tc;
+
+constexpr int K = 7, D = 1 << K;        // targets, complex columns of a tile
+constexpr int kRowBits = 7;             // 128 rows per tile (MMA M = 128)
+constexpr int NB = 3 * D;               // B rows: [Im U; Re U; -Im U]
+constexpr int PB = NB * D * 2;          // bytes of one FP16 B plane (96 KiB)
+constexpr int ATOM = NB * 128;          // one 128-byte K atom over all B rows
+constexpr int kDataWarps = 16;
+constexpr int kThreads = kDataWarps * 32;
+constexpr int CPT = D / 4;              // complex columns per data thread (4 warps per lane quadrant)
+constexpr uint32_t A0 = 2 * D;          // first A column in TMEM
+constexpr uint32_t TCOLS = 512;
+// kind::f16: FP32 accumulator, A and B FP16, K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(2 * D >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr float kScaleX = 32768.0f;     // 2^15
+constexpr double kScaleU = 16384.0;     // 2^14
+constexpr float kOut = 1.0f / (32768.0f * 16384.0f);
+constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 64 + 1024;
+
+enum Mode { kRows = 0, kPairs = 1, kQuads = 2 };
+
+struct Args {
+    int nS;              // 14 index bits covered by a tile
+    int spos[24];        // those bit positions, ascending
+    int rpos[kRowBits];  // row bit j <-> index bit rpos[j]
+    int tpos[K];         // column bit j <-> target j
+    uint64_t ntiles;
+    int from_basis;      // the input is |basis>, generated in registers instead of read
+    uint64_t basis;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
+            unsigned* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
+    uint64_t* mbar = sCol + D;  // full, done, B loaded
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 0)), "r"(kDataWarps) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 2)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t full = smem_u32(mbar + 0), done = smem_u32(mbar + 1), bbar = smem_u32(mbar + 2);
+    // programmatic dependent launch: the set-up above overlapped the previous kernel's tail
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (tid == 0) {
+        constexpr uint32_t kChunk = 16384, kBytes = 2u * PB;
+        static_assert(kBytes % kChunk == 0, "whole chunks");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bbar), "r"(kBytes) : "memory");
+#pragma unroll 1
+        for (uint32_t o = 0; o < kBytes; o += kChunk)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(sb) + o), "l"(reinterpret_cast<const char*>(bops) + o), "r"(kChunk),
+                            "r"(bbar) : "memory");
+    }
+    const uint64_t t0 = blockIdx.x, G = gridDim.x;
+    const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
+
+    {
+        // ---- MMA issue (lane 0 of warp 0, once every warp has written its part of the tile) ----
+        const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
+        const uint32_t dhi = (uint32_t)(desc0 >> 32);
+        // products (A plane, B plane): lo*hi, hi*lo, hi*hi; per product Re X on B rows 0..255, Im X on rows
+        // 128..383 (16 KiB further in every K atom); the first MMA of a tile starts the accumulator
+        auto issue = [&]() {
+            uint32_t dlo = (uint32_t)desc0, tb = tbase;
+            asm volatile("" : "+r"(dlo), "+r"(tb));
+            uint32_t acc = 0;
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+                const int pa = pr == 0 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const uint32_t acol = tb + A0 + (uint32_t)(pa * D + part * (D / 2));
+#pragma unroll
+                    for (int s = 0; s < D / 16; ++s) {
+                        const uint32_t off = (uint32_t)(pb * PB + (s >> 2) * ATOM + part * D * 128 + (s & 3) * 32);
+                        mma_ts_lohi<true>(tb, acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
+                        acc = 1;
+                    }
+                }
+            }
+        };
+        bool b_ready = false;     // lane 0 of warp 0: B has arrived in shared memory
+        bool issued = false;      // lane 0 of warp 0: MMAs issued, the last commit's phase in last_par
+        uint32_t last_par = 0;
+        // warp 0 (whole warp): wait for tile i's A planes, issue its MMAs and commit them to `done`; false
+        // (for the whole warp) when a wait expired
+        auto issue_tile = [&](uint64_t i) -> bool {
+            bool ok = true;
+            if (lane == 0) {
+                if (!b_ready) {
+                    b_ready = mbar_wait_bounded(bbar, 0);
+                    ok = b_ready;
+                }
+                ok = ok && mbar_wait_bounded(full, (uint32_t)(i & 1));
+                if (ok) {
+                    fence_after();
+                    issue();
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(done) : "memory");
+                    issued = true;
+                    last_par = (uint32_t)(i & 1);
+                }
+            }
+            return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        };
+
+        // ---- data warps ----
+        const int quad = warp & 3;
+        const int c0 = (warp >> 2) * CPT;
+        const int r = quad * 32 + lane;
+        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+        const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
+        // column offsets re-read from shared memory at each use (one broadcast load each) rather than held
+        // in 64-bit registers; the empty asm between accesses keeps those reads next to their accesses
+        const volatile uint64_t* vCol = sCol + c0;
+
+        auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
+            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+            if (a.from_basis) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) X[j] = make_float2(b + vCol[j] == a.basis ? 1.0f : 0.0f, 0.0f);
+            } else if constexpr (MODE == kQuads) {
+#pragma unroll
+                for (int j = 0; j < CPT; j += 4) {
+                    ld_v8(psi + b + vCol[j], X[j], X[j + 1], X[j + 2], X[j + 3]);
+                    asm volatile("" ::: "memory");
+                }
+            } else if constexpr (MODE == kPairs) {
+#pragma unroll
+                for (int j = 0; j < CPT; j += 2) {
+                    const float4 v = *reinterpret_cast<const float4*>(psi + b + vCol[j]);
+                    X[j] = make_float2(v.x, v.y);
+                    X[j + 1] = make_float2(v.z, v.w);
+                    asm volatile("" ::: "memory");
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    X[j] = psi[b + vCol[j]];
+                    asm volatile("" ::: "memory");
+                }
+            }
+        };
+        // A planes of tile X: for the Re and Im parts, plane 0 = FP16 rounding of the scaled value, plane 1 =
+        // FP16 rounding of the residual; columns 2q and 2q+1 share a 32-bit TMEM column (2q in the low half)
+        auto store_a = [&](const float2 (&X)[CPT]) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                uint32_t hi[CPT / 2], lo[CPT / 2];
+#pragma unroll
+                for (int q = 0; q < CPT / 2; ++q) {
+                    const float e = (part ? X[2 * q].y : X[2 * q].x) * kScaleX;
+                    const float o = (part ? X[2 * q + 1].y : X[2 * q + 1].x) * kScaleX;
+                    uint32_t h, l;
+                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(o), "f"(e));
+                    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&h));
+                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(o - hf.y), "f"(e - hf.x));
+                    hi[q] = h;
+                    lo[q] = l;
+                }
+                tmem_st<CPT / 2>(tbase + tlane + A0 + part * (D / 2) + c0 / 2, hi);
+                tmem_st<CPT / 2>(tbase + tlane + A0 + D + part * (D / 2) + c0 / 2, lo);
+            }
+            wait_st();
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full);
+        };
+        // The accumulator of tile t (Re Y at column 128 + c, Im Y at c), scaled back and stored in place.
+        auto drain = [&](uint64_t t) {
+            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+#pragma unroll
+            for (int h = 0; h < CPT / 8; ++h) {
+                uint32_t re[8], im[8], v[16];
+                tmem_ld<8>(tbase + tlane + D + c0 + 8 * h, re);
+                tmem_ld<8>(tbase + tlane + c0 + 8 * h, im);
+                wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[2 * j] = __float_as_uint(__uint_as_float(re[j]) * kOut);
+                    v[2 * j + 1] = __float_as_uint(__uint_as_float(im[j]) * kOut);
+                }
+                if constexpr (MODE == kQuads) {
+#pragma unroll
+                    for (int j = 0; j < 8; j += 4) {
+                        st_v8(psi + b + vCol[8 * h + j], v + 2 * j);
+                        asm volatile("" ::: "memory");
+                    }
+                } else if constexpr (MODE == kPairs) {
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) {
+                        *reinterpret_cast<float4*>(psi + b + vCol[8 * h + j]) =
+                            make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                        __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
+                        asm volatile("" ::: "memory");
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        psi[b + vCol[8 * h + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                        asm volatile("" ::: "memory");
+                    }
+                }
+            }
+        };
+        // warp-uniform bounded wait (the TMEM accesses that follow are .sync.aligned)
+        auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+            const bool ok = !__any_sync(0xffffffffu, !mbar_wait_bounded(bar, par));
+            fence_after();
+            return ok;
+        };
+        // Tile i: once the MMAs of tile i-1 are done (its accumulator final, the A planes free), drain tile
+        // i-1, write tile i's A planes, then load tile i+1, whose latency the MMAs of tile i cover.
+        bool bad = false;
+        float2 X[CPT];
+        if (m > 0) load_tile(X, t0);
+        for (uint64_t i = 0; i < m; ++i) {
+            if (i > 0) {
+                if (!wait(done, (uint32_t)((i - 1) & 1))) { bad = true; break; }
+                drain(t0 + (i - 1) * G);
+            }
+            store_a(X);
+            if (warp == 0 && !issue_tile(i)) { bad = true; break; }
+            if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);
+        }
+        if (!bad && m > 0) {
+            if (wait(done, (uint32_t)((m - 1) & 1))) drain(t0 + (m - 1) * G);
+            else bad = true;
+        }
+        if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+        if (warp == 0 && lane == 0) {
+            if (!b_ready) mbar_wait_bounded(bbar, 0);           // the bulk copy of B, if never waited for
+            if (bad && issued) mbar_wait_bounded(done, last_par);  // the MMAs already issued
+        }
+        __syncwarp();
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(TCOLS) : "memory");
+    }
+}
+
+// B operand: row n of [Im U; Re U; -Im U] (output index i = n mod 128) against input index c, scaled by 2^14
+// and split into two FP16 planes (value, residual), written in the swizzled shared-memory byte layout.
+__global__ void k_tc7_prepare(const double* __restrict__ U, unsigned char* __restrict__ out) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NB * D; idx += gridDim.x * blockDim.x) {
+        const int n = idx / D, c = idx % D;
+        const int blk = n / D, i = n % D;
+        const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
+        const double w = kScaleU * (blk == 0 ? ui : (blk == 1 ? ur : -ui));
+        const __half h = __float2half_rn((float)w);
+        const uint32_t off = sw128_offset(n, c, NB, 2);
+        *reinterpret_cast<__half*>(out + off) = h;
+        *reinterpret_cast<__half*>(out + PB + off) = __float2half_rn((float)(w - (double)__half2float(h)));
+    }
+}
+
+}  // namespace tc7
+
+size_t tc7_operand_bytes() { return 2 * (size_t)tc7::PB; }
+
+cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s) {
+    const int blocks = (tc7::NB * tc7::D + 255) / 256;
+    tc7::k_tc7_prepare<<<blocks, 256, 0, s>>>(dU, static_cast<unsigned char*>(dB));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* dB, unsigned* dev_err, cudaStream_t s,
+                             const DevInfo& d, const uint64_t* from_basis) {
+    if (n < tc7::K + tc7::kRowBits || n > 63 || (reinterpret_cast<uintptr_t>(dB) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(psi) & 15) != 0)
+        return cudaErrorInvalidValue;
+    tc7::Args a;
+    std::memset(&a, 0, sizeof(a));
+    uint64_t tmask = 0;
+    for (int j = 0; j < tc7::K; ++j) {
+        if (targets[j] < 0 || targets[j] >= n || ((tmask >> targets[j]) & 1)) return cudaErrorInvalidValue;
+        a.tpos[j] = targets[j];
+        tmask |= 1ull << targets[j];
+    }
+    int nr = 0;
+    for (int q = 0; q < n && nr < tc7::kRowBits; ++q)
+        if (!((tmask >> q) & 1)) a.rpos[nr++] = q;
+    uint64_t smask = tmask;
+    for (int j = 0; j < tc7::kRowBits; ++j) smask |= 1ull << a.rpos[j];
+    for (int q = 0; q < n; ++q)
+        if ((smask >> q) & 1) a.spos[a.nS++] = q;
+    a.ntiles = 1ull << (n - a.nS);
+    if (from_basis) {
+        a.from_basis = 1;
+        a.basis = *from_basis;
+    }
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
+    auto launch = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc7::kSmem);
+        if (e != cudaSuccess) return e;
+        // programmatic dependent launch, as for the 6-qubit block (griddepcontrol.wait before any access)
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.gridDim = dim3(grid, 1, 1);
+        cfg.blockDim = dim3(tc7::kThreads, 1, 1);
+        cfg.dynamicSmemBytes = tc7::kSmem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB),
+                                  dev_err);
+    };
+    if (a.tpos[0] == 0 && a.tpos[1] == 1 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
+        return launch(tc7::k_tc7_block<tc7::kQuads>);
+    if (a.tpos[0] == 0) return launch(tc7::k_tc7_block<tc7::kPairs>);
+    return launch(tc7::k_tc7_block<tc7::kRows>);
+}
+
+}  // namespace qsim

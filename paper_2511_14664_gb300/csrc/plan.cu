@@ -359,9 +359,14 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts_in) opts = *opts_in;
     if (opts.mode != QSIM_RUN_PLAIN && opts.mode != QSIM_RUN_FUSED) { set_error("unknown mode"); return QSIM_EINVAL; }
     int kmax = opts.max_fused == 0 ? 5 : opts.max_fused;
-    // dry runs (host-only pass counts) may also plan 7- and 8-qubit blocks, for sizing the fusion width
-    if (kmax < 1 || kmax > (opts.dry_run ? 8 : 6)) { set_error("max_fused must be 1..6 (1..8 in a dry run)"); return QSIM_EINVAL; }
+    // 7-qubit blocks run on the tensor cores in FP16 split products (complex64); dry runs (host-only pass
+    // counts) may also plan 7- and 8-qubit blocks at any precision, for sizing the fusion width
     if (opts.precision < QSIM_PREC_SIMT || opts.precision > QSIM_PREC_FP16X3) { set_error("unknown precision"); return QSIM_EINVAL; }
+    const int kmax_ok = opts.dry_run ? 8 : (opts.precision == QSIM_PREC_FP16X3 && dtype == QSIM_C64 ? 7 : 6);
+    if (kmax < 1 || kmax > kmax_ok) {
+        set_error("max_fused must be 1..6 (7 with QSIM_PREC_FP16X3 on a complex64 state; 1..8 in a dry run)");
+        return QSIM_EINVAL;
+    }
     // FP16X3 with pair_blocks: consecutive 6-qubit blocks are paired into one pass where they fit a tile
     const bool pair_blocks = opts.precision == QSIM_PREC_FP16X3 && opts.pair_blocks != 0;
     const int tc_min = opts.tc_min_k == 0 ? 5 : opts.tc_min_k;
@@ -405,6 +410,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // would move.
     std::vector<char> gwide(G, 0);
     const bool remap_later = opts.local_qubits > 0 && opts.local_qubits < n;  // global qubits: targets remapped
+    // 7-qubit tensor-core blocks need n >= 14 (a tile is 7 row bits x 7 targets); plans with global qubits
+    // keep 6-qubit blocks
+    if (!dry && kmax == 7 && (n < 14 || remap_later)) kmax = 6;
+    const bool tc7 = kmax == 7 && opts.precision == QSIM_PREC_FP16X3 && dtype == QSIM_C64 && n >= 14;
     const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !remap_later;
     for (int i = 0; i < G; ++i) gwide[i] = use_wide && gdiag[i] && phase_gate_ok(c->gates[i]);
     if (opts.mode == QSIM_RUN_PLAIN) {
@@ -572,7 +581,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             op.nc = g.nc;
             std::memcpy(op.controls, g.controls, sizeof(int) * g.nc);
         }
-        if (all_diag) {
+        if (all_diag && !(tc7 && kb == 7)) {  // (the diagonal kernel stops at 6 qubits)
             op.kind = OP_DIAG;
             // structural support: pattern m is touched if some gate's factor there is not exactly 1
             const int D = 1 << kb;
@@ -598,7 +607,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             // an FP16X3 block may still become a 3xTF32 one below (its line-group / pair-rows path): room for
             // the larger operand
             const int room_prec = opts.precision == QSIM_PREC_FP16X3 ? QSIM_PREC_TF32X3 : opts.precision;
-            dev_bytes = align(dev_bytes + tc_operand_bytes(kb, room_prec));
+            dev_bytes = align(dev_bytes + std::max(tc_operand_bytes(kb, opts.precision), tc_operand_bytes(kb, room_prec)));
         } else if (kb <= 4) {
             op.kind = OP_DENSE_SMALL;
         } else {
@@ -616,7 +625,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         PlanOp& op = p->ops[oi];
         if (op.kind != OP_PHASE) continue;
         PlanOp* prev = oi > 0 ? &p->ops[oi - 1] : nullptr;
-        if (prev && prev->kind == OP_TC && !prev->has_epi && prev->precision != QSIM_PREC_BF16X6) {
+        if (prev && prev->kind == OP_TC && prev->k <= 6 && !prev->has_epi && prev->precision != QSIM_PREC_BF16X6) {
             prev->has_epi = true;
             prev->form = std::move(op.form);
             prev->gates += op.gates;
@@ -632,7 +641,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // FP16 form, and the 16-bit paths move such tiles over partly used lines ----
     if (opts.precision == QSIM_PREC_FP16X3) {
         for (PlanOp& op : p->ops) {
-            if (op.kind != OP_TC) continue;
+            if (op.kind != OP_TC || op.k > 6) continue;  // 7-qubit blocks exist in FP16X3 only
             bool q0 = false, low = false;
             for (int j = 0; j < op.k; ++j) { q0 = q0 || op.targets[j] == 0; low = low || (op.targets[j] >= 1 && op.targets[j] <= 3); }
             // (a block with a phase epilogue has neither path: it runs on lanes on rows and stays FP16)

@@ -123,6 +123,30 @@ __device__ __forceinline__ void tmem_ld_16x256b_x4(uint32_t taddr, uint32_t (&v)
                    "=r"(v[15]) : "r"(taddr));
 }
 
+// Byte offset of element (n, kk) of an operand of NR rows (K-major) in the canonical SWIZZLE_128B layout:
+// K is cut into 128-byte atoms; atom a holds all NR rows, 8-row groups 1024 bytes apart, and the 16-byte
+// chunk index inside a 128-byte row is XOR-ed with (row mod 8).
+__host__ __device__ inline uint32_t sw128_offset(int n, int kk, int NR, int esize) {
+    const int epa = 128 / esize;
+    const int atom = kk / epa;
+    const int cb = (kk % epa) * esize;
+    const int chunk = cb >> 4, within = cb & 15;
+    const int g = n >> 3, r8 = n & 7;
+    return (uint32_t)(atom * (NR * 128) + g * 1024 + r8 * 128 + ((chunk ^ r8) << 4) + within);
+}
+
+// 32-byte global accesses (sm_100 and later); the address must be 32-byte aligned.
+__device__ __forceinline__ void ld_v8(const float2* p, float2& a, float2& b, float2& c, float2& d) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st_v8(float2* p, const uint32_t* v) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(addr) : "memory");
 }

@@ -201,6 +201,22 @@ def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
     assert sum(1 for q in paired if q["kind"] == "tc_pair") >= len(single) // 4
 
 
+def test_seven_qubit_blocks(qsim):
+    """max_fused = 7 with QSIM_PREC_FP16X3: 7-qubit tensor-core blocks in FP16 (no 3xTF32 form, no phase
+    epilogue), every gate placed once; the 30-qubit brickwork takes 49 passes instead of 64, and on the QFT
+    the phases after a 7-qubit block keep a pass of their own."""
+    c = W.brickwork(30, 40, seed=3)
+    _, ps = plan(qsim, c, mode=1, max_fused=7, precision=4, tc_min_k=5)
+    k7 = [q for q in ps if q["kind"] == "tc" and q["k"] == 7]
+    assert len(ps) <= 49 and len(k7) >= 40
+    assert all(q["precision"] == 4 and q["launches"] == 1 for q in k7)
+    assert all(q["algorithmic_bytes"] == 2 * 8 * 2.0 ** 30 for q in k7)
+    _, ps = plan(qsim, W.qft(20), mode=1, max_fused=7, precision=4, tc_min_k=5)
+    assert any(q["kind"] == "tc" and q["k"] == 7 for q in ps)
+    assert all(q["launches"] == 1 for q in ps if q["kind"] == "tc" and q["k"] == 7)
+    assert any(q["kind"] == "phase" for q in ps)
+
+
 @pytest.mark.parametrize("L", [16, 18, 22])
 def test_global_qubit_reorders_restore_identity(qsim, L):
     """Following a plan's reorder passes as exchanges of index bits, every gate pass must find its qubits
