@@ -503,9 +503,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             std::memcpy(op.targets, g.targets, sizeof(int) * g.k);
             std::memcpy(op.controls, g.controls, sizeof(int) * g.nc);
             const int D = 1 << g.k;
-            if (g.k >= 7) {
-                // 7 or 8 targets (diagonal or not): its own CUDA-core pass; the matrix is uploaded as given,
-                // in the state precision (no composition: one gate)
+            if (g.k >= 7 && !(tc7 && g.k == 7 && g.nc == 0 && !gdiag[blk[0]])) {
+                // 7 or 8 targets (diagonal or not; a dense 7-qubit gate without controls goes to the tensor
+                // cores in a 7-qubit FP16X3 plan, below): its own CUDA-core pass; the matrix is uploaded as
+                // given, in the state precision (no composition: one gate)
                 op.kind = OP_DENSE_TILE;
                 op.mat.assign(g.matrix, g.matrix + 2 * D * D);
                 op.dev_off = dev_bytes;
