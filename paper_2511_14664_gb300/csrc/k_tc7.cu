@@ -9,27 +9,31 @@
 // Operands. A tile is 128 rows (the 7 lowest index bits outside the targets) by the 128 columns of the
 // targets, and Y = X U^T per tile. The real form of U (256 x 256) would take 256 KiB of shared memory as two
 // FP16 planes, more than a CTA has, so the real and imaginary parts of X are separate A operands (K = 128
-// each) and B stacks three 128 x 128 blocks, [Im U; Re U; -Im U] by output row (192 KiB as two planes):
-// Re X multiplies B rows 0..255 and Im X rows 128..383, each an N = 256 MMA into one FP32 accumulator whose
-// columns 0..127 are Im Y and 128..255 Re Y:
-//     Im Y = Re X (Im U)^T + Im X (Re U)^T,   Re Y = Re X (Re U)^T + Im X (-Im U)^T.
+// each). The output columns are cut in two halves h (columns 64h .. 64h + 63), each with an accumulator of
+// 128 FP32 columns: [Im Y_h | Re Y_h]. B holds, per half, three 64-row blocks [Im U_h; Re U_h; -Im U_h]
+// (U_h = rows 64h.. of U; 384 rows, 192 KiB as two planes), so that Re X multiplies the 128-row window
+// starting at block 0 of its half and Im X the window starting at block 1, each an N = 128 MMA:
+//     Im Y_h = Re X (Im U_h)^T + Im X (Re U_h)^T,   Re Y_h = Re X (Re U_h)^T + Im X (-Im U_h)^T.
 // Scaling and split as in the 6-qubit FP16X3 block: amplitudes x 2^15, U x 2^14, each split into its FP16
 // rounding and the FP16 rounding of the residual, products lo*hi + hi*lo + hi*hi, output x 2^-29.
 //
-// Tensor memory (512 columns, the whole of it): the accumulator in [0, 256), A planes in [256, 512):
+// Tensor memory (512 columns, the whole of it): accumulator h at [128h, 128h + 128), A planes in [256, 512):
 // plane p (0 hi, 1 lo), part (0 Re, 1 Im) at 256 + 128 p + 64 part, two FP16 values per column (even K in
-// the low half). Nothing is double-buffered, so per tile: the warps drain the previous tile's accumulator,
-// write this tile's A planes and arrive on `full`; lane 0 of warp 0 then issues 48 MMAs (3 products x 2
-// parts x 8 K-steps of 16) and commits them to `done`; meanwhile every warp loads the next tile into
-// registers. The MMAs of a tile (3.6 us per SM at the measured FP16 rate) take less than the tile's share
-// of the HBM time (5.9 us), so the drain and the A writes fit in the gap.
+// the low half). Per tile the MMAs of half 0 and of half 1 are committed separately, so that the drain of
+// one half overlaps the MMAs of the other; the A planes are single-buffered, so the tensor cores wait only
+// while a tile's A planes are written. Sequence of tile i (every warp; "issue" = lane 0 of warp 0):
+//   wait done1(i-1); write A(i); arrive full        issue: wait full, MMAs of half 0, commit done0
+//   drain half 1 of tile i-1; arrive free1          issue: wait free1, MMAs of half 1, commit done1
+//   load tile i+1 into registers; wait done0(i); drain half 0 of tile i
+// The MMAs of a tile (3.6 us per SM at the measured FP16 rate) take less than the tile's share of the HBM
+// time (5.9 us).
 //
-// Sixteen warps (four per TMEM lane quadrant, 32 columns each; no separate MMA warp, whose seventeenth
-// slot would cap every thread at 96 registers), one CTA per SM (persistent over tiles). A thread owns one
-// row of a tile; like the 6-qubit block its amplitudes move as
-// 8-byte values, 16-byte pairs when qubit 0 is the first target, or 32-byte quads when qubits 0 and 1 are
-// the first two. Every mbarrier wait is bounded (2 s); on expiry the kernel records DEVERR_TIMEOUT, waits
-// once more (bounded) for its MMAs, frees its tensor memory and returns.
+// Sixteen warps (four per TMEM lane quadrant; no separate MMA warp, whose seventeenth slot would cap every
+// thread at 96 registers), one CTA per SM (persistent over tiles). A thread owns one row of a tile and 16
+// columns of each half; like the 6-qubit block its amplitudes move as 8-byte values, 16-byte pairs when
+// qubit 0 is the first target, or 32-byte quads when qubits 0 and 1 are the first two. Every mbarrier wait is
+// bounded (2 s); on expiry the kernel records DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees
+// its tensor memory and returns.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -45,21 +49,24 @@ namespace tc7 {
 using namespace qsim::tc;
 
 constexpr int K = 7, D = 1 << K;        // targets, complex columns of a tile
+constexpr int H = D / 2;                // columns per output half
 constexpr int kRowBits = 7;             // 128 rows per tile (MMA M = 128)
-constexpr int NB = 3 * D;               // B rows: [Im U; Re U; -Im U]
+constexpr int NB = 3 * D;               // B rows: per half [Im U_h; Re U_h; -Im U_h]
 constexpr int PB = NB * D * 2;          // bytes of one FP16 B plane (96 KiB)
 constexpr int ATOM = NB * 128;          // one 128-byte K atom over all B rows
-constexpr int kDataWarps = 16;
-constexpr int kThreads = kDataWarps * 32;
-constexpr int CPT = D / 4;              // complex columns per data thread (4 warps per lane quadrant)
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int CPH = H / 4;              // columns of each half per thread (4 warps per lane quadrant)
+constexpr int CPT = 2 * CPH;            // complex columns per thread
 constexpr uint32_t A0 = 2 * D;          // first A column in TMEM
 constexpr uint32_t TCOLS = 512;
-// kind::f16: FP32 accumulator, A and B FP16, K-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(2 * D >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// kind::f16: FP32 accumulator, A and B FP16, K-major, N = 128, M = 128
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(D >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 constexpr float kScaleX = 32768.0f;     // 2^15
 constexpr double kScaleU = 16384.0;     // 2^14
 constexpr float kOut = 1.0f / (32768.0f * 16384.0f);
-constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 64 + 1024;
+constexpr int kBars = 5;                // full, free1, done0, done1, B loaded
+constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 8 * kBars + 8 + 1024;
 
 enum Mode { kRows = 0, kPairs = 1, kQuads = 2 };
 
@@ -80,15 +87,15 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
-    uint64_t* mbar = sCol + D;  // full, done, B loaded
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+    uint64_t* mbar = sCol + D;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kBars);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 0)), "r"(kDataWarps) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 2)), "r"(1) : "memory");
+        const int count[kBars] = {kWarps, kWarps, 1, 1, 1};
+        for (int j = 0; j < kBars; ++j)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + j)), "r"(count[j]) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -100,7 +107,8 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     __syncthreads();
     fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t full = smem_u32(mbar + 0), done = smem_u32(mbar + 1), bbar = smem_u32(mbar + 2);
+    const uint32_t full = smem_u32(mbar + 0), free1 = smem_u32(mbar + 1), done0 = smem_u32(mbar + 2),
+                   done1 = smem_u32(mbar + 3), bbar = smem_u32(mbar + 4);
     // programmatic dependent launch: the set-up above overlapped the previous kernel's tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -117,186 +125,200 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
 
-    {
-        // ---- MMA issue (lane 0 of warp 0, once every warp has written its part of the tile) ----
-        const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
-        const uint32_t dhi = (uint32_t)(desc0 >> 32);
-        // products (A plane, B plane): lo*hi, hi*lo, hi*hi; per product Re X on B rows 0..255, Im X on rows
-        // 128..383 (16 KiB further in every K atom); the first MMA of a tile starts the accumulator
-        auto issue = [&]() {
-            uint32_t dlo = (uint32_t)desc0, tb = tbase;
-            asm volatile("" : "+r"(dlo), "+r"(tb));
-            uint32_t acc = 0;
+    // ---- MMA issue (lane 0 of warp 0) ----
+    const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
+    const uint32_t dhi = (uint32_t)(desc0 >> 32);
+    // The MMAs of output half h: products (A plane, B plane) lo*hi, hi*lo, hi*hi; Re X on the B window at
+    // block 0 of the half, Im X on the window at block 1 (64 rows = 8 KiB further in every K atom); the first
+    // MMA starts the half's accumulator.
+    auto issue_half = [&](int h) {
+        uint32_t dlo = (uint32_t)desc0, tb = tbase;
+        asm volatile("" : "+r"(dlo), "+r"(tb));
+        uint32_t acc = 0;
 #pragma unroll
-            for (int pr = 0; pr < 3; ++pr) {
-                const int pa = pr == 0 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+        for (int pr = 0; pr < 3; ++pr) {
+            const int pa = pr == 0 ? 1 : 0, pb = pr == 1 ? 1 : 0;
 #pragma unroll
-                for (int part = 0; part < 2; ++part) {
-                    const uint32_t acol = tb + A0 + (uint32_t)(pa * D + part * (D / 2));
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t acol = tb + A0 + (uint32_t)(pa * D + part * (D / 2));
 #pragma unroll
-                    for (int s = 0; s < D / 16; ++s) {
-                        const uint32_t off = (uint32_t)(pb * PB + (s >> 2) * ATOM + part * D * 128 + (s & 3) * 32);
-                        mma_ts_lohi<true>(tb, acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
-                        acc = 1;
-                    }
+                for (int s = 0; s < D / 16; ++s) {
+                    const uint32_t off = (uint32_t)(pb * PB + (s >> 2) * ATOM + (3 * H * h + H * part) * 128 + (s & 3) * 32);
+                    mma_ts_lohi<true>(tb + (uint32_t)(D * h), acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
+                    acc = 1;
                 }
             }
-        };
-        bool b_ready = false;     // lane 0 of warp 0: B has arrived in shared memory
-        bool issued = false;      // lane 0 of warp 0: MMAs issued, the last commit's phase in last_par
-        uint32_t last_par = 0;
-        // warp 0 (whole warp): wait for tile i's A planes, issue its MMAs and commit them to `done`; false
-        // (for the whole warp) when a wait expired
-        auto issue_tile = [&](uint64_t i) -> bool {
-            bool ok = true;
-            if (lane == 0) {
-                if (!b_ready) {
-                    b_ready = mbar_wait_bounded(bbar, 0);
-                    ok = b_ready;
-                }
-                ok = ok && mbar_wait_bounded(full, (uint32_t)(i & 1));
-                if (ok) {
-                    fence_after();
-                    issue();
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(done) : "memory");
-                    issued = true;
-                    last_par = (uint32_t)(i & 1);
-                }
+        }
+    };
+    auto commit = [&](uint32_t bar) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+    };
+    bool b_ready = false;  // lane 0 of warp 0: B has arrived in shared memory
+    bool issued = false;   // lane 0 of warp 0: MMAs issued; the last commit went to last_bar, phase last_par
+    uint32_t last_bar = 0, last_par = 0;
+    // warp 0 (whole warp): after a bounded wait on `bar` (phase par), issue the MMAs of half h of tile i and
+    // commit them; false for the whole warp when a wait expired
+    auto issue_after = [&](uint32_t bar, uint32_t par, int h, uint64_t i) -> bool {
+        bool ok = true;
+        if (lane == 0) {
+            if (!b_ready) {
+                b_ready = mbar_wait_bounded(bbar, 0);
+                ok = b_ready;
             }
-            return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        };
+            ok = ok && mbar_wait_bounded(bar, par);
+            if (ok) {
+                fence_after();
+                issue_half(h);
+                last_bar = h ? done1 : done0;
+                last_par = (uint32_t)(i & 1);
+                commit(last_bar);
+                issued = true;
+            }
+        }
+        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    };
 
-        // ---- data warps ----
-        const int quad = warp & 3;
-        const int c0 = (warp >> 2) * CPT;
-        const int r = quad * 32 + lane;
-        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-        const uint64_t rowoff = deposit((uint64_t)r, a.rpos, kRowBits);
-        // column offsets re-read from shared memory at each use (one broadcast load each) rather than held
-        // in 64-bit registers; the empty asm between accesses keeps those reads next to their accesses
-        const volatile uint64_t* vCol = sCol + c0;
+    // ---- data movement (every warp) ----
+    const int quad = warp & 3, w4 = warp >> 2;
+    const uint32_t tlane = (uint32_t)(quad * 32) << 16;
+    const uint64_t rowoff = deposit((uint64_t)(quad * 32 + lane), a.rpos, kRowBits);
+    // X[CPH * h + j] is column H h + CPH w4 + j. Column offsets are re-read from shared memory at each use
+    // (one broadcast load) rather than held in 64-bit registers; the empty asm between accesses keeps those
+    // reads next to their accesses.
+    const volatile uint64_t* vCol = sCol + CPH * w4;
+    auto col = [&](int x) { return vCol[(x / CPH) * H + x % CPH]; };
 
-        auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
-            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-            if (a.from_basis) {
+    auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+        if (a.from_basis) {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) X[j] = make_float2(b + vCol[j] == a.basis ? 1.0f : 0.0f, 0.0f);
-            } else if constexpr (MODE == kQuads) {
+            for (int x = 0; x < CPT; ++x) X[x] = make_float2(b + col(x) == a.basis ? 1.0f : 0.0f, 0.0f);
+        } else if constexpr (MODE == kQuads) {
 #pragma unroll
-                for (int j = 0; j < CPT; j += 4) {
-                    ld_v8(psi + b + vCol[j], X[j], X[j + 1], X[j + 2], X[j + 3]);
+            for (int x = 0; x < CPT; x += 4) {
+                ld_v8(psi + b + col(x), X[x], X[x + 1], X[x + 2], X[x + 3]);
+                asm volatile("" ::: "memory");
+            }
+        } else if constexpr (MODE == kPairs) {
+#pragma unroll
+            for (int x = 0; x < CPT; x += 2) {
+                const float4 v = *reinterpret_cast<const float4*>(psi + b + col(x));
+                X[x] = make_float2(v.x, v.y);
+                X[x + 1] = make_float2(v.z, v.w);
+                asm volatile("" ::: "memory");
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < CPT; ++x) {
+                X[x] = psi[b + col(x)];
+                asm volatile("" ::: "memory");
+            }
+        }
+    };
+    // A planes of tile X: for the Re and Im parts, plane 0 = FP16 rounding of the scaled value, plane 1 =
+    // FP16 rounding of the residual; columns 2q and 2q+1 share a 32-bit TMEM column (2q in the low half).
+    auto store_a = [&](const float2 (&X)[CPT]) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t hi[CPH / 2], lo[CPH / 2];
+#pragma unroll
+                for (int q = 0; q < CPH / 2; ++q) {
+                    const float2 xe = X[CPH * h + 2 * q], xo = X[CPH * h + 2 * q + 1];
+                    const float e = (part ? xe.y : xe.x) * kScaleX, o = (part ? xo.y : xo.x) * kScaleX;
+                    uint32_t vh, vl;
+                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vh) : "f"(o), "f"(e));
+                    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&vh));
+                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vl) : "f"(o - hf.y), "f"(e - hf.x));
+                    hi[q] = vh;
+                    lo[q] = vl;
+                }
+                const uint32_t c = A0 + (uint32_t)(part * (D / 2) + (H * h + CPH * w4) / 2);
+                tmem_st<CPH / 2>(tbase + tlane + c, hi);
+                tmem_st<CPH / 2>(tbase + tlane + D + c, lo);
+            }
+        wait_st();
+    };
+    // Half h of tile t's accumulator (Im Y at column 128 h + c', Re Y at 128 h + 64 + c'), scaled back and
+    // stored in place.
+    auto drain_half = [&](int h, uint64_t t) {
+        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+#pragma unroll
+        for (int ch = 0; ch < CPH / 8; ++ch) {
+            uint32_t re[8], im[8], v[16];
+            const uint32_t c = (uint32_t)(D * h + CPH * w4 + 8 * ch);
+            tmem_ld<8>(tbase + tlane + c, im);
+            tmem_ld<8>(tbase + tlane + c + H, re);
+            wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[2 * j] = __float_as_uint(__uint_as_float(re[j]) * kOut);
+                v[2 * j + 1] = __float_as_uint(__uint_as_float(im[j]) * kOut);
+            }
+            const int x0 = CPH * h + 8 * ch;
+            if constexpr (MODE == kQuads) {
+#pragma unroll
+                for (int j = 0; j < 8; j += 4) {
+                    st_v8(psi + b + col(x0 + j), v + 2 * j);
                     asm volatile("" ::: "memory");
                 }
             } else if constexpr (MODE == kPairs) {
 #pragma unroll
-                for (int j = 0; j < CPT; j += 2) {
-                    const float4 v = *reinterpret_cast<const float4*>(psi + b + vCol[j]);
-                    X[j] = make_float2(v.x, v.y);
-                    X[j + 1] = make_float2(v.z, v.w);
+                for (int j = 0; j < 8; j += 2) {
+                    *reinterpret_cast<float4*>(psi + b + col(x0 + j)) =
+                        make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
+                                    __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
                     asm volatile("" ::: "memory");
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    X[j] = psi[b + vCol[j]];
+                for (int j = 0; j < 8; ++j) {
+                    psi[b + col(x0 + j)] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
                     asm volatile("" ::: "memory");
                 }
             }
-        };
-        // A planes of tile X: for the Re and Im parts, plane 0 = FP16 rounding of the scaled value, plane 1 =
-        // FP16 rounding of the residual; columns 2q and 2q+1 share a 32-bit TMEM column (2q in the low half)
-        auto store_a = [&](const float2 (&X)[CPT]) {
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                uint32_t hi[CPT / 2], lo[CPT / 2];
-#pragma unroll
-                for (int q = 0; q < CPT / 2; ++q) {
-                    const float e = (part ? X[2 * q].y : X[2 * q].x) * kScaleX;
-                    const float o = (part ? X[2 * q + 1].y : X[2 * q + 1].x) * kScaleX;
-                    uint32_t h, l;
-                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(o), "f"(e));
-                    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&h));
-                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(o - hf.y), "f"(e - hf.x));
-                    hi[q] = h;
-                    lo[q] = l;
-                }
-                tmem_st<CPT / 2>(tbase + tlane + A0 + part * (D / 2) + c0 / 2, hi);
-                tmem_st<CPT / 2>(tbase + tlane + A0 + D + part * (D / 2) + c0 / 2, lo);
-            }
-            wait_st();
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(full);
-        };
-        // The accumulator of tile t (Re Y at column 128 + c, Im Y at c), scaled back and stored in place.
-        auto drain = [&](uint64_t t) {
-            const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
-#pragma unroll
-            for (int h = 0; h < CPT / 8; ++h) {
-                uint32_t re[8], im[8], v[16];
-                tmem_ld<8>(tbase + tlane + D + c0 + 8 * h, re);
-                tmem_ld<8>(tbase + tlane + c0 + 8 * h, im);
-                wait_ld();
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    v[2 * j] = __float_as_uint(__uint_as_float(re[j]) * kOut);
-                    v[2 * j + 1] = __float_as_uint(__uint_as_float(im[j]) * kOut);
-                }
-                if constexpr (MODE == kQuads) {
-#pragma unroll
-                    for (int j = 0; j < 8; j += 4) {
-                        st_v8(psi + b + vCol[8 * h + j], v + 2 * j);
-                        asm volatile("" ::: "memory");
-                    }
-                } else if constexpr (MODE == kPairs) {
-#pragma unroll
-                    for (int j = 0; j < 8; j += 2) {
-                        *reinterpret_cast<float4*>(psi + b + vCol[8 * h + j]) =
-                            make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
-                                        __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
-                        asm volatile("" ::: "memory");
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        psi[b + vCol[8 * h + j]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-                        asm volatile("" ::: "memory");
-                    }
-                }
-            }
-        };
-        // warp-uniform bounded wait (the TMEM accesses that follow are .sync.aligned)
-        auto wait = [&](uint32_t bar, uint32_t par) -> bool {
-            const bool ok = !__any_sync(0xffffffffu, !mbar_wait_bounded(bar, par));
-            fence_after();
-            return ok;
-        };
-        // Tile i: once the MMAs of tile i-1 are done (its accumulator final, the A planes free), drain tile
-        // i-1, write tile i's A planes, then load tile i+1, whose latency the MMAs of tile i cover.
-        bool bad = false;
-        float2 X[CPT];
-        if (m > 0) load_tile(X, t0);
-        for (uint64_t i = 0; i < m; ++i) {
-            if (i > 0) {
-                if (!wait(done, (uint32_t)((i - 1) & 1))) { bad = true; break; }
-                drain(t0 + (i - 1) * G);
-            }
-            store_a(X);
-            if (warp == 0 && !issue_tile(i)) { bad = true; break; }
-            if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);
         }
-        if (!bad && m > 0) {
-            if (wait(done, (uint32_t)((m - 1) & 1))) drain(t0 + (m - 1) * G);
-            else bad = true;
-        }
-        if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-        if (warp == 0 && lane == 0) {
-            if (!b_ready) mbar_wait_bounded(bbar, 0);           // the bulk copy of B, if never waited for
-            if (bad && issued) mbar_wait_bounded(done, last_par);  // the MMAs already issued
-        }
+    };
+    // one arrival per warp, after its TMEM accesses have completed
+    auto arrive = [&](uint32_t bar) {
+        fence_before();
         __syncwarp();
+        if (lane == 0) mbar_arrive(bar);
+    };
+    // warp-uniform bounded wait (the TMEM accesses that follow are .sync.aligned)
+    auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+        const bool ok = !__any_sync(0xffffffffu, !mbar_wait_bounded(bar, par));
+        fence_after();
+        return ok;
+    };
+
+    bool bad = false;
+    float2 X[CPT];
+    if (m > 0) load_tile(X, t0);
+    for (uint64_t i = 0; i < m; ++i) {
+        const uint32_t pc = (uint32_t)(i & 1), pp = (uint32_t)((i - 1) & 1);
+        if (i > 0 && !wait(done1, pp)) { bad = true; break; }  // A planes free, half 1 of tile i-1 final
+        store_a(X);
+        arrive(full);
+        if (warp == 0 && !issue_after(full, pc, 0, i)) { bad = true; break; }
+        if (i > 0) drain_half(1, t0 + (i - 1) * G);
+        arrive(free1);
+        if (warp == 0 && !issue_after(free1, pc, 1, i)) { bad = true; break; }
+        if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);
+        if (!wait(done0, pc)) { bad = true; break; }
+        drain_half(0, t0 + i * G);
     }
+    if (!bad && m > 0) {
+        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, t0 + (m - 1) * G);
+        else bad = true;
+    }
+    if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    if (warp == 0 && lane == 0) {
+        if (!b_ready) mbar_wait_bounded(bbar, 0);              // the bulk copy of B, if never waited for
+        if (bad && issued) mbar_wait_bounded(last_bar, last_par);  // the MMAs already issued
+    }
+    __syncwarp();
     fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -305,18 +327,19 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     }
 }
 
-// B operand: row n of [Im U; Re U; -Im U] (output index i = n mod 128) against input index c, scaled by 2^14
-// and split into two FP16 planes (value, residual), written in the swizzled shared-memory byte layout.
+// B operand: row n = 192 h + 64 blk + i' holds, for output row i = 64 h + i' of U, Im U (blk 0), Re U (blk 1)
+// or -Im U (blk 2) against input index c, scaled by 2^14 and split into two FP16 planes (value, residual), in
+// the swizzled shared-memory byte layout.
 __global__ void k_tc7_prepare(const double* __restrict__ U, unsigned char* __restrict__ out) {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NB * D; idx += gridDim.x * blockDim.x) {
         const int n = idx / D, c = idx % D;
-        const int blk = n / D, i = n % D;
+        const int h = n / (3 * H), blk = (n % (3 * H)) / H, i = H * h + n % H;
         const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
         const double w = kScaleU * (blk == 0 ? ui : (blk == 1 ? ur : -ui));
-        const __half h = __float2half_rn((float)w);
+        const __half hv = __float2half_rn((float)w);
         const uint32_t off = sw128_offset(n, c, NB, 2);
-        *reinterpret_cast<__half*>(out + off) = h;
-        *reinterpret_cast<__half*>(out + PB + off) = __float2half_rn((float)(w - (double)__half2float(h)));
+        *reinterpret_cast<__half*>(out + off) = hv;
+        *reinterpret_cast<__half*>(out + PB + off) = __float2half_rn((float)(w - (double)__half2float(hv)));
     }
 }
 
