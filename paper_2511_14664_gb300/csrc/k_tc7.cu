@@ -21,15 +21,20 @@
 // plane p (0 hi, 1 lo), part (0 Re, 1 Im) at 256 + 128 p + 64 part, two FP16 values per column (even K in
 // the low half). Per tile the MMAs of half 0 and of half 1 are committed separately, so that the drain of
 // one half overlaps the MMAs of the other; the A planes are single-buffered, so the tensor cores wait only
-// while a tile's A planes are written. Sequence of tile i (every warp; "issue" = lane 0 of warp 0):
-//   wait done1(i-1); write A(i); arrive full        issue: wait full, MMAs of half 0, commit done0
-//   drain half 1 of tile i-1; arrive free1          issue: wait free1, MMAs of half 1, commit done1
-//   load tile i+1 into registers; wait done0(i); drain half 0 of tile i
+// while a tile's A planes are written. Sequence of tile i (data warps, and the MMA issuer):
+//   wait done1(i-1); write A(i); arrive full        issuer: wait full, MMAs of half 0, commit done0
+//   drain half 1 of tile i-1; arrive free1          issuer: wait free1, MMAs of half 1, commit done1
+//   load tile i+1 into registers; wait done0(i); drain half 0 of tile i, splitting tile i+1 into its packed
+//   FP16 planes (in the registers it was loaded into) between the stores
+// The loads and stores issue at the rate this SM's share of the HBM bandwidth drains them, so the data
+// warps spend most of a tile in them; the MMAs of both halves run back to back while the warps drain half 1
+// and load, and only the tensor-memory stores of A sit between one tile's MMAs and the next.
 // The MMAs of a tile (3.6 us per SM at the measured FP16 rate) take less than the tile's share of the HBM
 // time (5.9 us).
 //
-// Sixteen warps (four per TMEM lane quadrant; no separate MMA warp, whose seventeenth slot would cap every
-// thread at 96 registers), one CTA per SM (persistent over tiles). A thread owns one row of a tile and 16
+// Sixteen data warps (four per TMEM lane quadrant) and one warp whose lane 0 issues the MMAs (an issuing
+// thread stalls until most of the MMAs it issued have run, so it has no other work), one CTA per SM
+// (persistent over tiles); 17 warps leave 96 registers per thread. A thread owns one row of a tile and 16
 // columns of each half; like the 6-qubit block its amplitudes move as 8-byte values, 16-byte pairs when
 // qubit 0 is the first target, or 32-byte quads when qubits 0 and 1 are the first two. Every mbarrier wait is
 // bounded (2 s); on expiry the kernel records DEVERR_TIMEOUT, waits once more (bounded) for its MMAs, frees
@@ -54,8 +59,8 @@ constexpr int kRowBits = 7;             // 128 rows per tile (MMA M = 128)
 constexpr int NB = 3 * D;               // B rows: per half [Im U_h; Re U_h; -Im U_h]
 constexpr int PB = NB * D * 2;          // bytes of one FP16 B plane (96 KiB)
 constexpr int ATOM = NB * 128;          // one 128-byte K atom over all B rows
-constexpr int kWarps = 16;
-constexpr int kThreads = kWarps * 32;
+constexpr int kWarps = 16;                // data warps; warp 16 issues the MMAs
+constexpr int kThreads = (kWarps + 1) * 32;
 constexpr int CPH = H / 4;              // columns of each half per thread (4 warps per lane quadrant)
 constexpr int CPT = 2 * CPH;            // complex columns per thread
 constexpr uint32_t A0 = 2 * D;          // first A column in TMEM
@@ -125,7 +130,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     const uint64_t t0 = blockIdx.x, G = gridDim.x;
     const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
 
-    // ---- MMA issue (lane 0 of warp 0) ----
+    // ---- MMA issue (lane 0 of warp 16) ----
     const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
     const uint32_t dhi = (uint32_t)(desc0 >> 32);
     // The MMAs of output half h: products (A plane, B plane) lo*hi, hi*lo, hi*hi; Re X on the B window at
@@ -153,32 +158,10 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     auto commit = [&](uint32_t bar) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
     };
-    bool b_ready = false;  // lane 0 of warp 0: B has arrived in shared memory
-    bool issued = false;   // lane 0 of warp 0: MMAs issued; the last commit went to last_bar, phase last_par
+    bool b_ready = false;  // the MMA issuer has waited for B
+    bool issued = false;   // MMAs issued; the last commit went to last_bar, phase last_par
     uint32_t last_bar = 0, last_par = 0;
-    // warp 0 (whole warp): after a bounded wait on `bar` (phase par), issue the MMAs of half h of tile i and
-    // commit them; false for the whole warp when a wait expired
-    auto issue_after = [&](uint32_t bar, uint32_t par, int h, uint64_t i) -> bool {
-        bool ok = true;
-        if (lane == 0) {
-            if (!b_ready) {
-                b_ready = mbar_wait_bounded(bbar, 0);
-                ok = b_ready;
-            }
-            ok = ok && mbar_wait_bounded(bar, par);
-            if (ok) {
-                fence_after();
-                issue_half(h);
-                last_bar = h ? done1 : done0;
-                last_par = (uint32_t)(i & 1);
-                commit(last_bar);
-                issued = true;
-            }
-        }
-        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    };
-
-    // ---- data movement (every warp) ----
+    // ---- data movement (warps 0..15) ----
     const int quad = warp & 3, w4 = warp >> 2;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
     const uint64_t rowoff = deposit((uint64_t)(quad * 32 + lane), a.rpos, kRowBits);
@@ -215,34 +198,62 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
             }
         }
     };
-    // A planes of tile X: for the Re and Im parts, plane 0 = FP16 rounding of the scaled value, plane 1 =
-    // FP16 rounding of the residual; columns 2q and 2q+1 share a 32-bit TMEM column (2q in the low half).
+    // A planes of tile X, packed in place: the pair of columns (2q, 2q+1) of output half h's share, X[CPH h + 2q]
+    // and X[CPH h + 2q + 1], becomes four 32-bit words (bits in the float2 fields): Re plane 0, Re plane 1, Im
+    // plane 0, Im plane 1, each holding the two columns' FP16 values (2q in the low half). Plane 0 = FP16
+    // rounding of the scaled value, plane 1 = FP16 rounding of the residual. Done before the wait for the
+    // tensor memory they go to, between the stores of the drain that precedes it (which issue only as fast as
+    // the memory system takes them).
+    auto convert_pair = [&](float2 (&X)[CPT], int x) {
+        {
+            uint32_t w[4];
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const float e = (part ? X[x].y : X[x].x) * kScaleX, o = (part ? X[x + 1].y : X[x + 1].x) * kScaleX;
+                uint32_t vh, vl;
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vh) : "f"(o), "f"(e));
+                const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&vh));
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vl) : "f"(o - hf.y), "f"(e - hf.x));
+                w[2 * part] = vh;
+                w[2 * part + 1] = vl;
+            }
+            X[x] = make_float2(__uint_as_float(w[0]), __uint_as_float(w[1]));
+            X[x + 1] = make_float2(__uint_as_float(w[2]), __uint_as_float(w[3]));
+        }
+    };
+    auto convert = [&](float2 (&X)[CPT]) {
+#pragma unroll
+        for (int x = 0; x < CPT; x += 2) convert_pair(X, x);
+    };
     auto store_a = [&](const float2 (&X)[CPT]) {
 #pragma unroll
         for (int part = 0; part < 2; ++part)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+                const uint32_t c = A0 + (uint32_t)(part * (D / 2) + (H * h + CPH * w4) / 2);
                 uint32_t hi[CPH / 2], lo[CPH / 2];
 #pragma unroll
                 for (int q = 0; q < CPH / 2; ++q) {
-                    const float2 xe = X[CPH * h + 2 * q], xo = X[CPH * h + 2 * q + 1];
-                    const float e = (part ? xe.y : xe.x) * kScaleX, o = (part ? xo.y : xo.x) * kScaleX;
-                    uint32_t vh, vl;
-                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vh) : "f"(o), "f"(e));
-                    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&vh));
-                    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vl) : "f"(o - hf.y), "f"(e - hf.x));
-                    hi[q] = vh;
-                    lo[q] = vl;
+                    const float2 v = X[CPH * h + 2 * q + part];
+                    hi[q] = __float_as_uint(v.x);
+                    lo[q] = __float_as_uint(v.y);
                 }
-                const uint32_t c = A0 + (uint32_t)(part * (D / 2) + (H * h + CPH * w4) / 2);
                 tmem_st<CPH / 2>(tbase + tlane + c, hi);
                 tmem_st<CPH / 2>(tbase + tlane + D + c, lo);
             }
         wait_st();
     };
     // Half h of tile t's accumulator (Im Y at column 128 h + c', Re Y at 128 h + 64 + c'), scaled back and
-    // stored in place.
-    auto drain_half = [&](int h, uint64_t t) {
+    // stored in place; with cv, the pairs of X are converted (convert_pair), evenly between the stores.
+    auto drain_half = [&](int h, uint64_t t, float2 (&X)[CPT], bool cv) {
+        constexpr int SPC = MODE == kQuads ? 2 : (MODE == kPairs ? 4 : 8);  // stores per chunk of 8 columns
+        constexpr int PPS = (CPT / 2) / (SPC * (CPH / 8));                    // pairs converted per store
+        auto after_store = [&](int k) {
+            if (cv) {
+#pragma unroll
+                for (int p = 0; p < PPS; ++p) convert_pair(X, 2 * (k * PPS + p));
+            }
+        };
         const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
 #pragma unroll
         for (int ch = 0; ch < CPH / 8; ++ch) {
@@ -262,6 +273,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
                 for (int j = 0; j < 8; j += 4) {
                     st_v8(psi + b + col(x0 + j), v + 2 * j);
                     asm volatile("" ::: "memory");
+                    after_store(ch * SPC + j / 4);
                 }
             } else if constexpr (MODE == kPairs) {
 #pragma unroll
@@ -270,12 +282,14 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
                         make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                     __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
                     asm volatile("" ::: "memory");
+                    after_store(ch * SPC + j / 2);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     psi[b + col(x0 + j)] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
                     asm volatile("" ::: "memory");
+                    after_store(ch * SPC + j);
                 }
             }
         }
@@ -294,31 +308,54 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     };
 
     bool bad = false;
+    if (warp == kWarps) {
+        // ---- MMA issuer: per tile, half 0 once every data warp has written the A planes, half 1 once every
+        // data warp has drained half 1 of the previous tile ----
+        if (lane == 0) {
+            bad = !mbar_wait_bounded(bbar, 0);
+            b_ready = true;
+            if (bad) mbar_wait_bounded(bbar, 0);  // once more for the copy still in flight
+            for (uint64_t i = 0; i < m && !bad; ++i) {
+                const uint32_t pc = (uint32_t)(i & 1);
+                for (int h = 0; h < 2 && !bad; ++h) {
+                    if (!mbar_wait_bounded(h ? free1 : full, pc)) { bad = true; break; }
+                    fence_after();
+                    issue_half(h);
+                    last_bar = h ? done1 : done0;
+                    last_par = pc;
+                    commit(last_bar);
+                    issued = true;
+                }
+            }
+            if (bad) {
+                atomicOr(err, DEVERR_TIMEOUT);
+                if (issued) mbar_wait_bounded(last_bar, last_par);  // the MMAs already issued
+            }
+        }
+        __syncwarp();
+    } else {
     float2 X[CPT];
-    if (m > 0) load_tile(X, t0);
+    if (m > 0) {
+        load_tile(X, t0);
+        convert(X);
+    }
     for (uint64_t i = 0; i < m; ++i) {
         const uint32_t pc = (uint32_t)(i & 1), pp = (uint32_t)((i - 1) & 1);
         if (i > 0 && !wait(done1, pp)) { bad = true; break; }  // A planes free, half 1 of tile i-1 final
         store_a(X);
         arrive(full);
-        if (warp == 0 && !issue_after(full, pc, 0, i)) { bad = true; break; }
-        if (i > 0) drain_half(1, t0 + (i - 1) * G);
+        if (i > 0) drain_half(1, t0 + (i - 1) * G, X, false);
         arrive(free1);
-        if (warp == 0 && !issue_after(free1, pc, 1, i)) { bad = true; break; }
-        if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);
+        if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);  // in flight during the MMAs and the drain below
         if (!wait(done0, pc)) { bad = true; break; }
-        drain_half(0, t0 + i * G);
+        drain_half(0, t0 + i * G, X, i + 1 < m);      // converts tile i+1 between its stores
     }
     if (!bad && m > 0) {
-        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, t0 + (m - 1) * G);
+        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, t0 + (m - 1) * G, X, false);
         else bad = true;
     }
     if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-    if (warp == 0 && lane == 0) {
-        if (!b_ready) mbar_wait_bounded(bbar, 0);              // the bulk copy of B, if never waited for
-        if (bad && issued) mbar_wait_bounded(last_bar, last_par);  // the MMAs already issued
     }
-    __syncwarp();
     fence_before();
     __syncthreads();
     if (warp == 0) {
