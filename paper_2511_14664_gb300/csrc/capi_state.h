@@ -47,7 +47,7 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
 // `lookahead` largest candidates by their size plus that of the best block after them.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
                                           int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1,
-                                          int lookahead = 0);
+                                          int lookahead = 0, uint64_t narrow = 0);
 
 }  // namespace qsim
 

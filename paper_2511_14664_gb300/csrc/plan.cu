@@ -78,9 +78,11 @@ static inline int popcnt(uint64_t v) { return __builtin_popcountll(v); }
 // One block: scan the unplaced gates in order and absorb every gate that is not blocked by an earlier
 // unplaced gate on a shared qubit (a diagonal gate is blocked only by non-diagonal ones) and that fits: with
 // a fixed window W, gates whose qubits lie inside W; otherwise (W = 0) gates that keep the growing qubit set
-// within kmax qubits, starting from `seed`.
+// within kmax qubits (kmax - 1 once it touches a qubit in `narrow`), starting from `seed`.
 static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
-                                    const std::vector<char>& done, int first, int seed, uint64_t W, int kmax) {
+                                    const std::vector<char>& done, int first, int seed, uint64_t W, int kmax,
+                                    uint64_t narrow) {
+    auto lim = [&](uint64_t S) { return (S & narrow) ? kmax - 1 : kmax; };
     const int G = (int)gmask.size();
     std::vector<int> blk;
     uint64_t Q = 0, bany = 0, bdiag = 0;
@@ -89,7 +91,7 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
         if (done[i] || i == seed) continue;
         const uint64_t qs = gmask[i];
         const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
-        const bool fits = W ? (qs & ~W) == 0 : popcnt(Q | qs) <= kmax;
+        const bool fits = W ? (qs & ~W) == 0 : popcnt(Q | qs) <= lim(Q | qs);
         if (!blocked && fits) {
             blk.push_back(i);
             Q |= qs;
@@ -99,7 +101,7 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
             bany |= qs;
         }
         // nothing further can join once every qubit a new gate could use is blocked by a non-diagonal gate
-        const uint64_t usable = W ? W : (popcnt(Q) >= kmax ? Q : ~0ull);
+        const uint64_t usable = W ? W : (popcnt(Q) >= lim(Q) ? Q : ~0ull);
         if ((usable & ~bany) == 0) break;
     }
     std::sort(blk.begin(), blk.end());
@@ -111,9 +113,11 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
 // earliest unplaced gate when no earlier unplaced gate blocks it, grown greedily. The plain greedy choice
 // (seeded at the earliest unplaced gate) is one of the candidates. On nearest-neighbour circuits the
 // windows tile the (qubit, time) plane in diamonds, about twice the gates per block of the plain greedy.
+// Blocks that touch a qubit in `narrow` hold at most kmax - 1 qubits (a window over such a qubit is one
+// qubit narrower).
 static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
                                                 int n, int kmax, const std::vector<char>* gwide, int wide_factor,
-                                                const std::vector<char>& done, int first) {
+                                                const std::vector<char>& done, int first, uint64_t narrow) {
     const int G = (int)gmask.size();
     std::vector<std::vector<int>> out;
     std::vector<int> wide;
@@ -133,8 +137,9 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
     size_t best = 0;
     const int wmax = std::min(kmax, n);
     for (int a0 = 0; a0 + wmax <= n; ++a0) {
-        const uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
-        auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax);
+        uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
+        if (W & narrow) W &= ~(1ull << (a0 + wmax - 1));
+        auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax, narrow);
         best = std::max(best, blk.size());
         if (!blk.empty()) out.push_back(std::move(blk));
     }
@@ -144,7 +149,7 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
         const uint64_t qs = gmask[i];
         const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
         if ((qs & ~seen) && !blocked && popcnt(qs) <= kmax) {
-            auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax);
+            auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax, narrow);
             best = std::max(best, blk.size());
             if (!blk.empty()) out.push_back(std::move(blk));
         }
@@ -163,7 +168,8 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
 // the candidate among the `lookahead` largest distinct ones whose size plus the size of the best block
 // after it is largest (one step of look-ahead; slower planning, sometimes fewer blocks).
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
-                                          int kmax, const std::vector<char>* gwide, int wide_factor, int lookahead) {
+                                          int kmax, const std::vector<char>* gwide, int wide_factor, int lookahead,
+                                          uint64_t narrow) {
     const int G = (int)gmask.size();
     const int LA = lookahead;
     std::vector<std::vector<int>> blocks;
@@ -173,7 +179,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
     while (true) {
         first = next_first(first);
         if (first >= G) break;
-        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first);
+        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first, narrow);
         size_t pick = 0;
         for (size_t c = 1; c < cands.size(); ++c)
             if (cands[c].size() > cands[pick].size()) pick = c;
@@ -194,7 +200,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
                 const int f2 = next_first(first);
                 size_t nxt = 0;
                 if (f2 < G) {
-                    auto c2 = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, f2);
+                    auto c2 = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, f2, narrow);
                     for (const auto& b2 : c2) nxt = std::max(nxt, b2.size());
                 }
                 for (int g : cb) done[g] = 0;
@@ -215,7 +221,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
 // that placed the same set of gates are kept once (Zobrist hash of the placed set).
 std::vector<std::vector<int>> group_gates_beam(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
                                                int n, int kmax, const std::vector<char>* gwide, int wide_factor,
-                                               int beam) {
+                                               int beam, uint64_t narrow) {
     const int G = (int)gmask.size();
     if (G == 0) return {};
     std::vector<uint64_t> zob(G);
@@ -247,7 +253,7 @@ std::vector<std::vector<int>> group_gates_beam(const std::vector<uint64_t>& gmas
         std::vector<Child> kids;
         for (int pi = 0; pi < (int)cur.size(); ++pi) {
             State& st = cur[pi];
-            auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, st.done, st.first);
+            auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, st.done, st.first, narrow);
             for (size_t c = 0; c < cands.size(); ++c) {
                 bool dup = false;
                 for (size_t d = 0; d < c && !dup; ++d) dup = cands[d] == cands[c];
@@ -414,24 +420,27 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // keep 6-qubit blocks
     if (!dry && kmax == 7 && (n < 14 || remap_later)) kmax = 6;
     const bool tc7 = kmax == 7 && opts.precision == QSIM_PREC_FP16X3 && dtype == QSIM_C64 && n >= 14;
+    // 7-qubit blocks keep off qubits 0..2: on those the 7-qubit kernel moves partly used lines (4.0-5.5 ms at 30
+    // qubits against 2.9-3.2 ms above them), while 6-qubit blocks there have the line-group and pair-rows paths
+    const uint64_t narrow = tc7 ? 0x7ull : 0;
     const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !remap_later;
     for (int i = 0; i < G; ++i) gwide[i] = use_wide && gdiag[i] && phase_gate_ok(c->gates[i]);
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, 1);
+        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, 1, 0, narrow);
         // whether a phase pass should wait for more diagonal gates depends on the circuit, and so does
         // whether looking one block ahead pays: keep the grouping with the fewest blocks
         for (int la = 0; la <= (opts.plan_effort > 0 ? 4 : 0); la += 4)
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
                 if (la == 0 && f == 1) continue;  // the first grouping above
-                auto alt = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f, la);
+                auto alt = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f, la, narrow);
                 if (alt.size() < blocks.size()) blocks.swap(alt);
             }
         if (opts.plan_effort >= 2)
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
                 auto alt = group_gates_beam(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f,
-                                            opts.plan_effort >= 3 ? 32 : 8);
+                                            opts.plan_effort >= 3 ? 32 : 8, narrow);
                 if (alt.size() < blocks.size()) blocks.swap(alt);
             }
     }
