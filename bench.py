@@ -165,7 +165,7 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {"dense_small": ["k_gates.cu"], "diag": ["k_gates.cu"], "dense_tile": ["k_gates.cu"],
-                  "tc": ["k_tc.cu", "tc_ptx.cuh", "tmem_io.cuh"],
+                  "tc": ["k_tc.cu", "k_tc7.cu", "tc_ptx.cuh", "tmem_io.cuh"],
                   "tc_pair": ["k_tc_pair.cu", "tc_ptx.cuh", "tmem_io.cuh"]}
 
 

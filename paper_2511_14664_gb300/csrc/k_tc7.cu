@@ -200,8 +200,8 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     };
     // A planes of tile X, packed in place: the pair of columns (2q, 2q+1) of output half h's share, X[CPH h + 2q]
     // and X[CPH h + 2q + 1], becomes four 32-bit words (bits in the float2 fields): Re plane 0, Re plane 1, Im
-    // plane 0, Im plane 1, each holding the two columns' FP16 values (2q in the low half). Plane 0 = FP16
-    // rounding of the scaled value, plane 1 = FP16 rounding of the residual. Done before the wait for the
+    // plane 0, Im plane 1, each holding the two columns' FP16 values (2q in the low half). Plane 0 = the
+    // scaled value's leading 11 significant bits, plane 1 = FP16 rounding of the remainder. Done before the wait for the
     // tensor memory they go to, between the stores of the drain that precedes it (which issue only as fast as
     // the memory system takes them).
     auto convert_pair = [&](float2 (&X)[CPT], int x) {
@@ -210,10 +210,14 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
                 const float e = (part ? X[x].y : X[x].x) * kScaleX, o = (part ? X[x + 1].y : X[x + 1].x) * kScaleX;
+                // Dekker's split (Veltkamp's constant 2^13 + 1): the leading 11 significant bits, exact in FP16 for
+                // scaled values from 2^-14 up, and the exact remainder, in FMA-pipe arithmetic (the _rn forms
+                // are never contracted); only the packing to FP16 takes the conversion unit
+                const float ce = __fmul_rn(e, 8193.0f), co = __fmul_rn(o, 8193.0f);
+                const float he = __fsub_rn(ce, __fsub_rn(ce, e)), ho = __fsub_rn(co, __fsub_rn(co, o));
                 uint32_t vh, vl;
-                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vh) : "f"(o), "f"(e));
-                const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&vh));
-                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vl) : "f"(o - hf.y), "f"(e - hf.x));
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vh) : "f"(ho), "f"(he));
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(vl) : "f"(__fsub_rn(o, ho)), "f"(__fsub_rn(e, he)));
                 w[2 * part] = vh;
                 w[2 * part + 1] = vl;
             }
