@@ -127,8 +127,9 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
                          :: "r"(smem_u32(sb) + o), "l"(reinterpret_cast<const char*>(bops) + o), "r"(kChunk),
                             "r"(bbar) : "memory");
     }
-    const uint64_t t0 = blockIdx.x, G = gridDim.x;
-    const uint64_t m = t0 < a.ntiles ? (a.ntiles - t0 + G - 1) / G : 0;  // tiles of this CTA
+    const uint32_t t0 = blockIdx.x, G = gridDim.x;  // (fewer than 2^32 tiles: checked by the host)
+    const uint32_t m = t0 < a.ntiles ? (uint32_t)((a.ntiles - t0 + G - 1) / G) : 0u;  // tiles of this CTA
+    auto tile = [&](uint32_t i) { return (uint64_t)t0 + (uint64_t)i * G; };
 
     // ---- MMA issue (lane 0 of warp 16) ----
     const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
@@ -164,7 +165,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     // ---- data movement (warps 0..15) ----
     const int quad = warp & 3, w4 = warp >> 2;
     const uint32_t tlane = (uint32_t)(quad * 32) << 16;
-    const uint64_t rowoff = deposit((uint64_t)(quad * 32 + lane), a.rpos, kRowBits);
+    float2* const prow = psi + deposit((uint64_t)(quad * 32 + lane), a.rpos, kRowBits);  // this thread's row
     // X[CPH * h + j] is column H h + CPH w4 + j. Column offsets are re-read from shared memory at each use
     // (one broadcast load) rather than held in 64-bit registers; the empty asm between accesses keeps those
     // reads next to their accesses.
@@ -172,20 +173,21 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     auto col = [&](int x) { return vCol[(x / CPH) * H + x % CPH]; };
 
     auto load_tile = [&](float2 (&X)[CPT], uint64_t t) {
-        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
+        const uint64_t b = insert_zeros(t, a.spos, a.nS);
         if (a.from_basis) {
+            const uint64_t rb = b + deposit((uint64_t)(quad * 32 + lane), a.rpos, kRowBits);
 #pragma unroll
-            for (int x = 0; x < CPT; ++x) X[x] = make_float2(b + col(x) == a.basis ? 1.0f : 0.0f, 0.0f);
+            for (int x = 0; x < CPT; ++x) X[x] = make_float2(rb + col(x) == a.basis ? 1.0f : 0.0f, 0.0f);
         } else if constexpr (MODE == kQuads) {
 #pragma unroll
             for (int x = 0; x < CPT; x += 4) {
-                ld_v8(psi + b + col(x), X[x], X[x + 1], X[x + 2], X[x + 3]);
+                ld_v8(prow + b + col(x), X[x], X[x + 1], X[x + 2], X[x + 3]);
                 asm volatile("" ::: "memory");
             }
         } else if constexpr (MODE == kPairs) {
 #pragma unroll
             for (int x = 0; x < CPT; x += 2) {
-                const float4 v = *reinterpret_cast<const float4*>(psi + b + col(x));
+                const float4 v = *reinterpret_cast<const float4*>(prow + b + col(x));
                 X[x] = make_float2(v.x, v.y);
                 X[x + 1] = make_float2(v.z, v.w);
                 asm volatile("" ::: "memory");
@@ -193,7 +195,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
         } else {
 #pragma unroll
             for (int x = 0; x < CPT; ++x) {
-                X[x] = psi[b + col(x)];
+                X[x] = prow[b + col(x)];
                 asm volatile("" ::: "memory");
             }
         }
@@ -250,6 +252,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     // Half h of tile t's accumulator (Im Y at column 128 h + c', Re Y at 128 h + 64 + c'), scaled back and
     // stored in place; with cv, the pairs of X are converted (convert_pair), evenly between the stores.
     auto drain_half = [&](int h, uint64_t t, float2 (&X)[CPT], bool cv) {
+        float2* const pt = prow + insert_zeros(t, a.spos, a.nS);
         constexpr int SPC = MODE == kQuads ? 2 : (MODE == kPairs ? 4 : 8);  // stores per chunk of 8 columns
         constexpr int PPS = (CPT / 2) / (SPC * (CPH / 8));                    // pairs converted per store
         auto after_store = [&](int k) {
@@ -258,7 +261,6 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
                 for (int p = 0; p < PPS; ++p) convert_pair(X, 2 * (k * PPS + p));
             }
         };
-        const uint64_t b = insert_zeros(t, a.spos, a.nS) + rowoff;
 #pragma unroll
         for (int ch = 0; ch < CPH / 8; ++ch) {
             uint32_t re[8], im[8], v[16];
@@ -275,14 +277,14 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
             if constexpr (MODE == kQuads) {
 #pragma unroll
                 for (int j = 0; j < 8; j += 4) {
-                    st_v8(psi + b + col(x0 + j), v + 2 * j);
+                    st_v8(pt + col(x0 + j), v + 2 * j);
                     asm volatile("" ::: "memory");
                     after_store(ch * SPC + j / 4);
                 }
             } else if constexpr (MODE == kPairs) {
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
-                    *reinterpret_cast<float4*>(psi + b + col(x0 + j)) =
+                    *reinterpret_cast<float4*>(pt + col(x0 + j)) =
                         make_float4(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]),
                                     __uint_as_float(v[2 * j + 2]), __uint_as_float(v[2 * j + 3]));
                     asm volatile("" ::: "memory");
@@ -291,7 +293,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    psi[b + col(x0 + j)] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+                    pt[col(x0 + j)] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
                     asm volatile("" ::: "memory");
                     after_store(ch * SPC + j);
                 }
@@ -319,7 +321,7 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
             bad = !mbar_wait_bounded(bbar, 0);
             b_ready = true;
             if (bad) mbar_wait_bounded(bbar, 0);  // once more for the copy still in flight
-            for (uint64_t i = 0; i < m && !bad; ++i) {
+            for (uint32_t i = 0; i < m && !bad; ++i) {
                 const uint32_t pc = (uint32_t)(i & 1);
                 for (int h = 0; h < 2 && !bad; ++h) {
                     if (!mbar_wait_bounded(h ? free1 : full, pc)) { bad = true; break; }
@@ -343,19 +345,19 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
         load_tile(X, t0);
         convert(X);
     }
-    for (uint64_t i = 0; i < m; ++i) {
+    for (uint32_t i = 0; i < m; ++i) {
         const uint32_t pc = (uint32_t)(i & 1), pp = (uint32_t)((i - 1) & 1);
         if (i > 0 && !wait(done1, pp)) { bad = true; break; }  // A planes free, half 1 of tile i-1 final
         store_a(X);
         arrive(full);
-        if (i > 0) drain_half(1, t0 + (i - 1) * G, X, false);
+        if (i > 0) drain_half(1, tile(i - 1), X, false);
         arrive(free1);
-        if (i + 1 < m) load_tile(X, t0 + (i + 1) * G);  // in flight during the MMAs and the drain below
+        if (i + 1 < m) load_tile(X, tile(i + 1));  // in flight during the MMAs and the drain below
         if (!wait(done0, pc)) { bad = true; break; }
-        drain_half(0, t0 + i * G, X, i + 1 < m);      // converts tile i+1 between its stores
+        drain_half(0, tile(i), X, i + 1 < m);      // converts tile i+1 between its stores
     }
     if (!bad && m > 0) {
-        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, t0 + (m - 1) * G, X, false);
+        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, tile(m - 1), X, false);
         else bad = true;
     }
     if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
@@ -415,6 +417,7 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
     for (int q = 0; q < n; ++q)
         if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
+    if (a.ntiles >> 32) return cudaErrorInvalidValue;  // 32-bit tile counters in the kernel
     if (from_basis) {
         a.from_basis = 1;
         a.basis = *from_basis;
