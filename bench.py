@@ -766,7 +766,9 @@ def run_qft(args):
                      ("tf32x3_k5", dict(mode=1, max_fused=5, precision=1, tc_min_k=5)),
                      ("bf16x6_k5", dict(mode=1, max_fused=5, precision=3, tc_min_k=5)),
                      ("tf32x3_k6", dict(mode=1, max_fused=6, precision=1, tc_min_k=5)),
-                     ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5))]:
+                     ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5)),
+                     ("fp16x3_k6", dict(mode=1, max_fused=6, precision=4, tc_min_k=5)),
+                     ("fp16x3_k7", dict(mode=1, max_fused=7, precision=4, tc_min_k=5))]:
         p = qsim.Plan(c, **kw)
 
         def step(i, p=p):
@@ -1034,7 +1036,9 @@ def run_paper33(args, kind):
     for name, kw in [("plain", dict(mode=0, max_fused=1)), ("tf32x3_k5", dict(mode=1, max_fused=5, precision=1, tc_min_k=5)),
                      ("tf32x3_k6", dict(mode=1, max_fused=6, precision=1, tc_min_k=5)),
                      ("tf32x3_k6_lookahead", dict(mode=1, max_fused=6, precision=1, tc_min_k=5, plan_effort=1)),
-                     ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5))]:
+                     ("bf16x6_k6", dict(mode=1, max_fused=6, precision=3, tc_min_k=5)),
+                     ("fp16x3_k6", dict(mode=1, max_fused=6, precision=4, tc_min_k=5)),
+                     ("fp16x3_k7", dict(mode=1, max_fused=7, precision=4, tc_min_k=5))]:
         if name == "plain" and args.no_variants:
             continue
         p = qsim.Plan(c, **kw)

@@ -425,24 +425,52 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     const uint64_t narrow = tc7 ? 0x7ull : 0;
     const bool use_wide = opts.mode == QSIM_RUN_FUSED && n >= 10 && !remap_later;
     for (int i = 0; i < G; ++i) gwide[i] = use_wide && gdiag[i] && phase_gate_ok(c->gates[i]);
-    if (opts.mode == QSIM_RUN_PLAIN) {
-        for (int i = 0; i < G; ++i) blocks.push_back({i});
-    } else {
-        blocks = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, 1, 0, narrow);
+    // Estimated cost of a grouping in passes: a 7-qubit tensor-core block streams the state like any pass
+    // but takes about 1.2 times as long (3.1-3.2 against 2.6 ms at 30 qubits); a phase pass counts 1, or 0.15
+    // when it follows a dense block of at most 6 qubits (it becomes that block's epilogue, which only a
+    // tensor-core precision has).
+    auto cost = [&](const std::vector<std::vector<int>>& bl) {
+        double cs = 0.0;
+        bool prev_dense6 = false;
+        for (const auto& b : bl) {
+            uint64_t Q = 0;
+            bool wide = use_wide, diag = true;
+            for (int gi : b) { Q |= gmask[gi]; wide = wide && gwide[gi]; diag = diag && gdiag[gi]; }
+            const int k = popcnt(Q);
+            if (wide && k > 6) cs += (prev_dense6 && opts.precision != QSIM_PREC_SIMT) ? 0.15 : 1.0;
+            else cs += (tc7 && k == 7 && !wide) ? 1.2 : 1.0;
+            prev_dense6 = !diag && k <= 6;
+        }
+        return cs;
+    };
+    auto group_all = [&](int km, uint64_t nar) {
+        auto bl = group_gates(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, 1, 0, nar);
         // whether a phase pass should wait for more diagonal gates depends on the circuit, and so does
-        // whether looking one block ahead pays: keep the grouping with the fewest blocks
+        // whether looking one block ahead pays: keep the cheapest grouping (the fewest blocks of each kind)
         for (int la = 0; la <= (opts.plan_effort > 0 ? 4 : 0); la += 4)
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
                 if (la == 0 && f == 1) continue;  // the first grouping above
-                auto alt = group_gates(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f, la, narrow);
-                if (alt.size() < blocks.size()) blocks.swap(alt);
+                auto alt = group_gates(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, f, la, nar);
+                if (cost(alt) < cost(bl)) bl.swap(alt);
             }
         if (opts.plan_effort >= 2)
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
-                auto alt = group_gates_beam(gmask, gdiag, n, kmax, use_wide ? &gwide : nullptr, f,
-                                            opts.plan_effort >= 3 ? 32 : 8, narrow);
-                if (alt.size() < blocks.size()) blocks.swap(alt);
+                auto alt = group_gates_beam(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, f,
+                                            opts.plan_effort >= 3 ? 32 : 8, nar);
+                if (cost(alt) < cost(bl)) bl.swap(alt);
             }
+        return bl;
+    };
+    if (opts.mode == QSIM_RUN_PLAIN) {
+        for (int i = 0; i < G; ++i) blocks.push_back({i});
+    } else {
+        blocks = group_all(kmax, narrow);
+        // 7-qubit blocks pay on nearest-neighbour circuits (whole windows of adjacent qubits), not always
+        // (random target sets, the QFT's phase epilogues): the 6-qubit grouping is kept when it is cheaper
+        if (tc7) {
+            auto b6 = group_all(6, 0);
+            if (cost(b6) <= cost(blocks)) blocks.swap(b6);
+        }
     }
     // A diagonal block moves after a tensor-core block that follows it when they share no qubit (so they
     // commute), and neighbouring diagonal blocks merge (diagonal gates commute): a phase pass then follows

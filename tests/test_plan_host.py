@@ -198,7 +198,8 @@ def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
             keep_tf32 = not epi and (t[:4] == [0, 1, 2, 3] or (0 not in t and any(x in t for x in (1, 2, 3))))
             assert q["precision"] == (1 if keep_tf32 else 4), (t, q["precision"])
     assert sum(q["gates"] for q in paired) == len(c)
-    assert sum(1 for q in paired if q["kind"] == "tc_pair") >= len(single) // 4
+    # (blocks with a phase epilogue do not pair)
+    assert sum(1 for q in paired if q["kind"] == "tc_pair") >= len(single) // 5
 
 
 def test_seven_qubit_blocks(qsim):
