@@ -40,6 +40,8 @@ def _close(got, ref, n, dtype):
 
 @pytest.mark.parametrize("dtype,kw", [
     (0, dict(mode=1, max_fused=6, precision=1)),      # fused 3xTF32 tensor-core blocks in every window
+    (0, dict(mode=1, max_fused=6, precision=4)),      # FP16 split products
+    (0, dict(mode=1, max_fused=7, precision=4)),      # FP16 split products, 7-qubit blocks where they pay
     (0, dict(mode=1, max_fused=4, precision=0)),      # CUDA-core fused blocks
     (1, dict(mode=0, max_fused=1, precision=0)),      # complex128, one pass per gate
 ])
