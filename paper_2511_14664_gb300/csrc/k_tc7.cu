@@ -350,9 +350,13 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
         if (i > 0 && !wait(done1, pp)) { bad = true; break; }  // A planes free, half 1 of tile i-1 final
         store_a(X);
         arrive(full);
+        // warps of odd column groups load before draining half 1, the others after: loads and stores from
+        // different warps overlap instead of every warp switching between them at once
+        const bool early = (w4 & 1) != 0;
+        if (early && i + 1 < m) load_tile(X, tile(i + 1));
         if (i > 0) drain_half(1, tile(i - 1), X, false);
         arrive(free1);
-        if (i + 1 < m) load_tile(X, tile(i + 1));  // in flight during the MMAs and the drain below
+        if (!early && i + 1 < m) load_tile(X, tile(i + 1));  // in flight during the MMAs and the drain below
         if (!wait(done0, pc)) { bad = true; break; }
         drain_half(0, tile(i), X, i + 1 < m);      // converts tile i+1 between its stores
     }
