@@ -31,7 +31,8 @@ def check(psi_gpu, ref, n):
 
 # target lists (in the order given, which fixes U's column bits) for each data path of the kernel
 TARGETS = {
-    "rows_high": (7, 8, 9, 10, 11, 12, 13),   # rows are qubits 0..6: whole lines per warp access
+    "rows_high": (7, 8, 9, 10, 11, 12, 13),   # rows are qubits 0..6: bulk copies of whole 1 KiB columns
+    "rows_q3": (3, 4, 6, 8, 10, 12, 13),      # targets from qubit 3 up: bulk copies of 8-amplitude runs
     "rows_mixed": (2, 5, 8, 9, 11, 3, 13),    # unsorted, qubits 2 and 3 among them
     "rows_q1": (1, 4, 6, 8, 10, 12, 13),      # qubit 1 but not 0
     "rows_q0_later": (5, 0, 1, 7, 9, 11, 13), # qubit 0 a target but not the first: rows path
@@ -58,7 +59,7 @@ def test_single_block_against_oracle(qsim, name, n):
     check(st.get_state(), ref, n)
 
 
-@pytest.mark.parametrize("name", ["rows_mixed", "quads", "pairs"])
+@pytest.mark.parametrize("name", ["rows_mixed", "quads", "pairs", "rows_high", "rows_q3"])
 def test_single_block_many_tiles_per_cta(qsim, name):
     """23 qubits: 512 tiles, several per CTA (the accumulator and A planes reused across tiles)."""
     n = 23
