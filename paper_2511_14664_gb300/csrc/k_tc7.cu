@@ -56,8 +56,8 @@ using namespace qsim::tc;
 constexpr int K = 7, D = 1 << K;        // targets, complex columns of a tile
 constexpr int H = D / 2;                // columns per output half
 constexpr int kRowBits = 7;             // 128 rows per tile (MMA M = 128)
-constexpr int NB = 2 * D;               // B rows: per half h, [Im U_h; Re U_h] (64 rows each)
-constexpr int PB = NB * D * 2;          // bytes of one FP16 B plane (64 KiB)
+constexpr int NB = 3 * D;               // B rows: per half [Im U_h; Re U_h; -Im U_h]
+constexpr int PB = NB * D * 2;          // bytes of one FP16 B plane (96 KiB)
 constexpr int ATOM = NB * 128;          // one 128-byte K atom over all B rows
 constexpr int kWarps = 16;                // data warps; warp 16 issues the MMAs
 constexpr int kThreads = (kWarps + 1) * 32;
@@ -65,22 +65,15 @@ constexpr int CPH = H / 4;              // columns of each half per thread (4 wa
 constexpr int CPT = 2 * CPH;            // complex columns per thread
 constexpr uint32_t A0 = 2 * D;          // first A column in TMEM
 constexpr uint32_t TCOLS = 512;
-// kind::f16: FP32 accumulator, A and B FP16, K-major, M = 128; N = 128, or N = 64 (IDESC64N: B negated,
-// instruction-descriptor bit 14)
+// kind::f16: FP32 accumulator, A and B FP16, K-major, N = 128, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(D >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-constexpr uint32_t IDESC64 = (1u << 4) | ((uint32_t)(H >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-constexpr uint32_t IDESC64N = IDESC64 | (1u << 14);
-constexpr int kStage = H * D * 8;       // one output half of a tile in shared memory (64 KiB), column-major
 constexpr float kScaleX = 32768.0f;     // 2^15
 constexpr double kScaleU = 16384.0;     // 2^14
 constexpr float kOut = 1.0f / (32768.0f * 16384.0f);
-constexpr int kBars = 7;                // full, free1, done0, done1, B loaded, stage free, stage written
-constexpr size_t kSmem = 2 * (size_t)PB + kStage + sizeof(uint64_t) * D + 8 * kBars + 8 + 1024;
+constexpr int kBars = 5;                // full, free1, done0, done1, B loaded
+constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 8 * kBars + 8 + 1024;
 
-// kRowsBulk: lanes on rows, the accumulator drained through a shared-memory stage and written by bulk
-// copies of the runs of rows that are contiguous in the state (targets from qubit 3 up: runs of >= 8
-// amplitudes, 64 bytes)
-enum Mode { kRows = 0, kPairs = 1, kQuads = 2, kRowsBulk = 3 };
+enum Mode { kRows = 0, kPairs = 1, kQuads = 2 };
 
 struct Args {
     int nS;              // 14 index bits covered by a tile
@@ -90,7 +83,6 @@ struct Args {
     uint64_t ntiles;
     int from_basis;      // the input is |basis>, generated in registers instead of read
     uint64_t basis;
-    int runlog;          // row bits 0..runlog-1 are qubits 0..runlog-1 (runs of 2^runlog contiguous rows)
 };
 
 template <int MODE>
@@ -99,15 +91,14 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
             unsigned* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sb = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    [[maybe_unused]] float2* const stage = reinterpret_cast<float2*>(sb + 2 * PB);  // [column of the half][row]
-    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB + kStage);
+    uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
     uint64_t* mbar = sCol + D;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kBars);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
     if (tid == 0) {
-        const int count[kBars] = {kWarps, kWarps, 1, 1, 1, 1, kWarps};
+        const int count[kBars] = {kWarps, kWarps, 1, 1, 1};
         for (int j = 0; j < kBars; ++j)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + j)), "r"(count[j]) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -123,7 +114,6 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     const uint32_t tbase = *tslot;
     const uint32_t full = smem_u32(mbar + 0), free1 = smem_u32(mbar + 1), done0 = smem_u32(mbar + 2),
                    done1 = smem_u32(mbar + 3), bbar = smem_u32(mbar + 4);
-    [[maybe_unused]] const uint32_t sfree = smem_u32(mbar + 5), sdone = smem_u32(mbar + 6);
     // programmatic dependent launch: the set-up above overlapped the previous kernel's tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -144,9 +134,9 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     // ---- MMA issue (lane 0 of warp 16) ----
     const uint64_t desc0 = sdesc_sw128(smem_u32(sb));
     const uint32_t dhi = (uint32_t)(desc0 >> 32);
-    // The MMAs of output half h: products (A plane, B plane) lo*hi, hi*lo, hi*hi. Re X on the half's 128 B
-    // rows [Im U_h; Re U_h] (N = 128) gives [Im Y_h | Re Y_h]; Im X on the Re U_h rows (N = 64) adds to Im Y_h
-    // and on the Im U_h rows, negated (N = 64), to Re Y_h. The first MMA (N = 128) starts the accumulator.
+    // The MMAs of output half h: products (A plane, B plane) lo*hi, hi*lo, hi*hi; Re X on the B window at
+    // block 0 of the half, Im X on the window at block 1 (64 rows = 8 KiB further in every K atom); the first
+    // MMA starts the half's accumulator.
     auto issue_half = [&](int h) {
         uint32_t dlo = (uint32_t)desc0, tb = tbase;
         asm volatile("" : "+r"(dlo), "+r"(tb));
@@ -154,14 +144,15 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
 #pragma unroll
         for (int pr = 0; pr < 3; ++pr) {
             const int pa = pr == 0 ? 1 : 0, pb = pr == 1 ? 1 : 0;
-            const uint32_t are = tb + A0 + (uint32_t)(pa * D), aim = are + D / 2;
 #pragma unroll
-            for (int s = 0; s < D / 16; ++s) {
-                const uint32_t off = (uint32_t)(pb * PB + (s >> 2) * ATOM + 2 * H * h * 128 + (s & 3) * 32);
-                mma_ts_lohi<true>(tb + (uint32_t)(D * h), are + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
-                acc = 1;
-                mma_ts_lohi<true>(tb + (uint32_t)(D * h), aim + 8 * s, dlo + ((off + H * 128) >> 4), dhi, IDESC64, 1);
-                mma_ts_lohi<true>(tb + (uint32_t)(D * h + H), aim + 8 * s, dlo + (off >> 4), dhi, IDESC64N, 1);
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t acol = tb + A0 + (uint32_t)(pa * D + part * (D / 2));
+#pragma unroll
+                for (int s = 0; s < D / 16; ++s) {
+                    const uint32_t off = (uint32_t)(pb * PB + (s >> 2) * ATOM + (3 * H * h + H * part) * 128 + (s & 3) * 32);
+                    mma_ts_lohi<true>(tb + (uint32_t)(D * h), acol + 8 * s, dlo + (off >> 4), dhi, IDESC, acc);
+                    acc = 1;
+                }
             }
         }
     };
@@ -321,61 +312,6 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
         fence_after();
         return ok;
     };
-    // kRowsBulk: half h of tile t's accumulator through the stage. Warp 0 first waits until its bulk copies
-    // of the previous drain have read the stage, and says so (sfree); every warp writes its rows and columns
-    // (column-major, a column's 128 rows contiguous) and arrives (sdone); warp 0 then copies each run of
-    // 2^runlog contiguous rows of each column to the state, its lanes taking the runs in turn. With cv the
-    // warps then split the next tile's registers (the copies proceed meanwhile). False when a wait expired.
-    [[maybe_unused]] uint32_t ndrain = 0;
-    auto drain_bulk = [&](int h, uint64_t t, float2 (&X)[CPT], bool cv) -> bool {
-        const uint32_t par = ndrain & 1u;
-        ++ndrain;
-        if (warp == 0) {
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(sfree);
-        }
-        if (!wait(sfree, par)) return false;
-        const int r = quad * 32 + lane;
-#pragma unroll
-        for (int ch = 0; ch < CPH / 8; ++ch) {
-            uint32_t re[8], im[8];
-            const uint32_t c = (uint32_t)(D * h + CPH * w4 + 8 * ch);
-            tmem_ld<8>(tbase + tlane + c, im);
-            tmem_ld<8>(tbase + tlane + c + H, re);
-            wait_ld();
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                stage[(CPH * w4 + 8 * ch + j) * D + r] =
-                    make_float2(__uint_as_float(re[j]) * kOut, __uint_as_float(im[j]) * kOut);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stage, for the bulk copies
-        arrive(sdone);
-        if (cv) convert(X);
-        if (warp == 0) {
-            if (!wait(sdone, par)) return false;
-            const uint64_t tb = insert_zeros(t, a.spos, a.nS);
-            const int rl = a.runlog, runs = D >> rl;
-            const uint32_t bytes = 8u << rl;
-            for (int j = lane; j < H * runs; j += 32) {
-                const int cl = j >> (kRowBits - rl), k = j & (runs - 1);
-                const uint64_t g = tb + deposit((uint64_t)k << rl, a.rpos, kRowBits) + sCol[H * h + cl];
-                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                             :: "l"(psi + g), "r"(smem_u32(stage + cl * D + (k << rl))), "r"(bytes) : "memory");
-            }
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-        return true;
-    };
-    // the drain of either kind
-    auto drain = [&](int h, uint64_t t, float2 (&X)[CPT], bool cv) -> bool {
-        if constexpr (MODE == kRowsBulk) {
-            return drain_bulk(h, t, X, cv);
-        } else {
-            drain_half(h, t, X, cv);
-            return true;
-        }
-    };
 
     bool bad = false;
     if (warp == kWarps) {
@@ -418,17 +354,17 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
         // different warps overlap instead of every warp switching between them at once
         const bool early = (w4 & 1) != 0;
         if (early && i + 1 < m) load_tile(X, tile(i + 1));
-        if (i > 0 && !drain(1, tile(i - 1), X, false)) { bad = true; break; }
+        if (i > 0) drain_half(1, tile(i - 1), X, false);
         arrive(free1);
         if (!early && i + 1 < m) load_tile(X, tile(i + 1));  // in flight during the MMAs and the drain below
         if (!wait(done0, pc)) { bad = true; break; }
-        if (!drain(0, tile(i), X, i + 1 < m)) { bad = true; break; }  // converts tile i+1 (between its stores)
+        drain_half(0, tile(i), X, i + 1 < m);      // converts tile i+1 between its stores
     }
     if (!bad && m > 0) {
-        if (!wait(done1, (uint32_t)((m - 1) & 1)) || !drain(1, tile(m - 1), X, false)) bad = true;
+        if (wait(done1, (uint32_t)((m - 1) & 1))) drain_half(1, tile(m - 1), X, false);
+        else bad = true;
     }
     if (bad && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-    if (MODE == kRowsBulk && warp == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // all written
     }
     fence_before();
     __syncthreads();
@@ -438,15 +374,15 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     }
 }
 
-// B operand: row n = 128 h + 64 blk + i' holds, for output row i = 64 h + i' of U, Im U (blk 0) or Re U
-// (blk 1) against input index c, scaled by 2^14 and split into two FP16 planes (value, residual), in the
-// swizzled shared-memory byte layout.
+// B operand: row n = 192 h + 64 blk + i' holds, for output row i = 64 h + i' of U, Im U (blk 0), Re U (blk 1)
+// or -Im U (blk 2) against input index c, scaled by 2^14 and split into two FP16 planes (value, residual), in
+// the swizzled shared-memory byte layout.
 __global__ void k_tc7_prepare(const double* __restrict__ U, unsigned char* __restrict__ out) {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NB * D; idx += gridDim.x * blockDim.x) {
         const int n = idx / D, c = idx % D;
-        const int h = n / (2 * H), blk = (n % (2 * H)) / H, i = H * h + n % H;
+        const int h = n / (3 * H), blk = (n % (3 * H)) / H, i = H * h + n % H;
         const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
-        const double w = kScaleU * (blk == 0 ? ui : ur);
+        const double w = kScaleU * (blk == 0 ? ui : (blk == 1 ? ur : -ui));
         const __half hv = __float2half_rn((float)w);
         const uint32_t off = sw128_offset(n, c, NB, 2);
         *reinterpret_cast<__half*>(out + off) = hv;
@@ -486,7 +422,6 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
         if ((smask >> q) & 1) a.spos[a.nS++] = q;
     a.ntiles = 1ull << (n - a.nS);
     if (a.ntiles >> 32) return cudaErrorInvalidValue;  // 32-bit tile counters in the kernel
-    while (a.runlog < tc7::kRowBits && a.rpos[a.runlog] == a.runlog) ++a.runlog;
     if (from_basis) {
         a.from_basis = 1;
         a.basis = *from_basis;
@@ -512,7 +447,6 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
     if (a.tpos[0] == 0 && a.tpos[1] == 1 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
         return launch(tc7::k_tc7_block<tc7::kQuads>);
     if (a.tpos[0] == 0) return launch(tc7::k_tc7_block<tc7::kPairs>);
-    if (a.runlog >= 3) return launch(tc7::k_tc7_block<tc7::kRowsBulk>);  // runs of >= 64 bytes
     return launch(tc7::k_tc7_block<tc7::kRows>);
 }
 

@@ -31,8 +31,8 @@ def check(psi_gpu, ref, n):
 
 # target lists (in the order given, which fixes U's column bits) for each data path of the kernel
 TARGETS = {
-    "rows_high": (7, 8, 9, 10, 11, 12, 13),   # rows are qubits 0..6: bulk copies of whole 1 KiB columns
-    "rows_q3": (3, 4, 6, 8, 10, 12, 13),      # targets from qubit 3 up: bulk copies of 8-amplitude runs
+    "rows_high": (7, 8, 9, 10, 11, 12, 13),   # rows are qubits 0..6: whole 256-byte runs per warp access
+    "rows_q3": (3, 4, 6, 8, 10, 12, 13),      # targets from qubit 3 up (the planner's 7-qubit blocks)
     "rows_mixed": (2, 5, 8, 9, 11, 3, 13),    # unsorted, qubits 2 and 3 among them
     "rows_q1": (1, 4, 6, 8, 10, 12, 13),      # qubit 1 but not 0
     "rows_q0_later": (5, 0, 1, 7, 9, 11, 13), # qubit 0 a target but not the first: rows path
