@@ -314,7 +314,7 @@ def timed_steps(qsim, torch, st, plan, steps, shots, per_pass=True):
 
 def path_states_at(qsim, W, n_small, depth, paths):
     """Final complex64 states of every path on the n_small-qubit instance of the same generator (accuracy is
-    judged on this instance: the full-size state has no FP64 reference)."""
+    measured on this instance: the full-size state has no FP64 reference)."""
     c = W.brickwork(n_small, depth, seed=SEED)
     out = {}
     st = qsim.State(n_small, qsim.C64)
