@@ -111,7 +111,8 @@ typedef struct {
        executed (QSIM_EINVAL). */
     int32_t dry_run;
     /* Batches only (qsim_batch_plan_create): with a tensor-core precision, circuits of at least this many
-       qubits run as fused tensor-core plans (6-qubit blocks, every pass on the whole GPU) inside the same
+       qubits run as fused tensor-core plans (6-qubit blocks, or up to 7 with QSIM_PREC_FP16X3; every pass on
+       the whole GPU) inside the same
        enqueue, instead of on one cluster of the persistent launch (0 = 20; at least 13). Ignored for
        QSIM_PREC_SIMT. */
     int32_t batch_tc_min_n;

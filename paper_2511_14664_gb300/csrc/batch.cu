@@ -810,7 +810,8 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         const int prc = !ok ? QSIM_ENOMEM : parallel_for(nw, nth, device, [&](int w, int my_slot) -> int {
             qsim_run_opts po{};
             po.mode = QSIM_RUN_FUSED;
-            po.max_fused = 6;
+            // FP16X3: 7-qubit blocks where the planner finds them cheaper (nearest-neighbour chains)
+            po.max_fused = opts.precision == QSIM_PREC_FP16X3 ? 7 : 6;
             po.precision = opts.precision;
             po.tc_min_k = 5;
             const int r = qsim_plan_create(&cs[wides[w]], QSIM_C64, &po, pst[my_slot], &wph[w], &wpi[w]);

@@ -126,13 +126,15 @@ def test_full_size_batch_256_tfim_chains(qsim):
     check([res[i] for i in small], [cs[i] for i in small])
 
 
-def test_full_size_batch_tensor_core_circuits_against_oracle(qsim):
-    """The same batch in the benchmark's configuration (3xTF32 tensor-core plans for the circuits of >= 20
-    qubits, on worker streams, graph replay): four of those circuits -- the two cheapest of 20-21 qubits and
-    the two cheapest of 22-24 qubits -- and twelve persistent-launch circuits against the oracle."""
+@pytest.mark.parametrize("prec", [1, 4])
+def test_full_size_batch_tensor_core_circuits_against_oracle(qsim, prec):
+    """The same batch in the benchmark's configuration (tensor-core plans for the circuits of >= 20 qubits:
+    3xTF32 with 6-qubit blocks, or FP16X3 with up to 7; on worker streams, graph replay): four of those
+    circuits -- the two cheapest of 20-21 qubits and the two cheapest of 22-24 qubits -- and twelve
+    persistent-launch circuits against the oracle."""
     batch = W.tfim_batch(256, seed=4, nmax=24)
     cs = [c for c, _, _ in batch]
-    b = qsim.Batch(cs, max_fused=0, precision=1, tc_min_n=20)
+    b = qsim.Batch(cs, max_fused=0, precision=prec, tc_min_n=20)
     assert b.info["tc_blocks"] > 0
     b.execute(use_graph=True)
     b.execute(use_graph=True)
@@ -146,7 +148,7 @@ def test_full_size_batch_tensor_core_circuits_against_oracle(qsim):
     check([res[i] for i in pick], [cs[i] for i in pick])
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 3, 4])
 def test_wide_circuits_as_tensor_core_plans(qsim, prec):
     """With a tensor-core precision, circuits of at least tc_min_n qubits run as fused tensor-core plans
     (their <Z> reduced on the device into the batch's outputs); the rest stay in the persistent launch."""
@@ -172,12 +174,13 @@ def test_only_wide_circuits(qsim):
     check(b.results(), cs)
 
 
-def test_deep_wide_circuit_normalised(qsim):
-    """A 20-qubit chain with 32 Trotter steps (1248 gates) as a tensor-core plan inside a batch: its blocks'
-    FP32 accumulation moves the norm by ~1e-5; the batch reports the normalised state's values, which stay
-    within 1e-5 of the FP64 oracle."""
+@pytest.mark.parametrize("prec", [1, 4])
+def test_deep_wide_circuit_normalised(qsim, prec):
+    """A 20-qubit chain with 32 Trotter steps (1248 gates) as a tensor-core plan inside a batch (3xTF32, or
+    FP16X3 with 7-qubit blocks): its blocks' FP32 accumulation moves the norm by ~1e-5; the batch reports the
+    normalised state's values, which stay within 1e-5 of the FP64 oracle."""
     cs = tfim_mix([20, 12], [32, 3], seed=13)
-    b = qsim.Batch(cs, max_fused=4, precision=1, tc_min_n=20)
+    b = qsim.Batch(cs, max_fused=4, precision=prec, tc_min_n=20)
     assert b.info["tc_blocks"] > 20
     b.execute()
     check(b.results(), cs)
