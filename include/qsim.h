@@ -244,6 +244,15 @@ int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h plan, uint64_t x, int64_t
 /* Release a plan and its device buffers. Library service, no passage. NULL is accepted. */
 int qsim_plan_destroy(qsim_plan_h plan);
 
+/*
+ * Library service (no passage). Plans group gates into blocks by the circuit's structure alone (each gate's
+ * qubits, whether it is diagonal, the planning options), so groupings are cached process-wide by structure
+ * (at most 1024, thread-safe): circuits that repeat a structure -- a batch of chains of one width and depth,
+ * one circuit planned again with new angles -- are grouped once. Matrices are composed anew every time.
+ * This empties the cache (for timing cold planning, or to release its host memory).
+ */
+int qsim_plan_cache_clear(void);
+
 /* One pass of a plan, for per-kernel timing and roofline accounting. */
 #define QSIM_PASS_DENSE_SMALL 0 /* dense k <= 4 on CUDA cores (register gather or warp-shuffle butterfly) */
 #define QSIM_PASS_DIAG 1        /* diagonal factors, non-unit entries only */

@@ -12,7 +12,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "capi_state.h"
@@ -291,6 +294,50 @@ std::vector<std::vector<int>> group_gates_beam(const std::vector<uint64_t>& gmas
     }
 }
 
+// Groupings by gate structure. A grouping depends only on each gate's qubit set, whether it is diagonal and
+// whether it may join a phase pass, and on the planning options -- not on the matrices -- so circuits that
+// repeat a structure (a batch of chains of one width and depth, or one circuit planned again with new angles)
+// are grouped once. Keys are kept whole (no reliance on the hash alone); at 1024 entries the cache starts
+// over. qsim_plan_cache_clear empties it.
+namespace {
+struct GroupCache {
+    std::mutex mu;
+    std::unordered_map<uint64_t, std::vector<std::pair<std::vector<uint64_t>, std::vector<std::vector<int>>>>> map;
+    size_t entries = 0;
+};
+GroupCache& group_cache() {
+    static GroupCache c;
+    return c;
+}
+uint64_t fnv1a(const std::vector<uint64_t>& w) {
+    uint64_t h = 1469598103934665603ull;
+    for (uint64_t v : w)
+        for (int b = 0; b < 8; ++b) { h ^= (v >> (8 * b)) & 0xFF; h *= 1099511628211ull; }
+    return h;
+}
+}  // namespace
+
+static bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::vector<int>>& out) {
+    GroupCache& c = group_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.map.find(fnv1a(key));
+    if (it == c.map.end()) return false;
+    for (const auto& e : it->second)
+        if (e.first == key) { out = e.second; return true; }
+    return false;
+}
+
+static void group_cache_put(const std::vector<uint64_t>& key, const std::vector<std::vector<int>>& blocks) {
+    GroupCache& c = group_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.entries >= 1024) { c.map.clear(); c.entries = 0; }
+    auto& bucket = c.map[fnv1a(key)];
+    for (const auto& e : bucket)
+        if (e.first == key) return;
+    bucket.emplace_back(key, blocks);
+    ++c.entries;
+}
+
 static double op_bytes(const PlanOp& op, int n, size_t amp) {
     if (op.kind == OP_SWAP) return 2.0 * amp * std::ldexp(1.0, n) * (1.0 - std::ldexp(1.0, -op.nswap));
     if (op.kind == OP_PHASE) return 2.0 * amp * std::ldexp(1.0, n);
@@ -351,6 +398,14 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
 using namespace qsim;
 
 extern "C" {
+
+int qsim_plan_cache_clear(void) {
+    GroupCache& c = group_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.map.clear();
+    c.entries = 0;
+    return QSIM_OK;
+}
 
 int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts_in, void* stream_v,
                      qsim_plan_h* out, qsim_plan_info* info) {
@@ -464,12 +519,23 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        blocks = group_all(kmax, narrow);
-        // 7-qubit blocks pay on nearest-neighbour circuits (whole windows of adjacent qubits), not always
-        // (random target sets, the QFT's phase epilogues): the 6-qubit grouping is kept when it is cheaper
-        if (tc7) {
-            auto b6 = group_all(6, 0);
-            if (cost(b6) <= cost(blocks)) blocks.swap(b6);
+        std::vector<uint64_t> key = {(uint64_t)n, (uint64_t)kmax, narrow, (uint64_t)use_wide,
+                                     (uint64_t)opts.plan_effort, (uint64_t)(opts.precision != QSIM_PREC_SIMT),
+                                     (uint64_t)tc7, (uint64_t)G};
+        key.reserve(key.size() + 2 * (size_t)G);
+        for (int i = 0; i < G; ++i) {
+            key.push_back(gmask[i]);
+            key.push_back((uint64_t)gdiag[i] | ((uint64_t)gwide[i] << 1));
+        }
+        if (!group_cache_get(key, blocks)) {
+            blocks = group_all(kmax, narrow);
+            // 7-qubit blocks pay on nearest-neighbour circuits (whole windows of adjacent qubits), not always
+            // (random target sets, the QFT's phase epilogues): the 6-qubit grouping is kept when it is cheaper
+            if (tc7) {
+                auto b6 = group_all(6, 0);
+                if (cost(b6) <= cost(blocks)) blocks.swap(b6);
+            }
+            group_cache_put(key, blocks);
         }
     }
     // A diagonal block moves after a tensor-core block that follows it when they share no qubit (so they

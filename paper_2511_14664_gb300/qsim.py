@@ -102,6 +102,7 @@ SIGNATURES = {
     "qsim_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
     "qsim_plan_execute": ([_vp, _vp], _i),
     "qsim_plan_destroy": ([_vp], _i),
+    "qsim_plan_cache_clear": ([], _i),
     "qsim_plan_num_passes": ([_vp, _P(_i64)], _i),
     "qsim_plan_pass_info": ([_vp, _i64, _P(PassInfo)], _i),
     "qsim_plan_execute_from_basis": ([_vp, _vp, _u64, _i64], _i),
@@ -494,6 +495,11 @@ def spill_sample(host_state, n: int, dtype: int, window_qubits: int, seed: int, 
                                    seed & (2**64 - 1), int(shots), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                    ctypes.byref(nrm)))
     return out[:shots], nrm.value
+
+
+def plan_cache_clear():
+    """Empty the planner's cache of groupings by circuit structure (qsim_plan_cache_clear)."""
+    _check(lib().qsim_plan_cache_clear())
 
 
 def tc_peak(kind: str = "tf32", n_cols: int = 128, seconds: float = 1.0):

@@ -162,3 +162,22 @@ def test_full_size_k7_forward_inverse(qsim):
     assert abs(norm - 1.0) <= 1e-6 * 2 * info["tc_blocks"], (norm, info["tc_blocks"])
     p = st.probs([0, 1, 2, 3, 29])
     assert p[0] / norm >= 1.0 - 1e-6
+
+
+def test_structure_cache_reuses_grouping_with_new_matrices(qsim):
+    """Groupings are cached by circuit structure (qubits, diagonal or not), not by matrices: a second chain
+    with the same structure and other angles is grouped like the first (its plan comes from the cache) and
+    is still computed with its own matrices."""
+    n = 16
+    qsim.plan_cache_clear()
+    c1 = W.tfim_chain(n, 4, 0.3, 0.7)
+    c2 = W.tfim_chain(n, 4, 1.1, 0.2)
+    p1 = qsim.Plan(c1, qsim.C64, **K7)
+    p2 = qsim.Plan(c2, qsim.C64, **K7)
+    assert [(q["kind"], q["targets"], q["gates"]) for q in p1.passes()] == \
+           [(q["kind"], q["targets"], q["gates"]) for q in p2.passes()]
+    for p, c in ((p2, c2), (p1, c1)):
+        st = qsim.State(n, qsim.C64)
+        p.execute_from_basis(st, 0)
+        check(st.get_state(), oracle.run(c), n)
+    qsim.plan_cache_clear()
