@@ -608,7 +608,13 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         }
         if (!wide[ci]) {
             const int kmax = std::min(n, opts.max_fused ? opts.max_fused : batch::tuned_k(n));
-            cblk[ci] = group_gates(gmask, gdiag, n, kmax);
+            std::vector<uint64_t> key = {1 /* a batch circuit */, (uint64_t)n, (uint64_t)kmax, (uint64_t)c.num_gates};
+            key.reserve(key.size() + 2 * (size_t)c.num_gates);
+            for (int i = 0; i < c.num_gates; ++i) { key.push_back(gmask[i]); key.push_back((uint64_t)gdiag[i]); }
+            if (!group_cache_get(key, cblk[ci])) {
+                cblk[ci] = group_gates(gmask, gdiag, n, kmax);
+                group_cache_put(key, cblk[ci]);
+            }
         }
         return QSIM_OK;
     });

@@ -48,6 +48,10 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
                                           int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1,
                                           int lookahead = 0, uint64_t narrow = 0);
+// Groupings cached by structure (plan.cu): key words describe the request (options, each gate's qubit mask and
+// flags); the first word tells the requester apart (0 plans, 1 batch circuits).
+bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::vector<int>>& out);
+void group_cache_put(const std::vector<uint64_t>& key, const std::vector<std::vector<int>>& blocks);
 
 }  // namespace qsim
 

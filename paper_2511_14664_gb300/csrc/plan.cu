@@ -317,7 +317,7 @@ uint64_t fnv1a(const std::vector<uint64_t>& w) {
 }
 }  // namespace
 
-static bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::vector<int>>& out) {
+bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::vector<int>>& out) {
     GroupCache& c = group_cache();
     std::lock_guard<std::mutex> lk(c.mu);
     auto it = c.map.find(fnv1a(key));
@@ -327,7 +327,7 @@ static bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::v
     return false;
 }
 
-static void group_cache_put(const std::vector<uint64_t>& key, const std::vector<std::vector<int>>& blocks) {
+void group_cache_put(const std::vector<uint64_t>& key, const std::vector<std::vector<int>>& blocks) {
     GroupCache& c = group_cache();
     std::lock_guard<std::mutex> lk(c.mu);
     if (c.entries >= 1024) { c.map.clear(); c.entries = 0; }
@@ -519,7 +519,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     if (opts.mode == QSIM_RUN_PLAIN) {
         for (int i = 0; i < G; ++i) blocks.push_back({i});
     } else {
-        std::vector<uint64_t> key = {(uint64_t)n, (uint64_t)kmax, narrow, (uint64_t)use_wide,
+        std::vector<uint64_t> key = {0 /* a plan */, (uint64_t)n, (uint64_t)kmax, narrow, (uint64_t)use_wide,
                                      (uint64_t)opts.plan_effort, (uint64_t)(opts.precision != QSIM_PREC_SIMT),
                                      (uint64_t)tc7, (uint64_t)G};
         key.reserve(key.size() + 2 * (size_t)G);
