@@ -327,37 +327,47 @@ _GATE_NP = np.dtype({"names": ["k", "nc", "targets", "controls", "matrix"],
 
 def _pack_gates(gs):
     """Gate records in the qsim_gate layout for the list `gs`, plus the matrix arrays they point into (one
-    per gate width, so that all gates of a width are copied with one array operation)."""
+    per gate width, so that all gates of a width are copied with one array operation). Three passes over
+    the gate objects to collect their fields; the rest is array work."""
     G = len(gs)
     rec = np.zeros(max(1, G), dtype=_GATE_NP)
     pools = []
     if G:
-        ks = np.fromiter((len(g.targets) for g in gs), dtype=np.int32, count=G)
-        ncs = np.fromiter((len(g.controls) for g in gs), dtype=np.int32, count=G)
+        tg = [g.targets for g in gs]
+        ct = [g.controls for g in gs]
+        mt = [g.matrix for g in gs]
+        ks = np.fromiter(map(len, tg), dtype=np.int32, count=G)
+        ncs = np.fromiter(map(len, ct), dtype=np.int32, count=G)
         if int(ks.max()) > MAX_TARGETS or int(ncs.max()) > MAX_CONTROLS:
             raise ValueError("a gate has more than %d targets or controls" % MAX_TARGETS)
         rec["k"][:G] = ks
         rec["nc"][:G] = ncs
+        ids = np.fromiter(map(id, mt), dtype=np.int64, count=G)
+
+        def fill(field, lists, lens):
+            # all lists chained into one array, then each gate's entries gathered by its offset
+            flat = np.fromiter(chain.from_iterable(lists), dtype=np.int32, count=int(lens.sum()))
+            off = np.zeros(G, dtype=np.int64)
+            np.cumsum(lens[:-1], out=off[1:])
+            for k in np.unique(lens):
+                k = int(k)
+                if k:
+                    idx = np.nonzero(lens == k)[0]
+                    rec[field][idx, :k] = flat[off[idx][:, None] + np.arange(k)]
+
+        fill("targets", tg, ks)
+        if int(ncs.max()):
+            fill("controls", ct, ncs)
         for k in np.unique(ks):  # gates of one width share an array of matrices
             idx = np.nonzero(ks == k)[0]
             k = int(k)
-            sub = [gs[i] for i in idx]
-            rec["targets"][idx, :k] = np.fromiter(chain.from_iterable(g.targets for g in sub), dtype=np.int32,
-                                                  count=len(idx) * k).reshape(len(idx), k)
             # one copy per distinct matrix object (circuits often reuse one array for many gates)
-            ids = np.fromiter((id(g.matrix) for g in sub), dtype=np.int64, count=len(sub))
-            uniq, first, inv = np.unique(ids, return_index=True, return_inverse=True)
-            M = np.ascontiguousarray(np.array([sub[j].matrix for j in first], dtype=np.complex128))
+            uniq, first, inv = np.unique(ids[idx], return_index=True, return_inverse=True)
+            M = np.ascontiguousarray(np.array([mt[idx[j]] for j in first], dtype=np.complex128))
             if M.shape[1:] != (1 << k, 1 << k):
                 raise ValueError("a %d-qubit gate needs a %dx%d matrix" % (k, 1 << k, 1 << k))
             pools.append(M)
             rec["matrix"][idx] = M.ctypes.data + inv.astype(np.uint64).ravel() * np.uint64(M[0].nbytes)
-        for c in np.unique(ncs):
-            if c:
-                idx = np.nonzero(ncs == c)[0]
-                c = int(c)
-                rec["controls"][idx, :c] = np.fromiter(chain.from_iterable(gs[i].controls for i in idx),
-                                                       dtype=np.int32, count=len(idx) * c).reshape(len(idx), c)
     return rec, pools
 
 
