@@ -170,10 +170,14 @@ KERNEL_SOURCES = {"dense_small": ["k_gates.cu"], "diag": ["k_gates.cu"], "dense_
 
 
 def source_sha(kind):
-    """Hash of the sources a kernel kind is built from (a profile's counters apply only while it holds)."""
+    """Hash of the code a kernel kind is built from, comments and layout removed (a profile's counters apply
+    only while the code is unchanged)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kind]:
-        h.update(open(os.path.join(ROOT, "paper_2511_14664_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2511_14664_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -14,8 +14,9 @@
 // (U_h = rows 64h.. of U; 384 rows, 192 KiB as two planes), so that Re X multiplies the 128-row window
 // starting at block 0 of its half and Im X the window starting at block 1, each an N = 128 MMA:
 //     Im Y_h = Re X (Im U_h)^T + Im X (Re U_h)^T,   Re Y_h = Re X (Re U_h)^T + Im X (-Im U_h)^T.
-// Scaling and split as in the 6-qubit FP16X3 block: amplitudes x 2^15, U x 2^14, each split into its FP16
-// rounding and the FP16 rounding of the residual, products lo*hi + hi*lo + hi*hi, output x 2^-29.
+// Scaling and split as in the 6-qubit FP16X3 block: amplitudes x 2^15, U x 2^14, each split into two FP16
+// parts (here the leading 11 significant bits by Dekker's split, and the FP16 rounding of the remainder),
+// products lo*hi + hi*lo + hi*hi, output x 2^-29.
 //
 // Tensor memory (512 columns, the whole of it): accumulator h at [128h, 128h + 128), A planes in [256, 512):
 // plane p (0 hi, 1 lo), part (0 Re, 1 Im) at 256 + 128 p + 64 part, two FP16 values per column (even K in
@@ -24,7 +25,8 @@
 // while a tile's A planes are written. Sequence of tile i (data warps, and the MMA issuer):
 //   wait done1(i-1); write A(i); arrive full        issuer: wait full, MMAs of half 0, commit done0
 //   drain half 1 of tile i-1; arrive free1          issuer: wait free1, MMAs of half 1, commit done1
-//   load tile i+1 into registers; wait done0(i); drain half 0 of tile i, splitting tile i+1 into its packed
+//   load tile i+1 into registers (odd column groups before the half-1 drain, so that loads and stores of
+//   different warps overlap); wait done0(i); drain half 0 of tile i, splitting tile i+1 into its packed
 //   FP16 planes (in the registers it was loaded into) between the stores
 // The loads and stores issue at the rate this SM's share of the HBM bandwidth drains them, so the data
 // warps spend most of a tile in them; the MMAs of both halves run back to back while the warps drain half 1
