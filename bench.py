@@ -715,6 +715,7 @@ def run_brick14(args):
     ts = []
     for i in range(max(3, args.warmup) + max(10, args.steps)):
         torch.cuda.synchronize()
+        qsim.plan_cache_clear()  # cold planning in every timed run
         t = time.perf_counter()
         st.set_basis(0)
         st.run(c, **kw)
