@@ -536,11 +536,13 @@ def test_local_qubits_reorder_plan(qsim, mode, k, local):
     close(st.get_state(), oracle.run(c), n, 0)
 
 
-def test_local_qubits_with_tensor_cores(qsim):
+@pytest.mark.parametrize("prec,k", [(1, 6), (4, 6), (4, 7)])
+def test_local_qubits_with_tensor_cores(qsim, prec, k):
+    """Global-qubit plans (reorder passes) with 3xTF32 or FP16X3 blocks (width 7 stays 6 with global qubits)."""
     n = 17
     c = W.brickwork(n, 8, seed=6)
     st = make_state(qsim, n, 0)
-    info = st.run(c, mode=1, max_fused=6, precision=1, tc_min_k=5, local_qubits=14)
+    info = st.run(c, mode=1, max_fused=k, precision=prec, tc_min_k=5, local_qubits=14)
     assert info["reorders"] > 0 and info["tc_blocks"] > 0
     close(st.get_state(), oracle.run(c), n, 0)
 
