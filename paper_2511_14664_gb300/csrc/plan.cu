@@ -1116,7 +1116,8 @@ int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h p, uint64_t x, int64_t co
     const int64_t nops = (int64_t)p->ops.size();
     if (count < 0) count = nops;
     if (count > nops) { set_error("pass range out of bounds"); return QSIM_EINVAL; }
-    // a first tensor-core block (3xTF32 / BF16x3) generates |x> as its input and writes every amplitude
+    // a first tensor-core block (any precision but BF16x6; block pairs and 7-qubit blocks too) generates |x>
+    // as its input and writes every amplitude
     if (count > 0 && ((p->ops[0].kind == OP_TC && p->ops[0].precision != QSIM_PREC_BF16X6) || p->ops[0].kind == OP_TC_PAIR))
         return enqueue_ops(h, p, 0, (size_t)count, &x);
     const int rc = qsim_set_basis(h, x);

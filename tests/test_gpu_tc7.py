@@ -181,3 +181,23 @@ def test_structure_cache_reuses_grouping_with_new_matrices(qsim):
         p.execute_from_basis(st, 0)
         check(st.get_state(), oracle.run(c), n)
     qsim.plan_cache_clear()
+
+
+@pytest.mark.parametrize("kw", [K7, dict(mode=0, max_fused=1), dict(mode=1, max_fused=4)])
+def test_empty_circuit_plans(qsim, kw):
+    """A circuit without gates plans to no passes: run from a basis state it leaves |x>, run on a state it
+    leaves the state as it was."""
+    n = 15
+    c = W.Circuit(n)
+    p = qsim.Plan(c, qsim.C64, **kw)
+    assert p.passes() == []
+    st = qsim.State(n, qsim.C64)
+    p.execute_from_basis(st, 12345)
+    psi = st.get_state()
+    want = np.zeros(1 << n, dtype=np.complex128)
+    want[12345] = 1.0
+    assert np.array_equal(psi.astype(np.complex128), want)
+    psi0 = random_state(n, 4)
+    st.set_state(psi0)
+    p.execute(st)
+    assert np.array_equal(st.get_state(), psi0.astype(np.complex64))
