@@ -76,7 +76,7 @@ cudaError_t launch_phase(int dtype, void* psi, int n, const void* dtab, const Ph
 struct TcEpiPacked {
     uint64_t c = 0;
     int ntt = 0;
-    int off[15] = {};  // tile-term lists per bit group (13 groups for 5- and 6-qubit blocks, 14 for 7)
+    int off[14] = {};
     size_t off_rowphase = 0, off_tt_ab = 0, off_tt_l = 0, off_tb_t = 0, off_tb_l = 0, off_thr = 0;
 };
 // Tables of a phase epilogue for a k-qubit block on `targets` (the order launch_tc_apply gets) in an n-qubit
@@ -109,16 +109,9 @@ bool tc_supported(int k, int precision);
 // ---- 7-qubit blocks (k_tc7.cu, FP16 split products; reached through the tensor-core entry points above
 // with k = 7 and QSIM_PREC_FP16X3) ----------------------------------------------------------------------------
 size_t tc7_operand_bytes();
-// rowphase (device, 128 radians, may be NULL): row i of U multiplied by exp(i rowphase[i]) first
-cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s, const double* rowphase = nullptr);
-// epi_tab / epi / epi_scratch: a phase epilogue packed by tc7_epi_pack (all NULL: none)
+cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s);
 cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* dB, unsigned* dev_err, cudaStream_t s,
-                             const DevInfo& d, const uint64_t* from_basis, const void* epi_tab = nullptr,
-                             const TcEpiPacked* epi = nullptr, void* epi_scratch = nullptr);
-// The phase epilogue of a 7-qubit block: the same tables as tc_epi_pack, with the bit groups of the 7-qubit
-// kernel (row bits 0..6, column bits 0..6)
-void tc7_epi_pack(int n, const int* targets, const PhaseForm& f, std::vector<unsigned char>& out, TcEpiPacked& pk);
-size_t tc7_epi_scratch_bytes(int n);
+                             const DevInfo& d, const uint64_t* from_basis);
 
 // ---- two 6-qubit blocks in one pass (k_tc_pair.cu, FP16 split products) -------------------------------------
 // True when blocks on t1 and then t2 (6 targets each, in their matrices' index order) fit one 13-bit tile of

@@ -1000,7 +1000,7 @@ cudaError_t launch_tc_prepare(const double* dU, int k, int precision, bool lines
                               const double* rowphase) {
     if (!tc_supported(k, precision)) return cudaErrorInvalidValue;
     if (lines && (precision != QSIM_PREC_TF32X3 || rowphase)) return cudaErrorInvalidValue;
-    if (k == 7) return lines ? cudaErrorInvalidValue : launch_tc7_prepare(dU, dB, s, rowphase);
+    if (k == 7) return rowphase || lines ? cudaErrorInvalidValue : launch_tc7_prepare(dU, dB, s);
     unsigned char* out = static_cast<unsigned char*>(dB);
     const int blocks = ((2 << k) * (2 << k) + 255) / 256;
     const int perm = lines ? 1 : 0;
@@ -1044,9 +1044,9 @@ cudaError_t launch_tc_apply(void* psi, int n, int k, const int* targets, const v
     if (lines && !tc_line_groups(k, targets, precision, epi != nullptr)) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(dB) & 15) != 0) return cudaErrorInvalidValue;
     if (epi && (!epi_tab || !epi_scratch || precision == QSIM_PREC_BF16X6)) return cudaErrorInvalidValue;
-    if (k == 7) {  // FP16X3 only; no line groups
-        if (lines) return cudaErrorInvalidValue;
-        return launch_tc7_apply(psi, n, targets, dB, dev_err, s, d, from_basis, epi_tab, epi, epi_scratch);
+    if (k == 7) {  // FP16X3 only; no phase epilogue, no line groups
+        if (epi || lines) return cudaErrorInvalidValue;
+        return launch_tc7_apply(psi, n, targets, dB, dev_err, s, d, from_basis);
     }
     tc::Args a;
     std::memset(&a, 0, sizeof(a));

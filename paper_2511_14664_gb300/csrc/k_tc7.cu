@@ -44,9 +44,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
-#include <cmath>
 #include <cstring>
-#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -74,11 +72,8 @@ constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(D >> 3) << 17) | ((uint32_t)(
 constexpr float kScaleX = 32768.0f;     // 2^15
 constexpr double kScaleU = 16384.0;     // 2^14
 constexpr float kOut = 1.0f / (32768.0f * 16384.0f);
-constexpr int kEpiGroups = 2 * K;       // phase epilogue: row bits 0..6, column bits 0..6
-constexpr int kEpiTile = 1 + kEpiGroups;  // factors per tile
 constexpr int kBars = 5;                // full, free1, done0, done1, B loaded
-constexpr int kThrBytes = D * 8 * 8;    // the epilogue's per-row table in shared memory
-constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 64 + kThrBytes + 1024;
+constexpr size_t kSmem = 2 * (size_t)PB + sizeof(uint64_t) * D + 8 * kBars + 8 + 1024;
 
 enum Mode { kRows = 0, kPairs = 1, kQuads = 2 };
 
@@ -90,15 +85,9 @@ struct Args {
     uint64_t ntiles;
     int from_basis;      // the input is |basis>, generated in registers instead of read
     uint64_t basis;
-    // Phase epilogue (EPI): every output amplitude x is multiplied by exp(i phi(x)), phi a quadratic form of its
-    // index bits (the run of diagonal gates that followed the block). Terms on column bits alone are in U;
-    // epi_tiles[tile][15]: the tile-only factor, then the cross-term factor of each row bit and of each column
-    // bit given the tile; epi_thr[row][8]: the row-only factor, then each column bit's factor given the row.
-    const float2* epi_tiles;
-    const float2* epi_thr;
 };
 
-template <int MODE, bool EPI>
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint4* __restrict__ bops,
             unsigned* __restrict__ err) {
@@ -107,15 +96,9 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
     uint64_t* sCol = reinterpret_cast<uint64_t*>(sb + 2 * PB);
     uint64_t* mbar = sCol + D;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + kBars);
-    static_assert(8 * kBars + 8 <= 64, "barriers and the TMEM slot in 64 bytes");
-    // EPI: the per-row table, transposed (sTh[slot * 128 + row]) so that a warp reads 32 consecutive entries
-    [[maybe_unused]] float2* sTh = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(sCol + D) + 64);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int c = tid; c < D; c += kThreads) sCol[c] = deposit((uint64_t)c, a.tpos, K);
-    if constexpr (EPI) {  // plan data, written before the kernels that precede this one
-        for (int i = tid; i < D * 8; i += kThreads) sTh[(i % 8) * D + i / 8] = a.epi_thr[i];
-    }
     if (tid == 0) {
         const int count[kBars] = {kWarps, kWarps, 1, 1, 1};
         for (int j = 0; j < kBars; ++j)
@@ -292,34 +275,6 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
                 v[2 * j] = __float_as_uint(__uint_as_float(re[j]) * kOut);
                 v[2 * j + 1] = __float_as_uint(__uint_as_float(im[j]) * kOut);
             }
-            if constexpr (EPI) {
-                // the chunk's columns 64 h + 16 w4 + 8 ch + jj: column bits 0..2 = jj, 3 = ch, 4..5 = w4, 6 = h
-                const float2* tf = a.epi_tiles + t * kEpiTile;
-                const int r = quad * 32 + lane;
-                auto colf = [&](int b) { return cmul(tf[1 + kRowBits + b], sTh[(1 + b) * D + r]); };
-                float2 e = cmul(tf[0], sTh[r]);
-#pragma unroll
-                for (int j = 0; j < kRowBits; ++j)
-                    if ((r >> j) & 1) e = cmul(e, tf[1 + j]);
-                if (w4 & 1) e = cmul(e, colf(4));
-                if (w4 & 2) e = cmul(e, colf(5));
-                if (h) e = cmul(e, colf(6));
-                if (ch) e = cmul(e, colf(3));
-                float2 fac[8];
-                fac[0] = e;
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float2 fb = colf(b);
-#pragma unroll
-                    for (int q = 0; q < (1 << b); ++q) fac[(1 << b) + q] = cmul(fac[q], fb);
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 y = cmul(make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])), fac[j]);
-                    v[2 * j] = __float_as_uint(y.x);
-                    v[2 * j + 1] = __float_as_uint(y.y);
-                }
-            }
             const int x0 = CPH * h + 8 * ch;
             if constexpr (MODE == kQuads) {
 #pragma unroll
@@ -424,21 +379,11 @@ k_tc7_block(float2* __restrict__ psi, const __grid_constant__ Args a, const uint
 // B operand: row n = 192 h + 64 blk + i' holds, for output row i = 64 h + i' of U, Im U (blk 0), Re U (blk 1)
 // or -Im U (blk 2) against input index c, scaled by 2^14 and split into two FP16 planes (value, residual), in
 // the swizzled shared-memory byte layout.
-// With rowphase (device, 128 radians) row i of U is multiplied by exp(i rowphase[i]) first: the phase
-// epilogue's terms on target bits alone.
-__global__ void k_tc7_prepare(const double* __restrict__ U, const double* __restrict__ rowphase,
-                              unsigned char* __restrict__ out) {
+__global__ void k_tc7_prepare(const double* __restrict__ U, unsigned char* __restrict__ out) {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < NB * D; idx += gridDim.x * blockDim.x) {
         const int n = idx / D, c = idx % D;
         const int h = n / (3 * H), blk = (n % (3 * H)) / H, i = H * h + n % H;
-        double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
-        if (rowphase) {
-            double sp, cp;
-            sincos(rowphase[i], &sp, &cp);
-            const double r2 = ur * cp - ui * sp;
-            ui = ur * sp + ui * cp;
-            ur = r2;
-        }
+        const double ur = U[2 * (i * D + c)], ui = U[2 * (i * D + c) + 1];
         const double w = kScaleU * (blk == 0 ? ui : (blk == 1 ? ur : -ui));
         const __half hv = __float2half_rn((float)w);
         const uint32_t off = sw128_offset(n, c, NB, 2);
@@ -447,123 +392,18 @@ __global__ void k_tc7_prepare(const double* __restrict__ U, const double* __rest
     }
 }
 
-// The phase epilogue's per-tile factors (one thread per tile): exp(i * terms on tile bits alone) and, for
-// each row bit and each column bit, exp(i * its cross terms with the tile's bits).
-__global__ void k_tc7_epi_tiles(uint64_t ntiles, Args a, TcEpiPacked pk, const unsigned char* __restrict__ tab,
-                                float2* __restrict__ out) {
-    const uint32_t* tt_ab = reinterpret_cast<const uint32_t*>(tab + pk.off_tt_ab);
-    const uint64_t* tt_l = reinterpret_cast<const uint64_t*>(tab + pk.off_tt_l);
-    const uint32_t* tb_t = reinterpret_cast<const uint32_t*>(tab + pk.off_tb_t);
-    const uint64_t* tb_l = reinterpret_cast<const uint64_t*>(tab + pk.off_tb_l);
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t tb = insert_zeros(t, a.spos, a.nS);
-        uint64_t s = pk.c;
-        for (int i = 0; i < pk.ntt; ++i)
-            if ((tb >> (tt_ab[i] & 0xFF)) & (tb >> (tt_ab[i] >> 8)) & 1) s += tt_l[i];
-        float2* o = out + t * kEpiTile;
-        o[0] = unit_phase(0.0f, s);
-        for (int g = 0; g < kEpiGroups; ++g) {
-            uint64_t k = 0;
-            for (int i = pk.off[g]; i < pk.off[g + 1]; ++i)
-                if ((tb >> tb_t[i]) & 1) k += tb_l[i];
-            o[1 + g] = unit_phase(0.0f, k);
-        }
-    }
-}
-
 }  // namespace tc7
 
 size_t tc7_operand_bytes() { return 2 * (size_t)tc7::PB; }
 
-size_t tc7_epi_scratch_bytes(int n) { return sizeof(float2) * tc7::kEpiTile * ((size_t)1 << (n - tc7::K - tc7::kRowBits)); }
-
-// Bit groups of the 7-qubit kernel: row bit j -> j, column bit v -> 7 + v, tile bits -> -1. Terms on column
-// bits alone (and the constant) become row phases of U; terms on row bits alone and the coefficient of each
-// column bit given the row bits form a table per row ([128][8]: slot 0, then 1 + v); terms with tile bits are
-// listed per group for k_tc7_epi_tiles.
-void tc7_epi_pack(int n, const int* targets, const PhaseForm& f, std::vector<unsigned char>& out, TcEpiPacked& pk) {
-    using tc7::D;
-    using tc7::K;
-    using tc7::kRowBits;
-    std::vector<int> grp(n, -1);
-    uint64_t tmask = 0;
-    for (int j = 0; j < K; ++j) tmask |= 1ull << targets[j];
-    int nr = 0;
-    for (int q = 0; q < n && nr < kRowBits; ++q)
-        if (!((tmask >> q) & 1)) grp[q] = nr++;
-    for (int v = 0; v < K; ++v) grp[targets[v]] = kRowBits + v;
-    std::vector<double> rowphase(D, f.c);
-    std::vector<uint32_t> tt_ab;
-    std::vector<uint64_t> tt_l;
-    std::vector<std::vector<std::pair<uint32_t, uint64_t>>> tb(tc7::kEpiGroups);
-    std::vector<double> thr((size_t)D * 8, 0.0);  // radians
-    auto row_add = [&](int slot, double L, int g1, int g2) {  // row groups g1, g2 (< 0: no condition)
-        for (int r = 0; r < D; ++r)
-            if ((g1 < 0 || ((r >> g1) & 1)) && (g2 < 0 || ((r >> g2) & 1))) thr[(size_t)r * 8 + slot] += L;
-    };
-    auto col_add = [&](double L, int c1, int c2) {  // column bits c1, c2 (c2 < 0: a single bit)
-        for (int m = 0; m < D; ++m)
-            if (((m >> c1) & 1) && (c2 < 0 || ((m >> c2) & 1))) rowphase[m] += L;
-    };
-    for (int a = 0; a < n; ++a) {
-        if (f.h[a] == 0.0) continue;
-        const int g = grp[a];
-        if (g < 0) { tt_ab.push_back((uint32_t)a | ((uint32_t)a << 8)); tt_l.push_back(phase_turns(f.h[a])); }
-        else if (g < kRowBits) row_add(0, f.h[a], g, -1);
-        else col_add(f.h[a], g - kRowBits, -1);
-    }
-    for (const auto& p : f.pairs) {
-        const int ga = grp[p.a], gb = grp[p.b];
-        if (ga < 0 && gb < 0) { tt_ab.push_back((uint32_t)p.a | ((uint32_t)p.b << 8)); tt_l.push_back(phase_turns(p.lam)); }
-        else if (ga < 0) tb[gb].push_back({(uint32_t)p.a, phase_turns(p.lam)});
-        else if (gb < 0) tb[ga].push_back({(uint32_t)p.b, phase_turns(p.lam)});
-        else if (ga >= kRowBits && gb >= kRowBits) col_add(p.lam, ga - kRowBits, gb - kRowBits);  // two columns
-        else if (ga < kRowBits && gb < kRowBits) row_add(0, p.lam, ga, gb);                       // two rows
-        else {  // a row bit and a column bit: that column bit's coefficient, given the row
-            const int gr = ga < kRowBits ? ga : gb, gc = ga < kRowBits ? gb : ga;
-            row_add(1 + gc - kRowBits, p.lam, gr, -1);
-        }
-    }
-    std::vector<uint32_t> tb_t;
-    std::vector<uint64_t> tb_l;
-    pk = TcEpiPacked();
-    pk.off[0] = 0;
-    for (int g = 0; g < tc7::kEpiGroups; ++g) {
-        for (const auto& t : tb[g]) { tb_t.push_back(t.first); tb_l.push_back(t.second); }
-        pk.off[g + 1] = (int)tb_t.size();
-    }
-    pk.c = 0;  // the constant went into U with the column-only terms
-    pk.ntt = (int)tt_ab.size();
-    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
-    size_t off = 0;
-    pk.off_rowphase = off; off = al(off + 8 * rowphase.size());
-    pk.off_tt_ab = off; off = al(off + 4 * tt_ab.size());
-    pk.off_tt_l = off;  off = al(off + 8 * tt_l.size());
-    pk.off_tb_t = off;  off = al(off + 4 * tb_t.size());
-    pk.off_tb_l = off;  off = al(off + 8 * tb_l.size());
-    pk.off_thr = off;   off = al(off + 8 * thr.size());
-    out.assign(off, 0);
-    auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(out.data() + o, src, bytes); };
-    put(pk.off_rowphase, rowphase.data(), 8 * rowphase.size());
-    put(pk.off_tt_ab, tt_ab.data(), 4 * tt_ab.size());
-    put(pk.off_tt_l, tt_l.data(), 8 * tt_l.size());
-    put(pk.off_tb_t, tb_t.data(), 4 * tb_t.size());
-    put(pk.off_tb_l, tb_l.data(), 8 * tb_l.size());
-    for (size_t i = 0; i < thr.size(); ++i) {
-        const float v2[2] = {(float)std::cos(thr[i]), (float)std::sin(thr[i])};
-        put(pk.off_thr + 8 * i, v2, 8);
-    }
-}
-
-cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s, const double* rowphase) {
+cudaError_t launch_tc7_prepare(const double* dU, void* dB, cudaStream_t s) {
     const int blocks = (tc7::NB * tc7::D + 255) / 256;
-    tc7::k_tc7_prepare<<<blocks, 256, 0, s>>>(dU, rowphase, static_cast<unsigned char*>(dB));
+    tc7::k_tc7_prepare<<<blocks, 256, 0, s>>>(dU, static_cast<unsigned char*>(dB));
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* dB, unsigned* dev_err, cudaStream_t s,
-                             const DevInfo& d, const uint64_t* from_basis, const void* epi_tab, const TcEpiPacked* epi,
-                             void* epi_scratch) {
+                             const DevInfo& d, const uint64_t* from_basis) {
     if (n < tc7::K + tc7::kRowBits || n > 63 || (reinterpret_cast<uintptr_t>(dB) & 15) != 0 ||
         (reinterpret_cast<uintptr_t>(psi) & 15) != 0)
         return cudaErrorInvalidValue;
@@ -588,18 +428,6 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
         a.from_basis = 1;
         a.basis = *from_basis;
     }
-    if (epi) {
-        if (!epi_tab || !epi_scratch) return cudaErrorInvalidValue;
-        // the tile factors go to the scratch (tc7_epi_scratch_bytes), read by the block kernel that follows
-        const unsigned char* b = static_cast<const unsigned char*>(epi_tab);
-        float2* tiles = static_cast<float2*>(epi_scratch);
-        const unsigned g = grid_for((int64_t)a.ntiles, 256, d.num_sms, 4);
-        tc7::k_tc7_epi_tiles<<<g, 256, 0, s>>>(a.ntiles, a, *epi, b, tiles);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        a.epi_tiles = tiles;
-        a.epi_thr = reinterpret_cast<const float2*>(b + epi->off_thr);
-    }
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
     auto launch = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc7::kSmem);
@@ -619,10 +447,9 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
                                   dev_err);
     };
     if (a.tpos[0] == 0 && a.tpos[1] == 1 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
-        return epi ? launch(tc7::k_tc7_block<tc7::kQuads, true>) : launch(tc7::k_tc7_block<tc7::kQuads, false>);
-    if (a.tpos[0] == 0)
-        return epi ? launch(tc7::k_tc7_block<tc7::kPairs, true>) : launch(tc7::k_tc7_block<tc7::kPairs, false>);
-    return epi ? launch(tc7::k_tc7_block<tc7::kRows, true>) : launch(tc7::k_tc7_block<tc7::kRows, false>);
+        return launch(tc7::k_tc7_block<tc7::kQuads>);
+    if (a.tpos[0] == 0) return launch(tc7::k_tc7_block<tc7::kPairs>);
+    return launch(tc7::k_tc7_block<tc7::kRows>);
 }
 
 }  // namespace qsim

@@ -483,7 +483,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     // Estimated cost of a grouping in passes: a 7-qubit tensor-core block streams the state like any pass
     // but takes about 1.2 times as long (3.1-3.2 against 2.6 ms at 30 qubits); a phase pass counts 1, or 0.15
     // when it follows a dense block of at most 6 qubits (it becomes that block's epilogue, which only a
-    // tensor-core precision has; with 7-qubit blocks, blocks of 7 too).
+    // tensor-core precision has).
     auto cost = [&](const std::vector<std::vector<int>>& bl) {
         double cs = 0.0;
         bool prev_dense6 = false;
@@ -494,7 +494,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             const int k = popcnt(Q);
             if (wide && k > 6) cs += (prev_dense6 && opts.precision != QSIM_PREC_SIMT) ? 0.15 : 1.0;
             else cs += (tc7 && k == 7 && !wide) ? 1.2 : 1.0;
-            prev_dense6 = !diag && k <= (tc7 ? 7 : 6);
+            prev_dense6 = !diag && k <= 6;
         }
         return cs;
     };
@@ -551,7 +551,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             const int kb = popcnt(qubits(blk));
             bool diag = true;
             for (int gi : blk) diag = diag && gdiag[gi];
-            return !diag && kb >= tc_min && kb <= (tc7 ? 7 : 6) && tc_supported(kb, opts.precision) && n >= kb + 7 &&
+            return !diag && kb >= tc_min && kb <= 6 && tc_supported(kb, opts.precision) && n >= kb + 7 &&
                    !(blk.size() == 1 && c->gates[blk[0]].nc > 0);
         };
         for (bool changed = true; changed;) {
@@ -729,7 +729,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         PlanOp& op = p->ops[oi];
         if (op.kind != OP_PHASE) continue;
         PlanOp* prev = oi > 0 ? &p->ops[oi - 1] : nullptr;
-        if (prev && prev->kind == OP_TC && !prev->has_epi && prev->precision != QSIM_PREC_BF16X6) {
+        if (prev && prev->kind == OP_TC && prev->k <= 6 && !prev->has_epi && prev->precision != QSIM_PREC_BF16X6) {
             prev->has_epi = true;
             prev->form = std::move(op.form);
             prev->gates += op.gates;
@@ -778,11 +778,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     size_t epi_scratch = 0;
     for (PlanOp& op : p->ops) {
         if (op.kind != OP_TC || !op.has_epi) continue;
-        if (op.k == 7) tc7_epi_pack(n, op.targets, op.form, op.blob, op.epi);
-        else tc_epi_pack(n, op.k, op.targets, op.form, op.blob, op.epi);
+        tc_epi_pack(n, op.k, op.targets, op.form, op.blob, op.epi);
         op.epi_off = dev_bytes;
         dev_bytes = align(dev_bytes + op.blob.size());
-        epi_scratch = std::max(epi_scratch, op.k == 7 ? tc7_epi_scratch_bytes(n) : tc_epi_scratch_bytes(n, op.k));
+        epi_scratch = std::max(epi_scratch, tc_epi_scratch_bytes(n, op.k));
     }
     p->extra.epi_scratch_off = dev_bytes;
     dev_bytes = align(dev_bytes + epi_scratch);

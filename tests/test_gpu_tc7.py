@@ -201,53 +201,3 @@ def test_empty_circuit_plans(qsim, kw):
     st.set_state(psi0)
     p.execute(st)
     assert np.array_equal(st.get_state(), psi0.astype(np.complex64))
-
-
-def _epi_circuit(n, targets, seed, ndiag=40):
-    """A 7-qubit block followed by diagonal gates (RZZ, phases, controlled phases) on random qubits: they form
-    the block's phase epilogue, with terms on tile, row and column bits and across them."""
-    import math
-    rng = np.random.default_rng(seed)
-    c = W.Circuit(n)
-    c.append(W.Gate(tuple(targets), (), W.haar_unitary(128, rng), "u7"))
-    for _ in range(ndiag):
-        a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
-        kind = int(rng.integers(3))
-        if kind == 0:
-            c.append(W.Gate((a, b), (), W.RZZ(float(rng.uniform(0, 2 * math.pi))), "rzz"))
-        elif kind == 1:
-            c.append(W.Gate((a,), (), np.diag(np.exp(1j * rng.uniform(0, 2 * math.pi, 2))), "p"))
-        else:
-            c.append(W.Gate((a, b), (), np.diag([1, 1, 1, np.exp(1j * rng.uniform(0, 2 * math.pi))]), "cp"))
-    return c
-
-
-EPI_TARGETS = {"rows": (5, 6, 7, 8, 9, 10, 11), "rows_q3": (3, 4, 6, 8, 10, 12, 13),
-               "quads": (0, 1, 4, 6, 7, 10, 13), "pairs": (0, 3, 5, 8, 9, 12, 14)}
-
-
-@pytest.mark.parametrize("name", list(EPI_TARGETS))
-@pytest.mark.parametrize("n", [16, 23])
-def test_k7_phase_epilogue_against_oracle(qsim, name, n):
-    """A 7-qubit block carrying the run of diagonal gates after it as its phase epilogue (one pass, two
-    launches: the per-tile factors, then the block), on every data path; 23 qubits: several tiles per CTA."""
-    c = _epi_circuit(n, EPI_TARGETS[name], n)
-    p = qsim.Plan(c, qsim.C64, **K7)
-    ps = p.passes()
-    assert [(q["kind"], q["k"], q["launches"]) for q in ps] == [("tc", 7, 2)]
-    psi0 = random_state(n, 6)
-    st = qsim.State(n, qsim.C64)
-    st.set_state(psi0)
-    p.execute(st)
-    check(st.get_state(), oracle.run(c, psi=psi0.copy()), n)
-
-
-def test_k7_phase_epilogue_from_basis(qsim):
-    n = 18
-    c = _epi_circuit(n, EPI_TARGETS["rows"], 9)
-    p = qsim.Plan(c, qsim.C64, **K7)
-    x = 0b101100111001010110
-    st = qsim.State(n, qsim.C64)
-    st.set_state(random_state(n, 2))  # garbage the first pass must not read
-    p.execute_from_basis(st, x)
-    check(st.get_state(), oracle.run(c, basis_state=x), n)

@@ -203,19 +203,16 @@ def test_pairs_are_consecutive_blocks_of_the_tf32_plan(qsim, make):
 
 
 def test_seven_qubit_blocks(qsim):
-    """max_fused = 7 with QSIM_PREC_FP16X3: 7-qubit tensor-core blocks in FP16 (no 3xTF32 form) that keep off
-    qubits 0..2, every gate placed once; the 30-qubit brickwork takes 49 passes instead of 64, its final CZ
-    layer the phase epilogue of the last 7-qubit block; where the 6-qubit grouping is cheaper (the QFT) it is
-    kept."""
+    """max_fused = 7 with QSIM_PREC_FP16X3: 7-qubit tensor-core blocks in FP16 (no 3xTF32 form, no phase
+    epilogue) that keep off qubits 0..2, every gate placed once; the 30-qubit brickwork takes 50 passes instead
+    of 64; where the 6-qubit grouping is cheaper (the QFT) it is kept."""
     c = W.brickwork(30, 40, seed=3)
     _, ps = plan(qsim, c, mode=1, max_fused=7, precision=4, tc_min_k=5)
     k7 = [q for q in ps if q["kind"] == "tc" and q["k"] == 7]
-    assert len(ps) <= 49 and len(k7) >= 40
+    assert len(ps) <= 50 and len(k7) >= 40
     assert all(min(q["targets"]) >= 3 for q in k7)
     assert all(q["k"] <= 6 for q in ps if q["kind"] == "tc" and min(q["targets"]) < 3)
-    assert all(q["precision"] == 4 for q in k7)
-    assert [q["launches"] for q in ps].count(2) == 1 and ps[-1]["k"] == 7 and ps[-1]["launches"] == 2
-    assert not any(q["kind"] == "phase" for q in ps)
+    assert all(q["precision"] == 4 and q["launches"] == 1 for q in k7)
     assert all(q["algorithmic_bytes"] == 2 * 8 * 2.0 ** 30 for q in k7)
     # the QFT's phases ride on 6-qubit blocks as epilogues, which 7-qubit blocks cannot carry: width 7 keeps the
     # (cheaper) 6-qubit grouping
