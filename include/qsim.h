@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define QSIM_ABI_VERSION 1
+#define QSIM_ABI_VERSION 2
 
 /* Status codes. */
 #define QSIM_OK 0
@@ -127,6 +127,12 @@ typedef struct {
        12 qubits as ONE pass (both products per tile while it is on chip). Correct, but measured slower than
        two single passes on GB300 (the pass is bound by instruction issue, not memory); for study. */
     int32_t pair_blocks;
+    /* Plans of states of at most 16 qubits whose passes are all CUDA-core dense blocks (k <= 4) or diagonals
+       (k <= 6) run every pass inside ONE cooperative launch, one CTA per SM resident over the plan and a grid
+       barrier between passes (Sec. 2.1: the passes applied in order; at these sizes a pass is a few
+       microseconds of arithmetic, less than a launch costs). Only a whole-plan execution does; a pass range
+       launches per pass. 1 = always one launch per pass (and the CUDA graph of use_graph). */
+    int32_t launch_per_pass;
 } qsim_run_opts;
 
 /* What a plan does per execution (filled by qsim_plan_create). */
@@ -139,6 +145,7 @@ typedef struct {
     int64_t reorders;        /* qubit-reorder passes */
     double algorithmic_bytes;/* HBM bytes the passes must move at minimum (read + write) */
     double host_plan_ms;     /* host time spent planning */
+    int64_t resident;        /* 1: a whole-plan execution is one cooperative launch (launch_per_pass) */
 } qsim_plan_info;
 
 /* ---- version and errors ------------------------------------------------------------------------------ */
@@ -419,6 +426,14 @@ int qsim_spill_sample(const void* host_state, int n, int dtype, int window_qubit
  * synchronises; QSIM_ETIMEOUT if a bounded wait of the probe expired.
  */
 int qsim_tc_peak(int kind, int n_cols, double seconds, double* tflops, double* ms);
+
+/*
+ * Measured FP64 FMA rate of this GPU (library service, no passage: the denominator against which the
+ * resident small-state runner's FP64 arithmetic is reported). Independent FP64 FMA chains on 32 warps per SM
+ * for about `seconds` seconds (0 < seconds <= 30); *tflops receives 2 x FMAs / elapsed time (CUDA events),
+ * *ms (may be NULL) the elapsed time. Runs on a private stream, allocates 8 bytes, and synchronises.
+ */
+int qsim_fp64_peak(double seconds, double* tflops, double* ms);
 
 /* ---- batches of independent circuits (one persistent launch) ---------------------------------------- */
 

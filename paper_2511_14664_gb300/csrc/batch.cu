@@ -820,6 +820,7 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             po.max_fused = opts.precision == QSIM_PREC_FP16X3 ? 7 : 6;
             po.precision = opts.precision;
             po.tc_min_k = 5;
+            po.launch_per_pass = 1;  // plans run concurrently on worker streams inside a captured graph
             const int r = qsim_plan_create(&cs[wides[w]], QSIM_C64, &po, pst[my_slot], &wph[w], &wpi[w]);
             if (r == QSIM_OK && cudaStreamSynchronize(pst[my_slot]) != cudaSuccess)
                 return cuda_fail(cudaGetLastError(), "tensor-core plan of a wide circuit");

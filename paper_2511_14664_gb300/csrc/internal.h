@@ -43,6 +43,29 @@ cudaError_t launch_set_basis(int dtype, void* psi, int n, uint64_t x, cudaStream
 // Convert a device FP64 matrix (2^k x 2^k complex) into the state precision (device -> device).
 cudaError_t launch_convert_matrix(int dtype, const double* src, void* dst, int64_t count, cudaStream_t s);
 
+// ---- every pass of a small-state plan in one cooperative launch (k_small.cu) --------------------------------
+constexpr int kSmallMaxQubits = 16;  // states of at most 2^16 amplitudes (1 MiB complex128): L2-resident
+struct PhaseForm;
+// One pass of such a plan: a dense U on k <= 4 targets or a diagonal on k <= 6 targets, with any controls, or a
+// phase pass (form).
+struct SmallOpDesc {
+    bool diag = false;
+    int k = 0, nc = 0;
+    const int* targets = nullptr;
+    const int* controls = nullptr;
+    const double* mat = nullptr;               // dense: 2^k x 2^k; diagonal: 2^k entries (interleaved, FP64)
+    const std::vector<int>* touch = nullptr;   // diagonal: entries with a factor other than 1
+    const PhaseForm* form = nullptr;           // phase pass: its combined phase (the other fields unused)
+};
+// Device bytes of the program of npass passes (a barrier word, then one fixed-size record per pass).
+size_t small_program_bytes(int dtype, int npass);
+// Write the program into host memory `out` (small_program_bytes bytes); false if a pass is outside the limits.
+bool small_program_build(int dtype, const std::vector<SmallOpDesc>& ops, unsigned char* out);
+// Run the uploaded program (16-byte aligned device copy) on the state in one cooperative launch, grid
+// barriers between passes; with from_basis the state is first set to |*from_basis>.
+cudaError_t launch_small_run(int dtype, void* psi, int n, void* dprog, int npass, unsigned* dev_err, cudaStream_t s,
+                             const DevInfo& d, const uint64_t* from_basis);
+
 // ---- phase pass: any number of 1- and 2-qubit diagonal gates (k_phase.cu) -----------------------------------
 // The combined phase c + sum_a h_a x_a + sum_{a<b} lam_ab x_a x_b (radians) of a run of diagonal gates.
 struct PhaseForm {

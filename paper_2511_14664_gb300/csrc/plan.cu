@@ -72,6 +72,8 @@ struct qsim_plan {
     cudaStream_t gstream = nullptr;
     qsim::PlanExtra extra;
     bool dry = false;  // planned on the host only: no device buffer, cannot execute
+    bool small = false;     // a whole-plan execution is one resident launch (k_small.cu)
+    size_t small_off = 0;   // its program in the plan buffer
 };
 
 namespace qsim {
@@ -350,6 +352,11 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
                        const uint64_t* first_from_basis = nullptr) {
     cudaError_t e = cudaSuccess;
     const size_t last = std::min(p->ops.size(), count == (size_t)-1 ? p->ops.size() : first + count);
+    if (p->small && first == 0 && last == p->ops.size()) {
+        e = launch_small_run(h->dtype, h->psi, h->n, static_cast<char*>(p->dbuf) + p->small_off, (int)last, h->derr,
+                             h->stream, h->dev, first_from_basis);
+        return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "resident plan launch");
+    }
     for (size_t oi = first; oi < last; ++oi) {
         const PlanOp& op = p->ops[oi];
         const uint64_t* fb = oi == first ? first_from_basis : nullptr;
@@ -793,7 +800,15 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     const size_t off_pool = align(off_out + sizeof(double) * 2 * (size_t)compose_out);
     const size_t off_cb = align(off_pool + sizeof(double) * pool.size());
     const size_t off_cg = align(off_cb + sizeof(ComposeBlock) * cblocks.size());
-    const size_t total = align(off_cg + sizeof(ComposeGate) * cgates.size()) + 1024;
+    // a small state whose passes are all CUDA-core dense blocks, diagonals or phase passes runs them in one
+    // resident launch
+    bool small = !opts.launch_per_pass && n <= kSmallMaxQubits && !(opts.local_qubits > 0 && opts.local_qubits < n) &&
+                 !p->ops.empty();
+    for (const PlanOp& op : p->ops)
+        small = small && ((op.kind == OP_DENSE_SMALL && op.k <= 4) || (op.kind == OP_DIAG && op.k <= 6) ||
+                          op.kind == OP_PHASE);
+    const size_t off_small = align(off_cg + sizeof(ComposeGate) * cgates.size());
+    const size_t total = off_small + (small ? align(small_program_bytes(dtype, (int)p->ops.size())) : 0) + 1024;
     e = cudaMalloc(&p->dbuf, total);
     if (e != cudaSuccess) { delete p; set_error("plan buffer of %zu bytes", total); return QSIM_ENOMEM; }
     p->dbuf_bytes = total;
@@ -877,6 +892,28 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
         op.mat.clear();
         op.mat.shrink_to_fit();
+    }
+    if (rc == QSIM_OK && small) {
+        std::vector<SmallOpDesc> sd(p->ops.size());
+        for (size_t i = 0; i < p->ops.size(); ++i) {
+            const PlanOp& op = p->ops[i];
+            sd[i].diag = op.kind == OP_DIAG;
+            sd[i].k = op.k;
+            sd[i].nc = op.nc;
+            sd[i].targets = op.targets;
+            sd[i].controls = op.controls;
+            sd[i].mat = op.mat.data();
+            sd[i].touch = &op.touch;
+            if (op.kind == OP_PHASE) sd[i].form = &op.form;
+        }
+        std::vector<unsigned char> prog(small_program_bytes(dtype, (int)p->ops.size()));
+        if (small_program_build(dtype, sd, prog.data())) {
+            e = cudaMemcpyAsync(base + off_small, prog.data(), prog.size(), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // pageable host source
+            if (e != cudaSuccess) rc = cuda_fail(e, "plan preparation");
+            p->small = true;
+            p->small_off = off_small;
+        }
     }
     if (rc) { cudaFree(p->dbuf); delete p; return rc; }
     }  // !dry
@@ -1027,6 +1064,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         else ++I.dense_blocks;
         I.algorithmic_bytes += op_bytes(op, n, amp);
     }
+    I.resident = p->small ? 1 : 0;
     I.host_plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = I;
     *out = p;
@@ -1038,7 +1076,7 @@ int qsim_plan_execute(qsim_h h, qsim_plan_h p) {
     set_error("%s", "");
     if (p->dry) { set_error("plan was created as a dry run"); return QSIM_EINVAL; }
     if (h->n != p->n || h->dtype != p->dtype) { set_error("plan was made for another n or dtype"); return QSIM_EINVAL; }
-    if (!p->use_graph || h->stream == nullptr) return enqueue_ops(h, p);
+    if (!p->use_graph || h->stream == nullptr || p->small) return enqueue_ops(h, p);  // a resident plan is one launch
     if (p->gexec && p->ghandle == h && p->gpsi == h->psi && p->gstream == h->stream) {
         cudaError_t e = cudaGraphLaunch(p->gexec, h->stream);
         return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "graph launch");
@@ -1120,6 +1158,8 @@ int qsim_plan_execute_from_basis(qsim_h h, qsim_plan_h p, uint64_t x, int64_t co
     // as its input and writes every amplitude
     if (count > 0 && ((p->ops[0].kind == OP_TC && p->ops[0].precision != QSIM_PREC_BF16X6) || p->ops[0].kind == OP_TC_PAIR))
         return enqueue_ops(h, p, 0, (size_t)count, &x);
+    // a resident plan sets |x> itself, in the same launch
+    if (p->small && count == nops) return enqueue_ops(h, p, 0, (size_t)count, &x);
     const int rc = qsim_set_basis(h, x);
     if (rc) return rc;
     return enqueue_ops(h, p, 0, (size_t)count);

@@ -222,6 +222,7 @@ extern "C" int qsim_spill_run(void* host_state, const qsim_circuit* c, int dtype
     ro.use_graph = 0;
     ro.dry_run = 0;
     ro.local_qubits = 0;
+    ro.launch_per_pass = 1;  // one plan runs on several windows at once (three streams)
     unsigned char* H = static_cast<unsigned char*>(host_state);
     const size_t slice_bytes = win.amp << L;
     std::vector<qsim_plan_h> plans;

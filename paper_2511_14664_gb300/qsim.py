@@ -44,7 +44,8 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_fused", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tc_min_k", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
                 ("dry_run", ctypes.c_int32), ("batch_tc_min_n", ctypes.c_int32),
-                ("plan_effort", ctypes.c_int32), ("pair_blocks", ctypes.c_int32)]
+                ("plan_effort", ctypes.c_int32), ("pair_blocks", ctypes.c_int32),
+                ("launch_per_pass", ctypes.c_int32)]
 
 
 class PassInfo(ctypes.Structure):
@@ -73,7 +74,8 @@ PASS_KINDS = {0: "dense_small", 1: "diag", 2: "dense_tile", 3: "tc", 4: "reorder
 class PlanInfo(ctypes.Structure):
     _fields_ = [("input_gates", ctypes.c_int64), ("passes", ctypes.c_int64), ("dense_blocks", ctypes.c_int64),
                 ("tc_blocks", ctypes.c_int64), ("diag_blocks", ctypes.c_int64), ("reorders", ctypes.c_int64),
-                ("algorithmic_bytes", ctypes.c_double), ("host_plan_ms", ctypes.c_double)]
+                ("algorithmic_bytes", ctypes.c_double), ("host_plan_ms", ctypes.c_double),
+                ("resident", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -121,6 +123,7 @@ SIGNATURES = {
     "qsim_spill_segments": ([_P(Circuit), _i, _i, _P(ctypes.c_int32), _P(_u64), _P(_i64)], _i),
     "qsim_spill_sample": ([_vp, _i, _i, _i, _u64, _i64, _P(_u64), _P(ctypes.c_double)], _i),
     "qsim_tc_peak": ([_i, _i, ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
+    "qsim_fp64_peak": ([ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double)], _i),
     "qsim_batch_workspace_bytes": ([_P(Circuit), _i, _P(_sz)], _i),
     "qsim_batch_plan_create": ([_P(Circuit), _i, _P(RunOpts), _vp, _P(_vp), _P(PlanInfo)], _i),
     "qsim_batch_execute": ([_vp, _vp, _sz, _vp, _i], _i),
@@ -258,10 +261,12 @@ class State:
         return self
 
     def run(self, circuit, mode: int = RUN_PLAIN, max_fused: int = 5, precision: int = PREC_SIMT,
-            tc_min_k: int = 5, local_qubits: int = 0, plan_effort: int = 0, pair_blocks: bool = False):
+            tc_min_k: int = 5, local_qubits: int = 0, plan_effort: int = 0, pair_blocks: bool = False,
+            launch_per_pass: bool = False):
         cc = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k, use_graph=0,
-                    local_qubits=local_qubits, plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0)
+                    local_qubits=local_qubits, plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0,
+                    launch_per_pass=1 if launch_per_pass else 0)
         info = PlanInfo()
         _check(lib().qsim_run(self.h, ctypes.byref(cc.c), ctypes.byref(o), ctypes.byref(info)))
         return info.as_dict()
@@ -406,14 +411,18 @@ class Plan:
 
     def __init__(self, circuit, dtype: int = C64, mode: int = RUN_PLAIN, max_fused: int = 5,
                  precision: int = PREC_SIMT, tc_min_k: int = 5, use_graph: bool = False, stream=None,
-                 local_qubits: int = 0, dry_run: bool = False, plan_effort: int = 0, pair_blocks: bool = False):
+                 local_qubits: int = 0, dry_run: bool = False, plan_effort: int = 0, pair_blocks: bool = False,
+                 launch_per_pass: bool = False):
         """dry_run: plan on the host only (no device needed); the plan lists its passes but cannot run.
         plan_effort 1: also try fusion with one block of look-ahead, keep the grouping with fewer blocks.
-        pair_blocks (with PREC_FP16X3): two consecutive 6-qubit blocks per pass where they fit a tile."""
+        pair_blocks (with PREC_FP16X3): two consecutive 6-qubit blocks per pass where they fit a tile.
+        launch_per_pass: one launch per pass even where the plan could run in one resident launch (states of
+        at most 16 qubits, CUDA-core passes only)."""
         self.args = CircuitArgs(circuit)
         o = RunOpts(mode=mode, max_fused=max_fused, precision=precision, tc_min_k=tc_min_k,
                     use_graph=1 if use_graph else 0, local_qubits=local_qubits, dry_run=1 if dry_run else 0,
-                    plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0)
+                    plan_effort=plan_effort, pair_blocks=1 if pair_blocks else 0,
+                    launch_per_pass=1 if launch_per_pass else 0)
         info = PlanInfo()
         p = ctypes.c_void_p()
         _check(lib().qsim_plan_create(ctypes.byref(self.args.c), dtype, ctypes.byref(o),
@@ -517,6 +526,13 @@ def tc_peak(kind: str = "tf32", n_cols: int = 128, seconds: float = 1.0):
     k = {"tf32": 0, "bf16": 1, "fp16": 2}[kind]
     t, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib().qsim_tc_peak(k, int(n_cols), float(seconds), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
+def fp64_peak(seconds: float = 1.0):
+    """Measured FP64 FMA rate (TFLOP/s, elapsed ms) of independent FMA chains on every SM."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qsim_fp64_peak(float(seconds), ctypes.byref(t), ctypes.byref(ms)))
     return t.value, ms.value
 
 

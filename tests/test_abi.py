@@ -29,7 +29,7 @@ def test_binding_covers_header():
 
 
 def test_abi_version():
-    assert qsim.lib().qsim_abi_version() == 1
+    assert qsim.lib().qsim_abi_version() == 2
 
 
 def test_state_bytes_matches_paper_memory_formula():
