@@ -44,10 +44,11 @@ int apply_gate_plain(qsim_state* h, const int* targets, int k, const int* contro
 // ones) and keeps the block within kmax qubits. gmask[i] = qubits of gate i (targets and controls). With
 // gwide, the diagonal gates it marks may also form one block of any width (a phase pass), chosen when it
 // holds more than wide_factor times the gates of the best other candidate. lookahead > 0: choose among the
-// `lookahead` largest candidates by their size plus that of the best block after them.
+// `lookahead` largest candidates by their size plus that of the best block after them. *wide_used (if given) is
+// set when a block was the phase candidate.
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
                                           int kmax, const std::vector<char>* gwide = nullptr, int wide_factor = 1,
-                                          int lookahead = 0, uint64_t narrow = 0);
+                                          int lookahead = 0, uint64_t narrow = 0, bool* wide_used = nullptr);
 // Groupings cached by structure (plan.cu): key words describe the request (options, each gate's qubit mask and
 // flags); the first word tells the requester apart (0 plans, 1 batch circuits).
 bool group_cache_get(const std::vector<uint64_t>& key, std::vector<std::vector<int>>& out);

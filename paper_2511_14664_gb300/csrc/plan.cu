@@ -122,7 +122,8 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
 // qubit narrower).
 static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
                                                 int n, int kmax, const std::vector<char>* gwide, int wide_factor,
-                                                const std::vector<char>& done, int first, uint64_t narrow) {
+                                                const std::vector<char>& done, int first, uint64_t narrow,
+                                                bool* wide_won = nullptr) {
     const int G = (int)gmask.size();
     std::vector<std::vector<int>> out;
     std::vector<int> wide;
@@ -164,7 +165,11 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
     // A phase pass costs a full pass whatever it holds, and it only grows while dense blocks make progress
     // (each one frees the diagonal gates behind it): it wins against dense blocks of less than
     // 1 / wide_factor of its size.
-    if (wide.size() > (size_t)wide_factor * best) { out.clear(); out.push_back(std::move(wide)); }
+    if (wide.size() > (size_t)wide_factor * best) {
+        out.clear();
+        out.push_back(std::move(wide));
+        if (wide_won) *wide_won = true;
+    }
     if (out.empty()) out.push_back({first});
     return out;
 }
@@ -174,7 +179,7 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
 // after it is largest (one step of look-ahead; slower planning, sometimes fewer blocks).
 std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag, int n,
                                           int kmax, const std::vector<char>* gwide, int wide_factor, int lookahead,
-                                          uint64_t narrow) {
+                                          uint64_t narrow, bool* wide_used) {
     const int G = (int)gmask.size();
     const int LA = lookahead;
     std::vector<std::vector<int>> blocks;
@@ -184,7 +189,7 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
     while (true) {
         first = next_first(first);
         if (first >= G) break;
-        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first, narrow);
+        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first, narrow, wide_used);
         size_t pick = 0;
         for (size_t c = 1; c < cands.size(); ++c)
             if (cands[c].size() > cands[pick].size()) pick = c;
@@ -506,15 +511,21 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
         return cs;
     };
     auto group_all = [&](int km, uint64_t nar) {
-        auto bl = group_gates(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, 1, 0, nar);
+        std::vector<std::vector<int>> bl;
+        bool have = false;
         // whether a phase pass should wait for more diagonal gates depends on the circuit, and so does
-        // whether looking one block ahead pays: keep the cheapest grouping (the fewest blocks of each kind)
-        for (int la = 0; la <= (opts.plan_effort > 0 ? 4 : 0); la += 4)
-            for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
-                if (la == 0 && f == 1) continue;  // the first grouping above
-                auto alt = group_gates(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, f, la, nar);
-                if (cost(alt) < cost(bl)) bl.swap(alt);
+        // whether looking one block ahead pays: keep the cheapest grouping (the fewest blocks of each kind).
+        // A grouping that never picked the phase candidate at factor f is also the grouping at 2f (every
+        // step sees the same candidates, and the phase candidate loses by a wider margin), so the larger
+        // factors are skipped then.
+        for (int la = 0; la <= (opts.plan_effort > 0 ? 4 : 0); la += 4) {
+            bool picked = true;
+            for (int f = 1; f <= (use_wide ? 4 : 1) && picked; f *= 2) {
+                picked = false;
+                auto alt = group_gates(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, f, la, nar, &picked);
+                if (!have || cost(alt) < cost(bl)) { bl.swap(alt); have = true; }
             }
+        }
         if (opts.plan_effort >= 2)
             for (int f = 1; f <= (use_wide ? 4 : 1); f *= 2) {
                 auto alt = group_gates_beam(gmask, gdiag, n, km, use_wide ? &gwide : nullptr, f,
