@@ -353,6 +353,51 @@ static double op_bytes(const PlanOp& op, int n, size_t amp) {
     return 2.0 * amp * groups * (double)(1 << op.k);
 }
 
+// Plan buffers come from a memory pool of the library's own (stream-ordered allocation): planning on several
+// host threads at once, and one-shot runs that create and destroy a plan per call, then avoid the device-wide
+// locking of cudaMalloc / cudaFree. Up to 256 MiB of freed plan buffers stay reserved in the pool for reuse.
+static cudaMemPool_t plan_pool(int device) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0) return nullptr;
+    if ((size_t)device >= pools.size()) pools.resize(device + 1, nullptr);
+    if (!pools[device]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        uint64_t keep = 256ull << 20;
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[device] = mp;
+    }
+    return pools[device];
+}
+
+static cudaError_t plan_buffer_alloc(void** out, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t mp = plan_pool(dev);
+    if (!mp) return cudaMalloc(out, bytes);
+    return cudaMallocFromPoolAsync(out, bytes, mp, s);
+}
+
+// Only once no work that uses the buffer can be in flight (the callers synchronise first).
+static void plan_buffer_free(void* ptr) {
+    if (!ptr) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && plan_pool(dev)) {
+        cudaFreeAsync(ptr, cudaStreamLegacy);
+        cudaStreamSynchronize(cudaStreamLegacy);  // returned to the pool before this call returns
+    } else {
+        cudaFree(ptr);
+    }
+}
+
 static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size_t count = (size_t)-1,
                        const uint64_t* first_from_basis = nullptr) {
     cudaError_t e = cudaSuccess;
@@ -820,7 +865,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                           op.kind == OP_PHASE);
     const size_t off_small = align(off_cg + sizeof(ComposeGate) * cgates.size());
     const size_t total = off_small + (small ? align(small_program_bytes(dtype, (int)p->ops.size())) : 0) + 1024;
-    e = cudaMalloc(&p->dbuf, total);
+    e = plan_buffer_alloc(&p->dbuf, total, s);
     if (e != cudaSuccess) { delete p; set_error("plan buffer of %zu bytes", total); return QSIM_ENOMEM; }
     p->dbuf_bytes = total;
     char* base = static_cast<char*>(p->dbuf);
@@ -846,7 +891,10 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                                reinterpret_cast<ComposeGate*>(base + off_cg), reinterpret_cast<double*>(base + off_pool),
                                reinterpret_cast<double*>(base + off_out), max_kb, s);
         // device operands and host copies of small composed matrices
-        std::vector<std::pair<int, std::vector<double>>> fetch;
+        // composed matrices the host keeps (CUDA-core dense blocks and diagonals: they travel as launch
+        // parameters or into a resident program): fetched below, in one copy where they lie close together
+        std::vector<std::pair<size_t, size_t>> fetch;  // (op index, offset in doubles from the compose output)
+        size_t lo = (size_t)-1, hi = 0, need = 0;
         for (const Pending& pd : pending) {
             if (e != cudaSuccess) break;
             PlanOp& op = p->ops[pd.op];
@@ -864,8 +912,24 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 e = launch_convert_matrix(dtype, U, base + op.dev_off, 2 * (int64_t)D * D, s);
             } else {
                 op.mat.resize(2 * (size_t)D * D);
-                e = cudaMemcpyAsync(op.mat.data(), U, sizeof(double) * 2 * D * D, cudaMemcpyDeviceToHost, s);
+                const size_t o = 2 * (size_t)cblocks[op.compose_idx].out_off;
+                fetch.emplace_back((size_t)pd.op, o);
+                lo = std::min(lo, o);
+                hi = std::max(hi, o + op.mat.size());
+                need += op.mat.size();
             }
+        }
+        std::vector<double> stage;
+        const bool one_copy = fetch.size() > 1 && hi - lo <= 4 * need + 8192;
+        if (e == cudaSuccess && one_copy) {
+            stage.resize(hi - lo);
+            e = cudaMemcpyAsync(stage.data(), reinterpret_cast<double*>(base + off_out) + lo, sizeof(double) * stage.size(),
+                                cudaMemcpyDeviceToHost, s);
+        }
+        for (size_t f = 0; e == cudaSuccess && !one_copy && f < fetch.size(); ++f) {
+            PlanOp& op = p->ops[fetch[f].first];
+            e = cudaMemcpyAsync(op.mat.data(), reinterpret_cast<double*>(base + off_out) + fetch[f].second,
+                                sizeof(double) * op.mat.size(), cudaMemcpyDeviceToHost, s);
         }
         for (PlanOp& op : p->ops) {
             if (e != cudaSuccess) break;
@@ -875,6 +939,11 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             e = launch_tc_pair_prepare(U1, U2, base + op.dev_off, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && one_copy)
+            for (const auto& fo : fetch) {
+                PlanOp& op = p->ops[fo.first];
+                std::memcpy(op.mat.data(), stage.data() + (fo.second - lo), sizeof(double) * op.mat.size());
+            }
         if (e == cudaSuccess) {
             for (const Pending& pd : pending) {
                 PlanOp& op = p->ops[pd.op];
@@ -926,7 +995,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             p->small_off = off_small;
         }
     }
-    if (rc) { cudaFree(p->dbuf); delete p; return rc; }
+    if (rc) { cudaStreamSynchronize(s); plan_buffer_free(p->dbuf); delete p; return rc; }
     }  // !dry
 
     // ---- global / local index bits: reorder before passes that touch a global qubit ------------------------
@@ -999,7 +1068,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 std::vector<int> glob;
                 for (int q = 0; q < n; ++q) if ((bring >> q) & 1) glob.push_back(phys[q]);
                 if (cand.size() < glob.size()) {
-                    cudaFree(p->dbuf);
+                    plan_buffer_free(p->dbuf);
                     delete p;
                     set_error("local_qubits = %d leaves too few idle local qubits for a %d-qubit pass", L, (int)op_qubits(op).size());
                     return QSIM_EINVAL;
@@ -1038,7 +1107,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 for (const auto& pr : *inv) std::swap(chk[pr.first], chk[pr.second]);
             for (int q = 0; q < n; ++q)
                 if (chk[q] != q) {
-                    cudaFree(p->dbuf);
+                    plan_buffer_free(p->dbuf);
                     delete p;
                     set_error("internal error: qubit order restore");
                     return QSIM_EINVAL;
@@ -1181,7 +1250,7 @@ int qsim_plan_destroy(qsim_plan_h p) {
     if (p->dry) { delete p; return QSIM_OK; }
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    cudaFree(p->dbuf);
+    plan_buffer_free(p->dbuf);
     delete p;
     return QSIM_OK;
 }
