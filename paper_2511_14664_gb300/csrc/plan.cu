@@ -84,16 +84,15 @@ static inline int popcnt(uint64_t v) { return __builtin_popcountll(v); }
 // unplaced gate on a shared qubit (a diagonal gate is blocked only by non-diagonal ones) and that fits: with
 // a fixed window W, gates whose qubits lie inside W; otherwise (W = 0) gates that keep the growing qubit set
 // within kmax qubits (kmax - 1 once it touches a qubit in `narrow`), starting from `seed`.
+// `und` lists the unplaced gates in circuit order.
 static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
-                                    const std::vector<char>& done, int first, int seed, uint64_t W, int kmax,
-                                    uint64_t narrow) {
+                                    const std::vector<int>& und, int seed, uint64_t W, int kmax, uint64_t narrow) {
     auto lim = [&](uint64_t S) { return (S & narrow) ? kmax - 1 : kmax; };
-    const int G = (int)gmask.size();
     std::vector<int> blk;
     uint64_t Q = 0, bany = 0, bdiag = 0;
     if (seed >= 0) { blk.push_back(seed); Q = gmask[seed]; }
-    for (int i = first; i < G; ++i) {
-        if (done[i] || i == seed) continue;
+    for (const int i : und) {
+        if (i == seed) continue;
         const uint64_t qs = gmask[i];
         const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
         const bool fits = W ? (qs & ~W) == 0 : popcnt(Q | qs) <= lim(Q | qs);
@@ -113,6 +112,14 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
     return blk;
 }
 
+// Window candidates kept across the steps of one grouping: a window's block depends only on the unplaced gates
+// that touch it (gates elsewhere neither fit it nor block the qubits it uses), so it is rebuilt only after a
+// block on one of its qubits was placed.
+struct WinCache {
+    std::vector<std::vector<int>> blk;
+    std::vector<char> valid;
+};
+
 // Candidates for the next block (group_gates keeps the largest, or looks one step ahead):
 // every window of kmax consecutive qubits (all available gates inside it), and, for every qubit, its
 // earliest unplaced gate when no earlier unplaced gate blocks it, grown greedily. The plain greedy choice
@@ -123,15 +130,20 @@ static std::vector<int> build_block(const std::vector<uint64_t>& gmask, const st
 static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gmask, const std::vector<char>& gdiag,
                                                 int n, int kmax, const std::vector<char>* gwide, int wide_factor,
                                                 const std::vector<char>& done, int first, uint64_t narrow,
-                                                bool* wide_won = nullptr) {
+                                                bool* wide_won = nullptr, WinCache* wc = nullptr) {
     const int G = (int)gmask.size();
     std::vector<std::vector<int>> out;
     std::vector<int> wide;
+    // the unplaced gates, in order: every candidate below scans a prefix of them
+    std::vector<int> und;
+    und.reserve(G - first);
+    for (int i = first; i < G; ++i)
+        if (!done[i]) und.push_back(i);
     if (gwide) {
         const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
         uint64_t bany = 0;
-        for (int i = first; i < G && bany != all; ++i) {
-            if (done[i]) continue;
+        for (size_t u = 0; u < und.size() && bany != all; ++u) {
+            const int i = und[u];
             if (gdiag[i] && (*gwide)[i] && (gmask[i] & bany) == 0) wide.push_back(i);
             else if (!gdiag[i]) bany |= gmask[i];
         }
@@ -142,20 +154,30 @@ static std::vector<std::vector<int>> candidates(const std::vector<uint64_t>& gma
     }
     size_t best = 0;
     const int wmax = std::min(kmax, n);
+    if (wc && wc->valid.size() != (size_t)std::max(0, n - wmax + 1)) {
+        wc->valid.assign(std::max(0, n - wmax + 1), 0);
+        wc->blk.assign(wc->valid.size(), {});
+    }
     for (int a0 = 0; a0 + wmax <= n; ++a0) {
-        uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
-        if (W & narrow) W &= ~(1ull << (a0 + wmax - 1));
-        auto blk = build_block(gmask, gdiag, done, first, -1, W, kmax, narrow);
+        std::vector<int> blk;
+        if (wc && wc->valid[a0]) {
+            blk = wc->blk[a0];
+        } else {
+            uint64_t W = ((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0;
+            if (W & narrow) W &= ~(1ull << (a0 + wmax - 1));
+            blk = build_block(gmask, gdiag, und, -1, W, kmax, narrow);
+            if (wc) { wc->blk[a0] = blk; wc->valid[a0] = 1; }
+        }
         best = std::max(best, blk.size());
         if (!blk.empty()) out.push_back(std::move(blk));
     }
     uint64_t seen = 0, bany = 0, bdiag = 0;
-    for (int i = first; i < G && popcnt(seen) < n; ++i) {
-        if (done[i]) continue;
+    for (size_t u = 0; u < und.size() && popcnt(seen) < n; ++u) {
+        const int i = und[u];
         const uint64_t qs = gmask[i];
         const bool blocked = gdiag[i] ? (qs & bany) != 0 : (qs & (bany | bdiag)) != 0;
         if ((qs & ~seen) && !blocked && popcnt(qs) <= kmax) {
-            auto blk = build_block(gmask, gdiag, done, first, i, 0, kmax, narrow);
+            auto blk = build_block(gmask, gdiag, und, i, 0, kmax, narrow);
             best = std::max(best, blk.size());
             if (!blk.empty()) out.push_back(std::move(blk));
         }
@@ -186,10 +208,12 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
     std::vector<char> done(G, 0);
     int first = 0;
     auto next_first = [&](int f) { while (f < G && done[f]) ++f; return f; };
+    WinCache wc;
+    const int wmax = std::min(kmax, n);
     while (true) {
         first = next_first(first);
         if (first >= G) break;
-        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first, narrow, wide_used);
+        auto cands = candidates(gmask, gdiag, n, kmax, gwide, wide_factor, done, first, narrow, wide_used, &wc);
         size_t pick = 0;
         for (size_t c = 1; c < cands.size(); ++c)
             if (cands[c].size() > cands[pick].size()) pick = c;
@@ -219,7 +243,10 @@ std::vector<std::vector<int>> group_gates(const std::vector<uint64_t>& gmask, co
             }
         }
         std::vector<int> best = std::move(cands[pick]);
-        for (int i : best) done[i] = 1;
+        uint64_t QB = 0;
+        for (int i : best) { done[i] = 1; QB |= gmask[i]; }
+        for (int a0 = 0; a0 < (int)wc.valid.size(); ++a0)
+            if (((((wmax == 64) ? ~0ull : ((1ull << wmax) - 1)) << a0) & QB) != 0) wc.valid[a0] = 0;
         blocks.push_back(std::move(best));
     }
     return blocks;
