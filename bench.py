@@ -853,11 +853,20 @@ def run_tfim_batch(args):
         simt_only = {"ms": ms_s, "gates_per_s": gates / (ms_s / 1000.0),
                      "max_abs_diff_zi_vs_main": max(float(np.max(np.abs(rs[i][0] - res[i][0]))) for i in range(len(cs)))}
         bs.close()
-    # end to end: plan from host circuits, one launch, results to host (best of three, with a breakdown)
+    # end to end: the one-shot call from host circuits to host results (qsim_batch_run: the GPU runs the
+    # circuits already planned while the host plans the others), best of three; beside it the same batch
+    # planned, then executed, with its breakdown
     e2e_runs = []
     for _ in range(3):
         torch.cuda.synchronize()
         qsim.plan_cache_clear()  # cold: only groupings repeated within this batch are reused
+        t = time.perf_counter()
+        _, rinfo = qsim.batch_run(cs, max_fused=0, precision=tc_prec, tc_min_n=tc_min_n)
+        e2e_runs.append({"total_s": time.perf_counter() - t, "c_plan_and_enqueue_ms": rinfo["host_plan_ms"]})
+    staged = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        qsim.plan_cache_clear()
         t = time.perf_counter()
         b2 = qsim.Batch(cs, max_fused=0, precision=tc_prec, tc_min_n=tc_min_n)
         t_plan = time.perf_counter()
@@ -865,8 +874,8 @@ def run_tfim_batch(args):
         b2.results()
         t_run = time.perf_counter()
         b2.close()
-        e2e_runs.append({"total_s": time.perf_counter() - t, "plan_s": t_plan - t,
-                         "c_plan_ms": b2.info["host_plan_ms"], "execute_results_s": t_run - t_plan})
+        staged.append({"total_s": time.perf_counter() - t, "plan_s": t_plan - t,
+                       "c_plan_ms": b2.info["host_plan_ms"], "execute_results_s": t_run - t_plan})
     best = min(e2e_runs, key=lambda r: r["total_s"])
     e2e_s = best["total_s"]
     peaks, src = measured_peaks()
@@ -923,6 +932,7 @@ def run_tfim_batch(args):
                              sum(16 * 4 ** len(g.targets) for c in cs for g in c.gates),
                              "d2h_bytes_per_step": 8 * sum(2 * c.n - 1 for c in cs)},
                         tune_s=tune_s, sample_zi0=list(res[0][0][:4]), one_by_one=one_by_one, e2e_breakdown=best,
+                        e2e_planned_then_executed=min(staged, key=lambda r: r["total_s"]),
                         persistent_launch_only=simt_only)
     if not args.no_cpu:
         import oracle as oracle_mod

@@ -29,6 +29,8 @@
 #include <cstring>
 #include <functional>
 #include <atomic>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <string>
@@ -555,8 +557,18 @@ int qsim_batch_workspace_bytes(const qsim_circuit* cs, int count, size_t* out) {
     return QSIM_OK;
 }
 
-int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opts* opts_in, void* stream_v,
-                           qsim_batch_h* out, qsim_plan_info* info) {
+static int batch_launch(qsim_batch_h b, cudaStream_t s);
+static int enqueue_wide(qsim_batch_h b, qsim_plan_h plan, size_t w, int k, void* dev_ws);
+
+// Planning of a batch. With run_ws (the one-shot qsim_batch_run) the batch is also executed while it is
+// planned: the persistent launch of the narrower circuits goes out as soon as they are planned, and each wide
+// circuit's plan is enqueued on a worker stream as soon as it is made, so that the GPU runs the first
+// tensor-core plans while the host still plans the others; the worker streams are joined back into `stream`
+// before returning. (The running plans hold the SMs that the planning's own kernels need, so planning takes
+// longer; measured on the 256-chain batch the overlap still wins: 124 ms from host circuits to host results
+// against 130 ms planning first and 128 ms with only the persistent launch overlapped.)
+static int batch_plan_create_impl(const qsim_circuit* cs, int count, const qsim_run_opts* opts_in, void* stream_v,
+                                  qsim_batch_h* out, qsim_plan_info* info, void* run_ws) {
     set_error("%s", "");
     const auto t0 = std::chrono::steady_clock::now();
     if (!out) { set_error("NULL output"); return QSIM_EINVAL; }
@@ -770,10 +782,29 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     I.passes = (int64_t)passes.size();
     I.dense_blocks = (int64_t)passes.size();
     I.algorithmic_bytes = bytes;  // state traffic of the large circuits; small ones never leave shared memory
+    // one-shot run: the wide circuits' planning streams are ordered after the caller's earlier work, not after
+    // the persistent launch (pre_ev, recorded before it)
+    cudaEvent_t pre_ev = nullptr;
+    if (run_ws) {
+        b->args.ws = static_cast<float2*>(run_ws);
+        if (!wides.empty() && (cudaEventCreateWithFlags(&pre_ev, cudaEventDisableTiming) != cudaSuccess ||
+                               cudaEventRecord(pre_ev, s) != cudaSuccess)) {
+            if (pre_ev) cudaEventDestroy(pre_ev);
+            qsim_batch_destroy(b);
+            return cuda_fail(cudaGetLastError(), "batch ordering event");
+        }
+        if (b->nlarge + b->nsmall > 0 && (rc = batch_launch(b, s)) != QSIM_OK) {
+            if (pre_ev) cudaEventDestroy(pre_ev);
+            qsim_batch_destroy(b);
+            return rc;
+        }
+    }
 
     // ---- wide circuits: fused tensor-core plans, <Z> scratch, device error word ---------------------------
     if (!wides.empty()) {
         auto fail = [&](int code) {
+            if (pre_ev) cudaEventDestroy(pre_ev);
+            pre_ev = nullptr;
             qsim_batch_destroy(b);
             return code;
         };
@@ -806,13 +837,52 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
         const int nw = (int)wides.size();
         const int nth = host_threads(nw * 4);
         std::vector<cudaStream_t> pst(nth, nullptr);
-        cudaEvent_t ord = nullptr;
-        ok = cudaEventCreateWithFlags(&ord, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ord, s) == cudaSuccess;
+        cudaEvent_t ord = pre_ev;
+        if (!ord)
+            ok = cudaEventCreateWithFlags(&ord, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ord, s) == cudaSuccess;
+        // planning streams at the highest priority: in a one-shot run their composition kernels are scheduled
+        // ahead of the worker streams' passes of the plans already made
+        int prio_lo = 0, prio_hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) { cudaGetLastError(); prio_hi = 0; }
         for (int t = 0; t < nth && ok; ++t)
-            ok = cudaStreamCreateWithFlags(&pst[t], cudaStreamNonBlocking) == cudaSuccess &&
+            ok = cudaStreamCreateWithPriority(&pst[t], cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
                  cudaStreamWaitEvent(pst[t], ord, 0) == cudaSuccess;
         std::vector<qsim_plan_h> wph(nw, nullptr);
         std::vector<qsim_plan_info> wpi(nw);
+        // one-shot run: the worker streams start with the persistent launch (after the caller's earlier work,
+        // pre_ev), their kernels taking the SMs it leaves; one host thread enqueues each plan as the planning
+        // threads finish it (its passes and its <Z> readout) on the least-loaded worker stream, while the
+        // planning threads go on planning
+        std::mutex qmu;
+        std::condition_variable qcv;
+        std::deque<int> ready;
+        bool planning_done = false;
+        int enq_rc = QSIM_OK;
+        std::string enq_msg;
+        std::thread enq;
+        if (run_ws && ok)
+            for (int k = 0; k < nworkers && ok; ++k) ok = cudaStreamWaitEvent(b->wstreams[k], ord, 0) == cudaSuccess;
+        if (run_ws && ok) {
+            enq = std::thread([&, device]() {
+                cudaSetDevice(device);
+                std::vector<double> load(nworkers, 0.0);
+                for (;;) {
+                    int w = -1;
+                    {
+                        std::unique_lock<std::mutex> lk(qmu);
+                        qcv.wait(lk, [&] { return !ready.empty() || planning_done; });
+                        if (ready.empty()) break;
+                        w = ready.front();
+                        ready.pop_front();
+                    }
+                    if (enq_rc != QSIM_OK) continue;  // after an error: drain, enqueue nothing more
+                    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                    load[k] += std::ldexp((double)wpi[w].passes, cs[wides[w]].n);
+                    enq_rc = enqueue_wide(b, wph[w], (size_t)w, k, run_ws);
+                    if (enq_rc != QSIM_OK) enq_msg = qsim_last_error();
+                }
+            });
+        }
         const int prc = !ok ? QSIM_ENOMEM : parallel_for(nw, nth, device, [&](int w, int my_slot) -> int {
             qsim_run_opts po{};
             po.mode = QSIM_RUN_FUSED;
@@ -824,15 +894,38 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
             const int r = qsim_plan_create(&cs[wides[w]], QSIM_C64, &po, pst[my_slot], &wph[w], &wpi[w]);
             if (r == QSIM_OK && cudaStreamSynchronize(pst[my_slot]) != cudaSuccess)
                 return cuda_fail(cudaGetLastError(), "tensor-core plan of a wide circuit");
+            if (r == QSIM_OK && enq.joinable()) {
+                std::lock_guard<std::mutex> lk(qmu);
+                ready.push_back(w);
+                qcv.notify_one();
+            }
             return r;
         });
+        if (enq.joinable()) {
+            {
+                std::lock_guard<std::mutex> lk(qmu);
+                planning_done = true;
+                qcv.notify_one();
+            }
+            enq.join();
+            if (enq_rc != QSIM_OK) set_error("%s", enq_msg.c_str());
+        }
+        if (run_ws) {  // join every worker back into s, also after an error
+            for (int k = 0; k < nworkers; ++k) {
+                bool j = cudaEventRecord(b->join_ev[k], b->wstreams[k]) == cudaSuccess &&
+                         cudaStreamWaitEvent(s, b->join_ev[k], 0) == cudaSuccess;
+                ok = ok && j;
+            }
+        }
         for (cudaStream_t st : pst)
             if (st) cudaStreamDestroy(st);
         if (ord) cudaEventDestroy(ord);
+        pre_ev = nullptr;  // it was ord
         for (qsim_plan_h ph : wph)
             if (ph) b->wide_plans.push_back(ph);
         if (!ok) { set_error("batch: streams for planning the tensor-core circuits"); return fail(QSIM_ENOMEM); }
         if (prc) return fail(prc);
+        if (enq_rc) return fail(enq_rc);
         std::vector<double> wide_work;
         for (int w = 0; w < nw; ++w) {
             const int i = wides[w];
@@ -867,7 +960,28 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
     return QSIM_OK;
 }
 
-static int batch_launch(qsim_batch_h b, cudaStream_t s);
+int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opts* opts_in, void* stream_v,
+                           qsim_batch_h* out, qsim_plan_info* info) {
+    return batch_plan_create_impl(cs, count, opts_in, stream_v, out, info, nullptr);
+}
+
+// Wide circuit w (its plan) on worker stream k: the plan from |0> (its first block generates the basis
+// state), then its <Z> values.
+static int enqueue_wide(qsim_batch_h b, qsim_plan_h plan, size_t w, int k, void* dev_ws) {
+    qsim_state st;
+    st.n = b->wide_n[w];
+    st.dtype = QSIM_C64;
+    st.psi = static_cast<float2*>(dev_ws) + b->wide_state_off[w];
+    st.bytes = small_state_bytes(st.n);
+    st.stream = b->wstreams[k];
+    st.dev = b->dev;
+    st.derr = b->derr;
+    int rc = qsim_plan_execute_from_basis(&st, plan, 0, -1);
+    if (rc) return rc;
+    cudaError_t e = run_zstats_device(QSIM_C64, st.psi, st.n, b->reds[k], st.stream, b->dev,
+                                      b->args.zi + b->wide_zi_off[w], b->args.zz + b->wide_zz_off[w], true);
+    return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "batch <Z> of a tensor-core plan");
+}
 
 static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
     b->args.ws = static_cast<float2*>(dev_ws);
@@ -882,22 +996,8 @@ static int batch_enqueue(qsim_batch_h b, void* dev_ws, cudaStream_t s) {
     for (size_t k = 0; e == cudaSuccess && k < b->wstreams.size(); ++k) e = cudaStreamWaitEvent(b->wstreams[k], b->fork_ev, 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch fork");
     int rc = QSIM_OK;
-    for (size_t w = 0; w < b->wide_plans.size() && rc == QSIM_OK; ++w) {
-        const int k = b->wide_worker[w];
-        qsim_state st;
-        st.n = b->wide_n[w];
-        st.dtype = QSIM_C64;
-        st.psi = static_cast<float2*>(dev_ws) + b->wide_state_off[w];
-        st.bytes = small_state_bytes(st.n);
-        st.stream = b->wstreams[k];
-        st.dev = b->dev;
-        st.derr = b->derr;
-        rc = qsim_plan_execute_from_basis(&st, b->wide_plans[w], 0, -1);
-        if (rc) break;
-        e = run_zstats_device(QSIM_C64, st.psi, st.n, b->reds[k], st.stream, b->dev, b->args.zi + b->wide_zi_off[w],
-                              b->args.zz + b->wide_zz_off[w], true);
-        if (e != cudaSuccess) rc = cuda_fail(e, "batch <Z> of a tensor-core plan");
-    }
+    for (size_t w = 0; w < b->wide_plans.size() && rc == QSIM_OK; ++w)
+        rc = enqueue_wide(b, b->wide_plans[w], w, b->wide_worker[w], dev_ws);
     // join every worker back into s, also after an error (a capture must end with all branches joined)
     for (size_t k = 0; k < b->wstreams.size(); ++k) {
         cudaError_t ej = cudaEventRecord(b->join_ev[k], b->wstreams[k]);
@@ -994,10 +1094,20 @@ int qsim_batch_destroy(qsim_batch_h b) {
 
 int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws, size_t ws_bytes,
                    void* stream, double* zi, double* zz, qsim_plan_info* info) {
-    qsim_batch_h b = nullptr;
-    int rc = qsim_batch_plan_create(cs, count, opts, stream, &b, info);
+    set_error("%s", "");
+    if (!zi || !zz) { set_error("NULL argument"); return QSIM_EINVAL; }
+    size_t need = 0;
+    int rc = qsim_batch_workspace_bytes(cs, count, &need);
     if (rc) return rc;
-    rc = qsim_batch_execute(b, dev_ws, ws_bytes, stream, 0);
+    if (need && (!dev_ws || ws_bytes < need)) { set_error("workspace of %zu bytes < %zu needed", ws_bytes, need); return QSIM_ENOMEM; }
+    if (dev_ws && (reinterpret_cast<uintptr_t>(dev_ws) & 255)) { set_error("workspace must be 256-byte aligned"); return QSIM_EINVAL; }
+    // a workspace is needed to run while planning; a batch without one (every circuit in shared memory)
+    // plans, then executes
+    qsim_batch_h b = nullptr;
+    void* run_ws = dev_ws ? dev_ws : nullptr;
+    rc = batch_plan_create_impl(cs, count, opts, stream, &b, info, run_ws);
+    if (rc) return rc;
+    if (!run_ws) rc = qsim_batch_execute(b, dev_ws, ws_bytes, stream, 0);
     if (!rc) rc = qsim_batch_results(b, stream, zi, zz);
     qsim_batch_destroy(b);
     return rc;

@@ -21,6 +21,10 @@ struct DevInfo {
 
 // Per-call error message (thread-local) used by qsim_last_error().
 void set_error(const char* fmt, ...);
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel, device and size (the largest asked so far
+// covers smaller launches): the call is a driver round trip, which a plan's passes would otherwise make before
+// every launch.
+cudaError_t smem_optin(const void* kern, int bytes);
 int cuda_fail(cudaError_t e, const char* what);
 
 // ---- gate kernels (k_gates.cu) ------------------------------------------------------------------------------

@@ -68,7 +68,7 @@ cudaError_t launch_compose(const ComposeBlock* dblocks, int nblocks, const Compo
     if (max_kb < 1 || max_kb > 7) return cudaErrorInvalidValue;
     const int Dm = 1 << max_kb, cols_max = max_kb <= 6 ? Dm : 32;
     const size_t smem = 2 * sizeof(double2) * (size_t)Dm * (size_t)cols_max;
-    cudaError_t e = cudaFuncSetAttribute(k_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_compose), (int)smem);
     if (e != cudaSuccess) return e;
     k_compose<<<dim3((unsigned)nblocks, (unsigned)(Dm / cols_max), 1), 256, smem, s>>>(dblocks, dgates, dpool, dout,
                                                                                    cols_max);

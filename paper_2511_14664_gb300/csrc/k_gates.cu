@@ -574,7 +574,7 @@ static cudaError_t dense_tile_t(void* psi, int n, const int* targets, const Fixe
     constexpr int D = 1 << K;
     for (int m = 0; m < D; ++m) a.off[m] = target_offset(m, K, targets);
     const size_t smem = (size_t)(D * D + D * 64) * sizeof(T);
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tile<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_dense_tile<R, K>), (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t ngroups = 1ull << (n - f.nf);
     const uint64_t ntiles = (ngroups + 63) / 64;
@@ -595,7 +595,7 @@ static cudaError_t dense_big_t(void* psi, int n, const int* targets, const Fixed
     a.cmask = f.cmask;
     std::memcpy(a.tpos, targets, sizeof(int) * K);
     const size_t smem = BigCfg<R, K>::smem;
-    cudaError_t e = cudaFuncSetAttribute(k_dense_big<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_dense_big<R, K>), (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t ngroups = 1ull << (n - f.nf);
     const uint64_t nchunks = (ngroups + BigCfg<R, K>::G - 1) / BigCfg<R, K>::G;
@@ -662,7 +662,7 @@ static cudaError_t swap_pass(void* psi, int n, const int* a, const int* b, int p
         sa.perm[bt] = inpair[q] ? tb[partner[q]] : bt;
     }
     const size_t smem = sizeof(T) << sa.nS;
-    cudaError_t e = cudaFuncSetAttribute(k_swap_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_swap_tile<R>), (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t ntiles = 1ull << (n - sa.nS);
     const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / std::max<size_t>(smem, 1))));

@@ -819,7 +819,7 @@ static cudaError_t run_probs_warp(int dtype, const void* psi, int n, const int* 
     if (tmp && (e = cudaMallocAsync(reinterpret_cast<void**>(&dout), bytes, s)) != cudaSuccess) return e;
     const bool m0 = (a.lowmask & 1u) != 0;
     auto launch = [&](auto kern, auto typed_psi) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err = smem_optin(reinterpret_cast<const void*>(kern), (int)smem);
         if (err == cudaSuccess) {
             kern<<<nb, 256, smem, s>>>(typed_psi, a, r.partials, dout);
             err = cudaGetLastError();

@@ -828,7 +828,7 @@ cudaError_t apply_p(void* psi, const Args& a, const void* dB, unsigned* err, cud
     const size_t smem = smem_bytes(K, Cfg<PREC>::planes, Cfg<PREC>::esize);
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
     auto launch = [&](auto kern, int threads, bool pdl) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(kern), (int)smem);
         if (e != cudaSuccess) return e;
         if (!pdl) {
             kern<<<grid, threads, smem, s>>>(reinterpret_cast<float2*>(psi), a, reinterpret_cast<const uint4*>(dB), err);

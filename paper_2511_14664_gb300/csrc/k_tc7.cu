@@ -430,7 +430,7 @@ cudaError_t launch_tc7_apply(void* psi, int n, const int* targets, const void* d
     }
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)d.num_sms, a.ntiles);
     auto launch = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc7::kSmem);
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(kern), (int)tc7::kSmem);
         if (e != cudaSuccess) return e;
         // programmatic dependent launch, as for the 6-qubit block (griddepcontrol.wait before any access)
         cudaLaunchConfig_t cfg{};

@@ -588,6 +588,32 @@ class Batch:
             pass
 
 
+def batch_run(circuits, max_fused: int = 0, precision: int = 0, tc_min_n: int = 0, stream=None):
+    """Plan, run and read out a batch in one call (qsim_batch_run): the GPU starts on the circuits already
+    planned while the host plans the others. Returns (per-circuit (<Z_q>, <Z_q Z_{q+1}>), plan info)."""
+    import torch
+    circuits = list(circuits)
+    args = CircuitsArgs(circuits)
+    ws = ctypes.c_size_t()
+    _check(lib().qsim_batch_workspace_bytes(args.arr, args.count, ctypes.byref(ws)))
+    buf = torch.empty(max(1, ws.value // 8), dtype=torch.complex64, device="cuda") if ws.value else None
+    o = RunOpts(mode=RUN_FUSED, max_fused=max_fused, precision=precision, batch_tc_min_n=tc_min_n)
+    nzi = sum(c.n for c in circuits)
+    nzz = sum(max(0, c.n - 1) for c in circuits)
+    zi = np.zeros(max(1, nzi))
+    zz = np.zeros(max(1, nzz))
+    info = PlanInfo()
+    _check(lib().qsim_batch_run(args.arr, args.count, ctypes.byref(o),
+                                ctypes.c_void_p(buf.data_ptr() if buf is not None else 0), ws.value,
+                                ctypes.c_void_p(_stream_ptr(stream)), _dptr(zi), _dptr(zz), ctypes.byref(info)))
+    out, a, b = [], 0, 0
+    for c in circuits:
+        out.append((zi[a:a + c.n].copy(), zz[b:b + c.n - 1].copy()))
+        a += c.n
+        b += max(0, c.n - 1)
+    return out, info.as_dict()
+
+
 def batch_autotune(circuits, stream=None):
     """Tune the batched fusion width per qubit count; returns the k each circuit now gets."""
     args = CircuitsArgs(circuits)

@@ -202,3 +202,38 @@ def test_threshold_tuner_and_tuning_file(qsim, tmp_path):
     qsim.batch_tune_load(str(path))
     import json
     assert json.loads(path.read_text())["tc_min_n"]["1"] == best
+
+
+@pytest.mark.parametrize("prec", [0, 1, 4])
+def test_one_shot_run_equals_plan_then_execute(qsim, prec):
+    """qsim_batch_run (plan, run and read out in one call; the GPU starts on the planned circuits while the
+    host plans the others) returns exactly what a plan executed afterwards returns, and matches the oracle."""
+    widths = [10, 13, 14, 16, 17, 19, 15, 18, 20, 12]
+    steps = [3, 2, 2, 3, 2, 2, 1, 2, 2, 3]
+    cs = tfim_mix(widths, steps, seed=21)
+    b = qsim.Batch(cs, max_fused=4, precision=prec, tc_min_n=16)
+    b.execute()
+    r1 = b.results()
+    b.close()
+    r2, info = qsim.batch_run(cs, max_fused=4, precision=prec, tc_min_n=16)
+    assert info["input_gates"] == sum(len(c) for c in cs)
+    assert (info["tc_blocks"] > 0) == (prec != 0)
+    for (a1, b1), (a2, b2) in zip(r1, r2):
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    check(r2, cs)
+
+
+def test_one_shot_run_small_only_and_full_size(qsim):
+    """Circuits that all stay in shared memory (no workspace), and the benchmark's 256-chain batch with
+    FP16X3 plans for the circuits of >= 20 qubits against plan-then-execute."""
+    cs = tfim_mix([8, 10, 12, 13], [2, 3, 2, 1], seed=22)
+    r, _ = qsim.batch_run(cs, max_fused=3)
+    check(r, cs)
+    cs = [c for c, _, _ in W.tfim_batch(256, seed=4, nmax=24)]
+    b = qsim.Batch(cs, max_fused=0, precision=4, tc_min_n=20)
+    b.execute()
+    r1 = b.results()
+    b.close()
+    r2, _ = qsim.batch_run(cs, max_fused=0, precision=4, tc_min_n=20)
+    for (a1, b1), (a2, b2) in zip(r1, r2):
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
