@@ -72,6 +72,7 @@ struct qsim_plan {
     cudaStream_t gstream = nullptr;
     qsim::PlanExtra extra;
     bool dry = false;  // planned on the host only: no device buffer, cannot execute
+    bool pooled = false;    // dbuf came from the library's memory pool
     bool small = false;     // a whole-plan execution is one resident launch (k_small.cu)
     size_t small_off = 0;   // its program in the plan buffer
 };
@@ -386,10 +387,15 @@ static double op_bytes(const PlanOp& op, int n, size_t amp) {
 static cudaMemPool_t plan_pool(int device) {
     static std::mutex mu;
     static std::vector<cudaMemPool_t> pools;
+    static std::vector<char> tried;
     std::lock_guard<std::mutex> lk(mu);
     if (device < 0) return nullptr;
-    if ((size_t)device >= pools.size()) pools.resize(device + 1, nullptr);
-    if (!pools[device]) {
+    if ((size_t)device >= pools.size()) {
+        pools.resize(device + 1, nullptr);
+        tried.resize(device + 1, 0);
+    }
+    if (!tried[device]) {  // one attempt per device; without a pool, plain cudaMalloc
+        tried[device] = 1;
         cudaMemPoolProps props{};
         props.allocType = cudaMemAllocationTypePinned;
         props.handleTypes = cudaMemHandleTypeNone;
@@ -404,20 +410,20 @@ static cudaMemPool_t plan_pool(int device) {
     return pools[device];
 }
 
-static cudaError_t plan_buffer_alloc(void** out, size_t bytes, cudaStream_t s) {
+static cudaError_t plan_buffer_alloc(void** out, size_t bytes, cudaStream_t s, bool* pooled) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     cudaMemPool_t mp = plan_pool(dev);
+    *pooled = mp != nullptr;
     if (!mp) return cudaMalloc(out, bytes);
     return cudaMallocFromPoolAsync(out, bytes, mp, s);
 }
 
 // Only once no work that uses the buffer can be in flight (the callers synchronise first).
-static void plan_buffer_free(void* ptr) {
+static void plan_buffer_free(void* ptr, bool pooled) {
     if (!ptr) return;
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && plan_pool(dev)) {
+    if (pooled) {
         cudaFreeAsync(ptr, cudaStreamLegacy);
         cudaStreamSynchronize(cudaStreamLegacy);  // returned to the pool before this call returns
     } else {
@@ -432,7 +438,15 @@ static int enqueue_ops(qsim_state* h, const qsim_plan* p, size_t first = 0, size
     if (p->small && first == 0 && last == p->ops.size()) {
         e = launch_small_run(h->dtype, h->psi, h->n, static_cast<char*>(p->dbuf) + p->small_off, (int)last, h->derr,
                              h->stream, h->dev, first_from_basis);
-        return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "resident plan launch");
+        if (e != cudaErrorCooperativeLaunchTooLarge) return e == cudaSuccess ? QSIM_OK : cuda_fail(e, "resident plan launch");
+        // fewer SMs available than the device has (e.g. a share of them under MPS): launch per pass
+        cudaGetLastError();
+        e = cudaSuccess;
+        if (first_from_basis) {
+            e = launch_set_basis(h->dtype, h->psi, h->n, *first_from_basis, h->stream, h->dev);
+            if (e != cudaSuccess) return cuda_fail(e, "plan pass launch");
+            first_from_basis = nullptr;
+        }
     }
     for (size_t oi = first; oi < last; ++oi) {
         const PlanOp& op = p->ops[oi];
@@ -892,7 +906,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                           op.kind == OP_PHASE);
     const size_t off_small = align(off_cg + sizeof(ComposeGate) * cgates.size());
     const size_t total = off_small + (small ? align(small_program_bytes(dtype, (int)p->ops.size())) : 0) + 1024;
-    e = plan_buffer_alloc(&p->dbuf, total, s);
+    e = plan_buffer_alloc(&p->dbuf, total, s, &p->pooled);
     if (e != cudaSuccess) { delete p; set_error("plan buffer of %zu bytes", total); return QSIM_ENOMEM; }
     p->dbuf_bytes = total;
     char* base = static_cast<char*>(p->dbuf);
@@ -1022,7 +1036,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
             p->small_off = off_small;
         }
     }
-    if (rc) { cudaStreamSynchronize(s); plan_buffer_free(p->dbuf); delete p; return rc; }
+    if (rc) { cudaStreamSynchronize(s); plan_buffer_free(p->dbuf, p->pooled); delete p; return rc; }
     }  // !dry
 
     // ---- global / local index bits: reorder before passes that touch a global qubit ------------------------
@@ -1095,7 +1109,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 std::vector<int> glob;
                 for (int q = 0; q < n; ++q) if ((bring >> q) & 1) glob.push_back(phys[q]);
                 if (cand.size() < glob.size()) {
-                    plan_buffer_free(p->dbuf);
+                    plan_buffer_free(p->dbuf, p->pooled);
                     delete p;
                     set_error("local_qubits = %d leaves too few idle local qubits for a %d-qubit pass", L, (int)op_qubits(op).size());
                     return QSIM_EINVAL;
@@ -1134,7 +1148,7 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 for (const auto& pr : *inv) std::swap(chk[pr.first], chk[pr.second]);
             for (int q = 0; q < n; ++q)
                 if (chk[q] != q) {
-                    plan_buffer_free(p->dbuf);
+                    plan_buffer_free(p->dbuf, p->pooled);
                     delete p;
                     set_error("internal error: qubit order restore");
                     return QSIM_EINVAL;
@@ -1277,7 +1291,7 @@ int qsim_plan_destroy(qsim_plan_h p) {
     if (p->dry) { delete p; return QSIM_OK; }
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    plan_buffer_free(p->dbuf);
+    plan_buffer_free(p->dbuf, p->pooled);
     delete p;
     return QSIM_OK;
 }
