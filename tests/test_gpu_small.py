@@ -158,3 +158,12 @@ def test_phase_passes(qsim, dtype, make):
     ref = oracle.run(c, psi=psi0.copy())
     close(res, ref, n, dtype)
     close(per, ref, n, dtype)
+
+
+def test_fp64_rate_probe(qsim):
+    """The FP64 rate probe (the resident runner's roofline denominator) reports a plausible rate for its
+    elapsed time: positive, below the FP64 rate of any GPU of this class (~100 TFLOP/s), and the run lasts
+    about as long as asked."""
+    tf, ms = qsim.fp64_peak(0.2)
+    assert 0.05 < tf < 100.0, tf
+    assert 50.0 < ms < 2000.0, ms
