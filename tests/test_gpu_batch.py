@@ -108,6 +108,12 @@ def test_batch_rejects_bad_input(qsim):
     c.append(W.Gate((0, 1, 2), (3, 4), np.eye(8), "wide"))
     with pytest.raises(qsim.QsimError):
         qsim.Batch([c])
+    # the one-shot call validates every circuit before any launch, and the library stays usable after it
+    ok = tfim_mix([12, 20], [2, 2], seed=3)
+    with pytest.raises(qsim.QsimError):
+        qsim.batch_run(ok + [c], max_fused=3, precision=4, tc_min_n=16)
+    r, _ = qsim.batch_run(ok, max_fused=3, precision=4, tc_min_n=16)
+    check(r, ok)
 
 
 def test_full_size_batch_256_tfim_chains(qsim):
