@@ -707,7 +707,8 @@ def run_brick14(args):
             ref = psi
         # FP64 arithmetic of the dense passes: every amplitude of a touched group is a 2^k-term complex dot
         # product (8 2^k real flops); diagonal and phase passes add a few flops per amplitude (not counted)
-        fp64 = sum(8.0 * (1 << q["k"]) * 2.0 ** (n - q["nc"]) for q in p.passes() if q["kind"] == "dense_small")
+        fp64 = sum(8.0 * (1 << q["k"]) * 2.0 ** (n - q["nc"]) for q in p.passes()
+                   if q["kind"] in ("dense_small", "dense_tile"))
         out[name] = {"ms_per_step": ms, "gates_per_s": len(c) / (ms / 1000.0), "passes": p.info["passes"],
                      "resident": bool(p.info["resident"]), "fp64_gflop": fp64 / 1e9,
                      "fp64_tflops": fp64 / (ms / 1000.0) / 1e12,

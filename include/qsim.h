@@ -127,8 +127,8 @@ typedef struct {
        12 qubits as ONE pass (both products per tile while it is on chip). Correct, but measured slower than
        two single passes on GB300 (the pass is bound by instruction issue, not memory); for study. */
     int32_t pair_blocks;
-    /* Plans of states of at most 16 qubits whose passes are all CUDA-core dense blocks (k <= 4) or diagonals
-       (k <= 6) run every pass inside ONE cooperative launch, one CTA per SM resident over the plan and a grid
+    /* Plans of states of at most 16 qubits whose passes are all CUDA-core dense blocks (k <= 5), diagonals
+       (k <= 6) or phase passes run every pass inside ONE cooperative launch, one CTA per SM resident over the plan and a grid
        barrier between passes (Sec. 2.1: the passes applied in order; at these sizes a pass is a few
        microseconds of arithmetic, less than a launch costs). Only a whole-plan execution does; a pass range
        launches per pass. 1 = always one launch per pass (and the CUDA graph of use_graph). */

@@ -50,7 +50,7 @@ cudaError_t launch_convert_matrix(int dtype, const double* src, void* dst, int64
 // ---- every pass of a small-state plan in one cooperative launch (k_small.cu) --------------------------------
 constexpr int kSmallMaxQubits = 16;  // states of at most 2^16 amplitudes (1 MiB complex128): L2-resident
 struct PhaseForm;
-// One pass of such a plan: a dense U on k <= 4 targets or a diagonal on k <= 6 targets, with any controls, or a
+// One pass of such a plan: a dense U on k <= 5 targets or a diagonal on k <= 6 targets, with any controls, or a
 // phase pass (form).
 struct SmallOpDesc {
     bool diag = false;

@@ -10,17 +10,19 @@
 // cannot wait on a CTA that has not started. The state stays in L2 (at most 1 MiB); loads of it bypass L1
 // (.cg) so that a pass reads what other SMs wrote in the pass before.
 //
-// Each pass is described by a fixed-size record holding its matrix (dense U on k <= 4 targets with any
+// Each pass is described by a fixed-size record holding its matrix (dense U on k <= 5 targets with any
 // controls, the non-unit entries of a diagonal on k <= 6 targets, or the terms of a phase pass), copied into
-// shared memory one pass ahead (two buffers) so that the copy hides behind the barrier. Dense and diagonal
-// passes do the arithmetic of the per-pass kernels (k_dense_small / k_dense_split and k_diag in k_gates.cu):
-// the same FMA chains in the same order, so the two paths give identical states. A phase pass (any run of
+// shared memory one pass ahead (two buffers) so that the copy hides behind the barrier. Dense passes of up to
+// 4 targets and diagonal passes do the arithmetic of the per-pass kernels (k_dense_small / k_dense_split and
+// k_diag in k_gates.cu): the same FMA chains in the same order, so the two paths give identical states. A
+// phase pass (any run of
 // commuting 1- and 2-qubit diagonal gates: exp(i phi(x)) with phi a quadratic form of the index bits) sums
 // its terms per amplitude in 64-bit fixed-point turns (exact, wrapping mod 2 pi) and takes one FP64
 // sine/cosine of the sum. Work is spread warp by warp over the CTAs (warp w of the grid is warp w / G of CTA
 // w mod G), so that a pass with a few hundred warps of work still occupies every SM's FP64 units.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "common.cuh"
@@ -30,7 +32,7 @@ namespace qsim {
 namespace small {
 
 constexpr int kThreads = 256;
-constexpr int kMaxDense = 4;   // dense targets
+constexpr int kMaxDense = 5;   // dense targets
 constexpr int kMaxDiag = 6;    // diagonal targets
 constexpr int kMaxTerms = 1 + kSmallMaxQubits + kSmallMaxQubits * (kSmallMaxQubits - 1) / 2;  // phase terms
 constexpr size_t kHeader = 256;  // the barrier word, padded
@@ -40,6 +42,8 @@ template <typename R>
 struct alignas(16) Pass {
     int32_t kind;                 // Kind
     int32_t k, nf, np;            // targets; fixed bits (targets + controls); diagonal entries / phase terms
+    int32_t next16;               // 16-byte chunks of the next record that hold data (what is copied of it)
+    int32_t pad[3];
     int32_t fixed[kMaxFixed];     // fixed bit positions, ascending
     uint64_t cmask;               // control bits, set in every group's base index
     uint64_t off[kMaxTerms];      // dense: offset of matrix index m; diagonal: offset of non-unit entry p;
@@ -87,13 +91,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned epoch, unsigne
     return *s_stop == 0;
 }
 
-// The next pass's record, copied into shared memory by asynchronous copies (no registers, no wait): the
-// copies run during this pass and are waited for just before the grid barrier.
+// The next pass's record (its first `chunks` 16-byte chunks: the header and the entries its kind uses), copied
+// into shared memory by asynchronous copies (no registers, no wait): the copies run during this pass and are
+// waited for just before the grid barrier.
 template <typename R>
-__device__ __forceinline__ void copy_pass(Pass<R>* dst, const Pass<R>* src) {
+__device__ __forceinline__ void copy_pass(Pass<R>* dst, const Pass<R>* src, int chunks) {
     const char* s = reinterpret_cast<const char*>(src);
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(Pass<R>) / 16); i += kThreads)
+    for (int i = threadIdx.x; i < chunks; i += kThreads)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d + 16 * i), "l"(s + 16 * i) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -132,6 +137,35 @@ __device__ __forceinline__ void dense_pass(typename Amp<R>::T* psi, int n, const
             }
             psi[base + P.off[r]] = make_amp<R>(re, im);
         }
+    }
+}
+
+// Dense pass on 5 targets: a group is one warp; lane c loads amplitude c of the group and lane r computes
+// row r, taking the other amplitudes from the lanes that hold them (shuffles, column order as above) rather
+// than loading all 32 of them (which would take 128 registers a thread in complex128). U is stored column-major
+// for this width, so that the lanes read consecutive entries. A lane's store follows shuffles that need every
+// lane's load, so all reads precede all writes without a warp barrier.
+template <typename R>
+__device__ __forceinline__ void dense_pass5(typename Amp<R>::T* psi, int n, const Pass<R>& P, uint64_t first,
+                                            uint64_t stride) {
+    using T = typename Amp<R>::T;
+    constexpr int D = 32;
+    const uint64_t items = (1ull << (n - P.nf)) << 5;  // whole warps
+    for (uint64_t it = first; it < items; it += stride) {
+        const uint64_t base = insert_zeros(it >> 5, P.fixed, P.nf) | P.cmask;
+        const int r = (int)(it & 31);  // this lane
+        const T v = __ldcg(psi + base + P.off[r]);
+        R re = 0, im = 0;
+#pragma unroll 8
+        for (int c = 0; c < D; ++c) {
+            const R vx = __shfl_sync(0xffffffffu, v.x, c), vy = __shfl_sync(0xffffffffu, v.y, c);
+            const R ur = P.m[2 * (c * D + r)], ui = P.m[2 * (c * D + r) + 1];
+            re = fmar(ur, vx, re);
+            re = fmar(-ui, vy, re);
+            im = fmar(ur, vy, im);
+            im = fmar(ui, vx, im);
+        }
+        psi[base + P.off[r]] = make_amp<R>(re, im);
     }
 }
 
@@ -186,7 +220,7 @@ k_small_run(typename Amp<R>::T* __restrict__ psi, int n, const Pass<R>* __restri
     auto sync = [&]() -> bool { ++epoch; return grid_sync(bar, epoch, G, err, &s_stop); };
 
     if (npass > 0) {
-        copy_pass(&sp[0], prog);
+        copy_pass(&sp[0], prog, (int)(sizeof(Pass<R>) / 16));
         copy_wait();
     }
     if (from_basis) {
@@ -199,7 +233,7 @@ k_small_run(typename Amp<R>::T* __restrict__ psi, int n, const Pass<R>* __restri
     for (int p = 0; p < npass; ++p) {
         const Pass<R>& P = sp[p & 1];
         // the other buffer was last read in pass p - 1, which every thread of this CTA has finished
-        if (p + 1 < npass) copy_pass(&sp[(p + 1) & 1], prog + p + 1);
+        if (p + 1 < npass) copy_pass(&sp[(p + 1) & 1], prog + p + 1, P.next16);
         if (P.kind == kDiag) {
             diag_pass<R>(psi, n, P, first, stride);
         } else if (P.kind == kPhase) {
@@ -209,7 +243,8 @@ k_small_run(typename Amp<R>::T* __restrict__ psi, int n, const Pass<R>* __restri
                 case 1: dense_pass<R, 1>(psi, n, P, first, stride); break;
                 case 2: dense_pass<R, 2>(psi, n, P, first, stride); break;
                 case 3: dense_pass<R, 3>(psi, n, P, first, stride); break;
-                default: dense_pass<R, 4>(psi, n, P, first, stride); break;
+                case 4: dense_pass<R, 4>(psi, n, P, first, stride); break;
+                default: dense_pass5<R>(psi, n, P, first, stride); break;
             }
         }
         if (p + 1 < npass) {
@@ -278,9 +313,25 @@ bool build_t(const std::vector<SmallOpDesc>& ops, unsigned char* out) {
         } else {
             const int D = 1 << o.k;
             for (int m = 0; m < D; ++m) q.off[m] = offset(m);
-            for (int e = 0; e < 2 * D * D; ++e) q.m[e] = (R)o.mat[e];
+            if (o.k == 5) {  // column-major (dense_pass5)
+                for (int r = 0; r < D; ++r)
+                    for (int c = 0; c < D; ++c) {
+                        q.m[2 * (c * D + r)] = (R)o.mat[2 * (r * D + c)];
+                        q.m[2 * (c * D + r) + 1] = (R)o.mat[2 * (r * D + c) + 1];
+                    }
+            } else {
+                for (int e = 0; e < 2 * D * D; ++e) q.m[e] = (R)o.mat[e];
+            }
         }
     }
+    // what the kernel copies of each record: the header and offsets, and the entries of m its kind uses
+    auto chunks = [](const Pass<R>& q) {
+        size_t mb = q.kind == kPhase ? sizeof(uint64_t) * q.np
+                    : q.kind == kDiag ? sizeof(R) * 2 * q.np
+                                      : sizeof(R) * ((size_t)2 << (2 * q.k));
+        return (int)((offsetof(Pass<R>, m) + mb + 15) / 16);
+    };
+    for (size_t i = 0; i + 1 < ops.size(); ++i) P[i].next16 = chunks(P[i + 1]);
     return true;
 }
 

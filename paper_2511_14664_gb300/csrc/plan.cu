@@ -902,8 +902,8 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
     bool small = !opts.launch_per_pass && n <= kSmallMaxQubits && !(opts.local_qubits > 0 && opts.local_qubits < n) &&
                  !p->ops.empty();
     for (const PlanOp& op : p->ops)
-        small = small && ((op.kind == OP_DENSE_SMALL && op.k <= 4) || (op.kind == OP_DIAG && op.k <= 6) ||
-                          op.kind == OP_PHASE);
+        small = small && ((op.kind == OP_DENSE_SMALL && op.k <= 4) || (op.kind == OP_DENSE_TILE && op.k == 5) ||
+                          (op.kind == OP_DIAG && op.k <= 6) || op.kind == OP_PHASE);
     const size_t off_small = align(off_cg + sizeof(ComposeGate) * cgates.size());
     const size_t total = off_small + (small ? align(small_program_bytes(dtype, (int)p->ops.size())) : 0) + 1024;
     e = plan_buffer_alloc(&p->dbuf, total, s, &p->pooled);
@@ -949,9 +949,12 @@ int qsim_plan_create(const qsim_circuit* c, int dtype, const qsim_run_opts* opts
                 e = launch_tc_prepare(U, pd.kb, op.precision, op.lines, base + op.dev_off, s,
                                       op.has_epi ? reinterpret_cast<const double*>(base + op.epi_off + op.epi.off_rowphase)
                                                  : nullptr);
-            } else if (pd.kind == OP_DENSE_TILE) {
+            } else if (pd.kind == OP_DENSE_TILE && !(small && pd.kb == 5)) {
                 e = launch_convert_matrix(dtype, U, base + op.dev_off, 2 * (int64_t)D * D, s);
             } else {
+                // a 5-qubit block of a resident plan: its device matrix (for pass-range launches) and its FP64
+                // matrix on the host (for the resident program), like the smaller blocks
+                if (pd.kind == OP_DENSE_TILE) e = launch_convert_matrix(dtype, U, base + op.dev_off, 2 * (int64_t)D * D, s);
                 op.mat.resize(2 * (size_t)D * D);
                 const size_t o = 2 * (size_t)cblocks[op.compose_idx].out_off;
                 fetch.emplace_back((size_t)pd.op, o);

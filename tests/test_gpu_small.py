@@ -2,9 +2,10 @@
 between passes) against the FP64 oracle and against the same plan launched pass by pass.
 
 Tolerances: complex64 -- max |amplitude error| <= 1e-5 and normalised infidelity <= 1e-9; complex128 -- max
-|amplitude error| <= 1e-12 and infidelity <= 1e-12. Resident and per-pass launches do the same arithmetic per
-amplitude (the same FMA chains), so their complex128 states must be identical; complex64 per-pass plans take a
-warp-shuffle kernel for single-qubit gates on qubits 1..5, so complex64 is compared within the tolerance.
+|amplitude error| <= 1e-12 and infidelity <= 1e-12. Resident and per-pass launches of dense blocks of up to 4
+qubits and of diagonals do the same arithmetic per amplitude (the same FMA chains), so their complex128 states
+must be identical; complex64 per-pass plans take a warp-shuffle kernel for single-qubit gates on qubits 1..5,
+and 5-qubit blocks a shared-memory kernel, so those are compared within the tolerance.
 """
 import numpy as np
 import pytest
@@ -58,7 +59,8 @@ def run_both(qsim, c, dtype, psi0, **kw):
 
 @pytest.mark.parametrize("dtype", [C64, C128])
 @pytest.mark.parametrize("n", [1, 2, 5, 9, 14, 16])
-@pytest.mark.parametrize("kw", [dict(mode=0, max_fused=1), dict(mode=1, max_fused=2), dict(mode=1, max_fused=4)])
+@pytest.mark.parametrize("kw", [dict(mode=0, max_fused=1), dict(mode=1, max_fused=2), dict(mode=1, max_fused=4),
+                                dict(mode=1, max_fused=5)])
 def test_random_circuits_against_oracle(qsim, dtype, n, kw):
     """Dense gates with controls and diagonal gates (some entries exactly 1), per-gate and fused plans; n = 1 and
     2 leave most lanes of a warp idle in every pass."""
@@ -68,16 +70,17 @@ def test_random_circuits_against_oracle(qsim, dtype, n, kw):
     ref = oracle.run(c, psi=psi0.copy())
     close(res, ref, n, dtype)
     close(per, ref, n, dtype)
-    if dtype == C128:
+    if dtype == C128 and kw["max_fused"] <= 4:
         assert np.array_equal(res, per)
 
 
 @pytest.mark.parametrize("dtype", [C64, C128])
-def test_brickwork_14q_complex128_config(qsim, dtype):
-    """The 14-qubit random brickwork (20 layers, 410 gates) fused at k = 4, from |0>: the resident plan against
-    the oracle."""
+@pytest.mark.parametrize("k", [4, 5])
+def test_brickwork_14q_complex128_config(qsim, dtype, k):
+    """The 14-qubit random brickwork (20 layers, 410 gates) fused at k = 4 and 5, from |0>: the resident plan
+    against the oracle."""
     c = W.brickwork(14, 20, seed=1)
-    p = qsim.Plan(c, dtype, mode=1, max_fused=4)
+    p = qsim.Plan(c, dtype, mode=1, max_fused=k)
     assert p.info["resident"] == 1 and p.info["passes"] > 10
     st = qsim.State(14, dtype)
     p.execute_from_basis(st, 0)
@@ -122,15 +125,15 @@ def test_many_passes_and_graph_option(qsim):
 
 
 def test_eligibility(qsim):
-    """Resident only for states of at most 16 qubits whose passes are all CUDA-core dense blocks (k <= 4),
+    """Resident only for states of at most 16 qubits whose passes are all CUDA-core dense blocks (k <= 5),
     diagonals or phase passes; a pass range still launches pass by pass and matches."""
     c17 = W.brickwork(17, 4, seed=2)
     assert qsim.Plan(c17, C128, mode=1, max_fused=4).info["resident"] == 0
     c = W.brickwork(14, 6, seed=2)
     assert qsim.Plan(c, C64, mode=1, max_fused=6, precision=1, tc_min_k=5).info["resident"] == 0  # tensor cores
-    assert qsim.Plan(c, C128, mode=1, max_fused=5).info["resident"] == 0                           # 5-qubit SIMT
+    assert qsim.Plan(c, C128, mode=1, max_fused=6).info["resident"] == 0                           # 6-qubit SIMT
     assert qsim.Plan(c, C128, mode=1, max_fused=4, local_qubits=12).info["resident"] == 0           # reorders
-    p = qsim.Plan(c, C128, mode=1, max_fused=3)
+    p = qsim.Plan(c, C128, mode=1, max_fused=5)
     assert p.info["resident"] == 1
     psi0 = random_state(14, 2)
     st = qsim.State(14, C128)
