@@ -342,7 +342,8 @@ def _pack_gates(gs):
         ct = [g.controls for g in gs]
         mt = [g.matrix for g in gs]
         ks = np.fromiter(map(len, tg), dtype=np.int32, count=G)
-        ncs = np.fromiter(map(len, ct), dtype=np.int32, count=G)
+        # (any() stops at the first gate with controls; without any, no per-gate lengths are needed)
+        ncs = np.fromiter(map(len, ct), dtype=np.int32, count=G) if any(map(len, ct)) else np.zeros(G, dtype=np.int32)
         if int(ks.max()) > MAX_TARGETS or int(ncs.max()) > MAX_CONTROLS:
             raise ValueError("a gate has more than %d targets or controls" % MAX_TARGETS)
         rec["k"][:G] = ks
