@@ -468,7 +468,15 @@ int qsim_batch_execute(qsim_batch_h b, void* dev_ws, size_t ws_bytes, void* stre
 int qsim_batch_results(qsim_batch_h b, void* stream, double* zi, double* zz);
 /* Release a batch plan and its device buffers. Library service, no passage. NULL is accepted. */
 int qsim_batch_destroy(qsim_batch_h b);
-/* Plan, execute, fetch results and destroy in one call. */
+/*
+ * Plan, execute, fetch results and destroy in one call (Sec. 1: many circuits for iterative algorithms). The
+ * work overlaps: the persistent launch of the narrower circuits goes out as soon as they are planned, and each
+ * tensor-core plan of a wide circuit is enqueued as soon as it is made, while the host plans the others. The
+ * results (zi, zz: host arrays laid out as for qsim_batch_results) are those of qsim_batch_plan_create +
+ * qsim_batch_execute + qsim_batch_results, bit for bit. dev_ws: at least qsim_batch_workspace_bytes,
+ * 256-byte aligned (QSIM_ENOMEM / QSIM_EINVAL otherwise, before any launch); every circuit is validated before
+ * any launch. Synchronises `stream`.
+ */
 int qsim_batch_run(const qsim_circuit* cs, int count, const qsim_run_opts* opts, void* dev_ws,
                    size_t ws_bytes, void* stream, double* zi, double* zz, qsim_plan_info* info);
 /*
