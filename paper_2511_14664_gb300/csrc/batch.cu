@@ -49,8 +49,9 @@ namespace batch {
 constexpr int kThreads = 256;
 constexpr int kKmax = 4;
 constexpr int kSmallMax = 13;  // largest width kept in shared memory (2^13 x 8 B = 64 KiB)
-constexpr size_t kWideStreams = 4;  // worker streams for the circuits run as tensor-core plans
-constexpr int kHalfGridBelow = 24;     // wide circuits narrower than this run their plans on half the SMs
+constexpr size_t kWideStreams = 8;  // worker streams for the circuits run as tensor-core plans
+constexpr int kHalfGridBelow = 24;     // wide circuits narrower than this run their plans on half the SMs,
+constexpr int kQuarterGridBelow = 22;  // and narrower than this on a quarter of them
 
 struct Pass {
     int k;
@@ -968,9 +969,9 @@ int qsim_batch_plan_create(const qsim_circuit* cs, int count, const qsim_run_opt
 
 // Wide circuit w (its plan) on worker stream k: the plan from |0> (its first block generates the basis
 // state), then its <Z> values. Below 24 qubits (fewer than 7 tiles of a tensor-core pass per SM) the plan's
-// kernels take half the SMs: each CTA then has twice the tiles to pipeline, and another worker stream's kernels
-// run on the other half (256-chain batch: 46.8 ms against 49.2 ms with every kernel on all SMs; 47.2 with half
-// the SMs at every width).
+// kernels take half the SMs, below 22 a quarter: each CTA then has more tiles to pipeline, and other worker
+// streams' kernels run on the rest (256-chain batch on 8 worker streams: 45.5 ms, against 49.2 ms with every
+// kernel on all SMs and 4 streams; half the SMs below 24 alone 46.8 ms).
 static int enqueue_wide(qsim_batch_h b, qsim_plan_h plan, size_t w, int k, void* dev_ws) {
     qsim_state st;
     st.n = b->wide_n[w];
@@ -979,7 +980,8 @@ static int enqueue_wide(qsim_batch_h b, qsim_plan_h plan, size_t w, int k, void*
     st.bytes = small_state_bytes(st.n);
     st.stream = b->wstreams[k];
     st.dev = b->dev;
-    if (st.n < batch::kHalfGridBelow && b->wstreams.size() > 1) st.dev.num_sms = std::max(1, b->dev.num_sms / 2);
+    if (b->wstreams.size() > 1 && st.n < batch::kHalfGridBelow)
+        st.dev.num_sms = std::max(1, b->dev.num_sms / (st.n < batch::kQuarterGridBelow ? 4 : 2));
     st.derr = b->derr;
     int rc = qsim_plan_execute_from_basis(&st, plan, 0, -1);
     if (rc) return rc;
