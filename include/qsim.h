@@ -446,9 +446,10 @@ int qsim_fp64_peak(double seconds, double* tflops, double* ms);
  * state in the caller's workspace, passes separated by cluster barriers), then one CTA per smaller circuit
  * with the whole state in shared memory. With opts->precision a tensor-core precision, circuits of at
  * least opts->batch_tc_min_n qubits (default 20) are planned as fused tensor-core plans instead (k = 6
- * blocks, their state in the workspace) and enqueued after the persistent launch, with their <Z> values
- * reduced on the device: one cluster streams a wide state at a fraction of the GPU's bandwidth, a plan's
- * passes use all of it. Those plans run on four streams the batch owns, forked from the caller's stream
+ * blocks, or up to 7 with QSIM_PREC_FP16X3; their state in the workspace) and enqueued after the persistent
+ * launch, with their <Z> values reduced on the device: one cluster streams a wide state at a fraction of the
+ * GPU's bandwidth, a plan's passes use all of it (below 24 qubits a half, below 22 a quarter of the SMs, so
+ * that several run side by side). Those plans run on eight streams the batch owns, forked from the caller's stream
  * and joined back into it, so all work of an execution is ordered before later work on that stream. For circuit i, <Z_q> lands at zi[zi_off(i) + q] (q < n_i) and
  * <Z_q Z_{q+1}> at zz[zz_off(i) + q] (q < n_i - 1), the offsets being the running sums of n_i and n_i - 1
  * in input order; sums are compensated (float-float per thread, double-double across threads), and the

@@ -15,10 +15,11 @@
 // With a tensor-core precision, circuits of at least batch_tc_min_n qubits (default 20) leave the persistent
 // launch: one cluster streams a state at a fraction of the GPU's bandwidth (about 0.44 TB/s for a 16-CTA
 // cluster on a 24-qubit state, where the whole GPU does 6.5), so each becomes a fused tensor-core plan
-// (6-qubit blocks) enqueued after the launch, its first block generating |0>, its <Z> values reduced on the
-// device into the same output arrays. These plans run on four worker streams forked from the caller's
-// stream and joined back, so that one circuit's pipeline fill and drain overlap another's passes. The whole
-// enqueue is one CUDA graph when replayed.
+// (6-qubit blocks, or up to 7 with FP16X3) enqueued after the launch, its first block generating |0>, its <Z>
+// values reduced on the device into the same output arrays. These plans run on eight worker streams forked
+// from the caller's stream and joined back, so that one circuit's pipeline fill and drain overlap another's
+// passes (the narrower circuits' kernels on a half or a quarter of the SMs, side by side). The whole enqueue
+// is one CUDA graph when replayed.
 #include <cooperative_groups.h>
 
 #include <algorithm>
