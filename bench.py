@@ -53,6 +53,9 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the other configurations' runs after the headline line (N = 1 only)")
+    p.add_argument("--configs-out", default=os.path.join("bench_out", "bench_configs.jsonl"),
+                   help="file (relative to the repository root unless absolute) for the other configurations' "
+                        "full JSON lines; a summary of each goes into the headline line")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--probe-seconds", type=float, default=1.5,
                    help="seconds per operand type of the tensor-core rate probe (0: skip it, no tensor fraction)")
@@ -601,10 +604,10 @@ def run_ours(args):
                 f"{oracle_mod.num_threads()} cores); every path's accuracy line is measured against it")
     if rank == 0 and ws == 1 and not args.no_configs:
         # the other configurations, each in a process of its own after this one's timed region: full lines
-        # to gpurun_out/bench_configs.jsonl, a summary of each in this line
+        # to the --configs-out file, a summary of each in this line
         del st, plans, plan
         torch.cuda.empty_cache()
-        line["configs"] = run_other_configs()
+        line["configs"] = run_other_configs(args.configs_out)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -621,11 +624,11 @@ OTHER_CONFIGS = [
 ]
 
 
-def run_other_configs():
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    os.makedirs(out_dir, exist_ok=True)
+def run_other_configs(out_path):
+    out_path = out_path if os.path.isabs(out_path) else os.path.join(ROOT, out_path)
+    os.makedirs(os.path.dirname(out_path), exist_ok=True)
     summary = {}
-    with open(os.path.join(out_dir, "bench_configs.jsonl"), "w") as f:
+    with open(out_path, "w") as f:
         for wl, extra in OTHER_CONFIGS:
             cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", wl, *extra]
             t = time.perf_counter()
